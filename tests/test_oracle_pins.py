@@ -1,0 +1,524 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, exact identities of a quadratic Hamiltonian,
+brute force on tiny inputs, or published known-answer vectors.  Runs on the
+CPU (no GPU marker).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import zeta
+
+import oracle
+from paper_1901_11350_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10 thermal-noise source (Eq. 4 and the text after it)
+# ----------------------------------------------------------------------------
+def _kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _kat()
+    assert len(rows) == 3
+    for r in rows:
+        assert oracle.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_thermal_normals_statistics():
+    # Eq. 4 text: three independent standard normals per spin and step.
+    z = np.array([oracle.thermal_normals(123, step, 0, i) for step in range(40) for i in range(2500)])
+    n = z.shape[0]
+    assert abs(z.mean()) < 5 / math.sqrt(3 * n)
+    assert np.allclose(z.mean(axis=0), 0, atol=5 / math.sqrt(n))
+    assert np.allclose(z.var(axis=0), 1, atol=0.02)
+    assert np.allclose(((z - z.mean(0)) ** 4).mean(0) / z.var(0) ** 2, 3.0, atol=0.1)
+    c = np.corrcoef(z.T)
+    assert np.abs(c - np.eye(3)).max() < 0.02
+    # different replicas and seeds give different streams
+    a = oracle.thermal_normals(1, 5, 0, 7)
+    assert not np.allclose(a, oracle.thermal_normals(1, 5, 1, 7))
+    assert not np.allclose(a, oracle.thermal_normals(2, 5, 0, 7))
+    assert np.array_equal(a, oracle.thermal_normals(1, 5, 0, 7))
+
+
+# ----------------------------------------------------------------------------
+# Single-spin damped Larmor precession (closed form of Sec. LLG, Fig. 5)
+# ----------------------------------------------------------------------------
+def _larmor_error(solver, dt, t_end=100.0, alpha=0.1, B=1.0, mu=2.0):
+    s = oracle.System(I.square(1, 1, mu_s=mu), dict(B=[0, 0, B]))
+    n = np.array([[1.0, 0.0, 0.0]])
+    err = 0.0
+    g = oracle.GAMMA
+    steps = int(round(t_end / dt))
+    chunk = 100
+    for k0 in range(0, steps, chunk):
+        for k in range(k0 + 1, min(steps, k0 + chunk) + 1):
+            n = s.llg(n, 1, solver=solver, dt=dt, alpha=alpha)
+            t = k * dt
+            nz = math.tanh(alpha * g * B * t / (1 + alpha ** 2))
+            ph = g * B * t / (1 + alpha ** 2)
+            r = math.sqrt(1 - nz * nz)
+            exact = np.array([math.cos(ph) * r, math.sin(ph) * r, nz])
+            err = max(err, float(np.abs(n[0] - exact).max()))
+    return err, n
+
+
+def test_larmor_depondt_matches_paper_error():
+    # Fig. 5: B = 1 T, alpha = 0.1, dt = 10 fs; Depondt error around 3e-7.
+    e1, n = _larmor_error("depondt", 0.01)
+    assert 1e-7 < e1 < 5e-7
+    assert abs(np.linalg.norm(n) - 1) < 1e-14
+    e2, _ = _larmor_error("depondt", 0.005)
+    assert 3.5 < e1 / e2 < 4.5  # second order
+
+
+def test_larmor_heun_matches_paper_error():
+    # Fig. 5 caption: Heun error within 1e-6.
+    e1, _ = _larmor_error("heun", 0.01)
+    assert 3e-7 < e1 < 1e-6
+    e2, _ = _larmor_error("heun", 0.005)
+    assert 3.5 < e1 / e2 < 4.5
+
+
+# ----------------------------------------------------------------------------
+# Geometry: neighbour shells against a brute-force O(N^2) distance scan
+# ----------------------------------------------------------------------------
+def _bond_counts(geometry, radii):
+    r = I.site_positions(geometry)
+    n0, n1, n2 = geometry["n_cells"]
+    per = geometry["periodic"]
+    A = np.asarray(geometry["bravais"], dtype=float) * geometry.get("lattice_constant", 1.0)
+    counts = [0] * len(radii)
+    shifts = [np.zeros(3)]
+    if any(per):
+        # all images within one period in each periodic direction
+        rng = [range(-1, 2) if (per[k] and geometry["n_cells"][k] > 1) else range(0, 1) for k in range(3)]
+        shifts = [a * A[0] * n0 + b * A[1] * n1 + c * A[2] * n2 for a in rng[0] for b in rng[1] for c in rng[2]]
+    for i in range(len(r)):
+        for sh in shifts:
+            d = np.linalg.norm(r[i + 1:] + sh - r[i], axis=1) if not any(per) else \
+                np.linalg.norm(r + sh - r[i], axis=1)
+            for q, R in enumerate(radii):
+                counts[q] += int(np.sum(np.abs(d - R) < 1e-9))
+    if any(per):
+        counts = [c // 2 for c in counts]
+    return counts
+
+
+@pytest.mark.parametrize("case", ["square_open", "hex_open", "sc_periodic"])
+def test_ferromagnet_energy_closed_form(case):
+    if case == "square_open":
+        cfg = I.cfg_square_32()
+        g, h, radii = cfg["geometry"], cfg["hamiltonian"], [1.0]
+    elif case == "hex_open":
+        g = I.hexagonal(13, 9, mu_s=3.0)
+        h = dict(B=[0, 0, 0.7], K=[0.2], Khat=[[0, 0, 1]], J=[1.0, 0.3], dmi_kind="interfacial", D=[0.3])
+        radii = [1.0, math.sqrt(3.0)]
+    else:
+        cfg = I.cfg_sc_128(6)
+        g, h, radii = cfg["geometry"], cfg["hamiltonian"], [1.0, math.sqrt(2.0), math.sqrt(3.0)]
+        h = dict(h, B=[0, 0, 0.4])
+    s = oracle.System(g, h)
+    for q, R in enumerate(radii):
+        assert abs(s.shell_radius(q) - R) < 1e-12
+    bonds = _bond_counts(g, radii)
+    N = s.N
+    mu = g["mu_s"][0]
+    E = -sum(J * nb for J, nb in zip(h["J"], bonds)) - N * h["K"][0] - N * mu * oracle.MU_B * h["B"][2]
+    e = s.energy(I.ferromagnet(N))
+    assert abs(e[0] - E) < 1e-9 * abs(E)
+    assert e[4] == 0.0  # DMI vanishes for a collinear state
+    if case == "square_open":
+        assert bonds == [1984]
+        assert abs(E - (-1984 - 102.4 - 1024 * 2 * oracle.MU_B)) < 1e-9
+
+
+def test_sc_shell_neighbour_counts():
+    s = oracle.System(I.cfg_sc_128(5)["geometry"], I.cfg_sc_128(5)["hamiltonian"])
+    assert s.n_neighbours(0) == 6 + 12 + 8
+    s = oracle.System(I.hexagonal(8, 8, periodic=(True, True)), dict(J=[1.0, 0.5, 0.1]))
+    assert s.n_neighbours(0) == 6 + 6 + 6
+    assert abs(s.shell_radius(2) - 2.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Flat spin spirals E(q) (closed forms for J shells + DMI)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [1, 2, 3, 5])
+def test_spiral_energy_sc_bulk_helix(m):
+    L = 16
+    cfg = I.cfg_sc_128(L)
+    g, h = cfg["geometry"], cfg["hamiltonian"]
+    s = oracle.System(g, h)
+    q = 2 * math.pi * m / L
+    n = I.flat_spiral(I.site_positions(g), [q, 0, 0], [0, 1, 0], [0, 0, 1])
+    J1, J2, J3 = h["J"]
+    D, K = h["D"][0], h["K"][0]
+    Ec = -J1 * (math.cos(q) + 2) - J2 * (4 * math.cos(q) + 2) - 4 * J3 * math.cos(q) - D * math.sin(q) - K / 2
+    assert abs(s.energy(n)[0] / s.N - Ec) < 1e-11
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_spiral_energy_hex_interfacial_cycloid(m):
+    L = 24
+    g = I.hexagonal(L, L, periodic=(True, True))
+    J, D, K = 1.0, 0.3, 0.2
+    s = oracle.System(g, dict(J=[J], dmi_kind="interfacial", D=[D], K=[K], Khat=[[0, 0, 1]]))
+    q = 4 * math.pi * m / L
+    n = I.flat_spiral(I.site_positions(g), [q, 0, 0], [0, 0, 1], [1, 0, 0])
+    half_shell = [(1.0, 0.0), (0.5, math.sqrt(3) / 2), (-0.5, math.sqrt(3) / 2)]
+    Ec = -sum(J * math.cos(q * dx) for dx, _ in half_shell) - D * sum(math.sin(q * dx) * dx for dx, _ in half_shell) - K / 2
+    assert abs(s.energy(n)[0] / s.N - Ec) < 1e-11
+
+
+def test_spiral_square_lattice_minimum():
+    # NN square lattice cycloid: E(q)/N = -J(cos q + 1) - D sin q, minimum at tan q = D/J
+    L = 40
+    g = I.square(L, L, periodic=(True, True))
+    J, D = 1.0, 0.3
+    s = oracle.System(g, dict(J=[J], dmi_kind="interfacial", D=[D]))
+    r = I.site_positions(g)
+    E = []
+    for m in range(0, 8):
+        q = 2 * math.pi * m / L
+        E.append(s.energy(I.flat_spiral(r, [q, 0, 0], [0, 0, 1], [1, 0, 0]))[0] / s.N)
+        assert abs(E[-1] - (-J * (math.cos(q) + 1) - D * math.sin(q))) < 1e-12
+    q_star = math.atan(D / J)
+    assert abs(2 * math.pi * int(np.argmin(E)) / L - q_star) < 2 * math.pi / L
+
+
+# ----------------------------------------------------------------------------
+# Exact identities of a Hamiltonian quadratic in n (Eq. 1 without quadruplets)
+# ----------------------------------------------------------------------------
+def _systems():
+    out = []
+    c = I.cfg_square_32()
+    out.append(("square", dict(c["geometry"], n_cells=[7, 6, 1]), c["hamiltonian"]))
+    c = I.cfg_sc_128(4)
+    out.append(("sc", c["geometry"], dict(c["hamiltonian"], B=[0.3, -0.2, 0.5])))
+    out.append(("hex_dipole", I.hexagonal(6, 5, mu_s=3.0),
+                dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.2], Khat=[[0, 0, 1]], dipole="direct",
+                     B=[0.1, 0, 0.2])))
+    out.append(("two_basis", dict(bravais=[[1, 0, 0], [0.3, 1.1, 0], [0.1, 0.2, 0.9]],
+                                  basis=[[0, 0, 0], [0.4, 0.3, 0.25]], n_cells=[3, 4, 2],
+                                  periodic=[0, 0, 0], lattice_constant=1.7, mu_s=[2.0, 0.8]),
+                dict(J=[1.0, -0.3], dmi_kind="bulk", D=[0.2, 0.05], K=[0.1, 0.3], Khat=[[0, 0, 1], [1, 1, 0]],
+                     dipole="direct", B=[0.3, 0.1, -0.4],
+                     pairs=[(0, 1, (1, 1, 0), 0.4, (0.1, -0.2, 0.3))])))
+    return out
+
+
+@pytest.mark.parametrize("name,g,h", _systems(), ids=[x[0] for x in _systems()])
+def test_gradient_is_exact_finite_difference(name, g, h):
+    s = oracle.System(g, h)
+    n = I.random_spins(s.N, 17)
+    B = s.field(n)
+    rng = np.random.default_rng(5)
+    hstep = 1e-3
+    E0 = abs(s.energy(n)[0]) + 1
+    for _ in range(12):
+        i, k = int(rng.integers(s.N)), int(rng.integers(3))
+        p, m = n.copy(), n.copy()
+        p[i, k] += hstep
+        m[i, k] -= hstep
+        fd = (s.energy(p)[0] - s.energy(m)[0]) / (2 * hstep)
+        # H is a polynomial of degree 2 in R^3N: central differences are exact
+        assert abs(fd + B[i, k]) < 1e-12 * E0 / hstep
+
+
+@pytest.mark.parametrize("name,g,h", _systems(), ids=[x[0] for x in _systems()])
+def test_energy_equals_quadratic_form(name, g, h):
+    s = oracle.System(g, h)
+    n = I.random_spins(s.N, 21)
+    B = s.field(n)
+    mu = np.asarray(g["mu_s"], dtype=float)[np.arange(s.N) % s.n_basis]
+    Bz = mu[:, None] * oracle.MU_B * np.asarray(h.get("B", [0, 0, 0]), dtype=float)[None, :]
+    quad = B - Bz
+    E_quad = -np.sum(n * (Bz + 0.5 * quad))
+    e = s.energy(n)
+    assert abs(e[0] - E_quad) < 1e-12 * (abs(e[0]) + 1)
+    assert abs(e[0] - e[1:].sum()) < 1e-12 * (abs(e[0]) + 1)
+
+
+def test_pair_swap_symmetry():
+    # relabelling i <-> j of an explicit pair (d -> -d, D -> -D) leaves E unchanged
+    g = dict(bravais=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], basis=[[0, 0, 0], [0.5, 0.5, 0]],
+             n_cells=[4, 3, 1], periodic=[1, 0, 0], lattice_constant=1.0, mu_s=[1.0, 2.0])
+    p1 = dict(pairs=[(0, 1, (1, 0, 0), 0.7, (0.1, 0.2, -0.3))])
+    p2 = dict(pairs=[(1, 0, (-1, 0, 0), 0.7, (-0.1, -0.2, 0.3))])
+    n = I.random_spins(24, 3)
+    a = oracle.System(g, p1).energy(n)
+    b = oracle.System(g, p2).energy(n)
+    assert np.allclose(a, b, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Dipole-dipole term (Sec. "Dipolar interactions")
+# ----------------------------------------------------------------------------
+def test_dipole_two_spins_by_hand():
+    # head-to-tail along the bond: E = -2 C mu^2 / r^3; side by side: +C mu^2 / r^3
+    r, mu = 2.5, 1.7
+    g = dict(bravais=[[r, 0, 0], [0, 1, 0], [0, 0, 1]], basis=[[0, 0, 0]], n_cells=[2, 1, 1],
+             periodic=[0, 0, 0], lattice_constant=1.0, mu_s=[mu])
+    s = oracle.System(g, dict(dipole="direct"))
+    C = oracle.C_DIP
+    assert abs(s.energy(np.array([[1.0, 0, 0], [1.0, 0, 0]]))[5] - (-2 * C * mu * mu / r ** 3)) < 1e-15
+    assert abs(s.energy(np.array([[0, 0, 1.0], [0, 0, 1.0]]))[5] - (C * mu * mu / r ** 3)) < 1e-15
+    # the head-to-tail pair is the lower-energy arrangement
+    sf = oracle.System(g, dict(dipole="fft"))
+    assert abs(sf.energy(np.array([[1.0, 0, 0], [1.0, 0, 0]]))[5] - (-2 * C * mu * mu / r ** 3)) < 1e-15
+
+
+@pytest.mark.parametrize("case", ["hex_2d", "two_basis_3d", "square_ragged"])
+def test_dipole_fft_equals_direct_sum(case):
+    # the paper's own check: FFT convolution vs direct summation for random
+    # states with spatially non-symmetric basis cells
+    if case == "hex_2d":
+        g = I.hexagonal(12, 10, mu_s=3.0)
+    elif case == "two_basis_3d":
+        g = dict(bravais=[[1, 0, 0], [0.5, math.sqrt(3) / 2, 0], [0, 0, 1]], basis=[[0, 0, 0], [0.3, 0.1, 0.2]],
+                 n_cells=[6, 5, 3], periodic=[0, 0, 0], lattice_constant=1.3, mu_s=[2.0, 0.7])
+    else:
+        g = I.square(9, 7, mu_s=2.0)
+    s = oracle.System(g, dict(dipole="direct"))
+    n = I.random_spins(s.N, 3)
+    Bd = s.dipole_field(n, "direct")
+    Bf = s.dipole_field(n, "fft")
+    assert np.abs(Bd - Bf).max() < 1e-12 * np.abs(Bd).max()
+    sf = oracle.System(g, dict(dipole="fft"))
+    assert abs(s.energy(n)[5] - sf.energy(n)[5]) < 1e-12 * abs(s.energy(n)[5])
+
+
+def test_dipole_monolayer_converges_to_lattice_sum():
+    # Homogeneously magnetised square monolayer: at the centre of an open
+    # (2R+1)^2 lattice B_z = -C mu^2 S_R with S_R -> S = sum' 1/|r|^3 =
+    # 4 zeta(3/2) beta(3/2) and S - S_R = 4 sqrt(2) / (R + 1/2) + O(R^-3).
+    beta = 4 ** -1.5 * (zeta(1.5, 0.25) - zeta(1.5, 0.75))
+    S = 4 * zeta(1.5) * beta
+    assert abs(S - 9.0336216831) < 1e-9
+    prev = None
+    for R in (8, 16, 32):
+        L = 2 * R + 1
+        s = oracle.System(I.square(L, L, mu_s=1.0), dict(dipole="fft"))
+        B = s.dipole_field(I.ferromagnet(s.N), "fft")
+        c = R + L * R
+        val = -B[c, 2] / oracle.C_DIP
+        assert abs(B[c, 0]) < 1e-12 and abs(B[c, 1]) < 1e-12
+        assert abs(val + 4 * math.sqrt(2) / (R + 0.5) - S) < 0.2 / R ** 2
+        if prev is not None:
+            assert abs(S - val) < 0.55 * abs(S - prev)  # error ~ 1/R
+        prev = val
+
+
+# ----------------------------------------------------------------------------
+# LLG invariants
+# ----------------------------------------------------------------------------
+def test_llg_unit_length_and_damped_energy_decrease():
+    c = I.cfg_square_32()
+    g = dict(c["geometry"], n_cells=[10, 9, 1])
+    s = oracle.System(g, c["hamiltonian"])
+    n = I.random_spins(s.N, 0)
+    E = [s.energy(n)[0]]
+    for _ in range(20):
+        n = s.llg(n, 10, solver="depondt", dt=2e-3, alpha=0.3)
+        E.append(s.energy(n)[0])
+        assert np.abs(np.linalg.norm(n, axis=1) - 1).max() < 1e-14
+    assert all(b < a for a, b in zip(E, E[1:]))
+    n2 = I.random_spins(s.N, 0)
+    for _ in range(20):
+        n2 = s.llg(n2, 10, solver="heun", dt=2e-3, alpha=0.3)
+        assert np.abs(np.linalg.norm(n2, axis=1) - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("solver", ["depondt", "heun"])
+def test_llg_energy_drift_second_order_at_zero_damping(solver):
+    c = I.cfg_square_32()
+    g = dict(c["geometry"], n_cells=[8, 8, 1])
+    s = oracle.System(g, c["hamiltonian"])
+    n0 = I.random_spins(s.N, 4)
+    E0 = s.energy(n0)[0]
+    # at alpha = 0 the energy is conserved by the flow; the integrators'
+    # drift (max over the run) must fall at least like dt^2 (Depondt's is
+    # observed to fall like dt^3)
+    drift = []
+    for dt in (0.005, 0.0025):
+        n, mx = n0.copy(), 0.0
+        for _ in range(int(round(0.5 / dt / 10))):
+            n = s.llg(n, 10, solver=solver, dt=dt, alpha=0.0)
+            mx = max(mx, abs(s.energy(n)[0] - E0))
+        drift.append(mx)
+    assert drift[0] / drift[1] > 3.5
+    assert drift[0] < 1e-3
+
+
+@pytest.mark.parametrize("solver", ["heun", "depondt"])
+def test_langevin_macrospin_equilibrium(solver):
+    # independent spins in a field: <n_z> = coth(x) - 1/x, x = mu B / (kB T)
+    mu, B, x = 1.0, 1.0, 1.0
+    T = mu * oracle.MU_B * B / (oracle.K_B * x)
+    s = oracle.System(I.square(40, 25, mu_s=mu), dict(B=[0, 0, B]))
+    n = I.random_spins(s.N, 11)
+    dt, alpha = 0.05, 0.5
+    n = s.llg(n, 400, solver=solver, dt=dt, alpha=alpha, T=T, seed=7)
+    acc = []
+    for k in range(60):
+        n = s.llg(n, 50, solver=solver, dt=dt, alpha=alpha, T=T, seed=7, step0=400 + 50 * k)
+        acc.append(n[:, 2].mean())
+    L = 1 / math.tanh(x) - 1 / x
+    assert abs(np.mean(acc) - L) < 0.012
+
+
+def test_thermal_run_is_reproducible_and_seeded():
+    s = oracle.System(I.square(5, 4, mu_s=2.0), dict(J=[1.0], B=[0, 0, 1.0]))
+    n0 = I.random_spins(s.N, 1)
+    a = s.llg(n0, 20, solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=9)
+    b = s.llg(s.llg(n0, 7, solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=9), 13, solver="heun", dt=1e-3,
+              alpha=0.1, T=10.0, seed=9, step0=7)
+    assert np.array_equal(a, b)  # counter-based: resuming at step0 is bit-exact
+    c = s.llg(n0, 20, solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=10)
+    assert np.abs(a - c).max() > 1e-4
+
+
+# ----------------------------------------------------------------------------
+# Velocity projection minimiser (Appendix D)
+# ----------------------------------------------------------------------------
+def test_vp_relaxes_to_ferromagnet_closed_form():
+    c = I.cfg_square_32()
+    g = dict(c["geometry"], n_cells=[16, 16, 1], periodic=[1, 1, 0])
+    s = oracle.System(g, c["hamiltonian"])
+    N = s.N
+    E_fm = -2 * N * 1.0 - N * 0.1 - N * 2.0 * oracle.MU_B * 1.0
+    n, v, it, mt = s.minimise(I.perturbed(I.ferromagnet(N), 0.1, 3), dt=0.1, tol=1e-10, max_iter=20000)
+    assert mt < 1e-10 and it < 20000
+    assert abs(s.energy(n)[0] - E_fm) < 1e-10 * abs(E_fm)
+
+
+def test_vp_relaxes_perturbed_spiral_back_to_its_energy():
+    # J + DMI, no anisotropy or field: every commensurate flat spiral is stationary
+    L = 40
+    g = dict(I.square(L, 4, periodic=(True, True)))
+    J, D = 1.0, 0.3
+    s = oracle.System(g, dict(J=[J], dmi_kind="interfacial", D=[D]))
+    m = 2  # q = 2 pi m / L closest to atan(D/J)
+    q = 2 * math.pi * m / L
+    n0 = I.flat_spiral(I.site_positions(g), [q, 0, 0], [0, 0, 1], [1, 0, 0])
+    n, v, it, mt = s.minimise(I.perturbed(n0, 0.02, 8), dt=0.1, tol=1e-9, max_iter=50000)
+    assert mt < 1e-9
+    E_exp = s.N * (-J * (math.cos(q) + 1) - D * math.sin(q))
+    assert abs(s.energy(n)[0] - E_exp) < 1e-9 * abs(E_exp)
+
+
+# ----------------------------------------------------------------------------
+# GNEB (Sec. GNEB, Appendix F)
+# ----------------------------------------------------------------------------
+def test_gneb_climbing_image_hits_stoner_wohlfarth_barrier():
+    # single uniaxial spin in a field along the axis: E = -K cos^2 - mu B cos,
+    # saddle at cos = -h, barrier from the metastable state K (1 - h)^2
+    mu, K, B = 2.0, 1.0, 3.0
+    s = oracle.System(I.square(1, 1, mu_s=mu), dict(B=[0, 0, B], K=[K], Khat=[[0, 0, 1]]))
+    h = mu * oracle.MU_B * B / (2 * K)
+    chain = I.slerp_chain(np.array([[0, 0, -1.0]]), np.array([[0, 0, 1.0]]), 9)
+    ch, v, E, mf, it = s.gneb(chain, n_iter=20000, tol=1e-12, dt=0.5, climbing=True)
+    assert mf < 1e-12
+    assert abs(E.max() - E[0] - K * (1 - h) ** 2) < 1e-12
+    ci = int(np.argmax(E))
+    assert abs(ch[ci, 0, 2] + h) < 1e-10  # at the saddle cos(theta) = -h
+    # without climbing the highest image only brackets the barrier
+    ch2, _, E2, mf2, _ = s.gneb(chain, n_iter=20000, tol=1e-12, dt=0.5, climbing=False)
+    assert E2.max() - E2[0] <= K * (1 - h) ** 2 + 1e-12
+
+
+def test_gneb_images_equidistant_without_climbing():
+    mu, K, B = 2.0, 1.0, 3.0
+    s = oracle.System(I.square(1, 1, mu_s=mu), dict(B=[0, 0, B], K=[K], Khat=[[0, 0, 1]]))
+    chain = I.slerp_chain(np.array([[0.3, 0, -1.0]]) / np.linalg.norm([0.3, 0, -1]), np.array([[0, 0, 1.0]]), 7)
+    ch, v, E, mf, it = s.gneb(chain, n_iter=40000, tol=1e-11, dt=0.3, climbing=False, k_spring=2.0)
+    _, _, l, _ = s.gneb_forces(ch, climbing=False, k_spring=2.0)
+    assert np.abs(l - l.mean()).max() < 1e-9
+
+
+def _tangent_hessian(s, n, h=1e-5):
+    # 2x2 Hessian of E on the sphere at n by finite differences of the
+    # projected gradient along an orthonormal tangent basis
+    n = n / np.linalg.norm(n)
+    t1 = np.cross(n, [0.3, 0.7, 0.1])
+    t1 /= np.linalg.norm(t1)
+    t2 = np.cross(n, t1)
+    Hm = np.zeros((2, 2))
+    for a, ta in enumerate((t1, t2)):
+        gp = -s.field(((n + h * ta) / np.linalg.norm(n + h * ta))[None])[0]
+        gm = -s.field(((n - h * ta) / np.linalg.norm(n - h * ta))[None])[0]
+        for b, tb in enumerate((t1, t2)):
+            Hm[a, b] = (np.dot(gp, tb) - np.dot(gm, tb)) / (2 * h)
+    # Riemannian correction -(n.grad) I for the embedded sphere
+    g0 = -s.field(n[None])[0]
+    return 0.5 * (Hm + Hm.T) - np.dot(n, g0) * np.eye(2)
+
+
+def test_gneb_gaussian_landscape_saddle():
+    # Appendix G landscape (Fig. 7): the climbing image converges onto a
+    # first-order saddle point found independently by Newton iteration.
+    G = np.loadtxt(os.path.join(GOLDEN, "gaussian_landscape.txt"))
+    assert G.shape == (7, 5)
+    s = oracle.System(I.square(1, 1, mu_s=1.0), dict(gauss=G.tolist()))
+    a = np.array([[-0.1906, -0.0058, -0.9816]])
+    b = np.array([[0.9859, -0.1633, -0.0367]])
+    a, _, _, ta = s.minimise(a / np.linalg.norm(a), dt=0.05, tol=1e-13, max_iter=100000)
+    b, _, _, tb = s.minimise(b / np.linalg.norm(b), dt=0.05, tol=1e-13, max_iter=100000)
+    assert ta < 1e-13 and tb < 1e-13
+    for m in (a, b):
+        assert np.all(np.linalg.eigvalsh(_tangent_hessian(s, m[0])) > 0)  # minima
+    chain = I.slerp_chain(a, b, 15)
+    ch, v, E, mf, it = s.gneb(chain, n_iter=200000, tol=1e-11, dt=0.02, climbing=True, k_spring=0.5)
+    assert mf < 1e-11
+    ci = int(np.argmax(E))
+    x = ch[ci, 0]
+    ev = np.linalg.eigvalsh(_tangent_hessian(s, x))
+    assert ev[0] < 0 < ev[1]  # first-order saddle
+    # Newton on the projected gradient from a perturbed start lands on the same point
+    y = x + np.array([2e-3, -1e-3, 1.5e-3])
+    y /= np.linalg.norm(y)
+    for _ in range(30):
+        t1 = np.cross(y, [0.3, 0.7, 0.1]); t1 /= np.linalg.norm(t1)
+        t2 = np.cross(y, t1)
+        g = -s.field(y[None])[0]
+        gt = np.array([np.dot(g, t1), np.dot(g, t2)])
+        step = np.linalg.solve(_tangent_hessian(s, y, 1e-6), -gt)
+        y = y + step[0] * t1 + step[1] * t2
+        y /= np.linalg.norm(y)
+    assert np.linalg.norm(y - x) < 1e-8
+    assert abs(s.energy(y[None])[0] - E[ci]) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Topological charge (Appendix A)
+# ----------------------------------------------------------------------------
+def test_topological_charge_octant_triangle():
+    # one spherical triangle spanned by x, y, z is an octant: A = 4 pi / 8
+    s = oracle.System(I.hexagonal(2, 2), dict())
+    n = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [0, 1.0, 0]])
+    assert abs(s.topological_charge(n) - 1 / 8) < 1e-15
+
+
+def test_topological_charge_of_skyrmion_and_ferromagnet():
+    L = 32
+    g = I.hexagonal(L, L, periodic=(True, True))
+    s = oracle.System(g, dict())
+    r = I.site_positions(g)
+    centre = r.mean(axis=0)
+    q = s.topological_charge(I.neel_skyrmion(r, centre, 8.0))
+    assert abs(q + 1) < 1e-9
+    assert abs(s.topological_charge(I.ferromagnet(s.N))) < 1e-12
