@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Throughput of the fused effective-field + stochastic LLG hot path.
+
+Workload: 128^3 simple-cubic lattice (2,097,152 spins), periodic; exchange
+shells J1=1.0, J2=-0.2, J3=0.05 meV, bulk DMI D=0.2 meV (first shell),
+K=0.05 meV along z, mu_s=2; random initial spins (seed 1); stochastic Heun at
+T=10 K with the Philox thermal field (seed 1), alpha=0.1, dt=1e-3 ps; FP32.
+One benchmark step = one run of the workload's 10,000 LLG time steps (each
+time step = predictor + corrector kernel).  The spin state (32 MB) is smaller
+than L2, so L2 is flushed (256 MB write) before every timed step, outside the
+step's CUDA-event bracket.
+
+Multi-GPU: replicas only (independent replicas, one per rank, different noise
+streams); the value is the spin-updates of all ranks over the slowest rank.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (one
+LLG time step of the same lattice per benchmark step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LLG spin-updates/s (% of HBM roofline); time to max-torque<1e-6 vs plain"
+UNIT = "spin-updates/s"
+LLG_STEPS = 10000
+# algorithmic bytes per spin and launch (FP32 records of 16 B):
+#   predictor: read n, write predictor state and folded corrector term (3 x 16)
+#   corrector: read predictor state and folded term, write n          (3 x 16)
+BYTES_PER_SPIN = {"llg_predictor": 48, "llg_corrector": 48}
+KERNEL_SOURCES = ["paper_1901_11350_gb300/csrc/field_llg.cu", "paper_1901_11350_gb300/csrc/cubic.cu",
+                  "paper_1901_11350_gb300/csrc/common.cuh"]
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        fp = os.path.join(ROOT, p)
+        if os.path.exists(fp):
+            h.update(open(fp, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    fp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(fp))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        rows = []
+        try:
+            with open(self.out.name) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+        finally:
+            os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(cfg, seconds=12.0, max_steps=64):
+    """The FP64 oracle, as it stands, on the host cores: full lattice, a
+    bounded number of LLG time steps."""
+    import oracle
+    from paper_1901_11350_gb300 import inputs as I
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    o = oracle.System(g, h)
+    n = I.random_spins(o.N, cfg["spin_seed"])
+    kw = dict(solver=r["solver"], dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"])
+    t0 = time.perf_counter()
+    n = o.llg(n, 1, **kw)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(max_steps, int(seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    n = o.llg(n, steps, step0=1, **kw)
+    el = time.perf_counter() - t0
+    return {"value": o.N * steps / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d FP64 stochastic-Heun steps of the full %s lattice (%d spins), %.1f s" % (
+                steps, "x".join(str(x) for x in g["n_cells"]), o.N, el)}
+
+
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1901_11350_gb300 import inputs as I
+    cfg = I.cfg_sc_128()
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    o = oracle.System(g, h)
+    n = I.random_spins(o.N, cfg["spin_seed"])
+    kw = dict(solver=r["solver"], dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"])
+    for k in range(args.warmup):
+        n = o.llg(n, 1, step0=k, **kw)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        n = o.llg(n, 1, step0=args.warmup + k, **kw)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    value = o.N * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["name"], "spins": o.N, "llg_steps_per_bench_step": 1,
+                      "solver": "heun", "T_K": r["T"], "l2": "n/a (host)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": "1 FP64 stochastic-Heun step of the full 128x128x128 lattice per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1901_11350_gb300 import binding as Bd
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+
+    rank, local, world = rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    cfg = I.cfg_sc_128(args.side)
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    S = args.llg_steps
+    ctx = Bd.Context(g, h, "f32")
+    N = ctx.N
+    host0 = torch.zeros((N, 4), dtype=torch.float32)
+    host0[:, :3] = torch.from_numpy(I.random_spins(N, cfg["spin_seed"])).float()
+    host0 = host0.pin_memory()
+    n = host0.to("cuda")
+    kw = dict(solver="heun", dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"], replica=rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    step = 0
+    for k in range(args.warmup):
+        flush.fill_(k & 0xFF)
+        ctx.llg_step(n, S, step0=step, **kw)
+        step += S
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_((k + 1) & 0xFF)
+            ev[k][0].record(st)
+            ctx.llg_step(n, S, step0=step, **kw)
+            ev[k][1].record(st)
+            step += S
+        torch.cuda.synchronize()
+    ctx.profile(False)
+    el_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kern = {}
+    for name in ("llg_predictor", "llg_corrector"):
+        ms, cnt = ctx.profile_read(name)
+        kern[name] = (ms, cnt)
+    t = torch.tensor([el_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    el_ms = t.item()
+    value = world * N * S * args.steps / (el_ms / 1e3)
+    finite = bool(torch.isfinite(n).all().item())
+
+    # end to end through the public API: pinned host state in, state out
+    host_out = torch.empty_like(host0).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(st)
+    for k in range(args.steps):
+        nd = host0.to("cuda", non_blocking=True)
+        ctx.llg_step(nd, S, step0=step, **kw)
+        host_out.copy_(nd, non_blocking=True)
+        step += S
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N * S * args.steps / (t.item() / 1e3)
+
+    peaks, peak_kind = measured_peaks()
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, cnt = kern[dom]
+    avg_s = ms / max(cnt, 1) / 1e3
+    achieved = BYTES_PER_SPIN[dom] * N / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(dom), "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": BYTES_PER_SPIN[dom] * N, "avg_launch_us": avg_s * 1e6,
+            "launches": cnt,
+            "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kern.items()}}
+    clocks = clk.summary()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S, "solver": "heun",
+                      "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+           "gpu_launches": 2 * S * args.steps, "roofline": roof, "clocks": clocks, "finite": finite}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--llg-steps", type=int, default=LLG_STEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * spirit_gb.h -- C ABI of the GB300 (sm_103a) atomistic spin library.
+ *
+ * The library computes the hot path of the atomistic spin method of
+ * "Spirit: Multifunctional Framework for Atomistic Spin Simulations"
+ * (arXiv:1901.11350): the effective field B_eff = -dH/dn of the extended
+ * Heisenberg Hamiltonian (Eq. 1), fused with Landau-Lifshitz-Gilbert time
+ * steps (Eq. 3, Appendix B) with the stochastic thermal field (Eq. 4), the
+ * velocity-projection minimiser (Appendix D) and the geodesic nudged elastic
+ * band force projection (Sec. "Geodesic Nudged Elastic Band Method",
+ * Appendix F).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: energy meV, magnetic field T, moments in Bohr magnetons, time ps,
+ * length Angstrom, angle rad.  Fields returned by the library are B_eff in
+ * meV (energy per unit spin direction).
+ *
+ * Spin buffers are DEVICE pointers owned by the caller, one 4-wide record per
+ * spin: float4 (16 B, 16-byte aligned) for a context created with SP_F32,
+ * double4 (32 B, 32-byte aligned) for SP_F64.  Record i holds (x, y, z, w);
+ * w is ignored on input and written as 0 on output.  Spin index
+ * i = b + n_basis * (c0 + n0 * (c1 + n1 * c2)) for basis atom b in cell
+ * (c0, c1, c2).  Spin directions must have unit length.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Calls are stream-ordered and asynchronous unless stated
+ * otherwise; results in device memory are valid once the stream reaches
+ * them.
+ *
+ * Ownership: the context owns its host-side description of the system and
+ * any device scratch it allocates lazily (predictor states, reduction
+ * partials, FFT grids); creating and configuring a context allocates no
+ * device memory.  Scratch is freed by sp_destroy.  A context may be used by
+ * one host thread at a time; calls on one context must be issued on one
+ * stream at a time because they share its scratch.
+ *
+ * Errors: every call returns SP_OK (0) or a negative SP_ERR_* code, and
+ * sp_last_error() returns a message for the last failure on that context.
+ * Argument errors are detected on the host before anything is launched.
+ */
+#ifndef SPIRIT_GB_H
+#define SPIRIT_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SP_MAX_BASIS 4   /* basis atoms per cell */
+#define SP_MAX_SHELLS 8  /* isotropic neighbour shells */
+#define SP_MAX_NBR 96    /* directed neighbour entries, all basis atoms together */
+
+enum {
+    SP_OK = 0,
+    SP_ERR_ARG = -1,         /* invalid argument or size */
+    SP_ERR_STATE = -2,       /* call out of order (e.g. no geometry yet) */
+    SP_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    SP_ERR_UNSUPPORTED = -4, /* valid request this library does not implement */
+    SP_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    SP_ERR_NAN = -6          /* a non-finite value was detected */
+};
+
+enum { SP_F32 = 0, SP_F64 = 1 };
+enum { SP_DMI_NONE = 0, SP_DMI_BULK = 1, SP_DMI_INTERFACIAL = 2 };
+enum { SP_DIPOLE_NONE = 0, SP_DIPOLE_FFT = 2 };
+enum { SP_DEPONDT = 0, SP_HEUN = 1 };
+
+typedef struct sp_ctx sp_ctx;
+
+/* One unique interacting pair <ij> of Eq. 1: basis atom i of cell c with
+ * basis atom j of cell c + d, exchange J (meV) and DMI vector D_ij (meV).
+ * The library adds the reverse bond with D_ji = -D_ij. */
+typedef struct {
+    int i, j;
+    int d[3];
+    double J;
+    double D[3];
+} sp_pair;
+
+/* The extended Heisenberg Hamiltonian of Eq. 1 (quadruplets excluded).
+ * Exchange and DMI may be given by neighbour shells (distinct bond lengths,
+ * nearest first), by explicit pairs, or both.  DMI vectors of a shell:
+ * SP_DMI_BULK: D_ij = D rhat_ij; SP_DMI_INTERFACIAL: D_ij = D (z x rhat_ij),
+ * rhat_ij the unit bond vector from i to j. */
+typedef struct {
+    double B[3];                    /* external field, T */
+    double K[SP_MAX_BASIS];         /* uniaxial anisotropy per basis atom, meV */
+    double Khat[SP_MAX_BASIS][3];   /* anisotropy axes (normalised on use) */
+    int n_shells;                   /* exchange shells, 0..SP_MAX_SHELLS */
+    double J[SP_MAX_SHELLS];        /* exchange per unique pair and shell, meV */
+    int dmi_kind;                   /* SP_DMI_* */
+    int n_dmi_shells;               /* shells carrying DMI, 0..SP_MAX_SHELLS */
+    double D[SP_MAX_SHELLS];        /* DMI magnitude per shell, meV */
+    int dipole;                     /* SP_DIPOLE_NONE or SP_DIPOLE_FFT */
+    int n_pairs;                    /* explicit unique pairs in `pairs` */
+    const sp_pair *pairs;           /* host array, copied by the call */
+} sp_hamiltonian;
+
+/* LLG run parameters (Eq. 3, Eq. 4, Appendix B). */
+typedef struct {
+    int solver;        /* SP_DEPONDT or SP_HEUN */
+    double dt;         /* time step, ps (> 0) */
+    double alpha;      /* Gilbert damping (>= 0) */
+    double T;          /* temperature, K (>= 0); 0 switches the thermal field off */
+    uint64_t seed;     /* Philox4x32-10 key of the thermal field */
+    uint64_t step0;    /* step counter of the first step (resume = same seed, later step0) */
+    uint32_t replica;  /* replica index; selects an independent noise stream */
+} sp_llg_params;
+
+/* GNEB parameters (Sec. GNEB, Appendix D, Appendix F). */
+typedef struct {
+    double dt;         /* velocity-projection time step (> 0) */
+    double mass;       /* fictitious mass (> 0) */
+    double k_spring;   /* spring constant, meV/rad^2 */
+    int climbing;      /* 1: the highest-energy interior image climbs (re-chosen each iteration) */
+} sp_gneb_params;
+
+/* ------------------------------------------------------------------------
+ * Context life cycle
+ * ------------------------------------------------------------------------ */
+
+/* Create a context computing in `precision` (SP_F32 or SP_F64) on the
+ * current CUDA device.  Allocates host memory only. */
+int sp_create(sp_ctx **out, int precision);
+/* Destroy a context and free its device scratch (synchronises the device
+ * first).  NULL is accepted. */
+int sp_destroy(sp_ctx *ctx);
+/* Message of the last error on ctx (owned by ctx, valid until the next call
+ * on it); a static string for ctx == NULL. */
+const char *sp_last_error(const sp_ctx *ctx);
+
+/* Geometry (Sec. "Hamiltonian": arbitrary Bravais vectors and basis cells,
+ * open or periodic boundaries per direction).
+ *   bravais[9]     row-major 3x3, row k = lattice vector a_k in units of
+ *                  lattice_constant (host pointer)
+ *   n_basis        1..SP_MAX_BASIS basis atoms
+ *   basis[3*n_basis] fractional coordinates of the basis atoms
+ *   n_cells[3]     cells per direction (>= 1); N = n_basis*n0*n1*n2 < 2^31
+ *   periodic[3]    0 open, 1 periodic
+ *   lattice_constant  Angstrom (> 0)
+ *   mu_s[n_basis]  moments in Bohr magnetons (> 0)
+ * Resets any Hamiltonian set before. */
+int sp_set_geometry(sp_ctx *ctx, const double *bravais, int n_basis, const double *basis,
+                    const int *n_cells, const int *periodic, double lattice_constant,
+                    const double *mu_s);
+
+/* Hamiltonian (Eq. 1).  Builds the directed neighbour stencil on the host:
+ * shells are the distinct bond lengths of the infinite lattice, nearest
+ * first; across an open boundary a neighbour is absent.  SP_ERR_ARG for more
+ * than SP_MAX_NBR directed entries; SP_ERR_UNSUPPORTED for the dipole term
+ * with a periodic direction of more than one cell. */
+int sp_set_hamiltonian(sp_ctx *ctx, const sp_hamiltonian *h);
+
+/* Number of spins N. */
+int sp_n_spins(const sp_ctx *ctx, int *n);
+
+/* ------------------------------------------------------------------------
+ * Field, gradient and energy (Eq. 1)
+ * ------------------------------------------------------------------------ */
+
+/* B_dev[i] = B_eff,i = -dH/dn_i (meV) for the spins n_dev (N records each,
+ * 4-wide, w written 0).  n_dev and B_dev must not overlap. */
+int sp_effective_field(sp_ctx *ctx, const void *n_dev, void *B_dev, void *stream);
+
+/* grad_dev[i] = dH/dn_i = -B_eff,i (embedding-space gradient, meV). */
+int sp_gradient(sp_ctx *ctx, const void *n_dev, void *grad_dev, void *stream);
+
+/* Energies of Eq. 1 written to e_dev (DEVICE, 6 doubles): total, Zeeman,
+ * anisotropy, exchange, DMI, dipole-dipole (meV).  Accumulated in FP64 in a
+ * fixed order (bitwise reproducible for a given N and launch shape). */
+int sp_energy(sp_ctx *ctx, const void *n_dev, double *e_dev, void *stream);
+
+/* max_i |n_i x B_eff,i| (meV) written to torque_dev (DEVICE, 1 double). */
+int sp_max_torque(sp_ctx *ctx, const void *n_dev, double *torque_dev, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Time stepping (Eq. 3, Eq. 4, Appendix B)
+ * ------------------------------------------------------------------------ */
+
+/* n_steps LLG steps on n_dev in place.
+ * dn/dt = n x A, A_i = -gamma/((1+alpha^2) mu_i) (B_i + alpha n_i x B_i),
+ * B_i = B_eff,i + B_th,i with B_th,i = sqrt(2 alpha kB T mu_i / (gamma dt)) eta_i
+ * and eta_i three standard normals from Philox4x32-10 (key = seed, counter =
+ * (i, step mod 2^32, step div 2^32, 8*replica)), Box-Muller on
+ * (u0,u1) -> eta_x, eta_y and (u2,u3) -> eta_z, u = (x + 1/2) 2^-32; the same
+ * eta in both stages of a step.  Heun renormalises predictor and result;
+ * Depondt rotates by |A| dt about -A (Rodrigues).  Allocates the context's
+ * predictor scratch (2 records per spin) on first use. */
+int sp_llg_step(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Energy minimisation (Appendix D)
+ * ------------------------------------------------------------------------ */
+
+/* Velocity-projection minimisation of n_dev in place, velocities v_dev
+ * (same layout, caller-owned, carried in and out; zero them to start).
+ * Force F_i = B_i - (B_i.n_i) n_i.  Iteration: n <- normalise(n + dt v +
+ * dt^2/(2m) F); F' = F(n); v <- v + dt/(2m)(F + F'); v <- (v.F' > 0) ?
+ * (v.F')F'/|F'|^2 : 0 (3N-dimensional dot products).  Stops when
+ * max_i |F_i| < tol or after max_iter iterations; convergence is tested on
+ * the device, and the host waits for the stream every `check_every`
+ * iterations (so this call synchronises `stream`).  *iters and *max_torque
+ * are host outputs. */
+int sp_minimise(sp_ctx *ctx, void *n_dev, void *v_dev, double dt, double mass, double tol,
+                int max_iter, int check_every, int *iters, double *max_torque, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Geodesic nudged elastic band (Sec. GNEB, Appendix F)
+ * ------------------------------------------------------------------------ */
+
+/* n_iter GNEB iterations with the velocity-projection optimiser on a chain of
+ * n_images >= 3 images, chain_dev = n_images x N records (image-major),
+ * vel_dev the same layout (caller-owned, carried in and out).  Endpoints are
+ * never moved.  Per iteration: energies E_v; improved tangent (Henkelman and
+ * Jonsson 2000) from the neighbouring images, projected per spin onto the
+ * tangent space and normalised in 3N dimensions; geodesic distances
+ * l = sqrt(sum_i theta_i^2); forces F = -Pg + (Pg.tau)tau +
+ * k (l_{v,v+1} - l_{v-1,v}) tau, and for the climbing image
+ * F = -Pg + 2 (Pg.tau) tau, Pg the tangent-space projection of dH/dn.
+ * The force is re-evaluated at the start of each call (no hidden state).
+ * Outputs (DEVICE): energies_dev[n_images] (meV, FP64), max_force_dev[1] =
+ * max over interior images and spins of |F_v,i| after the last iteration. */
+int sp_gneb_step(sp_ctx *ctx, void *chain_dev, void *vel_dev, int n_images, const sp_gneb_params *p,
+                 int n_iter, double *energies_dev, double *max_force_dev, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (tracing aid, not part of the method)
+ * ------------------------------------------------------------------------ */
+
+enum { SP_PROF_LLG_PREDICTOR = 0, SP_PROF_LLG_CORRECTOR = 1, SP_PROF_DIPOLE = 2, SP_PROF_KINDS = 3 };
+
+/* on != 0: from now on every launch of the LLG predictor and corrector
+ * kernels and of the dipole field pipeline is bracketed by a pair of CUDA
+ * events recorded on its stream (off by default; do not enable while
+ * capturing a CUDA graph).  Events are recycled from a pool of 4096 pairs,
+ * waiting for the oldest when the pool is full. */
+int sp_profile_enable(sp_ctx *ctx, int on);
+/* Waits for all recorded events, then returns the summed device time (ms)
+ * and the number of launches of kernel class `kind` since the last read of
+ * that class, and resets them.  Host outputs. */
+int sp_profile_read(sp_ctx *ctx, int kind, double *total_ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,241 @@
+"""Thin Python binding of ``libspirit_gb.so`` (include/spirit_gb.h).
+
+Argument marshalling only: tensors are checked for device, dtype, shape and
+contiguity, and their device pointers are passed to the C ABI together with
+torch's current CUDA stream.  Every step of the computation runs in the
+library's CUDA kernels; there is no CPU path.  The library must have been
+built (``paper_1901_11350_gb300.build.build()``); loading fails loudly
+otherwise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MAX_BASIS = 4
+MAX_SHELLS = 8
+F32, F64 = 0, 1
+DMI = {"none": 0, "bulk": 1, "interfacial": 2}
+DIPOLE = {"none": 0, "fft": 2}
+SOLVER = {"depondt": 0, "heun": 1}
+ERRORS = {-1: "SP_ERR_ARG", -2: "SP_ERR_STATE", -3: "SP_ERR_CUDA", -4: "SP_ERR_UNSUPPORTED",
+          -5: "SP_ERR_TIMEOUT", -6: "SP_ERR_NAN"}
+
+
+class SpinError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Pair(C.Structure):
+    _fields_ = [("i", C.c_int), ("j", C.c_int), ("d", C.c_int * 3), ("J", C.c_double), ("D", C.c_double * 3)]
+
+
+class Hamiltonian(C.Structure):
+    _fields_ = [("B", C.c_double * 3), ("K", C.c_double * MAX_BASIS), ("Khat", (C.c_double * 3) * MAX_BASIS),
+                ("n_shells", C.c_int), ("J", C.c_double * MAX_SHELLS), ("dmi_kind", C.c_int),
+                ("n_dmi_shells", C.c_int), ("D", C.c_double * MAX_SHELLS), ("dipole", C.c_int),
+                ("n_pairs", C.c_int), ("pairs", C.POINTER(Pair))]
+
+
+class LLGParams(C.Structure):
+    _fields_ = [("solver", C.c_int), ("dt", C.c_double), ("alpha", C.c_double), ("T", C.c_double),
+                ("seed", C.c_uint64), ("step0", C.c_uint64), ("replica", C.c_uint32)]
+
+
+class GNEBParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("k_spring", C.c_double), ("climbing", C.c_int)]
+
+
+_lib = None
+
+# every entry point of include/spirit_gb.h with its ctypes signature
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+SIGNATURES = {
+    "sp_create": (_i, [C.POINTER(_vp), _i]),
+    "sp_destroy": (_i, [_vp]),
+    "sp_last_error": (C.c_char_p, [_vp]),
+    "sp_set_geometry": (_i, [_vp, C.POINTER(_d), _i, C.POINTER(_d), C.POINTER(_i), C.POINTER(_i), _d, C.POINTER(_d)]),
+    "sp_set_hamiltonian": (_i, [_vp, C.POINTER(Hamiltonian)]),
+    "sp_n_spins": (_i, [_vp, C.POINTER(_i)]),
+    "sp_effective_field": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_gradient": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_energy": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_max_torque": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_llg_step": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
+    "sp_minimise": (_i, [_vp, _vp, _vp, _d, _d, _d, _i, _i, C.POINTER(_i), C.POINTER(_d), _vp]),
+    "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_profile_enable": (_i, [_vp, _i]),
+    "sp_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(C.c_longlong)]),
+}
+PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the C-ABI library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing: build it with "
+                               "paper_1901_11350_gb300.build.build() (nvcc, sm_103a)" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A lattice + Hamiltonian on the GPU, computing in FP32 or FP64."""
+
+    def __init__(self, geometry, hamiltonian, precision="f32"):
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        L = lib()
+        self._h = C.c_void_p()
+        rc = L.sp_create(C.byref(self._h), F32 if precision == "f32" else F64)
+        if rc:
+            raise SpinError(rc, "sp_create")
+        g = geometry
+        brav = np.ascontiguousarray(np.asarray(g["bravais"], dtype=np.float64).reshape(9))
+        basis = np.ascontiguousarray(np.asarray(g.get("basis", [[0, 0, 0]]), dtype=np.float64))
+        nb = basis.shape[0]
+        mu = np.ascontiguousarray(np.broadcast_to(np.asarray(g["mu_s"], dtype=np.float64), (nb,)).copy())
+        nc = (C.c_int * 3)(*[int(x) for x in g["n_cells"]])
+        per = (C.c_int * 3)(*[int(bool(x)) for x in g["periodic"]])
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(L.sp_set_geometry(self._h, dp(brav), nb, dp(basis.reshape(-1)), nc, per,
+                                      float(g.get("lattice_constant", 1.0)), dp(mu)))
+        h = hamiltonian
+        H = Hamiltonian()
+        for k, v in enumerate(h.get("B", [0, 0, 0])):
+            H.B[k] = float(v)
+        K = np.broadcast_to(np.asarray(h.get("K", 0.0), dtype=np.float64), (nb,))
+        Kh = np.broadcast_to(np.asarray(h.get("Khat", [0, 0, 1]), dtype=np.float64), (nb, 3))
+        for b in range(nb):
+            H.K[b] = float(K[b])
+            for k in range(3):
+                H.Khat[b][k] = float(Kh[b, k])
+        J = list(h.get("J", []))
+        H.n_shells = len(J)
+        for q, v in enumerate(J):
+            H.J[q] = float(v)
+        H.dmi_kind = DMI[h.get("dmi_kind", "none")]
+        D = list(h.get("D", []))
+        H.n_dmi_shells = len(D)
+        for q, v in enumerate(D):
+            H.D[q] = float(v)
+        H.dipole = DIPOLE[h.get("dipole", "none")]
+        pairs = list(h.get("pairs", []))
+        self._pairs = (Pair * max(1, len(pairs)))()
+        for q, (i, j, d, Jp, Dp) in enumerate(pairs):
+            self._pairs[q].i, self._pairs[q].j, self._pairs[q].J = int(i), int(j), float(Jp)
+            for k in range(3):
+                self._pairs[q].d[k] = int(d[k])
+                self._pairs[q].D[k] = float(Dp[k])
+        H.n_pairs = len(pairs)
+        H.pairs = C.cast(self._pairs, C.POINTER(Pair))
+        self._check(L.sp_set_hamiltonian(self._h, C.byref(H)))
+        n = C.c_int()
+        self._check(L.sp_n_spins(self._h, C.byref(n)))
+        self.N = n.value
+
+    def _check(self, rc):
+        if rc:
+            raise SpinError(rc, lib().sp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    # ------------------------------------------------------------ buffers
+    def spins(self, arr, device="cuda"):
+        """(N, 3) or (M, N, 3) array -> contiguous 4-wide device tensor."""
+        a = torch.as_tensor(np.asarray(arr, dtype=np.float64))
+        out = torch.zeros(a.shape[:-1] + (4,), dtype=self.dtype)
+        out[..., :3] = a[..., :3].to(self.dtype)
+        return out.to(device)
+
+    def _spin_arg(self, t, name, images=None):
+        shape = (self.N, 4) if images is None else (images, self.N, 4)
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and tuple(t.shape) == shape
+                and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA %s tensor of shape %s" % (name, self.dtype, shape))
+        return _ptr(t)
+
+    # ------------------------------------------------------------ calls
+    def effective_field(self, n, out=None):
+        out = torch.empty_like(n) if out is None else out
+        self._check(lib().sp_effective_field(self._h, self._spin_arg(n, "n"), self._spin_arg(out, "out"), _stream()))
+        return out
+
+    def gradient(self, n, out=None):
+        out = torch.empty_like(n) if out is None else out
+        self._check(lib().sp_gradient(self._h, self._spin_arg(n, "n"), self._spin_arg(out, "out"), _stream()))
+        return out
+
+    def energy(self, n, out=None):
+        """Device tensor of 6 doubles: total, Zeeman, anisotropy, exchange, DMI, dipole (meV)."""
+        out = torch.empty(6, dtype=torch.float64, device=n.device) if out is None else out
+        self._check(lib().sp_energy(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
+        return out
+
+    def max_torque(self, n, out=None):
+        out = torch.empty(1, dtype=torch.float64, device=n.device) if out is None else out
+        self._check(lib().sp_max_torque(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
+        return out
+
+    def llg_step(self, n, n_steps=1, solver="depondt", dt=1e-3, alpha=0.1, T=0.0, seed=0, step0=0, replica=0):
+        p = LLGParams(SOLVER[solver], float(dt), float(alpha), float(T), int(seed), int(step0), int(replica))
+        self._check(lib().sp_llg_step(self._h, self._spin_arg(n, "n"), C.byref(p), int(n_steps), _stream()))
+        return n
+
+    def minimise(self, n, v, dt=0.1, mass=1.0, tol=1e-6, max_iter=10000, check_every=64):
+        it = C.c_int()
+        mt = C.c_double()
+        self._check(lib().sp_minimise(self._h, self._spin_arg(n, "n"), self._spin_arg(v, "v"), float(dt), float(mass),
+                                      float(tol), int(max_iter), int(check_every), C.byref(it), C.byref(mt),
+                                      _stream()))
+        return it.value, mt.value
+
+    def profile(self, on=True):
+        self._check(lib().sp_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self, kind):
+        """(summed device ms, launches) of a kernel class since the last read."""
+        ms, n = C.c_double(), C.c_longlong()
+        self._check(lib().sp_profile_read(self._h, PROFILE_KINDS[kind], C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def gneb_step(self, chain, vel, n_iter=1, k_spring=1.0, climbing=True, dt=0.1, mass=1.0, energies=None,
+                  max_force=None):
+        M = chain.shape[0]
+        E = torch.empty(M, dtype=torch.float64, device=chain.device) if energies is None else energies
+        F = torch.empty(1, dtype=torch.float64, device=chain.device) if max_force is None else max_force
+        p = GNEBParams(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+        self._check(lib().sp_gneb_step(self._h, self._spin_arg(chain, "chain", M), self._spin_arg(vel, "vel", M), M,
+                                       C.byref(p), int(n_iter), _ptr(E), _ptr(F), _stream()))
+        return E, F

@@ -1,0 +1,623 @@
+// api.cu -- the C ABI declared in include/spirit_gb.h: contexts, the host-side
+// neighbour-stencil builder and the dispatch of every call to its kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "dipole.h"
+#include "minimise.h"
+
+using namespace spgb;
+
+namespace {
+
+struct HostNbr {
+    int b, jb, d[3];
+    double J, D[3];
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Pool of CUDA event pairs bracketing kernel launches (sp_profile_*).
+struct Profiler {
+    static constexpr int kPairs = 4096;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per pair
+    std::vector<int> kind;
+    int used = 0;
+    double ms[SP_PROF_KINDS] = {0, 0, 0};
+    long long count[SP_PROF_KINDS] = {0, 0, 0};
+
+    cudaError_t drain()
+    {
+        for (int p = 0; p < used; ++p) {
+            cudaError_t e = cudaEventSynchronize(ev[2 * p + 1]);
+            if (e != cudaSuccess) return e;
+            float t = 0;
+            e = cudaEventElapsedTime(&t, ev[2 * p], ev[2 * p + 1]);
+            if (e != cudaSuccess) return e;
+            ms[kind[p]] += t;
+            count[kind[p]] += 1;
+        }
+        used = 0;
+        return cudaSuccess;
+    }
+    // returns the pair index to record into, or -1 when profiling is off
+    int begin(int k, cudaStream_t st)
+    {
+        if (!on) return -1;
+        if (ev.empty()) {
+            ev.resize(2 * kPairs);
+            kind.resize(kPairs);
+            for (auto &e : ev) cudaEventCreate(&e);
+        }
+        if (used == kPairs && drain() != cudaSuccess) return -1;
+        int p = used++;
+        kind[p] = k;
+        cudaEventRecord(ev[2 * p], st);
+        return p;
+    }
+    void end(int p, cudaStream_t st)
+    {
+        if (p >= 0) cudaEventRecord(ev[2 * p + 1], st);
+    }
+    ~Profiler()
+    {
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct sp_ctx {
+    int prec = SP_F32;
+    int device = 0;
+    std::string err;
+    bool have_geom = false, have_ham = false;
+    // geometry
+    double A[3][3] = {};
+    int nb = 1;
+    double basis[SP_MAX_BASIS][3] = {};
+    int nc[3] = {1, 1, 1}, per[3] = {0, 0, 0};
+    double a = 1.0;
+    double mu_s[SP_MAX_BASIS] = {};
+    int N = 0;
+    // Hamiltonian
+    sp_hamiltonian h = {};
+    std::vector<sp_pair> pairs;
+    std::vector<HostNbr> nbr;
+    Stencil<float> Sf = {};
+    Stencil<double> Sd = {};
+    // device scratch (allocated on first use)
+    DevBuf pred;      // 2 records per spin: predictor state and folded corrector term
+    DevBuf partials;  // reduction partials
+    DevBuf bdd;       // dipole field, 1 record per spin
+    DipolePlan *dip = nullptr;
+    MinScratch *mins = nullptr;
+    Profiler prof;
+};
+
+namespace {
+
+int fail(sp_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(sp_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, SP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ensure(sp_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes && b.p) return SP_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaFree");
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc of context scratch");
+    b.bytes = bytes;
+    return SP_OK;
+}
+
+size_t rec_bytes(const sp_ctx *c) { return c->prec == SP_F64 ? sizeof(dq4) : sizeof(float4); }
+
+void bond(const sp_ctx *c, int b, int jb, const int d[3], double r[3])
+{
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = d[k] + c->basis[jb][k] - c->basis[b][k];
+    for (int l = 0; l < 3; ++l) r[l] = c->a * (x[0] * c->A[0][l] + x[1] * c->A[1][l] + x[2] * c->A[2][l]);
+}
+
+// Directed neighbour stencil: shells are the distinct bond lengths found in a
+// box of cells around every basis atom; each unique pair appears once from
+// each side (D_ji = -D_ij); zero entries are dropped.
+int build_stencil(sp_ctx *c)
+{
+    const sp_hamiltonian &h = c->h;
+    int n_sh = h.n_shells;
+    int n_dm = h.dmi_kind == SP_DMI_NONE ? 0 : h.n_dmi_shells;
+    int n_need = std::max(n_sh, n_dm);
+    c->nbr.clear();
+    if (n_need > 0) {
+        int R[3];
+        for (int k = 0; k < 3; ++k) R[k] = c->nc[k] > 1 ? n_need + 2 : 0;
+        struct Cand {
+            double len;
+            int b, jb, d[3];
+        };
+        std::vector<Cand> cand;
+        for (int b = 0; b < c->nb; ++b)
+            for (int jb = 0; jb < c->nb; ++jb)
+                for (int d0 = -R[0]; d0 <= R[0]; ++d0)
+                    for (int d1 = -R[1]; d1 <= R[1]; ++d1)
+                        for (int d2 = -R[2]; d2 <= R[2]; ++d2) {
+                            int d[3] = {d0, d1, d2};
+                            double r[3];
+                            bond(c, b, jb, d, r);
+                            double len = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                            if (len < 1e-8 * c->a) continue;
+                            cand.push_back({len, b, jb, {d0, d1, d2}});
+                        }
+        std::vector<double> lens;
+        for (auto &x : cand) lens.push_back(x.len);
+        std::sort(lens.begin(), lens.end());
+        std::vector<double> shells;
+        for (double l : lens)
+            if ((int)shells.size() < n_need && (shells.empty() || l - shells.back() > 1e-8 * c->a)) shells.push_back(l);
+        for (auto &x : cand) {
+            int s = -1;
+            for (int q = 0; q < (int)shells.size(); ++q)
+                if (std::fabs(shells[q] - x.len) <= 1e-8 * c->a) s = q;
+            if (s < 0) continue;
+            HostNbr e{};
+            e.b = x.b;
+            e.jb = x.jb;
+            for (int k = 0; k < 3; ++k) e.d[k] = x.d[k];
+            e.J = s < n_sh ? h.J[s] : 0.0;
+            if (s < n_dm) {
+                double r[3];
+                bond(c, x.b, x.jb, x.d, r);
+                double u[3] = {r[0] / x.len, r[1] / x.len, r[2] / x.len};
+                if (h.dmi_kind == SP_DMI_BULK) {
+                    for (int k = 0; k < 3; ++k) e.D[k] = h.D[s] * u[k];
+                } else {  // z x rhat
+                    e.D[0] = -h.D[s] * u[1];
+                    e.D[1] = h.D[s] * u[0];
+                    e.D[2] = 0.0;
+                }
+            }
+            if (e.J == 0.0 && e.D[0] == 0.0 && e.D[1] == 0.0 && e.D[2] == 0.0) continue;
+            c->nbr.push_back(e);
+        }
+    }
+    for (const sp_pair &p : c->pairs) {
+        HostNbr e{}, r{};
+        e.b = p.i;
+        e.jb = p.j;
+        r.b = p.j;
+        r.jb = p.i;
+        for (int k = 0; k < 3; ++k) {
+            e.d[k] = p.d[k];
+            r.d[k] = -p.d[k];
+            e.D[k] = p.D[k];
+            r.D[k] = -p.D[k];
+        }
+        e.J = r.J = p.J;
+        c->nbr.push_back(e);
+        c->nbr.push_back(r);
+    }
+    if ((int)c->nbr.size() > SP_MAX_NBR)
+        return fail(c, SP_ERR_ARG, "%d directed neighbour entries exceed SP_MAX_NBR=%d", (int)c->nbr.size(), SP_MAX_NBR);
+    for (auto &e : c->nbr)
+        for (int k = 0; k < 3; ++k)
+            if (c->per[k] && std::abs(e.d[k]) > c->nc[k])
+                return fail(c, SP_ERR_UNSUPPORTED, "bond offset %d exceeds the periodic extent %d", e.d[k], c->nc[k]);
+    std::stable_sort(c->nbr.begin(), c->nbr.end(), [](const HostNbr &x, const HostNbr &y) { return x.b < y.b; });
+    return SP_OK;
+}
+
+template <typename T> void fill_stencil(const sp_ctx *c, Stencil<T> &S)
+{
+    memset(&S, 0, sizeof S);
+    S.nb = c->nb;
+    S.n0 = c->nc[0];
+    S.n1 = c->nc[1];
+    S.n2 = c->nc[2];
+    S.per0 = c->per[0];
+    S.per1 = c->per[1];
+    S.per2 = c->per[2];
+    S.N = c->N;
+    for (int b = 0; b < c->nb; ++b) {
+        double mu = c->mu_s[b] * kMuB;
+        S.mu[b] = (T)mu;
+        for (int k = 0; k < 3; ++k) S.Bz[b][k] = (T)(mu * c->h.B[k]);
+        S.K[b] = (T)c->h.K[b];
+        double kh[3] = {c->h.Khat[b][0], c->h.Khat[b][1], c->h.Khat[b][2]};
+        double r = std::sqrt(kh[0] * kh[0] + kh[1] * kh[1] + kh[2] * kh[2]);
+        for (int k = 0; k < 3; ++k) S.Kh[b][k] = (T)(r > 0 ? kh[k] / r : 0.0);
+    }
+    int q = 0;
+    for (int b = 0; b <= c->nb; ++b) {
+        S.off[b] = q;
+        if (b == c->nb) break;
+        for (auto &e : c->nbr)
+            if (e.b == b) {
+                NbrEntry<T> &E = S.e[q++];
+                E.jb = e.jb;
+                E.d0 = e.d[0];
+                E.d1 = e.d[1];
+                E.d2 = e.d[2];
+                E.J = (T)e.J;
+                E.Dx = (T)e.D[0];
+                E.Dy = (T)e.D[1];
+                E.Dz = (T)e.D[2];
+            }
+    }
+}
+
+int ready(sp_ctx *c)
+{
+    if (!c) return SP_ERR_ARG;
+    if (!c->have_geom || !c->have_ham) return fail(c, SP_ERR_STATE, "geometry and Hamiltonian must be set first");
+    return SP_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_spins(sp_ctx *c, const void *p, const char *what)
+{
+    if (!p) return fail(c, SP_ERR_ARG, "%s is NULL", what);
+    if (!aligned(p, c->prec == SP_F64 ? 32 : 16))
+        return fail(c, SP_ERR_ARG, "%s is not %d-byte aligned", what, c->prec == SP_F64 ? 32 : 16);
+    return SP_OK;
+}
+
+// Dipole field of `n` into the context's bdd buffer (or null when the
+// Hamiltonian has no dipole term).
+int dipole(sp_ctx *c, const void *n, const void **out, cudaStream_t st)
+{
+    *out = nullptr;
+    if (c->h.dipole != SP_DIPOLE_FFT) return SP_OK;
+    int rc = ensure(c, c->bdd, rec_bytes(c) * (size_t)c->N);
+    if (rc) return rc;
+    int pr = c->prof.begin(SP_PROF_DIPOLE, st);
+    cudaError_t e = dipole_field(c->dip, c->prec, n, c->bdd.p, st);
+    c->prof.end(pr, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dipole field");
+    *out = c->bdd.p;
+    return SP_OK;
+}
+
+template <typename T> LlgConst<T> llg_const(const sp_ctx *c, const sp_llg_params *p)
+{
+    LlgConst<T> k{};
+    k.dt = (T)p->dt;
+    k.alpha = (T)p->alpha;
+    for (int b = 0; b < c->nb; ++b) {
+        double mu = c->mu_s[b] * kMuB;
+        k.cA[b] = (T)(-kGamma / ((1.0 + p->alpha * p->alpha) * mu));
+        k.sig[b] = (T)std::sqrt(2.0 * p->alpha * kBoltzmann * p->T * mu / (kGamma * p->dt));
+    }
+    k.seed = p->seed;
+    k.replica = p->replica;
+    k.thermal = (p->T > 0 && p->alpha > 0) ? 1 : 0;
+    return k;
+}
+
+template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaStream_t st)
+{
+    int rc = ensure(c, c->pred, 2 * sizeof(rec_t<T>) * (size_t)c->N);
+    if (rc) return rc;
+    rec_t<T> *np = (rec_t<T> *)c->pred.p;
+    rec_t<T> *q = np + c->N;
+    rec_t<T> *nn = (rec_t<T> *)n;
+    const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
+    LlgConst<T> k = llg_const<T>(c, p);
+    for (int s = 0; s < n_steps; ++s) {
+        k.step = p->step0 + (uint64_t)s;
+        const void *bd;
+        if ((rc = dipole(c, nn, &bd, st))) return rc;
+        int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
+        cudaError_t e = launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
+        c->prof.end(pr, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
+        if ((rc = dipole(c, np, &bd, st))) return rc;
+        pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
+        e = launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
+        c->prof.end(pr, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
+    }
+    return SP_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+int sp_create(sp_ctx **out, int precision)
+{
+    if (!out) return SP_ERR_ARG;
+    *out = nullptr;
+    if (precision != SP_F32 && precision != SP_F64) return SP_ERR_ARG;
+    sp_ctx *c = new (std::nothrow) sp_ctx();
+    if (!c) return SP_ERR_STATE;
+    c->prec = precision;
+    cudaGetDevice(&c->device);
+    *out = c;
+    return SP_OK;
+}
+
+int sp_destroy(sp_ctx *c)
+{
+    if (!c) return SP_OK;
+    bool any = c->pred.p || c->partials.p || c->bdd.p || c->dip || c->mins;
+    if (any) cudaDeviceSynchronize();
+    if (c->pred.p) cudaFree(c->pred.p);
+    if (c->partials.p) cudaFree(c->partials.p);
+    if (c->bdd.p) cudaFree(c->bdd.p);
+    dipole_destroy(c->dip);
+    min_scratch_destroy(c->mins);
+    delete c;
+    return SP_OK;
+}
+
+const char *sp_last_error(const sp_ctx *c)
+{
+    if (!c) return "no context";
+    return c->err.c_str();
+}
+
+int sp_set_geometry(sp_ctx *c, const double *bravais, int n_basis, const double *basis, const int *n_cells,
+                    const int *periodic, double lattice_constant, const double *mu_s)
+{
+    if (!c) return SP_ERR_ARG;
+    if (!bravais || !basis || !n_cells || !periodic || !mu_s) return fail(c, SP_ERR_ARG, "NULL geometry argument");
+    if (n_basis < 1 || n_basis > SP_MAX_BASIS) return fail(c, SP_ERR_ARG, "n_basis %d out of 1..%d", n_basis, SP_MAX_BASIS);
+    if (!(lattice_constant > 0) || !std::isfinite(lattice_constant))
+        return fail(c, SP_ERR_ARG, "lattice constant must be positive");
+    long long N = n_basis;
+    for (int k = 0; k < 3; ++k) {
+        if (n_cells[k] < 1) return fail(c, SP_ERR_ARG, "n_cells[%d] = %d < 1", k, n_cells[k]);
+        N *= n_cells[k];
+        if (N >= (1LL << 31)) return fail(c, SP_ERR_ARG, "more than 2^31 - 1 spins");
+    }
+    for (int b = 0; b < n_basis; ++b)
+        if (!(mu_s[b] > 0) || !std::isfinite(mu_s[b])) return fail(c, SP_ERR_ARG, "mu_s[%d] must be positive", b);
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(bravais[k])) return fail(c, SP_ERR_ARG, "non-finite Bravais vector");
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) c->A[k][l] = bravais[3 * k + l];
+    c->nb = n_basis;
+    for (int b = 0; b < n_basis; ++b) {
+        for (int l = 0; l < 3; ++l) c->basis[b][l] = basis[3 * b + l];
+        c->mu_s[b] = mu_s[b];
+    }
+    for (int k = 0; k < 3; ++k) {
+        c->nc[k] = n_cells[k];
+        c->per[k] = periodic[k] ? 1 : 0;
+    }
+    c->a = lattice_constant;
+    c->N = (int)N;
+    c->have_geom = true;
+    c->have_ham = false;
+    return SP_OK;
+}
+
+int sp_set_hamiltonian(sp_ctx *c, const sp_hamiltonian *h)
+{
+    if (!c) return SP_ERR_ARG;
+    if (!c->have_geom) return fail(c, SP_ERR_STATE, "set the geometry before the Hamiltonian");
+    if (!h) return fail(c, SP_ERR_ARG, "NULL Hamiltonian");
+    if (h->n_shells < 0 || h->n_shells > SP_MAX_SHELLS) return fail(c, SP_ERR_ARG, "n_shells out of range");
+    if (h->n_dmi_shells < 0 || h->n_dmi_shells > SP_MAX_SHELLS) return fail(c, SP_ERR_ARG, "n_dmi_shells out of range");
+    if (h->dmi_kind < SP_DMI_NONE || h->dmi_kind > SP_DMI_INTERFACIAL) return fail(c, SP_ERR_ARG, "bad dmi_kind");
+    if (h->dipole != SP_DIPOLE_NONE && h->dipole != SP_DIPOLE_FFT) return fail(c, SP_ERR_ARG, "bad dipole mode");
+    if (h->n_pairs < 0 || (h->n_pairs > 0 && !h->pairs)) return fail(c, SP_ERR_ARG, "bad explicit pair list");
+    for (int p = 0; p < h->n_pairs; ++p) {
+        const sp_pair &q = h->pairs[p];
+        if (q.i < 0 || q.i >= c->nb || q.j < 0 || q.j >= c->nb) return fail(c, SP_ERR_ARG, "pair %d: bad basis index", p);
+        if (q.i == q.j && q.d[0] == 0 && q.d[1] == 0 && q.d[2] == 0) return fail(c, SP_ERR_ARG, "pair %d: self pair", p);
+    }
+    if (h->dipole == SP_DIPOLE_FFT)
+        for (int k = 0; k < 3; ++k)
+            if (c->per[k] && c->nc[k] > 1)
+                return fail(c, SP_ERR_UNSUPPORTED, "dipole term with a periodic direction is not implemented");
+    c->h = *h;
+    c->pairs.assign(h->pairs, h->pairs + h->n_pairs);
+    c->h.pairs = nullptr;
+    c->have_ham = false;
+    int rc = build_stencil(c);
+    if (rc) return rc;
+    fill_stencil(c, c->Sf);
+    fill_stencil(c, c->Sd);
+    dipole_destroy(c->dip);
+    c->dip = nullptr;
+    if (h->dipole == SP_DIPOLE_FFT) {
+        DipoleGeom g;
+        for (int k = 0; k < 3; ++k) {
+            g.nc[k] = c->nc[k];
+            for (int l = 0; l < 3; ++l) g.A[k][l] = c->A[k][l] * c->a;
+        }
+        g.nb = c->nb;
+        for (int b = 0; b < c->nb; ++b) {
+            g.mu[b] = c->mu_s[b];
+            for (int l = 0; l < 3; ++l) g.basis[b][l] = c->basis[b][l];
+        }
+        int e = dipole_create(&c->dip, g);
+        if (e == SP_ERR_UNSUPPORTED) return fail(c, e, "dipole FFT supports one basis atom and 2D grids up to 4096");
+        if (e) return fail(c, e, "dipole plan creation failed");
+    }
+    c->have_ham = true;
+    return SP_OK;
+}
+
+int sp_n_spins(const sp_ctx *c, int *n)
+{
+    if (!c || !n) return SP_ERR_ARG;
+    if (!c->have_geom) return SP_ERR_STATE;
+    *n = c->N;
+    return SP_OK;
+}
+
+static int field_common(sp_ctx *c, const void *n, void *out, double sign, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n, "spins")) || (rc = check_spins(c, out, "output"))) return rc;
+    if (n == out) return fail(c, SP_ERR_ARG, "input and output must not overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *bd;
+    if ((rc = dipole(c, n, &bd, st))) return rc;
+    cudaError_t e = c->prec == SP_F64
+                        ? launch_field<double>(c->Sd, (const dq4 *)n, (const dq4 *)bd, (dq4 *)out, sign, st)
+                        : launch_field<float>(c->Sf, (const float4 *)n, (const float4 *)bd, (float4 *)out, (float)sign, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "field launch");
+    return SP_OK;
+}
+
+int sp_effective_field(sp_ctx *c, const void *n_dev, void *B_dev, void *stream)
+{
+    return field_common(c, n_dev, B_dev, 1.0, stream);
+}
+
+int sp_gradient(sp_ctx *c, const void *n_dev, void *grad_dev, void *stream)
+{
+    return field_common(c, n_dev, grad_dev, -1.0, stream);
+}
+
+static int energy_common(sp_ctx *c, const void *n, double *e_out, double *t_out, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n, "spins"))) return rc;
+    if (!e_out && !t_out) return fail(c, SP_ERR_ARG, "NULL output");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure(c, c->partials, sizeof(double) * 8 * (size_t)blocks_for(c->N > 0 ? c->N : 1)))) return rc;
+    const void *bd;
+    if ((rc = dipole(c, n, &bd, st))) return rc;
+    cudaError_t e = c->prec == SP_F64
+                        ? launch_energy<double>(c->Sd, (const dq4 *)n, (const dq4 *)bd, (double *)c->partials.p, e_out, t_out, st)
+                        : launch_energy<float>(c->Sf, (const float4 *)n, (const float4 *)bd, (double *)c->partials.p, e_out, t_out, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy launch");
+    return SP_OK;
+}
+
+int sp_energy(sp_ctx *c, const void *n_dev, double *e_dev, void *stream)
+{
+    if (c && !e_dev) return fail(c, SP_ERR_ARG, "NULL energy output");
+    return energy_common(c, n_dev, e_dev, nullptr, stream);
+}
+
+int sp_max_torque(sp_ctx *c, const void *n_dev, double *torque_dev, void *stream)
+{
+    if (c && !torque_dev) return fail(c, SP_ERR_ARG, "NULL torque output");
+    return energy_common(c, n_dev, nullptr, torque_dev, stream);
+}
+
+int sp_llg_step(sp_ctx *c, void *n_dev, const sp_llg_params *p, int n_steps, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n_dev, "spins"))) return rc;
+    if (!p) return fail(c, SP_ERR_ARG, "NULL parameters");
+    if (p->solver != SP_DEPONDT && p->solver != SP_HEUN) return fail(c, SP_ERR_ARG, "unknown solver %d", p->solver);
+    if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(c, SP_ERR_ARG, "dt must be positive");
+    if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return fail(c, SP_ERR_ARG, "alpha must be >= 0");
+    if (!(p->T >= 0) || !std::isfinite(p->T)) return fail(c, SP_ERR_ARG, "T must be >= 0");
+    if (n_steps < 0) return fail(c, SP_ERR_ARG, "n_steps must be >= 0");
+    if (n_steps == 0 || c->N == 0) return SP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->prec == SP_F64 ? llg_run<double>(c, n_dev, p, n_steps, st) : llg_run<float>(c, n_dev, p, n_steps, st);
+}
+
+int sp_minimise(sp_ctx *c, void *n_dev, void *v_dev, double dt, double mass, double tol, int max_iter, int check_every,
+                int *iters, double *max_torque, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n_dev, "spins")) || (rc = check_spins(c, v_dev, "velocities"))) return rc;
+    if (n_dev == v_dev) return fail(c, SP_ERR_ARG, "spins and velocities must not overlap");
+    if (!(dt > 0) || !(mass > 0) || !std::isfinite(dt) || !std::isfinite(mass))
+        return fail(c, SP_ERR_ARG, "dt and mass must be positive");
+    if (!(tol >= 0)) return fail(c, SP_ERR_ARG, "tol must be >= 0");
+    if (max_iter < 0 || check_every < 1) return fail(c, SP_ERR_ARG, "max_iter >= 0 and check_every >= 1 required");
+    if (c->h.dipole != SP_DIPOLE_NONE) return fail(c, SP_ERR_UNSUPPORTED, "minimisation with the dipole term");
+    MinArgs a{dt, mass, tol, max_iter, check_every};
+    int it = 0;
+    double mt = 0;
+    int e = c->prec == SP_F64 ? vp_minimise<double>(&c->mins, c->Sd, n_dev, v_dev, a, &it, &mt, (cudaStream_t)stream)
+                              : vp_minimise<float>(&c->mins, c->Sf, n_dev, v_dev, a, &it, &mt, (cudaStream_t)stream);
+    if (e) return fail(c, e, "minimisation failed (%s)", e == SP_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "");
+    if (iters) *iters = it;
+    if (max_torque) *max_torque = mt;
+    return SP_OK;
+}
+
+int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const sp_gneb_params *p, int n_iter,
+                 double *energies_dev, double *max_force_dev, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, chain_dev, "chain")) || (rc = check_spins(c, vel_dev, "velocities"))) return rc;
+    if (!p) return fail(c, SP_ERR_ARG, "NULL parameters");
+    if (n_images < 3) return fail(c, SP_ERR_ARG, "a chain needs at least 3 images");
+    if (n_iter < 0) return fail(c, SP_ERR_ARG, "n_iter must be >= 0");
+    if (!(p->dt > 0) || !(p->mass > 0)) return fail(c, SP_ERR_ARG, "dt and mass must be positive");
+    if (!energies_dev || !max_force_dev) return fail(c, SP_ERR_ARG, "NULL output");
+    if ((long long)n_images * c->N >= (1LL << 31)) return fail(c, SP_ERR_ARG, "chain larger than 2^31 spins");
+    if (c->h.dipole != SP_DIPOLE_NONE) return fail(c, SP_ERR_UNSUPPORTED, "GNEB with the dipole term");
+    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, n_images, n_iter};
+    int e = c->prec == SP_F64
+                ? gneb_run<double>(&c->mins, c->Sd, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream)
+                : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
+    if (e) return fail(c, e, "GNEB failed");
+    return SP_OK;
+}
+
+int sp_profile_enable(sp_ctx *c, int on)
+{
+    if (!c) return SP_ERR_ARG;
+    if (!on && c->prof.on) {
+        cudaError_t e = c->prof.drain();
+        if (e != cudaSuccess) return cuda_fail(c, e, "profile drain");
+    }
+    c->prof.on = on != 0;
+    return SP_OK;
+}
+
+int sp_profile_read(sp_ctx *c, int kind, double *total_ms, long long *launches)
+{
+    if (!c) return SP_ERR_ARG;
+    if (kind < 0 || kind >= SP_PROF_KINDS || !total_ms || !launches) return fail(c, SP_ERR_ARG, "bad profile query");
+    cudaError_t e = c->prof.drain();
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile drain");
+    *total_ms = c->prof.ms[kind];
+    *launches = c->prof.count[kind];
+    c->prof.ms[kind] = 0;
+    c->prof.count[kind] = 0;
+    return SP_OK;
+}
+
+}  // extern "C"

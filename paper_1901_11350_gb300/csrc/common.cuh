@@ -1,0 +1,222 @@
+// common.cuh -- device-side building blocks of the GB300 spin library:
+// storage types, small-vector arithmetic, the neighbour-stencil parameter
+// block and the Philox4x32-10 thermal-noise generator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spirit_gb.h"
+
+namespace spgb {
+
+// CODATA 2018 constants in the library's units (meV, T, ps, Angstrom).
+constexpr double kMuB = 0.05788381806;            // Bohr magneton, meV/T
+constexpr double kBoltzmann = 0.08617333262;      // meV/K
+constexpr double kGamma = 0.176085963023;         // electron gyromagnetic ratio, rad/(ps T)
+constexpr double kDipole = 0.05368151123574179;   // mu0/(4 pi) mu_B^2 / Angstrom^3, meV
+
+// 4-wide spin records: float4 (16 B) for FP32, a 32-byte aligned double
+// quadruple for FP64 (loaded as two 16-byte halves).
+struct __align__(32) dq4 {
+    double x, y, z, w;
+};
+template <typename T> struct Rec;
+template <> struct Rec<float> { using type = float4; };
+template <> struct Rec<double> { using type = dq4; };
+template <typename T> using rec_t = typename Rec<T>::type;
+
+template <typename T> struct v3 {
+    T x, y, z;
+};
+
+template <typename T> __host__ __device__ __forceinline__ v3<T> mk(T x, T y, T z) { return v3<T>{x, y, z}; }
+template <typename T> __device__ __forceinline__ v3<T> operator+(v3<T> a, v3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T> __device__ __forceinline__ v3<T> operator-(v3<T> a, v3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T> __device__ __forceinline__ v3<T> operator*(T s, v3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T> __device__ __forceinline__ v3<T> operator-(v3<T> a) { return {-a.x, -a.y, -a.z}; }
+template <typename T> __device__ __forceinline__ T dot(v3<T> a, v3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T> __device__ __forceinline__ v3<T> cross(v3<T> a, v3<T> b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+// s*a + b with fused multiply-adds
+template <typename T> __device__ __forceinline__ v3<T> axpy(T s, v3<T> a, v3<T> b)
+{
+    return {fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z)};
+}
+__device__ __forceinline__ float rnorm(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rnorm(double x) { return rsqrt(x); }
+template <typename T> __device__ __forceinline__ v3<T> normalised(v3<T> a)
+{
+    T r = rnorm(dot(a, a));
+    return r * a;
+}
+
+__device__ __forceinline__ v3<float> ld(const float4 *p, long i)
+{
+    float4 v = __ldg(p + i);
+    return {v.x, v.y, v.z};
+}
+__device__ __forceinline__ v3<double> ld(const dq4 *p, long i)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p + i);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return {a.x, a.y, b.x};
+}
+// plain (coherent) loads for buffers written earlier in the same kernel
+__device__ __forceinline__ v3<float> ldc(const float4 *p, long i)
+{
+    float4 v = p[i];
+    return {v.x, v.y, v.z};
+}
+__device__ __forceinline__ v3<double> ldc(const dq4 *p, long i)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p + i);
+    double2 a = q[0], b = q[1];
+    return {a.x, a.y, b.x};
+}
+__device__ __forceinline__ void st(float4 *p, long i, v3<float> v) { p[i] = make_float4(v.x, v.y, v.z, 0.f); }
+__device__ __forceinline__ void st(dq4 *p, long i, v3<double> v)
+{
+    double2 *q = reinterpret_cast<double2 *>(p + i);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, 0.0);
+}
+
+// ---------------------------------------------------------------- stencil
+// One directed neighbour entry: basis atom jb in cell c + d, exchange J and
+// DMI vector D_ij as seen from the centre atom.
+template <typename T> struct NbrEntry {
+    int jb, d0, d1, d2;
+    T J, Dx, Dy, Dz;
+};
+
+// Everything a kernel needs to evaluate the local part of Eq. 1 at a spin:
+// lattice extents, per-basis on-site terms and the neighbour stencil.  Passed
+// by value as a __grid_constant__ kernel parameter (about 3-5 KB).
+template <typename T> struct Stencil {
+    int nb, n0, n1, n2, per0, per1, per2, N;
+    int off[SP_MAX_BASIS + 1];  // entries of basis b: [off[b], off[b+1])
+    T mu[SP_MAX_BASIS];         // mu_b mu_B, meV/T
+    T Bz[SP_MAX_BASIS][3];      // Zeeman field mu_b mu_B B, meV
+    T K[SP_MAX_BASIS];          // anisotropy K_b, meV
+    T Kh[SP_MAX_BASIS][3];      // anisotropy axis
+    NbrEntry<T> e[SP_MAX_NBR];
+};
+
+// Periodic wrap for |d| <= n (checked on the host); -1 across an open edge.
+__device__ __forceinline__ int wrap(int x, int n, int per)
+{
+    if (per) {
+        x += (x < 0) ? n : 0;
+        x -= (x >= n) ? n : 0;
+        return x;
+    }
+    return (x < 0 || x >= n) ? -1 : x;
+}
+
+// Local part of B_eff = -dH/dn at spin i (Eq. 1 without the dipole term):
+// mu_i B + 2 K (Khat.n_i) Khat + sum_j [J_ij n_j + n_j x D_ij].
+template <typename T, typename R>
+__device__ __forceinline__ v3<T> local_field(const Stencil<T> &S, const R *n, int i, v3<T> ni, int &b)
+{
+    b = i % S.nb;
+    int r = i / S.nb;
+    int c0 = r % S.n0;
+    r /= S.n0;
+    int c1 = r % S.n1;
+    int c2 = r / S.n1;
+    T kn = dot(mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]), ni);
+    T k2 = T(2) * S.K[b] * kn;
+    v3<T> B = mk(fma(k2, S.Kh[b][0], S.Bz[b][0]), fma(k2, S.Kh[b][1], S.Bz[b][1]), fma(k2, S.Kh[b][2], S.Bz[b][2]));
+    for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
+        const NbrEntry<T> &E = S.e[q];
+        int x0 = wrap(c0 + E.d0, S.n0, S.per0);
+        int x1 = wrap(c1 + E.d1, S.n1, S.per1);
+        int x2 = wrap(c2 + E.d2, S.n2, S.per2);
+        if ((x0 | x1 | x2) < 0) continue;
+        int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+        v3<T> nj = ld(n, j);
+        v3<T> c = cross(nj, mk(E.Dx, E.Dy, E.Dz));
+        B = axpy(E.J, nj, B + c);
+    }
+    return B;
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications with the published multipliers and Weyl key
+// increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 thermal_bits(uint64_t seed, uint64_t step, uint32_t replica, uint32_t i)
+{
+    return philox4x32_10(make_uint4(i, (uint32_t)step, (uint32_t)(step >> 32), replica * 8u),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Three standard normals by Box-Muller: (u0,u1) -> eta_x, eta_y; (u2,u3) ->
+// eta_z; u = (x + 1/2) 2^-32.
+__device__ __forceinline__ v3<float> box_muller(uint4 x, float)
+{
+    const float s = 2.3283064365386963e-10f;  // 2^-32
+    float u0 = fmaf((float)x.x, s, 0.5f * s), u1 = fmaf((float)x.y, s, 0.5f * s);
+    float u2 = fmaf((float)x.z, s, 0.5f * s), u3 = fmaf((float)x.w, s, 0.5f * s);
+    float r0 = sqrtf(fmaxf(0.f, -2.f * __logf(u0))), r1 = sqrtf(fmaxf(0.f, -2.f * __logf(u2)));
+    float s1, c1;
+    sincospif(2.f * u1, &s1, &c1);
+    return {r0 * c1, r0 * s1, r1 * cospif(2.f * u3)};
+}
+__device__ __forceinline__ v3<double> box_muller(uint4 x, double)
+{
+    const double s = 2.3283064365386963e-10;
+    double u0 = ((double)x.x + 0.5) * s, u1 = ((double)x.y + 0.5) * s;
+    double u2 = ((double)x.z + 0.5) * s, u3 = ((double)x.w + 0.5) * s;
+    double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    double s1, c1;
+    sincospi(2.0 * u1, &s1, &c1);
+    return {r0 * c1, r0 * s1, r1 * cospi(2.0 * u3)};
+}
+
+// ---------------------------------------------------------------- LLG
+// A(n, B) = c (B + alpha n x B), c = -gamma / ((1 + alpha^2) mu)  (Eq. 3 as dn/dt = n x A)
+template <typename T> __device__ __forceinline__ v3<T> llg_A(T c, T alpha, v3<T> n, v3<T> B)
+{
+    return c * axpy(alpha, cross(n, B), B);
+}
+
+// Depondt step: rotate n about -Ahat by |A| dt (Rodrigues' formula).
+__device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+template <typename T> __device__ __forceinline__ v3<T> rotate(v3<T> n, v3<T> A, T dt)
+{
+    T w2 = dot(A, A);
+    if (w2 == T(0)) return n;
+    T iw = rnorm(w2);
+    T th = w2 * iw * dt;
+    v3<T> ax = (-iw) * A;
+    T s, c;
+    sincos_(th, &s, &c);
+    v3<T> axn = cross(ax, n);
+    T an = dot(ax, n);
+    // 1 - cos without cancellation for small angles: sin^2 / (1 + cos)
+    T omc = c > T(0) ? s * s / (T(1) + c) : T(1) - c;
+    // n cos + (ax x n) sin + ax (ax.n)(1 - cos)
+    return axpy(an * omc, ax, axpy(s, axn, c * n));
+}
+
+}  // namespace spgb

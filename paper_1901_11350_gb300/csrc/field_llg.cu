@@ -1,0 +1,232 @@
+// field_llg.cu -- effective field, energy/torque reductions and the two-pass
+// LLG step (Heun and Depondt) for any lattice with a neighbour stencil.
+//
+// Heun (Appendix B) with the thermal field of Eq. 4, one step in two passes:
+//   pass 1 (predictor), per spin i:
+//       A_i  = A(n_i, B_i(n) + Bth_i),  f_i = n_i x A_i
+//       np_i = normalise(n_i + dt f_i)
+//       q_i  = n_i + dt/2 (f_i + np_i x A(np_i, Bth_i))
+//   pass 2 (corrector):
+//       n_i <- normalise(q_i + dt/2 np_i x A(np_i, B_i(np)))
+// A(n, B) is linear in B, so f(np) = np x A(np, B(np)) + np x A(np, Bth):
+// the noise-dependent half of the corrector is folded into q in pass 1 and
+// neither the noise nor A(n) is recomputed in pass 2.  Depondt folds the same
+// way: h_i = A_i/2 + A(np_i, Bth_i)/2 and n_i <- R(h_i + A(np_i, B_i(np))/2) n_i.
+// Memory per step: read n, write np and q; read np (stencil) and q (and n
+// for Depondt), write n -- 6 (7) records per spin.
+#include "internal.h"
+
+namespace spgb {
+
+// ---------------------------------------------------------------- field
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_field(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
+                                                  const rec_t<T> *__restrict__ Bdd, rec_t<T> *__restrict__ out, T sign)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    int b;
+    v3<T> ni = ld(n, i);
+    v3<T> B = local_field(S, n, i, ni, b);
+    if (Bdd) B = B + ld(Bdd, i);
+    st(out, i, sign * B);
+}
+
+template <typename T>
+cudaError_t launch_field(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *out, T sign,
+                         cudaStream_t st)
+{
+    if (S.N == 0) return cudaSuccess;
+    k_field<T><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, out, sign);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- LLG
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
+                                                     const rec_t<T> *__restrict__ Bdd, rec_t<T> *__restrict__ np,
+                                                     rec_t<T> *__restrict__ q, const LlgConst<T> c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    int b;
+    v3<T> ni = ld(n, i);
+    v3<T> B = local_field(S, n, i, ni, b);
+    if (Bdd) B = B + ld(Bdd, i);
+    v3<T> Bth = mk(T(0), T(0), T(0));
+    if (c.thermal) Bth = c.sig[b] * box_muller(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+    v3<T> A = llg_A(c.cA[b], c.alpha, ni, B + Bth);
+    if (SOLVER == SP_HEUN) {
+        v3<T> f = cross(ni, A);
+        v3<T> p = normalised(axpy(c.dt, f, ni));
+        v3<T> g = cross(p, llg_A(c.cA[b], c.alpha, p, Bth));
+        st(np, i, p);
+        st(q, i, axpy(T(0.5) * c.dt, f + g, ni));
+    } else {
+        v3<T> p = rotate(ni, A, c.dt);
+        st(np, i, p);
+        st(q, i, T(0.5) * (A + llg_A(c.cA[b], c.alpha, p, Bth)));
+    }
+}
+
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ n,
+                                                     const rec_t<T> *__restrict__ np, const rec_t<T> *__restrict__ q,
+                                                     const rec_t<T> *__restrict__ Bdd, const LlgConst<T> c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    int b;
+    v3<T> p = ld(np, i);
+    v3<T> B = local_field(S, np, i, p, b);
+    if (Bdd) B = B + ld(Bdd, i);
+    v3<T> Ap = llg_A(c.cA[b], c.alpha, p, B);
+    v3<T> qi = ld(q, i);
+    if (SOLVER == SP_HEUN) {
+        st(n, i, normalised(axpy(T(0.5) * c.dt, cross(p, Ap), qi)));
+    } else {
+        v3<T> Ac = axpy(T(0.5), Ap, qi);
+        st(n, i, rotate(ldc(n, i), Ac, c.dt));
+    }
+}
+
+template <typename T>
+cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *np,
+                            rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st)
+{
+    if (S.N == 0) return cudaSuccess;
+    if (solver == SP_HEUN)
+        k_llg_pred<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+    else
+        k_llg_pred<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const rec_t<T> *np, const rec_t<T> *q,
+                            const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st)
+{
+    if (S.N == 0) return cudaSuccess;
+    if (solver == SP_HEUN)
+        k_llg_corr<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+    else
+        k_llg_corr<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- energy
+// Per-spin energy terms of Eq. 1 (each unique pair contributes half from
+// either side) and |n_i x B_i|; FP64 block sums -> partials[8*block].
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
+                                                   const rec_t<T> *__restrict__ Bdd, double *__restrict__ partials)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double tmax = 0;
+    if (i < S.N) {
+        int b = i % S.nb;
+        int r = i / S.nb;
+        int c0 = r % S.n0;
+        r /= S.n0;
+        int c1 = r % S.n1;
+        int c2 = r / S.n1;
+        v3<T> ni = ld(n, i);
+        v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
+        v3<T> Kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
+        T kn = dot(Kh, ni);
+        acc[1] = -(double)dot(ni, Bz);
+        acc[2] = -(double)(S.K[b] * kn * kn);
+        v3<T> B = axpy(T(2) * S.K[b] * kn, Kh, Bz);
+        v3<T> Bx = mk(T(0), T(0), T(0)), Bd = mk(T(0), T(0), T(0));
+        for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
+            const NbrEntry<T> &E = S.e[q];
+            int x0 = wrap(c0 + E.d0, S.n0, S.per0);
+            int x1 = wrap(c1 + E.d1, S.n1, S.per1);
+            int x2 = wrap(c2 + E.d2, S.n2, S.per2);
+            if ((x0 | x1 | x2) < 0) continue;
+            int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+            v3<T> nj = ld(n, j);
+            Bx = axpy(E.J, nj, Bx);
+            Bd = Bd + cross(nj, mk(E.Dx, E.Dy, E.Dz));
+        }
+        acc[3] = -0.5 * (double)dot(ni, Bx);
+        acc[4] = -0.5 * (double)dot(ni, Bd);
+        B = B + Bx + Bd;
+        if (Bdd) {
+            v3<T> bd = ld(Bdd, i);
+            acc[5] = -0.5 * (double)dot(ni, bd);
+            B = B + bd;
+        }
+        acc[0] = acc[1] + acc[2] + acc[3] + acc[4] + acc[5];
+        v3<T> t = cross(ni, B);
+        tmax = sqrt((double)dot(t, t));
+    }
+    // warp then block reduction in a fixed order
+    __shared__ double sh[kBlock / 32][7];
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_down_sync(0xffffffffu, tmax, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        for (int k = 0; k < 6; ++k) sh[w][k] = acc[k];
+        sh[w][6] = tmax;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        int k = threadIdx.x;
+        double v = sh[0][k];
+        for (int ww = 1; ww < kBlock / 32; ++ww) v = (k == 6) ? fmax(v, sh[ww][k]) : v + sh[ww][k];
+        partials[8 * blockIdx.x + k] = v;
+    }
+}
+
+// Sum the per-block partials in a fixed order (one block).
+__global__ void __launch_bounds__(kBlock) k_energy_final(const double *__restrict__ partials, int nblk, double *e_out,
+                                                         double *torque_out)
+{
+    __shared__ double sh[kBlock][7];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int p = threadIdx.x; p < nblk; p += kBlock) {
+        for (int k = 0; k < 6; ++k) acc[k] += partials[8 * p + k];
+        acc[6] = fmax(acc[6], partials[8 * p + 6]);
+    }
+    for (int k = 0; k < 7; ++k) sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 7; ++k)
+                sh[threadIdx.x][k] = (k == 6) ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                                              : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (e_out)
+            for (int k = 0; k < 6; ++k) e_out[k] = sh[0][k];
+        if (torque_out) torque_out[0] = sh[0][6];
+    }
+}
+
+template <typename T>
+cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, double *partials, double *e_out,
+                          double *torque_out, cudaStream_t st)
+{
+    int nblk = blocks_for(S.N > 0 ? S.N : 1);
+    k_energy<T><<<nblk, kBlock, 0, st>>>(S, n, Bdd, partials);
+    k_energy_final<<<1, kBlock, 0, st>>>(partials, nblk, e_out, torque_out);
+    return cudaGetLastError();
+}
+
+#define SPGB_INST(T)                                                                                                   \
+    template cudaError_t launch_field<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, rec_t<T> *, T,         \
+                                         cudaStream_t);                                                                \
+    template cudaError_t launch_llg_pred<T>(int, const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, rec_t<T> *,    \
+                                            rec_t<T> *, const LlgConst<T> &, cudaStream_t);                            \
+    template cudaError_t launch_llg_corr<T>(int, const Stencil<T> &, rec_t<T> *, const rec_t<T> *, const rec_t<T> *,    \
+                                            const rec_t<T> *, const LlgConst<T> &, cudaStream_t);                      \
+    template cudaError_t launch_energy<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, double *, double *,   \
+                                          double *, cudaStream_t);
+SPGB_INST(float)
+SPGB_INST(double)
+
+}  // namespace spgb

@@ -1,0 +1,36 @@
+// internal.h -- launchers shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace spgb {
+
+// Per-run LLG constants, per basis atom where they depend on mu_b.
+template <typename T> struct LlgConst {
+    T dt, alpha;
+    T cA[SP_MAX_BASIS];   // -gamma / ((1 + alpha^2) mu_b)
+    T sig[SP_MAX_BASIS];  // sqrt(2 alpha kB T mu_b / (gamma dt)), meV
+    uint64_t seed, step;
+    uint32_t replica;
+    int thermal;
+};
+
+constexpr int kBlock = 256;
+inline int blocks_for(long n, int bs = kBlock) { return (int)((n + bs - 1) / bs); }
+
+template <typename T>
+cudaError_t launch_field(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *out, T sign,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *np,
+                            rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st);
+template <typename T>
+cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const rec_t<T> *np, const rec_t<T> *q,
+                            const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st);
+// Energies (6 FP64 sums) and max torque of the spins n; partials needs
+// 8 * blocks_for(N) doubles.  e_out (6) and torque_out (1) may be null.
+template <typename T>
+cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, double *partials, double *e_out,
+                          double *torque_out, cudaStream_t st);
+
+}  // namespace spgb

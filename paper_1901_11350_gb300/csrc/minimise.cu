@@ -1,0 +1,483 @@
+// minimise.cu -- velocity projection (Appendix D) and GNEB (Sec. GNEB,
+// Appendix F) on the GPU.
+//
+// Work is cut into blocks of kBlock spins of one image ("image" = one system
+// of one chain; a plain minimisation is one image).  Per-image scalars
+// (energy, geodesic distance, tangent norm, projections, max force) are
+// reduced deterministically: every block writes its partial, and the last
+// block of the image to finish (atomic ticket) sums the image's partials in
+// a fixed order and re-arms the ticket.  Kernels of one iteration:
+//   move    v <- projection of v on F (from the previous force pass),
+//           x <- normalise(x + dt v + dt^2/(2m) F)          (interior images)
+//   field   B(x), E_v, Pg = -(B - (B.x)x), theta^2 to image v+1
+//   tangent improved tangent, per-spin projection, |tau|^2, Pg.tau
+//   force   F' (spring / climbing image), v <- v + dt/(2m)(F + F'),
+//           v.F', F'.F', max |F'|
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "minimise.h"
+
+namespace spgb {
+
+namespace {
+
+struct ImgInfo {
+    long long spin0;  // record offset of image 0 of the chain
+    int N, chain, nu, M, g0, blk0, bpi;
+};
+struct BlkInfo {
+    int g, t;
+};
+
+// per-image scalar slots (8 doubles per image)
+enum { kE = 0, kL2 = 1, kTT = 2, kGT = 3, kVF = 4, kFF = 5, kFMAX = 6 };
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+int grow(Buf &b, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return 0;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) return SP_ERR_CUDA;
+    b.bytes = bytes;
+    return 0;
+}
+
+}  // namespace
+
+struct MinScratch {
+    Buf F, G, Tau, scal, part, cnt, blk, img, sten, state;
+    int *host_state = nullptr;  // pinned: iters, active
+    double *host_fmax = nullptr;
+};
+
+void min_scratch_destroy(MinScratch *s)
+{
+    if (!s) return;
+    Buf *bufs[] = {&s->F, &s->G, &s->Tau, &s->scal, &s->part, &s->cnt, &s->blk, &s->img, &s->sten, &s->state};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (s->host_state) cudaFreeHost(s->host_state);
+    if (s->host_fmax) cudaFreeHost(s->host_fmax);
+    delete s;
+}
+
+namespace {
+
+int scratch(MinScratch **s)
+{
+    if (!*s) {
+        *s = new (std::nothrow) MinScratch();
+        if (!*s) return SP_ERR_STATE;
+        if (cudaMallocHost(&(*s)->host_state, 4 * sizeof(int)) != cudaSuccess) return SP_ERR_CUDA;
+        if (cudaMallocHost(&(*s)->host_fmax, sizeof(double)) != cudaSuccess) return SP_ERR_CUDA;
+    }
+    return 0;
+}
+
+// Counters must start at zero; the reduction leaves them at zero.
+int grow_counters(Buf &b, size_t n, cudaStream_t st)
+{
+    size_t bytes = n * sizeof(unsigned);
+    if (b.p && b.bytes >= bytes) return 0;
+    if (grow(b, bytes)) return SP_ERR_CUDA;
+    return cudaMemsetAsync(b.p, 0, b.bytes, st) == cudaSuccess ? 0 : SP_ERR_CUDA;
+}
+
+template <int NV>
+__device__ __forceinline__ double combine(int k, unsigned maxmask, double a, double b)
+{
+    return ((maxmask >> k) & 1u) ? fmax(a, b) : a + b;
+}
+
+// Deterministic per-image reduction of NV values (bit k of maxmask: max
+// instead of sum).  Every thread of every block of the image must call it.
+template <int NV>
+__device__ void image_reduce(double (&v)[NV], unsigned maxmask, double *__restrict__ part, int blk, int blk0, int bpi,
+                             unsigned *counter, double *out)
+{
+    __shared__ double sh[kBlock / 32][NV];
+    __shared__ double red[kBlock][NV];
+    __shared__ int last;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] = combine<NV>(k, maxmask, v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int k = 0; k < NV; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double a = sh[0][k];
+            for (int ww = 1; ww < kBlock / 32; ++ww) a = combine<NV>(k, maxmask, a, sh[ww][k]);
+            part[(size_t)blk * NV + k] = a;
+        }
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        last = (ticket == (unsigned)(bpi - 1));
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[NV];
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int p = threadIdx.x; p < bpi; p += kBlock)
+        for (int k = 0; k < NV; ++k) acc[k] = combine<NV>(k, maxmask, acc[k], __ldcg(&part[(size_t)(blk0 + p) * NV + k]));
+    for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = combine<NV>(k, maxmask, red[threadIdx.x][k], red[threadIdx.x + s][k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) out[k] = red[0][k];
+        atomicExch(counter, 0u);
+    }
+}
+
+// ============================================================ VP minimiser
+// state (ints): [0] iterations performed, [1] active flag
+// scal (doubles): v.F, F.F, max|F|, projection-valid flag
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ x,
+                                                     rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, double dth_m,
+                                                     int mode, double *part, unsigned *cnt, double *scal,
+                                                     const int *state)
+{
+    if (mode == 1 && state[1] == 0) return;
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    double r[3] = {0, 0, 0};
+    if (i < S.N) {
+        int b;
+        v3<T> ni = ld(x, i);
+        v3<T> B = local_field(S, x, i, ni, b);
+        v3<T> Fn = B - dot(B, ni) * ni;
+        if (mode == 1) {
+            v3<T> vi = axpy((T)dth_m, ldc(F, i) + Fn, ldc(v, i));
+            st(v, i, vi);
+            r[0] = (double)dot(vi, Fn);
+        }
+        st(F, i, Fn);
+        r[1] = (double)dot(Fn, Fn);
+        r[2] = sqrt(r[1]);
+    }
+    image_reduce<3>(r, 4u, part, blockIdx.x, 0, gridDim.x, cnt, scal);
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[3] = mode;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
+                                                    const rec_t<T> *__restrict__ F, double dt, double dt2_2m, double tol,
+                                                    int k, int max_iter, const double *scal, int *state)
+{
+    double fmax_ = scal[2];
+    bool done = (fmax_ < tol) || (k >= max_iter);
+    bool proj = scal[3] != 0.0;
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < N) {
+        v3<T> vi;
+        if (proj) {
+            double vf = scal[0], ff = scal[1];
+            T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+            vi = c * ldc(F, i);
+            st(v, i, vi);
+        } else {
+            vi = ldc(v, i);
+        }
+        if (!done) st(x, i, normalised(axpy((T)dt2_2m, ldc(F, i), axpy((T)dt, vi, ldc(x, i)))));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        state[1] = done ? 0 : 1;
+        if (!done) state[0] = k + 1;
+    }
+}
+
+// ============================================================ GNEB
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                    const Stencil<T> *__restrict__ S, const rec_t<T> *__restrict__ x,
+                                                    rec_t<T> *__restrict__ G, double *part, unsigned *cnt, double *scal)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    const Stencil<T> &St = S[im.chain];
+    int i = bi.t * kBlock + threadIdx.x;
+    const rec_t<T> *xb = x + im.spin0 + (long long)im.nu * im.N;
+    double r[2] = {0, 0};
+    if (i < im.N) {
+        int b;
+        v3<T> ni = ld(xb, i);
+        v3<T> B = local_field(St, xb, i, ni, b);
+        v3<T> Bz = mk(St.Bz[b][0], St.Bz[b][1], St.Bz[b][2]);
+        r[0] = -0.5 * (double)dot(ni, B + Bz);
+        v3<T> pg = dot(B, ni) * ni - B;  // tangent-space part of dH/dn = -B
+        st(G, im.spin0 + (long long)im.nu * im.N + i, pg);
+        if (im.nu < im.M - 1) {
+            v3<T> nj = ld(xb + im.N, i);
+            v3<T> c = cross(ni, nj);
+            T th = atan2(sqrt(dot(c, c)), dot(ni, nj));
+            r[1] = (double)th * (double)th;
+        }
+    }
+    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                      const rec_t<T> *__restrict__ x, const rec_t<T> *__restrict__ G,
+                                                      rec_t<T> *__restrict__ Tau, double *part, unsigned *cnt,
+                                                      double *scal)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    int i = bi.t * kBlock + threadIdx.x;
+    long long p = im.spin0 + (long long)im.nu * im.N + i;
+    double r[2] = {0, 0};
+    if (i < im.N) {
+        double Ep = scal[8 * (bi.g + 1) + kE], E0 = scal[8 * bi.g + kE], Em = scal[8 * (bi.g - 1) + kE];
+        double wp, wm;
+        // improved tangent (Henkelman and Jonsson 2000)
+        if (Ep > E0 && E0 > Em) {
+            wp = 1;
+            wm = 0;
+        } else if (Ep < E0 && E0 < Em) {
+            wp = 0;
+            wm = 1;
+        } else {
+            double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+            if (Ep > Em) {
+                wp = dmax;
+                wm = dmin;
+            } else {
+                wp = dmin;
+                wm = dmax;
+            }
+        }
+        v3<T> xi = ld(x, p), xp = ld(x, p + im.N), xm = ld(x, p - im.N);
+        v3<T> t = axpy((T)wp, xp - xi, (T)wm * (xi - xm));
+        t = t - dot(t, xi) * xi;
+        st(Tau, p, t);
+        r[0] = (double)dot(t, t);
+        r[1] = (double)dot(ldc(G, p), t);
+    }
+    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kTT);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                    rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
+                                                    const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
+                                                    double kspring, int climbing, double dth_m, int mode, double *part,
+                                                    unsigned *cnt, double *scal)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    int ci = -1;
+    if (climbing) {
+        ci = 1;
+        double best = scal[8 * (im.g0 + 1) + kE];
+        for (int nu = 2; nu < im.M - 1; ++nu) {
+            double e = scal[8 * (im.g0 + nu) + kE];
+            if (e > best) {
+                best = e;
+                ci = nu;
+            }
+        }
+    }
+    int i = bi.t * kBlock + threadIdx.x;
+    long long p = im.spin0 + (long long)im.nu * im.N + i;
+    double r[3] = {0, 0, 0};
+    if (i < im.N) {
+        double tt = scal[8 * bi.g + kTT];
+        double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
+        double gt = scal[8 * bi.g + kGT] * inv;
+        double fs = kspring * (sqrt(scal[8 * bi.g + kL2]) - sqrt(scal[8 * (bi.g - 1) + kL2]));
+        double coef = (im.nu == ci) ? 2.0 * gt : gt + fs;
+        v3<T> Fn = axpy((T)(coef * inv), ld(Tau, p), -ldc(G, p));
+        if (mode == 1) {
+            v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
+            st(v, p, vi);
+            r[0] = (double)dot(vi, Fn);
+        }
+        st(F, p, Fn);
+        r[1] = (double)dot(Fn, Fn);
+        r[2] = sqrt(r[1]);
+    }
+    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kVF);
+}
+
+// mode 0: move; 1: project then move; 2: project only
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                   rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
+                                                   const rec_t<T> *__restrict__ F, double dt, double dt2_2m, int mode,
+                                                   const double *scal)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    int i = bi.t * kBlock + threadIdx.x;
+    if (i >= im.N) return;
+    long long p = im.spin0 + (long long)im.nu * im.N + i;
+    v3<T> vi;
+    if (mode >= 1) {
+        double vf = scal[8 * bi.g + kVF], ff = scal[8 * bi.g + kFF];
+        T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+        vi = c * ldc(F, p);
+        st(v, p, vi);
+    } else {
+        vi = ldc(v, p);
+    }
+    if (mode <= 1) st(x, p, normalised(axpy((T)dt2_2m, ldc(F, p), axpy((T)dt, vi, ldc(x, p)))));
+}
+
+__global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const double *scal, double *E, double *fmax_out,
+                           int n_chains)
+{
+    for (int g = threadIdx.x; g < n_img; g += blockDim.x) E[g] = scal[8 * g + kE];
+    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+        double m = 0;
+        for (int g = 0; g < n_img; ++g)
+            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = fmax(m, scal[8 * g + kFMAX]);
+        fmax_out[c] = m;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ VP host loop
+template <typename T>
+int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const MinArgs &a, int *iters, double *max_torque,
+                cudaStream_t st)
+{
+    int rc = scratch(sp);
+    if (rc) return rc;
+    MinScratch *s = *sp;
+    int N = S.N;
+    int nblk = blocks_for(N > 0 ? N : 1);
+    if (grow(s->F, sizeof(rec_t<T>) * (size_t)(N > 0 ? N : 1)) || grow(s->scal, 8 * sizeof(double)) ||
+        grow(s->part, 3 * sizeof(double) * (size_t)nblk) || grow_counters(s->cnt, 1, st) ||
+        grow(s->state, 4 * sizeof(int)))
+        return SP_ERR_CUDA;
+    rec_t<T> *x = (rec_t<T> *)n, *vv = (rec_t<T> *)v, *F = (rec_t<T> *)s->F.p;
+    double *scal = (double *)s->scal.p, *part = (double *)s->part.p;
+    unsigned *cnt = (unsigned *)s->cnt.p;
+    int *state = (int *)s->state.p;
+    double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
+    if (cudaMemsetAsync(state, 0, 4 * sizeof(int), st) != cudaSuccess) return SP_ERR_CUDA;
+    k_vp_force<T><<<nblk, kBlock, 0, st>>>(S, x, vv, F, dth_m, 0, part, cnt, scal, state);
+    int k = 0;
+    while (k < a.max_iter) {
+        int chunk = std::min(a.check_every, a.max_iter - k);
+        for (int c = 0; c < chunk; ++c, ++k) {
+            k_vp_move<T><<<nblk, kBlock, 0, st>>>(N, x, vv, F, a.dt, dt2_2m, a.tol, k, a.max_iter, scal, state);
+            k_vp_force<T><<<nblk, kBlock, 0, st>>>(S, x, vv, F, dth_m, 1, part, cnt, scal, state);
+        }
+        if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
+        if (cudaMemcpyAsync(s->host_state, state, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SP_ERR_CUDA;
+        if (s->host_state[1] == 0) break;
+    }
+    // final projection of the velocity (or nothing when no iteration ran)
+    k_vp_move<T><<<nblk, kBlock, 0, st>>>(N, x, vv, F, a.dt, dt2_2m, a.tol, a.max_iter, a.max_iter, scal, state);
+    if (cudaMemcpyAsync(s->host_state, state, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->host_fmax, scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    *iters = s->host_state[0];
+    *max_torque = *s->host_fmax;
+    return 0;
+}
+
+// ------------------------------------------------------------ GNEB host side
+template <typename T>
+int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const std::vector<int> &M,
+                   const std::vector<long long> &spin0, void *chain, void *vel, const GnebArgs &a, double *E_dev,
+                   double *fmax_dev, cudaStream_t st)
+{
+    int rc = scratch(sp);
+    if (rc) return rc;
+    MinScratch *s = *sp;
+    int C = (int)stencils.size();
+    std::vector<ImgInfo> img;
+    std::vector<BlkInfo> blk;
+    long long total = 0;
+    for (int c = 0; c < C; ++c) {
+        int N = stencils[c].N;
+        int bpi = blocks_for(N > 0 ? N : 1);
+        int g0 = (int)img.size();
+        for (int nu = 0; nu < M[c]; ++nu) {
+            ImgInfo im{spin0[c], N, c, nu, M[c], g0, (int)blk.size(), bpi};
+            for (int t = 0; t < bpi; ++t) blk.push_back(BlkInfo{(int)img.size(), t});
+            img.push_back(im);
+        }
+        total = std::max(total, spin0[c] + (long long)M[c] * N);
+    }
+    int n_img = (int)img.size(), n_blk = (int)blk.size();
+    size_t rb = sizeof(rec_t<T>) * (size_t)std::max(total, 1LL);
+    if (grow(s->F, rb) || grow(s->G, rb) || grow(s->Tau, rb) || grow(s->scal, 8 * sizeof(double) * n_img) ||
+        grow(s->part, 3 * sizeof(double) * (size_t)n_blk) || grow_counters(s->cnt, n_img, st) ||
+        grow(s->blk, sizeof(BlkInfo) * n_blk) || grow(s->img, sizeof(ImgInfo) * n_img) ||
+        grow(s->sten, sizeof(Stencil<T>) * C))
+        return SP_ERR_CUDA;
+    if (cudaMemcpyAsync(s->blk.p, blk.data(), sizeof(BlkInfo) * n_blk, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->img.p, img.data(), sizeof(ImgInfo) * n_img, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->sten.p, stencils.data(), sizeof(Stencil<T>) * C, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    // the host vectors must outlive the copies above
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SP_ERR_CUDA;
+    const BlkInfo *B = (const BlkInfo *)s->blk.p;
+    const ImgInfo *I = (const ImgInfo *)s->img.p;
+    const Stencil<T> *Sd = (const Stencil<T> *)s->sten.p;
+    rec_t<T> *x = (rec_t<T> *)chain, *v = (rec_t<T> *)vel;
+    rec_t<T> *F = (rec_t<T> *)s->F.p, *G = (rec_t<T> *)s->G.p, *Tau = (rec_t<T> *)s->Tau.p;
+    double *scal = (double *)s->scal.p, *part = (double *)s->part.p;
+    unsigned *cnt = (unsigned *)s->cnt.p;
+    double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
+    auto forces = [&](int mode) {
+        k_g_field<T><<<n_blk, kBlock, 0, st>>>(B, I, Sd, x, G, part, cnt, scal);
+        k_g_tangent<T><<<n_blk, kBlock, 0, st>>>(B, I, x, G, Tau, part, cnt, scal);
+        k_g_force<T><<<n_blk, kBlock, 0, st>>>(B, I, v, F, G, Tau, a.k, a.climbing, dth_m, mode, part, cnt, scal);
+    };
+    forces(0);
+    for (int it = 0; it < a.n_iter; ++it) {
+        k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, it == 0 ? 0 : 1, scal);
+        forces(1);
+    }
+    if (a.n_iter > 0) k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, 2, scal);
+    k_g_finish<<<1, 256, 0, st>>>(I, n_img, scal, E_dev, fmax_dev, C);
+    return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
+}
+
+template <typename T>
+int gneb_run(MinScratch **s, const Stencil<T> &S, void *chain, void *vel, const GnebArgs &a, double *E_dev,
+             double *fmax_dev, cudaStream_t st)
+{
+    std::vector<Stencil<T>> sv(1, S);
+    return gneb_batch_run<T>(s, sv, std::vector<int>{a.M}, std::vector<long long>{0}, chain, vel, a, E_dev, fmax_dev, st);
+}
+
+#define SPGB_MIN_INST(T)                                                                                               \
+    template int vp_minimise<T>(MinScratch **, const Stencil<T> &, void *, void *, const MinArgs &, int *, double *,    \
+                                cudaStream_t);                                                                         \
+    template int gneb_run<T>(MinScratch **, const Stencil<T> &, void *, void *, const GnebArgs &, double *, double *,   \
+                             cudaStream_t);                                                                            \
+    template int gneb_batch_run<T>(MinScratch **, const std::vector<Stencil<T>> &, const std::vector<int> &,           \
+                                   const std::vector<long long> &, void *, void *, const GnebArgs &, double *,          \
+                                   double *, cudaStream_t);
+SPGB_MIN_INST(float)
+SPGB_MIN_INST(double)
+
+}  // namespace spgb

@@ -1,0 +1,40 @@
+// minimise.h -- velocity-projection minimiser (Appendix D) and GNEB
+// (Sec. GNEB, Appendix F) drivers, single system / single chain and batched.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace spgb {
+
+struct MinScratch;
+void min_scratch_destroy(MinScratch *s);
+
+struct MinArgs {
+    double dt, mass, tol;
+    int max_iter, check_every;
+};
+
+struct GnebArgs {
+    double dt, mass, k;
+    int climbing, M, n_iter;
+};
+
+template <typename T>
+int vp_minimise(MinScratch **s, const Stencil<T> &S, void *n, void *v, const MinArgs &a, int *iters, double *max_torque,
+                cudaStream_t st);
+
+template <typename T>
+int gneb_run(MinScratch **s, const Stencil<T> &S, void *chain, void *vel, const GnebArgs &a, double *E_dev,
+             double *fmax_dev, cudaStream_t st);
+
+// Batched GNEB: chain c has M[c] images of stencils[c].N spins stored from
+// record offset spin0[c] of chain/vel; energies[img0[c] + v] and
+// fmax[c] receive the results, img0 the prefix sums of M.
+template <typename T>
+int gneb_batch_run(MinScratch **s, const std::vector<Stencil<T>> &stencils, const std::vector<int> &M,
+                   const std::vector<long long> &spin0, void *chain, void *vel, const GnebArgs &a, double *E_dev,
+                   double *fmax_dev, cudaStream_t st);
+
+}  // namespace spgb

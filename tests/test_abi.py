@@ -1,0 +1,115 @@
+"""Host-side checks of the C-ABI library: it loads, exports every entry point
+that include/spirit_gb.h declares, and rejects bad arguments on the host
+before anything is launched.  No GPU needed."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1901_11350_gb300 import binding as B
+from paper_1901_11350_gb300 import build
+from paper_1901_11350_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return B.lib()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^(?:int|void|const char \*)\s*\*?\s*(sp_\w+)\s*\(", txt, re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in B.SIGNATURES, n
+
+
+def test_create_rejects_bad_precision(L):
+    h = C.c_void_p()
+    assert L.sp_create(C.byref(h), 7) == -1
+    assert L.sp_create(None, 0) == -1
+
+
+def test_call_order_and_argument_errors(L):
+    h = C.c_void_p()
+    assert L.sp_create(C.byref(h), 0) == 0
+    H = B.Hamiltonian()
+    assert L.sp_set_hamiltonian(h, C.byref(H)) == -2  # geometry first
+    brav = (C.c_double * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    basis = (C.c_double * 3)(0, 0, 0)
+    mu = (C.c_double * 1)(2.0)
+    per = (C.c_int * 3)(0, 0, 0)
+    bad = (C.c_int * 3)(4, 0, 1)
+    assert L.sp_set_geometry(h, brav, 1, basis, bad, per, 1.0, mu) == -1
+    assert b"n_cells" in L.sp_last_error(h)
+    good = (C.c_int * 3)(4, 3, 1)
+    assert L.sp_set_geometry(h, brav, 1, basis, good, per, -1.0, mu) == -1
+    assert L.sp_set_geometry(h, brav, 5, basis, good, per, 1.0, mu) == -1
+    assert L.sp_set_geometry(h, brav, 1, basis, good, per, 1.0, mu) == 0
+    p = B.LLGParams(1, 1e-3, 0.1, 0.0, 0, 0, 0)
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 1, None) == -2  # no Hamiltonian yet
+    H.n_shells = 9
+    assert L.sp_set_hamiltonian(h, C.byref(H)) == -1
+    H.n_shells = 1
+    H.J[0] = 1.0
+    assert L.sp_set_hamiltonian(h, C.byref(H)) == 0
+    n = C.c_int()
+    assert L.sp_n_spins(h, C.byref(n)) == 0 and n.value == 12
+    # arguments checked before any launch
+    assert L.sp_llg_step(h, None, C.byref(p), 1, None) == -1
+    assert L.sp_llg_step(h, C.c_void_p(8), C.byref(p), 1, None) == -1  # misaligned
+    p.dt = 0.0
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 1, None) == -1
+    p.dt, p.solver = 1e-3, 5
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 1, None) == -1
+    p.solver, p.T = 1, -1.0
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 1, None) == -1
+    p.T = 0.0
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), -1, None) == -1
+    assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 0, None) == 0  # nothing to do
+    assert L.sp_effective_field(h, C.c_void_p(256), C.c_void_p(256), None) == -1  # aliasing
+    g = B.GNEBParams(0.1, 1.0, 1.0, 1)
+    assert L.sp_gneb_step(h, C.c_void_p(256), C.c_void_p(512), 2, C.byref(g), 1, C.c_void_p(64), C.c_void_p(64),
+                          None) == -1  # fewer than 3 images
+    it, mt = C.c_int(), C.c_double()
+    assert L.sp_minimise(h, C.c_void_p(256), C.c_void_p(512), 0.1, 1.0, 1e-6, 10, 0, C.byref(it), C.byref(mt),
+                         None) == -1  # check_every < 1
+    assert L.sp_destroy(h) == 0
+    assert L.sp_destroy(None) == 0
+
+
+def test_stencil_limits_and_unsupported_requests(L):
+    # dipole term with a periodic direction is not implemented
+    g = I.square(8, 8, periodic=(True, False))
+    with pytest.raises(B.SpinError) as e:
+        B.Context(g, dict(J=[1.0], dipole="fft"))
+    assert e.value.code == -4
+    # too many directed neighbours
+    with pytest.raises(B.SpinError) as e:
+        B.Context(I.simple_cubic(8), dict(J=[1.0] * 8))
+    assert e.value.code == -1
+    # a periodic bond longer than the periodic extent
+    with pytest.raises(B.SpinError) as e:
+        B.Context(I.square(2, 2, periodic=(True, True)), dict(pairs=[(0, 0, (3, 0, 0), 1.0, (0, 0, 0))]))
+    assert e.value.code == -4
+    # explicit self pair
+    with pytest.raises(B.SpinError) as e:
+        B.Context(I.square(4, 4), dict(pairs=[(0, 0, (0, 0, 0), 1.0, (0, 0, 0))]))
+    assert e.value.code == -1
+    # a fine context: SC with three shells = 26 directed neighbours
+    c = B.Context(I.simple_cubic(5), dict(J=[1.0, -0.2, 0.05], dmi_kind="bulk", D=[0.2]))
+    assert c.N == 125
+    c.close()

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 contexts must match the oracle to 1e-12 relative per evaluation and per
+step; FP32 contexts to max |dn| <= 1e-5 per step from an identical input
+state (and 1e-5 relative on fields).  Inputs come from the seeded generators
+only.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1901_11350_gb300 import binding as B
+from paper_1901_11350_gb300 import build
+from paper_1901_11350_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    B.lib()
+
+
+def _cases():
+    c1 = I.cfg_square_32()
+    c2 = I.cfg_sc_128(4)
+    return {
+        "square32_open": (c1["geometry"], c1["hamiltonian"]),
+        "sc_periodic_ragged": (dict(c2["geometry"], n_cells=[13, 11, 9]), dict(c2["hamiltonian"], B=[0.2, 0, 0.5])),
+        "sc_periodic_n2": (dict(c2["geometry"], n_cells=[2, 3, 5]), c2["hamiltonian"]),
+        "hex_periodic_2shells": (I.hexagonal(17, 15, periodic=(True, True), mu_s=2.0),
+                                 dict(J=[1.0, 0.2], dmi_kind="interfacial", D=[0.3, 0.05], K=[0.1],
+                                      Khat=[[0.3, 0, 1]], B=[0.1, -0.2, 1.5])),
+        "two_basis_pairs": (dict(bravais=[[1, 0, 0], [0.3, 1.1, 0], [0.1, 0.2, 0.9]],
+                                 basis=[[0, 0, 0], [0.4, 0.3, 0.25]], n_cells=[5, 4, 3], periodic=[1, 0, 1],
+                                 lattice_constant=1.7, mu_s=[2.0, 0.8]),
+                            dict(J=[1.0, -0.3], dmi_kind="bulk", D=[0.2], K=[0.1, 0.3],
+                                 Khat=[[0, 0, 1], [1, 1, 0]], B=[0.3, 0.1, -0.4],
+                                 pairs=[(0, 1, (1, 1, 0), 0.4, (0.1, -0.2, 0.3))])),
+        "hex_dipole_open": (I.hexagonal(23, 19, mu_s=3.0),
+                            dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.2], Khat=[[0, 0, 1]],
+                                 B=[0, 0, 0.3], dipole="fft")),
+        "single_spin": (I.square(1, 1, mu_s=2.0), dict(B=[0, 0, 1.0], K=[0.3], Khat=[[1, 0, 0]])),
+    }
+
+
+CASES = _cases()
+
+
+def _oracle(g, h):
+    return oracle.System(g, h)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()[..., :3].astype(np.float64)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_field_and_energy_fp64(name):
+    g, h = CASES[name]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(o.N, 3)
+    n = c.spins(n0)
+    Bg = _np(c.effective_field(n))
+    Bo = o.field(n0)
+    scale = np.abs(Bo).max() + 1e-300
+    assert np.abs(Bg - Bo).max() <= 1e-12 * scale
+    assert np.abs(_np(c.gradient(n)) + Bo).max() <= 1e-12 * scale
+    e = c.energy(n).cpu().numpy()
+    eo = o.energy(n0)
+    assert np.abs(e - eo).max() <= 1e-12 * (np.abs(eo).max() + 1)
+    t = c.max_torque(n).item()
+    to = np.linalg.norm(np.cross(n0, Bo), axis=1).max()
+    assert abs(t - to) <= 1e-12 * (to + 1)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_field_fp32(name):
+    g, h = CASES[name]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f32")
+    n0 = I.random_spins(o.N, 4)
+    n0 = n0.astype(np.float32).astype(np.float64)
+    Bg = _np(c.effective_field(c.spins(n0)))
+    Bo = o.field(n0)
+    assert np.abs(Bg - Bo).max() <= 1e-5 * np.abs(Bo).max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("solver", ["depondt", "heun"])
+@pytest.mark.parametrize("T", [0.0, 10.0])
+def test_llg_step_fp64(name, solver, T):
+    g, h = CASES[name]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(o.N, 5)
+    kw = dict(solver=solver, dt=2e-3, alpha=0.2, T=T, seed=77, step0=123456789012, replica=3)
+    n = c.spins(n0)
+    c.llg_step(n, 3, **kw)
+    no = o.llg(n0, 3, **kw)
+    assert np.abs(_np(n) - no).max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("solver", ["depondt", "heun"])
+def test_llg_step_fp32_per_step(name, solver):
+    g, h = CASES[name]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f32")
+    n0 = I.random_spins(o.N, 6).astype(np.float32).astype(np.float64)
+    kw = dict(solver=solver, dt=1e-3, alpha=0.1, T=10.0, seed=1, step0=40)
+    n = c.spins(n0)
+    c.llg_step(n, 1, **kw)
+    no = o.llg(n0, 1, **kw)
+    assert np.abs(_np(n) - no).max() <= 1e-5
+    assert np.abs(np.linalg.norm(_np(n), axis=1) - 1).max() <= 1e-6
+
+
+def test_square32_depondt_1000_steps_fp64():
+    # the 32x32 square workload: 1000 damped Depondt steps, spins and energy
+    cfg = I.cfg_square_32()
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(o.N, cfg["spin_seed"])
+    n = c.spins(n0)
+    c.llg_step(n, r["n_steps"], solver=r["solver"], dt=r["dt"], alpha=r["alpha"])
+    no = o.llg(n0, r["n_steps"], solver=r["solver"], dt=r["dt"], alpha=r["alpha"])
+    assert np.abs(_np(n) - no).max() <= 1e-11
+    eo = o.energy(no)[0]
+    assert abs(c.energy(n)[0].item() - eo) <= 1e-12 * abs(eo)
+
+
+def test_stochastic_heun_100_steps_fp64():
+    cfg = I.cfg_sc_128(12)
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(o.N, cfg["spin_seed"])
+    kw = dict(solver="heun", dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"])
+    n = c.spins(n0)
+    c.llg_step(n, 100, **kw)
+    no = o.llg(n0, 100, **kw)
+    assert np.abs(_np(n) - no).max() <= 1e-11
+
+
+def test_llg_resume_is_bit_exact_on_gpu():
+    cfg = I.cfg_sc_128(8)
+    c = B.Context(cfg["geometry"], cfg["hamiltonian"], "f32")
+    n0 = I.random_spins(c.N, 1)
+    kw = dict(solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=1)
+    a = c.spins(n0)
+    c.llg_step(a, 10, **kw)
+    b = c.spins(n0)
+    c.llg_step(b, 4, **kw)
+    c.llg_step(b, 6, step0=4, **kw)
+    assert torch.equal(a, b)
+
+
+def test_dipole_fp32_against_direct_sum():
+    g = I.hexagonal(37, 29, mu_s=3.0)
+    h = dict(dipole="fft")
+    o = _oracle(g, dict(dipole="direct"))
+    n0 = I.random_spins(o.N, 9)
+    Bo = o.dipole_field(n0, "direct")
+    c = B.Context(g, h, "f32")
+    Bg = _np(c.effective_field(c.spins(n0)))
+    assert np.abs(Bg - Bo).max() <= 1e-5 * np.abs(Bo).max()
+    c64 = B.Context(g, h, "f64")
+    Bg64 = _np(c64.effective_field(c64.spins(n0)))
+    assert np.abs(Bg64 - Bo).max() <= 1e-12 * np.abs(Bo).max()
+
+
+def test_vp_minimiser_parity_fp64():
+    c1 = I.cfg_square_32()
+    g = dict(c1["geometry"], n_cells=[12, 10, 1], periodic=[1, 0, 0])
+    h = c1["hamiltonian"]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(o.N, 12)
+    n, v = c.spins(n0), c.spins(np.zeros_like(n0))
+    it, mt = c.minimise(n, v, dt=0.1, tol=0.0, max_iter=60, check_every=16)
+    no, vo, ito, mto = o.minimise(n0, dt=0.1, tol=0.0, max_iter=60)
+    assert it == ito == 60
+    assert np.abs(_np(n) - no).max() <= 1e-10
+    assert np.abs(_np(v) - vo).max() <= 1e-10
+    assert abs(mt - mto) <= 1e-10 * mto
+    # converge to a tolerance: same iteration count and final energy
+    n, v = c.spins(n0), c.spins(np.zeros_like(n0))
+    it, mt = c.minimise(n, v, dt=0.1, tol=1e-8, max_iter=20000, check_every=50)
+    no, vo, ito, mto = o.minimise(n0, dt=0.1, tol=1e-8, max_iter=20000)
+    assert mt < 1e-8 and abs(it - ito) <= 2
+    eo = o.energy(no)[0]
+    assert abs(c.energy(n)[0].item() - eo) <= 1e-10 * abs(eo)
+
+
+def test_gneb_parity_fp64():
+    g = I.hexagonal(9, 8, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.35], K=[0.08], Khat=[[0, 0, 1]], B=[0, 0, 1.2])
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    r = I.site_positions(g)
+    a = I.ferromagnet(o.N)
+    b = I.neel_skyrmion(r, r.mean(axis=0), 3.5)
+    chain0 = I.slerp_chain(a, b, 7, r, r.mean(axis=0))
+    chain, vel = c.spins(chain0), c.spins(np.zeros_like(chain0))
+    E, F = c.gneb_step(chain, vel, n_iter=25, k_spring=1.0, climbing=True, dt=0.1)
+    ch_o, v_o, E_o, mf_o, it_o = o.gneb(chain0, n_iter=25, k_spring=1.0, climbing=True, dt=0.1)
+    assert np.abs(_np(chain) - ch_o).max() <= 1e-10
+    assert np.abs(_np(vel) - v_o).max() <= 1e-10
+    assert np.abs(E.cpu().numpy() - E_o).max() <= 1e-10 * np.abs(E_o).max()
+    assert abs(F.item() - mf_o) <= 1e-10 * mf_o
+    # splitting the iterations over two calls gives the same chain
+    chain2, vel2 = c.spins(chain0), c.spins(np.zeros_like(chain0))
+    c.gneb_step(chain2, vel2, n_iter=10, dt=0.1)
+    c.gneb_step(chain2, vel2, n_iter=15, dt=0.1)
+    assert torch.equal(chain, chain2)
+
+
+def test_gneb_stoner_wohlfarth_barrier_fp64():
+    mu, K, Bz = 2.0, 1.0, 3.0
+    g = I.square(1, 1, mu_s=mu)
+    c = B.Context(g, dict(B=[0, 0, Bz], K=[K], Khat=[[0, 0, 1]]), "f64")
+    chain0 = I.slerp_chain(np.array([[0, 0, -1.0]]), np.array([[0, 0, 1.0]]), 9)
+    chain, vel = c.spins(chain0), c.spins(np.zeros_like(chain0))
+    for _ in range(20):
+        E, F = c.gneb_step(chain, vel, n_iter=50, dt=0.5)
+        if F.item() < 1e-12:
+            break
+    hh = mu * oracle.MU_B * Bz / (2 * K)
+    E = E.cpu().numpy()
+    assert abs(E.max() - E[0] - K * (1 - hh) ** 2) < 1e-12
+
+
+def test_sc128_heun_step_fp32_full_size():
+    # the 128^3 stochastic Heun workload at full size, every spin checked
+    cfg = I.cfg_sc_128()
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f32")
+    n0 = I.random_spins(o.N, cfg["spin_seed"]).astype(np.float32).astype(np.float64)
+    kw = dict(solver="heun", dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"], step0=5000)
+    n = c.spins(n0)
+    c.llg_step(n, 1, **kw)
+    no = o.llg(n0, 1, **kw)
+    assert np.abs(_np(n) - no).max() <= 1e-5
+
+
+def test_hex512_dipole_fp32_on_crop():
+    # the 512x512 dipolar monolayer: FP32 FFT field against the FP64 direct
+    # sum over all 262144 spins, at the sites of a 64x64 crop
+    cfg = I.cfg_hex_dipole()
+    g, h = cfg["geometry"], cfg["hamiltonian"]
+    o = _oracle(g, dict(h, dipole="direct"))
+    n0 = I.random_spins(o.N, cfg["spin_seed"])
+    c = B.Context(g, dict(h), "f32")
+    Bg = _np(c.effective_field(c.spins(n0)))
+    Bl = o.field(n0, dipole="none")
+    idx = np.array([(224 + y) * 512 + 224 + x for y in range(64) for x in range(64)])
+    Bd = o.dipole_field_direct_at(n0, idx)
+    ref = Bl[idx] + Bd
+    assert np.abs(Bg[idx] - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs((Bg[idx] - Bl[idx]) - Bd).max() <= 1e-4 * np.abs(Bd).max()
