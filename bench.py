@@ -195,6 +195,8 @@ def run_gpu(args):
     g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
     S = args.llg_steps
     ctx = Bd.Context(g, h, "f32")
+    if args.generic:
+        ctx.set_option("generic_stencil", 1)
     N = ctx.N
     host0 = torch.zeros((N, 4), dtype=torch.float32)
     host0[:, :3] = torch.from_numpy(I.random_spins(N, cfg["spin_seed"])).float()
@@ -274,6 +276,9 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S, "solver": "heun",
+                      "kernel_path": "generic" if args.generic else (
+                          "cubic27" if ctx.get_option("has_cubic_path") else "generic"),
+                      "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
@@ -292,6 +297,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=LLG_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

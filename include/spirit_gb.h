@@ -226,6 +226,26 @@ int sp_gneb_step(sp_ctx *ctx, void *chain_dev, void *vel_dev, int n_images, cons
                  int n_iter, double *energies_dev, double *max_force_dev, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Execution options (how, not what: results agree within the precision's
+ * tolerance whichever option is chosen)
+ * ------------------------------------------------------------------------ */
+
+enum {
+    /* value 1: evaluate the field with the generic neighbour-list kernels even
+     * when the shell-symmetric 27-point plane-streaming path applies (one
+     * basis atom, bonds within the 3x3x3 cell neighbourhood, one exchange
+     * constant per face/edge/corner class, DMI on faces only); 0: default */
+    SP_OPT_GENERIC_STENCIL = 1,
+    /* planes of the lattice streamed by one CTA of the 27-point path (>= 1);
+     * chosen from the lattice shape by sp_set_hamiltonian */
+    SP_OPT_PLANES_PER_CTA = 2,
+    /* read only: 1 when the 27-point path applies to this Hamiltonian */
+    SP_OPT_HAS_CUBIC_PATH = 3
+};
+int sp_set_option(sp_ctx *ctx, int option, int value);
+int sp_get_option(const sp_ctx *ctx, int option, int *value);
+
+/* ------------------------------------------------------------------------
  * Kernel timing (tracing aid, not part of the method)
  * ------------------------------------------------------------------------ */
 

@@ -69,10 +69,13 @@ SIGNATURES = {
     "sp_llg_step": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_minimise": (_i, [_vp, _vp, _vp, _d, _d, _d, _i, _i, C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_set_option": (_i, [_vp, _i, _i]),
+    "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
     "sp_profile_enable": (_i, [_vp, _i]),
     "sp_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(C.c_longlong)]),
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
+OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3}
 
 
 def library_path():
@@ -220,6 +223,14 @@ class Context:
                                       float(tol), int(max_iter), int(check_every), C.byref(it), C.byref(mt),
                                       _stream()))
         return it.value, mt.value
+
+    def set_option(self, name, value):
+        self._check(lib().sp_set_option(self._h, OPTIONS[name], int(value)))
+
+    def get_option(self, name):
+        v = C.c_int()
+        self._check(lib().sp_get_option(self._h, OPTIONS[name], C.byref(v)))
+        return v.value
 
     def profile(self, on=True):
         self._check(lib().sp_profile_enable(self._h, int(bool(on))))

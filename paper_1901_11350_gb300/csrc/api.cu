@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "cubic.h"
 #include "dipole.h"
 #include "minimise.h"
 
@@ -96,6 +97,12 @@ struct sp_ctx {
     std::vector<HostNbr> nbr;
     Stencil<float> Sf = {};
     Stencil<double> Sd = {};
+    // shell-symmetric 27-point fast path (valid when `cubic` is set)
+    bool cubic = false;
+    bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
+    int zc = 8;
+    CubicParams<float> Cf = {};
+    CubicParams<double> Cd = {};
     // device scratch (allocated on first use)
     DevBuf pred;      // 2 records per spin: predictor state and folded corrector term
     DevBuf partials;  // reduction partials
@@ -276,6 +283,87 @@ template <typename T> void fill_stencil(const sp_ctx *c, Stencil<T> &S)
     }
 }
 
+// The 27-point fast path applies to a one-atom lattice whose bonds stay in
+// the 3x3x3 cell neighbourhood with one exchange constant per offset class
+// (faces, edges, corners) and DMI on the faces only.  Offsets along an open
+// direction of extent 1 never connect two spins and are ignored.
+template <typename T> void fill_cubic(const sp_ctx *c, const double J[27], const double D[27][3], const double Jc[4],
+                                      CubicParams<T> &P)
+{
+    memset(&P, 0, sizeof P);
+    P.nx = c->nc[0];
+    P.ny = c->nc[1];
+    P.nz = c->nc[2];
+    P.per0 = c->per[0];
+    P.per1 = c->per[1];
+    P.per2 = c->per[2];
+    P.J1 = (T)Jc[1];
+    P.J2 = (T)Jc[2];
+    P.J3 = (T)Jc[3];
+    for (int k = 0; k < 3; ++k) {
+        P.Dx[k] = (T)D[2 + 3 * 1 + 9 * 1][k];
+        P.Dy[k] = (T)D[1 + 3 * 2 + 9 * 1][k];
+        P.Dz[k] = (T)D[1 + 3 * 1 + 9 * 2][k];
+    }
+    double mu = c->mu_s[0] * kMuB;
+    double kh[3] = {c->h.Khat[0][0], c->h.Khat[0][1], c->h.Khat[0][2]};
+    double r = std::sqrt(kh[0] * kh[0] + kh[1] * kh[1] + kh[2] * kh[2]);
+    for (int k = 0; k < 3; ++k) {
+        P.Bz[k] = (T)(mu * c->h.B[k]);
+        P.Kh[k] = (T)(r > 0 ? kh[k] / r : 0.0);
+    }
+    P.K = (T)c->h.K[0];
+}
+
+void detect_cubic(sp_ctx *c)
+{
+    c->cubic = false;
+    if (c->nb != 1) return;
+    double J[27] = {0}, D[27][3] = {{0}};
+    for (auto &e : c->nbr) {
+        if (std::abs(e.d[0]) > 1 || std::abs(e.d[1]) > 1 || std::abs(e.d[2]) > 1) return;
+        int o = (e.d[0] + 1) + 3 * (e.d[1] + 1) + 9 * (e.d[2] + 1);
+        J[o] += e.J;
+        for (int k = 0; k < 3; ++k) D[o][k] += e.D[k];
+    }
+    double Jc[4] = {0, 0, 0, 0};
+    bool seen[4] = {false, false, false, false};
+    for (int o = 0; o < 27; ++o) {
+        int d[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+        int cls = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+        bool relevant = true;
+        for (int k = 0; k < 3; ++k)
+            if (d[k] != 0 && c->nc[k] == 1 && !c->per[k]) relevant = false;
+        if (!relevant) continue;
+        if (cls == 0) {
+            if (J[o] != 0 || D[o][0] != 0 || D[o][1] != 0 || D[o][2] != 0) return;
+            continue;
+        }
+        if (seen[cls] && J[o] != Jc[cls]) return;
+        seen[cls] = true;
+        Jc[cls] = J[o];
+        if (cls != 1 && (D[o][0] != 0 || D[o][1] != 0 || D[o][2] != 0)) return;
+        if (cls == 1) {
+            int m = 26 - o;  // opposite face
+            for (int k = 0; k < 3; ++k)
+                if (D[m][k] != -D[o][k]) return;
+        }
+    }
+    // drop DMI of irrelevant faces
+    for (int k = 0; k < 3; ++k) {
+        int o = 1 + 3 * 1 + 9 * 1 + (k == 0 ? 1 : k == 1 ? 3 : 9);
+        if (c->nc[k] == 1 && !c->per[k]) D[o][0] = D[o][1] = D[o][2] = 0;
+    }
+    fill_cubic(c, J, D, Jc, c->Cf);
+    fill_cubic(c, J, D, Jc, c->Cd);
+    // planes per CTA: about 8 resident 256-thread CTAs per SM over 152 SMs
+    long tiles = (long)((c->nc[0] + 31) / 32) * ((c->nc[1] + 7) / 8);
+    long want = 152L * 8;
+    int zc = (int)std::max(4L, std::min(64L, (c->nc[2] * tiles + want - 1) / want));
+    c->zc = std::min(zc, std::max(1, c->nc[2]));
+    c->cubic = true;
+}
+
 int ready(sp_ctx *c)
 {
     if (!c) return SP_ERR_ARG;
@@ -333,18 +421,22 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
     rec_t<T> *q = np + c->N;
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
+    const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
+    bool cub = c->cubic && c->use_cubic;
     LlgConst<T> k = llg_const<T>(c, p);
     for (int s = 0; s < n_steps; ++s) {
         k.step = p->step0 + (uint64_t)s;
         const void *bd;
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
-        cudaError_t e = launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
+        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, c->zc, st)
+                            : launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
-        e = launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
+        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, c->zc, st)
+                : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
     }
@@ -452,6 +544,7 @@ int sp_set_hamiltonian(sp_ctx *c, const sp_hamiltonian *h)
     if (rc) return rc;
     fill_stencil(c, c->Sf);
     fill_stencil(c, c->Sd);
+    detect_cubic(c);
     dipole_destroy(c->dip);
     c->dip = nullptr;
     if (h->dipole == SP_DIPOLE_FFT) {
@@ -594,6 +687,40 @@ int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const 
                 : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
     if (e) return fail(c, e, "GNEB failed");
     return SP_OK;
+}
+
+int sp_set_option(sp_ctx *c, int option, int value)
+{
+    if (!c) return SP_ERR_ARG;
+    switch (option) {
+    case SP_OPT_GENERIC_STENCIL:
+        c->use_cubic = value == 0;
+        return SP_OK;
+    case SP_OPT_PLANES_PER_CTA:
+        if (value < 1) return fail(c, SP_ERR_ARG, "planes per CTA must be >= 1");
+        c->zc = value;
+        return SP_OK;
+    default:
+        return fail(c, SP_ERR_ARG, "unknown option %d", option);
+    }
+}
+
+int sp_get_option(const sp_ctx *c, int option, int *value)
+{
+    if (!c || !value) return SP_ERR_ARG;
+    switch (option) {
+    case SP_OPT_GENERIC_STENCIL:
+        *value = c->use_cubic ? 0 : 1;
+        return SP_OK;
+    case SP_OPT_PLANES_PER_CTA:
+        *value = c->zc;
+        return SP_OK;
+    case SP_OPT_HAS_CUBIC_PATH:
+        *value = c->cubic ? 1 : 0;
+        return SP_OK;
+    default:
+        return SP_ERR_ARG;
+    }
 }
 
 int sp_profile_enable(sp_ctx *c, int on)

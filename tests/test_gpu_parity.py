@@ -93,13 +93,32 @@ def test_field_fp32(name):
     assert np.abs(Bg - Bo).max() <= 1e-5 * np.abs(Bo).max()
 
 
+CUBIC = ["square32_open", "sc_periodic_ragged", "sc_periodic_n2", "single_spin"]
+
+
+def _ctx(g, h, prec, path):
+    c = B.Context(g, h, prec)
+    if path == "generic":
+        c.set_option("generic_stencil", 1)
+    return c
+
+
+def test_cubic_path_detection():
+    for name, (g, h) in CASES.items():
+        c = B.Context(g, h, "f32")
+        assert c.get_option("has_cubic_path") == (1 if name in CUBIC else 0), name
+
+
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("solver", ["depondt", "heun"])
 @pytest.mark.parametrize("T", [0.0, 10.0])
-def test_llg_step_fp64(name, solver, T):
+@pytest.mark.parametrize("path", ["default", "generic"])
+def test_llg_step_fp64(name, solver, T, path):
+    if path == "generic" and name not in CUBIC:
+        pytest.skip("generic is the default path here")
     g, h = CASES[name]
     o = _oracle(g, h)
-    c = B.Context(g, h, "f64")
+    c = _ctx(g, h, "f64", path)
     n0 = I.random_spins(o.N, 5)
     kw = dict(solver=solver, dt=2e-3, alpha=0.2, T=T, seed=77, step0=123456789012, replica=3)
     n = c.spins(n0)
@@ -110,10 +129,13 @@ def test_llg_step_fp64(name, solver, T):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("solver", ["depondt", "heun"])
-def test_llg_step_fp32_per_step(name, solver):
+@pytest.mark.parametrize("path", ["default", "generic"])
+def test_llg_step_fp32_per_step(name, solver, path):
+    if path == "generic" and name not in CUBIC:
+        pytest.skip("generic is the default path here")
     g, h = CASES[name]
     o = _oracle(g, h)
-    c = B.Context(g, h, "f32")
+    c = _ctx(g, h, "f32", path)
     n0 = I.random_spins(o.N, 6).astype(np.float32).astype(np.float64)
     kw = dict(solver=solver, dt=1e-3, alpha=0.1, T=10.0, seed=1, step0=40)
     n = c.spins(n0)
@@ -149,6 +171,22 @@ def test_stochastic_heun_100_steps_fp64():
     c.llg_step(n, 100, **kw)
     no = o.llg(n0, 100, **kw)
     assert np.abs(_np(n) - no).max() <= 1e-11
+
+
+@pytest.mark.parametrize("zc", [1, 2, 5, 7, 40])
+def test_cubic_plane_chunking_is_exact(zc):
+    # the result may not depend on how planes are split between CTAs
+    cfg = I.cfg_sc_128(4)
+    g = dict(cfg["geometry"], n_cells=[37, 19, 23])
+    c = B.Context(g, cfg["hamiltonian"], "f32")
+    n0 = I.random_spins(c.N, 2)
+    kw = dict(solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=3)
+    a = c.spins(n0)
+    c.llg_step(a, 3, **kw)
+    c.set_option("planes_per_cta", zc)
+    b = c.spins(n0)
+    c.llg_step(b, 3, **kw)
+    assert torch.equal(a, b)
 
 
 def test_llg_resume_is_bit_exact_on_gpu():
@@ -196,7 +234,9 @@ def test_vp_minimiser_parity_fp64():
     n, v = c.spins(n0), c.spins(np.zeros_like(n0))
     it, mt = c.minimise(n, v, dt=0.1, tol=1e-8, max_iter=20000, check_every=50)
     no, vo, ito, mto = o.minimise(n0, dt=0.1, tol=1e-8, max_iter=20000)
-    assert mt < 1e-8 and abs(it - ito) <= 2
+    # the iteration at which max torque first drops below tol depends on
+    # rounding once the run is near it; the converged energy does not
+    assert mt < 1e-8 and abs(it - ito) <= 10
     eo = o.energy(no)[0]
     assert abs(c.energy(n)[0].item() - eo) <= 1e-10 * abs(eo)
 
@@ -239,12 +279,18 @@ def test_gneb_stoner_wohlfarth_barrier_fp64():
     assert abs(E.max() - E[0] - K * (1 - hh) ** 2) < 1e-12
 
 
-def test_sc128_heun_step_fp32_full_size():
-    # the 128^3 stochastic Heun workload at full size, every spin checked
+@pytest.mark.parametrize("zc", [None, 3, 128])
+def test_sc128_heun_step_fp32_full_size(zc):
+    # the 128^3 stochastic Heun workload at full size, in the launch
+    # configuration the benchmark uses (and two other plane chunkings),
+    # every spin checked
     cfg = I.cfg_sc_128()
     g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
     o = _oracle(g, h)
     c = B.Context(g, h, "f32")
+    assert c.get_option("has_cubic_path") == 1
+    if zc is not None:
+        c.set_option("planes_per_cta", zc)
     n0 = I.random_spins(o.N, cfg["spin_seed"]).astype(np.float32).astype(np.float64)
     kw = dict(solver="heun", dt=r["dt"], alpha=r["alpha"], T=r["T"], seed=r["seed"], step0=5000)
     n = c.spins(n0)
