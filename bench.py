@@ -197,6 +197,8 @@ def run_gpu(args):
     ctx = Bd.Context(g, h, "f32")
     if args.generic:
         ctx.set_option("generic_stencil", 1)
+    if args.zc:
+        ctx.set_option("planes_per_cta", args.zc)
     N = ctx.N
     host0 = torch.zeros((N, 4), dtype=torch.float32)
     host0[:, :3] = torch.from_numpy(I.random_spins(N, cfg["spin_seed"])).float()
@@ -297,6 +299,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=LLG_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
     args = ap.parse_args()
