@@ -175,6 +175,16 @@ int sp_energy(sp_ctx *ctx, const void *n_dev, double *e_dev, void *stream);
 /* max_i |n_i x B_eff,i| (meV) written to torque_dev (DEVICE, 1 double). */
 int sp_max_torque(sp_ctx *ctx, const void *n_dev, double *torque_dev, void *stream);
 
+/* Berg-Luescher topological charge (Appendix A) of a 2D lattice with one
+ * basis atom (n2 = 1), written to Q_dev (DEVICE, 1 double): the signed solid
+ * angles of the two elementary triangles (c0,c1)(c0+1,c1)(c0,c1+1) and
+ * (c0+1,c1)(c0+1,c1+1)(c0,c1+1) of every cell, numbered counter-clockwise
+ * about +z, summed in FP64 and divided by 4 pi; triangles crossing an open
+ * edge are left out.  A_l = 2 atan2(n_i.(n_j x n_k), 1 + n_i.n_j + n_i.n_k +
+ * n_j.n_k), the same angle and sign as the paper's half-angle cosine form.
+ * SP_ERR_UNSUPPORTED for other lattices. */
+int sp_topological_charge(sp_ctx *ctx, const void *n_dev, double *Q_dev, void *stream);
+
 /* ------------------------------------------------------------------------
  * Time stepping (Eq. 3, Eq. 4, Appendix B)
  * ------------------------------------------------------------------------ */
@@ -224,6 +234,30 @@ int sp_minimise(sp_ctx *ctx, void *n_dev, void *v_dev, double dt, double mass, d
  * max over interior images and spins of |F_v,i| after the last iteration. */
 int sp_gneb_step(sp_ctx *ctx, void *chain_dev, void *vel_dev, int n_images, const sp_gneb_params *p,
                  int n_iter, double *energies_dev, double *max_force_dev, void *stream);
+
+/* Batched GNEB: n_chains independent chains, each with its own context
+ * (geometry and Hamiltonian; all contexts of one precision, no dipole term),
+ * stepped together -- every kernel of an iteration covers all images of all
+ * chains in one launch, whatever their lattice sizes and image counts.
+ *   ctxs[c]       context of chain c (host array)
+ *   chains_dev    ONE device buffer; chain c's n_images[c] x N_c records start
+ *                 at record offset offsets[c] (image-major); chains must not
+ *                 overlap
+ *   vel_dev       velocities, same layout (caller-owned, carried in and out)
+ *   offsets[c], n_images[c] (>= 3)   host arrays
+ *   energies_dev  DEVICE, sum(n_images) doubles: chain c's image energies at
+ *                 the prefix sum of n_images before c
+ *   max_force_dev DEVICE, n_chains doubles: per chain, max over interior
+ *                 images and spins of |F|, after the last iteration
+ * Same iteration as sp_gneb_step.  Scratch and tables belong to ctxs[0].  The
+ * first call with a given batch layout uploads tables and allocates scratch
+ * (it synchronises the stream): make it before any stream capture; calls with
+ * an unchanged layout only launch kernels.  Outside a capture, runs of
+ * iterations are replayed from a CUDA graph on a private stream ordered
+ * after and before `stream` by events. */
+int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void *vel_dev, const long long *offsets,
+                       const int *n_images, const sp_gneb_params *p, int n_iter, double *energies_dev,
+                       double *max_force_dev, void *stream);
 
 /* ------------------------------------------------------------------------
  * Execution options (how, not what: results agree within the precision's

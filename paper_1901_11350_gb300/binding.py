@@ -66,9 +66,12 @@ SIGNATURES = {
     "sp_gradient": (_i, [_vp, _vp, _vp, _vp]),
     "sp_energy": (_i, [_vp, _vp, _vp, _vp]),
     "sp_max_torque": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_topological_charge": (_i, [_vp, _vp, _vp, _vp]),
     "sp_llg_step": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_minimise": (_i, [_vp, _vp, _vp, _d, _d, _d, _i, _i, C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
+                               C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_set_option": (_i, [_vp, _i, _i]),
     "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
     "sp_profile_enable": (_i, [_vp, _i]),
@@ -211,6 +214,11 @@ class Context:
         self._check(lib().sp_max_torque(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
         return out
 
+    def topological_charge(self, n, out=None):
+        out = torch.empty(1, dtype=torch.float64, device=n.device) if out is None else out
+        self._check(lib().sp_topological_charge(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
+        return out
+
     def llg_step(self, n, n_steps=1, solver="depondt", dt=1e-3, alpha=0.1, T=0.0, seed=0, step0=0, replica=0):
         p = LLGParams(SOLVER[solver], float(dt), float(alpha), float(T), int(seed), int(step0), int(replica))
         self._check(lib().sp_llg_step(self._h, self._spin_arg(n, "n"), C.byref(p), int(n_steps), _stream()))
@@ -250,3 +258,27 @@ class Context:
         self._check(lib().sp_gneb_step(self._h, self._spin_arg(chain, "chain", M), self._spin_arg(vel, "vel", M), M,
                                        C.byref(p), int(n_iter), _ptr(E), _ptr(F), _stream()))
         return E, F
+
+
+def gneb_batch_step(ctxs, chains, vel, offsets, n_images, n_iter=1, k_spring=1.0, climbing=True, dt=0.1, mass=1.0,
+                    energies=None, max_force=None):
+    """Step many chains (one context each) together; `chains` and `vel` are
+    one flat CUDA tensor of 4-wide records each, chain c starting at record
+    offsets[c].  Returns (energies, max_force) device tensors."""
+    L = lib()
+    n = len(ctxs)
+    dtype = ctxs[0].dtype
+    for t, name in ((chains, "chains"), (vel, "vel")):
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.shape[-1] == 4):
+            raise ValueError("%s must be a contiguous CUDA %s tensor of 4-wide records" % (name, dtype))
+    E = torch.empty(int(sum(n_images)), dtype=torch.float64, device=chains.device) if energies is None else energies
+    F = torch.empty(n, dtype=torch.float64, device=chains.device) if max_force is None else max_force
+    handles = (C.c_void_p * n)(*[c._h for c in ctxs])
+    offs = (C.c_longlong * n)(*[int(x) for x in offsets])
+    ims = (C.c_int * n)(*[int(x) for x in n_images])
+    p = GNEBParams(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+    rc = L.sp_gneb_batch_step(handles, n, _ptr(chains), _ptr(vel), offs, ims, C.byref(p), int(n_iter), _ptr(E),
+                              _ptr(F), _stream())
+    if rc:
+        raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
+    return E, F

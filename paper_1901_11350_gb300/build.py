@@ -14,11 +14,14 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspirit_gb.so")
-SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "static_step.cu"]
+SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "topo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                 "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
+# extra nvcc flags for experiments (e.g. -DSPGB_CUBIC_MINB=4); a change of
+# flags rebuilds everything
+EXTRA = os.environ.get("SPGB_NVCC_EXTRA", "").split()
 
 
 def _deps():
@@ -47,6 +50,15 @@ def _compile(src, extra):
 
 def build(verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
+    extra = list(extra) + EXTRA
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags = " ".join(FLAGS + extra)
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        for f in os.listdir(BUILD):
+            if f.endswith(".o"):
+                os.remove(os.path.join(BUILD, f))
+        with open(stamp, "w") as fh:
+            fh.write(flags)
     srcs = [os.path.join(CSRC, s) for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))

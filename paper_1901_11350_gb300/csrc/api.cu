@@ -8,109 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
-#include "cubic.h"
-#include "dipole.h"
-#include "minimise.h"
-
-using namespace spgb;
-
-namespace {
-
-struct HostNbr {
-    int b, jb, d[3];
-    double J, D[3];
-};
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-// Pool of CUDA event pairs bracketing kernel launches (sp_profile_*).
-struct Profiler {
-    static constexpr int kPairs = 4096;
-    bool on = false;
-    std::vector<cudaEvent_t> ev;  // 2 per pair
-    std::vector<int> kind;
-    int used = 0;
-    double ms[SP_PROF_KINDS] = {0, 0, 0};
-    long long count[SP_PROF_KINDS] = {0, 0, 0};
-
-    cudaError_t drain()
-    {
-        for (int p = 0; p < used; ++p) {
-            cudaError_t e = cudaEventSynchronize(ev[2 * p + 1]);
-            if (e != cudaSuccess) return e;
-            float t = 0;
-            e = cudaEventElapsedTime(&t, ev[2 * p], ev[2 * p + 1]);
-            if (e != cudaSuccess) return e;
-            ms[kind[p]] += t;
-            count[kind[p]] += 1;
-        }
-        used = 0;
-        return cudaSuccess;
-    }
-    // returns the pair index to record into, or -1 when profiling is off
-    int begin(int k, cudaStream_t st)
-    {
-        if (!on) return -1;
-        if (ev.empty()) {
-            ev.resize(2 * kPairs);
-            kind.resize(kPairs);
-            for (auto &e : ev) cudaEventCreate(&e);
-        }
-        if (used == kPairs && drain() != cudaSuccess) return -1;
-        int p = used++;
-        kind[p] = k;
-        cudaEventRecord(ev[2 * p], st);
-        return p;
-    }
-    void end(int p, cudaStream_t st)
-    {
-        if (p >= 0) cudaEventRecord(ev[2 * p + 1], st);
-    }
-    ~Profiler()
-    {
-        for (auto &e : ev) cudaEventDestroy(e);
-    }
-};
-
-}  // namespace
-
-struct sp_ctx {
-    int prec = SP_F32;
-    int device = 0;
-    std::string err;
-    bool have_geom = false, have_ham = false;
-    // geometry
-    double A[3][3] = {};
-    int nb = 1;
-    double basis[SP_MAX_BASIS][3] = {};
-    int nc[3] = {1, 1, 1}, per[3] = {0, 0, 0};
-    double a = 1.0;
-    double mu_s[SP_MAX_BASIS] = {};
-    int N = 0;
-    // Hamiltonian
-    sp_hamiltonian h = {};
-    std::vector<sp_pair> pairs;
-    std::vector<HostNbr> nbr;
-    Stencil<float> Sf = {};
-    Stencil<double> Sd = {};
-    // shell-symmetric 27-point fast path (valid when `cubic` is set)
-    bool cubic = false;
-    bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
-    int zc = 8;
-    CubicParams<float> Cf = {};
-    CubicParams<double> Cd = {};
-    // device scratch (allocated on first use)
-    DevBuf pred;      // 2 records per spin: predictor state and folded corrector term
-    DevBuf partials;  // reduction partials
-    DevBuf bdd;       // dipole field, 1 record per spin
-    DipolePlan *dip = nullptr;
-    MinScratch *mins = nullptr;
-    Profiler prof;
-};
+#include "ctx.h"
 
 namespace {
 
@@ -313,6 +211,19 @@ template <typename T> void fill_cubic(const sp_ctx *c, const double J[27], const
         P.Kh[k] = (T)(r > 0 ? kh[k] / r : 0.0);
     }
     P.K = (T)c->h.K[0];
+    // DMI kind: none, bulk-like (face vector along its bond, one magnitude) or general
+    bool none = true, bulk = true;
+    double Dm = D[2 + 3 * 1 + 9 * 1][0];
+    const int faces[3] = {2 + 3 * 1 + 9 * 1, 1 + 3 * 2 + 9 * 1, 1 + 3 * 1 + 9 * 2};
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            double v = D[faces[a]][k];
+            if (v != 0) none = false;
+            double want = (k == a) ? Dm : 0.0;
+            bool irrelevant = c->nc[a] == 1 && !c->per[a];
+            if (!irrelevant && v != want) bulk = false;
+        }
+    P.dmi_mode = none ? 0 : (bulk ? 1 : 2);
 }
 
 void detect_cubic(sp_ctx *c)
@@ -686,6 +597,75 @@ int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const 
                 ? gneb_run<double>(&c->mins, c->Sd, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream)
                 : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
     if (e) return fail(c, e, "GNEB failed");
+    return SP_OK;
+}
+
+int sp_topological_charge(sp_ctx *c, const void *n_dev, double *Q_dev, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n_dev, "spins"))) return rc;
+    if (!Q_dev) return fail(c, SP_ERR_ARG, "NULL output");
+    if (c->nb != 1 || c->nc[2] != 1) return fail(c, SP_ERR_UNSUPPORTED, "topological charge needs a 2D one-atom lattice");
+    double cz = c->A[0][0] * c->A[1][1] - c->A[0][1] * c->A[1][0];
+    if ((rc = ensure(c, c->partials, sizeof(double) * 8 * (size_t)blocks_for(c->N)))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = c->prec == SP_F64
+                        ? launch_topo<double>(c->Sd, (const dq4 *)n_dev, cz < 0, (double *)c->partials.p, Q_dev, st)
+                        : launch_topo<float>(c->Sf, (const float4 *)n_dev, cz < 0, (double *)c->partials.p, Q_dev, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "topological charge launch");
+    return SP_OK;
+}
+
+int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void *vel_dev, const long long *offsets,
+                       const int *n_images, const sp_gneb_params *p, int n_iter, double *energies_dev,
+                       double *max_force_dev, void *stream)
+{
+    if (!ctxs || n_chains < 1 || !ctxs[0]) return SP_ERR_ARG;
+    sp_ctx *c0 = ctxs[0];
+    if (!offsets || !n_images || !p) return fail(c0, SP_ERR_ARG, "NULL batch description");
+    if (!energies_dev || !max_force_dev) return fail(c0, SP_ERR_ARG, "NULL output");
+    int rc;
+    if ((rc = check_spins(c0, chains_dev, "chains")) || (rc = check_spins(c0, vel_dev, "velocities"))) return rc;
+    if (n_iter < 0 || !(p->dt > 0) || !(p->mass > 0)) return fail(c0, SP_ERR_ARG, "bad iteration parameters");
+    struct Span {
+        long long a, b;
+    };
+    std::vector<Span> spans;
+    std::vector<int> M;
+    std::vector<long long> off;
+    for (int k = 0; k < n_chains; ++k) {
+        sp_ctx *c = ctxs[k];
+        if (!c) return fail(c0, SP_ERR_ARG, "NULL context for chain %d", k);
+        if (!c->have_geom || !c->have_ham) return fail(c0, SP_ERR_STATE, "chain %d: context not configured", k);
+        if (c->prec != c0->prec) return fail(c0, SP_ERR_ARG, "chain %d: precision differs from chain 0", k);
+        if (c->h.dipole != SP_DIPOLE_NONE) return fail(c0, SP_ERR_UNSUPPORTED, "chain %d: GNEB with the dipole term", k);
+        if (n_images[k] < 3) return fail(c0, SP_ERR_ARG, "chain %d: at least 3 images", k);
+        if (offsets[k] < 0) return fail(c0, SP_ERR_ARG, "chain %d: negative offset", k);
+        long long len = (long long)n_images[k] * c->N;
+        if (offsets[k] + len >= (1LL << 31)) return fail(c0, SP_ERR_ARG, "batch larger than 2^31 records");
+        spans.push_back({offsets[k], offsets[k] + len});
+        M.push_back(n_images[k]);
+        off.push_back(offsets[k]);
+    }
+    std::vector<Span> sorted = spans;
+    std::sort(sorted.begin(), sorted.end(), [](const Span &x, const Span &y) { return x.a < y.a; });
+    for (size_t k = 1; k < sorted.size(); ++k)
+        if (sorted[k].a < sorted[k - 1].b) return fail(c0, SP_ERR_ARG, "chains overlap in the batch buffer");
+    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, 0, n_iter};
+    int e;
+    if (c0->prec == SP_F64) {
+        std::vector<Stencil<double>> S;
+        for (int k = 0; k < n_chains; ++k) S.push_back(ctxs[k]->Sd);
+        e = gneb_batch_run<double>(&c0->mins, S, M, off, chains_dev, vel_dev, a, energies_dev, max_force_dev,
+                                   (cudaStream_t)stream);
+    } else {
+        std::vector<Stencil<float>> S;
+        for (int k = 0; k < n_chains; ++k) S.push_back(ctxs[k]->Sf);
+        e = gneb_batch_run<float>(&c0->mins, S, M, off, chains_dev, vel_dev, a, energies_dev, max_force_dev,
+                                  (cudaStream_t)stream);
+    }
+    if (e) return fail(c0, e, "batched GNEB failed");
     return SP_OK;
 }
 

@@ -1,0 +1,113 @@
+// ctx.h -- the context behind the opaque sp_ctx handle (shared by the
+// translation units that implement the C ABI).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "cubic.h"
+#include "dipole.h"
+#include "internal.h"
+#include "minimise.h"
+
+using namespace spgb;
+
+namespace spgb_ctx {
+
+struct HostNbr {
+    int b, jb, d[3];
+    double J, D[3];
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Pool of CUDA event pairs bracketing kernel launches (sp_profile_*).
+struct Profiler {
+    static constexpr int kPairs = 4096;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per pair
+    std::vector<int> kind;
+    int used = 0;
+    double ms[SP_PROF_KINDS] = {0, 0, 0};
+    long long count[SP_PROF_KINDS] = {0, 0, 0};
+
+    cudaError_t drain()
+    {
+        for (int p = 0; p < used; ++p) {
+            cudaError_t e = cudaEventSynchronize(ev[2 * p + 1]);
+            if (e != cudaSuccess) return e;
+            float t = 0;
+            e = cudaEventElapsedTime(&t, ev[2 * p], ev[2 * p + 1]);
+            if (e != cudaSuccess) return e;
+            ms[kind[p]] += t;
+            count[kind[p]] += 1;
+        }
+        used = 0;
+        return cudaSuccess;
+    }
+    // returns the pair index to record into, or -1 when profiling is off
+    int begin(int k, cudaStream_t st)
+    {
+        if (!on) return -1;
+        if (ev.empty()) {
+            ev.resize(2 * kPairs);
+            kind.resize(kPairs);
+            for (auto &e : ev) cudaEventCreate(&e);
+        }
+        if (used == kPairs && drain() != cudaSuccess) return -1;
+        int p = used++;
+        kind[p] = k;
+        cudaEventRecord(ev[2 * p], st);
+        return p;
+    }
+    void end(int p, cudaStream_t st)
+    {
+        if (p >= 0) cudaEventRecord(ev[2 * p + 1], st);
+    }
+    ~Profiler()
+    {
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace spgb_ctx
+
+using namespace spgb_ctx;
+
+struct sp_ctx {
+    int prec = SP_F32;
+    int device = 0;
+    std::string err;
+    bool have_geom = false, have_ham = false;
+    // geometry
+    double A[3][3] = {};
+    int nb = 1;
+    double basis[SP_MAX_BASIS][3] = {};
+    int nc[3] = {1, 1, 1}, per[3] = {0, 0, 0};
+    double a = 1.0;
+    double mu_s[SP_MAX_BASIS] = {};
+    int N = 0;
+    // Hamiltonian
+    sp_hamiltonian h = {};
+    std::vector<sp_pair> pairs;
+    std::vector<HostNbr> nbr;
+    Stencil<float> Sf = {};
+    Stencil<double> Sd = {};
+    // shell-symmetric 27-point fast path (valid when `cubic` is set)
+    bool cubic = false;
+    bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
+    int zc = 8;
+    CubicParams<float> Cf = {};
+    CubicParams<double> Cd = {};
+    // device scratch (allocated on first use)
+    DevBuf pred;      // 2 records per spin: predictor state and folded corrector term
+    DevBuf partials;  // reduction partials
+    DevBuf bdd;       // dipole field, 1 record per spin
+    DipolePlan *dip = nullptr;
+    MinScratch *mins = nullptr;
+    Profiler prof;
+};
+

@@ -25,6 +25,11 @@ namespace spgb {
 
 namespace {
 
+// resident CTAs per SM the register allocation is held to
+#ifndef SPGB_CUBIC_MINB
+#define SPGB_CUBIC_MINB 3
+#endif
+
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
 
@@ -36,96 +41,184 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <typename T> struct TileRec;
-template <> struct TileRec<float> { using type = float4; };
-template <> struct TileRec<double> { using type = dq4; };
+// ------------------------------------------------------------ arithmetic
+// 3-vectors for the stencil sums: FP32 keeps (x, y) in a float2 so that the
+// sums run on Blackwell's packed f32x2 pipe (one instruction per pair, the
+// same IEEE rounding per component); FP64 uses plain v3<double>.
+struct pv {
+    float2 xy;
+    float z;
+};
+__device__ __forceinline__ pv padd(pv a, pv b) { return {__fadd2_rn(a.xy, b.xy), a.z + b.z}; }
+__device__ __forceinline__ pv psub(pv a, pv b) { return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), a.z - b.z}; }
+__device__ __forceinline__ pv paxpy(float s, pv a, pv b) { return {__ffma2_rn(make_float2(s, s), a.xy, b.xy), fmaf(s, a.z, b.z)}; }
+__device__ __forceinline__ pv pscale(float s, pv a) { return {__fmul2_rn(make_float2(s, s), a.xy), s * a.z}; }
+__device__ __forceinline__ v3<float> tov(pv a) { return {a.xy.x, a.xy.y, a.z}; }
+__device__ __forceinline__ pv fromv(v3<float> a) { return {make_float2(a.x, a.y), a.z}; }
 
-// stage plane z (with halo) into `tile`; out-of-lattice entries are zero
+__device__ __forceinline__ v3<double> padd(v3<double> a, v3<double> b) { return a + b; }
+__device__ __forceinline__ v3<double> psub(v3<double> a, v3<double> b) { return a - b; }
+__device__ __forceinline__ v3<double> paxpy(double s, v3<double> a, v3<double> b) { return axpy(s, a, b); }
+__device__ __forceinline__ v3<double> pscale(double s, v3<double> a) { return s * a; }
+__device__ __forceinline__ v3<double> tov(v3<double> a) { return a; }
+__device__ __forceinline__ v3<double> fromv(v3<double> a) { return a; }
+
+template <typename T> struct PV;
+template <> struct PV<float> { using type = pv; };
+template <> struct PV<double> { using type = v3<double>; };
+template <typename T> using pv_t = typename PV<T>::type;
+
+__device__ __forceinline__ pv tload(const float4 *t, int e)
+{
+    float4 v = t[e];
+    return {make_float2(v.x, v.y), v.z};
+}
+__device__ __forceinline__ v3<double> tload(const dq4 *t, int e) { return ldc(t, e); }
+
+// Box-Muller for FP32 from the multi-function unit: sin/cos of
+// 2 pi (u - 1/2) in (-pi, pi) (so sin(2 pi u) = -sin, cos(2 pi u) = -cos), and
+// sqrt(t) = t rsqrt(t).  Absolute error of eta ~1e-6.
+__device__ __forceinline__ v3<float> box_muller_fast(uint4 x)
+{
+    const float s = 2.3283064365386963e-10f, h = 0.5f * 2.3283064365386963e-10f;
+    const float twopi = 6.283185307179586f;
+    float u0 = fmaf((float)x.x, s, h), u1 = fmaf((float)x.y, s, h);
+    float u2 = fmaf((float)x.z, s, h), u3 = fmaf((float)x.w, s, h);
+    float t0 = fmaxf(-2.f * __logf(u0), 1e-30f), t1 = fmaxf(-2.f * __logf(u2), 1e-30f);
+    float r0 = t0 * rsqrtf(t0), r1 = t1 * rsqrtf(t1);
+    float sa, ca;
+    __sincosf(twopi * (u1 - 0.5f), &sa, &ca);
+    float cb = __cosf(twopi * (u3 - 0.5f));
+    return {-r0 * ca, -r0 * sa, -r1 * cb};
+}
+__device__ __forceinline__ v3<float> thermal_eta(uint4 x, float) { return box_muller_fast(x); }
+__device__ __forceinline__ v3<double> thermal_eta(uint4 x, double) { return box_muller(x, 0.0); }
+
+// ------------------------------------------------------------ plane staging
+// The halo tile of a plane is (TX+2) x (TY+2) records; each thread copies at
+// most two of them.  Their in-plane offsets (periodic wrap or "absent" for an
+// open edge) do not depend on z and are computed once per CTA.
+struct HaloSlot {
+    long off;  // gy * nx + gx
+    int ok;    // inside the lattice in-plane
+};
+
+template <typename T>
+__device__ __forceinline__ HaloSlot halo_slot(const CubicParams<T> &P, int x0, int y0, int e)
+{
+    HaloSlot h{0, 0};
+    if (e >= HN) return h;
+    int hx = e % HX, hy = e / HX;
+    int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+    bool in = true;
+    if (P.per0) {
+        gx %= P.nx;
+        gx += gx < 0 ? P.nx : 0;
+    } else {
+        in = in && gx >= 0 && gx < P.nx;
+    }
+    if (P.per1) {
+        gy %= P.ny;
+        gy += gy < 0 ? P.ny : 0;
+    } else {
+        in = in && gy >= 0 && gy < P.ny;
+    }
+    h.off = (long)gy * P.nx + gx;
+    h.ok = in;
+    return h;
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_rec(rec_t<T> *dst, const rec_t<T> *src)
+{
+    cp_async16(dst, src);
+    if (sizeof(rec_t<T>) == 32) cp_async16(reinterpret_cast<char *>(dst) + 16, reinterpret_cast<const char *>(src) + 16);
+}
+
 template <typename T>
 __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<T> *__restrict__ src, rec_t<T> *tile,
-                                           int x0, int y0, int z)
+                                           const HaloSlot &h0, const HaloSlot &h1, int z)
 {
     bool zin = true;
     if (P.per2) {
-        z %= P.nz;
         z += z < 0 ? P.nz : 0;
+        z -= z >= P.nz ? P.nz : 0;
     } else {
         zin = z >= 0 && z < P.nz;
     }
-    for (int e = threadIdx.x; e < HN; e += TX * TY) {
-        int hx = e % HX, hy = e / HX;
-        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-        bool in = zin;
-        if (P.per0) {
-            gx %= P.nx;
-            gx += gx < 0 ? P.nx : 0;
-        } else {
-            in = in && gx >= 0 && gx < P.nx;
-        }
-        if (P.per1) {
-            gy %= P.ny;
-            gy += gy < 0 ? P.ny : 0;
-        } else {
-            in = in && gy >= 0 && gy < P.ny;
-        }
-        if (in) {
-            const rec_t<T> *g = src + ((long)z * P.ny + gy) * P.nx + gx;
-            if (sizeof(rec_t<T>) == 16) {
-                cp_async16(tile + e, g);
-            } else {
-                cp_async16(tile + e, g);
-                cp_async16(reinterpret_cast<char *>(tile + e) + 16, reinterpret_cast<const char *>(g) + 16);
-            }
-        } else {
-            rec_t<T> zero{};
-            tile[e] = zero;
-        }
+    const rec_t<T> *plane = src + (long)z * P.nx * P.ny;
+    int e0 = threadIdx.x, e1 = threadIdx.x + TX * TY;
+    rec_t<T> zero{};
+    if (zin && h0.ok)
+        copy_rec<T>(tile + e0, plane + h0.off);
+    else
+        tile[e0] = zero;
+    if (e1 < HN) {
+        if (zin && h1.ok)
+            copy_rec<T>(tile + e1, plane + h1.off);
+        else
+            tile[e1] = zero;
     }
-}
-
-template <typename T> __device__ __forceinline__ v3<T> tl(const rec_t<T> *tile, int hx, int hy)
-{
-    return ldc(tile, hy * HX + hx);
 }
 
 // per-plane column summary: centre, in-plane face sum, in-plane corner sum,
 // in-plane face DMI field
 template <typename T> struct Col {
-    v3<T> c, f, k, dm;
+    pv_t<T> c, f, k, dm;
 };
 
-template <typename T>
+// DM: 0 no DMI, 1 bulk (D_o = D ohat on the faces), 2 any face vectors
+template <typename T, int DM>
 __device__ __forceinline__ Col<T> column(const CubicParams<T> &P, const rec_t<T> *tile, int tx, int ty)
 {
-    int hx = tx + 1, hy = ty + 1;
+    int e = (ty + 1) * HX + tx + 1;
     Col<T> r;
-    r.c = tl<T>(tile, hx, hy);
-    v3<T> xp = tl<T>(tile, hx + 1, hy), xm = tl<T>(tile, hx - 1, hy);
-    v3<T> yp = tl<T>(tile, hx, hy + 1), ym = tl<T>(tile, hx, hy - 1);
-    r.f = (xp + xm) + (yp + ym);
-    r.k = (tl<T>(tile, hx + 1, hy + 1) + tl<T>(tile, hx - 1, hy - 1)) +
-          (tl<T>(tile, hx + 1, hy - 1) + tl<T>(tile, hx - 1, hy + 1));
-    r.dm = cross(xp - xm, mk(P.Dx[0], P.Dx[1], P.Dx[2])) + cross(yp - ym, mk(P.Dy[0], P.Dy[1], P.Dy[2]));
+    r.c = tload(tile, e);
+    pv_t<T> xp = tload(tile, e + 1), xm = tload(tile, e - 1);
+    pv_t<T> yp = tload(tile, e + HX), ym = tload(tile, e - HX);
+    r.f = padd(padd(xp, xm), padd(yp, ym));
+    r.k = padd(padd(tload(tile, e + HX + 1), tload(tile, e - HX - 1)), padd(tload(tile, e - HX + 1), tload(tile, e + HX - 1)));
+    if (DM == 0) {
+        r.dm = pscale(T(0), r.c);
+    } else {
+        v3<T> dx = tov(psub(xp, xm)), dy = tov(psub(yp, ym));
+        if (DM == 1) {
+            // D [(n(+x) - n(-x)) x xhat + (n(+y) - n(-y)) x yhat]
+            T D = P.Dx[0];
+            r.dm = fromv(mk(-D * dy.z, D * dx.z, D * (dy.x - dx.y)));
+        } else {
+            r.dm = fromv(cross(dx, mk(P.Dx[0], P.Dx[1], P.Dx[2])) + cross(dy, mk(P.Dy[0], P.Dy[1], P.Dy[2])));
+        }
+    }
     return r;
 }
 
 // Full local field of the middle plane m from planes lo (z-1), m, hi (z+1).
-template <typename T>
+template <typename T, int DM>
 __device__ __forceinline__ v3<T> field_mid(const CubicParams<T> &P, const Col<T> &lo, const Col<T> &m, const Col<T> &hi)
 {
-    v3<T> s1 = m.f + (lo.c + hi.c);
-    v3<T> s2 = m.k + (lo.f + hi.f);
-    v3<T> s3 = lo.k + hi.k;
-    v3<T> B = axpy(P.J1, s1, axpy(P.J2, s2, P.J3 * s3));
-    B = B + m.dm + cross(hi.c - lo.c, mk(P.Dz[0], P.Dz[1], P.Dz[2]));
+    pv_t<T> s1 = padd(m.f, padd(lo.c, hi.c));
+    pv_t<T> s2 = padd(m.k, padd(lo.f, hi.f));
+    pv_t<T> s3 = padd(lo.k, hi.k);
+    pv_t<T> Bp = paxpy(P.J1, s1, paxpy(P.J2, s2, pscale(P.J3, s3)));
+    if (DM != 0) Bp = padd(Bp, m.dm);
+    v3<T> B = tov(Bp);
+    if (DM == 1) {
+        v3<T> dz = tov(psub(hi.c, lo.c));  // D (n(+z) - n(-z)) x zhat
+        B.x = fma(P.Dz[2], dz.y, B.x);
+        B.y = fma(-P.Dz[2], dz.x, B.y);
+    } else if (DM == 2) {
+        B = B + cross(tov(psub(hi.c, lo.c)), mk(P.Dz[0], P.Dz[1], P.Dz[2]));
+    }
     v3<T> Kh = mk(P.Kh[0], P.Kh[1], P.Kh[2]);
-    T kn = T(2) * P.K * dot(Kh, m.c);
+    v3<T> mc = tov(m.c);
+    T kn = T(2) * P.K * dot(Kh, mc);
     return axpy(kn, Kh, B + mk(P.Bz[0], P.Bz[1], P.Bz[2]));
 }
 
 // PASS 0: predictor on n; PASS 1: corrector on np (q folded term, n out).
-template <typename T, int SOLVER, int PASS>
-__global__ void __launch_bounds__(TX *TY) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
+template <typename T, int SOLVER, int PASS, int DM>
+__global__ void __launch_bounds__(TX *TY, SPGB_CUBIC_MINB) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
                                                   rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                                   const LlgConst<T> c, int ZC)
@@ -136,41 +229,43 @@ __global__ void __launch_bounds__(TX *TY) k_cubic(const __grid_constant__ CubicP
     int x = x0 + tx, y = y0 + ty;
     bool own = x < P.nx && y < P.ny;
     int zend = min(z0 + ZC, P.nz);
+    HaloSlot h0 = halo_slot(P, x0, y0, threadIdx.x), h1 = halo_slot(P, x0, y0, threadIdx.x + TX * TY);
     // Pipeline: plane p lives in tiles[(p - z0 + 1) & 1].  Before the output
     // of plane z the columns of planes z-1 (lo) and z (mid) are in registers
     // and plane z+1 is in flight; plane z+2 is fetched while plane z is
     // finished.
-    load_plane<T>(P, src, tiles[0], x0, y0, z0 - 1);
+    load_plane<T>(P, src, tiles[0], h0, h1, z0 - 1);
     cp_async_commit();
-    load_plane<T>(P, src, tiles[1], x0, y0, z0);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    Col<T> lo = column<T>(P, tiles[0], tx, ty);
-    __syncthreads();
-    load_plane<T>(P, src, tiles[0], x0, y0, z0 + 1);
+    load_plane<T>(P, src, tiles[1], h0, h1, z0);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    Col<T> mid = column<T>(P, tiles[1], tx, ty);
-    for (int z = z0; z < zend; ++z) {
+    Col<T> lo = column<T, DM>(P, tiles[0], tx, ty);
+    __syncthreads();
+    load_plane<T>(P, src, tiles[0], h0, h1, z0 + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    Col<T> mid = column<T, DM>(P, tiles[1], tx, ty);
+    long plane_sz = (long)P.nx * P.ny;
+    long i = (long)z0 * plane_sz + (long)y * P.nx + x;
+    for (int z = z0; z < zend; ++z, i += plane_sz) {
         rec_t<T> *bnext = tiles[(z - z0) & 1];      // plane z+1 (in flight)
         rec_t<T> *bfree = tiles[(z - z0 + 1) & 1];  // plane z, already summarised
         cp_async_wait<0>();
         __syncthreads();
         if (z + 2 <= zend) {
-            load_plane<T>(P, src, bfree, x0, y0, z + 2);
+            load_plane<T>(P, src, bfree, h0, h1, z + 2);
             cp_async_commit();
         }
-        Col<T> hi = column<T>(P, bnext, tx, ty);
+        Col<T> hi = column<T, DM>(P, bnext, tx, ty);
         if (own) {
-            long i = ((long)z * P.ny + y) * P.nx + x;
-            v3<T> B = field_mid<T>(P, lo, mid, hi);
+            v3<T> B = field_mid<T, DM>(P, lo, mid, hi);
             if (Bdd) B = B + ld(Bdd, i);
             if (PASS == 0) {
-                v3<T> ni = mid.c;
+                v3<T> ni = tov(mid.c);
                 v3<T> Bth = mk(T(0), T(0), T(0));
-                if (c.thermal) Bth = c.sig[0] * box_muller(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+                if (c.thermal) Bth = c.sig[0] * thermal_eta(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
                 v3<T> A = llg_A(c.cA[0], c.alpha, ni, B + Bth);
                 if (SOLVER == SP_HEUN) {
                     v3<T> f = cross(ni, A);
@@ -184,7 +279,7 @@ __global__ void __launch_bounds__(TX *TY) k_cubic(const __grid_constant__ CubicP
                     st(q, i, T(0.5) * (A + llg_A(c.cA[0], c.alpha, p, Bth)));
                 }
             } else {
-                v3<T> p = mid.c;
+                v3<T> p = tov(mid.c);
                 v3<T> Ap = llg_A(c.cA[0], c.alpha, p, B);
                 v3<T> qi = ld(q, i);
                 if (SOLVER == SP_HEUN) {
@@ -199,6 +294,23 @@ __global__ void __launch_bounds__(TX *TY) k_cubic(const __grid_constant__ CubicP
     }
 }
 
+template <typename T, int DM>
+void launch_dm(int pass, int solver, dim3 grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
+               rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int zc, cudaStream_t st)
+{
+    if (pass == 0) {
+        if (solver == SP_HEUN)
+            k_cubic<T, SP_HEUN, 0, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
+        else
+            k_cubic<T, SP_DEPONDT, 0, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
+    } else {
+        if (solver == SP_HEUN)
+            k_cubic<T, SP_HEUN, 1, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
+        else
+            k_cubic<T, SP_DEPONDT, 1, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -206,17 +318,12 @@ cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const re
                          rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int zc, cudaStream_t st)
 {
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zc - 1) / zc);
-    if (pass == 0) {
-        if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 0><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-        else
-            k_cubic<T, SP_DEPONDT, 0><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-    } else {
-        if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 1><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-        else
-            k_cubic<T, SP_DEPONDT, 1><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-    }
+    if (P.dmi_mode == 0)
+        launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
+    else if (P.dmi_mode == 1)
+        launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
+    else
+        launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ template <typename T> struct CubicParams {
     T Dx[3], Dy[3], Dz[3]; // DMI vectors of the +x, +y, +z faces (the -o face carries -D_o)
     T Bz[3];               // Zeeman field mu B, meV
     T K, Kh[3];            // anisotropy
+    int dmi_mode;          // 0 none, 1 bulk (D_o = D ohat, one D), 2 any face vectors
 };
 
 // pass 0: predictor (stencil on src = n, writes np and q);

@@ -33,4 +33,10 @@ template <typename T>
 cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, double *partials, double *e_out,
                           double *torque_out, cudaStream_t st);
 
+// Topological charge of a 2D one-atom lattice; flip swaps the triangle
+// orientation (for left-handed in-plane lattice vectors); partials needs
+// blocks_for(n0 * n1) doubles.
+template <typename T>
+cudaError_t launch_topo(const Stencil<T> &S, const rec_t<T> *n, int flip, double *partials, double *Q, cudaStream_t st);
+
 }  // namespace spgb

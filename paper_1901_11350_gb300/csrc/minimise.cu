@@ -57,7 +57,17 @@ struct MinScratch {
     Buf F, G, Tau, scal, part, cnt, blk, img, sten, state;
     int *host_state = nullptr;  // pinned: iters, active
     double *host_fmax = nullptr;
+    // batch layout last uploaded (block/image tables and stencils)
+    std::vector<char> layout;
+    int n_img = 0, n_blk = 0, n_chains = 0;
+    // CUDA graph of kGraphIters steady-state GNEB iterations
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<char> gkey;
 };
+
+constexpr int kGraphIters = 8;
 
 void min_scratch_destroy(MinScratch *s)
 {
@@ -67,6 +77,10 @@ void min_scratch_destroy(MinScratch *s)
         if (b->p) cudaFree(b->p);
     if (s->host_state) cudaFreeHost(s->host_state);
     if (s->host_fmax) cudaFreeHost(s->host_fmax);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->gstream) cudaStreamDestroy(s->gstream);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
     delete s;
 }
 
@@ -432,12 +446,22 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
         grow(s->blk, sizeof(BlkInfo) * n_blk) || grow(s->img, sizeof(ImgInfo) * n_img) ||
         grow(s->sten, sizeof(Stencil<T>) * C))
         return SP_ERR_CUDA;
-    if (cudaMemcpyAsync(s->blk.p, blk.data(), sizeof(BlkInfo) * n_blk, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(s->img.p, img.data(), sizeof(ImgInfo) * n_img, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(s->sten.p, stencils.data(), sizeof(Stencil<T>) * C, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return SP_ERR_CUDA;
-    // the host vectors must outlive the copies above
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SP_ERR_CUDA;
+    // upload the tables only when the layout changed (a call with an
+    // unchanged layout launches kernels only, so it can be stream-captured)
+    std::vector<char> key(sizeof(int) + img.size() * sizeof(ImgInfo) + stencils.size() * sizeof(Stencil<T>));
+    int tsz = (int)sizeof(T);
+    memcpy(key.data(), &tsz, sizeof(int));
+    memcpy(key.data() + sizeof(int), img.data(), img.size() * sizeof(ImgInfo));
+    memcpy(key.data() + sizeof(int) + img.size() * sizeof(ImgInfo), stencils.data(), stencils.size() * sizeof(Stencil<T>));
+    if (key != s->layout) {
+        if (cudaMemcpyAsync(s->blk.p, blk.data(), sizeof(BlkInfo) * n_blk, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(s->img.p, img.data(), sizeof(ImgInfo) * n_img, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(s->sten.p, stencils.data(), sizeof(Stencil<T>) * C, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SP_ERR_CUDA;
+        // the host vectors must outlive the copies above
+        if (cudaStreamSynchronize(st) != cudaSuccess) return SP_ERR_CUDA;
+        s->layout.swap(key);
+    }
     const BlkInfo *B = (const BlkInfo *)s->blk.p;
     const ImgInfo *I = (const ImgInfo *)s->img.p;
     const Stencil<T> *Sd = (const Stencil<T> *)s->sten.p;
@@ -446,16 +470,60 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     double *scal = (double *)s->scal.p, *part = (double *)s->part.p;
     unsigned *cnt = (unsigned *)s->cnt.p;
     double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
-    auto forces = [&](int mode) {
-        k_g_field<T><<<n_blk, kBlock, 0, st>>>(B, I, Sd, x, G, part, cnt, scal);
-        k_g_tangent<T><<<n_blk, kBlock, 0, st>>>(B, I, x, G, Tau, part, cnt, scal);
-        k_g_force<T><<<n_blk, kBlock, 0, st>>>(B, I, v, F, G, Tau, a.k, a.climbing, dth_m, mode, part, cnt, scal);
+    auto forces = [&](int mode, cudaStream_t ss) {
+        k_g_field<T><<<n_blk, kBlock, 0, ss>>>(B, I, Sd, x, G, part, cnt, scal);
+        k_g_tangent<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, G, Tau, part, cnt, scal);
+        k_g_force<T><<<n_blk, kBlock, 0, ss>>>(B, I, v, F, G, Tau, a.k, a.climbing, dth_m, mode, part, cnt, scal);
     };
-    forces(0);
-    for (int it = 0; it < a.n_iter; ++it) {
-        k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, it == 0 ? 0 : 1, scal);
-        forces(1);
+    auto iteration = [&](cudaStream_t ss) {
+        k_g_move<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, v, F, a.dt, dt2_2m, 1, scal);
+        forces(1, ss);
+    };
+    forces(0, st);
+    int remaining = a.n_iter;
+    if (remaining > 0) {
+        k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, 0, scal);
+        forces(1, st);
+        --remaining;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SP_ERR_CUDA;
+    if (remaining >= kGraphIters && cap == cudaStreamCaptureStatusNone) {
+        // replay kGraphIters iterations per graph launch on a private stream
+        if (!s->gstream) {
+            if (cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s->ev0, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s->ev1, cudaEventDisableTiming) != cudaSuccess)
+                return SP_ERR_CUDA;
+        }
+        struct GKey {
+            const void *x, *v, *F, *G, *Tau, *scal, *part, *cnt, *blk, *img, *sten;
+            double dt, mass, k;
+            int climbing, n_blk;
+        } gk{x, v, F, G, Tau, scal, part, cnt, B, I, Sd, a.dt, a.mass, a.k, a.climbing, n_blk};
+        std::vector<char> gkey(sizeof gk + s->layout.size());
+        memcpy(gkey.data(), &gk, sizeof gk);
+        memcpy(gkey.data() + sizeof gk, s->layout.data(), s->layout.size());
+        if (!s->gexec || gkey != s->gkey) {
+            if (s->gexec) cudaGraphExecDestroy(s->gexec);
+            s->gexec = nullptr;
+            cudaGraph_t graph;
+            if (cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SP_ERR_CUDA;
+            for (int r = 0; r < kGraphIters; ++r) iteration(s->gstream);
+            if (cudaStreamEndCapture(s->gstream, &graph) != cudaSuccess) return SP_ERR_CUDA;
+            cudaError_t e = cudaGraphInstantiate(&s->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return SP_ERR_CUDA;
+            s->gkey.swap(gkey);
+        }
+        if (cudaEventRecord(s->ev0, st) != cudaSuccess || cudaStreamWaitEvent(s->gstream, s->ev0, 0) != cudaSuccess)
+            return SP_ERR_CUDA;
+        for (; remaining >= kGraphIters; remaining -= kGraphIters)
+            if (cudaGraphLaunch(s->gexec, s->gstream) != cudaSuccess) return SP_ERR_CUDA;
+        if (cudaEventRecord(s->ev1, s->gstream) != cudaSuccess || cudaStreamWaitEvent(st, s->ev1, 0) != cudaSuccess)
+            return SP_ERR_CUDA;
+    }
+    for (; remaining > 0; --remaining) iteration(st);
     if (a.n_iter > 0) k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, 2, scal);
     k_g_finish<<<1, 256, 0, st>>>(I, n_img, scal, E_dev, fmax_dev, C);
     return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;

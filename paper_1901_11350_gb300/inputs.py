@@ -172,21 +172,30 @@ def cfg_hex_dipole(n=512):
     return dict(name="hex%d_dipole_depondt" % n, geometry=g, hamiltonian=h, run=run, spin_seed=2)
 
 
-def gneb_batch(n_chains=48, seed=4, sizes=(64, 96, 128), images=(12, 40)):
-    """Draws for the batched GNEB workload: per chain the image count
-    U{12..40}, a periodic hexagonal lattice from `sizes`, skyrmion radius
+# With the interfacial convention D_ij = D (z x rhat_ij) and D > 0, the
+# metastable Neel skyrmion in a +z background has helicity pi (its in-plane
+# part points towards the core); helicity 0 unwinds.
+SKYRMION_HELICITY = math.pi
+
+
+def gneb_draw(seed, index, attempt=0, sizes=(64, 96, 128), images=(12, 40)):
+    """Parameters of chain `index` of the batched GNEB workload: image count
+    U{12..40}, periodic hexagonal lattice side from `sizes`, skyrmion radius
     U{3..8} sites, J=1, D~U[0.25,0.4], K~U[0.05,0.1] (z), B~U[0.5,2] T (z),
-    mu_s=2."""
-    rng = np.random.default_rng(seed)
-    out = []
-    for c in range(n_chains):
-        L = int(rng.choice(sizes))
-        M = int(rng.integers(images[0], images[1] + 1))
-        R = int(rng.integers(3, 9))
-        D = float(rng.uniform(0.25, 0.4))
-        K = float(rng.uniform(0.05, 0.1))
-        B = float(rng.uniform(0.5, 2.0))
-        g = hexagonal(L, L, periodic=(True, True), mu_s=2.0)
-        h = dict(B=[0, 0, B], K=[K], Khat=[[0, 0, 1]], J=[1.0], dmi_kind="interfacial", D=[D])
-        out.append(dict(index=c, L=L, n_images=M, radius=R, geometry=g, hamiltonian=h))
-    return out
+    mu_s=2.  `attempt` > 0 gives the redraw used when a draw has no
+    metastable isolated skyrmion."""
+    rng = np.random.default_rng([seed, index, attempt])
+    L = int(rng.choice(sizes))
+    M = int(rng.integers(images[0], images[1] + 1))
+    R = int(rng.integers(3, 9))
+    D = float(rng.uniform(0.25, 0.4))
+    K = float(rng.uniform(0.05, 0.1))
+    B = float(rng.uniform(0.5, 2.0))
+    g = hexagonal(L, L, periodic=(True, True), mu_s=2.0)
+    h = dict(B=[0, 0, B], K=[K], Khat=[[0, 0, 1]], J=[1.0], dmi_kind="interfacial", D=[D])
+    return dict(index=index, attempt=attempt, seed=seed, L=L, n_images=M, radius=R, geometry=g, hamiltonian=h)
+
+
+def gneb_batch(n_chains=48, seed=4, sizes=(64, 96, 128), images=(12, 40)):
+    """First draws of the batched GNEB workload (see gneb_draw)."""
+    return [gneb_draw(seed, c, 0, sizes, images) for c in range(n_chains)]

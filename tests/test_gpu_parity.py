@@ -314,3 +314,64 @@ def test_hex512_dipole_fp32_on_crop():
     ref = Bl[idx] + Bd
     assert np.abs(Bg[idx] - ref).max() <= 1e-5 * np.abs(ref).max()
     assert np.abs((Bg[idx] - Bl[idx]) - Bd).max() <= 1e-4 * np.abs(Bd).max()
+
+
+def _batch_chains():
+    out = []
+    g = I.hexagonal(9, 8, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.35], K=[0.08], Khat=[[0, 0, 1]], B=[0, 0, 1.2])
+    r = I.site_positions(g)
+    out.append((g, h, I.slerp_chain(I.ferromagnet(72), I.neel_skyrmion(r, r.mean(0), 3.5), 7, r, r.mean(0))))
+    g = I.square(6, 5, periodic=(True, False), mu_s=1.5)
+    h = dict(J=[1.0, 0.1], dmi_kind="interfacial", D=[0.2], K=[0.2], Khat=[[0, 0, 1]], B=[0, 0, 0.5])
+    out.append((g, h, I.slerp_chain(I.random_spins(30, 1), I.random_spins(30, 2), 5)))
+    g = I.simple_cubic(4, 4, 3, periodic=(True, True, False))
+    h = dict(J=[1.0, -0.2], dmi_kind="bulk", D=[0.2], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0, 0.3])
+    out.append((g, h, I.slerp_chain(I.ferromagnet(48), I.ferromagnet(48, (0, 0.2, -1)), 4)))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gneb_batch_matches_single_chains(prec):
+    chains = _batch_chains()
+    ctxs, single, offs, Ms = [], [], [], []
+    off = 0
+    for g, h, ch0 in chains:
+        c = B.Context(g, h, prec)
+        ch, v = c.spins(ch0), c.spins(np.zeros_like(ch0))
+        E, F = c.gneb_step(ch, v, n_iter=25, k_spring=0.7, climbing=True, dt=0.1)
+        single.append((ch, v, E, F))
+        ctxs.append(c)
+        offs.append(off)
+        Ms.append(ch0.shape[0])
+        off += ch0.shape[0] * ch0.shape[1]
+    flat = torch.cat([c.spins(ch0).reshape(-1, 4) for c, (_, _, ch0) in zip(ctxs, chains)])
+    vel = torch.zeros_like(flat)
+    E, F = B.gneb_batch_step(ctxs, flat, vel, offs, Ms, n_iter=25, k_spring=0.7, climbing=True, dt=0.1)
+    e0 = 0
+    for k, (ch, v, Es, Fs) in enumerate(single):
+        n = ch.numel() // 4
+        assert torch.equal(flat[offs[k]:offs[k] + n], ch.reshape(-1, 4))
+        assert torch.equal(vel[offs[k]:offs[k] + n], v.reshape(-1, 4))
+        assert torch.equal(E[e0:e0 + Ms[k]], Es)
+        assert F[k].item() == Fs.item()
+        e0 += Ms[k]
+    if prec == "f64":
+        for k, (g, h, ch0) in enumerate(chains):
+            ch_o, v_o, E_o, mf_o, _ = _oracle(g, h).gneb(ch0, n_iter=25, k_spring=0.7, climbing=True, dt=0.1)
+            assert np.abs(_np(single[k][0]) - ch_o).max() <= 1e-10
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_topological_charge_matches_oracle(periodic):
+    L = 24
+    g = I.hexagonal(L, L, periodic=(periodic, periodic))
+    r = I.site_positions(g)
+    n0 = I.perturbed(I.neel_skyrmion(r, r.mean(axis=0), 6.0), 0.05, 4)
+    qo = _oracle(g, dict()).topological_charge(n0)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        c = B.Context(g, dict(J=[1.0]), prec)
+        q = c.topological_charge(c.spins(n0)).item()
+        assert abs(q - qo) <= tol
+    if periodic:
+        assert abs(qo + 1) < 1e-9
