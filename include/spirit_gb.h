@@ -260,6 +260,36 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
                        double *max_force_dev, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free LLG stepping
+ * ------------------------------------------------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory while they run: programs whose device memory
+ * is owned by another allocator or held to a fixed budget, and loops where
+ * the implicit device synchronisation of cudaMalloc is not acceptable.
+ * Creating and configuring a context allocates no device memory, and this
+ * call allocates none either: the predictor state and the folded corrector
+ * term (2 records per spin) live in one file-scope device array of
+ * 2 * 32 * SP_STATIC_MAX_SPINS bytes (4 MiB) that every GPU loading the
+ * library holds until the process exits.
+ *
+ * Same arguments, same arithmetic and same results as sp_llg_step.  Limits
+ * and behaviour:
+ *   - N > SP_STATIC_MAX_SPINS: SP_ERR_ARG with a message, nothing launched;
+ *   - a Hamiltonian with the dipole term: SP_ERR_UNSUPPORTED (its FFT needs
+ *     device buffers of its own);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current) and
+ *     may load the library's kernels: make that first call before any CUDA
+ *     stream capture;
+ *   - every call, on every context and stream of a device, shares the one
+ *     array, which keeps the last call's contents (nothing in it needs to
+ *     start at zero): calls that overlap on the GPU race and give wrong
+ *     results, so serialise them (one stream, or events between streams);
+ *   - kernel timing (sp_profile_enable) does not apply to this call. */
+#define SP_STATIC_MAX_SPINS 65536
+int sp_llg_step_static(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, void *stream);
+
+/* ------------------------------------------------------------------------
  * Execution options (how, not what: results agree within the precision's
  * tolerance whichever option is chosen)
  * ------------------------------------------------------------------------ */

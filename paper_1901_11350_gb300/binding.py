@@ -72,6 +72,7 @@ SIGNATURES = {
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
                                C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_llg_step_static": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_set_option": (_i, [_vp, _i, _i]),
     "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
     "sp_profile_enable": (_i, [_vp, _i]),
