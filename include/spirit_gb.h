@@ -300,13 +300,24 @@ enum {
      * basis atom, bonds within the 3x3x3 cell neighbourhood, one exchange
      * constant per face/edge/corner class, DMI on faces only); 0: default */
     SP_OPT_GENERIC_STENCIL = 1,
-    /* planes of the lattice streamed by one CTA of the 27-point path (>= 1);
-     * chosen from the lattice shape by sp_set_hamiltonian */
+    /* work of one CTA of the 27-point path, in (32 x 8 column tile, plane)
+     * units taken in tile-major order (>= 1); 0 (default): the units spread
+     * evenly over one wave of the CTAs the device keeps resident (reading
+     * the option then returns that value once it has been computed) */
     SP_OPT_PLANES_PER_CTA = 2,
     /* read only: 1 when the 27-point path applies to this Hamiltonian */
     SP_OPT_HAS_CUBIC_PATH = 3
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
+/* Choose SP_OPT_PLANES_PER_CTA by measurement: times the LLG predictor pass
+ * of the 27-point path (Heun with the thermal field on; it reads n_dev and
+ * writes only context scratch, so the spins are unchanged) with CUDA events
+ * on `stream` for the balanced split, finer splits and a few fixed run
+ * lengths, and keeps the fastest.  Allocates
+ * the LLG scratch if needed and synchronises `stream`.  SP_OK without effect
+ * when the 27-point path does not apply.  *chosen (host, may be NULL)
+ * receives the value kept. */
+int sp_autotune(sp_ctx *ctx, const void *n_dev, int *chosen, void *stream);
 int sp_get_option(const sp_ctx *ctx, int option, int *value);
 
 /* ------------------------------------------------------------------------

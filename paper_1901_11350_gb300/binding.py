@@ -75,6 +75,7 @@ SIGNATURES = {
     "sp_llg_step_static": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_set_option": (_i, [_vp, _i, _i]),
     "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
+    "sp_autotune": (_i, [_vp, _vp, C.POINTER(_i), _vp]),
     "sp_profile_enable": (_i, [_vp, _i]),
     "sp_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(C.c_longlong)]),
 }
@@ -239,6 +240,12 @@ class Context:
     def get_option(self, name):
         v = C.c_int()
         self._check(lib().sp_get_option(self._h, OPTIONS[name], C.byref(v)))
+        return v.value
+
+    def autotune(self, n):
+        """Pick the planes-per-CTA of the 27-point path by timing (spins unchanged)."""
+        v = C.c_int()
+        self._check(lib().sp_autotune(self._h, self._spin_arg(n, "n"), C.byref(v), _stream()))
         return v.value
 
     def profile(self, on=True):

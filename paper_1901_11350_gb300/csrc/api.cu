@@ -267,11 +267,7 @@ void detect_cubic(sp_ctx *c)
     }
     fill_cubic(c, J, D, Jc, c->Cf);
     fill_cubic(c, J, D, Jc, c->Cd);
-    // planes per CTA: about 8 resident 256-thread CTAs per SM over 152 SMs
-    long tiles = (long)((c->nc[0] + 31) / 32) * ((c->nc[1] + 7) / 8);
-    long want = 152L * 8;
-    int zc = (int)std::max(4L, std::min(64L, (c->nc[2] * tiles + want - 1) / want));
-    c->zc = std::min(zc, std::max(1, c->nc[2]));
+    c->zc_auto = 0;  // recomputed for the new lattice on first use
     c->cubic = true;
 }
 
@@ -340,17 +336,76 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         const void *bd;
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
-        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, c->zc, st)
+        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, cubic_per(c), st)
                             : launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
-        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, c->zc, st)
+        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, cubic_per(c), st)
                 : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
     }
+    return SP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T> int autotune_run(sp_ctx *c, const void *n, int *chosen, cudaStream_t st)
+{
+    int rc = ensure(c, c->pred, 2 * sizeof(rec_t<T>) * (size_t)c->N);
+    if (rc) return rc;
+    rec_t<T> *np = (rec_t<T> *)c->pred.p;
+    rec_t<T> *q = np + c->N;
+    const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
+    sp_llg_params p{SP_HEUN, 1e-3, 0.1, 10.0, 0, 0, 0};
+    LlgConst<T> k = llg_const<T>(c, &p);
+    k.step = 0;
+    // candidates: the balanced single-wave split and finer ones (more CTAs,
+    // shorter runs of planes), plus a few fixed run lengths
+    int user = c->zc;
+    c->zc = 0;
+    int bal = cubic_per(c);
+    c->zc = user;
+    std::vector<int> cands = {bal, (bal + 1) / 2, (bal + 2) / 3, (bal + 3) / 4, (bal + 5) / 6, 4, 8, 16, 32};
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, SP_ERR_CUDA, "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, SP_ERR_CUDA, "cudaEventCreate");
+    }
+    float best = 1e30f;
+    int best_per = bal;
+    cudaError_t e = cudaSuccess;
+    for (int per : cands) {
+        if (per < 1) continue;
+        e = launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st);  // warm-up
+        float t = 0;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            t += ms;
+        }
+        if (e != cudaSuccess) break;
+        if (t < best) {
+            best = t;
+            best_per = per;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    c->zc = best_per;
+    if (chosen) *chosen = best_per;
     return SP_OK;
 }
 
@@ -677,12 +732,25 @@ int sp_set_option(sp_ctx *c, int option, int value)
         c->use_cubic = value == 0;
         return SP_OK;
     case SP_OPT_PLANES_PER_CTA:
-        if (value < 1) return fail(c, SP_ERR_ARG, "planes per CTA must be >= 1");
+        if (value < 0) return fail(c, SP_ERR_ARG, "units per CTA must be >= 0 (0: balanced)");
         c->zc = value;
         return SP_OK;
     default:
         return fail(c, SP_ERR_ARG, "unknown option %d", option);
     }
+}
+
+int sp_autotune(sp_ctx *c, const void *n_dev, int *chosen, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, n_dev, "spins"))) return rc;
+    if (!c->cubic || c->N == 0) {
+        if (chosen) *chosen = c->zc;
+        return SP_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->prec == SP_F64 ? autotune_run<double>(c, n_dev, chosen, st) : autotune_run<float>(c, n_dev, chosen, st);
 }
 
 int sp_get_option(const sp_ctx *c, int option, int *value)
@@ -693,7 +761,7 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         *value = c->use_cubic ? 0 : 1;
         return SP_OK;
     case SP_OPT_PLANES_PER_CTA:
-        *value = c->zc;
+        *value = c->zc > 0 ? c->zc : c->zc_auto;
         return SP_OK;
     case SP_OPT_HAS_CUBIC_PATH:
         *value = c->cubic ? 1 : 0;

@@ -36,6 +36,11 @@ template <typename T> __device__ __forceinline__ v3<T> operator-(v3<T> a, v3<T> 
 template <typename T> __device__ __forceinline__ v3<T> operator*(T s, v3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
 template <typename T> __device__ __forceinline__ v3<T> operator-(v3<T> a) { return {-a.x, -a.y, -a.z}; }
 template <typename T> __device__ __forceinline__ T dot(v3<T> a, v3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// dot product accumulated in FP64 (energies of FP32 states)
+template <typename T> __device__ __forceinline__ double ddot(v3<T> a, v3<T> b)
+{
+    return fma((double)a.x, (double)b.x, fma((double)a.y, (double)b.y, (double)a.z * (double)b.z));
+}
 template <typename T> __device__ __forceinline__ v3<T> cross(v3<T> a, v3<T> b)
 {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};

@@ -2,6 +2,7 @@
 // translation units that implement the C ABI).
 #pragma once
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -99,7 +100,8 @@ struct sp_ctx {
     // shell-symmetric 27-point fast path (valid when `cubic` is set)
     bool cubic = false;
     bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
-    int zc = 8;
+    int zc = 0;             // units per CTA of the 27-point path; 0 = balanced (see cubic_per)
+    int zc_auto = 0;        // balanced value, computed on first use
     CubicParams<float> Cf = {};
     CubicParams<double> Cd = {};
     // device scratch (allocated on first use)
@@ -111,3 +113,18 @@ struct sp_ctx {
     Profiler prof;
 };
 
+// Units per CTA of the 27-point path: the user's choice, or the units spread
+// evenly over one wave of resident CTAs on the current device.
+inline int cubic_per(sp_ctx *c)
+{
+    if (c->zc > 0) return c->zc;
+    if (c->zc_auto <= 0) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+        long slots = (long)nsm * cubic_resident_ctas(c->prec);
+        long units = cubic_units(c->nc[0], c->nc[1], c->nc[2]);
+        c->zc_auto = (int)std::max(1L, (units + slots - 1) / slots);
+    }
+    return c->zc_auto;
+}

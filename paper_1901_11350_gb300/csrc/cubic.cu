@@ -54,25 +54,31 @@ __device__ __forceinline__ pv psub(pv a, pv b) { return {__ffma2_rn(b.xy, make_f
 __device__ __forceinline__ pv paxpy(float s, pv a, pv b) { return {__ffma2_rn(make_float2(s, s), a.xy, b.xy), fmaf(s, a.z, b.z)}; }
 __device__ __forceinline__ pv pscale(float s, pv a) { return {__fmul2_rn(make_float2(s, s), a.xy), s * a.z}; }
 __device__ __forceinline__ v3<float> tov(pv a) { return {a.xy.x, a.xy.y, a.z}; }
-__device__ __forceinline__ pv fromv(v3<float> a) { return {make_float2(a.x, a.y), a.z}; }
 
-__device__ __forceinline__ v3<double> padd(v3<double> a, v3<double> b) { return a + b; }
-__device__ __forceinline__ v3<double> psub(v3<double> a, v3<double> b) { return a - b; }
-__device__ __forceinline__ v3<double> paxpy(double s, v3<double> a, v3<double> b) { return axpy(s, a, b); }
-__device__ __forceinline__ v3<double> pscale(double s, v3<double> a) { return s * a; }
-__device__ __forceinline__ v3<double> tov(v3<double> a) { return a; }
-__device__ __forceinline__ v3<double> fromv(v3<double> a) { return a; }
+template <typename T> __device__ __forceinline__ v3<T> padd(v3<T> a, v3<T> b) { return a + b; }
+template <typename T> __device__ __forceinline__ v3<T> psub(v3<T> a, v3<T> b) { return a - b; }
+template <typename T> __device__ __forceinline__ v3<T> paxpy(T s, v3<T> a, v3<T> b) { return axpy(s, a, b); }
+template <typename T> __device__ __forceinline__ v3<T> pscale(T s, v3<T> a) { return s * a; }
+template <typename T> __device__ __forceinline__ v3<T> tov(v3<T> a) { return a; }
 
+// SPGB_SCALAR_STENCIL: plain scalar FP32 sums (for comparison with the packed form)
 template <typename T> struct PV;
+#ifdef SPGB_SCALAR_STENCIL
+template <> struct PV<float> { using type = v3<float>; };
+#else
 template <> struct PV<float> { using type = pv; };
+#endif
 template <> struct PV<double> { using type = v3<double>; };
 template <typename T> using pv_t = typename PV<T>::type;
 
-__device__ __forceinline__ pv tload(const float4 *t, int e)
+template <typename P> __device__ __forceinline__ P tload_as(const float4 *t, int e);
+template <> __device__ __forceinline__ pv tload_as<pv>(const float4 *t, int e)
 {
     float4 v = t[e];
     return {make_float2(v.x, v.y), v.z};
 }
+template <> __device__ __forceinline__ v3<float> tload_as<v3<float>>(const float4 *t, int e) { return ldc(t, e); }
+__device__ __forceinline__ pv_t<float> tload(const float4 *t, int e) { return tload_as<pv_t<float>>(t, e); }
 __device__ __forceinline__ v3<double> tload(const dq4 *t, int e) { return ldc(t, e); }
 
 // Box-Muller for FP32 from the multi-function unit: sin/cos of
@@ -99,8 +105,8 @@ __device__ __forceinline__ v3<double> thermal_eta(uint4 x, double) { return box_
 // most two of them.  Their in-plane offsets (periodic wrap or "absent" for an
 // open edge) do not depend on z and are computed once per CTA.
 struct HaloSlot {
-    long off;  // gy * nx + gx
-    int ok;    // inside the lattice in-plane
+    int off;  // gy * nx + gx
+    int ok;   // inside the lattice in-plane
 };
 
 template <typename T>
@@ -123,7 +129,7 @@ __device__ __forceinline__ HaloSlot halo_slot(const CubicParams<T> &P, int x0, i
     } else {
         in = in && gy >= 0 && gy < P.ny;
     }
-    h.off = (long)gy * P.nx + gx;
+    h.off = gy * P.nx + gx;
     h.ok = in;
     return h;
 }
@@ -146,7 +152,7 @@ __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<
     } else {
         zin = z >= 0 && z < P.nz;
     }
-    const rec_t<T> *plane = src + (long)z * P.nx * P.ny;
+    const rec_t<T> *plane = src + z * (P.nx * P.ny);
     int e0 = threadIdx.x, e1 = threadIdx.x + TX * TY;
     rec_t<T> zero{};
     if (zin && h0.ok)
@@ -161,109 +167,128 @@ __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<
     }
 }
 
-// per-plane column summary: centre, in-plane face sum, in-plane corner sum,
-// in-plane face DMI field
-template <typename T> struct Col {
-    pv_t<T> c, f, k, dm;
+// Summary of one plane at a thread's column: its centre spin c, the part
+// `w` it contributes to the planes above and below (exchange J1 c + J2 f +
+// J3 k, f and k the sums of the four in-plane face and corner neighbours)
+// and the part `e` it contributes to itself (J1 f + J2 k + in-plane face DMI).
+template <typename T> struct Plane {
+    v3<T> c, w, e;
 };
 
 // DM: 0 no DMI, 1 bulk (D_o = D ohat on the faces), 2 any face vectors
 template <typename T, int DM>
-__device__ __forceinline__ Col<T> column(const CubicParams<T> &P, const rec_t<T> *tile, int tx, int ty)
+__device__ __forceinline__ Plane<T> summarise(const CubicParams<T> &P, const rec_t<T> *tile, int tx, int ty)
 {
     int e = (ty + 1) * HX + tx + 1;
-    Col<T> r;
-    r.c = tload(tile, e);
+    pv_t<T> c = tload(tile, e);
     pv_t<T> xp = tload(tile, e + 1), xm = tload(tile, e - 1);
     pv_t<T> yp = tload(tile, e + HX), ym = tload(tile, e - HX);
-    r.f = padd(padd(xp, xm), padd(yp, ym));
-    r.k = padd(padd(tload(tile, e + HX + 1), tload(tile, e - HX - 1)), padd(tload(tile, e - HX + 1), tload(tile, e + HX - 1)));
-    if (DM == 0) {
-        r.dm = pscale(T(0), r.c);
-    } else {
+    pv_t<T> f = padd(padd(xp, xm), padd(yp, ym));
+    pv_t<T> k = padd(padd(tload(tile, e + HX + 1), tload(tile, e - HX - 1)), padd(tload(tile, e - HX + 1), tload(tile, e + HX - 1)));
+    Plane<T> r;
+    r.c = tov(c);
+    r.w = tov(paxpy(P.J1, c, paxpy(P.J2, f, pscale(P.J3, k))));
+    v3<T> ee = tov(paxpy(P.J1, f, pscale(P.J2, k)));
+    if (DM != 0) {
         v3<T> dx = tov(psub(xp, xm)), dy = tov(psub(yp, ym));
         if (DM == 1) {
             // D [(n(+x) - n(-x)) x xhat + (n(+y) - n(-y)) x yhat]
             T D = P.Dx[0];
-            r.dm = fromv(mk(-D * dy.z, D * dx.z, D * (dy.x - dx.y)));
+            ee.x = fma(-D, dy.z, ee.x);
+            ee.y = fma(D, dx.z, ee.y);
+            ee.z = fma(D, dy.x - dx.y, ee.z);
         } else {
-            r.dm = fromv(cross(dx, mk(P.Dx[0], P.Dx[1], P.Dx[2])) + cross(dy, mk(P.Dy[0], P.Dy[1], P.Dy[2])));
+            ee = ee + cross(dx, mk(P.Dx[0], P.Dx[1], P.Dx[2])) + cross(dy, mk(P.Dy[0], P.Dy[1], P.Dy[2]));
         }
     }
+    r.e = ee;
     return r;
 }
 
-// Full local field of the middle plane m from planes lo (z-1), m, hi (z+1).
-template <typename T, int DM>
-__device__ __forceinline__ v3<T> field_mid(const CubicParams<T> &P, const Col<T> &lo, const Col<T> &m, const Col<T> &hi)
+// c x D_{+z}: the DMI field a spin c on the plane below gets from ... (sign
+// applied by the caller)
+template <typename T, int DM> __device__ __forceinline__ v3<T> zdmi(const CubicParams<T> &P, v3<T> c)
 {
-    pv_t<T> s1 = padd(m.f, padd(lo.c, hi.c));
-    pv_t<T> s2 = padd(m.k, padd(lo.f, hi.f));
-    pv_t<T> s3 = padd(lo.k, hi.k);
-    pv_t<T> Bp = paxpy(P.J1, s1, paxpy(P.J2, s2, pscale(P.J3, s3)));
-    if (DM != 0) Bp = padd(Bp, m.dm);
-    v3<T> B = tov(Bp);
-    if (DM == 1) {
-        v3<T> dz = tov(psub(hi.c, lo.c));  // D (n(+z) - n(-z)) x zhat
-        B.x = fma(P.Dz[2], dz.y, B.x);
-        B.y = fma(-P.Dz[2], dz.x, B.y);
-    } else if (DM == 2) {
-        B = B + cross(tov(psub(hi.c, lo.c)), mk(P.Dz[0], P.Dz[1], P.Dz[2]));
-    }
-    v3<T> Kh = mk(P.Kh[0], P.Kh[1], P.Kh[2]);
-    v3<T> mc = tov(m.c);
-    T kn = T(2) * P.K * dot(Kh, mc);
-    return axpy(kn, Kh, B + mk(P.Bz[0], P.Bz[1], P.Bz[2]));
+    if (DM == 0) return mk(T(0), T(0), T(0));
+    if (DM == 1) return mk(P.Dz[2] * c.y, -P.Dz[2] * c.x, T(0));
+    return cross(c, mk(P.Dz[0], P.Dz[1], P.Dz[2]));
 }
 
-// PASS 0: predictor on n; PASS 1: corrector on np (q folded term, n out).
-template <typename T, int SOLVER, int PASS, int DM>
-__global__ void __launch_bounds__(TX *TY, SPGB_CUBIC_MINB) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
-                                                  rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
-                                                  rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
-                                                  const LlgConst<T> c, int ZC)
+// on-site part: Zeeman + anisotropy
+template <typename T> __device__ __forceinline__ v3<T> onsite(const CubicParams<T> &P, v3<T> c)
 {
-    __shared__ __align__(32) rec_t<T> tiles[2][HN];
+    v3<T> Kh = mk(P.Kh[0], P.Kh[1], P.Kh[2]);
+    T kn = T(2) * P.K * dot(Kh, c);
+    return axpy(kn, Kh, mk(P.Bz[0], P.Bz[1], P.Bz[2]));
+}
+
+// One segment: planes [za, zb) of the column tile at (x0, y0).
+//
+// Streaming in z: when plane p+1 arrives the field of plane p is complete,
+//     B(p) = A(p) + w(p+1) + c(p+1) x D_{+z},
+// and plane p+1 opens its own accumulator
+//     A(p+1) = e(p+1) + w(p) - c(p) x D_{+z} + onsite(c(p+1)),
+// so only A, w and c of one plane stay live between iterations.
+// PASS 0: predictor on n; PASS 1: corrector on np (q folded term, n out).
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD>
+__device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> *__restrict__ src,
+                                        rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
+                                        rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
+                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], int x0, int y0, int za, int zb)
+{
     int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZC;
     int x = x0 + tx, y = y0 + ty;
     bool own = x < P.nx && y < P.ny;
-    int zend = min(z0 + ZC, P.nz);
     HaloSlot h0 = halo_slot(P, x0, y0, threadIdx.x), h1 = halo_slot(P, x0, y0, threadIdx.x + TX * TY);
-    // Pipeline: plane p lives in tiles[(p - z0 + 1) & 1].  Before the output
-    // of plane z the columns of planes z-1 (lo) and z (mid) are in registers
-    // and plane z+1 is in flight; plane z+2 is fetched while plane z is
-    // finished.
-    load_plane<T>(P, src, tiles[0], h0, h1, z0 - 1);
+    // plane p lives in tiles[(p - za + 1) & 1]; plane p+2 is fetched while
+    // plane p is finished
+    load_plane<T>(P, src, tiles[0], h0, h1, za - 1);
     cp_async_commit();
-    load_plane<T>(P, src, tiles[1], h0, h1, z0);
+    load_plane<T>(P, src, tiles[1], h0, h1, za);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    Col<T> lo = column<T, DM>(P, tiles[0], tx, ty);
+    Plane<T> below = summarise<T, DM>(P, tiles[0], tx, ty);
     __syncthreads();
-    load_plane<T>(P, src, tiles[0], h0, h1, z0 + 1);
+    load_plane<T>(P, src, tiles[0], h0, h1, za + 1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    Col<T> mid = column<T, DM>(P, tiles[1], tx, ty);
-    long plane_sz = (long)P.nx * P.ny;
-    long i = (long)z0 * plane_sz + (long)y * P.nx + x;
-    for (int z = z0; z < zend; ++z, i += plane_sz) {
-        rec_t<T> *bnext = tiles[(z - z0) & 1];      // plane z+1 (in flight)
-        rec_t<T> *bfree = tiles[(z - z0 + 1) & 1];  // plane z, already summarised
+    Plane<T> cur = summarise<T, DM>(P, tiles[1], tx, ty);
+    v3<T> acc = cur.e + below.w - zdmi<T, DM>(P, below.c) + onsite(P, cur.c);
+    v3<T> wcur = cur.w, ccur = cur.c;
+    const int plane_sz = P.nx * P.ny;  // N < 2^31
+    int i = za * plane_sz + y * P.nx + x;
+    // per-spin global inputs of the plane being finished, fetched one plane
+    // ahead so that their latency overlaps the stencil of the current plane
+    v3<T> qn = mk(T(0), T(0), T(0)), bn = mk(T(0), T(0), T(0));
+    if (own) {
+        if (PASS == 1) qn = ld(q, i);
+        if (HAS_BDD) bn = ld(Bdd, i);
+    }
+    for (int z = za; z < zb; ++z, i += plane_sz) {
+        rec_t<T> *bnext = tiles[(z - za) & 1];      // plane z+1 (in flight)
+        rec_t<T> *bfree = tiles[(z - za + 1) & 1];  // plane z, already summarised
+        v3<T> qi = qn, bi = bn;
+        if (own && z + 1 < zb) {
+            if (PASS == 1) qn = ld(q, i + plane_sz);
+            if (HAS_BDD) bn = ld(Bdd, i + plane_sz);
+        }
         cp_async_wait<0>();
         __syncthreads();
-        if (z + 2 <= zend) {
+        if (z + 2 <= zb) {
             load_plane<T>(P, src, bfree, h0, h1, z + 2);
             cp_async_commit();
         }
-        Col<T> hi = column<T, DM>(P, bnext, tx, ty);
+        Plane<T> up = summarise<T, DM>(P, bnext, tx, ty);
+        v3<T> B = acc + up.w + zdmi<T, DM>(P, up.c);
+        acc = up.e + wcur - zdmi<T, DM>(P, ccur) + onsite(P, up.c);
+        v3<T> ni = ccur;
+        wcur = up.w;
+        ccur = up.c;
         if (own) {
-            v3<T> B = field_mid<T, DM>(P, lo, mid, hi);
-            if (Bdd) B = B + ld(Bdd, i);
+            if (HAS_BDD) B = B + bi;
             if (PASS == 0) {
-                v3<T> ni = tov(mid.c);
                 v3<T> Bth = mk(T(0), T(0), T(0));
                 if (c.thermal) Bth = c.sig[0] * thermal_eta(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
                 v3<T> A = llg_A(c.cA[0], c.alpha, ni, B + Bth);
@@ -279,52 +304,96 @@ __global__ void __launch_bounds__(TX *TY, SPGB_CUBIC_MINB) k_cubic(const __grid_
                     st(q, i, T(0.5) * (A + llg_A(c.cA[0], c.alpha, p, Bth)));
                 }
             } else {
-                v3<T> p = tov(mid.c);
-                v3<T> Ap = llg_A(c.cA[0], c.alpha, p, B);
-                v3<T> qi = ld(q, i);
+                v3<T> Ap = llg_A(c.cA[0], c.alpha, ni, B);
                 if (SOLVER == SP_HEUN) {
-                    st(nout, i, normalised(axpy(T(0.5) * c.dt, cross(p, Ap), qi)));
+                    st(nout, i, normalised(axpy(T(0.5) * c.dt, cross(ni, Ap), qi)));
                 } else {
                     st(nout, i, rotate(ldc(nout, i), axpy(T(0.5), Ap, qi), c.dt));
                 }
             }
         }
-        lo = mid;
-        mid = hi;
+    }
+    __syncthreads();  // the next segment reuses the tiles
+}
+
+// The work is the list of (column tile, plane) units, tile-major.  CTA b
+// takes units [b*per, (b+1)*per): a few contiguous runs of planes, each
+// streamed as one segment.  With per = units / (SMs x resident CTAs) every SM
+// gets the same amount of work in a single wave.
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD>
+__global__ void __launch_bounds__(TX *TY, SPGB_CUBIC_MINB) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
+                                                  rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
+                                                  rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
+                                                  const LlgConst<T> c, int per)
+{
+    __shared__ __align__(32) rec_t<T> tiles[2][HN];
+    int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
+    long total = (long)tiles_x * tiles_y * P.nz;
+    long u = (long)blockIdx.x * per, u1 = min(u + per, total);
+    while (u < u1) {
+        int tile = (int)(u / P.nz), za = (int)(u % P.nz);
+        int zb = (int)min((long)P.nz, za + (u1 - u));
+        segment<T, SOLVER, PASS, DM, HAS_BDD>(P, src, np, q, nout, Bdd, c, tiles, (tile % tiles_x) * TX,
+                                              (tile / tiles_x) * TY, za, zb);
+        u += zb - za;
+    }
+}
+
+template <typename T, int DM, bool HB>
+void launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
+                rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
+{
+    if (pass == 0) {
+        if (solver == SP_HEUN)
+            k_cubic<T, SP_HEUN, 0, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+        else
+            k_cubic<T, SP_DEPONDT, 0, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+    } else {
+        if (solver == SP_HEUN)
+            k_cubic<T, SP_HEUN, 1, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+        else
+            k_cubic<T, SP_DEPONDT, 1, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
     }
 }
 
 template <typename T, int DM>
-void launch_dm(int pass, int solver, dim3 grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-               rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int zc, cudaStream_t st)
+void launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
+               rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
 {
-    if (pass == 0) {
-        if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 0, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-        else
-            k_cubic<T, SP_DEPONDT, 0, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-    } else {
-        if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 1, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-        else
-            k_cubic<T, SP_DEPONDT, 1, DM><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, zc);
-    }
+    if (Bdd)
+        launch_dmb<T, DM, true>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    else
+        launch_dmb<T, DM, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int zc, cudaStream_t st)
+                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
 {
-    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zc - 1) / zc);
+    long total = cubic_units(P.nx, P.ny, P.nz);
+    if (total == 0) return cudaSuccess;
+    if (per < 1) per = 1;
+    int grid = (int)((total + per - 1) / per);
     if (P.dmi_mode == 0)
-        launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
+        launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
     else if (P.dmi_mode == 1)
-        launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
+        launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
     else
-        launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, zc, st);
+        launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
     return cudaGetLastError();
+}
+
+long cubic_units(int nx, int ny, int nz) { return (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz; }
+
+int cubic_resident_ctas(int prec)
+{
+    int n = 0;
+    cudaError_t e = prec == SP_F64
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false>, TX * TY, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false>, TX * TY, 0);
+    return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 template cudaError_t launch_cubic<float>(int, int, const CubicParams<float> &, const float4 *, float4 *, float4 *,

@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
         v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
         v3<T> Kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
         T kn = dot(Kh, ni);
-        acc[1] = -(double)dot(ni, Bz);
-        acc[2] = -(double)(S.K[b] * kn * kn);
+        acc[1] = -ddot(ni, Bz);
+        acc[2] = -(double)S.K[b] * (double)kn * (double)kn;
         v3<T> B = axpy(T(2) * S.K[b] * kn, Kh, Bz);
         v3<T> Bx = mk(T(0), T(0), T(0)), Bd = mk(T(0), T(0), T(0));
         for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
@@ -150,12 +150,12 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
             Bx = axpy(E.J, nj, Bx);
             Bd = Bd + cross(nj, mk(E.Dx, E.Dy, E.Dz));
         }
-        acc[3] = -0.5 * (double)dot(ni, Bx);
-        acc[4] = -0.5 * (double)dot(ni, Bd);
+        acc[3] = -0.5 * ddot(ni, Bx);
+        acc[4] = -0.5 * ddot(ni, Bd);
         B = B + Bx + Bd;
         if (Bdd) {
             v3<T> bd = ld(Bdd, i);
-            acc[5] = -0.5 * (double)dot(ni, bd);
+            acc[5] = -0.5 * ddot(ni, bd);
             B = B + bd;
         }
         acc[0] = acc[1] + acc[2] + acc[3] + acc[4] + acc[5];

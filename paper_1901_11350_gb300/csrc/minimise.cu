@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ 
         v3<T> ni = ld(xb, i);
         v3<T> B = local_field(St, xb, i, ni, b);
         v3<T> Bz = mk(St.Bz[b][0], St.Bz[b][1], St.Bz[b][2]);
-        r[0] = -0.5 * (double)dot(ni, B + Bz);
+        r[0] = -0.5 * ddot(ni, B + Bz);
         v3<T> pg = dot(B, ni) * ni - B;  // tangent-space part of dH/dn = -B
         st(G, im.spin0 + (long long)im.nu * im.N + i, pg);
         if (im.nu < im.M - 1) {

@@ -173,9 +173,10 @@ def test_stochastic_heun_100_steps_fp64():
     assert np.abs(_np(n) - no).max() <= 1e-11
 
 
-@pytest.mark.parametrize("zc", [1, 2, 5, 7, 40])
+@pytest.mark.parametrize("zc", [1, 2, 5, 7, 40, 1000])
 def test_cubic_plane_chunking_is_exact(zc):
-    # the result may not depend on how planes are split between CTAs
+    # the result may not depend on how (tile, plane) units are split between
+    # CTAs, including runs that cross from one column tile to the next
     cfg = I.cfg_sc_128(4)
     g = dict(cfg["geometry"], n_cells=[37, 19, 23])
     c = B.Context(g, cfg["hamiltonian"], "f32")
@@ -187,6 +188,17 @@ def test_cubic_plane_chunking_is_exact(zc):
     b = c.spins(n0)
     c.llg_step(b, 3, **kw)
     assert torch.equal(a, b)
+
+
+def test_autotune_keeps_spins_and_picks_a_valid_chunking():
+    cfg = I.cfg_sc_128(4)
+    g = dict(cfg["geometry"], n_cells=[40, 24, 30])
+    c = B.Context(g, cfg["hamiltonian"], "f32")
+    n = c.spins(I.random_spins(c.N, 3))
+    before = n.clone()
+    zc = c.autotune(n)
+    assert torch.equal(n, before)
+    assert zc >= 1 and c.get_option("planes_per_cta") == zc
 
 
 def test_llg_resume_is_bit_exact_on_gpu():
