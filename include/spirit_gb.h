@@ -65,7 +65,7 @@ enum {
 enum { SP_F32 = 0, SP_F64 = 1 };
 enum { SP_DMI_NONE = 0, SP_DMI_BULK = 1, SP_DMI_INTERFACIAL = 2 };
 enum { SP_DIPOLE_NONE = 0, SP_DIPOLE_FFT = 2 };
-enum { SP_DEPONDT = 0, SP_HEUN = 1 };
+enum { SP_DEPONDT = 0, SP_HEUN = 1, SP_SIB = 2, SP_RK4 = 3 };
 
 typedef struct sp_ctx sp_ctx;
 
@@ -100,7 +100,7 @@ typedef struct {
 
 /* LLG run parameters (Eq. 3, Eq. 4, Appendix B). */
 typedef struct {
-    int solver;        /* SP_DEPONDT or SP_HEUN */
+    int solver;        /* SP_DEPONDT, SP_HEUN, SP_SIB or SP_RK4 */
     double dt;         /* time step, ps (> 0) */
     double alpha;      /* Gilbert damping (>= 0) */
     double T;          /* temperature, K (>= 0); 0 switches the thermal field off */
@@ -195,9 +195,13 @@ int sp_topological_charge(sp_ctx *ctx, const void *n_dev, double *Q_dev, void *s
  * and eta_i three standard normals from Philox4x32-10 (key = seed, counter =
  * (i, step mod 2^32, step div 2^32, 8*replica)), Box-Muller on
  * (u0,u1) -> eta_x, eta_y and (u2,u3) -> eta_z, u = (x + 1/2) 2^-32; the same
- * eta in both stages of a step.  Heun renormalises predictor and result;
- * Depondt rotates by |A| dt about -A (Rodrigues).  Allocates the context's
- * predictor scratch (2 records per spin) on first use. */
+ * eta in all stages of a step.  Heun renormalises predictor and result;
+ * Depondt rotates by |A| dt about -A (Rodrigues); SIB (Appendix C) solves the
+ * implicit-midpoint predictor with A(n) and the corrector with A at the
+ * predictor's midpoint (n + n^p)/2, each M x = M^T n with M = I + skew(dt A/2)
+ * (norm-preserving, no renormalisation); RK4 takes four field evaluations
+ * and renormalises the result.  Allocates the context's scratch (2 records
+ * per spin, 3 for RK4) on first use. */
 int sp_llg_step(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, void *stream);
 
 /* ------------------------------------------------------------------------
@@ -275,8 +279,8 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
  * Same arguments, same arithmetic and same results as sp_llg_step.  Limits
  * and behaviour:
  *   - N > SP_STATIC_MAX_SPINS: SP_ERR_ARG with a message, nothing launched;
- *   - a Hamiltonian with the dipole term: SP_ERR_UNSUPPORTED (its FFT needs
- *     device buffers of its own);
+ *   - a Hamiltonian with the dipole term, or the RK4 solver (3 records per
+ *     spin): SP_ERR_UNSUPPORTED;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, once per device, with that device current) and
  *     may load the library's kernels: make that first call before any CUDA

@@ -28,7 +28,7 @@ MAX_SHELLS = 8
 MAX_GAUSS = 16
 DMI = {"none": 0, "bulk": 1, "interfacial": 2}
 DIPOLE = {"none": 0, "direct": 1, "fft": 2}
-SOLVER = {"depondt": 0, "heun": 1}
+SOLVER = {"depondt": 0, "heun": 1, "sib": 2, "rk4": 3}
 
 # Constants as the oracle states them (CODATA 2018), for tests' closed forms.
 MU_B = 0.05788381806

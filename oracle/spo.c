@@ -7,6 +7,7 @@
  *   Sec. "Dipolar interactions"    -> dipole_direct(), dipole_fft()
  *   Eq. 3/4 (LLG, thermal field)   -> llg_A(), spo_llg()
  *   Appendix B (Heun, Depondt)     -> spo_llg()
+ *   Appendix C (SIB), RK4          -> sib_solve(), spo_llg()
  *   Appendix D (velocity proj.)    -> spo_minimise(), spo_gneb()
  *   Sec. GNEB + Appendix F         -> spo_gneb_forces()
  *   Appendix A (topological charge)-> spo_topological_charge()
@@ -728,10 +729,71 @@ static void rotate(const double *n, const double *A, double dt, double *out)
     for (int k = 0; k < 3; ++k) out[k] = n[k] * ct + axn[k] * st + ax[k] * an * (1.0 - ct);
 }
 
+static double det3(const double m[3][3])
+{
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+/* Appendix C: the implicit-midpoint update x = n + dt (n + x)/2 x A, written
+ * as M x = M^T n with M = I + skew(a), a = dt A / 2 (reading: the matrix of
+ * Appendix C carries the factor dt/2 of the midpoint rule), solved by
+ * Cramer's rule x_k = det(M^k) / det(M), M^k = M with column k replaced by
+ * the right-hand side M^T n = n + n x a. */
+static void sib_solve(const double *n, const double *A, double dt, double *x)
+{
+    double a[3] = {0.5 * dt * A[0], 0.5 * dt * A[1], 0.5 * dt * A[2]};
+    double M[3][3] = {{1.0, -a[2], a[1]}, {a[2], 1.0, -a[0]}, {-a[1], a[0], 1.0}};
+    double nxa[3];
+    cross3(n, a, nxa);
+    double rhs[3] = {n[0] + nxa[0], n[1] + nxa[1], n[2] + nxa[2]};
+    double d = det3(M);
+    for (int k = 0; k < 3; ++k) {
+        double Mk[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) Mk[r][c] = (c == k) ? rhs[r] : M[r][c];
+        x[k] = det3(Mk) / d;
+    }
+}
+
+/* Fourth-order Runge-Kutta (named in Sec. LLG) for dn/dt = n x A(n, B(n) + B_th)
+ * with the same thermal field in all four stages, the result renormalised. */
+static int rk4_step(const spo_system *s, double *n, const spo_llg_params *p, const double *Bth)
+{
+    size_t sz = sizeof(double) * 3 * (size_t)s->N;
+    double *y = (double *)malloc(sz), *B = (double *)malloc(sz), *acc = (double *)malloc(sz);
+    if (!y || !B || !acc) { free(y); free(B); free(acc); return SPO_ERR_STATE; }
+    static const double cy[4] = {0.5, 0.5, 1.0, 0.0}; /* next stage state: n + cy*dt*k */
+    static const double w[4] = {1.0, 2.0, 2.0, 1.0};
+    memcpy(y, n, sz);
+    memset(acc, 0, sz);
+    int rc = SPO_OK;
+    for (int st = 0; st < 4 && !rc; ++st) {
+        rc = spo_effective_field(s, y, B, -1);
+        if (rc) break;
+        for (int i = 0; i < s->N; ++i) {
+            double mu = s->mu[i % s->nb] * MU_B, Bi[3], A[3], k[3];
+            for (int c = 0; c < 3; ++c) Bi[c] = B[3 * i + c] + Bth[3 * i + c];
+            llg_A(mu, p->alpha, y + 3 * i, Bi, A);
+            cross3(y + 3 * i, A, k);
+            for (int c = 0; c < 3; ++c) acc[3 * i + c] += w[st] * k[c];
+            if (st < 3)
+                for (int c = 0; c < 3; ++c) y[3 * i + c] = n[3 * i + c] + cy[st] * p->dt * k[c];
+        }
+    }
+    if (!rc)
+        for (int i = 0; i < s->N; ++i) {
+            for (int c = 0; c < 3; ++c) n[3 * i + c] += p->dt / 6.0 * acc[3 * i + c];
+            normalise3(n + 3 * i);
+        }
+    free(y); free(B); free(acc);
+    return rc;
+}
+
 int spo_llg(const spo_system *s, double *n, const spo_llg_params *p, int n_steps)
 {
     if (!s || !s->have_ham || !n || !p) return SPO_ERR_STATE;
-    if (p->solver != SPO_DEPONDT && p->solver != SPO_HEUN) return SPO_ERR_ARG;
+    if (p->solver < SPO_DEPONDT || p->solver > SPO_RK4) return SPO_ERR_ARG;
     if (!(p->dt > 0) || p->alpha < 0 || p->T < 0 || n_steps < 0) return SPO_ERR_ARG;
     size_t sz = sizeof(double) * 3 * (size_t)s->N;
     double *B = (double *)malloc(sz), *np = (double *)malloc(sz), *A = (double *)malloc(sz),
@@ -749,13 +811,23 @@ int spo_llg(const spo_system *s, double *n, const spo_llg_params *p, int n_steps
             if (p->T > 0) spo_thermal_normals(p->seed, step, p->replica, (uint32_t)i, eta);
             for (int k = 0; k < 3; ++k) Bth[3 * i + k] = sig * eta[k];
         }
+        if (p->solver == SPO_RK4) {
+            rc = rk4_step(s, n, p, Bth);
+            continue;
+        }
         rc = spo_effective_field(s, n, B, -1);
         if (rc) break;
         for (int i = 0; i < s->N; ++i) {
             double mu = s->mu[i % s->nb] * MU_B, Bi[3];
             for (int k = 0; k < 3; ++k) Bi[k] = B[3 * i + k] + Bth[3 * i + k];
             llg_A(mu, p->alpha, n + 3 * i, Bi, A + 3 * i);
-            if (p->solver == SPO_DEPONDT) {
+            if (p->solver == SPO_SIB) {
+                /* predictor (Appendix C): implicit midpoint with A(n);
+                 * np holds the midpoint (n + n^p)/2 for the corrector */
+                double x[3];
+                sib_solve(n + 3 * i, A + 3 * i, p->dt, x);
+                for (int k = 0; k < 3; ++k) np[3 * i + k] = 0.5 * (n[3 * i + k] + x[k]);
+            } else if (p->solver == SPO_DEPONDT) {
                 rotate(n + 3 * i, A + 3 * i, p->dt, np + 3 * i);
             } else {
                 double f[3];
@@ -770,7 +842,12 @@ int spo_llg(const spo_system *s, double *n, const spo_llg_params *p, int n_steps
             double mu = s->mu[i % s->nb] * MU_B, Bi[3], Ap[3];
             for (int k = 0; k < 3; ++k) Bi[k] = B[3 * i + k] + Bth[3 * i + k];
             llg_A(mu, p->alpha, np + 3 * i, Bi, Ap);
-            if (p->solver == SPO_DEPONDT) {
+            if (p->solver == SPO_SIB) {
+                /* corrector: implicit midpoint with A at the midpoint state */
+                double x[3];
+                sib_solve(n + 3 * i, Ap, p->dt, x);
+                for (int k = 0; k < 3; ++k) n[3 * i + k] = x[k];
+            } else if (p->solver == SPO_DEPONDT) {
                 double Ac[3];
                 for (int k = 0; k < 3; ++k) Ac[k] = 0.5 * (A[3 * i + k] + Ap[k]);
                 double out[3];

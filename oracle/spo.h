@@ -33,7 +33,7 @@ extern "C" {
 enum { SPO_OK = 0, SPO_ERR_ARG = -1, SPO_ERR_STATE = -2, SPO_ERR_UNSUPPORTED = -4 };
 enum { SPO_DMI_NONE = 0, SPO_DMI_BULK = 1, SPO_DMI_INTERFACIAL = 2 };
 enum { SPO_DIPOLE_NONE = 0, SPO_DIPOLE_DIRECT = 1, SPO_DIPOLE_FFT = 2 };
-enum { SPO_DEPONDT = 0, SPO_HEUN = 1 };
+enum { SPO_DEPONDT = 0, SPO_HEUN = 1, SPO_SIB = 2, SPO_RK4 = 3 };
 
 /* One unique interacting pair <ij> (Eq. 1): basis atom i in cell c interacts
  * with basis atom j in cell c + d, with exchange J and DMI vector D_ij. */
@@ -65,7 +65,7 @@ typedef struct {
 } spo_hamiltonian;
 
 typedef struct {
-    int solver;        /* SPO_DEPONDT or SPO_HEUN */
+    int solver;        /* SPO_DEPONDT, SPO_HEUN, SPO_SIB or SPO_RK4 */
     double dt;         /* ps */
     double alpha;      /* Gilbert damping */
     double T;          /* K */

@@ -20,7 +20,7 @@ MAX_SHELLS = 8
 F32, F64 = 0, 1
 DMI = {"none": 0, "bulk": 1, "interfacial": 2}
 DIPOLE = {"none": 0, "fft": 2}
-SOLVER = {"depondt": 0, "heun": 1}
+SOLVER = {"depondt": 0, "heun": 1, "sib": 2, "rk4": 3}
 ERRORS = {-1: "SP_ERR_ARG", -2: "SP_ERR_STATE", -3: "SP_ERR_CUDA", -4: "SP_ERR_UNSUPPORTED",
           -5: "SP_ERR_TIMEOUT", -6: "SP_ERR_NAN"}
 

@@ -322,18 +322,33 @@ template <typename T> LlgConst<T> llg_const(const sp_ctx *c, const sp_llg_params
 
 template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaStream_t st)
 {
-    int rc = ensure(c, c->pred, 2 * sizeof(rec_t<T>) * (size_t)c->N);
+    bool rk4 = p->solver == SP_RK4;
+    int rc = ensure(c, c->pred, (rk4 ? 3 : 2) * sizeof(rec_t<T>) * (size_t)c->N);
     if (rc) return rc;
     rec_t<T> *np = (rec_t<T> *)c->pred.p;
     rec_t<T> *q = np + c->N;
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
-    bool cub = c->cubic && c->use_cubic;
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
     LlgConst<T> k = llg_const<T>(c, p);
     for (int s = 0; s < n_steps; ++s) {
         k.step = p->step0 + (uint64_t)s;
         const void *bd;
+        if (rk4) {
+            // stage states ping-pong between np and q; acc follows them
+            rec_t<T> *acc = q + c->N;
+            const rec_t<T> *src[4] = {nn, np, q, np};
+            rec_t<T> *dst[4] = {np, q, np, nn};
+            for (int stg = 0; stg < 4; ++stg) {
+                if ((rc = dipole(c, src[stg], &bd, st))) return rc;
+                int pr = c->prof.begin(stg == 0 ? SP_PROF_LLG_PREDICTOR : SP_PROF_LLG_CORRECTOR, st);
+                cudaError_t e = launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, (const rec_t<T> *)bd, k, st);
+                c->prof.end(pr, st);
+                if (e != cudaSuccess) return cuda_fail(c, e, "RK4 stage launch");
+            }
+            continue;
+        }
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
         cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, cubic_per(c), st)
@@ -601,7 +616,7 @@ int sp_llg_step(sp_ctx *c, void *n_dev, const sp_llg_params *p, int n_steps, voi
     if (rc) return rc;
     if ((rc = check_spins(c, n_dev, "spins"))) return rc;
     if (!p) return fail(c, SP_ERR_ARG, "NULL parameters");
-    if (p->solver != SP_DEPONDT && p->solver != SP_HEUN) return fail(c, SP_ERR_ARG, "unknown solver %d", p->solver);
+    if (p->solver < SP_DEPONDT || p->solver > SP_RK4) return fail(c, SP_ERR_ARG, "unknown solver %d", p->solver);
     if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(c, SP_ERR_ARG, "dt must be positive");
     if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return fail(c, SP_ERR_ARG, "alpha must be >= 0");
     if (!(p->T >= 0) || !std::isfinite(p->T)) return fail(c, SP_ERR_ARG, "T must be >= 0");

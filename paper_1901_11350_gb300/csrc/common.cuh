@@ -224,4 +224,15 @@ template <typename T> __device__ __forceinline__ v3<T> rotate(v3<T> n, v3<T> A, 
     return axpy(an * omc, ax, axpy(s, axn, c * n));
 }
 
+// SIB step (Appendix C): the solution of M x = M^T n with M = I + skew(a),
+// a = dt A / 2, which Cramer's rule gives in closed form as the Cayley
+// rotation x = [(1 - a.a) n + 2 (a.n) a + 2 n x a] / (1 + a.a).
+template <typename T> __device__ __forceinline__ v3<T> sib_solve(v3<T> n, v3<T> A, T dt)
+{
+    v3<T> a = (T(0.5) * dt) * A;
+    T aa = dot(a, a), an = dot(a, n);
+    v3<T> x = axpy(T(2) * an, a, axpy(T(2), cross(n, a), (T(1) - aa) * n));
+    return (T(1) / (T(1) + aa)) * x;
+}
+
 }  // namespace spgb

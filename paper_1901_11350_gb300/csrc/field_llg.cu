@@ -62,6 +62,11 @@ __global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Ste
         v3<T> g = cross(p, llg_A(c.cA[b], c.alpha, p, Bth));
         st(np, i, p);
         st(q, i, axpy(T(0.5) * c.dt, f + g, ni));
+    } else if (SOLVER == SP_SIB) {
+        // np holds the midpoint (n + x_p)/2, q the thermal part of A there
+        v3<T> m = T(0.5) * (ni + sib_solve(ni, A, c.dt));
+        st(np, i, m);
+        st(q, i, llg_A(c.cA[b], c.alpha, m, Bth));
     } else {
         v3<T> p = rotate(ni, A, c.dt);
         st(np, i, p);
@@ -84,6 +89,8 @@ __global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Ste
     v3<T> qi = ld(q, i);
     if (SOLVER == SP_HEUN) {
         st(n, i, normalised(axpy(T(0.5) * c.dt, cross(p, Ap), qi)));
+    } else if (SOLVER == SP_SIB) {
+        st(n, i, sib_solve(ldc(n, i), Ap + qi, c.dt));
     } else {
         v3<T> Ac = axpy(T(0.5), Ap, qi);
         st(n, i, rotate(ldc(n, i), Ac, c.dt));
@@ -97,6 +104,8 @@ cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, 
     if (S.N == 0) return cudaSuccess;
     if (solver == SP_HEUN)
         k_llg_pred<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+    else if (solver == SP_SIB)
+        k_llg_pred<T, SP_SIB><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
     else
         k_llg_pred<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
     return cudaGetLastError();
@@ -109,8 +118,56 @@ cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const 
     if (S.N == 0) return cudaSuccess;
     if (solver == SP_HEUN)
         k_llg_corr<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+    else if (solver == SP_SIB)
+        k_llg_corr<T, SP_SIB><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
     else
         k_llg_corr<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- RK4
+// Stage s of the fourth-order Runge-Kutta step on y' = y x A(y, B(y) + B_th),
+// the same thermal field in every stage: k = y x A at the stage state y (src),
+// acc accumulates k1 + 2 k2 + 2 k3, the next stage state n + c dt k goes to
+// dst; stage 3 writes normalise(n + dt/6 (acc + k4)) to n.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(kBlock) k_rk4(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ n,
+                                                const rec_t<T> *__restrict__ src, rec_t<T> *__restrict__ dst,
+                                                rec_t<T> *__restrict__ acc, const rec_t<T> *__restrict__ Bdd,
+                                                const LlgConst<T> c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    int b;
+    v3<T> y = ld(src, i);
+    v3<T> B = local_field(S, src, i, y, b);
+    if (Bdd) B = B + ld(Bdd, i);
+    if (c.thermal) B = B + c.sig[b] * box_muller(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+    v3<T> k = cross(y, llg_A(c.cA[b], c.alpha, y, B));
+    v3<T> ni = ldc(n, i);
+    if (STAGE == 0) {
+        st(acc, i, k);
+        st(dst, i, axpy(T(0.5) * c.dt, k, ni));
+    } else if (STAGE < 3) {
+        st(acc, i, axpy(T(2), k, ldc(acc, i)));
+        st(dst, i, axpy((STAGE == 1 ? T(0.5) : T(1)) * c.dt, k, ni));
+    } else {
+        st(n, i, normalised(axpy(c.dt / T(6), ldc(acc, i) + k, ni)));
+    }
+}
+
+template <typename T>
+cudaError_t launch_rk4_stage(int stage, const Stencil<T> &S, rec_t<T> *n, const rec_t<T> *src, rec_t<T> *dst,
+                             rec_t<T> *acc, const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st)
+{
+    if (S.N == 0) return cudaSuccess;
+    int g = blocks_for(S.N);
+    switch (stage) {
+    case 0: k_rk4<T, 0><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
+    case 1: k_rk4<T, 1><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
+    case 2: k_rk4<T, 2><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
+    default: k_rk4<T, 3><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
+    }
     return cudaGetLastError();
 }
 
@@ -224,6 +281,8 @@ cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T>
                                             rec_t<T> *, const LlgConst<T> &, cudaStream_t);                            \
     template cudaError_t launch_llg_corr<T>(int, const Stencil<T> &, rec_t<T> *, const rec_t<T> *, const rec_t<T> *,    \
                                             const rec_t<T> *, const LlgConst<T> &, cudaStream_t);                      \
+    template cudaError_t launch_rk4_stage<T>(int, const Stencil<T> &, rec_t<T> *, const rec_t<T> *, rec_t<T> *,        \
+                                             rec_t<T> *, const rec_t<T> *, const LlgConst<T> &, cudaStream_t);         \
     template cudaError_t launch_energy<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, double *, double *,   \
                                           double *, cudaStream_t);
 SPGB_INST(float)

@@ -27,6 +27,10 @@ cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, 
 template <typename T>
 cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const rec_t<T> *np, const rec_t<T> *q,
                             const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st);
+// RK4 stage 0..3 (stage 0 reads src = n; stage 3 writes n).
+template <typename T>
+cudaError_t launch_rk4_stage(int stage, const Stencil<T> &S, rec_t<T> *n, const rec_t<T> *src, rec_t<T> *dst,
+                             rec_t<T> *acc, const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st);
 // Energies (6 FP64 sums) and max torque of the spins n; partials needs
 // 8 * blocks_for(N) doubles.  e_out (6) and torque_out (1) may be null.
 template <typename T>

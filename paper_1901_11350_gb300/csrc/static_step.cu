@@ -57,7 +57,7 @@ template <typename T> int run_static(sp_ctx *c, void *n, const sp_llg_params *p,
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
-    bool cub = c->cubic && c->use_cubic;
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
     LlgConst<T> k{};
     k.dt = (T)p->dt;
     k.alpha = (T)p->alpha;
@@ -93,7 +93,9 @@ extern "C" int sp_llg_step_static(sp_ctx *c, void *n_dev, const sp_llg_params *p
     if (!n_dev || ((uintptr_t)n_dev % (c->prec == SP_F64 ? 32 : 16)) != 0)
         return fail_static(c, SP_ERR_ARG, "spins must be a non-NULL, record-aligned device pointer");
     if (!p) return fail_static(c, SP_ERR_ARG, "NULL parameters");
-    if (p->solver != SP_DEPONDT && p->solver != SP_HEUN) return fail_static(c, SP_ERR_ARG, "unknown solver");
+    if (p->solver < SP_DEPONDT || p->solver > SP_RK4) return fail_static(c, SP_ERR_ARG, "unknown solver");
+    if (p->solver == SP_RK4)
+        return fail_static(c, SP_ERR_UNSUPPORTED, "sp_llg_step_static: RK4 needs 3 scratch records per spin");
     if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail_static(c, SP_ERR_ARG, "dt must be positive");
     if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return fail_static(c, SP_ERR_ARG, "alpha must be >= 0");
     if (!(p->T >= 0) || !std::isfinite(p->T)) return fail_static(c, SP_ERR_ARG, "T must be >= 0");

@@ -110,7 +110,7 @@ def test_cubic_path_detection():
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("solver", ["depondt", "heun"])
+@pytest.mark.parametrize("solver", ["depondt", "heun", "sib", "rk4"])
 @pytest.mark.parametrize("T", [0.0, 10.0])
 @pytest.mark.parametrize("path", ["default", "generic"])
 def test_llg_step_fp64(name, solver, T, path):
@@ -128,7 +128,7 @@ def test_llg_step_fp64(name, solver, T, path):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("solver", ["depondt", "heun"])
+@pytest.mark.parametrize("solver", ["depondt", "heun", "sib", "rk4"])
 @pytest.mark.parametrize("path", ["default", "generic"])
 def test_llg_step_fp32_per_step(name, solver, path):
     if path == "generic" and name not in CUBIC:

@@ -522,3 +522,47 @@ def test_topological_charge_of_skyrmion_and_ferromagnet():
     q = s.topological_charge(I.neel_skyrmion(r, centre, 8.0))
     assert abs(q + 1) < 1e-9
     assert abs(s.topological_charge(I.ferromagnet(s.N))) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# SIB (Appendix C) and RK4
+# ----------------------------------------------------------------------------
+def test_sib_is_second_order_and_norm_preserving():
+    e = [_larmor_error("sib", dt, t_end=40.0)[0] for dt in (0.02, 0.01)]
+    assert 3.8 < e[0] / e[1] < 4.2
+    # the implicit midpoint step is a Cayley rotation: |n| = 1 without renormalisation
+    c = I.cfg_square_32()
+    s = oracle.System(dict(c["geometry"], n_cells=[9, 7, 1]), c["hamiltonian"])
+    n = s.llg(I.random_spins(s.N, 2), 500, solver="sib", dt=2e-3, alpha=0.2, T=20.0, seed=3)
+    assert np.abs(np.linalg.norm(n, axis=1) - 1).max() < 1e-13
+
+
+def test_sib_step_solves_the_two_implicit_midpoint_equations():
+    # Appendix C for one spin in a constant field, solved here with a library
+    # linear solver instead of Cramer's rule:
+    #   predictor  x_p = n + dt (n + x_p)/2 x A(n)
+    #   corrector  x   = n + dt (n + x)/2 x A((n + x_p)/2)
+    # i.e. (I + dt/2 [A]x) y = n + dt/2 n x A with [A]x y = A x y.
+    mu, alpha, dt = 1.5, 0.2, 0.05
+    s = oracle.System(I.square(1, 1, mu_s=mu), dict(B=[0.3, -0.4, 1.1]))
+    n0 = np.array([0.6, 0.0, 0.8])
+    B = s.field(n0[None])[0]  # Zeeman only: the same for any spin direction
+    gp = -oracle.GAMMA / ((1 + alpha ** 2) * mu * oracle.MU_B)
+
+    def A(m):
+        return gp * (B + alpha * np.cross(m, B))
+
+    def midpoint_solve(n, a):
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        return np.linalg.solve(np.eye(3) + 0.5 * dt * K, n + 0.5 * dt * np.cross(n, a))
+
+    xp = midpoint_solve(n0, A(n0))
+    x = midpoint_solve(n0, A(0.5 * (n0 + xp)))
+    n1 = s.llg(n0[None], 1, solver="sib", dt=dt, alpha=alpha)[0]
+    assert np.abs(n1 - x).max() < 1e-15
+
+
+def test_rk4_is_fourth_order():
+    e = [_larmor_error("rk4", dt, t_end=40.0)[0] for dt in (0.04, 0.02)]
+    assert 14.0 < e[0] / e[1] < 18.0
+    assert e[1] < 1e-10
