@@ -310,7 +310,11 @@ enum {
      * the option then returns that value once it has been computed) */
     SP_OPT_PLANES_PER_CTA = 2,
     /* read only: 1 when the 27-point path applies to this Hamiltonian */
-    SP_OPT_HAS_CUBIC_PATH = 3
+    SP_OPT_HAS_CUBIC_PATH = 3,
+    /* value 1: evaluate the dipole field with the radix-2 shared-memory FFT
+     * kernels even where the FP32 warp-FFT path (1024 x 1024 padded grid)
+     * applies; 0: default */
+    SP_OPT_GENERIC_FFT = 4
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose SP_OPT_PLANES_PER_CTA by measurement: times the LLG predictor pass

@@ -80,7 +80,7 @@ SIGNATURES = {
     "sp_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(C.c_longlong)]),
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
-OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3}
+OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4}
 
 
 def library_path():

@@ -540,6 +540,7 @@ int sp_set_hamiltonian(sp_ctx *c, const sp_hamiltonian *h)
             for (int l = 0; l < 3; ++l) g.basis[b][l] = c->basis[b][l];
         }
         int e = dipole_create(&c->dip, g);
+        if (!e) dipole_force_generic(c->dip, c->generic_fft);
         if (e == SP_ERR_UNSUPPORTED) return fail(c, e, "dipole FFT supports one basis atom and 2D grids up to 4096");
         if (e) return fail(c, e, "dipole plan creation failed");
     }
@@ -746,6 +747,10 @@ int sp_set_option(sp_ctx *c, int option, int value)
     case SP_OPT_GENERIC_STENCIL:
         c->use_cubic = value == 0;
         return SP_OK;
+    case SP_OPT_GENERIC_FFT:
+        c->generic_fft = value != 0;
+        dipole_force_generic(c->dip, c->generic_fft);
+        return SP_OK;
     case SP_OPT_PLANES_PER_CTA:
         if (value < 0) return fail(c, SP_ERR_ARG, "units per CTA must be >= 0 (0: balanced)");
         c->zc = value;
@@ -780,6 +785,9 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_HAS_CUBIC_PATH:
         *value = c->cubic ? 1 : 0;
+        return SP_OK;
+    case SP_OPT_GENERIC_FFT:
+        *value = c->generic_fft ? 1 : 0;
         return SP_OK;
     default:
         return SP_ERR_ARG;

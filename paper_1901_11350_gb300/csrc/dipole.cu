@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "dipole.h"
+#include "dipole_fast.h"
 
 namespace spgb {
 
@@ -202,6 +203,9 @@ struct DipolePlan {
     void *K[2] = {nullptr, nullptr}, *S[2] = {nullptr, nullptr}, *tw0[2] = {nullptr, nullptr},
          *tw1[2] = {nullptr, nullptr};
     bool ready[2] = {false, false};
+    // FP32 warp-FFT path on a 1024 x 1024 grid
+    bool fast = false, force_generic = false;
+    void *Kt = nullptr, *ST = nullptr;
 };
 
 namespace {
@@ -279,6 +283,21 @@ template <typename T> cudaError_t prepare(DipolePlan *p, cudaStream_t st)
     for (int ky = 0; ky < d.P1; ++ky)
         for (int kx = 0; kx < d.ncols; ++kx)
             for (int c = 0; c < 6; ++c) K[((size_t)ky * d.ncols + kx) * 6 + c] = (T)(grid[c * M + (long)ky * d.P0 + kx].real() * scale);
+    if (sizeof(T) == 4 && d.P0 == 1024 && d.P1 == 1024) {
+        // column-major copy for the warp-FFT path: Kt[kx][ky][6]
+        std::vector<float> Kt((size_t)513 * 1024 * 6);
+        for (int kx = 0; kx < 513; ++kx)
+            for (int ky = 0; ky < 1024; ++ky)
+                for (int c = 0; c < 6; ++c)
+                    Kt[((size_t)kx * 1024 + ky) * 6 + c] = (float)(grid[c * M + (long)ky * d.P0 + kx].real() * scale);
+        cudaError_t e;
+        if ((e = cudaMalloc(&p->Kt, sizeof(float) * Kt.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&p->ST, sizeof(float2) * 3 * 513 * (size_t)d.n1)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(p->Kt, Kt.data(), sizeof(float) * Kt.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if ((e = dipole_fast_setup()) != cudaSuccess) return e;
+        p->fast = true;
+    }
     std::vector<C> t0(std::max(1, d.P0 / 2)), t1(std::max(1, d.P1 / 2));
     for (int k = 0; k < d.P0 / 2; ++k) t0[k] = C{(T)std::cos(2 * M_PI * k / d.P0), (T)-std::sin(2 * M_PI * k / d.P0)};
     for (int k = 0; k < d.P1 / 2; ++k) t1[k] = C{(T)std::cos(2 * M_PI * k / d.P1), (T)-std::sin(2 * M_PI * k / d.P1)};
@@ -307,6 +326,8 @@ template <typename T> cudaError_t run(DipolePlan *p, const void *n, void *out, c
     int ix = sizeof(T) == 8 ? 1 : 0;
     using C = cx_t<T>;
     const Dims &d = p->d;
+    if (sizeof(T) == 4 && p->fast && !p->force_generic)
+        return dipole_fast_run(d.n0, d.n1, (const float4 *)n, (float2 *)p->ST, (const float *)p->Kt, (float4 *)out, st);
     size_t row_smem = 2 * sizeof(C) * d.P0, col_smem = 3 * sizeof(C) * (size_t)d.cw * d.P1;
     C *S = (C *)p->S[ix];
     k_dip_rows<T><<<d.n1, 256, row_smem, st>>>(d, (const rec_t<T> *)n, S, (const C *)p->tw0[ix]);
@@ -351,7 +372,14 @@ void dipole_destroy(DipolePlan *p)
         if (p->tw0[k]) cudaFree(p->tw0[k]);
         if (p->tw1[k]) cudaFree(p->tw1[k]);
     }
+    if (p->Kt) cudaFree(p->Kt);
+    if (p->ST) cudaFree(p->ST);
     delete p;
+}
+
+void dipole_force_generic(DipolePlan *p, bool on)
+{
+    if (p) p->force_generic = on;
 }
 
 cudaError_t dipole_field(DipolePlan *p, int prec, const void *n, void *out, cudaStream_t st)

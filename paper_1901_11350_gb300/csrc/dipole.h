@@ -24,5 +24,8 @@ void dipole_destroy(DipolePlan *p);
 // Dipole field (meV) of the spins n into out (prec SP_F32: float4, SP_F64:
 // 32-byte records).  Builds the transformed kernel on first use.
 cudaError_t dipole_field(DipolePlan *p, int prec, const void *n, void *out, cudaStream_t st);
+// Use the radix-2 shared-memory transforms even where the FP32 warp-FFT path
+// applies (to compare the two).
+void dipole_force_generic(DipolePlan *p, bool on);
 
 }  // namespace spgb

@@ -1,0 +1,305 @@
+// dipole_fast.cu -- FP32 dipole convolution on a 1024 x 1024 padded grid
+// (one-atom 2D lattices with 257..512 cells per side), same mathematics as
+// dipole.cu with transforms laid out for the GPU:
+//
+// * every 1024-point transform is done by one warp as a four-step FFT,
+//   1024 = 32 x 32: lane l holds x[32 n2 + l]; a 32-point FFT over n2 in
+//   registers; twiddle W_1024^(l k2); transpose through shared memory; a
+//   32-point FFT over n1 in registers -> lane m holds X[m + 32 k1];
+// * row spectra are stored column-contiguous, ST[c][kx][y], so the column
+//   pass reads and writes coalesced runs, and the row passes move 32-byte
+//   runs of four rows;
+// * the column pass multiplies by Khat in the strided register layout the
+//   inverse transform takes as input, so no reordering is needed.
+#include <cmath>
+
+#include "dipole.h"
+#include "dipole_fast.h"
+
+namespace spgb {
+
+namespace {
+
+constexpr int kRows = 4;         // rows per block in the row passes
+constexpr int kTr = 32 * 33;     // transpose tile per warp (padded rows)
+
+// W_32^j = exp(-2 pi i j / 32), j = 0..15
+__constant__ float2 c_w32[16] = {
+    {1.000000000e+00f, 0.000000000e+00f},   {9.807852804e-01f, -1.950903220e-01f},
+    {9.238795325e-01f, -3.826834324e-01f},  {8.314696123e-01f, -5.555702330e-01f},
+    {7.071067812e-01f, -7.071067812e-01f},  {5.555702330e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, -9.238795325e-01f},  {1.950903220e-01f, -9.807852804e-01f},
+    {0.000000000e+00f, -1.000000000e+00f},  {-1.950903220e-01f, -9.807852804e-01f},
+    {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
+    {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
+
+__device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 ca(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cs(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cj(float2 a) { return make_float2(a.x, -a.y); }
+
+constexpr int rev5(int i)
+{
+    return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+}
+
+// In-register radix-2 DIT FFT of 32 points (natural order in and out);
+// INV: conjugate twiddles (unnormalised inverse).
+template <bool INV> __device__ __forceinline__ void fft32(float2 (&a)[32])
+{
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int j = rev5(i);
+        if (i < j) {
+            float2 t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+#pragma unroll
+    for (int s = 1; s <= 5; ++s) {
+        const int half = 1 << (s - 1), span = 1 << s;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int j = k % half, i0 = (k / half) * span + j, i1 = i0 + half;
+            float2 t;
+            if (j == 0) {
+                t = a[i1];
+            } else {
+                float2 w = c_w32[j * (32 / span)];
+                if (INV) w.y = -w.y;
+                t = cm(a[i1], w);
+            }
+            a[i1] = cs(a[i0], t);
+            a[i0] = ca(a[i0], t);
+        }
+    }
+}
+
+// Per-lane twiddles W_1024^(l k2): the base W^l and anchors W^(8 l), W^(16 l),
+// W^(24 l); the other powers follow by at most 7 multiplications.
+struct Tw {
+    float2 base, a8, a16, a24;
+};
+
+__device__ __forceinline__ Tw twiddles(int lane, bool inv)
+{
+    Tw t;
+    float s, c;
+    float sg = inv ? 1.f : -1.f;
+    sincospif(sg * (float)lane / 512.f, &s, &c);
+    t.base = make_float2(c, s);
+    sincospif(sg * (float)(8 * lane) / 512.f, &s, &c);
+    t.a8 = make_float2(c, s);
+    sincospif(sg * (float)(16 * lane) / 512.f, &s, &c);
+    t.a16 = make_float2(c, s);
+    sincospif(sg * (float)(24 * lane) / 512.f, &s, &c);
+    t.a24 = make_float2(c, s);
+    return t;
+}
+
+// Four-step 1024-point FFT by one warp: on entry a[n2] = x[32 n2 + lane], on
+// exit a[k1] = X[lane + 32 k1].  tr: this warp's 32 x 33 transpose tile.
+template <bool INV> __device__ __forceinline__ void fft1024(float2 (&a)[32], float2 *tr, int lane, const Tw &tw)
+{
+    fft32<INV>(a);
+    float2 w = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+        if (k2 == 8) w = tw.a8;
+        else if (k2 == 16) w = tw.a16;
+        else if (k2 == 24) w = tw.a24;
+        else if (k2 > 0) w = cm(w, tw.base);
+        if (k2 > 0) a[k2] = cm(a[k2], w);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) tr[k2 * 33 + lane] = a[k2];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) a[n1] = tr[lane * 33 + n1];
+    __syncwarp();
+    fft32<INV>(a);
+}
+
+// ------------------------------------------------------------ row pass
+// Block: kRows rows.  Writes ST[c][k][y] for k = 0..512: half spectra of the
+// x and y moment components (packed into one complex transform) and of z.
+__global__ void __launch_bounds__(32 * kRows) k_rows(int n0, int n1, const float4 *__restrict__ n, float2 *__restrict__ ST)
+{
+    extern __shared__ float2 sm[];
+    float2 *stage = sm;                                 // [3][513][kRows]
+    float2 *tr = sm + 3 * 513 * kRows + (threadIdx.x / 32) * kTr;  // per warp
+    int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int y0 = blockIdx.x * kRows, y = y0 + w;
+    bool row = y < n1;
+    Tw tw = twiddles(lane, false);
+    float2 a[32];
+    // z component
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int x = 32 * n2 + lane;
+        float z = (row && x < n0) ? __ldg(&n[(long)y * n0 + x]).z : 0.f;
+        a[n2] = make_float2(z, 0.f);
+    }
+    fft1024<false>(a, tr, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 <= 16; ++k1) {
+        int k = lane + 32 * k1;
+        if (k <= 512) stage[(2 * 513 + k) * kRows + w] = a[k1];
+    }
+    // x + i y
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int x = 32 * n2 + lane;
+        float4 v = (row && x < n0) ? __ldg(&n[(long)y * n0 + x]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[n2] = make_float2(v.x, v.y);
+    }
+    fft1024<false>(a, tr, lane, tw);
+    // separate X and Y: X = (C[k] + conj C[-k]) / 2, Y = (C[k] - conj C[-k]) / 2i
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) tr[lane + 32 * k1] = a[k1];  // spectrum, natural order
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 <= 16; ++k1) {
+        int k = lane + 32 * k1;
+        if (k <= 512) {
+            float2 A = tr[k], Bc = cj(tr[(1024 - k) & 1023]);
+            float2 d = cs(A, Bc);
+            stage[(0 * 513 + k) * kRows + w] = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y + Bc.y));
+            stage[(1 * 513 + k) * kRows + w] = make_float2(0.5f * d.y, -0.5f * d.x);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * 513 * kRows; t += blockDim.x) {
+        int r = t % kRows, ck = t / kRows;
+        if (y0 + r < n1) ST[(long)ck * n1 + y0 + r] = stage[t];
+    }
+}
+
+// ------------------------------------------------------------ column pass
+// Block: one column kx, warp c = component.  Forward transform over y
+// (zero rows y >= n1), product with Khat, inverse transform, rows y < n1
+// written back in place.
+__global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, const float *__restrict__ Kt)
+{
+    extern __shared__ float2 sm[];
+    float2 *spec = sm;                                  // [3][1024]
+    float2 *tr = sm + 3 * 1024 + (threadIdx.x / 32) * kTr;
+    int c = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int kx = blockIdx.x;
+    float2 *col = ST + ((long)c * 513 + kx) * n1;
+    float2 a[32];
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int y = 32 * n2 + lane;
+        a[n2] = y < n1 ? col[y] : make_float2(0.f, 0.f);
+    }
+    fft1024<false>(a, tr, lane, twiddles(lane, false));
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) spec[c * 1024 + lane + 32 * k1] = a[k1];
+    __syncthreads();
+    const float *K = Kt + (long)kx * 1024 * 6;
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int ky = 32 * n2 + lane;
+        const float *k6 = K + ky * 6;
+        // symmetric tensor xx xy xz yy yz zz; row c
+        float r0, r1, r2;
+        if (c == 0) {
+            r0 = __ldg(k6 + 0);
+            r1 = __ldg(k6 + 1);
+            r2 = __ldg(k6 + 2);
+        } else if (c == 1) {
+            r0 = __ldg(k6 + 1);
+            r1 = __ldg(k6 + 3);
+            r2 = __ldg(k6 + 4);
+        } else {
+            r0 = __ldg(k6 + 2);
+            r1 = __ldg(k6 + 4);
+            r2 = __ldg(k6 + 5);
+        }
+        float2 X = spec[ky], Y = spec[1024 + ky], Z = spec[2048 + ky];
+        a[n2] = make_float2(r0 * X.x + r1 * Y.x + r2 * Z.x, r0 * X.y + r1 * Y.y + r2 * Z.y);
+    }
+    fft1024<true>(a, tr, lane, twiddles(lane, true));
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+        int y = lane + 32 * k1;
+        if (y < n1) col[y] = a[k1];
+    }
+}
+
+// ------------------------------------------------------------ inverse rows
+// Block: kRows rows.  Complex-to-real inverse of each row (x and y packed as
+// X + i Y, z alone), cropped to x < n0 and written as 4-wide records.
+__global__ void __launch_bounds__(32 * kRows) k_irows(int n0, int n1, const float2 *__restrict__ ST, float4 *__restrict__ out)
+{
+    extern __shared__ float2 sm[];
+    float2 *stage = sm;
+    float2 *tr = sm + 3 * 513 * kRows + (threadIdx.x / 32) * kTr;
+    int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int y0 = blockIdx.x * kRows, y = y0 + w;
+    for (int t = threadIdx.x; t < 3 * 513 * kRows; t += blockDim.x) {
+        int r = t % kRows, ck = t / kRows;
+        stage[t] = (y0 + r < n1) ? ST[(long)ck * n1 + y0 + r] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    Tw tw = twiddles(lane, true);
+    float2 a[32];
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int k = 32 * n2 + lane;
+        a[n2] = k <= 512 ? stage[(2 * 513 + k) * kRows + w] : cj(stage[(2 * 513 + 1024 - k) * kRows + w]);
+    }
+    fft1024<true>(a, tr, lane, tw);
+    float zr[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) zr[k1] = a[k1].x;
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+        int k = 32 * n2 + lane;
+        float2 X, Y;
+        if (k <= 512) {
+            X = stage[(0 * 513 + k) * kRows + w];
+            Y = stage[(1 * 513 + k) * kRows + w];
+        } else {
+            X = cj(stage[(0 * 513 + 1024 - k) * kRows + w]);
+            Y = cj(stage[(1 * 513 + 1024 - k) * kRows + w]);
+        }
+        a[n2] = make_float2(X.x - Y.y, X.y + Y.x);  // X + i Y
+    }
+    fft1024<true>(a, tr, lane, tw);
+    if (y < n1) {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            int x = lane + 32 * k1;
+            if (x < n0) out[(long)y * n0 + x] = make_float4(a[k1].x, a[k1].y, zr[k1], 0.f);
+        }
+    }
+}
+
+constexpr size_t kRowSmem = sizeof(float2) * (3 * 513 * kRows + kRows * kTr);
+constexpr size_t kColSmem = sizeof(float2) * (3 * 1024 + 3 * kTr);
+
+}  // namespace
+
+cudaError_t dipole_fast_setup()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_irows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem);
+    return e;
+}
+
+cudaError_t dipole_fast_run(int n0, int n1, const float4 *n, float2 *ST, const float *Kt, float4 *out, cudaStream_t st)
+{
+    int rb = (n1 + kRows - 1) / kRows;
+    k_rows<<<rb, 32 * kRows, kRowSmem, st>>>(n0, n1, n, ST);
+    k_cols<<<513, 96, kColSmem, st>>>(n1, ST, Kt);
+    k_irows<<<rb, 32 * kRows, kRowSmem, st>>>(n0, n1, ST, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spgb

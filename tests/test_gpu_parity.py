@@ -228,6 +228,25 @@ def test_dipole_fp32_against_direct_sum():
     assert np.abs(Bg64 - Bo).max() <= 1e-12 * np.abs(Bo).max()
 
 
+def test_dipole_warp_fft_path_ragged_sizes():
+    # 300 x 283 cells pad to 1024 x 1024: the FP32 warp-FFT path, with rows
+    # not a multiple of its 4-row blocks; against the FP64 direct sum at
+    # sampled sites and against the radix-2 kernels on every site
+    g = I.hexagonal(300, 283, mu_s=3.0)
+    h = dict(J=[1.0], dipole="fft")
+    n0 = I.random_spins(300 * 283, 13)
+    c = B.Context(g, h, "f32")
+    Bf = _np(c.effective_field(c.spins(n0)))
+    c.set_option("generic_fft", 1)
+    Bg = _np(c.effective_field(c.spins(n0)))
+    assert np.abs(Bf - Bg).max() <= 2e-6 * np.abs(Bg).max()
+    o = _oracle(g, dict(J=[1.0], dipole="direct"))
+    idx = np.random.default_rng(1).choice(o.N, 300, replace=False)
+    idx = np.concatenate([idx, [0, 299, 300 * 282, o.N - 1]])
+    ref = o.field(n0, dipole="none")[idx] + o.dipole_field_direct_at(n0, idx)
+    assert np.abs(Bf[idx] - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
 def test_vp_minimiser_parity_fp64():
     c1 = I.cfg_square_32()
     g = dict(c1["geometry"], n_cells=[12, 10, 1], periodic=[1, 0, 0])
