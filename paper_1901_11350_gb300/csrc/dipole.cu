@@ -284,12 +284,12 @@ template <typename T> cudaError_t prepare(DipolePlan *p, cudaStream_t st)
         for (int kx = 0; kx < d.ncols; ++kx)
             for (int c = 0; c < 6; ++c) K[((size_t)ky * d.ncols + kx) * 6 + c] = (T)(grid[c * M + (long)ky * d.P0 + kx].real() * scale);
     if (sizeof(T) == 4 && d.P0 == 1024 && d.P1 == 1024) {
-        // column-major copy for the warp-FFT path: Kt[kx][ky][6]
+        // per-column structure of arrays for the warp-FFT path: Kt[kx][6][ky]
         std::vector<float> Kt((size_t)513 * 1024 * 6);
         for (int kx = 0; kx < 513; ++kx)
-            for (int ky = 0; ky < 1024; ++ky)
-                for (int c = 0; c < 6; ++c)
-                    Kt[((size_t)kx * 1024 + ky) * 6 + c] = (float)(grid[c * M + (long)ky * d.P0 + kx].real() * scale);
+            for (int c = 0; c < 6; ++c)
+                for (int ky = 0; ky < 1024; ++ky)
+                    Kt[((size_t)kx * 6 + c) * 1024 + ky] = (float)(grid[c * M + (long)ky * d.P0 + kx].real() * scale);
         cudaError_t e;
         if ((e = cudaMalloc(&p->Kt, sizeof(float) * Kt.size())) != cudaSuccess) return e;
         if ((e = cudaMalloc(&p->ST, sizeof(float2) * 3 * 513 * (size_t)d.n1)) != cudaSuccess) return e;

@@ -7,8 +7,8 @@
 //   registers; twiddle W_1024^(l k2); transpose through shared memory; a
 //   32-point FFT over n1 in registers -> lane m holds X[m + 32 k1];
 // * row spectra are stored column-contiguous, ST[c][kx][y], so the column
-//   pass reads and writes coalesced runs, and the row passes move 32-byte
-//   runs of four rows;
+//   pass reads and writes coalesced runs, and the row passes move runs of
+//   two rows;
 // * the column pass multiplies by Khat in the strided register layout the
 //   inverse transform takes as input, so no reordering is needed.
 #include <cmath>
@@ -20,7 +20,7 @@ namespace spgb {
 
 namespace {
 
-constexpr int kRows = 4;         // rows per block in the row passes
+constexpr int kRows = 2;         // rows per block in the row passes (two warps each)
 constexpr int kTr = 32 * 33;     // transpose tile per warp (padded rows)
 
 // W_32^j = exp(-2 pi i j / 32), j = 0..15
@@ -123,52 +123,47 @@ template <bool INV> __device__ __forceinline__ void fft1024(float2 (&a)[32], flo
 }
 
 // ------------------------------------------------------------ row pass
-// Block: kRows rows.  Writes ST[c][k][y] for k = 0..512: half spectra of the
-// x and y moment components (packed into one complex transform) and of z.
-__global__ void __launch_bounds__(32 * kRows) k_rows(int n0, int n1, const float4 *__restrict__ n, float2 *__restrict__ ST)
+// Block: kRows rows, two warps per row (z, and x + i y).  Writes ST[c][k][y]
+// for k = 0..512: half spectra of the x and y moment components (packed into
+// one complex transform) and of z.
+__global__ void __launch_bounds__(64 * kRows) k_rows(int n0, int n1, const float4 *__restrict__ n, float2 *__restrict__ ST)
 {
     extern __shared__ float2 sm[];
-    float2 *stage = sm;                                 // [3][513][kRows]
+    float2 *stage = sm;                                             // [3][513][kRows]
     float2 *tr = sm + 3 * 513 * kRows + (threadIdx.x / 32) * kTr;  // per warp
-    int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int w = wid >> 1, part = wid & 1;  // row in block; 0: z, 1: x + i y
     int y0 = blockIdx.x * kRows, y = y0 + w;
     bool row = y < n1;
     Tw tw = twiddles(lane, false);
     float2 a[32];
-    // z component
-#pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) {
-        int x = 32 * n2 + lane;
-        float z = (row && x < n0) ? __ldg(&n[(long)y * n0 + x]).z : 0.f;
-        a[n2] = make_float2(z, 0.f);
-    }
-    fft1024<false>(a, tr, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 <= 16; ++k1) {
-        int k = lane + 32 * k1;
-        if (k <= 512) stage[(2 * 513 + k) * kRows + w] = a[k1];
-    }
-    // x + i y
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) {
         int x = 32 * n2 + lane;
         float4 v = (row && x < n0) ? __ldg(&n[(long)y * n0 + x]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        a[n2] = make_float2(v.x, v.y);
+        a[n2] = part ? make_float2(v.x, v.y) : make_float2(v.z, 0.f);
     }
     fft1024<false>(a, tr, lane, tw);
-    // separate X and Y: X = (C[k] + conj C[-k]) / 2, Y = (C[k] - conj C[-k]) / 2i
-    __syncwarp();
+    if (part == 0) {
 #pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) tr[lane + 32 * k1] = a[k1];  // spectrum, natural order
-    __syncwarp();
+        for (int k1 = 0; k1 <= 16; ++k1) {
+            int k = lane + 32 * k1;
+            if (k <= 512) stage[(2 * 513 + k) * kRows + w] = a[k1];
+        }
+    } else {
+        // separate X and Y: X = (C[k] + conj C[-k]) / 2, Y = (C[k] - conj C[-k]) / 2i
 #pragma unroll
-    for (int k1 = 0; k1 <= 16; ++k1) {
-        int k = lane + 32 * k1;
-        if (k <= 512) {
-            float2 A = tr[k], Bc = cj(tr[(1024 - k) & 1023]);
-            float2 d = cs(A, Bc);
-            stage[(0 * 513 + k) * kRows + w] = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y + Bc.y));
-            stage[(1 * 513 + k) * kRows + w] = make_float2(0.5f * d.y, -0.5f * d.x);
+        for (int k1 = 0; k1 < 32; ++k1) tr[lane + 32 * k1] = a[k1];  // spectrum, natural order
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 <= 16; ++k1) {
+            int k = lane + 32 * k1;
+            if (k <= 512) {
+                float2 A = tr[k], Bc = cj(tr[(1024 - k) & 1023]);
+                float2 d = cs(A, Bc);
+                stage[(0 * 513 + k) * kRows + w] = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y + Bc.y));
+                stage[(1 * 513 + k) * kRows + w] = make_float2(0.5f * d.y, -0.5f * d.x);
+            }
         }
     }
     __syncthreads();
@@ -179,16 +174,28 @@ __global__ void __launch_bounds__(32 * kRows) k_rows(int n0, int n1, const float
 }
 
 // ------------------------------------------------------------ column pass
-// Block: one column kx, warp c = component.  Forward transform over y
-// (zero rows y >= n1), product with Khat, inverse transform, rows y < n1
+// Block: one column kx, warp c = component.  Khat of the column (6 x 1024
+// reals, structure of arrays) is copied to shared memory with cp.async while
+// the forward transform over y runs (zero rows y >= n1); product with Khat
+// in the strided layout of the inverse transform's input; rows y < n1
 // written back in place.
+__device__ __forceinline__ void cp16(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
 __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, const float *__restrict__ Kt)
 {
     extern __shared__ float2 sm[];
     float2 *spec = sm;                                  // [3][1024]
     float2 *tr = sm + 3 * 1024 + (threadIdx.x / 32) * kTr;
+    float *ks = reinterpret_cast<float *>(sm + 3 * 1024 + 3 * kTr);  // [6][1024]
     int c = threadIdx.x / 32, lane = threadIdx.x % 32;
     int kx = blockIdx.x;
+    const float *K = Kt + (long)kx * 6 * 1024;
+    for (int t = threadIdx.x; t < 6 * 1024 / 4; t += blockDim.x) cp16(ks + 4 * t, K + 4 * t);
+    asm volatile("cp.async.commit_group;\n" ::);
     float2 *col = ST + ((long)c * 513 + kx) * n1;
     float2 a[32];
 #pragma unroll
@@ -199,27 +206,16 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
     fft1024<false>(a, tr, lane, twiddles(lane, false));
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) spec[c * 1024 + lane + 32 * k1] = a[k1];
+    asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
-    const float *K = Kt + (long)kx * 1024 * 6;
+    // row c of the symmetric tensor (xx xy xz yy yz zz)
+    const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2);
+    const int i1 = c == 0 ? 1 : (c == 1 ? 3 : 4);
+    const int i2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) {
         int ky = 32 * n2 + lane;
-        const float *k6 = K + ky * 6;
-        // symmetric tensor xx xy xz yy yz zz; row c
-        float r0, r1, r2;
-        if (c == 0) {
-            r0 = __ldg(k6 + 0);
-            r1 = __ldg(k6 + 1);
-            r2 = __ldg(k6 + 2);
-        } else if (c == 1) {
-            r0 = __ldg(k6 + 1);
-            r1 = __ldg(k6 + 3);
-            r2 = __ldg(k6 + 4);
-        } else {
-            r0 = __ldg(k6 + 2);
-            r1 = __ldg(k6 + 4);
-            r2 = __ldg(k6 + 5);
-        }
+        float r0 = ks[i0 * 1024 + ky], r1 = ks[i1 * 1024 + ky], r2 = ks[i2 * 1024 + ky];
         float2 X = spec[ky], Y = spec[1024 + ky], Z = spec[2048 + ky];
         a[n2] = make_float2(r0 * X.x + r1 * Y.x + r2 * Z.x, r0 * X.y + r1 * Y.y + r2 * Z.y);
     }
@@ -232,14 +228,16 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
 }
 
 // ------------------------------------------------------------ inverse rows
-// Block: kRows rows.  Complex-to-real inverse of each row (x and y packed as
-// X + i Y, z alone), cropped to x < n0 and written as 4-wide records.
-__global__ void __launch_bounds__(32 * kRows) k_irows(int n0, int n1, const float2 *__restrict__ ST, float4 *__restrict__ out)
+// Block: kRows rows, two warps per row: complex-to-real inverse of z, and of
+// X + i Y; cropped to x < n0 and written as 4-wide records.
+__global__ void __launch_bounds__(64 * kRows) k_irows(int n0, int n1, const float2 *__restrict__ ST, float4 *__restrict__ out)
 {
     extern __shared__ float2 sm[];
     float2 *stage = sm;
     float2 *tr = sm + 3 * 513 * kRows + (threadIdx.x / 32) * kTr;
-    int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    float *zs = reinterpret_cast<float *>(sm + 3 * 513 * kRows + 2 * kRows * kTr);  // [kRows][512]
+    int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int w = wid >> 1, part = wid & 1;
     int y0 = blockIdx.x * kRows, y = y0 + w;
     for (int t = threadIdx.x; t < 3 * 513 * kRows; t += blockDim.x) {
         int r = t % kRows, ck = t / kRows;
@@ -251,37 +249,37 @@ __global__ void __launch_bounds__(32 * kRows) k_irows(int n0, int n1, const floa
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) {
         int k = 32 * n2 + lane;
-        a[n2] = k <= 512 ? stage[(2 * 513 + k) * kRows + w] : cj(stage[(2 * 513 + 1024 - k) * kRows + w]);
-    }
-    fft1024<true>(a, tr, lane, tw);
-    float zr[16];
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) zr[k1] = a[k1].x;
-#pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) {
-        int k = 32 * n2 + lane;
-        float2 X, Y;
-        if (k <= 512) {
-            X = stage[(0 * 513 + k) * kRows + w];
-            Y = stage[(1 * 513 + k) * kRows + w];
+        if (part == 0) {
+            a[n2] = k <= 512 ? stage[(2 * 513 + k) * kRows + w] : cj(stage[(2 * 513 + 1024 - k) * kRows + w]);
         } else {
-            X = cj(stage[(0 * 513 + 1024 - k) * kRows + w]);
-            Y = cj(stage[(1 * 513 + 1024 - k) * kRows + w]);
+            float2 X, Y;
+            if (k <= 512) {
+                X = stage[(0 * 513 + k) * kRows + w];
+                Y = stage[(1 * 513 + k) * kRows + w];
+            } else {
+                X = cj(stage[(0 * 513 + 1024 - k) * kRows + w]);
+                Y = cj(stage[(1 * 513 + 1024 - k) * kRows + w]);
+            }
+            a[n2] = make_float2(X.x - Y.y, X.y + Y.x);  // X + i Y
         }
-        a[n2] = make_float2(X.x - Y.y, X.y + Y.x);  // X + i Y
     }
     fft1024<true>(a, tr, lane, tw);
-    if (y < n1) {
+    if (part == 0) {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) zs[w * 512 + lane + 32 * k1] = a[k1].x;
+    }
+    __syncthreads();
+    if (part == 1 && y < n1) {
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
             int x = lane + 32 * k1;
-            if (x < n0) out[(long)y * n0 + x] = make_float4(a[k1].x, a[k1].y, zr[k1], 0.f);
+            if (x < n0) out[(long)y * n0 + x] = make_float4(a[k1].x, a[k1].y, zs[w * 512 + x], 0.f);
         }
     }
 }
 
-constexpr size_t kRowSmem = sizeof(float2) * (3 * 513 * kRows + kRows * kTr);
-constexpr size_t kColSmem = sizeof(float2) * (3 * 1024 + 3 * kTr);
+constexpr size_t kRowSmem = sizeof(float2) * (3 * 513 * kRows + 2 * kRows * kTr) + sizeof(float) * kRows * 512;
+constexpr size_t kColSmem = sizeof(float2) * (3 * 1024 + 3 * kTr) + sizeof(float) * 6 * 1024;
 
 }  // namespace
 
@@ -296,9 +294,9 @@ cudaError_t dipole_fast_setup()
 cudaError_t dipole_fast_run(int n0, int n1, const float4 *n, float2 *ST, const float *Kt, float4 *out, cudaStream_t st)
 {
     int rb = (n1 + kRows - 1) / kRows;
-    k_rows<<<rb, 32 * kRows, kRowSmem, st>>>(n0, n1, n, ST);
+    k_rows<<<rb, 64 * kRows, kRowSmem, st>>>(n0, n1, n, ST);
     k_cols<<<513, 96, kColSmem, st>>>(n1, ST, Kt);
-    k_irows<<<rb, 32 * kRows, kRowSmem, st>>>(n0, n1, ST, out);
+    k_irows<<<rb, 64 * kRows, kRowSmem, st>>>(n0, n1, ST, out);
     return cudaGetLastError();
 }
 
