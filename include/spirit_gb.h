@@ -220,6 +220,20 @@ int sp_llg_step(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, v
 int sp_minimise(sp_ctx *ctx, void *n_dev, void *v_dev, double dt, double mass, double tol,
                 int max_iter, int check_every, int *iters, double *max_torque, void *stream);
 
+/* Batched velocity-projection minimisation: n_sys independent systems, one
+ * context each (same precision, no dipole term), relaxed together -- every
+ * kernel of an iteration covers all systems in one launch -- with the
+ * iteration of sp_minimise applied per system (its own 3N dot products,
+ * convergence test and iteration count; a converged system stops moving).
+ *   spins_dev, vel_dev  ONE device buffer each; system c's N_c records start
+ *                       at record offset offsets[c]; systems must not overlap
+ *   iters[c], max_torque[c]  host outputs
+ * Synchronises `stream` every check_every iterations.  Scratch belongs to
+ * ctxs[0]. */
+int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel_dev, const long long *offsets,
+                      double dt, double mass, double tol, int max_iter, int check_every, int *iters,
+                      double *max_torque, void *stream);
+
 /* ------------------------------------------------------------------------
  * Geodesic nudged elastic band (Sec. GNEB, Appendix F)
  * ------------------------------------------------------------------------ */

@@ -72,6 +72,8 @@ SIGNATURES = {
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
                                C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_minimise_batch": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), _d, _d, _d, _i, _i,
+                              C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_llg_step_static": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_set_option": (_i, [_vp, _i, _i]),
     "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
@@ -290,3 +292,24 @@ def gneb_batch_step(ctxs, chains, vel, offsets, n_images, n_iter=1, k_spring=1.0
     if rc:
         raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
     return E, F
+
+
+def minimise_batch(ctxs, spins, vel, offsets, dt=0.1, mass=1.0, tol=1e-6, max_iter=10000, check_every=64):
+    """Relax many systems (one context each) together; `spins` and `vel` are
+    one flat CUDA tensor of 4-wide records each.  Returns (iters, max_torque)
+    as numpy arrays."""
+    L = lib()
+    n = len(ctxs)
+    dtype = ctxs[0].dtype
+    for t, name in ((spins, "spins"), (vel, "vel")):
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.shape[-1] == 4):
+            raise ValueError("%s must be a contiguous CUDA %s tensor of 4-wide records" % (name, dtype))
+    handles = (C.c_void_p * n)(*[c._h for c in ctxs])
+    offs = (C.c_longlong * n)(*[int(x) for x in offsets])
+    it = (C.c_int * n)()
+    mt = (C.c_double * n)()
+    rc = L.sp_minimise_batch(handles, n, _ptr(spins), _ptr(vel), offs, float(dt), float(mass), float(tol),
+                             int(max_iter), int(check_every), it, mt, _stream())
+    if rc:
+        raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
+    return np.array(it[:], dtype=np.int64), np.array(mt[:])

@@ -688,6 +688,48 @@ int sp_topological_charge(sp_ctx *c, const void *n_dev, double *Q_dev, void *str
     return SP_OK;
 }
 
+int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel_dev, const long long *offsets,
+                      double dt, double mass, double tol, int max_iter, int check_every, int *iters,
+                      double *max_torque, void *stream)
+{
+    if (!ctxs || n_sys < 1 || !ctxs[0]) return SP_ERR_ARG;
+    sp_ctx *c0 = ctxs[0];
+    if (!offsets || !iters || !max_torque) return fail(c0, SP_ERR_ARG, "NULL batch argument");
+    int rc;
+    if ((rc = check_spins(c0, spins_dev, "spins")) || (rc = check_spins(c0, vel_dev, "velocities"))) return rc;
+    if (spins_dev == vel_dev) return fail(c0, SP_ERR_ARG, "spins and velocities must not overlap");
+    if (!(dt > 0) || !(mass > 0) || !(tol >= 0) || max_iter < 0 || check_every < 1)
+        return fail(c0, SP_ERR_ARG, "bad minimiser parameters");
+    std::vector<std::pair<long long, long long>> spans;
+    std::vector<long long> off;
+    for (int k = 0; k < n_sys; ++k) {
+        sp_ctx *c = ctxs[k];
+        if (!c) return fail(c0, SP_ERR_ARG, "NULL context for system %d", k);
+        if (!c->have_geom || !c->have_ham) return fail(c0, SP_ERR_STATE, "system %d: context not configured", k);
+        if (c->prec != c0->prec) return fail(c0, SP_ERR_ARG, "system %d: precision differs from system 0", k);
+        if (c->h.dipole != SP_DIPOLE_NONE) return fail(c0, SP_ERR_UNSUPPORTED, "system %d: dipole term", k);
+        if (offsets[k] < 0 || offsets[k] + c->N >= (1LL << 31)) return fail(c0, SP_ERR_ARG, "system %d: bad offset", k);
+        spans.push_back({offsets[k], offsets[k] + c->N});
+        off.push_back(offsets[k]);
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t k = 1; k < spans.size(); ++k)
+        if (spans[k].first < spans[k - 1].second) return fail(c0, SP_ERR_ARG, "systems overlap in the batch buffer");
+    MinArgs a{dt, mass, tol, max_iter, check_every};
+    int e;
+    if (c0->prec == SP_F64) {
+        std::vector<Stencil<double>> S;
+        for (int k = 0; k < n_sys; ++k) S.push_back(ctxs[k]->Sd);
+        e = vp_batch_run<double>(&c0->mins, S, off, spins_dev, vel_dev, a, iters, max_torque, (cudaStream_t)stream);
+    } else {
+        std::vector<Stencil<float>> S;
+        for (int k = 0; k < n_sys; ++k) S.push_back(ctxs[k]->Sf);
+        e = vp_batch_run<float>(&c0->mins, S, off, spins_dev, vel_dev, a, iters, max_torque, (cudaStream_t)stream);
+    }
+    if (e) return fail(c0, e, "batched minimisation failed");
+    return SP_OK;
+}
+
 int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void *vel_dev, const long long *offsets,
                        const int *n_images, const sp_gneb_params *p, int n_iter, double *energies_dev,
                        double *max_force_dev, void *stream)

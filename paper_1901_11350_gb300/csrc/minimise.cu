@@ -415,6 +415,165 @@ int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const Mi
     return 0;
 }
 
+// ------------------------------------------------------------ batched VP
+// One image per system.  Per system g: scal[8g + kVF, kFF, kFMAX] from the
+// last force pass, state[2g] iterations moved, state[2g+1] active flag,
+// proj[g] whether the last force pass updated the velocity.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                      const Stencil<T> *__restrict__ S, const rec_t<T> *__restrict__ x,
+                                                      rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, double dth_m,
+                                                      int mode, double *part, unsigned *cnt, double *scal,
+                                                      const int *state, int *proj)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    if (mode == 1 && state[2 * bi.g + 1] == 0) return;
+    const Stencil<T> &St = S[im.chain];
+    int i = bi.t * kBlock + threadIdx.x;
+    const rec_t<T> *xb = x + im.spin0;
+    double r[3] = {0, 0, 0};
+    if (i < im.N) {
+        int b;
+        long long p = im.spin0 + i;
+        v3<T> ni = ld(xb, i);
+        v3<T> B = local_field(St, xb, i, ni, b);
+        v3<T> Fn = B - dot(B, ni) * ni;
+        if (mode == 1) {
+            v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
+            st(v, p, vi);
+            r[0] = (double)dot(vi, Fn);
+        }
+        st(F, p, Fn);
+        r[1] = (double)dot(Fn, Fn);
+        r[2] = sqrt(r[1]);
+    }
+    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kVF);
+    if (bi.t == 0 && threadIdx.x == 0) proj[bi.g] = mode;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bvp_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                     rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
+                                                     const rec_t<T> *__restrict__ F, double dt, double dt2_2m, double tol,
+                                                     int k, int max_iter, const double *scal, int *state,
+                                                     const int *proj)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    const double *sc = scal + 8 * bi.g;
+    bool done = (sc[kFMAX] < tol) || (k >= max_iter);
+    int i = bi.t * kBlock + threadIdx.x;
+    if (i < im.N) {
+        long long p = im.spin0 + i;
+        v3<T> vi;
+        if (proj[bi.g]) {
+            double vf = sc[kVF], ff = sc[kFF];
+            T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+            vi = c * ldc(F, p);
+            st(v, p, vi);
+        } else {
+            vi = ldc(v, p);
+        }
+        if (!done) st(x, p, normalised(axpy((T)dt2_2m, ldc(F, p), axpy((T)dt, vi, ldc(x, p)))));
+    }
+    if (bi.t == 0 && threadIdx.x == 0) {
+        state[2 * bi.g + 1] = done ? 0 : 1;
+        if (!done) state[2 * bi.g] = k + 1;
+    }
+}
+
+template <typename T>
+int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const std::vector<long long> &spin0,
+                 void *spins, void *vel, const MinArgs &a, int *iters, double *max_torque, cudaStream_t st)
+{
+    int rc = scratch(sp);
+    if (rc) return rc;
+    MinScratch *s = *sp;
+    int C = (int)stencils.size();
+    std::vector<ImgInfo> img;
+    std::vector<BlkInfo> blk;
+    long long total = 0;
+    for (int c = 0; c < C; ++c) {
+        int N = stencils[c].N;
+        int bpi = blocks_for(N > 0 ? N : 1);
+        ImgInfo im{spin0[c], N, c, 0, 1, c, (int)blk.size(), bpi};
+        for (int t = 0; t < bpi; ++t) blk.push_back(BlkInfo{c, t});
+        img.push_back(im);
+        total = std::max(total, spin0[c] + (long long)N);
+    }
+    int n_full = (int)blk.size();
+    size_t rb = sizeof(rec_t<T>) * (size_t)std::max(total, 1LL);
+    // blk holds the full table followed by room for a compacted copy
+    if (grow(s->F, rb) || grow(s->scal, 8 * sizeof(double) * C) || grow(s->part, 3 * sizeof(double) * (size_t)n_full) ||
+        grow_counters(s->cnt, C, st) || grow(s->blk, 2 * sizeof(BlkInfo) * n_full) ||
+        grow(s->img, sizeof(ImgInfo) * C) || grow(s->sten, sizeof(Stencil<T>) * C) ||
+        grow(s->state, sizeof(int) * 3 * C))
+        return SP_ERR_CUDA;
+    BlkInfo *Bfull = (BlkInfo *)s->blk.p, *Bact = Bfull + n_full;
+    ImgInfo *I = (ImgInfo *)s->img.p;
+    if (cudaMemcpyAsync(Bfull, blk.data(), sizeof(BlkInfo) * n_full, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(Bact, blk.data(), sizeof(BlkInfo) * n_full, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(I, img.data(), sizeof(ImgInfo) * C, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->sten.p, stencils.data(), sizeof(Stencil<T>) * C, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(s->state.p, 0, sizeof(int) * 3 * C, st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SP_ERR_CUDA;
+    s->layout.clear();  // the GNEB tables were overwritten
+    const Stencil<T> *Sd = (const Stencil<T> *)s->sten.p;
+    rec_t<T> *x = (rec_t<T> *)spins, *v = (rec_t<T> *)vel, *F = (rec_t<T> *)s->F.p;
+    double *scal = (double *)s->scal.p, *part = (double *)s->part.p;
+    unsigned *cnt = (unsigned *)s->cnt.p;
+    int *state = (int *)s->state.p, *proj = state + 2 * C;
+    double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
+    std::vector<int> hs(2 * C);
+    k_bvp_force<T><<<n_full, kBlock, 0, st>>>(Bfull, I, Sd, x, v, F, dth_m, 0, part, cnt, scal, state, proj);
+    int k = 0, n_act = n_full;
+    while (k < a.max_iter) {
+        int chunk = std::min(a.check_every, a.max_iter - k);
+        for (int c = 0; c < chunk; ++c, ++k) {
+            k_bvp_move<T><<<n_act, kBlock, 0, st>>>(Bact, I, x, v, F, a.dt, dt2_2m, a.tol, k, a.max_iter, scal, state,
+                                                    proj);
+            k_bvp_force<T><<<n_act, kBlock, 0, st>>>(Bact, I, Sd, x, v, F, dth_m, 1, part, cnt, scal, state, proj);
+        }
+        if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
+        if (cudaMemcpyAsync(hs.data(), state, sizeof(int) * 2 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SP_ERR_CUDA;
+        // Drop converged systems from the launch tables once a quarter of the
+        // launched blocks belongs to them.  A converged system is frozen: its
+        // force pass returns at once and its move re-applies the same
+        // projection, so leaving it out changes no result.
+        std::vector<BlkInfo> act;
+        for (int c = 0; c < C; ++c)
+            if (hs[2 * c + 1]) {
+                img[c].blk0 = (int)act.size();
+                for (int t = 0; t < img[c].bpi; ++t) act.push_back(BlkInfo{c, t});
+            }
+        if (act.empty()) break;
+        if (4 * (long long)act.size() <= 3LL * n_act) {
+            n_act = (int)act.size();
+            if (cudaMemcpyAsync(Bact, act.data(), sizeof(BlkInfo) * n_act, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(I, img.data(), sizeof(ImgInfo) * C, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return SP_ERR_CUDA;
+        }
+    }
+    // final projection (where the last force pass updated the velocity)
+    k_bvp_move<T><<<n_full, kBlock, 0, st>>>(Bfull, I, x, v, F, a.dt, dt2_2m, a.tol, a.max_iter, a.max_iter, scal, state,
+                                             proj);
+    std::vector<double> hsc(8 * C);
+    if (cudaMemcpyAsync(hs.data(), state, sizeof(int) * 2 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hsc.data(), scal, sizeof(double) * 8 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    for (int c = 0; c < C; ++c) {
+        iters[c] = hs[2 * c];
+        max_torque[c] = hsc[8 * c + kFMAX];
+    }
+    return 0;
+}
+
 // ------------------------------------------------------------ GNEB host side
 template <typename T>
 int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const std::vector<int> &M,
@@ -538,6 +697,8 @@ int gneb_run(MinScratch **s, const Stencil<T> &S, void *chain, void *vel, const 
 }
 
 #define SPGB_MIN_INST(T)                                                                                               \
+    template int vp_batch_run<T>(MinScratch **, const std::vector<Stencil<T>> &, const std::vector<long long> &, void *, \
+                                 void *, const MinArgs &, int *, double *, cudaStream_t);                              \
     template int vp_minimise<T>(MinScratch **, const Stencil<T> &, void *, void *, const MinArgs &, int *, double *,    \
                                 cudaStream_t);                                                                         \
     template int gneb_run<T>(MinScratch **, const Stencil<T> &, void *, void *, const GnebArgs &, double *, double *,   \

@@ -37,4 +37,10 @@ int gneb_batch_run(MinScratch **s, const std::vector<Stencil<T>> &stencils, cons
                    const std::vector<long long> &spin0, void *chain, void *vel, const GnebArgs &a, double *E_dev,
                    double *fmax_dev, cudaStream_t st);
 
+// Batched velocity projection: system c has stencils[c].N spins from record
+// offset spin0[c]; iters[c] and max_torque[c] (host) receive the results.
+template <typename T>
+int vp_batch_run(MinScratch **s, const std::vector<Stencil<T>> &stencils, const std::vector<long long> &spin0,
+                 void *spins, void *vel, const MinArgs &a, int *iters, double *max_torque, cudaStream_t st);
+
 }  // namespace spgb

@@ -406,3 +406,34 @@ def test_topological_charge_matches_oracle(periodic):
         assert abs(q - qo) <= tol
     if periodic:
         assert abs(qo + 1) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_minimise_batch_matches_single_systems(prec):
+    # systems of different sizes and Hamiltonians relaxed together must each
+    # follow the single-system iteration exactly
+    systems = [
+        (I.hexagonal(12, 9, periodic=(True, True)), dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.1],
+                                                         Khat=[[0, 0, 1]], B=[0, 0, 1.0])),
+        (I.square(7, 5, periodic=(True, False)), dict(J=[1.0, 0.2], dmi_kind="interfacial", D=[0.2], B=[0, 0, 2.0])),
+        (I.simple_cubic(4, 3, 3), dict(J=[1.0], K=[0.3], Khat=[[1, 0, 0]], B=[0.1, 0, 0.5])),
+    ]
+    ctxs, single, offs = [], [], []
+    off = 0
+    for k, (g, h) in enumerate(systems):
+        c = B.Context(g, h, prec)
+        n0 = I.random_spins(c.N, 40 + k)
+        n, v = c.spins(n0), c.spins(np.zeros_like(n0))
+        it, mt = c.minimise(n, v, dt=0.1, tol=1e-7, max_iter=3000, check_every=50)
+        ctxs.append(c)
+        single.append((n0, n, v, it, mt))
+        offs.append(off)
+        off += c.N
+    flat = torch.cat([c.spins(s[0]) for c, s in zip(ctxs, single)])
+    vel = torch.zeros_like(flat)
+    its, mts = B.minimise_batch(ctxs, flat, vel, offs, dt=0.1, tol=1e-7, max_iter=3000, check_every=50)
+    for k, (n0, n, v, it, mt) in enumerate(single):
+        N = ctxs[k].N
+        assert its[k] == it and mts[k] == mt
+        assert torch.equal(flat[offs[k]:offs[k] + N], n)
+        assert torch.equal(vel[offs[k]:offs[k] + N], v)
