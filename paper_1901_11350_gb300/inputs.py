@@ -199,3 +199,58 @@ def gneb_draw(seed, index, attempt=0, sizes=(64, 96, 128), images=(12, 40)):
 def gneb_batch(n_chains=48, seed=4, sizes=(64, 96, 128), images=(12, 40)):
     """First draws of the batched GNEB workload (see gneb_draw)."""
     return [gneb_draw(seed, c, 0, sizes, images) for c in range(n_chains)]
+
+
+# ---------------------------------------------------------------- warm start
+WARMSTART_SEEDS = dict(train=5, heldout=6)
+
+
+def warmstart_draw(seed, index, L=128):
+    """System `index` of the learned warm-start workload: an L x L periodic
+    hexagonal monolayer, mu_s=2, J=1 meV, interfacial D~U[0.1,0.5] meV,
+    K~U[0,0.2] meV along z, B~U[0,3] T along z, spins uniform on the sphere.
+    Each system has its own generator (seed, index), so any subset can be
+    drawn without the others."""
+    rng = np.random.default_rng([seed, index])
+    D = float(rng.uniform(0.1, 0.5))
+    K = float(rng.uniform(0.0, 0.2))
+    B = float(rng.uniform(0.0, 3.0))
+    spin_seed = int(rng.integers(0, 2**62))
+    g = hexagonal(L, L, periodic=(True, True), mu_s=2.0)
+    h = dict(B=[0, 0, B], K=[K], Khat=[[0, 0, 1]], J=[1.0], dmi_kind="interfacial", D=[D])
+    return dict(index=index, seed=seed, L=L, J=1.0, D=D, K=K, B=B, geometry=g, hamiltonian=h,
+                spins=random_spins(L * L, spin_seed))
+
+
+def warmstart_features(draw):
+    """The 4 per-system scalars the warm-start network sees: J, D/0.5, K/0.2
+    and B/3 (the workload's parameter ranges scaled to about [0, 1])."""
+    return np.array([draw["J"], draw["D"] / 0.5, draw["K"] / 0.2, draw["B"] / 3.0], dtype=np.float32)
+
+
+# (cin, cout) of the network's 14 convolutions, in parameter order: encoder
+# 32-32, 32-64, 64-128, 128-256 (two each), decoder 384-128, 128-128,
+# 192-64, 64-64, 96-32, 32-32; then the 32 -> 3 head.
+UNET_LAYERS = [(32, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (128, 256), (256, 256),
+               (384, 128), (128, 128), (192, 64), (64, 64), (96, 32), (32, 32)]
+UNET_REAL_INPUTS = 7  # n (3) + features (4); the other input channels are zero
+
+
+def unet_n_params(layers=UNET_LAYERS, head_in=32):
+    return sum(co * 9 * ci + co for ci, co in layers) + 3 * head_in + 3
+
+
+def unet_init(seed, layers=UNET_LAYERS, head_in=32, real_inputs=UNET_REAL_INPUTS):
+    """Initial flat parameters (float32): He-normal convolution weights
+    (std sqrt(2 / (9 * fan-in channels))), zero on the first layer's padding
+    channels, zero biases, head weights with std sqrt(1 / head_in)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (ci, co) in enumerate(layers):
+        fan = real_inputs if l == 0 else ci
+        W = rng.standard_normal((co, 9, ci)) * math.sqrt(2.0 / (9 * fan))
+        if l == 0:
+            W[:, :, real_inputs:] = 0.0
+        parts += [W.ravel(), np.zeros(co)]
+    parts += [rng.standard_normal(3 * head_in) * math.sqrt(1.0 / head_in), np.zeros(3)]
+    return np.concatenate(parts).astype(np.float32)

@@ -566,3 +566,132 @@ def test_rk4_is_fourth_order():
     e = [_larmor_error("rk4", dt, t_end=40.0)[0] for dt in (0.04, 0.02)]
     assert 14.0 < e[0] / e[1] < 18.0
     assert e[1] < 1e-10
+
+
+# ---------------------------------------------------------------- warm-start network
+from oracle import unet as U  # noqa: E402
+
+
+def _brute_conv(x, W, b):
+    B, H, Wd, Ci = x.shape
+    Co = W.shape[0]
+    out = np.zeros((B, H, Wd, Co))
+    for bb in range(B):
+        for y in range(H):
+            for xx in range(Wd):
+                for o in range(Co):
+                    s = b[o]
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            t = 3 * (dy + 1) + (dx + 1)
+                            for i in range(Ci):
+                                s += W[o, t, i] * x[bb, (y + dy) % H, (xx + dx) % Wd, i]
+                    out[bb, y, xx, o] = s
+    return out
+
+
+def test_unet_conv_matches_brute_force():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 3, 4, 2))
+    W = rng.standard_normal((3, 9, 2))
+    b = rng.standard_normal(3)
+    assert np.allclose(U.conv3x3(x, W, b), _brute_conv(x, W, b), rtol=0, atol=1e-12)
+
+
+def _fd_grad(f, arr, idx, h=1e-6):
+    old = arr[idx]
+    arr[idx] = old + h
+    fp = f()
+    arr[idx] = old - h
+    fm = f()
+    arr[idx] = old
+    return (fp - fm) / (2 * h)
+
+
+def test_unet_conv_backward_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 4, 4, 3))
+    W = rng.standard_normal((2, 9, 3))
+    b = rng.standard_normal(2)
+    R = rng.standard_normal((2, 4, 4, 2))
+    f = lambda: float(np.sum(R * U.conv3x3(x, W, b)))  # noqa: E731
+    dx, dW, db = U.conv3x3_backward(x, W, R)
+    for arr, g in ((x, dx), (W, dW), (b, db)):
+        for idx in np.ndindex(arr.shape):
+            assert abs(_fd_grad(f, arr, idx) - g[idx]) < 1e-7
+
+
+def test_unet_pool_upsample_backward_match_finite_differences():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((1, 4, 6, 2))
+    for fwd, bwd in ((U.pool, U.pool_backward), (U.upsample, U.upsample_backward)):
+        R = rng.standard_normal(fwd(x).shape)
+        f = lambda: float(np.sum(R * fwd(x)))  # noqa: E731
+        g = bwd(R)
+        for idx in np.ndindex(x.shape):
+            assert abs(_fd_grad(f, x, idx) - g[idx]) < 1e-8
+    # mean pooling of a constant is that constant; upsampling then pooling is the identity
+    assert np.allclose(U.pool(np.full((1, 4, 4, 1), 2.5)), 2.5)
+    assert np.allclose(U.pool(U.upsample(x)), x)
+
+
+def _small_net(seed, widths=(4, 4, 6, 8), in_ch=8, L=8, B=2):
+    rng = np.random.default_rng(seed)
+    arch = U.architecture(widths, in_ch)
+    flat = []
+    for _, ci, co, _ in arch:
+        flat += [rng.standard_normal(co * 9 * ci) * np.sqrt(2.0 / (9 * ci)), rng.standard_normal(co) * 0.1]
+    flat += [rng.standard_normal(3 * widths[0]), rng.standard_normal(3) * 0.1]
+    params = U.unpack(np.concatenate(flat), widths, in_ch)
+    spins = rng.standard_normal((B, L * L, 3))
+    spins /= np.linalg.norm(spins, axis=-1, keepdims=True)
+    feats = rng.uniform(0, 1, (B, 4))
+    x = U.network_input(spins, feats, L, in_ch)
+    t = rng.standard_normal((B, L, L, 3))
+    t /= np.linalg.norm(t, axis=-1, keepdims=True)
+    return params, x, t
+
+
+def test_unet_network_gradient_matches_finite_differences():
+    params, x, t = _small_net(4)
+    loss, grads = U.loss_and_gradient(params, x, t)
+    _, _, y = U.forward(params, x)
+    assert abs(loss - U.loss_of(y, t)) < 1e-14
+    rng = np.random.default_rng(5)
+    f = lambda: U.loss_of(U.forward(params, x)[2], t)  # noqa: E731
+    for name in list(params):
+        for k in (0, 1):
+            arr, g = params[name][k], grads[name][k]
+            for _ in range(3):
+                idx = tuple(int(rng.integers(0, s)) for s in arr.shape)
+                fd = _fd_grad(f, arr, idx, h=1e-5)
+                assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(g[idx])) + 1e-9, (name, k, idx, fd, g[idx])
+
+
+def test_unet_loss_special_cases():
+    params, x, t = _small_net(6)
+    _, _, y = U.forward(params, x)
+    m = y / np.linalg.norm(y, axis=-1, keepdims=True)
+    assert abs(U.loss_of(y, m)) < 1e-14          # prediction equal to the target
+    assert abs(U.loss_of(y, -m) - 2.0) < 1e-14   # opposite target
+    assert abs(U.loss_of(3.7 * y, t) - U.loss_of(y, t)) < 1e-14  # only the direction counts
+
+
+def test_unet_adam_first_step_closed_form():
+    # from zero moments the bias-corrected first step is lr * g / (|g| + eps)
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p = np.array([1.0, 1.0, 1.0, 1.0])
+    p1, m1, v1 = U.adam_step(p, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+
+
+def test_unet_layout_matches_the_input_recipe():
+    from paper_1901_11350_gb300 import inputs as I
+    arch = U.architecture()
+    assert [(ci, co) for _, ci, co, _ in arch] == I.UNET_LAYERS
+    flat = I.unet_init(7)
+    assert flat.size == I.unet_n_params()
+    params = U.unpack(flat)
+    assert np.array_equal(U.pack(params), flat.astype(np.float64))
+    assert np.all(params["e1a"][0][:, :, I.UNET_REAL_INPUTS:] == 0)
