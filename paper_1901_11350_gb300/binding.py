@@ -80,6 +80,21 @@ SIGNATURES = {
     "sp_autotune": (_i, [_vp, _vp, C.POINTER(_i), _vp]),
     "sp_profile_enable": (_i, [_vp, _i]),
     "sp_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(C.c_longlong)]),
+    # warm-start network (spirit_gb_unet.h)
+    "sp_unet_n_params": (C.c_longlong, []),
+    "sp_unet_layer": (_i, [_i, C.POINTER(_i), C.POINTER(_i), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "sp_unet_create": (_i, [C.POINTER(_vp), _i, _i]),
+    "sp_unet_destroy": (None, [_vp]),
+    "sp_unet_last_error": (C.c_char_p, [_vp]),
+    "sp_unet_set_params": (_i, [_vp, _vp, C.c_longlong]),
+    "sp_unet_get_params": (_i, [_vp, _vp, C.c_longlong]),
+    "sp_unet_predict": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "sp_unet_loss_grad": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "sp_unet_adam": (_i, [_vp, _d, _d, _d, _d, _i, _vp]),
+    "sp_conv3x3_forward": (_i, [_vp, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _i, _i, _i, _vp, _vp]),
+    "sp_conv3x3_transpose": (_i, [_vp, _i, _i, _vp, _vp]),
+    "sp_conv3x3_wgrad_workspace": (C.c_longlong, [_i, _i, _i, _i, _i]),
+    "sp_conv3x3_wgrad": (_i, [_vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, C.c_longlong, _vp]),
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
 OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4}

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspirit_gb.so")
-SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "topo.cu", "static_step.cu", "dipole_fast.cu"]
+SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "topo.cu", "static_step.cu", "dipole_fast.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
@@ -25,7 +25,7 @@ EXTRA = os.environ.get("SPGB_NVCC_EXTRA", "").split()
 
 
 def _deps():
-    out = [os.path.join(INCLUDE, "spirit_gb.h")]
+    out = [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     return out
 

@@ -1,0 +1,1056 @@
+// unet.cu -- BF16 U-Net that warm-starts energy minimisation (the C ABI of
+// include/spirit_gb_unet.h): periodic 3x3 implicit-GEMM convolutions on the
+// tensor cores (forward, data gradient, weight gradient), the pointwise
+// kernels around them, the FP32 head with its loss, and Adam.
+//
+// Convolution as a GEMM: M = pixels, N = output channels, K = 9 taps x input
+// channels.  A CTA owns 128 pixels x BN channels; each K step stages one tap
+// x 32 input channels of the (virtual) input -- periodic wrap, nearest
+// upsampling and channel concatenation are resolved in the address
+// computation -- and the matching weight slice in shared memory with
+// cp.async, three stages deep, and feeds m16n8k16 BF16 MMAs with FP32
+// accumulators.  Shared-memory rows are 64 bytes with the 16-byte chunks
+// XOR-swizzled so ldmatrix reads are free of bank conflicts.
+#include <cuda_bf16.h>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spirit_gb.h"
+#include "spirit_gb_unet.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kBM = 128;     // pixels per convolution CTA
+constexpr int kBK = 32;      // input channels per K step
+constexpr int kStages = 3;   // cp.async pipeline depth
+constexpr int kThreads = 256;
+
+struct ConvSrc {
+    const bf16 *s0;
+    int C0, up0;
+    const bf16 *s1;
+    int C1;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm4t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Byte offset of 16-byte chunk c of row r in a tile of 64-byte rows, and in a
+// tile of 128-byte rows.  Eight consecutive rows at one logical chunk land on
+// eight distinct bank groups.
+__device__ __forceinline__ unsigned swz64(int r, int c) { return (unsigned)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4)); }
+__device__ __forceinline__ unsigned swz128(int r, int c) { return (unsigned)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Address of channels [c, c+8) of the virtual input at pixel (b, y, x).
+__device__ __forceinline__ const bf16 *src_at(const ConvSrc &S, int b, int y, int x, int H, int W, int c)
+{
+    if (c < S.C0) {
+        if (S.up0) return S.s0 + ((size_t)(b * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * S.C0 + c;
+        return S.s0 + ((size_t)(b * H + y) * W + x) * S.C0 + c;
+    }
+    return S.s1 + ((size_t)(b * H + y) * W + x) * S.C1 + (c - S.C0);
+}
+
+// ------------------------------------------------------------------ conv
+// out[p][co] = act(bias[co] + sum_{t,ci} Wk[co][t][ci] in[p + off(t)][ci]),
+// zeroed where mask[p][co] is not > 0.  Grid (P/128, Cout/BN), 256 threads as
+// 4 (pixels) x 2 (channels) warps of 32 x BN/2.
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv(ConvSrc S, const bf16 *__restrict__ Wk, const float *__restrict__ bias,
+                                                   int relu, const bf16 *__restrict__ mask, int H, int W, int Cout,
+                                                   bf16 *__restrict__ out)
+{
+    constexpr int A_BYTES = kBM * 64, STAGE = A_BYTES + BN * 64;
+    constexpr int WN = BN / 2, NT = WN / 8;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int Cin = S.C0 + S.C1, nkc = Cin / kBK, nk = 9 * nkc;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int HW = H * W;
+    const int ar = tid >> 2, ac = tid & 3;
+    int pb[2], py[2], px[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        int p = m0 + ar + 64 * j;
+        pb[j] = p / HW;
+        int q = p - pb[j] * HW;
+        py[j] = q / W;
+        px[j] = q - py[j] * W;
+    }
+    const unsigned sbase = smem_u32(smem);
+    auto load = [&](int k, int stage) {
+        int t = k / nkc, cc = (k - t * nkc) * kBK;
+        int dy = t / 3 - 1, dx = t % 3 - 1;
+        unsigned sa = sbase + stage * STAGE;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            cp16(sa + swz64(ar + 64 * j, ac),
+                 src_at(S, pb[j], wrap(py[j] + dy, H), wrap(px[j] + dx, W), H, W, cc + ac * 8));
+        unsigned sb = sa + A_BYTES;
+        for (int idx = tid; idx < BN * 4; idx += kThreads) {
+            int r = idx >> 2, c = idx & 3;
+            cp16(sb + swz64(r, c), Wk + (size_t)(n0 + r) * 9 * Cin + t * Cin + cc + c * 8);
+        }
+    };
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    const int lj = lane >> 3, lr = lane & 7;
+    for (int k = 0; k < nk; ++k) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        int kn = k + kStages - 1;
+        if (kn < nk) load(kn, kn % kStages);
+        cp_commit();
+        unsigned sa = sbase + (k % kStages) * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            unsigned a[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm4(sa + swz64(wm * 32 + mi * 16 + lr + (lj & 1) * 8, kk * 2 + (lj >> 1)), a[mi][0], a[mi][1],
+                      a[mi][2], a[mi][3]);
+#pragma unroll
+            for (int ni = 0; ni < NT; ni += 2) {
+                unsigned b0, b1, b2, b3;
+                ldsm4(sb + swz64(wn * WN + ni * 8 + lr + (lj >> 1) * 8, kk * 2 + (lj & 1)), b0, b1, b2, b3);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    mma16816(acc[mi][ni], a[mi], b0, b1);
+                    mma16816(acc[mi][ni + 1], a[mi], b2, b3);
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) {
+            int co = n0 + wn * WN + ni * 8 + 2 * t4;
+            float c0 = bias ? bias[co] : 0.f, c1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int p = m0 + wm * 32 + mi * 16 + g + h * 8;
+                float v0 = acc[mi][ni][2 * h] + c0, v1 = acc[mi][ni][2 * h + 1] + c1;
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                size_t o = (size_t)p * Cout + co;
+                if (mask) {
+                    __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
+                    if (!(__low2float(mk) > 0.f)) v0 = 0.f;
+                    if (!(__high2float(mk) > 0.f)) v1 = 0.f;
+                }
+                *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+}
+
+// ------------------------------------------------------------------ wgrad
+// part[z][co][t][ci] = sum over pixels p of split z of dz[p][co] in[p+off(t)][ci].
+// Grid (Cout/BMC, 9 * Cin/32, splits), 128 threads as 2 x 2 warps of
+// BMC/2 x 16; K steps of 32 pixels.  Both operands are stored pixel-major and
+// read with transposing ldmatrix.
+template <int BMC>
+__global__ void __launch_bounds__(128) k_wgrad(ConvSrc S, const bf16 *__restrict__ dz, int H, int W, int Cout, int P,
+                                               int pix_per_split, float *__restrict__ part)
+{
+    constexpr int A_BYTES = 32 * BMC * 2, STAGE = A_BYTES + 32 * 64;
+    constexpr int MT = BMC / 32;  // m16 tiles per warp
+    __shared__ __align__(128) unsigned char smem[kStages * STAGE];
+    const int Cin = S.C0 + S.C1, nkc = Cin / kBK;
+    const int co0 = blockIdx.x * BMC;
+    const int t = blockIdx.y / nkc, ci0 = (blockIdx.y - t * nkc) * kBK;
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const int p_begin = blockIdx.z * pix_per_split;
+    const int p_end = min(P, p_begin + pix_per_split);
+    const int nk = (p_end - p_begin) / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int HW = H * W;
+    const unsigned sbase = smem_u32(smem);
+    // B rows: thread tid loads chunk (tid & 3) of pixel row (tid >> 2)
+    const int br = tid >> 2, bc = tid & 3;
+    auto load = [&](int k, int stage) {
+        int pk = p_begin + k * 32;
+        unsigned sa = sbase + stage * STAGE;
+        for (int idx = tid; idx < 32 * (BMC / 8); idx += 128) {
+            int r = idx / (BMC / 8), c = idx % (BMC / 8);
+            unsigned off = BMC == 64 ? swz128(r, c) : swz64(r, c);
+            cp16(sa + off, dz + (size_t)(pk + r) * Cout + co0 + c * 8);
+        }
+        int p = pk + br;
+        int b = p / HW, q = p - b * HW, y = q / W, x = q - y * W;
+        cp16(sa + A_BYTES + swz64(br, bc), src_at(S, b, wrap(y + dy, H), wrap(x + dx, W), H, W, ci0 + bc * 8));
+    };
+    float acc[MT][2][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    const int lj = lane >> 3, lr = lane & 7;
+    for (int k = 0; k < nk; ++k) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        int kn = k + kStages - 1;
+        if (kn < nk) load(kn, kn % kStages);
+        cp_commit();
+        unsigned sa = sbase + (k % kStages) * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            unsigned a[MT][4];
+#pragma unroll
+            for (int mi = 0; mi < MT; ++mi) {
+                int row = kk * 16 + lr + (lj >> 1) * 8;
+                int ch = (wm * (BMC / 2) + mi * 16 + (lj & 1) * 8) >> 3;
+                unsigned off = BMC == 64 ? swz128(row, ch) : swz64(row, ch);
+                ldsm4t(sa + off, a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+            }
+            unsigned b0, b1, b2, b3;
+            {
+                int row = kk * 16 + lr + (lj & 1) * 8;
+                int ch = (wn * 16 + (lj >> 1) * 8) >> 3;
+                ldsm4t(sb + swz64(row, ch), b0, b1, b2, b3);
+            }
+#pragma unroll
+            for (int mi = 0; mi < MT; ++mi) {
+                mma16816(acc[mi][0], a[mi], b0, b1);
+                mma16816(acc[mi][1], a[mi], b2, b3);
+            }
+        }
+    }
+    cp_wait<0>();
+    const int g = lane >> 2, t4 = lane & 3;
+    float *pz = part + (size_t)blockIdx.z * Cout * 9 * Cin;
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) {
+            int ci = ci0 + wn * 16 + ni * 8 + 2 * t4;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int co = co0 + wm * (BMC / 2) + mi * 16 + g + h * 8;
+                *reinterpret_cast<float2 *>(pz + ((size_t)co * 9 + t) * Cin + ci) =
+                    make_float2(acc[mi][ni][2 * h], acc[mi][ni][2 * h + 1]);
+            }
+        }
+}
+
+// out[i] = sum_{z < nz} part[z * n + i], in order of z.
+__global__ void k_sum_parts(const float *__restrict__ part, int nz, long long n, float *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < nz; ++z) s += part[(size_t)z * n + i];
+        out[i] = s;
+    }
+}
+
+// part[blk][c] = sum over the block's pixels of dz[p][c]; C in {32,...,256}
+// dividing 256.
+__global__ void __launch_bounds__(256) k_colsum(const bf16 *__restrict__ dz, int P, int C, int pix_per_blk,
+                                                float *__restrict__ part)
+{
+    __shared__ float sh[256];
+    int c = threadIdx.x % C, r = threadIdx.x / C, R = 256 / C;
+    int p0 = blockIdx.x * pix_per_blk, p1 = min(P, p0 + pix_per_blk);
+    float s = 0.f;
+    for (int p = p0 + r; p < p1; p += R) s += __bfloat162float(dz[(size_t)p * C + c]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float a = 0.f;
+        for (int k = 0; k < R; ++k) a += sh[k * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = a;
+    }
+}
+
+// ------------------------------------------------------------------ pointwise
+// x[p][0..31] = (n_x, n_y, n_z, f0..f3, 0...), one thread per 8 channels.
+__global__ void k_build_input(const float4 *__restrict__ spins, const float *__restrict__ feat, int HW, long long P,
+                              bf16 *__restrict__ x)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P * 4) return;
+    long long p = i >> 2;
+    int part = (int)(i & 3);
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16(0.f);
+    if (part == 0) {
+        float4 n = spins[p];
+        const float *f = feat + (p / HW) * SP_UNET_FEATURES;
+        v[0] = __float2bfloat16(n.x);
+        v[1] = __float2bfloat16(n.y);
+        v[2] = __float2bfloat16(n.z);
+        v[3] = __float2bfloat16(f[0]);
+        v[4] = __float2bfloat16(f[1]);
+        v[5] = __float2bfloat16(f[2]);
+        v[6] = __float2bfloat16(f[3]);
+    }
+    *reinterpret_cast<uint4 *>(x + p * SP_UNET_IN_CH + part * 8) = *reinterpret_cast<uint4 *>(v);
+}
+
+// 2x2 mean pooling of a [B][H][W][C] tensor, one thread per 8 channels of an
+// output pixel.
+__global__ void k_pool(const bf16 *__restrict__ a, int B, int H, int W, int C, bf16 *__restrict__ out)
+{
+    int Ho = H / 2, Wo = W / 2, G = C / 8;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    int g = (int)(i % G);
+    long long q = i / G;
+    int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho), b = (int)(q / ((long long)Wo * Ho));
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        size_t src = ((size_t)(b * H + 2 * yo + (d >> 1)) * W + 2 * xo + (d & 1)) * C + g * 8;
+        uint4 u = *reinterpret_cast<const uint4 *>(a + src);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(e[k]);
+    }
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(0.25f * s[k]);
+    *reinterpret_cast<uint4 *>(out + (size_t)q * C + g * 8) = *reinterpret_cast<uint4 *>(o);
+}
+
+// Backward of a concatenation [up(coarse) C0 | skip C1] at H x W:
+// dcoarse[q][c] = (sum of the 2x2 fine gradients of channel c) where
+// coarse[q][c] > 0 (ReLU), else 0.  One thread per 8 channels of a coarse pixel.
+__global__ void k_cat_coarse(const bf16 *__restrict__ dcat, int C0, int C1, const bf16 *__restrict__ coarse, int B,
+                             int H, int W, bf16 *__restrict__ dcoarse)
+{
+    int Ho = H / 2, Wo = W / 2, G = C0 / 8, Ct = C0 + C1;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    int g = (int)(i % G);
+    long long q = i / G;
+    int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho), b = (int)(q / ((long long)Wo * Ho));
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        size_t src = ((size_t)(b * H + 2 * yo + (d >> 1)) * W + 2 * xo + (d & 1)) * Ct + g * 8;
+        uint4 u = *reinterpret_cast<const uint4 *>(dcat + src);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(e[k]);
+    }
+    uint4 um = *reinterpret_cast<const uint4 *>(coarse + (size_t)q * C0 + g * 8);
+    const bf16 *m = reinterpret_cast<const bf16 *>(&um);
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(__bfloat162float(m[k]) > 0.f ? s[k] : 0.f);
+    *reinterpret_cast<uint4 *>(dcoarse + (size_t)q * C0 + g * 8) = *reinterpret_cast<uint4 *>(o);
+}
+
+// dz[p][c] = (dcat[p][C0 + c] + dpool[p/2][c] / 4) where a[p][c] > 0, else 0:
+// the skip tensor a feeds both the concatenation and the 2x2 mean pool.
+__global__ void k_skip_grad(const bf16 *__restrict__ dcat, int C0, int C1, const bf16 *__restrict__ dpool,
+                            const bf16 *__restrict__ a, int B, int H, int W, bf16 *__restrict__ dz)
+{
+    int G = C1 / 8, Ct = C0 + C1;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W * G) return;
+    int g = (int)(i % G);
+    long long p = i / G;
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    uint4 u0 = *reinterpret_cast<const uint4 *>(dcat + (size_t)p * Ct + C0 + g * 8);
+    uint4 u1 = *reinterpret_cast<const uint4 *>(dpool + ((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * C1 + g * 8);
+    uint4 u2 = *reinterpret_cast<const uint4 *>(a + (size_t)p * C1 + g * 8);
+    const bf16 *e0 = reinterpret_cast<const bf16 *>(&u0), *e1 = reinterpret_cast<const bf16 *>(&u1),
+               *e2 = reinterpret_cast<const bf16 *>(&u2);
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float v = __bfloat162float(e0[k]) + 0.25f * __bfloat162float(e1[k]);
+        o[k] = __float2bfloat16(__bfloat162float(e2[k]) > 0.f ? v : 0.f);
+    }
+    *reinterpret_cast<uint4 *>(dz + (size_t)p * C1 + g * 8) = *reinterpret_cast<uint4 *>(o);
+}
+
+// ------------------------------------------------------------------ head
+constexpr int kHeadVals = 3 * 32 + 3 + 1;  // dWh, dbh, loss
+
+// Per pixel: y = Wh a + bh, m = y/|y|.  predict: out[p] = (m, 0).  train:
+// loss 1 - m.m_t, dy = -(m_t - (m.m_t) m) / (|y| P), dz[p][c] = (Wh^T dy)_c
+// where a[p][c] > 0, and per-block sums of dy a^T, dy and the loss.
+template <bool TRAIN>
+__global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ a, const float *__restrict__ Wh,
+                                              const float *__restrict__ target, long long P, float inv_P,
+                                              float4 *__restrict__ out, bf16 *__restrict__ dz, float *__restrict__ part)
+{
+    __shared__ float w[3 * 32 + 3];
+    __shared__ float red[8][kHeadVals];
+    for (int k = threadIdx.x; k < 3 * 32 + 3; k += blockDim.x) w[k] = Wh[k];
+    __syncthreads();
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float av[32];
+    float y[3] = {0.f, 0.f, 0.f};
+    bool live = p < P;
+    if (live) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint4 u = *reinterpret_cast<const uint4 *>(a + p * 32 + g * 8);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) av[g * 8 + k] = __bfloat162float(e[k]);
+        }
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            float s = w[96 + o];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) s = fmaf(w[o * 32 + c], av[c], s);
+            y[o] = s;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) av[c] = 0.f;
+    }
+    float ny = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+    float inv = ny > 0.f ? 1.f / ny : 0.f;
+    float m[3] = {y[0] * inv, y[1] * inv, y[2] * inv};
+    if (!TRAIN) {
+        if (live) out[p] = make_float4(m[0], m[1], m[2], 0.f);
+        return;
+    }
+    float dy[3] = {0.f, 0.f, 0.f}, loss = 0.f;
+    if (live) {
+        float4 tt = reinterpret_cast<const float4 *>(target)[p];
+        float mt[3] = {tt.x, tt.y, tt.z};
+        float c = m[0] * mt[0] + m[1] * mt[1] + m[2] * mt[2];
+        loss = 1.f - c;
+        float s = -inv * inv_P;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) dy[o] = s * (mt[o] - c * m[o]);
+        __align__(16) bf16 d[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            float v = w[k] * dy[0] + w[32 + k] * dy[1] + w[64 + k] * dy[2];
+            d[k] = __float2bfloat16(av[k] > 0.f ? v : 0.f);
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            *reinterpret_cast<uint4 *>(dz + p * 32 + g * 8) = reinterpret_cast<const uint4 *>(d)[g];
+    }
+    // block sums: value j of kHeadVals; warp shuffles, then 8 warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = 0; j < kHeadVals; ++j) {
+        float v;
+        if (j < 96) v = dy[j / 32] * av[j % 32];
+        else if (j < 99) v = dy[j - 96];
+        else v = loss;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][j] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kHeadVals; j += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) s += red[k][j];
+        part[(size_t)blockIdx.x * kHeadVals + j] = s;
+    }
+}
+
+// grad[0..98] = sum of the per-block head sums; *loss = their loss sum / P.
+__global__ void k_head_reduce(const float *__restrict__ part, int nblk, double inv_P, float *__restrict__ grad,
+                              double *__restrict__ loss)
+{
+    int j = threadIdx.x;
+    if (j >= kHeadVals) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * kHeadVals + j];
+    if (j < 99) grad[j] = (float)s;
+    else if (loss) *loss = s * inv_P;
+}
+
+// ------------------------------------------------------------------ weights
+struct LayerTab {
+    int n;
+    long long w_off[SP_UNET_LAYERS], bf_off[SP_UNET_LAYERS];
+    int cout[SP_UNET_LAYERS], cin[SP_UNET_LAYERS];
+};
+
+// Wk[co][t][ci] = bf16(W) and Wt[ci][8-t][co] = bf16(W) for every layer.
+__global__ void k_prep_weights(LayerTab L, const float *__restrict__ params, bf16 *__restrict__ wk, bf16 *__restrict__ wt)
+{
+    for (int l = 0; l < L.n; ++l) {
+        int Co = L.cout[l], Ci = L.cin[l];
+        long long n = (long long)Co * 9 * Ci;
+        const float *W = params + L.w_off[l];
+        bf16 *k = wk + L.bf_off[l], *tr = wt + L.bf_off[l];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+            int ci = (int)(i % Ci);
+            long long r = i / Ci;
+            int t = (int)(r % 9), co = (int)(r / 9);
+            bf16 v = __float2bfloat16(W[i]);
+            k[i] = v;
+            tr[((size_t)ci * 9 + (8 - t)) * Co + co] = v;
+        }
+    }
+}
+
+__global__ void k_transpose(const bf16 *__restrict__ W, int Co, int Ci, bf16 *__restrict__ Wt)
+{
+    long long n = (long long)Co * 9 * Ci;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int ci = (int)(i % Ci);
+        long long r = i / Ci;
+        int t = (int)(r % 9), co = (int)(r / 9);
+        Wt[((size_t)ci * 9 + (8 - t)) * Co + co] = W[i];
+    }
+}
+
+// Adam (Kingma & Ba): m, v moving averages of g and g^2, bias-corrected step.
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+// exact grid for one thread per item
+unsigned blocks(long long n, int threads = 256) { return (unsigned)((n + threads - 1) / threads); }
+
+// capped grid for grid-stride loops
+int grid_for(long long n, int threads = 256)
+{
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > 152LL * 64 ? 152LL * 64 : b));
+}
+
+bool conv_shape_ok(int C0, int C1, int up0, int B, int H, int W, int Cout)
+{
+    long long P = (long long)B * H * W;
+    if (B < 1 || H < 1 || W < 1 || P % kBM != 0) return false;
+    if (C0 < 32 || C0 % 32 || C1 < 0 || C1 % 32 || Cout < 32 || Cout % 32) return false;
+    if (up0 && (H % 2 || W % 2)) return false;
+    return P < (1LL << 31) - 256;
+}
+
+cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask, int B, int H,
+                        int Wd, int Cout, bf16 *out, cudaStream_t st)
+{
+    long long P = (long long)B * H * Wd;
+    int bn = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
+    dim3 grid((unsigned)(P / kBM), (unsigned)(Cout / bn));
+    size_t sm;
+    switch (bn) {
+    case 128:
+        sm = kStages * (kBM * 64 + 128 * 64);
+        k_conv<128><<<grid, kThreads, sm, st>>>(S, W, bias, relu, mask, H, Wd, Cout, out);
+        break;
+    case 64:
+        sm = kStages * (kBM * 64 + 64 * 64);
+        k_conv<64><<<grid, kThreads, sm, st>>>(S, W, bias, relu, mask, H, Wd, Cout, out);
+        break;
+    default:
+        sm = kStages * (kBM * 64 + 32 * 64);
+        k_conv<32><<<grid, kThreads, sm, st>>>(S, W, bias, relu, mask, H, Wd, Cout, out);
+    }
+    return cudaGetLastError();
+}
+
+struct WgradPlan {
+    int bmc, splits, pix_per_split, bias_blocks, bias_pix;
+    long long part_floats;  // partial weight sums
+    long long bias_floats;  // partial bias sums
+};
+
+WgradPlan wgrad_plan(long long P, int Cin, int Cout)
+{
+    WgradPlan w;
+    w.bmc = Cout % 64 == 0 ? 64 : 32;
+    long long base = (long long)(Cout / w.bmc) * 9 * (Cin / kBK);
+    long long chunks = P / 32;
+    long long s = (4LL * 152 + base - 1) / base;
+    if (s > chunks) s = chunks;
+    if (s < 1) s = 1;
+    long long per = (chunks + s - 1) / s;
+    w.pix_per_split = (int)(per * 32);
+    w.splits = (int)((chunks + per - 1) / per);
+    w.part_floats = (long long)w.splits * Cout * 9 * Cin;
+    w.bias_pix = 2048;
+    w.bias_blocks = (int)((P + w.bias_pix - 1) / w.bias_pix);
+    w.bias_floats = (long long)w.bias_blocks * Cout;
+    return w;
+}
+
+long long wgrad_ws_bytes(long long P, int Cin, int Cout)
+{
+    WgradPlan w = wgrad_plan(P, Cin, Cout);
+    return (w.part_floats + w.bias_floats) * (long long)sizeof(float);
+}
+
+cudaError_t wgrad_launch(const ConvSrc &S, const bf16 *dz, int B, int H, int Wd, int Cout, float *dW, float *db,
+                         float *ws, cudaStream_t st)
+{
+    long long P = (long long)B * H * Wd;
+    int Cin = S.C0 + S.C1;
+    WgradPlan w = wgrad_plan(P, Cin, Cout);
+    dim3 grid((unsigned)(Cout / w.bmc), (unsigned)(9 * (Cin / kBK)), (unsigned)w.splits);
+    if (w.bmc == 64)
+        k_wgrad<64><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
+    else
+        k_wgrad<32><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
+    long long n = (long long)Cout * 9 * Cin;
+    k_sum_parts<<<grid_for(n), 256, 0, st>>>(ws, w.splits, n, dW);
+    if (db) {
+        float *bp = ws + w.part_floats;
+        k_colsum<<<w.bias_blocks, 256, 0, st>>>(dz, (int)P, Cout, w.bias_pix, bp);
+        k_sum_parts<<<grid_for(Cout), 256, 0, st>>>(bp, w.bias_blocks, Cout, db);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ network
+struct LayerDef {
+    int cin0, up, cin1, cout, level;
+};
+// inputs: cin0 channels of the previous tensor (upsampled when up), cin1
+// skip channels; level 0..3 = L, L/2, L/4, L/8
+const LayerDef kLayers[SP_UNET_LAYERS] = {
+    {32, 0, 0, 32, 0},   {32, 0, 0, 32, 0},     {32, 0, 0, 64, 1},   {64, 0, 0, 64, 1},   {64, 0, 0, 128, 2},
+    {128, 0, 0, 128, 2}, {128, 0, 0, 256, 3},   {256, 0, 0, 256, 3}, {256, 1, 128, 128, 2}, {128, 0, 0, 128, 2},
+    {128, 1, 64, 64, 1}, {64, 0, 0, 64, 1},     {64, 1, 32, 32, 0},  {32, 0, 0, 32, 0}};
+
+struct Offsets {
+    long long w[SP_UNET_LAYERS + 1], b[SP_UNET_LAYERS + 1], total;
+};
+
+Offsets param_offsets()
+{
+    Offsets o;
+    long long k = 0;
+    for (int l = 0; l < SP_UNET_LAYERS; ++l) {
+        int cin = kLayers[l].cin0 + kLayers[l].cin1;
+        o.w[l] = k;
+        k += (long long)kLayers[l].cout * 9 * cin;
+        o.b[l] = k;
+        k += kLayers[l].cout;
+    }
+    o.w[SP_UNET_LAYERS] = k;
+    k += 3 * 32;
+    o.b[SP_UNET_LAYERS] = k;
+    k += 3;
+    o.total = k;
+    return o;
+}
+
+}  // namespace
+
+struct sp_unet {
+    int L = 0, bmax = 0;
+    std::string err;
+    Offsets off;
+    LayerTab tab;
+    long long n_bf = 0;  // BF16 weight elements
+    void *arena = nullptr;
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *wk = nullptr, *wt = nullptr;
+    bf16 *x = nullptr, *act[SP_UNET_LAYERS] = {}, *pool[3] = {}, *dz[SP_UNET_LAYERS] = {}, *dpool[3] = {};
+    bf16 *dcat[3] = {};  // level 0..2 concatenation gradients
+    float *ws = nullptr, *head_part = nullptr;
+    long long ws_floats = 0;
+    int head_blocks = 0;
+};
+
+namespace {
+
+int ufail(sp_unet *n, int code, const char *fmt, ...)
+{
+    if (n) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        n->err = buf;
+    }
+    return code;
+}
+
+int cfail(sp_unet *n, cudaError_t e, const char *what)
+{
+    return ufail(n, SP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+long long level_pixels(const sp_unet *n, int batch, int level)
+{
+    long long s = n->L >> level;
+    return (long long)batch * s * s;
+}
+
+ConvSrc layer_src(const sp_unet *n, int l)
+{
+    ConvSrc S{nullptr, kLayers[l].cin0, kLayers[l].up, nullptr, kLayers[l].cin1};
+    switch (l) {
+    case 0: S.s0 = n->x; break;
+    case 2: S.s0 = n->pool[0]; break;
+    case 4: S.s0 = n->pool[1]; break;
+    case 6: S.s0 = n->pool[2]; break;
+    case 8: S.s0 = n->act[7]; S.s1 = n->act[5]; break;
+    case 10: S.s0 = n->act[9]; S.s1 = n->act[3]; break;
+    case 12: S.s0 = n->act[11]; S.s1 = n->act[1]; break;
+    default: S.s0 = n->act[l - 1];
+    }
+    return S;
+}
+
+int check_batch(sp_unet *n, int batch)
+{
+    if (batch < 1 || batch > n->bmax) return ufail(n, SP_ERR_ARG, "batch %d outside 1..%d", batch, n->bmax);
+    if (level_pixels(n, batch, 3) % kBM) return ufail(n, SP_ERR_ARG, "batch * (L/8)^2 must be a multiple of 128");
+    return SP_OK;
+}
+
+cudaError_t forward(sp_unet *n, const float *spins, const float *feat, int batch, cudaStream_t st)
+{
+    int L = n->L;
+    long long P0 = level_pixels(n, batch, 0);
+    k_build_input<<<blocks(P0 * 4), 256, 0, st>>>((const float4 *)spins, feat, L * L, P0, n->x);
+    for (int l = 0; l < SP_UNET_LAYERS; ++l) {
+        int s = L >> kLayers[l].level;
+        cudaError_t e = conv_launch(layer_src(n, l), n->wk + n->tab.bf_off[l], n->params + n->off.b[l], 1, nullptr,
+                                    batch, s, s, kLayers[l].cout, n->act[l], st);
+        if (e != cudaSuccess) return e;
+        if (l == 1 || l == 3 || l == 5) {
+            int k = l / 2, C = kLayers[l].cout;
+            long long work = level_pixels(n, batch, k + 1) * (C / 8);
+            k_pool<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n->act[l], batch, s, s, C, n->pool[k]);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t backward(sp_unet *n, int batch, cudaStream_t st)
+{
+    int L = n->L;
+    for (int l = SP_UNET_LAYERS - 1; l >= 0; --l) {
+        const LayerDef &d = kLayers[l];
+        int s = L >> d.level;
+        ConvSrc S = layer_src(n, l);
+        cudaError_t e = wgrad_launch(S, n->dz[l], batch, s, s, d.cout, n->grad + n->off.w[l], n->grad + n->off.b[l],
+                                     n->ws, st);
+        if (e != cudaSuccess) return e;
+        if (l == 0) break;
+        int cin = d.cin0 + d.cin1;
+        ConvSrc G{n->dz[l], d.cout, 0, nullptr, 0};
+        const bf16 *wt = n->wt + n->tab.bf_off[l];
+        if (d.cin1) {  // concatenation input: dcat, then split it
+            int k = d.level;
+            e = conv_launch(G, wt, nullptr, 0, nullptr, batch, s, s, cin, n->dcat[k], st);
+            if (e != cudaSuccess) return e;
+            long long work = level_pixels(n, batch, k + 1) * (d.cin0 / 8);
+            k_cat_coarse<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n->dcat[k], d.cin0, d.cin1, S.s0, batch, s, s,
+                                                                        n->dz[l - 1]);
+        } else if (l == 2 || l == 4 || l == 6) {  // pooled input: gradient of the pool, then the skip tensor
+            int k = l / 2 - 1;
+            e = conv_launch(G, wt, nullptr, 0, nullptr, batch, s, s, cin, n->dpool[k], st);
+            if (e != cudaSuccess) return e;
+            int sf = L >> k, Cs = kLayers[l - 1].cout;
+            long long work = level_pixels(n, batch, k) * (Cs / 8);
+            // the decoder layer that reads skip tensor act[l-1]
+            int dec = 12 - 2 * k;
+            k_skip_grad<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n->dcat[k], kLayers[dec].cin0, Cs, n->dpool[k],
+                                                                       n->act[l - 1], batch, sf, sf, n->dz[l - 1]);
+        } else {  // plain input: mask with the input's ReLU
+            e = conv_launch(G, wt, nullptr, 0, n->act[l - 1], batch, s, s, cin, n->dz[l - 1], st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+long long sp_unet_n_params(void) { return param_offsets().total; }
+
+int sp_unet_layer(int layer, int *cout, int *cin, long long *w_offset, long long *b_offset)
+{
+    if (layer < 0 || layer > SP_UNET_LAYERS) return SP_ERR_ARG;
+    Offsets o = param_offsets();
+    if (layer == SP_UNET_LAYERS) {
+        if (cout) *cout = 3;
+        if (cin) *cin = 32;
+    } else {
+        if (cout) *cout = kLayers[layer].cout;
+        if (cin) *cin = kLayers[layer].cin0 + kLayers[layer].cin1;
+    }
+    if (w_offset) *w_offset = o.w[layer];
+    if (b_offset) *b_offset = o.b[layer];
+    return SP_OK;
+}
+
+const char *sp_unet_last_error(const sp_unet *net) { return net ? net->err.c_str() : "NULL network"; }
+
+void sp_unet_destroy(sp_unet *net)
+{
+    if (!net) return;
+    if (net->arena) cudaFree(net->arena);
+    delete net;
+}
+
+int sp_unet_create(sp_unet **out, int L, int batch_max)
+{
+    if (!out) return SP_ERR_ARG;
+    *out = nullptr;
+    if (L < 8 || L % 8 || L > 4096 || batch_max < 1) return SP_ERR_ARG;
+    sp_unet *n = new sp_unet;
+    n->L = L;
+    n->bmax = batch_max;
+    n->off = param_offsets();
+    n->tab.n = SP_UNET_LAYERS;
+    long long kb = 0;
+    for (int l = 0; l < SP_UNET_LAYERS; ++l) {
+        n->tab.cout[l] = kLayers[l].cout;
+        n->tab.cin[l] = kLayers[l].cin0 + kLayers[l].cin1;
+        n->tab.w_off[l] = n->off.w[l];
+        n->tab.bf_off[l] = kb;
+        kb += (long long)n->tab.cout[l] * 9 * n->tab.cin[l];
+    }
+    n->n_bf = kb;
+    // workspace: largest wgrad plan over the layers at batch_max
+    long long ws = 0;
+    for (int l = 0; l < SP_UNET_LAYERS; ++l) {
+        long long P = level_pixels(n, batch_max, kLayers[l].level);
+        long long b = wgrad_ws_bytes(P, n->tab.cin[l], kLayers[l].cout) / (long long)sizeof(float);
+        if (b > ws) ws = b;
+    }
+    n->ws_floats = ws;
+    long long P0 = level_pixels(n, batch_max, 0);
+    n->head_blocks = (int)((P0 + 255) / 256);
+    // carve one allocation, 256-byte aligned pieces
+    std::vector<std::pair<void **, size_t>> pieces;
+    auto add = [&](void **p, size_t bytes) { pieces.push_back({p, bytes}); };
+    size_t np = (size_t)n->off.total;
+    add((void **)&n->params, np * 4);
+    add((void **)&n->grad, np * 4);
+    add((void **)&n->m, np * 4);
+    add((void **)&n->v, np * 4);
+    add((void **)&n->wk, (size_t)kb * 2);
+    add((void **)&n->wt, (size_t)kb * 2);
+    add((void **)&n->x, (size_t)P0 * SP_UNET_IN_CH * 2);
+    for (int l = 0; l < SP_UNET_LAYERS; ++l) {
+        size_t b = (size_t)level_pixels(n, batch_max, kLayers[l].level) * kLayers[l].cout * 2;
+        add((void **)&n->act[l], b);
+        add((void **)&n->dz[l], b);
+    }
+    for (int k = 0; k < 3; ++k) {
+        int C = kLayers[2 * k + 1].cout;
+        size_t b = (size_t)level_pixels(n, batch_max, k + 1) * C * 2;
+        add((void **)&n->pool[k], b);
+        add((void **)&n->dpool[k], b);
+        int dec = 12 - 2 * k;
+        add((void **)&n->dcat[k], (size_t)level_pixels(n, batch_max, k) * (kLayers[dec].cin0 + kLayers[dec].cin1) * 2);
+    }
+    add((void **)&n->ws, (size_t)ws * 4);
+    add((void **)&n->head_part, (size_t)n->head_blocks * kHeadVals * 4);
+    size_t total = 0;
+    for (auto &pc : pieces) total += (pc.second + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&n->arena, total);
+    if (e != cudaSuccess) {
+        delete n;
+        return SP_ERR_CUDA;
+    }
+    size_t o = 0;
+    for (auto &pc : pieces) {
+        *pc.first = (char *)n->arena + o;
+        o += (pc.second + 255) / 256 * 256;
+    }
+    e = cudaMemset(n->arena, 0, total);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        sp_unet_destroy(n);
+        return SP_ERR_CUDA;
+    }
+    *out = n;
+    return SP_OK;
+}
+
+int sp_unet_set_params(sp_unet *net, const float *host, long long n)
+{
+    if (!net) return SP_ERR_ARG;
+    if (!host || n != net->off.total) return ufail(net, SP_ERR_ARG, "expected %lld parameters", net->off.total);
+    size_t b = (size_t)n * 4;
+    cudaError_t e = cudaMemcpy(net->params, host, b, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(net->m, 0, b);
+    if (e == cudaSuccess) e = cudaMemset(net->v, 0, b);
+    if (e != cudaSuccess) return cfail(net, e, "set_params");
+    k_prep_weights<<<grid_for(net->n_bf), 256>>>(net->tab, net->params, net->wk, net->wt);
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : cfail(net, e, "prepare weights");
+}
+
+int sp_unet_get_params(sp_unet *net, float *host, long long n)
+{
+    if (!net) return SP_ERR_ARG;
+    if (!host || n != net->off.total) return ufail(net, SP_ERR_ARG, "expected %lld parameters", net->off.total);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, net->params, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SP_OK : cfail(net, e, "get_params");
+}
+
+int sp_unet_predict(sp_unet *net, const float *spins_dev, const float *features_dev, int batch, float *out_dev,
+                    void *stream)
+{
+    if (!net) return SP_ERR_ARG;
+    if (!spins_dev || !features_dev || !out_dev) return ufail(net, SP_ERR_ARG, "NULL device pointer");
+    int rc = check_batch(net, batch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = forward(net, spins_dev, features_dev, batch, st);
+    if (e != cudaSuccess) return cfail(net, e, "forward");
+    long long P = level_pixels(net, batch, 0);
+    k_head<false><<<(unsigned)((P + 255) / 256), 256, 0, st>>>(net->act[SP_UNET_LAYERS - 1], net->params + net->off.w[SP_UNET_LAYERS],
+                                                               nullptr, P, 0.f, (float4 *)out_dev, nullptr, nullptr);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : cfail(net, e, "head");
+}
+
+int sp_unet_loss_grad(sp_unet *net, const float *spins_dev, const float *features_dev, const float *target_dev,
+                      int batch, double *loss_dev, float *grad_dev, void *stream)
+{
+    if (!net) return SP_ERR_ARG;
+    if (!spins_dev || !features_dev || !target_dev || !loss_dev) return ufail(net, SP_ERR_ARG, "NULL device pointer");
+    int rc = check_batch(net, batch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = forward(net, spins_dev, features_dev, batch, st);
+    if (e != cudaSuccess) return cfail(net, e, "forward");
+    long long P = level_pixels(net, batch, 0);
+    int nb = (int)((P + 255) / 256);
+    k_head<true><<<nb, 256, 0, st>>>(net->act[SP_UNET_LAYERS - 1], net->params + net->off.w[SP_UNET_LAYERS], target_dev,
+                                     P, (float)(1.0 / (double)P), nullptr, net->dz[SP_UNET_LAYERS - 1], net->head_part);
+    k_head_reduce<<<1, 128, 0, st>>>(net->head_part, nb, 1.0 / (double)P, net->grad + net->off.w[SP_UNET_LAYERS],
+                                     loss_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cfail(net, e, "head");
+    e = backward(net, batch, st);
+    if (e != cudaSuccess) return cfail(net, e, "backward");
+    if (grad_dev) {
+        e = cudaMemcpyAsync(grad_dev, net->grad, (size_t)net->off.total * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cfail(net, e, "copy gradient");
+    }
+    return SP_OK;
+}
+
+int sp_unet_adam(sp_unet *net, double lr, double beta1, double beta2, double eps, int step, void *stream)
+{
+    if (!net) return SP_ERR_ARG;
+    if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0) || step < 1)
+        return ufail(net, SP_ERR_ARG, "bad Adam parameters");
+    cudaStream_t st = (cudaStream_t)stream;
+    double c1 = 1.0 / (1.0 - pow(beta1, step)), c2 = 1.0 / (1.0 - pow(beta2, step));
+    k_adam<<<grid_for(net->off.total), 256, 0, st>>>(net->params, net->grad, net->m, net->v, net->off.total, (float)lr,
+                                                      (float)beta1, (float)beta2, (float)eps, (float)c1, (float)c2);
+    k_prep_weights<<<grid_for(net->n_bf), 256, 0, st>>>(net->tab, net->params, net->wk, net->wt);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : cfail(net, e, "adam");
+}
+
+int sp_conv3x3_forward(const uint16_t *src0, int C0, int up0, const uint16_t *src1, int C1, const uint16_t *W,
+                       const float *bias, int relu, const uint16_t *mask, int B, int H, int Wd, int Cout,
+                       uint16_t *out, void *stream)
+{
+    if (!src0 || !W || !out || (C1 && !src1)) return SP_ERR_ARG;
+    if (!conv_shape_ok(C0, C1, up0, B, H, Wd, Cout)) return SP_ERR_ARG;
+    ConvSrc S{(const bf16 *)src0, C0, up0 ? 1 : 0, (const bf16 *)src1, C1};
+    cudaError_t e = conv_launch(S, (const bf16 *)W, bias, relu, (const bf16 *)mask, B, H, Wd, Cout, (bf16 *)out,
+                                (cudaStream_t)stream);
+    return e == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, void *stream)
+{
+    if (!W || !Wt || Cout < 1 || Cin < 1) return SP_ERR_ARG;
+    k_transpose<<<grid_for((long long)Cout * 9 * Cin), 256, 0, (cudaStream_t)stream>>>((const bf16 *)W, Cout, Cin,
+                                                                                        (bf16 *)Wt);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+long long sp_conv3x3_wgrad_workspace(int B, int H, int Wd, int Cin, int Cout)
+{
+    if (B < 1 || H < 1 || Wd < 1 || Cin < 32 || Cout < 32) return -1;
+    return wgrad_ws_bytes((long long)B * H * Wd, Cin, Cout);
+}
+
+int sp_conv3x3_wgrad(const uint16_t *src0, int C0, int up0, const uint16_t *src1, int C1, const uint16_t *dz, int B,
+                     int H, int Wd, int Cout, float *dW, float *db, void *workspace, long long workspace_bytes,
+                     void *stream)
+{
+    if (!src0 || !dz || !dW || !workspace || (C1 && !src1)) return SP_ERR_ARG;
+    if (!conv_shape_ok(C0, C1, up0, B, H, Wd, Cout)) return SP_ERR_ARG;
+    if (workspace_bytes < wgrad_ws_bytes((long long)B * H * Wd, C0 + C1, Cout)) return SP_ERR_ARG;
+    ConvSrc S{(const bf16 *)src0, C0, up0 ? 1 : 0, (const bf16 *)src1, C1};
+    cudaError_t e = wgrad_launch(S, (const bf16 *)dz, B, H, Wd, Cout, dW, db, (float *)workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -113,3 +113,26 @@ def test_stencil_limits_and_unsupported_requests(L):
     c = B.Context(I.simple_cubic(5), dict(J=[1.0, -0.2, 0.05], dmi_kind="bulk", D=[0.2]))
     assert c.N == 125
     c.close()
+
+
+def test_unet_layout_and_host_side_rejections():
+    import ctypes as C
+    from paper_1901_11350_gb300 import inputs as I
+    from paper_1901_11350_gb300 import unet as UN
+    L = UN.lib()
+    assert UN.n_params() == I.unet_n_params()
+    off = 0
+    for l, (ci, co) in enumerate(I.UNET_LAYERS):
+        assert UN.layer(l) == (co, ci, off, off + co * 9 * ci)
+        off += co * 9 * ci + co
+    assert UN.layer(14) == (3, 32, off, off + 96)
+    h = C.c_void_p()
+    assert L.sp_unet_create(C.byref(h), 12, 4) == -1     # L not a multiple of 8
+    assert L.sp_unet_create(C.byref(h), 128, 0) == -1    # empty batch
+    dummy = C.c_void_p(256)
+    # channel counts below 32 or not multiples of 32, pixel counts not multiples of 128, NULL inputs
+    assert L.sp_conv3x3_forward(dummy, 16, 0, None, 0, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
+    assert L.sp_conv3x3_forward(dummy, 32, 0, None, 0, dummy, None, 1, None, 1, 10, 10, 32, dummy, None) == -1
+    assert L.sp_conv3x3_forward(dummy, 32, 0, None, 32, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
+    assert L.sp_conv3x3_forward(None, 32, 0, None, 0, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
+    assert L.sp_conv3x3_wgrad(dummy, 32, 0, None, 0, dummy, 1, 16, 16, 32, dummy, None, dummy, 0, None) == -1
