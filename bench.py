@@ -415,6 +415,64 @@ def run_hex_dipole(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start (BF16 U-Net, 128x128 periodic hexagonal lattices):
+    device seconds until every held-out system has FP64 max torque < 1e-6 meV,
+    for the unaided FP64 minimiser and for network prediction + FP32 + FP64,
+    plus the network's own tensor-core throughput.  Needs trained parameters
+    (``python -m paper_1901_11350_gb300.warmstart --out <prefix>``)."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+    from paper_1901_11350_gb300 import unet as UN
+    from paper_1901_11350_gb300 import warmstart as W
+
+    torch.cuda.set_device(0)
+    build.build()
+    params = W.load_params(args.weights)
+    L, bm = 128, 64
+    net = UN.UNet(L, bm, params)
+    # network throughput: forward (predict) and training step on one batch
+    draws = [I.warmstart_draw(I.WARMSTART_SEEDS["heldout"], 100000 + i, L) for i in range(bm)]
+    s = W._records(np.stack([d["spins"] for d in draws]))
+    f = W._features(draws)
+    flops = W.unet_flops(L)
+    times = {}
+    for name, fn in (("predict", lambda: net.predict(s, f)), ("train_step", lambda: net.loss_grad(s, f, s))):
+        for _ in range(args.warmup):
+            fn()
+        with W._Timer() as t:
+            for _ in range(10):
+                fn()
+        times[name] = t.seconds / 10
+    net.set_params(params)  # loss_grad above changed no parameter, but keep the state clean
+    peaks, kind = measured_peaks()
+    tf_pred = bm * flops / times["predict"] / 1e12
+    tf_train = 3 * bm * flops / times["train_step"] / 1e12
+    rep = W.evaluate(net, I.WARMSTART_SEEDS["heldout"], args.systems, L, max_iter=args.eval_max_iter,
+                     polish_max_iter=5000, chunk=args.systems, per_system=args.per_system, log=lambda m: None)
+    warm, una = rep["warm"], rep["unaided"]
+    loop = rep["unaided_per_system_loop"]
+    out = {"metric": "device seconds to FP64 max torque < 1e-6 meV for all systems, warm start vs unaided FP64",
+           "value": warm["batched_seconds"], "unit": "s", "higher_is_better": False,
+           "dtype": "bf16 network, f32 then f64 minimiser", "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": "warmstart_hex128", "systems": args.systems, "lattice": [L, L],
+                      "max_iter": args.eval_max_iter, "params": os.path.basename(args.weights)},
+           "unaided_fp64": {"batched_seconds": una["batched_seconds"], "per_system_loop_seconds_est":
+                            loop["est_seconds_all"], "per_system_loop_sample": loop},
+           "arms": {k: rep[k] for k in ("unaided", "batched", "warm", "uniform")},
+           "speedup_vs_unaided_per_system_loop": loop["est_seconds_all"] / warm["batched_seconds"],
+           "network": {"flop_per_sample_forward": flops, "batch": bm,
+                       "predict_ms": 1e3 * times["predict"], "train_step_ms": 1e3 * times["train_step"],
+                       "roofline": {"bound": "tensor", "achieved": tf_pred, "peak": peaks["bf16_tflops"],
+                                    "unit": "TFLOP/s", "frac": tf_pred / peaks["bf16_tflops"], "traffic": None,
+                                    "peak_kind": kind + " bf16 burst"},
+                       "train_tflops": tf_train}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,7 +484,12 @@ def main():
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
     ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
-    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512"])
+    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart"])
+    ap.add_argument("--systems", type=int, default=200, help="warmstart: held-out systems")
+    ap.add_argument("--eval-max-iter", type=int, default=30000, help="warmstart: iteration cap per relaxation")
+    ap.add_argument("--per-system", type=int, default=4, help="warmstart: systems timed in the one-system loop")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1901_11350_gb300", "weights",
+                                                      "warmstart_hex128.npz"))
     ap.add_argument("--chains", type=int, default=48)
     ap.add_argument("--gneb-chunk", type=int, default=50)
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
@@ -439,6 +502,8 @@ def main():
         return run_gneb(args)
     if args.workload == "hex512":
         return run_hex_dipole(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_gpu(args)
 
 

@@ -106,16 +106,18 @@ int grow_counters(Buf &b, size_t n, cudaStream_t st)
     return cudaMemsetAsync(b.p, 0, b.bytes, st) == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
 
-template <int NV>
-__device__ __forceinline__ double combine(int k, unsigned maxmask, double a, double b)
+template <int NV, typename V>
+__device__ __forceinline__ V combine(int k, unsigned maxmask, V a, V b)
 {
-    return ((maxmask >> k) & 1u) ? fmax(a, b) : a + b;
+    return ((maxmask >> k) & 1u) ? (a > b ? a : b) : a + b;
 }
 
 // Deterministic per-image reduction of NV values (bit k of maxmask: max
 // instead of sum).  Every thread of every block of the image must call it.
-template <int NV>
-__device__ void image_reduce(double (&v)[NV], unsigned maxmask, double *__restrict__ part, int blk, int blk0, int bpi,
+// The warp-level step runs in the values' own type V; warp results, block
+// partials and the image total are FP64.
+template <int NV, typename V>
+__device__ void image_reduce(V (&v)[NV], unsigned maxmask, double *__restrict__ part, int blk, int blk0, int bpi,
                              unsigned *counter, double *out)
 {
     __shared__ double sh[kBlock / 32][NV];
@@ -126,12 +128,12 @@ __device__ void image_reduce(double (&v)[NV], unsigned maxmask, double *__restri
         for (int o = 16; o > 0; o >>= 1) v[k] = combine<NV>(k, maxmask, v[k], __shfl_down_sync(0xffffffffu, v[k], o));
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0)
-        for (int k = 0; k < NV; ++k) sh[w][k] = v[k];
+        for (int k = 0; k < NV; ++k) sh[w][k] = (double)v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 0; k < NV; ++k) {
             double a = sh[0][k];
-            for (int ww = 1; ww < kBlock / 32; ++ww) a = combine<NV>(k, maxmask, a, sh[ww][k]);
+            for (int ww = 1; ww < kBlock / 32; ++ww) a = combine<NV, double>(k, maxmask, a, sh[ww][k]);
             part[(size_t)blk * NV + k] = a;
         }
         __threadfence();
@@ -144,12 +146,14 @@ __device__ void image_reduce(double (&v)[NV], unsigned maxmask, double *__restri
     double acc[NV];
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
     for (int p = threadIdx.x; p < bpi; p += kBlock)
-        for (int k = 0; k < NV; ++k) acc[k] = combine<NV>(k, maxmask, acc[k], __ldcg(&part[(size_t)(blk0 + p) * NV + k]));
+        for (int k = 0; k < NV; ++k)
+            acc[k] = combine<NV, double>(k, maxmask, acc[k], __ldcg(&part[(size_t)(blk0 + p) * NV + k]));
     for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = acc[k];
     __syncthreads();
     for (int s = kBlock / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)
-            for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = combine<NV>(k, maxmask, red[threadIdx.x][k], red[threadIdx.x + s][k]);
+            for (int k = 0; k < NV; ++k)
+                red[threadIdx.x][k] = combine<NV, double>(k, maxmask, red[threadIdx.x][k], red[threadIdx.x + s][k]);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -160,7 +164,10 @@ __device__ void image_reduce(double (&v)[NV], unsigned maxmask, double *__restri
 
 // ============================================================ VP minimiser
 // state (ints): [0] iterations performed, [1] active flag
-// scal (doubles): v.F, F.F, max|F|, projection-valid flag
+// scal (doubles): v.F, F.F, max|F|^2, projection-valid flag
+// (max |F|^2 rather than max |F|: one square root per image instead of one
+// per spin; sqrt is monotonic and correctly rounded, so sqrt(max |F|^2) is
+// exactly max |F| in FP64)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ x,
                                                      rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, double dth_m,
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Ste
 {
     if (mode == 1 && state[1] == 0) return;
     int i = blockIdx.x * kBlock + threadIdx.x;
-    double r[3] = {0, 0, 0};
+    T r[3] = {0, 0, 0};
     if (i < S.N) {
         int b;
         v3<T> ni = ld(x, i);
@@ -178,11 +185,11 @@ __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Ste
         if (mode == 1) {
             v3<T> vi = axpy((T)dth_m, ldc(F, i) + Fn, ldc(v, i));
             st(v, i, vi);
-            r[0] = (double)dot(vi, Fn);
+            r[0] = dot(vi, Fn);
         }
         st(F, i, Fn);
-        r[1] = (double)dot(Fn, Fn);
-        r[2] = sqrt(r[1]);
+        r[1] = dot(Fn, Fn);
+        r[2] = r[1];
     }
     image_reduce<3>(r, 4u, part, blockIdx.x, 0, gridDim.x, cnt, scal);
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[3] = mode;
@@ -193,15 +200,21 @@ __global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict_
                                                     const rec_t<T> *__restrict__ F, double dt, double dt2_2m, double tol,
                                                     int k, int max_iter, const double *scal, int *state)
 {
-    double fmax_ = scal[2];
-    bool done = (fmax_ < tol) || (k >= max_iter);
+    __shared__ T s_c;
+    __shared__ int s_done;
+    if (threadIdx.x == 0) {
+        double vf = scal[0], ff = scal[1];
+        s_c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+        s_done = (sqrt(scal[2]) < tol) || (k >= max_iter);
+    }
+    __syncthreads();
+    bool done = s_done;
     bool proj = scal[3] != 0.0;
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i < N) {
         v3<T> vi;
         if (proj) {
-            double vf = scal[0], ff = scal[1];
-            T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+            T c = s_c;
             vi = c * ldc(F, i);
             st(v, i, vi);
         } else {
@@ -411,7 +424,7 @@ int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const Mi
         cudaStreamSynchronize(st) != cudaSuccess)
         return SP_ERR_CUDA;
     *iters = s->host_state[0];
-    *max_torque = *s->host_fmax;
+    *max_torque = sqrt(*s->host_fmax);
     return 0;
 }
 
@@ -432,7 +445,7 @@ __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict_
     const Stencil<T> &St = S[im.chain];
     int i = bi.t * kBlock + threadIdx.x;
     const rec_t<T> *xb = x + im.spin0;
-    double r[3] = {0, 0, 0};
+    T r[3] = {0, 0, 0};
     if (i < im.N) {
         int b;
         long long p = im.spin0 + i;
@@ -442,11 +455,11 @@ __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict_
         if (mode == 1) {
             v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
             st(v, p, vi);
-            r[0] = (double)dot(vi, Fn);
+            r[0] = dot(vi, Fn);
         }
         st(F, p, Fn);
-        r[1] = (double)dot(Fn, Fn);
-        r[2] = sqrt(r[1]);
+        r[1] = dot(Fn, Fn);
+        r[2] = r[1];
     }
     image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kVF);
     if (bi.t == 0 && threadIdx.x == 0) proj[bi.g] = mode;
@@ -462,14 +475,21 @@ __global__ void __launch_bounds__(kBlock) k_bvp_move(const BlkInfo *__restrict__
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
     const double *sc = scal + 8 * bi.g;
-    bool done = (sc[kFMAX] < tol) || (k >= max_iter);
+    __shared__ T s_c;
+    __shared__ int s_done;
+    if (threadIdx.x == 0) {
+        double vf = sc[kVF], ff = sc[kFF];
+        s_c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+        s_done = (sqrt(sc[kFMAX]) < tol) || (k >= max_iter);
+    }
+    __syncthreads();
+    bool done = s_done;
     int i = bi.t * kBlock + threadIdx.x;
     if (i < im.N) {
         long long p = im.spin0 + i;
         v3<T> vi;
         if (proj[bi.g]) {
-            double vf = sc[kVF], ff = sc[kFF];
-            T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+            T c = s_c;
             vi = c * ldc(F, p);
             st(v, p, vi);
         } else {
@@ -569,7 +589,7 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
         return SP_ERR_CUDA;
     for (int c = 0; c < C; ++c) {
         iters[c] = hs[2 * c];
-        max_torque[c] = hsc[8 * c + kFMAX];
+        max_torque[c] = sqrt(hsc[8 * c + kFMAX]);
     }
     return 0;
 }
