@@ -234,7 +234,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ctx.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -245,13 +244,23 @@ def run_gpu(args):
             ev[k][1].record(st)
             step += S
         torch.cuda.synchronize()
-    ctx.profile(False)
     el_ms = sum(a.elapsed_time(b) for a, b in ev)
+    el_ms = max_over_ranks(el_ms, "cuda")
+    # per-kernel durations: a separate pass with CUDA events around every
+    # launch (the events keep consecutive launches from overlapping, so they
+    # stay out of the timed region above)
+    prof_steps = min(args.steps, 2)
+    ctx.profile(True)
+    for k in range(prof_steps):
+        flush.fill_((k + 7) & 0xFF)
+        ctx.llg_step(n, S, step0=step, **kw)
+        step += S
+    torch.cuda.synchronize()
+    ctx.profile(False)
     kern = {}
     for name in ("llg_predictor", "llg_corrector"):
         ms, cnt = ctx.profile_read(name)
         kern[name] = (ms, cnt)
-    el_ms = max_over_ranks(el_ms, "cuda")
     if world > 1:
         dist.barrier()
     value = whole_job_rate(world, N * S * args.steps, el_ms)
@@ -281,7 +290,10 @@ def run_gpu(args):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(dom), "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": BYTES_PER_SPIN[dom] * N, "avg_launch_us": avg_s * 1e6,
-            "launches": cnt,
+            "launches": cnt, "kernel_timing": "CUDA events around each launch, %d profiled steps after the timed region"
+            % prof_steps,
+            "pair_frac_timed_region": sum(BYTES_PER_SPIN.values()) * N * S * args.steps / (el_ms / 1e3) / 1e9
+            / peaks["hbm_gbs"],
             "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kern.items()}}
     clocks = clk.summary()
     if world > 1:
@@ -378,7 +390,6 @@ def run_hex_dipole(args):
         flush.fill_(k)
         ctx.llg_step(n, 50, **kw)
     torch.cuda.synchronize()
-    ctx.profile(True)
     st = torch.cuda.current_stream()
     tot = 0.0
     for k in range(args.steps):
@@ -389,6 +400,10 @@ def run_hex_dipole(args):
         e1.record(st)
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
+    # per-kernel split from a separate profiled pass (events around launches)
+    ctx.profile(True)
+    ctx.llg_step(n, S, **kw)
+    torch.cuda.synchronize()
     ctx.profile(False)
     kern = {k: ctx.profile_read(k) for k in ("llg_predictor", "llg_corrector", "dipole")}
     dip_ms, dip_n = kern["dipole"]
@@ -411,6 +426,76 @@ def run_hex_dipole(args):
            "dipole": {"us_per_evaluation": 1e3 * dip_ms / max(dip_n, 1), "algorithmic_bytes": dip_bytes,
                       "achieved_GBs": dip_bytes / (dip_ms / max(dip_n, 1) / 1e3) / 1e9, "peak_GBs": peaks["hbm_gbs"]},
            "finite": bool(torch.isfinite(n).all().item())}
+    print(json.dumps(out))
+    return 0
+
+
+def run_unet(args):
+    """The warm-start network alone (BF16 U-Net, 128x128 inputs, batch 64):
+    training samples/s of a full step (forward, backward, Adam) and
+    prediction samples/s, on held-out draws; tensor-core roofline."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+    from paper_1901_11350_gb300 import unet as UN
+    from paper_1901_11350_gb300 import warmstart as W
+
+    torch.cuda.set_device(0)
+    build.build()
+    L, bm = 128, 64
+    net = UN.UNet(L, bm, I.unet_init(0))
+    draws = [I.warmstart_draw(I.WARMSTART_SEEDS["heldout"], 100000 + i, L) for i in range(bm)]
+    s = W._records(np.stack([d["spins"] for d in draws]))
+    f = W._features(draws)
+    t = torch.zeros_like(s)
+    t[..., 2] = 1.0
+    flops = W.unet_flops(L)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    res = {}
+    for name, fn, mult in (("train_step", lambda: net.train_step(s, f, t, 1e-4), 3), ("predict", lambda: net.predict(s, f), 1)):
+        for _ in range(args.warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(st)
+            fn()
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        res[name] = (ms, mult * bm * flops / (ms / 1e3) / 1e12)
+    UN.check_device_error()
+    # end to end: pinned host batch in, loss out, every step
+    hs, hf, ht = s.cpu().pin_memory(), f.cpu().pin_memory(), t.cpu().pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for k in range(args.steps):
+        loss = net.train_step(hs.to("cuda", non_blocking=True), hf.to("cuda", non_blocking=True),
+                              ht.to("cuda", non_blocking=True), 1e-4)
+        loss.item()
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    peaks, kind = measured_peaks()
+    ms, tf = res["train_step"]
+    out = {"metric": "U-Net training samples/s (BF16, 128x128, forward + backward + Adam)", "value": bm / (ms / 1e3),
+           "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": "unet_hex128_b64", "batch": bm, "lattice": [L, L],
+                      "widths": [32, 64, 128, 256], "conv_kernel": UN.conv_kernel(),
+                      "l2": "flushed (256 MB write) before each step"},
+           "e2e": {"value": bm / (e2e_ms / 1e3), "unit": "samples/s", "h2d_bytes_per_step": 2 * bm * L * L * 16 + bm * 16,
+                   "d2h_bytes_per_step": 8},
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                        "frac": tf / peaks["bf16_tflops"], "traffic": None,
+                        "peak_source": kind + " bf16 burst", "flop_per_sample_forward": flops,
+                        "note": "whole training step (all kernels) against the convolution FLOPs x 3"},
+           "predict": {"ms": res["predict"][0], "tflops": res["predict"][1],
+                       "frac": res["predict"][1] / peaks["bf16_tflops"], "samples_per_s": bm / (res["predict"][0] / 1e3)}}
     print(json.dumps(out))
     return 0
 
@@ -484,7 +569,7 @@ def main():
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
     ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
-    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart"])
+    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet"])
     ap.add_argument("--systems", type=int, default=200, help="warmstart: held-out systems")
     ap.add_argument("--eval-max-iter", type=int, default=30000, help="warmstart: iteration cap per relaxation")
     ap.add_argument("--per-system", type=int, default=4, help="warmstart: systems timed in the one-system loop")
@@ -504,6 +589,8 @@ def main():
         return run_hex_dipole(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "unet":
+        return run_unet(args)
     return run_gpu(args)
 
 

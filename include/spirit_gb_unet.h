@@ -115,6 +115,18 @@ int sp_conv3x3_forward(const uint16_t *src0, int C0, int up0, const uint16_t *sr
  * convolution of a layer with W [Cout][9][Cin]. */
 int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, void *stream);
 
+/* Which kernel computes the 3x3 convolutions (forward and data gradient) of
+ * this process: 1 (default) = tcgen05 MMAs with tensor-memory accumulators,
+ * 0 = the mma.sync kernel.  SP_ERR_ARG for other values.  Not thread-safe:
+ * set it before launching work. */
+int sp_conv3x3_set_kernel(int tcgen05);
+int sp_conv3x3_get_kernel(void);
+
+/* SP_ERR_TIMEOUT if, since the last call, a convolution CTA gave up a bounded
+ * wait on its tensor-core pipeline (its outputs were not written), else
+ * SP_OK.  Synchronises the device and clears the flag. */
+int sp_unet_device_error(void);
+
 /* Workspace bytes sp_conv3x3_wgrad needs for this shape. */
 long long sp_conv3x3_wgrad_workspace(int B, int H, int Wd, int Cin, int Cout);
 

@@ -194,6 +194,220 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc S, const bf16 *__rest
         }
 }
 
+// ------------------------------------------------------------------ conv, tcgen05
+// The same convolution on the 5th-generation tensor cores: one thread issues
+// 128 x BN x 16 MMAs (kind::f16, BF16 in, FP32 out) whose accumulator lives
+// in tensor memory; operands are the shared-memory stages above, read through
+// K-major SWIZZLE_64B descriptors (the 64-byte XOR layout of swz64 is that
+// swizzle).  Each stage is released by a tcgen05.commit on its own mbarrier.
+// Every wait is bounded: on a timeout the CTA records an error, stops
+// issuing work, waits (bounded) for the MMAs it issued, frees its tensor
+// memory and returns.
+constexpr int kTcStages = 4;
+
+__device__ int g_tc_error;  // set when a bounded wait ran out
+
+__device__ __forceinline__ uint64_t desc_sw64(unsigned addr)
+{
+    // start >> 4 | leading byte offset 16 B (unused for swizzled K-major) |
+    // stride byte offset 512 B (8 rows of 64 B) | descriptor version 1 |
+    // layout 4 = 64-byte swizzle
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Wait for completion of the phase with this parity, for at most ~2^32
+// cycles (about two seconds); false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 32)) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned idesc, unsigned acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int BN>
+constexpr size_t conv_tc_smem()
+{
+    return 1024 + (size_t)kTcStages * (kBM * 64 + BN * 64) + 8 * kTcStages + 16;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__restrict__ Wk,
+                                                      const float *__restrict__ bias, int relu,
+                                                      const bf16 *__restrict__ mask, int H, int W, int Cout,
+                                                      bf16 *__restrict__ out)
+{
+    constexpr int A_BYTES = kBM * 64, STAGE = A_BYTES + BN * 64;
+    constexpr unsigned TCOLS = BN;  // 32, 64 or 128: a power of two >= 32
+    constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
+                               ((unsigned)(kBM >> 4) << 24);
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = smem_u32(smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment here
+    const unsigned bar0 = base + kTcStages * STAGE;
+    const unsigned slot = bar0 + 8 * kTcStages;
+    volatile unsigned *slot_ptr = reinterpret_cast<volatile unsigned *>(smem_raw + (slot - raw));
+
+    const int Cin = S.C0 + S.C1, nkc = Cin / kBK, nk = 9 * nkc;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HW = H * W;
+    const int ar = tid >> 2, ac = tid & 3;
+    int pb[2], py[2], px[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        int p = m0 + ar + 64 * j;
+        pb[j] = p / HW;
+        int q = p - pb[j] * HW;
+        py[j] = q / W;
+        px[j] = q - py[j] * W;
+    }
+    auto load = [&](int k, int stage) {
+        int t = k / nkc, cc = (k - t * nkc) * kBK;
+        int dy = t / 3 - 1, dx = t % 3 - 1;
+        unsigned sa = base + stage * STAGE;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            cp16(sa + swz64(ar + 64 * j, ac),
+                 src_at(S, pb[j], wrap(py[j] + dy, H), wrap(px[j] + dx, W), H, W, cc + ac * 8));
+        unsigned sb = sa + A_BYTES;
+        for (int idx = tid; idx < BN * 4; idx += kThreads) {
+            int r = idx >> 2, c = idx & 3;
+            cp16(sb + swz64(r, c), Wk + (size_t)(n0 + r) * 9 * Cin + t * Cin + cc + c * 8);
+        }
+    };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot_ptr;
+
+#pragma unroll
+    for (int s = 0; s < kTcStages - 1; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    int failed = 0, issued = 0;
+    for (int k = 0; k < nk; ++k) {
+        const int s = k % kTcStages;
+        cp_wait<kTcStages - 2>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (__syncthreads_or(failed)) {
+            failed = 1;
+            break;
+        }
+        if (tid == 0) {
+            tc_fence_after();
+            const unsigned sa = base + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+                tc_mma(tmem, desc_sw64(sa + kk * 32), desc_sw64(sb + kk * 32), IDESC, (k > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(bar0 + 8 * s);
+        }
+        issued = k + 1;
+        const int kn = k + kTcStages - 1;
+        if (kn < nk) {
+            const int sn = kn % kTcStages;  // the stage the MMAs of iteration k-1 read
+            if (k >= 1 && !mbar_wait(bar0 + 8 * sn, ((k - 1) / kTcStages) & 1)) failed = 1;
+            if (!failed) load(kn, sn);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    // the last commit tracks every MMA issued before it
+    if (issued > 0 && !mbar_wait(bar0 + 8 * ((issued - 1) % kTcStages), ((issued - 1) / kTcStages) & 1)) failed = 1;
+    failed = __syncthreads_or(failed) || issued < nk;
+    tc_fence_after();
+    const int q = warp & 3, half = warp >> 2;
+    const int p = m0 + q * 32 + lane;
+#pragma unroll
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+        float v[16];
+        tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0, v);
+        if (failed) continue;
+        const int co = n0 + c0;
+        size_t o = (size_t)p * Cout + co;
+        __align__(16) bf16 mk[16];
+        if (mask) {
+            *reinterpret_cast<uint4 *>(mk) = *reinterpret_cast<const uint4 *>(mask + o);
+            *reinterpret_cast<uint4 *>(mk + 8) = *reinterpret_cast<const uint4 *>(mask + o + 8);
+        }
+        __align__(16) bf16 r[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            float x = v[e] + (bias ? bias[co + e] : 0.f);
+            if (relu) x = fmaxf(x, 0.f);
+            if (mask && !(__bfloat162float(mk[e]) > 0.f)) x = 0.f;
+            r[e] = __float2bfloat16(x);
+        }
+        *reinterpret_cast<uint4 *>(out + o) = *reinterpret_cast<const uint4 *>(r);
+        *reinterpret_cast<uint4 *>(out + o + 8) = *reinterpret_cast<const uint4 *>(r + 8);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+    if (failed && tid == 0) atomicExch(&g_tc_error, 1);
+}
+
 // ------------------------------------------------------------------ wgrad
 // part[z][co][t][ci] = sum over pixels p of split z of dz[p][co] in[p+off(t)][ci].
 // Grid (Cout/BMC, 9 * Cin/32, splits), 128 threads as 2 x 2 warps of
@@ -591,12 +805,36 @@ bool conv_shape_ok(int C0, int C1, int up0, int B, int H, int W, int Cout)
     return P < (1LL << 31) - 256;
 }
 
+int g_use_tc = 1;  // tcgen05 convolution (1, default) or the mma.sync one (0)
+
+template <int BN>
+cudaError_t conv_tc_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask,
+                           int H, int Wd, int Cout, bf16 *out, cudaStream_t st)
+{
+    static bool attr = false;  // per process; the attribute is per function
+    constexpr size_t sm = conv_tc_smem<BN>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_conv_tc<BN><<<grid, kThreads, sm, st>>>(S, W, bias, relu, mask, H, Wd, Cout, out);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask, int B, int H,
                         int Wd, int Cout, bf16 *out, cudaStream_t st)
 {
     long long P = (long long)B * H * Wd;
     int bn = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
     dim3 grid((unsigned)(P / kBM), (unsigned)(Cout / bn));
+    if (g_use_tc) {
+        switch (bn) {
+        case 128: return conv_tc_launch<128>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        case 64: return conv_tc_launch<64>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        default: return conv_tc_launch<32>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        }
+    }
     size_t sm;
     switch (bn) {
     case 128:
@@ -1033,6 +1271,24 @@ int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, voi
     k_transpose<<<grid_for((long long)Cout * 9 * Cin), 256, 0, (cudaStream_t)stream>>>((const bf16 *)W, Cout, Cin,
                                                                                         (bf16 *)Wt);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+int sp_conv3x3_set_kernel(int tcgen05)
+{
+    if (tcgen05 != 0 && tcgen05 != 1) return SP_ERR_ARG;
+    g_use_tc = tcgen05;
+    return SP_OK;
+}
+
+int sp_conv3x3_get_kernel(void) { return g_use_tc; }
+
+int sp_unet_device_error(void)
+{
+    int v = 0, zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof v) != cudaSuccess) return SP_ERR_CUDA;
+    if (v && cudaMemcpyToSymbol(g_tc_error, &zero, sizeof zero) != cudaSuccess) return SP_ERR_CUDA;
+    return v ? SP_ERR_TIMEOUT : SP_OK;
 }
 
 long long sp_conv3x3_wgrad_workspace(int B, int H, int Wd, int Cin, int Cout)

@@ -22,6 +22,24 @@ def _check_cuda(t, dtype, name):
         raise ValueError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
 
 
+def set_conv_kernel(name):
+    """'tcgen05' (tensor-memory accumulators) or 'mma' (mma.sync)."""
+    rc = lib().sp_conv3x3_set_kernel({"mma": 0, "tcgen05": 1}[name])
+    if rc:
+        raise SpinError(rc, "bad kernel name")
+
+
+def conv_kernel():
+    return {0: "mma", 1: "tcgen05"}[lib().sp_conv3x3_get_kernel()]
+
+
+def check_device_error():
+    """Raise if a convolution CTA gave up a bounded wait since the last check."""
+    rc = lib().sp_unet_device_error()
+    if rc:
+        raise SpinError(rc, "a tensor-core pipeline wait timed out (outputs not written)")
+
+
 def n_params():
     return int(lib().sp_unet_n_params())
 

@@ -40,6 +40,15 @@ def rand_bf(rng, shape, scale=1.0):
     return t, f64(t)
 
 
+@pytest.fixture(params=["mma", "tcgen05"])
+def kernel(request):
+    old = UN.conv_kernel()
+    UN.set_conv_kernel(request.param)
+    yield request.param
+    UN.check_device_error()
+    UN.set_conv_kernel(old)
+
+
 def virtual_input(x0, x1, up0):
     x = U.upsample(x0) if up0 else x0
     return x if x1 is None else np.concatenate([x, x1], axis=-1)
@@ -58,7 +67,7 @@ CONV_CASES = [
 
 @pytest.mark.parametrize("case", CONV_CASES)
 @pytest.mark.parametrize("relu", [False, True])
-def test_conv_forward(case, relu):
+def test_conv_forward(case, relu, kernel):
     B, H, W, C0, up0, C1, Cout = case
     rng = np.random.default_rng(hash(case) % 2**32)
     h0, w0 = (H // 2, W // 2) if up0 else (H, W)
@@ -79,7 +88,7 @@ def test_conv_forward(case, relu):
 
 
 @pytest.mark.parametrize("case", [(2, 16, 16, 96, 32), (2, 8, 8, 256, 256), (4, 16, 16, 32, 64)])
-def test_conv_data_gradient(case):
+def test_conv_data_gradient(case, kernel):
     # the data gradient is the forward kernel with transposed weights and the
     # input's ReLU mask
     B, H, W, Cin, Cout = case
@@ -159,7 +168,7 @@ def _oracle_view(flat, spins, feats, target, L):
     return params, x, t
 
 
-def test_network_loss_and_gradient_match_oracle():
+def test_network_loss_and_gradient_match_oracle(kernel):
     L, B = 32, 8
     flat, spins, feats, target = _net_case(L, B, target="+z")
     net = UN.UNet(L, B, flat)
@@ -179,7 +188,7 @@ def test_network_loss_and_gradient_match_oracle():
             assert rel < 3e-2, (name, k, rel)
 
 
-def test_network_predict_and_adam():
+def test_network_predict_and_adam(kernel):
     L, B = 32, 8
     flat, spins, feats, target = _net_case(L, B, seed=5)
     net = UN.UNet(L, B, flat)
