@@ -58,7 +58,25 @@ class _LLG(C.Structure):
 
 class _GNEB(C.Structure):
     _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("k_spring", C.c_double),
-                ("climbing", C.c_int)]
+                ("climbing", C.c_int), ("image_types", C.POINTER(C.c_int)), ("energy_weight", C.c_double)]
+
+
+IMAGE = {"normal": 0, "climbing": 1, "falling": 2}
+
+
+def segment_length(Ea, Eb, da, db, h, w):
+    """Energy-weighted length of a path segment (see spo.h)."""
+    return lib().spo_segment_length(float(Ea), float(Eb), float(da), float(db), float(h), float(w))
+
+
+def _gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight):
+    """The parameter block and the int array it points to (keep both alive)."""
+    types = None
+    if image_types is not None:
+        types = (C.c_int * len(image_types))(*[IMAGE[t] if isinstance(t, str) else int(t) for t in image_types])
+    p = _GNEB(float(dt), float(mass), float(k_spring), int(bool(climbing)),
+              C.cast(types, C.POINTER(C.c_int)) if types is not None else None, float(energy_weight))
+    return p, types
 
 
 _lib = None
@@ -90,6 +108,9 @@ def lib():
         L.spo_gneb.argtypes = [C.c_void_p, d, d, C.c_int, P(_GNEB), C.c_int, C.c_double, d, d,
                                P(C.c_int)]
         L.spo_gneb_forces.argtypes = [C.c_void_p, d, C.c_int, P(_GNEB), d, d, d, P(C.c_int)]
+        L.spo_gneb_path.argtypes = [C.c_void_p, d, C.c_int, C.c_int, d, d, d, d, d, d]
+        L.spo_segment_length.argtypes = [C.c_double] * 6
+        L.spo_segment_length.restype = C.c_double
         L.spo_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.spo_philox4x32_10.restype = None
         L.spo_thermal_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, d]
@@ -254,19 +275,20 @@ class System:
                                   int(max_iter), C.byref(it), C.byref(mt)), "minimise")
         return n, v, it.value, mt.value
 
-    def gneb_forces(self, chain, k_spring=1.0, climbing=True, dt=0.1, mass=1.0):
+    def gneb_forces(self, chain, k_spring=1.0, climbing=True, dt=0.1, mass=1.0, image_types=None, energy_weight=0.0):
         ch = np.ascontiguousarray(np.asarray(chain, dtype=np.float64)[..., :3]).copy()
         M = ch.shape[0]
         F = np.zeros_like(ch)
         E = np.zeros(M)
         l = np.zeros(max(M - 1, 1))
         ci = C.c_int()
-        p = _GNEB(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+        p, _keep = _gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight)
         _check(lib().spo_gneb_forces(self._h, _dp(ch), M, C.byref(p), _dp(F), _dp(E), _dp(l),
                                      C.byref(ci)), "gneb_forces")
         return F, E, l[:M - 1], ci.value
 
-    def gneb(self, chain, vel=None, n_iter=100, tol=0.0, k_spring=1.0, climbing=True, dt=0.1, mass=1.0):
+    def gneb(self, chain, vel=None, n_iter=100, tol=0.0, k_spring=1.0, climbing=True, dt=0.1, mass=1.0,
+             image_types=None, energy_weight=0.0):
         ch = np.ascontiguousarray(np.asarray(chain, dtype=np.float64)[..., :3]).copy()
         M = ch.shape[0]
         v = np.zeros_like(ch) if vel is None else np.ascontiguousarray(
@@ -274,10 +296,24 @@ class System:
         E = np.zeros(M)
         mf = C.c_double()
         it = C.c_int()
-        p = _GNEB(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+        p, _keep = _gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight)
         _check(lib().spo_gneb(self._h, _dp(ch), _dp(v), M, C.byref(p), int(n_iter), float(tol),
                               _dp(E), C.byref(mf), C.byref(it)), "gneb")
         return ch, v, E, mf.value, it.value
+
+    def gneb_path(self, chain, n_interp=10, charge=False):
+        """Per image (r, E, dE/dr[, Q]) and the cubic interpolation (r_i, E_i)."""
+        ch = np.ascontiguousarray(np.asarray(chain, dtype=np.float64)[..., :3]).copy()
+        M = ch.shape[0]
+        r, E, sl = np.zeros(M), np.zeros(M), np.zeros(M)
+        Q = np.zeros(M) if charge else None
+        ri, Ei = np.zeros((M - 1) * n_interp + 1), np.zeros((M - 1) * n_interp + 1)
+        _check(lib().spo_gneb_path(self._h, _dp(ch), M, int(n_interp), _dp(r), _dp(E), _dp(sl),
+                                   _dp(Q) if charge else None, _dp(ri), _dp(Ei)), "gneb_path")
+        out = dict(r=r, E=E, slope=sl, r_interp=ri, E_interp=Ei)
+        if charge:
+            out["Q"] = Q
+        return out
 
     def topological_charge(self, n):
         n = self._spins(n)

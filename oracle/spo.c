@@ -947,39 +947,67 @@ static double geodesic(long N, const double *x, const double *y)
     return sqrt(acc);
 }
 
-int spo_gneb_forces(const spo_system *s, const double *chain, int M, const spo_gneb_params *p,
-                    double *forces, double *energies, double *dist, int *ci_out)
+/* Cubic Hermite interpolant of E on [0, h] with values Ea, Eb and slopes da,
+ * db at the ends: value and derivative at s. */
+static void hermite(double Ea, double Eb, double da, double db, double h, double s, double *E, double *dE)
 {
-    if (!s || !s->have_ham || !chain || !forces || !p || M < 2) return SPO_ERR_STATE;
-    long N = s->N;
+    double t = s / h;
+    double h00 = 2 * t * t * t - 3 * t * t + 1, h10 = t * t * t - 2 * t * t + t;
+    double h01 = -2 * t * t * t + 3 * t * t, h11 = t * t * t - t * t;
+    *E = h00 * Ea + h10 * h * da + h01 * Eb + h11 * h * db;
+    double g00 = 6 * t * t - 6 * t, g10 = 3 * t * t - 4 * t + 1, g01 = -6 * t * t + 6 * t, g11 = 3 * t * t - 2 * t;
+    *dE = (g00 * Ea + g01 * Eb) / h + g10 * da + g11 * db;
+}
+
+/* Reading of the energy-weighted spring (Sec. GNEB: springs measured along
+ * the cubic interpolation of the path energy, with a weight between energy
+ * and reaction coordinate): the length of the segment of the curve
+ * ((1-w) r, w E(r)) over the geodesic distance h, E(r) the cubic Hermite
+ * interpolant; integrated by adaptive Simpson (Lyness' criterion |S2 - S1|
+ * <= 15 eps, Richardson-corrected) to eps = 1e-13 h.  w = 0 gives h. */
+typedef struct { double Ea, Eb, da, db, h, w; } seg_t;
+
+static double seg_integrand(const seg_t *g, double s)
+{
+    double E, dE;
+    hermite(g->Ea, g->Eb, g->da, g->db, g->h, s, &E, &dE);
+    return sqrt((1 - g->w) * (1 - g->w) + g->w * g->w * dE * dE);
+}
+
+static double simpson_step(const seg_t *g, double a, double b, double fa, double fm, double fb, double whole,
+                           double eps, int depth)
+{
+    double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = seg_integrand(g, lm), frm = seg_integrand(g, rm);
+    double left = (m - a) / 6 * (fa + 4 * flm + fm), right = (b - m) / 6 * (fm + 4 * frm + fb);
+    double d = left + right - whole;
+    if (depth <= 0 || fabs(d) <= 15 * eps) return left + right + d / 15;
+    return simpson_step(g, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+           simpson_step(g, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+double spo_segment_length(double Ea, double Eb, double da, double db, double h, double w)
+{
+    if (w == 0.0) return h;
+    if (!(h > 0)) return 0.0;
+    seg_t g = {Ea, Eb, da, db, h, w};
+    double fa = seg_integrand(&g, 0), fm = seg_integrand(&g, 0.5 * h), fb = seg_integrand(&g, h);
+    return simpson_step(&g, 0, h, fa, fm, fb, h / 6 * (fa + 4 * fm + fb), 1e-13 * h, 40);
+}
+
+/* Tangent of image v (improved tangent of Henkelman and Jonsson 2000 for
+ * interior images; the one-sided difference to the neighbour at the
+ * endpoints), projected per spin onto the tangent space of the image and
+ * normalised in 3N dimensions. */
+static void image_tangent(long N, const double *chain, int M, int v, const double *E, double *tau)
+{
     size_t img = 3 * (size_t)N;
-    double *E = energies ? energies : (double *)malloc(sizeof(double) * M);
-    double *l = (double *)malloc(sizeof(double) * (M - 1));
-    double *B = (double *)malloc(sizeof(double) * img * M);
-    double *tau = (double *)malloc(sizeof(double) * img);
-    if (!E || !l || !B || !tau) {
-        if (!energies) free(E);
-        free(l); free(B); free(tau);
-        return SPO_ERR_STATE;
-    }
-    int rc = SPO_OK;
-    for (int v = 0; v < M && !rc; ++v) {
-        double e[6];
-        rc = spo_energy(s, chain + v * img, e);
-        E[v] = e[0];
-        if (!rc) rc = spo_effective_field(s, chain + v * img, B + v * img, -1);
-    }
-    for (int v = 0; v + 1 < M; ++v) l[v] = geodesic(N, chain + v * img, chain + (v + 1) * img);
-    int ci = -1;
-    if (p->climbing && M > 2) {
-        ci = 1;
-        for (int v = 2; v < M - 1; ++v)
-            if (E[v] > E[ci]) ci = v;
-    }
-    memset(forces, 0, sizeof(double) * img * M);
-    for (int v = 1; v < M - 1 && !rc; ++v) {
-        const double *x = chain + v * img, *xp = chain + (v + 1) * img, *xm = chain + (v - 1) * img;
-        /* improved tangent (Henkelman and Jonsson 2000) */
+    const double *x = chain + v * img;
+    if (v == 0 || v == M - 1) {
+        const double *a = v == 0 ? x : chain + (v - 1) * img, *b = v == 0 ? chain + img : x;
+        for (long q = 0; q < 3 * N; ++q) tau[q] = b[q] - a[q];
+    } else {
+        const double *xp = chain + (v + 1) * img, *xm = chain + (v - 1) * img;
         double Ep = E[v + 1], E0 = E[v], Em = E[v - 1];
         double wp, wm;
         if (Ep > E0 && E0 > Em) { wp = 1; wm = 0; }
@@ -991,41 +1019,133 @@ int spo_gneb_forces(const spo_system *s, const double *chain, int M, const spo_g
             else { wp = dmin; wm = dmax; }
         }
         for (long q = 0; q < 3 * N; ++q) tau[q] = wp * (xp[q] - x[q]) + wm * (x[q] - xm[q]);
-        /* project onto the tangent space of the image (Eq. tangent projection),
-         * then normalise in 3N dimensions */
-        double tt = 0;
-        for (long i = 0; i < N; ++i) {
-            double tn = dot3(tau + 3 * i, x + 3 * i);
-            for (int k = 0; k < 3; ++k) tau[3 * i + k] -= tn * x[3 * i + k];
-            tt += dot3(tau + 3 * i, tau + 3 * i);
-        }
-        double tn = sqrt(tt);
-        if (tn > 0)
-            for (long q = 0; q < 3 * N; ++q) tau[q] /= tn;
-        /* projected gradient Pg, g = dH/dn = -B */
-        double *F = forces + v * img;
+    }
+    /* project onto the tangent space of the image, then normalise in 3N dimensions */
+    double tt = 0;
+    for (long i = 0; i < N; ++i) {
+        double tn = dot3(tau + 3 * i, x + 3 * i);
+        for (int k = 0; k < 3; ++k) tau[3 * i + k] -= tn * x[3 * i + k];
+        tt += dot3(tau + 3 * i, tau + 3 * i);
+    }
+    double tn = sqrt(tt);
+    if (tn > 0)
+        for (long q = 0; q < 3 * N; ++q) tau[q] /= tn;
+}
+
+/* Energies, fields, tangents, slopes dE/dr = Pg.tau and distances of a chain. */
+static int chain_state(const spo_system *s, const double *chain, int M, double *E, double *B, double *tau,
+                       double *slope, double *l)
+{
+    long N = s->N;
+    size_t img = 3 * (size_t)N;
+    int rc = SPO_OK;
+    for (int v = 0; v < M && !rc; ++v) {
+        double e[6];
+        rc = spo_energy(s, chain + v * img, e);
+        E[v] = e[0];
+        if (!rc) rc = spo_effective_field(s, chain + v * img, B + v * img, -1);
+    }
+    if (rc) return rc;
+    for (int v = 0; v + 1 < M; ++v) l[v] = geodesic(N, chain + v * img, chain + (v + 1) * img);
+    for (int v = 0; v < M; ++v) {
+        const double *x = chain + v * img;
+        double *t = tau + v * img;
+        image_tangent(N, chain, M, v, E, t);
         double gt = 0;
         for (long i = 0; i < N; ++i) {
             const double *b = B + v * img + 3 * i;
             double bn = dot3(b, x + 3 * i);
-            for (int k = 0; k < 3; ++k) {
-                double pg = -(b[k] - bn * x[3 * i + k]);
-                F[3 * i + k] = pg; /* temporarily Pg */
-                gt += pg * tau[3 * i + k];
-            }
+            for (int k = 0; k < 3; ++k) gt += -(b[k] - bn * x[3 * i + k]) * t[3 * i + k];
         }
-        /* Reading of Eq. Spring_Force: F^S = k (l_{v,v+1} - l_{v-1,v}) tau */
-        double fs = p->k_spring * (l[v] - l[v - 1]);
-        for (long q = 0; q < 3 * N; ++q) {
-            double pg = F[q];
-            if (v == ci) F[q] = -pg + 2.0 * gt * tau[q];
-            else F[q] = -pg + gt * tau[q] + fs * tau[q];
+        slope[v] = gt;
+    }
+    return SPO_OK;
+}
+
+int spo_gneb_forces(const spo_system *s, const double *chain, int M, const spo_gneb_params *p,
+                    double *forces, double *energies, double *dist, int *ci_out)
+{
+    if (!s || !s->have_ham || !chain || !forces || !p || M < 2) return SPO_ERR_STATE;
+    if (!(p->energy_weight >= 0 && p->energy_weight < 1)) return SPO_ERR_ARG;
+    long N = s->N;
+    size_t img = 3 * (size_t)N;
+    double *E = energies ? energies : (double *)malloc(sizeof(double) * M);
+    double *l = (double *)malloc(sizeof(double) * (M - 1));
+    double *L = (double *)malloc(sizeof(double) * (M - 1));
+    double *slope = (double *)malloc(sizeof(double) * M);
+    double *B = (double *)malloc(sizeof(double) * img * M);
+    double *tau = (double *)malloc(sizeof(double) * img * M);
+    if (!E || !l || !L || !slope || !B || !tau) {
+        if (!energies) free(E);
+        free(l); free(L); free(slope); free(B); free(tau);
+        return SPO_ERR_STATE;
+    }
+    int rc = chain_state(s, chain, M, E, B, tau, slope, l);
+    for (int v = 0; v + 1 < M && !rc; ++v)
+        L[v] = spo_segment_length(E[v], E[v + 1], slope[v], slope[v + 1], l[v], p->energy_weight);
+    /* image kinds: explicit, or the highest interior image climbs */
+    int ci = -1;
+    if (!p->image_types && p->climbing && M > 2) {
+        ci = 1;
+        for (int v = 2; v < M - 1; ++v)
+            if (E[v] > E[ci]) ci = v;
+    }
+    memset(forces, 0, sizeof(double) * img * M);
+    for (int v = 1; v < M - 1 && !rc; ++v) {
+        const double *x = chain + v * img, *t = tau + v * img;
+        int kind = p->image_types ? p->image_types[v] : (v == ci ? SPO_IMAGE_CLIMBING : SPO_IMAGE_NORMAL);
+        double *F = forces + v * img;
+        double gt = slope[v];
+        /* Reading of Eq. Spring_Force: F^S = k (L_{v,v+1} - L_{v-1,v}) tau */
+        double fs = p->k_spring * (L[v] - L[v - 1]);
+        for (long i = 0; i < N; ++i) {
+            const double *b = B + v * img + 3 * i;
+            double bn = dot3(b, x + 3 * i);
+            for (int k = 0; k < 3; ++k) {
+                long q = 3 * i + k;
+                double pg = -(b[k] - bn * x[q]);
+                if (kind == SPO_IMAGE_CLIMBING) F[q] = -pg + 2.0 * gt * t[q];
+                else if (kind == SPO_IMAGE_FALLING) F[q] = -pg; /* no spring, full gradient: falls to a minimum */
+                else F[q] = -pg + gt * t[q] + fs * t[q];
+            }
         }
     }
     if (dist) memcpy(dist, l, sizeof(double) * (M - 1));
     if (ci_out) *ci_out = ci;
     if (!energies) free(E);
-    free(l); free(B); free(tau);
+    free(l); free(L); free(slope); free(B); free(tau);
+    return rc;
+}
+
+int spo_gneb_path(const spo_system *s, const double *chain, int M, int n_interp, double *r, double *E, double *slope,
+                  double *Q, double *r_i, double *E_i)
+{
+    if (!s || !s->have_ham || !chain || M < 2 || n_interp < 1 || !r || !E || !slope) return SPO_ERR_ARG;
+    long N = s->N;
+    size_t img = 3 * (size_t)N;
+    double *B = (double *)malloc(sizeof(double) * img * M);
+    double *tau = (double *)malloc(sizeof(double) * img * M);
+    double *l = (double *)malloc(sizeof(double) * (M - 1));
+    if (!B || !tau || !l) { free(B); free(tau); free(l); return SPO_ERR_STATE; }
+    int rc = chain_state(s, chain, M, E, B, tau, slope, l);
+    if (!rc) {
+        r[0] = 0;
+        for (int v = 1; v < M; ++v) r[v] = r[v - 1] + l[v - 1];
+        if (r_i && E_i) {
+            for (int v = 0; v + 1 < M; ++v)
+                for (int q = 0; q < n_interp; ++q) {
+                    double sq = l[v] * q / n_interp, e, de;
+                    hermite(E[v], E[v + 1], slope[v], slope[v + 1], l[v], sq, &e, &de);
+                    r_i[v * n_interp + q] = r[v] + sq;
+                    E_i[v * n_interp + q] = e;
+                }
+            r_i[(M - 1) * n_interp] = r[M - 1];
+            E_i[(M - 1) * n_interp] = E[M - 1];
+        }
+        if (Q)
+            for (int v = 0; v < M && !rc; ++v) rc = spo_topological_charge(s, chain + v * img, &Q[v]);
+    }
+    free(B); free(tau); free(l);
     return rc;
 }
 

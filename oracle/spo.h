@@ -74,11 +74,15 @@ typedef struct {
     uint32_t replica;  /* replica index (Philox counter word 3 = 8*replica) */
 } spo_llg_params;
 
+enum { SPO_IMAGE_NORMAL = 0, SPO_IMAGE_CLIMBING = 1, SPO_IMAGE_FALLING = 2 };
+
 typedef struct {
     double dt;         /* fictitious time step */
     double mass;       /* fictitious mass m */
     double k_spring;   /* spring constant, meV/rad^2 */
-    int climbing;      /* 1: the highest interior image climbs */
+    int climbing;      /* 1: the highest interior image climbs (used when image_types is NULL) */
+    const int *image_types;  /* NULL, or one SPO_IMAGE_* per image (endpoints ignored) */
+    double energy_weight;    /* w in [0, 1): spring lengths measured along E(r) (0: geodesic) */
 } spo_gneb_params;
 
 typedef struct spo_system spo_system;
@@ -130,6 +134,19 @@ int spo_gneb(const spo_system *s, double *chain, double *vel, int n_images,
 int spo_gneb_forces(const spo_system *s, const double *chain, int n_images,
                     const spo_gneb_params *p, double *forces, double *energies,
                     double *dist, int *ci);
+
+/* Path analysis of a chain (Sec. GNEB): per image the energy E, reaction
+ * coordinate r (cumulative geodesic distance) and slope dE/dr along the
+ * tangent (one-sided at the endpoints); the cubic Hermite interpolation of
+ * E(r) at n_interp points per segment into r_i, E_i ((M-1)*n_interp + 1
+ * values).  Q (may be NULL) receives each image's topological charge. */
+int spo_gneb_path(const spo_system *s, const double *chain, int n_images, int n_interp, double *r, double *E,
+                  double *slope, double *Q, double *r_i, double *E_i);
+
+/* Energy-weighted length of one path segment: arc length of the curve
+ * ((1-w) r, w E(r)), r in [0, h], E the cubic Hermite interpolant with end
+ * values Ea, Eb and end slopes da, db (w = 0: h). */
+double spo_segment_length(double Ea, double Eb, double da, double db, double h, double w);
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */
 void spo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

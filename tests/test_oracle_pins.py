@@ -695,3 +695,134 @@ def test_unet_layout_matches_the_input_recipe():
     params = U.unpack(flat)
     assert np.array_equal(U.pack(params), flat.astype(np.float64))
     assert np.all(params["e1a"][0][:, :, I.UNET_REAL_INPUTS:] == 0)
+
+
+# ----------------------------------------------------------------------------
+# GNEB refinements (Sec. GNEB): falling image, energy-weighted springs,
+# path interpolation
+# ----------------------------------------------------------------------------
+WELL_SIGMA = 0.15
+THREE_WELLS = [[-1.0, WELL_SIGMA, 1.0, 0.0, 0.0], [-1.0, WELL_SIGMA, 0.0, 1.0, 0.0],
+               [-1.0, WELL_SIGMA, -1.0, 0.0, 0.0]]
+
+
+def _equator_chain(M, phi0=0.0, phi1=np.pi):
+    phi = np.linspace(phi0, phi1, M)
+    return np.stack([np.cos(phi), np.sin(phi), np.zeros(M)], axis=1)[:, None, :], phi
+
+
+def _three_well_system():
+    return oracle.System(I.square(1, 1, mu_s=1.0), dict(gauss=THREE_WELLS))
+
+
+def test_gneb_falling_image_reaches_the_minimum_fixed_by_symmetry():
+    # wells at x, y and -x: on the path x -> y -> -x the mirror symmetry
+    # x -> -x fixes the intermediate minimum at y exactly; the climbing
+    # images converge onto two first-order saddles that are mirror images.
+    s = _three_well_system()
+    # an asymmetric start: image 4 at 73 degrees, so every image has to move
+    phi = np.pi * (np.arange(9) / 8.0) ** 1.3
+    ch0 = np.stack([np.cos(phi), np.sin(phi), np.zeros(9)], axis=1)[:, None, :]
+    assert abs(phi[4] - np.pi / 2) > 0.25
+    a, _, _, ta = s.minimise(ch0[0], dt=0.05, tol=1e-13, max_iter=100000)
+    b, _, _, tb = s.minimise(ch0[-1], dt=0.05, tol=1e-13, max_iter=100000)
+    assert ta < 1e-13 and tb < 1e-13
+    ch0[0], ch0[-1] = a, b
+    types = ["normal", "normal", "climbing", "normal", "falling", "normal", "climbing", "normal", "normal"]
+    ch, v, E, mf, it = s.gneb(ch0, n_iter=300000, tol=1e-11, dt=0.02, k_spring=0.5, image_types=types)
+    assert mf < 1e-11
+    # the well is quartic at its centre (force ~ offset^3), so the position is
+    # fixed to about the cube root of the force tolerance and the energy to
+    # its fourth power
+    assert np.linalg.norm(ch[4, 0] - np.array([0.0, 1.0, 0.0])) < 1e-3
+    e_y = -1.0 - 2.0 * np.exp(-1.0 / (2 * WELL_SIGMA ** 2))
+    assert abs(E[4] - e_y) < 1e-12
+    # a minimum: the energy rises for every small tilt (the well is quartic at
+    # its centre, so its Hessian vanishes there)
+    for ang in np.linspace(0, 2 * np.pi, 12, endpoint=False):
+        d = np.array([np.cos(ang), 0.0, np.sin(ang)]) * 0.05
+        y = (ch[4, 0] + d) / np.linalg.norm(ch[4, 0] + d)
+        assert s.energy(y[None])[0] > E[4]
+    for k in (2, 6):
+        ev = np.linalg.eigvalsh(_tangent_hessian(s, ch[k, 0]))
+        assert ev[0] < 0 < ev[1]
+    mirror = ch[2, 0] * np.array([-1.0, 1.0, 1.0])
+    assert np.linalg.norm(mirror - ch[6, 0]) < 1e-8
+    assert abs(E[2] - E[6]) < 1e-12
+    assert E[2] > E[4] and E[6] > E[4]
+
+
+def test_gneb_path_slopes_and_coordinates_in_closed_form():
+    # a chain on the equator of the three-well landscape: the reaction
+    # coordinate is the azimuth, and dE/dr is the derivative of
+    # E(phi) = sum_k a exp(-(1 - cos(phi - phi_k))^2 / (2 s^2)).
+    s = _three_well_system()
+    ch, phi = _equator_chain(13, 0.1, 2.9)
+    P = s.gneb_path(ch, n_interp=8)
+    assert np.allclose(P["r"], phi - phi[0], rtol=0, atol=1e-13)
+    centres = [0.0, np.pi / 2, np.pi]
+    s2 = WELL_SIGMA ** 2
+    E = lambda p: sum(-np.exp(-(1 - np.cos(p - c)) ** 2 / (2 * s2)) for c in centres)  # noqa: E731
+    dE = lambda p: sum(-np.exp(-(1 - np.cos(p - c)) ** 2 / (2 * s2)) * (-(1 - np.cos(p - c)) * np.sin(p - c) / s2)
+                       for c in centres)  # noqa: E731
+    assert np.allclose(P["E"], E(phi), rtol=0, atol=1e-14)
+    assert np.allclose(P["slope"], dE(phi), rtol=0, atol=1e-12)
+
+
+def test_gneb_path_interpolation_is_the_cubic_hermite_spline():
+    from scipy.interpolate import CubicHermiteSpline
+    s = _three_well_system()
+    ch, _ = _equator_chain(7, 0.2, 2.6)
+    ch = ch + 0.05 * np.random.default_rng(2).standard_normal(ch.shape)  # off the great circle
+    ch /= np.linalg.norm(ch, axis=-1, keepdims=True)
+    P = s.gneb_path(ch, n_interp=5)
+    spl = CubicHermiteSpline(P["r"], P["E"], P["slope"])
+    assert np.allclose(P["E_interp"], spl(P["r_interp"]), rtol=0, atol=1e-13)
+    # the reaction coordinate is the running sum of geodesic angles
+    ang = [np.arctan2(np.linalg.norm(np.cross(ch[k, 0], ch[k + 1, 0])), np.dot(ch[k, 0], ch[k + 1, 0]))
+           for k in range(len(ch) - 1)]
+    assert np.allclose(P["r"][1:], np.cumsum(ang), rtol=0, atol=1e-14)
+
+
+def test_energy_weighted_segment_length_against_quadrature():
+    from scipy.integrate import quad
+    from scipy.interpolate import CubicHermiteSpline
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        h = rng.uniform(0.05, 2.0)
+        Ea, Eb = rng.uniform(-5, 5, 2)
+        da, db = rng.uniform(-30, 30, 2)
+        w = rng.uniform(0, 0.95)
+        d = CubicHermiteSpline([0, h], [Ea, Eb], [da, db]).derivative()
+        ref, _ = quad(lambda x: np.sqrt((1 - w) ** 2 + w ** 2 * d(x) ** 2), 0, h, epsabs=0, epsrel=1e-13, limit=500)
+        assert abs(oracle.segment_length(Ea, Eb, da, db, h, w) - ref) <= 1e-12 * ref
+    assert oracle.segment_length(1.0, 2.0, 3.0, 4.0, 0.7, 0.0) == 0.7  # w = 0: the geodesic distance
+    # a flat segment (no slope, equal energies) has length (1 - w) h
+    assert abs(oracle.segment_length(1.0, 1.0, 0.0, 0.0, 0.8, 0.4) - 0.6 * 0.8) < 1e-15
+
+
+def test_energy_weighted_springs_equalise_segment_lengths():
+    # with w > 0 and no climbing image, the converged chain has equal
+    # energy-weighted segment lengths, measured here by an independent
+    # quadrature of the spline through the chain's path data
+    from scipy.integrate import quad
+    from scipy.interpolate import CubicHermiteSpline
+    s = _three_well_system()
+    ch0, _ = _equator_chain(9, 0.0, np.pi / 2)
+    a, _, _, _ = s.minimise(ch0[0], dt=0.05, tol=1e-13, max_iter=100000)
+    b, _, _, _ = s.minimise(ch0[-1], dt=0.05, tol=1e-13, max_iter=100000)
+    ch0[0], ch0[-1] = a, b
+    w = 0.6
+    ch, v, E, mf, it = s.gneb(ch0, n_iter=400000, tol=1e-10, dt=0.02, k_spring=1.0, climbing=False, energy_weight=w)
+    assert mf < 1e-10
+    P = s.gneb_path(ch)
+    L = []
+    for k in range(len(ch) - 1):
+        h = P["r"][k + 1] - P["r"][k]
+        d = CubicHermiteSpline([0, h], [P["E"][k], P["E"][k + 1]], [P["slope"][k], P["slope"][k + 1]]).derivative()
+        L.append(quad(lambda x: np.sqrt((1 - w) ** 2 + w ** 2 * d(x) ** 2), 0, h, epsabs=0, epsrel=1e-12)[0])
+    L = np.array(L)
+    assert np.max(np.abs(L - L.mean())) < 1e-8
+    # and they differ from the geodesic spacing: images crowd where E changes
+    dr = np.diff(P["r"])
+    assert np.max(dr) / np.min(dr) > 1.2
