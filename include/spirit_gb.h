@@ -109,12 +109,22 @@ typedef struct {
     uint32_t replica;  /* replica index; selects an independent noise stream */
 } sp_llg_params;
 
+/* Kinds of GNEB images (Sec. GNEB): a climbing image converges onto a saddle
+ * point, a falling image onto a local minimum along the path. */
+enum { SP_IMAGE_NORMAL = 0, SP_IMAGE_CLIMBING = 1, SP_IMAGE_FALLING = 2 };
+
 /* GNEB parameters (Sec. GNEB, Appendix D, Appendix F). */
 typedef struct {
     double dt;         /* velocity-projection time step (> 0) */
     double mass;       /* fictitious mass (> 0) */
     double k_spring;   /* spring constant, meV/rad^2 */
-    int climbing;      /* 1: the highest-energy interior image climbs (re-chosen each iteration) */
+    int climbing;      /* 1: the highest-energy interior image climbs (re-chosen each
+                          iteration); used only when image_types is NULL */
+    const int *image_types; /* HOST, NULL or one SP_IMAGE_* per image (for a batch: all
+                               images of all chains in order); endpoints ignored */
+    double energy_weight;   /* w in [0, 1): 0 = springs on geodesic distances; w > 0 =
+                               springs on the arc length of ((1-w) r, w E(r)) along the
+                               cubic interpolation of the path energy (Sec. GNEB) */
 } sp_gneb_params;
 
 /* ------------------------------------------------------------------------
@@ -246,12 +256,30 @@ int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel
  * tangent space and normalised in 3N dimensions; geodesic distances
  * l = sqrt(sum_i theta_i^2); forces F = -Pg + (Pg.tau)tau +
  * k (l_{v,v+1} - l_{v-1,v}) tau, and for the climbing image
- * F = -Pg + 2 (Pg.tau) tau, Pg the tangent-space projection of dH/dn.
+ * F = -Pg + 2 (Pg.tau) tau, Pg the tangent-space projection of dH/dn; a
+ * falling image gets F = -Pg (no spring).  With energy_weight w > 0 the
+ * spring uses, instead of l, the arc length of the curve ((1-w) r, w E(r))
+ * over each segment, E(r) the cubic Hermite interpolant of the two images'
+ * energies and slopes dE/dr = Pg.tau (tangents at the endpoints: the
+ * one-sided difference to the neighbour), integrated by adaptive Simpson to
+ * 1e-13 l; SP_ERR_ARG for w outside [0, 1) or an unknown image type.
  * The force is re-evaluated at the start of each call (no hidden state).
  * Outputs (DEVICE): energies_dev[n_images] (meV, FP64), max_force_dev[1] =
  * max over interior images and spins of |F_v,i| after the last iteration. */
 int sp_gneb_step(sp_ctx *ctx, void *chain_dev, void *vel_dev, int n_images, const sp_gneb_params *p,
                  int n_iter, double *energies_dev, double *max_force_dev, void *stream);
+
+/* Path analysis of a chain of n_images >= 2 images (chain_dev as in
+ * sp_gneb_step): HOST outputs per image E[v] (meV, FP64 accumulation),
+ * reaction coordinate r[v] (cumulative geodesic distance, r[0] = 0) and slope
+ * dE/dr = Pg.tau along the image's tangent (improved tangent inside, one-sided
+ * at the endpoints); if r_interp and E_interp are not NULL, the cubic Hermite
+ * interpolation of E(r) at n_interp >= 1 equally spaced points per segment
+ * ((n_images-1) * n_interp + 1 values, ending at the last image); if Q is not
+ * NULL, each image's topological charge (Appendix A; 2D one-atom lattices,
+ * else SP_ERR_UNSUPPORTED).  Synchronises `stream`. */
+int sp_gneb_path(sp_ctx *ctx, const void *chain_dev, int n_images, int n_interp, double *r, double *E, double *slope,
+                 double *Q, double *r_interp, double *E_interp, void *stream);
 
 /* Batched GNEB: n_chains independent chains, each with its own context
  * (geometry and Hamiltonian; all contexts of one precision, no dipole term),

@@ -48,7 +48,21 @@ class LLGParams(C.Structure):
 
 
 class GNEBParams(C.Structure):
-    _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("k_spring", C.c_double), ("climbing", C.c_int)]
+    _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("k_spring", C.c_double), ("climbing", C.c_int),
+                ("image_types", C.POINTER(C.c_int)), ("energy_weight", C.c_double)]
+
+
+IMAGE_KINDS = {"normal": 0, "climbing": 1, "falling": 2}
+
+
+def gneb_params(dt, mass, k_spring, climbing, image_types=None, energy_weight=0.0):
+    """The parameter block and the int array it points to (keep both alive)."""
+    arr = None
+    if image_types is not None:
+        arr = (C.c_int * len(image_types))(*[IMAGE_KINDS[t] if isinstance(t, str) else int(t) for t in image_types])
+    p = GNEBParams(float(dt), float(mass), float(k_spring), int(bool(climbing)),
+                   C.cast(arr, C.POINTER(C.c_int)) if arr is not None else None, float(energy_weight))
+    return p, arr
 
 
 _lib = None
@@ -72,6 +86,7 @@ SIGNATURES = {
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
                                C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_gneb_path": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sp_minimise_batch": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), _d, _d, _d, _i, _i,
                               C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_llg_step_static": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
@@ -236,6 +251,20 @@ class Context:
         self._check(lib().sp_max_torque(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
         return out
 
+    def gneb_path(self, chain, n_interp=10, charge=False):
+        """Per image (r, E, dE/dr[, Q]) and the cubic interpolation (r_i, E_i), as numpy arrays."""
+        M = chain.shape[0]
+        r, E, sl = (np.zeros(M) for _ in range(3))
+        Q = np.zeros(M) if charge else None
+        ri, Ei = np.zeros((M - 1) * n_interp + 1), np.zeros((M - 1) * n_interp + 1)
+        dp = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None  # noqa: E731
+        self._check(lib().sp_gneb_path(self._h, self._spin_arg(chain, "chain", M), M, int(n_interp), dp(r), dp(E),
+                                       dp(sl), dp(Q), dp(ri), dp(Ei), _stream()))
+        out = dict(r=r, E=E, slope=sl, r_interp=ri, E_interp=Ei)
+        if charge:
+            out["Q"] = Q
+        return out
+
     def topological_charge(self, n, out=None):
         out = torch.empty(1, dtype=torch.float64, device=n.device) if out is None else out
         self._check(lib().sp_topological_charge(self._h, self._spin_arg(n, "n"), _ptr(out), _stream()))
@@ -278,18 +307,18 @@ class Context:
         return ms.value, n.value
 
     def gneb_step(self, chain, vel, n_iter=1, k_spring=1.0, climbing=True, dt=0.1, mass=1.0, energies=None,
-                  max_force=None):
+                  max_force=None, image_types=None, energy_weight=0.0):
         M = chain.shape[0]
         E = torch.empty(M, dtype=torch.float64, device=chain.device) if energies is None else energies
         F = torch.empty(1, dtype=torch.float64, device=chain.device) if max_force is None else max_force
-        p = GNEBParams(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+        p, _keep = gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight)
         self._check(lib().sp_gneb_step(self._h, self._spin_arg(chain, "chain", M), self._spin_arg(vel, "vel", M), M,
                                        C.byref(p), int(n_iter), _ptr(E), _ptr(F), _stream()))
         return E, F
 
 
 def gneb_batch_step(ctxs, chains, vel, offsets, n_images, n_iter=1, k_spring=1.0, climbing=True, dt=0.1, mass=1.0,
-                    energies=None, max_force=None):
+                    energies=None, max_force=None, image_types=None, energy_weight=0.0):
     """Step many chains (one context each) together; `chains` and `vel` are
     one flat CUDA tensor of 4-wide records each, chain c starting at record
     offsets[c].  Returns (energies, max_force) device tensors."""
@@ -304,7 +333,7 @@ def gneb_batch_step(ctxs, chains, vel, offsets, n_images, n_iter=1, k_spring=1.0
     handles = (C.c_void_p * n)(*[c._h for c in ctxs])
     offs = (C.c_longlong * n)(*[int(x) for x in offsets])
     ims = (C.c_int * n)(*[int(x) for x in n_images])
-    p = GNEBParams(float(dt), float(mass), float(k_spring), int(bool(climbing)))
+    p, _keep = gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight)
     rc = L.sp_gneb_batch_step(handles, n, _ptr(chains), _ptr(vel), offs, ims, C.byref(p), int(n_iter), _ptr(E),
                               _ptr(F), _stream())
     if rc:

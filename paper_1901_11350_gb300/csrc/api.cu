@@ -450,6 +450,7 @@ int sp_destroy(sp_ctx *c)
     if (c->pred.p) cudaFree(c->pred.p);
     if (c->partials.p) cudaFree(c->partials.p);
     if (c->bdd.p) cudaFree(c->bdd.p);
+    if (c->qbuf.p) cudaFree(c->qbuf.p);
     dipole_destroy(c->dip);
     min_scratch_destroy(c->mins);
     delete c;
@@ -663,11 +664,63 @@ int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const 
     if (!energies_dev || !max_force_dev) return fail(c, SP_ERR_ARG, "NULL output");
     if ((long long)n_images * c->N >= (1LL << 31)) return fail(c, SP_ERR_ARG, "chain larger than 2^31 spins");
     if (c->h.dipole != SP_DIPOLE_NONE) return fail(c, SP_ERR_UNSUPPORTED, "GNEB with the dipole term");
-    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, n_images, n_iter};
+    if (!(p->energy_weight >= 0 && p->energy_weight < 1)) return fail(c, SP_ERR_ARG, "energy_weight must be in [0, 1)");
+    if (p->image_types)
+        for (int v = 0; v < n_images; ++v)
+            if (p->image_types[v] < SP_IMAGE_NORMAL || p->image_types[v] > SP_IMAGE_FALLING)
+                return fail(c, SP_ERR_ARG, "image %d: unknown image type %d", v, p->image_types[v]);
+    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, n_images, n_iter, p->image_types, p->energy_weight};
     int e = c->prec == SP_F64
                 ? gneb_run<double>(&c->mins, c->Sd, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream)
                 : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
     if (e) return fail(c, e, "GNEB failed");
+    return SP_OK;
+}
+
+int sp_gneb_path(sp_ctx *c, const void *chain_dev, int n_images, int n_interp, double *r, double *E, double *slope,
+                 double *Q, double *r_interp, double *E_interp, void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, chain_dev, "chain"))) return rc;
+    if (n_images < 2) return fail(c, SP_ERR_ARG, "a chain needs at least 2 images");
+    if (n_interp < 1) return fail(c, SP_ERR_ARG, "n_interp must be >= 1");
+    if (!r || !E || !slope) return fail(c, SP_ERR_ARG, "NULL output");
+    if ((long long)n_images * c->N >= (1LL << 31)) return fail(c, SP_ERR_ARG, "chain larger than 2^31 spins");
+    if (c->h.dipole != SP_DIPOLE_NONE) return fail(c, SP_ERR_UNSUPPORTED, "path analysis with the dipole term");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> dist(n_images - 1);
+    int e = c->prec == SP_F64 ? gneb_path_scalars<double>(&c->mins, c->Sd, chain_dev, n_images, E, dist.data(), slope, st)
+                              : gneb_path_scalars<float>(&c->mins, c->Sf, chain_dev, n_images, E, dist.data(), slope, st);
+    if (e) return fail(c, e, "path analysis failed");
+    r[0] = 0;
+    for (int v = 1; v < n_images; ++v) r[v] = r[v - 1] + dist[v - 1];
+    if (r_interp && E_interp) {
+        // cubic Hermite interpolation of E(r) on every segment
+        for (int v = 0; v + 1 < n_images; ++v) {
+            double h = dist[v];
+            for (int q = 0; q < n_interp; ++q) {
+                double t = (double)q / n_interp;
+                double h00 = 2 * t * t * t - 3 * t * t + 1, h10 = t * t * t - 2 * t * t + t;
+                double h01 = -2 * t * t * t + 3 * t * t, h11 = t * t * t - t * t;
+                r_interp[v * n_interp + q] = r[v] + t * h;
+                E_interp[v * n_interp + q] = h00 * E[v] + h10 * h * slope[v] + h01 * E[v + 1] + h11 * h * slope[v + 1];
+            }
+        }
+        r_interp[(n_images - 1) * n_interp] = r[n_images - 1];
+        E_interp[(n_images - 1) * n_interp] = E[n_images - 1];
+    }
+    if (Q) {
+        size_t rb = c->prec == SP_F64 ? 32 : 16;
+        if ((rc = ensure(c, c->qbuf, sizeof(double) * (size_t)n_images))) return rc;
+        for (int v = 0; v < n_images; ++v) {
+            rc = sp_topological_charge(c, (const char *)chain_dev + rb * (size_t)v * c->N, (double *)c->qbuf.p + v, stream);
+            if (rc) return rc;
+        }
+        cudaError_t ce = cudaMemcpyAsync(Q, c->qbuf.p, sizeof(double) * n_images, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "topological charge copy");
+    }
     return SP_OK;
 }
 
@@ -765,7 +818,15 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
     std::sort(sorted.begin(), sorted.end(), [](const Span &x, const Span &y) { return x.a < y.a; });
     for (size_t k = 1; k < sorted.size(); ++k)
         if (sorted[k].a < sorted[k - 1].b) return fail(c0, SP_ERR_ARG, "chains overlap in the batch buffer");
-    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, 0, n_iter};
+    if (!(p->energy_weight >= 0 && p->energy_weight < 1)) return fail(c0, SP_ERR_ARG, "energy_weight must be in [0, 1)");
+    if (p->image_types) {
+        long long tot = 0;
+        for (int k = 0; k < n_chains; ++k) tot += n_images[k];
+        for (long long g = 0; g < tot; ++g)
+            if (p->image_types[g] < SP_IMAGE_NORMAL || p->image_types[g] > SP_IMAGE_FALLING)
+                return fail(c0, SP_ERR_ARG, "image %lld: unknown image type %d", g, p->image_types[g]);
+    }
+    GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, 0, n_iter, p->image_types, p->energy_weight};
     int e;
     if (c0->prec == SP_F64) {
         std::vector<Stencil<double>> S;

@@ -109,6 +109,7 @@ struct sp_ctx {
     DevBuf pred;      // 2 records per spin: predictor state and folded corrector term
     DevBuf partials;  // reduction partials
     DevBuf bdd;       // dipole field, 1 record per spin
+    DevBuf qbuf;      // per-image topological charges of a path analysis
     DipolePlan *dip = nullptr;
     MinScratch *mins = nullptr;
     Profiler prof;

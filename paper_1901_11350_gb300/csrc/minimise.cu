@@ -27,13 +27,14 @@ namespace {
 struct ImgInfo {
     long long spin0;  // record offset of image 0 of the chain
     int N, chain, nu, M, g0, blk0, bpi;
+    int kind;  // SP_IMAGE_* or -1: climbing decided by the climbing flag
 };
 struct BlkInfo {
     int g, t;
 };
 
 // per-image scalar slots (8 doubles per image)
-enum { kE = 0, kL2 = 1, kTT = 2, kGT = 3, kVF = 4, kFF = 5, kFMAX = 6 };
+enum { kE = 0, kL2 = 1, kTT = 2, kGT = 3, kVF = 4, kFF = 5, kFMAX = 6, kLW = 7 };
 
 struct Buf {
     void *p = nullptr;
@@ -54,7 +55,7 @@ int grow(Buf &b, size_t bytes)
 }  // namespace
 
 struct MinScratch {
-    Buf F, G, Tau, scal, part, cnt, blk, img, sten, state;
+    Buf F, G, Tau, scal, part, cnt, blk, img, sten, state, aux;
     int *host_state = nullptr;  // pinned: iters, active
     double *host_fmax = nullptr;
     // batch layout last uploaded (block/image tables and stencils)
@@ -72,7 +73,7 @@ constexpr int kGraphIters = 8;
 void min_scratch_destroy(MinScratch *s)
 {
     if (!s) return;
-    Buf *bufs[] = {&s->F, &s->G, &s->Tau, &s->scal, &s->part, &s->cnt, &s->blk, &s->img, &s->sten, &s->state};
+    Buf *bufs[] = {&s->F, &s->G, &s->Tau, &s->scal, &s->part, &s->cnt, &s->blk, &s->img, &s->sten, &s->state, &s->aux};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (s->host_state) cudaFreeHost(s->host_state);
@@ -266,11 +267,19 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
 {
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
-    if (im.nu == 0 || im.nu == im.M - 1) return;
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     double r[2] = {0, 0};
-    if (i < im.N) {
+    if (i < im.N && (im.nu == 0 || im.nu == im.M - 1)) {
+        // endpoints: one-sided difference to the neighbouring image (only its
+        // slope dE/dr is used, for the interpolated path energy)
+        v3<T> xi = ld(x, p);
+        v3<T> t = im.nu == 0 ? ld(x, p + im.N) - xi : xi - ld(x, p - im.N);
+        t = t - dot(t, xi) * xi;
+        st(Tau, p, t);
+        r[0] = (double)dot(t, t);
+        r[1] = (double)dot(ldc(G, p), t);
+    } else if (i < im.N) {
         double Ep = scal[8 * (bi.g + 1) + kE], E0 = scal[8 * bi.g + kE], Em = scal[8 * (bi.g - 1) + kE];
         double wp, wm;
         // improved tangent (Henkelman and Jonsson 2000)
@@ -300,18 +309,80 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
     image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kTT);
 }
 
+// Slope dE/dr of image g along its normalised tangent.
+__device__ __forceinline__ double slope_of(const double *scal, int g)
+{
+    double tt = scal[8 * g + kTT];
+    return tt > 0 ? scal[8 * g + kGT] / sqrt(tt) : 0.0;
+}
+
+// Energy-weighted length of the segment from image a to a+1 (reading of the
+// paper's spring modulation: arc length of the curve ((1-w) r, w E(r)) over
+// the geodesic distance h, E(r) the cubic Hermite interpolant of the two
+// images' energies and slopes), by adaptive Simpson with Lyness' criterion
+// and Richardson correction to 1e-13 h, subdivision depth at most 40 (an
+// explicit stack of at most 41 intervals).
+__device__ double seg_integrand(double Ea, double Eb, double da, double db, double h, double w, double s)
+{
+    double t = s / h;
+    double dE = ((6 * t * t - 6 * t) * Ea + (-6 * t * t + 6 * t) * Eb) / h + (3 * t * t - 4 * t + 1) * da +
+                (3 * t * t - 2 * t) * db;
+    return sqrt((1 - w) * (1 - w) + w * w * dE * dE);
+}
+
+__device__ double seg_length(double Ea, double Eb, double da, double db, double h, double w)
+{
+    if (w == 0.0) return h;
+    if (!(h > 0)) return 0.0;
+    struct Iv {
+        double a, b, fa, fm, fb, whole, eps;
+        int depth;
+    } stk[44];
+    int sp = 0;
+    double fa = seg_integrand(Ea, Eb, da, db, h, w, 0.0), fm = seg_integrand(Ea, Eb, da, db, h, w, 0.5 * h),
+           fb = seg_integrand(Ea, Eb, da, db, h, w, h);
+    stk[sp++] = Iv{0.0, h, fa, fm, fb, h / 6 * (fa + 4 * fm + fb), 1e-13 * h, 40};
+    double total = 0.0;
+    while (sp > 0) {
+        Iv c = stk[--sp];
+        double m = 0.5 * (c.a + c.b), lm = 0.5 * (c.a + m), rm = 0.5 * (m + c.b);
+        double flm = seg_integrand(Ea, Eb, da, db, h, w, lm), frm = seg_integrand(Ea, Eb, da, db, h, w, rm);
+        double left = (m - c.a) / 6 * (c.fa + 4 * flm + c.fm), right = (c.b - m) / 6 * (c.fm + 4 * frm + c.fb);
+        double d = left + right - c.whole;
+        if (c.depth <= 0 || fabs(d) <= 15 * c.eps) {
+            total += left + right + d / 15;
+        } else {
+            // right half below the left one: the left half is finished first
+            stk[sp++] = Iv{m, c.b, c.fm, frm, c.fb, right, 0.5 * c.eps, c.depth - 1};
+            stk[sp++] = Iv{c.a, m, c.fa, flm, c.fm, left, 0.5 * c.eps, c.depth - 1};
+        }
+    }
+    return total;
+}
+
+// scal[8g + kLW] = energy-weighted length of segment (g, g+1), one thread per image.
+__global__ void k_g_seglen(const ImgInfo *__restrict__ img, int n_img, double w, double *scal)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_img) return;
+    ImgInfo im = img[g];
+    if (im.nu >= im.M - 1) return;
+    scal[8 * g + kLW] = seg_length(scal[8 * g + kE], scal[8 * (g + 1) + kE], slope_of(scal, g), slope_of(scal, g + 1),
+                                   sqrt(scal[8 * g + kL2]), w);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
                                                     rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
                                                     const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
-                                                    double kspring, int climbing, double dth_m, int mode, double *part,
-                                                    unsigned *cnt, double *scal)
+                                                    double kspring, int climbing, int weighted, double dth_m, int mode,
+                                                    double *part, unsigned *cnt, double *scal)
 {
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
     int ci = -1;
-    if (climbing) {
+    if (climbing && im.kind < 0) {
         ci = 1;
         double best = scal[8 * (im.g0 + 1) + kE];
         for (int nu = 2; nu < im.M - 1; ++nu) {
@@ -329,8 +400,12 @@ __global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ 
         double tt = scal[8 * bi.g + kTT];
         double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
         double gt = scal[8 * bi.g + kGT] * inv;
-        double fs = kspring * (sqrt(scal[8 * bi.g + kL2]) - sqrt(scal[8 * (bi.g - 1) + kL2]));
-        double coef = (im.nu == ci) ? 2.0 * gt : gt + fs;
+        double fs = weighted ? kspring * (scal[8 * bi.g + kLW] - scal[8 * (bi.g - 1) + kLW])
+                             : kspring * (sqrt(scal[8 * bi.g + kL2]) - sqrt(scal[8 * (bi.g - 1) + kL2]));
+        int kind = im.kind >= 0 ? im.kind : (im.nu == ci ? SP_IMAGE_CLIMBING : SP_IMAGE_NORMAL);
+        // climbing: tangential component inverted, no spring; falling: the full
+        // projected gradient, no spring (descends to a minimum along the path)
+        double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : gt + fs);
         v3<T> Fn = axpy((T)(coef * inv), ld(Tau, p), -ldc(G, p));
         if (mode == 1) {
             v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
@@ -517,7 +592,7 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
     for (int c = 0; c < C; ++c) {
         int N = stencils[c].N;
         int bpi = blocks_for(N > 0 ? N : 1);
-        ImgInfo im{spin0[c], N, c, 0, 1, c, (int)blk.size(), bpi};
+        ImgInfo im{spin0[c], N, c, 0, 1, c, (int)blk.size(), bpi, -1};
         for (int t = 0; t < bpi; ++t) blk.push_back(BlkInfo{c, t});
         img.push_back(im);
         total = std::max(total, spin0[c] + (long long)N);
@@ -612,7 +687,8 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
         int bpi = blocks_for(N > 0 ? N : 1);
         int g0 = (int)img.size();
         for (int nu = 0; nu < M[c]; ++nu) {
-            ImgInfo im{spin0[c], N, c, nu, M[c], g0, (int)blk.size(), bpi};
+            int kind = a.kinds ? a.kinds[g0 + nu] : -1;
+            ImgInfo im{spin0[c], N, c, nu, M[c], g0, (int)blk.size(), bpi, kind};
             for (int t = 0; t < bpi; ++t) blk.push_back(BlkInfo{(int)img.size(), t});
             img.push_back(im);
         }
@@ -649,10 +725,13 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     double *scal = (double *)s->scal.p, *part = (double *)s->part.p;
     unsigned *cnt = (unsigned *)s->cnt.p;
     double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
+    const int weighted = a.w != 0.0;
     auto forces = [&](int mode, cudaStream_t ss) {
         k_g_field<T><<<n_blk, kBlock, 0, ss>>>(B, I, Sd, x, G, part, cnt, scal);
         k_g_tangent<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, G, Tau, part, cnt, scal);
-        k_g_force<T><<<n_blk, kBlock, 0, ss>>>(B, I, v, F, G, Tau, a.k, a.climbing, dth_m, mode, part, cnt, scal);
+        if (weighted) k_g_seglen<<<(n_img + 127) / 128, 128, 0, ss>>>(I, n_img, a.w, scal);
+        k_g_force<T><<<n_blk, kBlock, 0, ss>>>(B, I, v, F, G, Tau, a.k, a.climbing, weighted, dth_m, mode, part, cnt,
+                                              scal);
     };
     auto iteration = [&](cudaStream_t ss) {
         k_g_move<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, v, F, a.dt, dt2_2m, 1, scal);
@@ -677,9 +756,9 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
         }
         struct GKey {
             const void *x, *v, *F, *G, *Tau, *scal, *part, *cnt, *blk, *img, *sten;
-            double dt, mass, k;
+            double dt, mass, k, w;
             int climbing, n_blk;
-        } gk{x, v, F, G, Tau, scal, part, cnt, B, I, Sd, a.dt, a.mass, a.k, a.climbing, n_blk};
+        } gk{x, v, F, G, Tau, scal, part, cnt, B, I, Sd, a.dt, a.mass, a.k, a.w, a.climbing, n_blk};
         std::vector<char> gkey(sizeof gk + s->layout.size());
         memcpy(gkey.data(), &gk, sizeof gk);
         memcpy(gkey.data() + sizeof gk, s->layout.data(), s->layout.size());
@@ -716,7 +795,37 @@ int gneb_run(MinScratch **s, const Stencil<T> &S, void *chain, void *vel, const 
     return gneb_batch_run<T>(s, sv, std::vector<int>{a.M}, std::vector<long long>{0}, chain, vel, a, E_dev, fmax_dev, st);
 }
 
+template <typename T>
+int gneb_path_scalars(MinScratch **sp, const Stencil<T> &S, const void *chain, int M, double *E, double *dist,
+                      double *slope, cudaStream_t st)
+{
+    int rc = scratch(sp);
+    if (rc) return rc;
+    if (grow((*sp)->aux, sizeof(double) * (size_t)(M + 1))) return SP_ERR_CUDA;
+    double *Ed = (double *)(*sp)->aux.p;
+    // zero iterations: energies, distances, tangents and slopes of every
+    // image are evaluated and nothing moves (the velocity is not touched)
+    GnebArgs a{0.1, 1.0, 0.0, 0, M, 0, nullptr, 0.0};
+    std::vector<Stencil<T>> sv(1, S);
+    rc = gneb_batch_run<T>(sp, sv, std::vector<int>{M}, std::vector<long long>{0}, const_cast<void *>(chain),
+                           const_cast<void *>(chain), a, Ed, Ed + M, st);
+    if (rc) return rc;
+    std::vector<double> sc(8 * (size_t)M);
+    if (cudaMemcpyAsync(sc.data(), (*sp)->scal.p, sizeof(double) * 8 * M, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    for (int g = 0; g < M; ++g) {
+        E[g] = sc[8 * g + kE];
+        if (g + 1 < M) dist[g] = sqrt(sc[8 * g + kL2]);
+        double tt = sc[8 * g + kTT];
+        slope[g] = tt > 0 ? sc[8 * g + kGT] / sqrt(tt) : 0.0;
+    }
+    return 0;
+}
+
 #define SPGB_MIN_INST(T)                                                                                               \
+    template int gneb_path_scalars<T>(MinScratch **, const Stencil<T> &, const void *, int, double *, double *,         \
+                                      double *, cudaStream_t);                                                         \
     template int vp_batch_run<T>(MinScratch **, const std::vector<Stencil<T>> &, const std::vector<long long> &, void *, \
                                  void *, const MinArgs &, int *, double *, cudaStream_t);                              \
     template int vp_minimise<T>(MinScratch **, const Stencil<T> &, void *, void *, const MinArgs &, int *, double *,    \

@@ -19,6 +19,8 @@ struct MinArgs {
 struct GnebArgs {
     double dt, mass, k;
     int climbing, M, n_iter;
+    const int *kinds;  // host, one SP_IMAGE_* per image of all chains, or NULL
+    double w;          // energy weight of the spring lengths (0: geodesic)
 };
 
 template <typename T>
@@ -36,6 +38,12 @@ template <typename T>
 int gneb_batch_run(MinScratch **s, const std::vector<Stencil<T>> &stencils, const std::vector<int> &M,
                    const std::vector<long long> &spin0, void *chain, void *vel, const GnebArgs &a, double *E_dev,
                    double *fmax_dev, cudaStream_t st);
+
+// Path analysis of one chain: per image the FP64 energy, geodesic distance
+// to the next image and slope dE/dr (host arrays of M; dist has M-1).
+template <typename T>
+int gneb_path_scalars(MinScratch **s, const Stencil<T> &S, const void *chain, int M, double *E, double *dist,
+                      double *slope, cudaStream_t st);
 
 // Batched velocity projection: system c has stencils[c].N spins from record
 // offset spin0[c]; iters[c] and max_torque[c] (host) receive the results.

@@ -81,7 +81,7 @@ def test_call_order_and_argument_errors(L):
     assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), -1, None) == -1
     assert L.sp_llg_step(h, C.c_void_p(256), C.byref(p), 0, None) == 0  # nothing to do
     assert L.sp_effective_field(h, C.c_void_p(256), C.c_void_p(256), None) == -1  # aliasing
-    g = B.GNEBParams(0.1, 1.0, 1.0, 1)
+    g = B.GNEBParams(0.1, 1.0, 1.0, 1, None, 0.0)
     assert L.sp_gneb_step(h, C.c_void_p(256), C.c_void_p(512), 2, C.byref(g), 1, C.c_void_p(64), C.c_void_p(64),
                           None) == -1  # fewer than 3 images
     it, mt = C.c_int(), C.c_double()
