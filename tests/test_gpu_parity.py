@@ -437,3 +437,66 @@ def test_minimise_batch_matches_single_systems(prec):
         assert its[k] == it and mts[k] == mt
         assert torch.equal(flat[offs[k]:offs[k] + N], n)
         assert torch.equal(vel[offs[k]:offs[k] + N], v)
+
+
+def _skyrmion_chain_case(M=9):
+    g = I.hexagonal(9, 8, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.35], K=[0.08], Khat=[[0, 0, 1]], B=[0, 0, 1.2])
+    r = I.site_positions(g)
+    a = I.ferromagnet(I.n_spins(g))
+    b = I.neel_skyrmion(r, r.mean(axis=0), 3.5)
+    return g, h, I.slerp_chain(a, b, M, r, r.mean(axis=0))
+
+
+@pytest.mark.parametrize("w", [0.0, 0.5])
+def test_gneb_image_kinds_and_energy_weight_fp64(w):
+    # explicit climbing and falling images and energy-weighted springs follow
+    # the oracle iteration for iteration.  The velocity projection amplifies
+    # rounding: a 1e-15 change of the start grows to ~1e-11 in 30 iterations
+    # (measured on the oracle), so the chains are compared after 12.
+    g, h, chain0 = _skyrmion_chain_case(9)
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    kinds = ["normal", "normal", "falling", "normal", "climbing", "normal", "normal", "climbing", "normal"]
+    chain, vel = c.spins(chain0), c.spins(np.zeros_like(chain0))
+    E, F = c.gneb_step(chain, vel, n_iter=12, k_spring=1.0, dt=0.1, image_types=kinds, energy_weight=w)
+    ch_o, v_o, E_o, mf_o, _ = o.gneb(chain0, n_iter=12, k_spring=1.0, dt=0.1, image_types=kinds, energy_weight=w)
+    assert np.abs(_np(chain) - ch_o).max() <= 1e-11
+    assert np.abs(_np(vel) - v_o).max() <= 1e-11
+    assert np.abs(E.cpu().numpy() - E_o).max() <= 1e-12 * np.abs(E_o).max()
+    assert abs(F.item() - mf_o) <= 1e-10 * mf_o
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_gneb_path_analysis_matches_oracle(prec, tol):
+    g, h, chain0 = _skyrmion_chain_case(7)
+    o = _oracle(g, h)
+    c = B.Context(g, h, prec)
+    chain = c.spins(chain0)
+    P = c.gneb_path(chain, n_interp=6, charge=True)
+    Po = o.gneb_path(chain0, n_interp=6, charge=True)
+    scale = np.abs(Po["E"]).max()
+    assert np.abs(P["E"] - Po["E"]).max() <= tol * scale
+    assert np.abs(P["r"] - Po["r"]).max() <= tol * Po["r"][-1]
+    assert np.abs(P["slope"] - Po["slope"]).max() <= tol * max(1.0, np.abs(Po["slope"]).max()) * 10
+    assert np.abs(P["E_interp"] - Po["E_interp"]).max() <= tol * scale * 10
+    assert np.abs(P["Q"] - Po["Q"]).max() <= 10 * tol
+    assert abs(Po["Q"][0]) < 1e-9 and abs(Po["Q"][-1] + 1) < 1e-6
+
+
+def test_gneb_batch_with_image_kinds_matches_single_chains():
+    g, h, chain0 = _skyrmion_chain_case(7)
+    kinds = ["normal", "falling", "normal", "climbing", "normal", "normal", "normal"]
+    ctxs = [B.Context(g, h, "f64"), B.Context(g, h, "f64")]
+    single = []
+    for c in ctxs:
+        ch, v = c.spins(chain0), c.spins(np.zeros_like(chain0))
+        c.gneb_step(ch, v, n_iter=20, dt=0.1, image_types=kinds, energy_weight=0.3)
+        single.append(ch)
+    N = ctxs[0].N
+    flat = torch.cat([ctxs[0].spins(chain0).reshape(-1, 4)] * 2)
+    vel = torch.zeros_like(flat)
+    B.gneb_batch_step(ctxs, flat, vel, [0, 7 * N], [7, 7], n_iter=20, dt=0.1, image_types=kinds * 2,
+                      energy_weight=0.3)
+    for k in range(2):
+        assert torch.equal(flat[k * 7 * N:(k + 1) * 7 * N].reshape(7, N, 4), single[k].reshape(7, N, 4))
