@@ -64,6 +64,10 @@ class _GNEB(C.Structure):
 IMAGE = {"normal": 0, "climbing": 1, "falling": 2}
 
 
+class _MC(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("sweep0", C.c_uint64), ("target_accept", C.c_double), ("sample", C.c_int)]
+
+
 def segment_length(Ea, Eb, da, db, h, w):
     """Energy-weighted length of a path segment (see spo.h)."""
     return lib().spo_segment_length(float(Ea), float(Eb), float(da), float(db), float(h), float(w))
@@ -109,6 +113,8 @@ def lib():
                                P(C.c_int)]
         L.spo_gneb_forces.argtypes = [C.c_void_p, d, C.c_int, P(_GNEB), d, d, d, P(C.c_int)]
         L.spo_gneb_path.argtypes = [C.c_void_p, d, C.c_int, C.c_int, d, d, d, d, d, d]
+        L.spo_mc.argtypes = [C.c_void_p, d, C.c_int, d, P(_MC), C.c_int, d, d]
+        L.spo_mc_colours.argtypes = [C.c_void_p]
         L.spo_segment_length.argtypes = [C.c_double] * 6
         L.spo_segment_length.restype = C.c_double
         L.spo_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
@@ -314,6 +320,21 @@ class System:
         if charge:
             out["Q"] = Q
         return out
+
+    def mc_colours(self):
+        return lib().spo_mc_colours(self._h)
+
+    def mc(self, spins, T, n_sweeps, seed=0, sweep0=0, target_accept=0.5, sample=True, cone=None, stats=None):
+        """Metropolis sweeps of replicas spins [R, N, 3] at temperatures T[R];
+        returns (spins, cone[R], stats[R, 8])."""
+        x = np.ascontiguousarray(np.asarray(spins, dtype=np.float64)[..., :3]).copy()
+        R = x.shape[0]
+        Tk = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(R))
+        cn = np.full(R, 0.5) if cone is None else np.ascontiguousarray(np.asarray(cone, dtype=np.float64)).copy()
+        st = np.zeros((R, 8)) if stats is None else np.ascontiguousarray(np.asarray(stats, dtype=np.float64)).copy()
+        p = _MC(int(seed), int(sweep0), float(target_accept), int(bool(sample)))
+        _check(lib().spo_mc(self._h, _dp(x), R, _dp(Tk), C.byref(p), int(n_sweeps), _dp(cn), _dp(st)), "mc")
+        return x, cn, st
 
     def topological_charge(self, n):
         n = self._spins(n)

@@ -1253,3 +1253,153 @@ int spo_topological_charge(const spo_system *s, const double *n, double *Q)
     *Q = acc / (4.0 * M_PI);
     return SPO_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Metropolis Monte Carlo (Sec. Monte Carlo)                            */
+/* ------------------------------------------------------------------ */
+/* Reading of the sweep: the paper visits every spin once per iteration in a
+ * random sequential order; here the sweep visits the colours of a lattice
+ * colouring in order (colour = basis atom and, per direction, the cell index
+ * modulo 2, or modulo 3 for a periodic direction of odd size divisible by 3),
+ * so that spins of one colour never interact and may be updated in any order.
+ * Every update is still a Metropolis step with the rest of the system fixed,
+ * so the sampled distribution is the same Boltzmann distribution. */
+static int mc_moduli(const spo_system *s, int m[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        int any = 0;
+        for (int b = 0; b < s->nb; ++b)
+            for (int e = 0; e < s->n_nbr[b]; ++e) {
+                int dd = s->nbr[b][e].d[d];
+                if (dd > 1 || dd < -1) return 0;
+                if (dd != 0) any = 1;
+            }
+        if (s->nc[d] == 1) {
+            if (any) return 0;
+            m[d] = 1;
+        } else if (!s->per[d] || s->nc[d] % 2 == 0) {
+            m[d] = 2;
+        } else if (s->nc[d] % 3 == 0) {
+            m[d] = 3;
+        } else {
+            return 0;
+        }
+    }
+    return 1;
+}
+
+int spo_mc_colours(const spo_system *s)
+{
+    int m[3];
+    if (!s || !s->have_ham || !mc_moduli(s, m)) return 0;
+    return s->nb * m[0] * m[1] * m[2];
+}
+
+/* Field terms linear in n_i: Zeeman, exchange and DMI. */
+static void mc_linear_field(const spo_system *s, const double *n, int i, double *Bl)
+{
+    int b, c[3];
+    decode(s, i, &b, c);
+    for (int k = 0; k < 3; ++k) Bl[k] = s->mu[b] * MU_B * s->h.B[k];
+    for (int e = 0; e < s->n_nbr[b]; ++e) {
+        const nbr_t *q = &s->nbr[b][e];
+        int j = neighbour(s, c, q->d, q->jb);
+        if (j < 0) continue;
+        double nxd[3];
+        cross3(n + 3 * j, q->D, nxd);
+        for (int k = 0; k < 3; ++k) Bl[k] += q->J * n[3 * j + k] + nxd[k];
+    }
+}
+
+/* Energy of spin i's own terms that are not linear in n_i: anisotropy and
+ * the Gaussian landscape. */
+static double mc_self_energy(const spo_system *s, int b, const double *ni)
+{
+    double kn = dot3(s->h.Khat[b], ni);
+    double dummy[3] = {0, 0, 0};
+    return -s->h.K[b] * kn * kn + gauss_terms(s, ni, dummy);
+}
+
+int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
+           double *cone, double *stats)
+{
+    if (!s || !s->have_ham || !spins || n_rep < 1 || !T || !p || n_sweeps < 0 || !cone || !stats) return SPO_ERR_ARG;
+    if (s->h.dipole != SPO_DIPOLE_NONE) return SPO_ERR_ARG;
+    int m[3];
+    if (!mc_moduli(s, m)) return SPO_ERR_ARG;
+    int n_col = s->nb * m[0] * m[1] * m[2];
+    long N = s->N;
+    double *Bs = (double *)malloc(sizeof(double) * 3 * N);
+    if (!Bs) return SPO_ERR_STATE;
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        uint64_t sweep = p->sweep0 + (uint64_t)sw;
+        for (int r = 0; r < n_rep; ++r) {
+            double *x = spins + 3 * N * (size_t)r;
+            double ct = cos(cone[r]);
+            double accepted = 0;
+            for (int col = 0; col < n_col; ++col)
+                for (long i = 0; i < N; ++i) {
+                    int b, c[3];
+                    decode(s, (int)i, &b, c);
+                    int cc = b + s->nb * (c[0] % m[0] + m[0] * (c[1] % m[1] + m[1] * (c[2] % m[2])));
+                    if (cc != col) continue;
+                    /* three uniforms in (0, 1) from Philox: azimuth, cone, acceptance */
+                    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)r + 1u};
+                    uint32_t o[4];
+                    spo_philox4x32_10(ctr, key, o);
+                    double u0 = (o[0] + 0.5) * 2.3283064365386963e-10;
+                    double u1 = (o[1] + 0.5) * 2.3283064365386963e-10;
+                    double u2 = (o[2] + 0.5) * 2.3283064365386963e-10;
+                    /* trial direction: uniform on the cap of half-angle theta_cone
+                     * around n_i (cos theta uniform in [cos theta_cone, 1]) */
+                    double *ni = x + 3 * i;
+                    double cth = 1.0 - u1 * (1.0 - ct), sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+                    double ph = 2.0 * M_PI * u0;
+                    double a[3] = {1, 0, 0};
+                    if (fabs(ni[0]) >= 0.9) { a[0] = 0; a[1] = 1; }
+                    double an = dot3(a, ni), e1[3], e2[3];
+                    for (int k = 0; k < 3; ++k) e1[k] = a[k] - an * ni[k];
+                    normalise3(e1);
+                    cross3(ni, e1, e2);
+                    double nt[3];
+                    for (int k = 0; k < 3; ++k) nt[k] = cth * ni[k] + sth * (cos(ph) * e1[k] + sin(ph) * e2[k]);
+                    normalise3(nt);
+                    double Bl[3];
+                    mc_linear_field(s, x, (int)i, Bl);
+                    double dE = -(dot3(nt, Bl) - dot3(ni, Bl)) + mc_self_energy(s, b, nt) - mc_self_energy(s, b, ni);
+                    int acc = T[r] > 0 ? (u2 < exp(-dE / (K_B * T[r]))) : (dE < 0);
+                    if (acc) {
+                        for (int k = 0; k < 3; ++k) ni[k] = nt[k];
+                        accepted += 1;
+                    }
+                }
+            double *st = stats + 8 * (size_t)r;
+            st[6] += accepted;
+            st[7] += (double)N;
+            /* reading of the adaptive cone: multiplicative feedback towards
+             * the target acceptance ratio, theta <- theta exp(ratio - target),
+             * kept in [1e-4, pi] */
+            if (p->target_accept > 0) {
+                double th = cone[r] * exp(accepted / (double)N - p->target_accept);
+                cone[r] = fmin(M_PI, fmax(1e-4, th));
+            }
+            if (p->sample) {
+                double M[3] = {0, 0, 0};
+                for (long i = 0; i < N; ++i)
+                    for (int k = 0; k < 3; ++k) M[k] += x[3 * i + k];
+                double mm = sqrt(dot3(M, M)) / (double)N;
+                double e[6];
+                spo_energy(s, x, e);
+                st[0] += mm;
+                st[1] += mm * mm;
+                st[2] += mm * mm * mm * mm;
+                st[3] += e[0];
+                st[4] += e[0] * e[0];
+                st[5] += 1;
+            }
+        }
+    }
+    free(Bs);
+    return SPO_OK;
+}

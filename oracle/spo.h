@@ -148,6 +148,26 @@ int spo_gneb_path(const spo_system *s, const double *chain, int n_images, int n_
  * values Ea, Eb and end slopes da, db (w = 0: h). */
 double spo_segment_length(double Ea, double Eb, double da, double db, double h, double w);
 
+/* Metropolis Monte Carlo with cone trial moves (Sec. Monte Carlo). */
+typedef struct {
+    uint64_t seed;          /* Philox key */
+    uint64_t sweep0;        /* index of the first sweep (Philox counter) */
+    double target_accept;   /* > 0: adapt each replica's cone after every sweep; 0: fixed cone */
+    int sample;             /* 1: accumulate observables after every sweep */
+} spo_mc_params;
+
+/* Number of colours of the sweep (0 when the lattice cannot be coloured:
+ * a neighbour more than one cell away, or a periodic direction whose size
+ * is odd and not a multiple of 3, or a one-cell direction with offsets). */
+int spo_mc_colours(const spo_system *s);
+/* n_sweeps Metropolis sweeps of n_rep replicas of the system (spins
+ * n_rep x N x 3, replica r at temperature T[r] K).  cone[r] (radians,
+ * in/out) is the trial cone's half-angle.  stats[r*8 + k] accumulates
+ * (sum m, m^2, m^4, E, E^2, samples, accepted, trials), m = |sum n_i|/N,
+ * E the total energy (meV). */
+int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
+           double *cone, double *stats);
+
 /* Philox4x32-10 block (Salmon et al., SC'11). */
 void spo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* The three standard normals of the thermal field of spin i at step `step`. */

@@ -826,3 +826,78 @@ def test_energy_weighted_springs_equalise_segment_lengths():
     # and they differ from the geodesic spacing: images crowd where E changes
     dr = np.diff(P["r"])
     assert np.max(dr) / np.min(dr) > 1.2
+
+
+# ----------------------------------------------------------------------------
+# Metropolis Monte Carlo (Sec. Monte Carlo)
+# ----------------------------------------------------------------------------
+def _langevin(x):
+    return 1.0 / np.tanh(x) - 1.0 / x
+
+
+def _mc_run(s, R, T, thermal, samples, seed, start=None):
+    x0 = np.tile(I.ferromagnet(s.N)[None], (R, 1, 1)) if start is None else start
+    x, cone, _ = s.mc(x0, T, thermal, seed=seed, target_accept=0.5, sample=False)
+    x, cone, st = s.mc(x, T, samples, seed=seed, sweep0=thermal, target_accept=0.0, sample=True, cone=cone)
+    return x, cone, st
+
+
+def test_mc_single_spin_in_a_field_is_langevin():
+    # one moment in B along z: <n_z> = L(x), var(n_z) = 1 - 2 L(x)/x - L(x)^2,
+    # x = mu B / (k_B T); E = -mu B n_z
+    mu, Bz, T = 2.0, 1.0, 1.0
+    s = oracle.System(I.square(1, 1, mu_s=mu), dict(B=[0, 0, Bz]))
+    assert s.mc_colours() == 1
+    R = 64
+    _, _, st = _mc_run(s, R, [T] * R, 200, 3000, seed=11)
+    muB = mu * oracle.MU_B * Bz
+    x = muB / (oracle.K_B * T)
+    nz = -st[:, 3].sum() / st[:, 5].sum() / muB
+    nz2 = st[:, 4].sum() / st[:, 5].sum() / muB ** 2
+    L = _langevin(x)
+    assert abs(nz - L) < 5e-3
+    assert abs((nz2 - nz ** 2) - (1 - 2 * L / x - L ** 2)) < 5e-3
+
+
+def test_mc_single_spin_anisotropy_matches_quadrature():
+    # E = -K n_z^2: <n_z^2> = int u^2 exp(K u^2/kT) du / int exp(K u^2/kT) du
+    from scipy.integrate import quad
+    K, T = 0.1, 0.8
+    s = oracle.System(I.square(1, 1, mu_s=2.0), dict(K=[K], Khat=[[0, 0, 1]]))
+    R = 64
+    _, _, st = _mc_run(s, R, [T] * R, 200, 3000, seed=12)
+    kap = K / (oracle.K_B * T)
+    ref = quad(lambda u: u * u * np.exp(kap * u * u), -1, 1)[0] / quad(lambda u: np.exp(kap * u * u), -1, 1)[0]
+    assert abs(-st[:, 3].sum() / st[:, 5].sum() / K - ref) < 5e-3
+
+
+def test_mc_exchange_dimer_is_langevin_in_j_over_kt():
+    # two spins coupled by J: the angle between them has density ~ exp(x cos g),
+    # so <n1.n2> = L(J / kT) and <E> = -J L(J / kT)
+    J, T = 0.2, 1.5
+    s = oracle.System(I.square(2, 1, periodic=(False, False), mu_s=2.0), dict(J=[J]))
+    assert s.mc_colours() == 2
+    R = 64
+    _, _, st = _mc_run(s, R, [T] * R, 200, 3000, seed=13)
+    x = J / (oracle.K_B * T)
+    assert abs(-st[:, 3].sum() / st[:, 5].sum() / J - _langevin(x)) < 6e-3
+
+
+def test_mc_cone_adapts_to_the_target_acceptance_and_limits():
+    s = oracle.System(I.simple_cubic(4, 4, 4), dict(J=[1.0], B=[0, 0, 0.5]))
+    assert s.mc_colours() == 8
+    x0 = np.tile(I.random_spins(s.N, 3)[None], (3, 1, 1))
+    x, cone, st = s.mc(x0, [5.0, 12.0, 60.0], 400, seed=5, target_accept=0.4, sample=False)
+    # acceptance of the next 100 sweeps at the adapted cone
+    _, _, st = s.mc(x, [5.0, 12.0, 60.0], 100, seed=5, sweep0=400, target_accept=0.0, sample=False, cone=cone)
+    assert np.all(np.abs(st[:2, 6] / st[:2, 7] - 0.4) < 0.03)
+    # far above Tc even whole-sphere trials are accepted more often than the
+    # target: the cone stops at pi
+    assert cone[2] == np.pi and st[2, 6] / st[2, 7] > 0.4
+    # T = 0 accepts only moves that lower the energy: E never increases
+    E0 = s.energy(x0[0])[0]
+    y, _, st0 = s.mc(x0[:1], [0.0], 30, seed=6, target_accept=0.0, sample=True, cone=[0.3])
+    assert st0[0, 3] / st0[0, 5] < E0 and s.energy(y[0])[0] <= E0
+    # at a very high temperature every trial is accepted
+    _, _, sth = s.mc(x0[:1], [1e12], 5, seed=7, target_accept=0.0, sample=False, cone=[1.0])
+    assert sth[0, 6] == sth[0, 7]
