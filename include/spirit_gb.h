@@ -306,6 +306,44 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
                        double *max_force_dev, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Metropolis Monte Carlo (Sec. Monte Carlo)
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t seed;          /* Philox key */
+    uint64_t sweep0;        /* index of the first sweep (Philox counter; resume = same seed, later sweep0) */
+    double target_accept;   /* in (0, 1): after every sweep each replica's cone angle is multiplied
+                               by exp(acceptance - target) and kept in [1e-4, pi]; 0: fixed cone */
+    int sample;             /* 1: accumulate observables after every sweep */
+} sp_mc_params;
+
+/* Number of colours of this context's Monte Carlo sweep (0: the lattice has
+ * no colouring -- a neighbour more than one cell away, a periodic direction
+ * of odd size not divisible by 3, or offsets along a direction of one cell). */
+int sp_mc_colours(sp_ctx *ctx, int *n_colours);
+
+/* n_sweeps Metropolis sweeps of n_rep replicas of the context's system,
+ * replica r at temperature T[r] (K, host array; 0 = accept only moves that
+ * lower the energy).  A trial move of spin i is a direction drawn uniformly
+ * on the cap of half-angle cone_dev[r] around n_i (Philox4x32-10, counter
+ * (i, sweep lo, sweep hi, 8 r + 1)), accepted with probability
+ * min(1, exp(-dE / k_B T)), dE the exact energy change (Zeeman, exchange,
+ * DMI, anisotropy; no dipole term).  A sweep updates the lattice colour by
+ * colour (spins of one colour do not interact; the paper visits spins in a
+ * random sequential order -- both sample the Boltzmann distribution).
+ *   spins_dev  n_rep x N records, replica-major
+ *   cone_dev   DEVICE, n_rep doubles (radians), in/out
+ *   stats_dev  DEVICE, n_rep x 8 doubles, accumulated (not reset): sum of m,
+ *              m^2, m^4, E, E^2 (m = |sum_i n_i| / N, E total energy in meV,
+ *              each after every sweep when p->sample), the number of samples,
+ *              accepted trials and trials
+ * SP_ERR_UNSUPPORTED for the dipole term or a lattice without colouring.
+ * Runs of sweeps are replayed from a CUDA graph on a private stream ordered
+ * after and before `stream` by events. */
+int sp_mc_sweeps(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const sp_mc_params *p, int n_sweeps,
+                 double *cone_dev, double *stats_dev, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free LLG stepping
  * ------------------------------------------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -55,6 +55,10 @@ class GNEBParams(C.Structure):
 IMAGE_KINDS = {"normal": 0, "climbing": 1, "falling": 2}
 
 
+class MCParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("sweep0", C.c_uint64), ("target_accept", C.c_double), ("sample", C.c_int)]
+
+
 def gneb_params(dt, mass, k_spring, climbing, image_types=None, energy_weight=0.0):
     """The parameter block and the int array it points to (keep both alive)."""
     arr = None
@@ -86,6 +90,8 @@ SIGNATURES = {
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
                                C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_mc_colours": (_i, [_vp, C.POINTER(_i)]),
+    "sp_mc_sweeps": (_i, [_vp, _vp, _i, C.POINTER(_d), C.POINTER(MCParams), _i, _vp, _vp, _vp]),
     "sp_gneb_path": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sp_minimise_batch": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), _d, _d, _d, _i, _i,
                               C.POINTER(_i), C.POINTER(_d), _vp]),
@@ -264,6 +270,27 @@ class Context:
         if charge:
             out["Q"] = Q
         return out
+
+    def mc_colours(self):
+        n = C.c_int()
+        self._check(lib().sp_mc_colours(self._h, C.byref(n)))
+        return n.value
+
+    def mc_sweeps(self, spins, T, n_sweeps, seed=0, sweep0=0, target_accept=0.5, sample=True, cone=None, stats=None):
+        """Metropolis sweeps of replicas spins [R, N, 4] (CUDA, this context's
+        dtype) at temperatures T[R]; cone [R] and stats [R, 8] are float64
+        CUDA tensors, updated in place (created when None).  Returns (cone, stats)."""
+        R = spins.shape[0]
+        if spins.dim() != 3 or spins.shape[1] != self.N:
+            raise ValueError("spins must be [replicas, N, 4]")
+        self._spin_arg(spins, "spins", R)
+        cone = torch.full((R,), 0.5, dtype=torch.float64, device=spins.device) if cone is None else cone
+        stats = torch.zeros((R, 8), dtype=torch.float64, device=spins.device) if stats is None else stats
+        Th = (C.c_double * R)(*[float(t) for t in T])
+        p = MCParams(int(seed), int(sweep0), float(target_accept), int(bool(sample)))
+        self._check(lib().sp_mc_sweeps(self._h, _ptr(spins), R, Th, C.byref(p), int(n_sweeps), _ptr(cone), _ptr(stats),
+                                       _stream()))
+        return cone, stats
 
     def topological_charge(self, n, out=None):
         out = torch.empty(1, dtype=torch.float64, device=n.device) if out is None else out

@@ -78,6 +78,9 @@ struct Profiler {
 
 using namespace spgb_ctx;
 
+struct McScratch;  // Monte Carlo scratch (mc.cu)
+void mc_scratch_destroy(McScratch *m);
+
 struct sp_ctx {
     int prec = SP_F32;
     int device = 0;
@@ -112,6 +115,7 @@ struct sp_ctx {
     DevBuf qbuf;      // per-image topological charges of a path analysis
     DipolePlan *dip = nullptr;
     MinScratch *mins = nullptr;
+    McScratch *mc = nullptr;
     Profiler prof;
 };
 

@@ -500,3 +500,66 @@ def test_gneb_batch_with_image_kinds_matches_single_chains():
                       energy_weight=0.3)
     for k in range(2):
         assert torch.equal(flat[k * 7 * N:(k + 1) * 7 * N].reshape(7, N, 4), single[k].reshape(7, N, 4))
+
+
+MC_CASES = [
+    ("sc4", I.simple_cubic(4, 4, 4), dict(J=[1.0, -0.2], dmi_kind="bulk", D=[0.2], K=[0.1], Khat=[[0, 0, 1]],
+                                         B=[0, 0.3, 0.8]), 8),
+    ("hex9", I.hexagonal(9, 9, periodic=(True, True), mu_s=2.0),
+     dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0, 1.0]), 9),
+    ("hex6open", I.hexagonal(6, 5, periodic=(True, False), mu_s=3.0), dict(J=[1.0], B=[0.2, 0, 0.5]), 4),
+]
+
+
+@pytest.mark.parametrize("name,g,h,ncol", MC_CASES, ids=[c[0] for c in MC_CASES])
+def test_mc_sweeps_fp64_match_oracle(name, g, h, ncol):
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    assert c.mc_colours() == ncol == o.mc_colours()
+    R = 3
+    T = [2.0, 8.0, 30.0]
+    x0 = np.stack([I.random_spins(c.N, 70 + r) for r in range(R)])
+    x = torch.stack([c.spins(x0[r]) for r in range(R)])
+    # thermalisation with the adaptive cone, then sampling with the cone fixed
+    cone, stats = c.mc_sweeps(x, T, 20, seed=9, target_accept=0.4, sample=False)
+    cone, stats = c.mc_sweeps(x, T, 20, seed=9, sweep0=20, target_accept=0.0, sample=True, cone=cone, stats=stats)
+    xo, co, so = o.mc(x0, T, 20, seed=9, target_accept=0.4, sample=False)
+    xo, co, so = o.mc(xo, T, 20, seed=9, sweep0=20, target_accept=0.0, sample=True, cone=co, stats=so)
+    assert np.abs(_np(x) - xo).max() <= 1e-11
+    assert np.abs(cone.cpu().numpy() - co).max() <= 1e-12
+    st = stats.cpu().numpy()
+    assert np.array_equal(st[:, 5:], so[:, 5:])          # sample, accepted and trial counts
+    assert np.allclose(st[:, :5], so[:, :5], rtol=1e-10, atol=1e-12)
+
+
+def test_mc_graph_replay_and_resume_are_bit_exact():
+    # 40 sweeps in one call (graph replay) equal 40 single-sweep calls
+    g, h = MC_CASES[0][1], MC_CASES[0][2]
+    c = B.Context(g, h, "f64")
+    x0 = c.spins(I.random_spins(c.N, 5))[None].repeat(2, 1, 1).contiguous()
+    x1 = x0.clone()
+    ca, sa = c.mc_sweeps(x0, [4.0, 9.0], 40, seed=3, target_accept=0.5)
+    cb, sb = None, None
+    for k in range(40):
+        cb, sb = c.mc_sweeps(x1, [4.0, 9.0], 1, seed=3, sweep0=k, target_accept=0.5, cone=cb, stats=sb)
+    assert torch.equal(x0, x1) and torch.equal(ca, cb) and torch.equal(sa, sb)
+
+
+def test_mc_fp32_samples_the_same_distribution():
+    # FP32 decisions differ from FP64 ones near the acceptance threshold, so
+    # the FP32 chain is compared through its mean energy and magnetisation
+    g = I.simple_cubic(8, 8, 8)
+    h = dict(J=[1.0], B=[0, 0, 0.2])
+    res = {}
+    for prec in ("f64", "f32"):
+        c = B.Context(g, h, prec)
+        R = 16
+        x = c.spins(I.ferromagnet(c.N))[None].repeat(R, 1, 1).contiguous()
+        cone, st = c.mc_sweeps(x, [12.0] * R, 300, seed=1, target_accept=0.5, sample=False)
+        cone, st = c.mc_sweeps(x, [12.0] * R, 1500, seed=1, sweep0=300, target_accept=0.0, cone=cone)
+        st = st.cpu().numpy()
+        res[prec] = (st[:, 3] / st[:, 5], st[:, 0] / st[:, 5])
+    for k in range(2):
+        a, b = res["f64"][k], res["f32"][k]
+        err = np.sqrt(a.var() / len(a) + b.var() / len(b))
+        assert abs(a.mean() - b.mean()) < 5 * err + 1e-12, (k, a.mean(), b.mean(), err)
