@@ -430,6 +430,89 @@ def run_hex_dipole(args):
     return 0
 
 
+def run_mc(args):
+    """Metropolis Monte Carlo of the simple-cubic ferromagnet (J = 1 meV,
+    periodic, B = 0): all temperatures of a grid as replicas of one launch;
+    per temperature args.mc_thermal sweeps with the adaptive cone (target
+    acceptance 0.5) and args.mc_samples sampled sweeps with the cone fixed.
+    Reports spin-updates/s and the critical temperature from the Binder
+    cumulant crossings of the sizes and the susceptibility peak."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import binding as Bd
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    build.build()
+    sizes = [int(v) for v in args.mc_sizes.split(",")]
+    T = np.round(np.arange(args.mc_tmin, args.mc_tmax + 1e-9, args.mc_dt), 6)
+    R = len(T)
+    kB = 0.08617333262
+    res, tot_updates, tot_s = {}, 0.0, 0.0
+    st_cuda = torch.cuda.current_stream()
+    for L in sizes:
+        ctx = Bd.Context(I.simple_cubic(L, L, L, periodic=(True, True, True), mu_s=2.0), dict(J=[1.0]), "f32")
+        N = ctx.N
+        x = ctx.spins(I.ferromagnet(N))[None].repeat(R, 1, 1).contiguous()
+        cone = torch.full((R,), 0.5, dtype=torch.float64, device="cuda")
+        stats = torch.zeros((R, 8), dtype=torch.float64, device="cuda")
+        ctx.mc_sweeps(x, T, args.warmup, seed=L, target_accept=0.5, sample=False, cone=cone, stats=stats)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(st_cuda)
+        ctx.mc_sweeps(x, T, args.mc_thermal, seed=L, sweep0=args.warmup, target_accept=0.5, sample=False, cone=cone,
+                      stats=stats)
+        e1.record(st_cuda)
+        stats.zero_()
+        ctx.mc_sweeps(x, T, args.mc_samples, seed=L, sweep0=args.warmup + args.mc_thermal, target_accept=0.0,
+                      sample=True, cone=cone, stats=stats)
+        e2.record(st_cuda)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e2) / 1e3
+        sweeps = args.mc_thermal + args.mc_samples
+        tot_updates += float(sweeps) * N * R
+        tot_s += secs
+        s = stats.cpu().numpy()
+        n = s[:, 5]
+        m, m2, m4, E, E2 = (s[:, k] / n for k in range(5))
+        res[L] = dict(N=N, seconds=secs, thermal_s=e0.elapsed_time(e1) / 1e3, m=m, m2=m2, m4=m4,
+                      U4=1 - m4 / (3 * m2 ** 2), chi=N * (m2 - m ** 2) / (kB * T), cv=(E2 - E ** 2) / (kB * T ** 2) / N,
+                      accept=s[:, 6] / s[:, 7], cone=cone.cpu().numpy())
+    # Binder-cumulant crossings of consecutive sizes (linear interpolation)
+    cross = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        d = res[a]["U4"] - res[b]["U4"]
+        for k in range(R - 1):
+            if d[k] < 0 <= d[k + 1] or d[k] > 0 >= d[k + 1]:
+                cross.append(float(T[k] + (T[k + 1] - T[k]) * d[k] / (d[k] - d[k + 1])))
+                break
+    Lmax = max(sizes)
+    chi = res[Lmax]["chi"]
+    k = int(np.argmax(chi))
+    tpk = float(T[k])
+    if 0 < k < R - 1:  # parabola through the peak and its neighbours
+        y0, y1, y2 = chi[k - 1], chi[k], chi[k + 1]
+        den = y0 - 2 * y1 + y2
+        if den != 0:
+            tpk = float(T[k] + 0.5 * (T[1] - T[0]) * (y0 - y2) / den)
+    out = {"metric": "Metropolis spin-updates/s, simple-cubic ferromagnet (Tc validation)",
+           "value": tot_updates / tot_s, "unit": "spin-updates/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32 field and trials, f64 observables", "data": "synthetic",
+           "config": {"workload": "mc_sc_ferromagnet_tc", "sizes": sizes, "temperatures_K": [float(t) for t in T],
+                      "thermal_sweeps": args.mc_thermal, "sample_sweeps": args.mc_samples, "J_meV": 1.0,
+                      "target_accept": 0.5, "colours": 8},
+           "tc_K": {"binder_crossings": cross, "binder_mean": float(np.mean(cross)) if cross else None,
+                    "chi_peak_L%d" % Lmax: tpk, "expected_high_T_series": 16.71, "paper_mc": 16.60},
+           "per_size": {str(L): {"seconds": r["seconds"], "spins": r["N"],
+                                 "m": [round(float(v), 5) for v in r["m"]], "U4": [round(float(v), 5) for v in r["U4"]],
+                                 "chi": [round(float(v), 3) for v in r["chi"]], "cv": [round(float(v), 5) for v in r["cv"]],
+                                 "accept": [round(float(v), 3) for v in r["accept"]]}
+                        for L, r in res.items()}}
+    print(json.dumps(out))
+    return 0
+
+
 def run_unet(args):
     """The warm-start network alone (BF16 U-Net, 128x128 inputs, batch 64):
     training samples/s of a full step (forward, backward, Adam) and
@@ -569,7 +652,13 @@ def main():
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
     ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
-    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet"])
+    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30"])
+    ap.add_argument("--mc-sizes", default="10,15,20,30", help="mc30: lattice sides")
+    ap.add_argument("--mc-thermal", type=int, default=10000, help="mc30: thermalisation sweeps")
+    ap.add_argument("--mc-samples", type=int, default=100000, help="mc30: sampled sweeps")
+    ap.add_argument("--mc-tmin", type=float, default=10.0)
+    ap.add_argument("--mc-tmax", type=float, default=24.0)
+    ap.add_argument("--mc-dt", type=float, default=0.5)
     ap.add_argument("--systems", type=int, default=200, help="warmstart: held-out systems")
     ap.add_argument("--eval-max-iter", type=int, default=30000, help="warmstart: iteration cap per relaxation")
     ap.add_argument("--per-system", type=int, default=4, help="warmstart: systems timed in the one-system loop")
@@ -591,6 +680,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "unet":
         return run_unet(args)
+    if args.workload == "mc30":
+        return run_mc(args)
     return run_gpu(args)
 
 
