@@ -113,6 +113,8 @@ def lib():
                                P(C.c_int)]
         L.spo_gneb_forces.argtypes = [C.c_void_p, d, C.c_int, P(_GNEB), d, d, d, P(C.c_int)]
         L.spo_gneb_path.argtypes = [C.c_void_p, d, C.c_int, C.c_int, d, d, d, d, d, d]
+        L.spo_hessian_apply.argtypes = [C.c_void_p, d, d, d]
+        L.spo_hessian_dense.argtypes = [C.c_void_p, d, d, d]
         L.spo_mc.argtypes = [C.c_void_p, d, C.c_int, d, P(_MC), C.c_int, d, d]
         L.spo_mc_colours.argtypes = [C.c_void_p]
         L.spo_segment_length.argtypes = [C.c_double] * 6
@@ -320,6 +322,57 @@ class System:
         if charge:
             out["Q"] = Q
         return out
+
+    def hessian_apply(self, n, v):
+        n = self._spins(n)
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.float64)[..., :3]).reshape(-1, 3).copy()
+        out = np.zeros_like(n)
+        _check(lib().spo_hessian_apply(self._h, _dp(n), _dp(v), _dp(out)), "hessian_apply")
+        return out
+
+    def hessian_dense(self, n):
+        """(H [2N, 2N], T [N, 3, 2]) of the covariant Hessian in the tangent basis."""
+        n = self._spins(n)
+        H = np.zeros((2 * self.N, 2 * self.N))
+        T = np.zeros((self.N, 3, 2))
+        _check(lib().spo_hessian_dense(self._h, _dp(n), _dp(H), _dp(T)), "hessian_dense")
+        return H, T
+
+    def lowest_mode(self, n):
+        """Lowest eigenvalue of the covariant Hessian and its eigenvector as
+        an N x 3 unit tangent field (dense eigen-decomposition)."""
+        H, T = self.hessian_dense(n)
+        w, V = np.linalg.eigh(0.5 * (H + H.T))
+        mode = np.einsum("ikc,ic->ik", T, V[:, 0].reshape(-1, 2))
+        return w[0], mode / np.linalg.norm(mode)
+
+    def mmf(self, n, n_iter, dt=0.1, mass=1.0, vel=None):
+        """Minimum mode following (Sec. MMF): velocity projection (Appendix D)
+        with the effective force F - 2 (F.l) l, l the lowest mode; where the
+        lowest eigenvalue is not negative, -(F.l) l (reading: climb along the
+        lowest mode only).  Returns (n, v, F, lambda_min)."""
+        x = self._spins(n).copy()
+        v = np.zeros_like(x) if vel is None else np.asarray(vel, dtype=np.float64)[..., :3].reshape(-1, 3).copy()
+
+        def force(x):
+            B = self.field(x)
+            F = B - np.sum(B * x, axis=1, keepdims=True) * x
+            lam, l = self.lowest_mode(x)
+            fl = np.sum(F * l)
+            Fe = F - 2.0 * fl * l if lam < 0 else -fl * l
+            return F, Fe, lam
+
+        F, Fe, lam = force(x)
+        for _ in range(n_iter):
+            y = x + dt * v + dt * dt / (2 * mass) * Fe
+            y /= np.linalg.norm(y, axis=1, keepdims=True)
+            F2, Fe2, lam = force(y)
+            v = v + dt / (2 * mass) * (Fe + Fe2)
+            vf = np.sum(v * Fe2)
+            ff = np.sum(Fe2 * Fe2)
+            v = (vf / ff) * Fe2 if (vf > 0 and ff > 0) else np.zeros_like(v)
+            x, F, Fe = y, F2, Fe2
+        return x, v, F, lam
 
     def mc_colours(self):
         return lib().spo_mc_colours(self._h)

@@ -1403,3 +1403,111 @@ int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const
     free(Bs);
     return SPO_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Covariant Hessian (Sec. MMF and its appendix on the spin manifold)  */
+/* ------------------------------------------------------------------ */
+/* Embedding second derivatives applied to w: the negative of the field's
+ * terms that are linear in the spins -- exchange J w_j, DMI w_j x D_ij,
+ * anisotropy 2 K (Khat.w_i) Khat -- and the Gaussian landscape's
+ * (e/s^2)(u^2/s^2 - 1) c (c.w_i). */
+static void hbar_apply(const spo_system *s, const double *n, const double *w, long i, double *out)
+{
+    int b, c[3];
+    decode(s, (int)i, &b, c);
+    const spo_hamiltonian *h = &s->h;
+    double acc[3] = {0, 0, 0};
+    double kw = dot3(h->Khat[b], w + 3 * i);
+    for (int k = 0; k < 3; ++k) acc[k] = 2.0 * h->K[b] * kw * h->Khat[b][k];
+    for (int e = 0; e < s->n_nbr[b]; ++e) {
+        const nbr_t *q = &s->nbr[b][e];
+        int j = neighbour(s, c, q->d, q->jb);
+        if (j < 0) continue;
+        double wxd[3];
+        cross3(w + 3 * j, q->D, wxd);
+        for (int k = 0; k < 3; ++k) acc[k] += q->J * w[3 * j + k] + wxd[k];
+    }
+    for (int k = 0; k < 3; ++k) out[k] = -acc[k];
+    const double *ni = n + 3 * i;
+    for (int g = 0; g < h->n_gauss; ++g) {
+        const double *G = h->gauss[g];
+        double a = G[0], sig = G[1];
+        const double *cc = &G[2];
+        double u = 1.0 - dot3(ni, cc);
+        double eg = a * exp(-u * u / (2 * sig * sig));
+        double f = eg / (sig * sig) * (u * u / (sig * sig) - 1.0) * dot3(cc, w + 3 * i);
+        for (int k = 0; k < 3; ++k) out[k] += f * cc[k];
+    }
+}
+
+int spo_hessian_apply(const spo_system *s, const double *n, const double *v, double *out)
+{
+    if (!s || !s->have_ham || !n || !v || !out) return SPO_ERR_ARG;
+    if (s->h.dipole != SPO_DIPOLE_NONE) return SPO_ERR_ARG;
+    long N = s->N;
+    double *w = (double *)malloc(sizeof(double) * 3 * N), *B = (double *)malloc(sizeof(double) * 3 * N);
+    if (!w || !B) { free(w); free(B); return SPO_ERR_STATE; }
+    for (long i = 0; i < N; ++i) {
+        double vn = dot3(v + 3 * i, n + 3 * i);
+        for (int k = 0; k < 3; ++k) w[3 * i + k] = v[3 * i + k] - vn * n[3 * i + k];
+    }
+    int rc = spo_effective_field(s, n, B, -1);
+    for (long i = 0; i < N && !rc; ++i) {
+        double hb[3];
+        hbar_apply(s, n, w, i, hb);
+        const double *ni = n + 3 * i;
+        double hn = dot3(hb, ni);
+        double nB = dot3(ni, B + 3 * i); /* -(n . grad Hbar) = n . B */
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = hb[k] - hn * ni[k] + nB * w[3 * i + k];
+    }
+    free(w); free(B);
+    return rc;
+}
+
+/* Tangent basis of spin i: e1 = P x (or P y when |n_x| >= 0.9), normalised;
+ * e2 = n x e1. */
+static void tangent_basis(const double *ni, double *e1, double *e2)
+{
+    double a[3] = {1, 0, 0};
+    if (fabs(ni[0]) >= 0.9) { a[0] = 0; a[1] = 1; }
+    double an = dot3(a, ni);
+    for (int k = 0; k < 3; ++k) e1[k] = a[k] - an * ni[k];
+    normalise3(e1);
+    cross3(ni, e1, e2);
+}
+
+int spo_hessian_dense(const spo_system *s, const double *n, double *H, double *T)
+{
+    if (!s || !s->have_ham || !n || !H) return SPO_ERR_ARG;
+    long N = s->N, M = 2 * N;
+    double *Tb = (double *)malloc(sizeof(double) * 6 * N);
+    double *v = (double *)calloc(3 * N, sizeof(double)), *hv = (double *)malloc(sizeof(double) * 3 * N);
+    if (!Tb || !v || !hv) { free(Tb); free(v); free(hv); return SPO_ERR_STATE; }
+    for (long i = 0; i < N; ++i) {
+        double e1[3], e2[3];
+        tangent_basis(n + 3 * i, e1, e2);
+        for (int k = 0; k < 3; ++k) {
+            Tb[6 * i + 2 * k] = e1[k];
+            Tb[6 * i + 2 * k + 1] = e2[k];
+        }
+    }
+    int rc = SPO_OK;
+    for (long col = 0; col < M && !rc; ++col) {
+        long j = col / 2;
+        int a = (int)(col % 2);
+        memset(v, 0, sizeof(double) * 3 * N);
+        for (int k = 0; k < 3; ++k) v[3 * j + k] = Tb[6 * j + 2 * k + a];
+        rc = spo_hessian_apply(s, n, v, hv);
+        for (long row = 0; row < M && !rc; ++row) {
+            long i = row / 2;
+            int bb = (int)(row % 2);
+            double x = 0;
+            for (int k = 0; k < 3; ++k) x += Tb[6 * i + 2 * k + bb] * hv[3 * i + k];
+            H[row * M + col] = x;
+        }
+    }
+    if (T) memcpy(T, Tb, sizeof(double) * 6 * N);
+    free(Tb); free(v); free(hv);
+    return rc;
+}
+

@@ -168,6 +168,16 @@ int spo_mc_colours(const spo_system *s);
 int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
            double *cone, double *stats);
 
+/* Covariant Hessian (Sec. MMF and its appendix on the spin manifold): the
+ * action on v (N x 3, projected onto each spin's tangent plane first) of
+ * H v|_i = P_i sum_j Hbar_ij v_j - (n_i . grad_i Hbar) v_i, Hbar the second
+ * derivatives of the Hamiltonian continued to R^{3N} (no dipole term). */
+int spo_hessian_apply(const spo_system *s, const double *n, const double *v, double *out);
+/* The same operator as a dense 2N x 2N matrix in the tangent basis
+ * T_i = (e1_i, e2_i) (e1 = P_i x or P_i y normalised, e2 = n_i x e1), with
+ * the basis itself (N x 3 x 2) in T when not NULL. */
+int spo_hessian_dense(const spo_system *s, const double *n, double *H, double *T);
+
 /* Philox4x32-10 block (Salmon et al., SC'11). */
 void spo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* The three standard normals of the thermal field of spin i at step `step`. */

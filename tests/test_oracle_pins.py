@@ -901,3 +901,71 @@ def test_mc_cone_adapts_to_the_target_acceptance_and_limits():
     # at a very high temperature every trial is accepted
     _, _, sth = s.mc(x0[:1], [1e12], 5, seed=7, target_accept=0.0, sample=False, cone=[1.0])
     assert sth[0, 6] == sth[0, 7]
+
+
+# ----------------------------------------------------------------------------
+# Covariant Hessian and minimum mode following (Sec. MMF, manifold appendix)
+# ----------------------------------------------------------------------------
+def _retract(n, z, eps):
+    y = n + eps * z
+    return y / np.linalg.norm(y, axis=1, keepdims=True)
+
+
+def test_hessian_matches_finite_differences_of_the_riemannian_gradient():
+    # Hess f(x)[z] = P_x d/de grad f(R_x(e z)) at e = 0, with grad f = -P B;
+    # central differences along a retraction, projected back onto T_x
+    g = I.hexagonal(3, 3, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.4], K=[0.3], Khat=[[0.2, 0.3, 0.93]], B=[0.1, -0.4, 1.3])
+    s = oracle.System(g, h)
+    n = I.random_spins(s.N, 17)
+    H, T = s.hessian_dense(n)
+    assert np.abs(H - H.T).max() < 1e-12  # symmetric in the tangent basis
+
+    def rgrad(x):
+        B = s.field(x)
+        return -(B - np.sum(B * x, axis=1, keepdims=True) * x)
+
+    eps = 1e-5
+    for col in range(2 * s.N):
+        z = np.zeros((s.N, 3))
+        z[col // 2] = T[col // 2, :, col % 2]
+        d = (rgrad(_retract(n, z, eps)) - rgrad(_retract(n, z, -eps))) / (2 * eps)
+        d -= np.sum(d * n, axis=1, keepdims=True) * n
+        fd = np.einsum("ikc,ik->ic", T, d).reshape(-1)
+        assert np.abs(fd - H[:, col]).max() < 1e-7
+
+
+def test_hessian_of_the_ferromagnet_is_the_magnon_spectrum():
+    # n = z on an L x L periodic square lattice with B, K along z and exchange
+    # J: eigenvalues mu B + 2K + J (4 - 2 cos qx - 2 cos qy), each twice
+    L, mu, Bz, K, J = 4, 2.0, 0.7, 0.15, 1.0
+    s = oracle.System(I.square(L, L, periodic=(True, True), mu_s=mu), dict(J=[J], K=[K], Khat=[[0, 0, 1]], B=[0, 0, Bz]))
+    H, _ = s.hessian_dense(I.ferromagnet(s.N))
+    q = 2 * np.pi * np.arange(L) / L
+    lam = [mu * oracle.MU_B * Bz + 2 * K + J * (4 - 2 * np.cos(a) - 2 * np.cos(b)) for a in q for b in q]
+    assert np.allclose(np.sort(np.linalg.eigvalsh(H)), np.sort(lam + lam), rtol=0, atol=1e-12)
+
+
+def test_mmf_single_spin_climbs_onto_a_first_order_saddle():
+    # one spin: Zeeman along z, easy axis along x.  Started near the minimum,
+    # minimum mode following ends on a point with zero gradient and exactly
+    # one negative Hessian eigenvalue, which Newton's method confirms.
+    s = oracle.System(I.square(1, 1, mu_s=2.0), dict(B=[0, 0, 2.0], K=[0.3], Khat=[[1, 0, 0]]))
+    x0, _, _, _ = s.minimise(np.array([[0.9, 0.1, 0.4]]) / np.linalg.norm([0.9, 0.1, 0.4]), dt=0.1, tol=1e-12,
+                             max_iter=100000)
+    assert np.all(np.linalg.eigvalsh(s.hessian_dense(x0)[0]) > 0)
+    start = _retract(x0, np.array([[0.0, 0.3, -0.2]]), 0.3)
+    x, v, F, lam = s.mmf(start, 3000, dt=0.1)
+    assert np.abs(F).max() < 1e-9
+    ev = np.linalg.eigvalsh(s.hessian_dense(x)[0])
+    assert ev[0] < 0 < ev[1] and abs(lam - ev[0]) < 1e-12
+    # Newton on the Riemannian gradient from a perturbed start: same point
+    y = _retract(x, np.array([[1e-3, -2e-3, 1e-3]]), 1.0)
+    for _ in range(40):
+        Hy, Ty = s.hessian_dense(y)
+        B = s.field(y)
+        gr = -(B - np.sum(B * y, axis=1, keepdims=True) * y)
+        step = np.linalg.solve(Hy, -np.einsum("ikc,ik->ic", Ty, gr).reshape(-1))
+        y = _retract(y, np.einsum("ikc,ic->ik", Ty, step.reshape(-1, 2)), 1.0)
+    assert np.linalg.norm(y - x) < 1e-8
+    assert s.energy(x)[0] > s.energy(x0)[0]
