@@ -344,6 +344,44 @@ int sp_mc_sweeps(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const
                  double *cone_dev, double *stats_dev, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Covariant Hessian, lowest mode and minimum mode following (Sec. MMF and
+ * the appendix on the manifold of constant-length spins)
+ * ------------------------------------------------------------------------ */
+
+/* out = H v: the covariant Hessian of the energy at the configuration n_dev
+ * acting on v_dev (N records each; v is first projected per spin onto the
+ * tangent plane of n):  H v|_i = P_i (Hbar v)_i - (n_i . grad_i Hbar) v_i,
+ * Hbar the second derivatives of the Hamiltonian continued to R^{3N}
+ * (exchange, DMI, anisotropy; the Zeeman term is linear), grad_i Hbar = -B_i.
+ * out_dev is tangent; it must not alias v_dev.  No dipole term. */
+int sp_hessian_apply(sp_ctx *ctx, const void *n_dev, const void *v_dev, void *out_dev, void *stream);
+
+/* Lowest eigenvalue (*lambda, host) and unit eigenvector (mode_dev, N
+ * records, in/out: a non-zero mode_dev is the start vector, zero selects a
+ * fixed pseudo-random start) of the covariant Hessian at n_dev, by `krylov`
+ * (1..256) Lanczos steps with full reorthogonalisation.  In exact arithmetic
+ * krylov >= 2N gives the exact lowest pair.  Synchronises `stream`. */
+int sp_lowest_mode(sp_ctx *ctx, const void *n_dev, void *mode_dev, int krylov, double *lambda, void *stream);
+
+typedef struct {
+    double dt;    /* velocity-projection time step (> 0) */
+    double mass;  /* fictitious mass (> 0) */
+    int krylov;   /* Lanczos steps per lowest-mode evaluation (1..256) */
+} sp_mmf_params;
+
+/* n_iter iterations of minimum mode following: the velocity projection of
+ * Appendix D with the effective force F_eff = F - 2 (F.l) l, F the
+ * tangent-space force, l the lowest mode of the Hessian at the current
+ * state (recomputed by sp_lowest_mode at every force evaluation, started
+ * from the previous mode); where the lowest eigenvalue is not negative,
+ * F_eff = -(F.l) l (climbs along the lowest mode only).  n_dev, vel_dev and
+ * mode_dev (N records each) are carried in and out.  *max_force (host) =
+ * max_i |F_i| and *lambda the lowest eigenvalue at the final state.
+ * Synchronises `stream`. */
+int sp_mmf(sp_ctx *ctx, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf_params *p, int n_iter,
+           double *max_force, double *lambda, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free LLG stepping
  * ------------------------------------------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -55,6 +55,10 @@ class GNEBParams(C.Structure):
 IMAGE_KINDS = {"normal": 0, "climbing": 1, "falling": 2}
 
 
+class MMFParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("krylov", C.c_int)]
+
+
 class MCParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("sweep0", C.c_uint64), ("target_accept", C.c_double), ("sample", C.c_int)]
 
@@ -90,6 +94,9 @@ SIGNATURES = {
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
                                C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
+    "sp_hessian_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "sp_lowest_mode": (_i, [_vp, _vp, _vp, _i, C.POINTER(_d), _vp]),
+    "sp_mmf": (_i, [_vp, _vp, _vp, _vp, C.POINTER(MMFParams), _i, C.POINTER(_d), C.POINTER(_d), _vp]),
     "sp_mc_colours": (_i, [_vp, C.POINTER(_i)]),
     "sp_mc_sweeps": (_i, [_vp, _vp, _i, C.POINTER(_d), C.POINTER(MCParams), _i, _vp, _vp, _vp]),
     "sp_gneb_path": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -270,6 +277,29 @@ class Context:
         if charge:
             out["Q"] = Q
         return out
+
+    def hessian_apply(self, n, v, out=None):
+        out = torch.empty_like(n) if out is None else out
+        self._check(lib().sp_hessian_apply(self._h, self._spin_arg(n, "n"), self._spin_arg(v, "v"),
+                                           self._spin_arg(out, "out"), _stream()))
+        return out
+
+    def lowest_mode(self, n, mode=None, krylov=64):
+        """(lowest eigenvalue, unit mode [N, 4]); `mode` (updated in place) is the start vector."""
+        mode = torch.zeros_like(n) if mode is None else mode
+        lam = C.c_double()
+        self._check(lib().sp_lowest_mode(self._h, self._spin_arg(n, "n"), self._spin_arg(mode, "mode"), int(krylov),
+                                         C.byref(lam), _stream()))
+        return lam.value, mode
+
+    def mmf(self, n, vel, mode, n_iter, dt=0.1, mass=1.0, krylov=64):
+        """Minimum mode following in place; returns (max |F|, lowest eigenvalue)."""
+        p = MMFParams(float(dt), float(mass), int(krylov))
+        mf, lam = C.c_double(), C.c_double()
+        self._check(lib().sp_mmf(self._h, self._spin_arg(n, "n"), self._spin_arg(vel, "vel"),
+                                 self._spin_arg(mode, "mode"), C.byref(p), int(n_iter), C.byref(mf), C.byref(lam),
+                                 _stream()))
+        return mf.value, lam.value
 
     def mc_colours(self):
         n = C.c_int()

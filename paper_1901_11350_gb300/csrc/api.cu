@@ -452,6 +452,7 @@ int sp_destroy(sp_ctx *c)
     if (c->bdd.p) cudaFree(c->bdd.p);
     if (c->qbuf.p) cudaFree(c->qbuf.p);
     mc_scratch_destroy(c->mc);
+    hess_scratch_destroy(c->hess);
     dipole_destroy(c->dip);
     min_scratch_destroy(c->mins);
     delete c;

@@ -80,6 +80,8 @@ using namespace spgb_ctx;
 
 struct McScratch;  // Monte Carlo scratch (mc.cu)
 void mc_scratch_destroy(McScratch *m);
+struct HessScratch;  // Hessian / Lanczos / MMF scratch (hessian.cu)
+void hess_scratch_destroy(HessScratch *h);
 
 struct sp_ctx {
     int prec = SP_F32;
@@ -116,6 +118,7 @@ struct sp_ctx {
     DipolePlan *dip = nullptr;
     MinScratch *mins = nullptr;
     McScratch *mc = nullptr;
+    HessScratch *hess = nullptr;
     Profiler prof;
 };
 

@@ -563,3 +563,61 @@ def test_mc_fp32_samples_the_same_distribution():
         a, b = res["f64"][k], res["f32"][k]
         err = np.sqrt(a.var() / len(a) + b.var() / len(b))
         assert abs(a.mean() - b.mean()) < 5 * err + 1e-12, (k, a.mean(), b.mean(), err)
+
+
+HESS_CASE = (I.hexagonal(3, 3, periodic=(True, True), mu_s=2.0),
+             dict(J=[1.0], dmi_kind="interfacial", D=[0.4], K=[0.3], Khat=[[0.2, 0.3, 0.93]], B=[0.1, -0.4, 1.3]))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_hessian_apply_matches_oracle(prec, tol):
+    g, h = HESS_CASE
+    o = _oracle(g, h)
+    c = B.Context(g, h, prec)
+    n0 = I.random_spins(c.N, 17)
+    v0 = np.random.default_rng(2).standard_normal((c.N, 3))
+    out = c.hessian_apply(c.spins(n0), c.spins(v0))
+    ref = o.hessian_apply(n0, v0)
+    assert np.abs(_np(out) - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_lowest_mode_matches_dense_eigendecomposition():
+    g, h = HESS_CASE
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    n0 = I.random_spins(c.N, 17)
+    lam, mode = c.lowest_mode(c.spins(n0), krylov=2 * c.N)
+    lam_o, mode_o = o.lowest_mode(n0)
+    assert abs(lam - lam_o) <= 1e-10 * max(1.0, abs(lam_o))
+    assert abs(abs(np.sum(_np(mode) * mode_o)) - 1.0) < 1e-9
+
+
+def test_lowest_mode_of_a_large_ferromagnet_is_the_magnon_gap():
+    # 32 x 32 hexagonal ferromagnet along z, B and K along z, no DMI: the
+    # lowest eigenvalue is the q = 0 magnon, mu B + 2K
+    mu, Bz, K = 2.0, 0.8, 0.1
+    g = I.hexagonal(32, 32, periodic=(True, True), mu_s=mu)
+    c = B.Context(g, dict(J=[1.0], K=[K], Khat=[[0, 0, 1]], B=[0, 0, Bz]), "f64")
+    lam, _ = c.lowest_mode(c.spins(I.perturbed(I.ferromagnet(c.N), 0.0, 0)), krylov=120)
+    assert abs(lam - (mu * oracle.MU_B * Bz + 2 * K)) < 1e-8
+
+
+@pytest.mark.parametrize("case", ["single", "hex3"])
+def test_mmf_matches_oracle(case):
+    if case == "single":
+        g, h = I.square(1, 1, mu_s=2.0), dict(B=[0, 0, 2.0], K=[0.3], Khat=[[1, 0, 0]])
+        n0 = np.array([[0.82, 0.33, 0.47]])
+        it = 60
+    else:
+        g, h = HESS_CASE
+        n0 = I.perturbed(I.ferromagnet(9), 0.3, 4)
+        it = 15
+    n0 = n0 / np.linalg.norm(n0, axis=1, keepdims=True)
+    o = _oracle(g, h)
+    c = B.Context(g, h, "f64")
+    x, v, mode = c.spins(n0), c.spins(np.zeros_like(n0)), c.spins(np.zeros_like(n0))
+    mf, lam = c.mmf(x, v, mode, it, dt=0.1, krylov=2 * c.N)
+    xo, vo, Fo, lam_o = o.mmf(n0, it, dt=0.1)
+    assert np.abs(_np(x) - xo).max() <= 1e-9
+    assert abs(lam - lam_o) <= 1e-9 * max(1.0, abs(lam_o))
+    assert abs(mf - np.linalg.norm(Fo, axis=1).max()) <= 1e-9 * max(1.0, mf)
