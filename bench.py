@@ -513,6 +513,66 @@ def run_mc(args):
     return 0
 
 
+def run_hessian(args):
+    """Covariant Hessian-vector products on a 2048x2048 hexagonal monolayer
+    (FP32, interfacial DMI, anisotropy, field): product rate and HBM
+    roofline (algorithmic bytes: read n and v, write H v, 3 x 16 B per
+    spin); and the lowest mode of a 128x128 skyrmion state by 64 Lanczos
+    steps (FP64)."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import binding as Bd
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    build.build()
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0, 1.5])
+    g = I.hexagonal(2048, 2048, periodic=(True, True), mu_s=2.0)
+    c = Bd.Context(g, h, "f32")
+    N = c.N
+    n = c.spins(I.random_spins(N, 1))
+    v = c.spins(I.random_spins(N, 2))
+    out = torch.empty_like(n)
+    for _ in range(args.warmup):
+        c.hessian_apply(n, v, out)
+    K = 200
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(K):
+        c.hessian_apply(n, v, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    peaks, kind = measured_peaks()
+    gbs = 48.0 * N / (ms / 1e3) / 1e9
+    # lowest mode of a relaxed skyrmion (Lanczos, FP64)
+    g2 = I.hexagonal(128, 128, periodic=(True, True), mu_s=2.0)
+    c2 = Bd.Context(g2, h, "f64")
+    r = I.site_positions(g2)
+    x = c2.spins(I.neel_skyrmion(r, r.mean(axis=0), 6.0, I.SKYRMION_HELICITY))
+    c2.minimise(x, c2.spins(np.zeros((c2.N, 3))), dt=0.2, tol=1e-8, max_iter=20000)
+    c2.lowest_mode(x, krylov=8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, _ = c2.lowest_mode(x, krylov=64)
+    lanczos_s = time.perf_counter() - t0
+    out_j = {"metric": "covariant Hessian-vector products/s, 2048x2048 hexagonal monolayer (FP32)",
+             "value": 1e3 / ms, "unit": "products/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+             "data": "synthetic", "ms_per_step": ms,
+             "config": {"workload": "hessian_hex2048", "spins": N, "products_timed": K,
+                        "l2": "working set (201 MB) larger than L2"},
+             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                          "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": kind,
+                          "algorithmic_bytes_per_launch": 48 * N},
+             "lanczos": {"lattice": [128, 128], "state": "relaxed Neel skyrmion", "krylov": 64,
+                         "seconds": lanczos_s, "lowest_eigenvalue_meV": lam}}
+    print(json.dumps(out_j))
+    return 0
+
+
 def run_unet(args):
     """The warm-start network alone (BF16 U-Net, 128x128 inputs, batch 64):
     training samples/s of a full step (forward, backward, Adam) and
@@ -652,7 +712,7 @@ def main():
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
     ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
-    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30"])
+    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian"])
     ap.add_argument("--mc-sizes", default="10,15,20,30", help="mc30: lattice sides")
     ap.add_argument("--mc-thermal", type=int, default=10000, help="mc30: thermalisation sweeps")
     ap.add_argument("--mc-samples", type=int, default=100000, help="mc30: sampled sweeps")
@@ -682,6 +742,8 @@ def main():
         return run_unet(args)
     if args.workload == "mc30":
         return run_mc(args)
+    if args.workload == "hessian":
+        return run_hessian(args)
     return run_gpu(args)
 
 

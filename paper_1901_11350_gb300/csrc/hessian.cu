@@ -39,19 +39,42 @@ int grow_h(DevBuf &b, size_t bytes)
     return 0;
 }
 
+// H v with v projected onto the tangent planes on the fly: one pass over
+// the stencil loads n_j and v_j together and accumulates the field of n and
+// the field of the projected w without the Zeeman term.
 template <typename T>
 __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
-                                             const rec_t<T> *__restrict__ w, rec_t<T> *__restrict__ out)
+                                             const rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ out)
 {
     int i = blockIdx.x * kHB + threadIdx.x;
     if (i >= S.N) return;
-    int b;
-    v3<T> ni = ld(n, i), wi = ld(w, i);
-    v3<T> B = local_field(S, n, i, ni, b);
-    v3<T> Lw = local_field(S, w, i, wi, b);
-    v3<T> hb = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]) - Lw;  // -(field of w without Zeeman)
-    v3<T> r = hb - dot(hb, ni) * ni + dot(ni, B) * wi;
-    st(out, i, r);
+    int b = i % S.nb;
+    int r = i / S.nb;
+    int c0 = r % S.n0;
+    r /= S.n0;
+    int c1 = r % S.n1;
+    int c2 = r / S.n1;
+    v3<T> ni = ld(n, i), vi = ld(v, i);
+    v3<T> wi = vi - dot(vi, ni) * ni;
+    v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
+    v3<T> Bn = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]) + (T(2) * S.K[b] * dot(kh, ni)) * kh;
+    v3<T> Lw = (T(2) * S.K[b] * dot(kh, wi)) * kh;
+    for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
+        const NbrEntry<T> &E = S.e[q];
+        int x0 = wrap(c0 + E.d0, S.n0, S.per0);
+        int x1 = wrap(c1 + E.d1, S.n1, S.per1);
+        int x2 = wrap(c2 + E.d2, S.n2, S.per2);
+        if ((x0 | x1 | x2) < 0) continue;
+        int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+        v3<T> nj = ld(n, j), vj = ld(v, j);
+        v3<T> wj = vj - dot(vj, nj) * nj;
+        v3<T> D = mk(E.Dx, E.Dy, E.Dz);
+        Bn = axpy(E.J, nj, Bn + cross(nj, D));
+        Lw = axpy(E.J, wj, Lw + cross(wj, D));
+    }
+    // P (Hbar w) with Hbar w = -Lw, plus the Weingarten term (n . B) w
+    v3<T> r3 = (dot(Lw, ni) * ni - Lw) + dot(ni, Bn) * wi;
+    st(out, i, r3);
 }
 
 // out = v projected per spin onto the tangent plane of n
@@ -431,15 +454,11 @@ int sp_hessian_apply(sp_ctx *c, const void *n_dev, const void *v_dev, void *out_
     if (!n_dev || !v_dev || !out_dev) return hfail(c, SP_ERR_ARG, "NULL argument");
     if (v_dev == out_dev) return hfail(c, SP_ERR_ARG, "v and out must differ");
     cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = c->prec == SP_F64 ? setup<double>(c, 1) : setup<float>(c, 1))) return hfail(c, rc, "scratch");
     unsigned nb = hblocks(c->N);
-    if (c->prec == SP_F64) {
-        k_project<double><<<nb, kHB, 0, st>>>(c->N, (const dq4 *)n_dev, (const dq4 *)v_dev, (dq4 *)c->hess->w.p);
-        k_hvp<double><<<nb, kHB, 0, st>>>(c->Sd, (const dq4 *)n_dev, (const dq4 *)c->hess->w.p, (dq4 *)out_dev);
-    } else {
-        k_project<float><<<nb, kHB, 0, st>>>(c->N, (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)c->hess->w.p);
-        k_hvp<float><<<nb, kHB, 0, st>>>(c->Sf, (const float4 *)n_dev, (const float4 *)c->hess->w.p, (float4 *)out_dev);
-    }
+    if (c->prec == SP_F64)
+        k_hvp<double><<<nb, kHB, 0, st>>>(c->Sd, (const dq4 *)n_dev, (const dq4 *)v_dev, (dq4 *)out_dev);
+    else
+        k_hvp<float><<<nb, kHB, 0, st>>>(c->Sf, (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev);
     return cudaGetLastError() == cudaSuccess ? SP_OK : hfail(c, SP_ERR_CUDA, "Hessian launch failed");
 }
 
