@@ -20,7 +20,7 @@
 #include "ctx.h"
 
 struct McScratch {
-    DevBuf T, acc, sweep, part, cnt;
+    DevBuf T, acc, sweep, part, cnt, cosc;
     cudaStream_t gs = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -43,7 +43,7 @@ struct McColour {
 template <typename T>
 __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ x,
                                                         int n_rep, McColour col, const double *__restrict__ TK,
-                                                        const double *__restrict__ cone,
+                                                        const double *__restrict__ cosc,
                                                         const unsigned long long *__restrict__ sweep_dev,
                                                         uint64_t seed, unsigned long long *__restrict__ acc)
 {
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
         const T scale = T(2.3283064365386963e-10);
         T u0 = ((T)o.x + T(0.5)) * scale, u1 = ((T)o.y + T(0.5)) * scale, u2 = ((T)o.z + T(0.5)) * scale;
-        T ct = (T)cos(cone[rep]);
+        T ct = (T)cosc[rep];  // cos of the replica's cone angle
         T cth = T(1) - u1 * (T(1) - ct);
         T sth = sqrt(fmax(T(0), T(1) - cth * cth));
         T ph = T(6.283185307179586) * u0;
@@ -101,17 +101,23 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
 // After a sweep: acceptance into the statistics, the cone's feedback
 // (theta <- theta exp(ratio - target), kept in [1e-4, pi]) and the sweep
 // counter.
-__global__ void k_mc_cone(int n_rep, long long N, unsigned long long *acc, double *cone, double target, double *stats,
-                          unsigned long long *sweep_dev)
+__global__ void k_mc_cone(int n_rep, long long N, unsigned long long *acc, double *cone, double *cosc, double target,
+                          double *stats, unsigned long long *sweep_dev)
 {
     for (int r = threadIdx.x; r < n_rep; r += blockDim.x) {
         double a = (double)acc[r];
         stats[8 * r + 6] += a;
         stats[8 * r + 7] += (double)N;
         if (target > 0) cone[r] = fmin(3.141592653589793, fmax(1e-4, cone[r] * exp(a / (double)N - target)));
+        cosc[r] = cos(cone[r]);
         acc[r] = 0;
     }
     if (threadIdx.x == 0) *sweep_dev += 1;
+}
+
+__global__ void k_mc_cos(int n_rep, const double *cone, double *cosc)
+{
+    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) cosc[r] = cos(cone[r]);
 }
 
 // Observables of every replica: sum of n (3 components) and the energy
@@ -250,7 +256,7 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
     int bpr = (S.N + kMcBlock - 1) / kMcBlock;
     if (grow_buf(ms->T, sizeof(double) * n_rep) || grow_buf(ms->acc, sizeof(unsigned long long) * (n_rep + kMcBlock)) ||
         grow_buf(ms->sweep, sizeof(unsigned long long)) || grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) ||
-        grow_buf(ms->cnt, sizeof(unsigned) * n_rep))
+        grow_buf(ms->cnt, sizeof(unsigned) * n_rep) || grow_buf(ms->cosc, sizeof(double) * n_rep))
         return SP_ERR_CUDA;
     unsigned long long s0 = p->sweep0;
     if (cudaMemcpyAsync(ms->T.p, T_host, sizeof(double) * n_rep, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -261,16 +267,18 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
         return SP_ERR_CUDA;
     rec_t<T> *x = (rec_t<T> *)spins;
     const double *TK = (const double *)ms->T.p;
+    double *cosc = (double *)ms->cosc.p;
+    k_mc_cos<<<1, 256, 0, st>>>(n_rep, cone, cosc);
     unsigned long long *acc = (unsigned long long *)ms->acc.p, *sw = (unsigned long long *)ms->sweep.p;
     double *part = (double *)ms->part.p;
     unsigned *tk = (unsigned *)ms->cnt.p;
     auto sweep = [&](cudaStream_t ss) {
         for (const McColour &col : cols) {
             long long work = col.per * n_rep;
-            k_mc_colour<T><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(S, x, n_rep, col, TK, cone,
+            k_mc_colour<T><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(S, x, n_rep, col, TK, cosc,
                                                                                             sw, p->seed, acc);
         }
-        k_mc_cone<<<1, 256, 0, ss>>>(n_rep, (long long)S.N, acc, cone, p->target_accept, stats, sw);
+        k_mc_cone<<<1, 256, 0, ss>>>(n_rep, (long long)S.N, acc, cone, cosc, p->target_accept, stats, sw);
         if (p->sample) k_mc_sample<T><<<(unsigned)(bpr * n_rep), kMcBlock, 0, ss>>>(S, x, bpr, part, tk, stats);
     };
     int k = 0;
@@ -284,11 +292,11 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
                 return SP_ERR_CUDA;
         }
         struct Key {
-            const void *x, *cone, *stats, *temps, *acc, *sw, *part, *cnt;
+            const void *x, *cone, *stats, *temps, *acc, *sw, *part, *cnt, *cosc;
             uint64_t seed;
             double target;
             int sample, n_rep, prec;
-        } key{x, cone, stats, TK, acc, sw, part, tk, p->seed, p->target_accept, p->sample, n_rep, (int)sizeof(T)};
+        } key{x, cone, stats, TK, acc, sw, part, tk, cosc, p->seed, p->target_accept, p->sample, n_rep, (int)sizeof(T)};
         std::vector<char> gk(sizeof key + sizeof(Stencil<T>));
         memcpy(gk.data(), &key, sizeof key);
         memcpy(gk.data() + sizeof key, &S, sizeof(Stencil<T>));
@@ -326,7 +334,7 @@ int mfail(sp_ctx *c, int code, const char *msg)
 void mc_scratch_destroy(McScratch *m)
 {
     if (!m) return;
-    DevBuf *bufs[] = {&m->T, &m->acc, &m->sweep, &m->part, &m->cnt};
+    DevBuf *bufs[] = {&m->T, &m->acc, &m->sweep, &m->part, &m->cnt, &m->cosc};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
