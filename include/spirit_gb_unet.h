@@ -117,8 +117,9 @@ int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, voi
 
 /* Which kernel computes the 3x3 convolutions (forward and data gradient) of
  * this process: 1 (default) = tcgen05 MMAs with tensor-memory accumulators,
- * 0 = the mma.sync kernel.  SP_ERR_ARG for other values.  Not thread-safe:
- * set it before launching work. */
+ * 2 = the same with warp-specialised loads and MMA issue (mbarrier
+ * pipeline), 0 = the mma.sync kernel.  SP_ERR_ARG for other values.  Not
+ * thread-safe: set it before launching work. */
 int sp_conv3x3_set_kernel(int tcgen05);
 int sp_conv3x3_get_kernel(void);
 

@@ -408,6 +408,177 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
     if (failed && tid == 0) atomicExch(&g_tc_error, 1);
 }
 
+// ------------------------------------------------------------------ conv, tcgen05, warp-specialised
+// The same convolution with the loads and the MMAs decoupled: warps 0-6 load
+// stages with cp.async and signal each stage's "full" mbarrier when their
+// copies land (cp.async.mbarrier.arrive.noinc), one lane of warp 7 waits for
+// a full stage, makes the copies visible to the tensor cores' proxy, issues
+// the stage's MMAs and commits them to the stage's "empty" mbarrier, which
+// the loaders wait for before refilling it.  No CTA-wide barrier in the main
+// loop.  Input rows are read through L1 (cp.async.ca): the nine taps read
+// shifted copies of the same rows.  Every wait is bounded as in k_conv_tc.
+constexpr int kWsStages = 6;
+constexpr int kWsLoaders = 224;  // warps 0-6
+constexpr int kWsRows = (kBM * 4 + kWsLoaders - 1) / kWsLoaders;  // A chunks per loader (3)
+
+__device__ __forceinline__ void cp16_ca(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+
+__device__ __forceinline__ void cp_arrive_noinc(unsigned bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+constexpr size_t conv_ws_smem()
+{
+    return 1024 + (size_t)kWsStages * (kBM * 64 + BN * 64) + 16 * kWsStages + 16 + 16;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv_ws(ConvSrc S, const bf16 *__restrict__ Wk,
+                                                      const float *__restrict__ bias, int relu,
+                                                      const bf16 *__restrict__ mask, int H, int W, int Cout,
+                                                      bf16 *__restrict__ out)
+{
+    constexpr int A_BYTES = kBM * 64, STAGE = A_BYTES + BN * 64;
+    constexpr unsigned TCOLS = BN;
+    constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
+                               ((unsigned)(kBM >> 4) << 24);
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = smem_u32(smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;
+    const unsigned full0 = base + kWsStages * STAGE;  // kWsStages "full" barriers
+    const unsigned empty0 = full0 + 8 * kWsStages;    // kWsStages "empty" barriers
+    const unsigned done = empty0 + 8 * kWsStages;     // last MMA finished
+    const unsigned slot = done + 8;
+    volatile unsigned *slot_ptr = reinterpret_cast<volatile unsigned *>(smem_raw + (slot - raw));
+    __shared__ int s_fail;
+
+    const int Cin = S.C0 + S.C1, nkc = Cin / kBK, nk = 9 * nkc;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HW = H * W;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            mbar_init(full0 + 8 * s, kWsLoaders);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot_ptr;
+    int failed = 0;
+
+    if (warp < 7) {
+        // loaders: A chunks idx = tid + 224 j (512 of them), B chunks likewise;
+        // the pixel of each A chunk is decoded once
+        int pb[kWsRows], py[kWsRows], px[kWsRows];
+#pragma unroll
+        for (int j = 0; j < kWsRows; ++j) {
+            int idx = tid + kWsLoaders * j;
+            int p = m0 + (idx >> 2);
+            pb[j] = p / HW;
+            int q = p - pb[j] * HW;
+            py[j] = q / W;
+            px[j] = q - py[j] * W;
+        }
+        for (int k = 0; k < nk && !failed; ++k) {
+            const int s = k % kWsStages, u = k / kWsStages;
+            if (u > 0 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1)) {
+                failed = 1;
+                break;
+            }
+            const int t = k / nkc, cc = (k - t * nkc) * kBK;
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            const unsigned sa = base + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < kWsRows; ++j) {
+                int idx = tid + kWsLoaders * j;
+                if (idx < kBM * 4) {
+                    int r = idx >> 2, c = idx & 3;
+                    cp16_ca(sa + swz64(r, c),
+                            src_at(S, pb[j], wrap(py[j] + dy, H), wrap(px[j] + dx, W), H, W, cc + c * 8));
+                }
+            }
+            for (int idx = tid; idx < BN * 4; idx += kWsLoaders) {
+                int r = idx >> 2, c = idx & 3;
+                cp16(sb + swz64(r, c), Wk + (size_t)(n0 + r) * 9 * Cin + t * Cin + cc + c * 8);
+            }
+            cp_arrive_noinc(full0 + 8 * s);
+        }
+        // the copies above belong to no commit group: wait for all of them
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else if (lane == 0) {
+        // MMA issuer
+        int k = 0;
+        for (; k < nk; ++k) {
+            const int s = k % kWsStages, u = k / kWsStages;
+            if (!mbar_wait(full0 + 8 * s, u & 1)) {
+                failed = 1;
+                break;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            tc_fence_after();
+            const unsigned sa = base + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+                tc_mma(tmem, desc_sw64(sa + kk * 32), desc_sw64(sb + kk * 32), IDESC, (k > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(empty0 + 8 * s);
+        }
+        // completion of every MMA issued (possibly none)
+        tc_commit(done);
+        if (k < nk) failed = 1;
+    }
+    if (failed) s_fail = 1;
+    // wait for the accumulator (bounded), then every warp reads its lanes
+    if (!mbar_wait(done, 0)) failed = 1;
+    failed = __syncthreads_or(failed || s_fail);
+    tc_fence_after();
+    const int q = warp & 3, half = warp >> 2;
+    const int p = m0 + q * 32 + lane;
+#pragma unroll
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+        float v[16];
+        tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0, v);
+        if (failed) continue;
+        const int co = n0 + c0;
+        size_t o = (size_t)p * Cout + co;
+        __align__(16) bf16 mk[16];
+        if (mask) {
+            *reinterpret_cast<uint4 *>(mk) = *reinterpret_cast<const uint4 *>(mask + o);
+            *reinterpret_cast<uint4 *>(mk + 8) = *reinterpret_cast<const uint4 *>(mask + o + 8);
+        }
+        __align__(16) bf16 r[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            float x = v[e] + (bias ? bias[co + e] : 0.f);
+            if (relu) x = fmaxf(x, 0.f);
+            if (mask && !(__bfloat162float(mk[e]) > 0.f)) x = 0.f;
+            r[e] = __float2bfloat16(x);
+        }
+        *reinterpret_cast<uint4 *>(out + o) = *reinterpret_cast<const uint4 *>(r);
+        *reinterpret_cast<uint4 *>(out + o + 8) = *reinterpret_cast<const uint4 *>(r + 8);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+    if (failed && tid == 0) atomicExch(&g_tc_error, 1);
+}
+
 // ------------------------------------------------------------------ wgrad
 // part[z][co][t][ci] = sum over pixels p of split z of dz[p][co] in[p+off(t)][ci].
 // Grid (Cout/BMC, 9 * Cin/32, splits), 128 threads as 2 x 2 warps of
@@ -805,7 +976,7 @@ bool conv_shape_ok(int C0, int C1, int up0, int B, int H, int W, int Cout)
     return P < (1LL << 31) - 256;
 }
 
-int g_use_tc = 1;  // tcgen05 convolution (1, default) or the mma.sync one (0)
+int g_use_tc = 1;  // 0: mma.sync, 1: tcgen05 (default), 2: tcgen05 warp-specialised
 
 template <int BN>
 cudaError_t conv_tc_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask,
@@ -822,12 +993,34 @@ cudaError_t conv_tc_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const flo
     return cudaGetLastError();
 }
 
+template <int BN>
+cudaError_t conv_ws_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask,
+                           int H, int Wd, int Cout, bf16 *out, cudaStream_t st)
+{
+    static bool attr = false;
+    constexpr size_t sm = conv_ws_smem<BN>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_ws<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_conv_ws<BN><<<grid, kThreads, sm, st>>>(S, W, bias, relu, mask, H, Wd, Cout, out);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask, int B, int H,
                         int Wd, int Cout, bf16 *out, cudaStream_t st)
 {
     long long P = (long long)B * H * Wd;
     int bn = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
     dim3 grid((unsigned)(P / kBM), (unsigned)(Cout / bn));
+    if (g_use_tc == 2) {
+        switch (bn) {
+        case 128: return conv_ws_launch<128>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        case 64: return conv_ws_launch<64>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        default: return conv_ws_launch<32>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
+        }
+    }
     if (g_use_tc) {
         switch (bn) {
         case 128: return conv_tc_launch<128>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
@@ -1275,7 +1468,7 @@ int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, voi
 
 int sp_conv3x3_set_kernel(int tcgen05)
 {
-    if (tcgen05 != 0 && tcgen05 != 1) return SP_ERR_ARG;
+    if (tcgen05 < 0 || tcgen05 > 2) return SP_ERR_ARG;
     g_use_tc = tcgen05;
     return SP_OK;
 }

@@ -23,14 +23,15 @@ def _check_cuda(t, dtype, name):
 
 
 def set_conv_kernel(name):
-    """'tcgen05' (tensor-memory accumulators) or 'mma' (mma.sync)."""
-    rc = lib().sp_conv3x3_set_kernel({"mma": 0, "tcgen05": 1}[name])
+    """'tcgen05' (tensor-memory accumulators), 'tcgen05_ws' (the same with
+    warp-specialised loads and MMA issue) or 'mma' (mma.sync)."""
+    rc = lib().sp_conv3x3_set_kernel({"mma": 0, "tcgen05": 1, "tcgen05_ws": 2}[name])
     if rc:
         raise SpinError(rc, "bad kernel name")
 
 
 def conv_kernel():
-    return {0: "mma", 1: "tcgen05"}[lib().sp_conv3x3_get_kernel()]
+    return {0: "mma", 1: "tcgen05", 2: "tcgen05_ws"}[lib().sp_conv3x3_get_kernel()]
 
 
 def check_device_error():

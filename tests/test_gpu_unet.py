@@ -40,7 +40,7 @@ def rand_bf(rng, shape, scale=1.0):
     return t, f64(t)
 
 
-@pytest.fixture(params=["mma", "tcgen05"])
+@pytest.fixture(params=["mma", "tcgen05", "tcgen05_ws"])
 def kernel(request):
     old = UN.conv_kernel()
     UN.set_conv_kernel(request.param)
