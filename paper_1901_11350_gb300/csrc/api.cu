@@ -153,6 +153,9 @@ template <typename T> void fill_stencil(const sp_ctx *c, Stencil<T> &S)
     S.per1 = c->per[1];
     S.per2 = c->per[2];
     S.N = c->N;
+    S.fnb = make_fastdiv(c->nb);
+    S.fn0 = make_fastdiv(c->nc[0]);
+    S.fn1 = make_fastdiv(c->nc[1]);
     for (int b = 0; b < c->nb; ++b) {
         double mu = c->mu_s[b] * kMuB;
         S.mu[b] = (T)mu;

@@ -97,11 +97,38 @@ template <typename T> struct NbrEntry {
     T J, Dx, Dy, Dz;
 };
 
+// Division of a non-negative int below 2^31 by a fixed positive divisor d
+// as q = (umulhi(n, m) + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1 (Granlund and Montgomery, PLDI 1994):
+// a multiply-high, an add and a shift instead of a full integer division.
+struct FastDiv {
+    uint32_t m;
+    int s, d;
+};
+
+inline FastDiv make_fastdiv(int d)
+{
+    FastDiv f;
+    f.d = d;
+    f.s = 0;
+    while ((1LL << f.s) < (long long)d) ++f.s;
+    unsigned long long one = 1;
+    f.m = (uint32_t)(((one << 32) * ((one << f.s) - (unsigned long long)d)) / (unsigned long long)d + 1);
+    return f;
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f)
+{
+    uint32_t t = __umulhi((uint32_t)n, f.m);
+    return (int)((t + (uint32_t)n) >> f.s);
+}
+
 // Everything a kernel needs to evaluate the local part of Eq. 1 at a spin:
 // lattice extents, per-basis on-site terms and the neighbour stencil.  Passed
 // by value as a __grid_constant__ kernel parameter (about 3-5 KB).
 template <typename T> struct Stencil {
     int nb, n0, n1, n2, per0, per1, per2, N;
+    FastDiv fnb, fn0, fn1;      // division by nb, n0, n1
     int off[SP_MAX_BASIS + 1];  // entries of basis b: [off[b], off[b+1])
     T mu[SP_MAX_BASIS];         // mu_b mu_B, meV/T
     T Bz[SP_MAX_BASIS][3];      // Zeeman field mu_b mu_B B, meV
@@ -121,17 +148,25 @@ __device__ __forceinline__ int wrap(int x, int n, int per)
     return (x < 0 || x >= n) ? -1 : x;
 }
 
+// Spin index i = b + nb (c0 + n0 (c1 + n1 c2)) -> (b, c0, c1, c2).
+template <typename T>
+__device__ __forceinline__ void decode_site(const Stencil<T> &S, int i, int &b, int &c0, int &c1, int &c2)
+{
+    int r = fdiv(i, S.fnb);
+    b = i - r * S.nb;
+    int r1 = fdiv(r, S.fn0);
+    c0 = r - r1 * S.n0;
+    c2 = fdiv(r1, S.fn1);
+    c1 = r1 - c2 * S.n1;
+}
+
 // Local part of B_eff = -dH/dn at spin i (Eq. 1 without the dipole term):
 // mu_i B + 2 K (Khat.n_i) Khat + sum_j [J_ij n_j + n_j x D_ij].
 template <typename T, typename R>
 __device__ __forceinline__ v3<T> local_field(const Stencil<T> &S, const R *n, int i, v3<T> ni, int &b)
 {
-    b = i % S.nb;
-    int r = i / S.nb;
-    int c0 = r % S.n0;
-    r /= S.n0;
-    int c1 = r % S.n1;
-    int c2 = r / S.n1;
+    int c0, c1, c2;
+    decode_site(S, i, b, c0, c1, c2);
     T kn = dot(mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]), ni);
     T k2 = T(2) * S.K[b] * kn;
     v3<T> B = mk(fma(k2, S.Kh[b][0], S.Bz[b][0]), fma(k2, S.Kh[b][1], S.Bz[b][1]), fma(k2, S.Kh[b][2], S.Bz[b][2]));

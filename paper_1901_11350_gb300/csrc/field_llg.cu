@@ -182,12 +182,8 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double tmax = 0;
     if (i < S.N) {
-        int b = i % S.nb;
-        int r = i / S.nb;
-        int c0 = r % S.n0;
-        r /= S.n0;
-        int c1 = r % S.n1;
-        int c2 = r / S.n1;
+        int b, c0, c1, c2;
+        decode_site(S, i, b, c0, c1, c2);
         v3<T> ni = ld(n, i);
         v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
         v3<T> Kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);

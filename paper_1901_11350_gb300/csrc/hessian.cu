@@ -48,12 +48,8 @@ __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> 
 {
     int i = blockIdx.x * kHB + threadIdx.x;
     if (i >= S.N) return;
-    int b = i % S.nb;
-    int r = i / S.nb;
-    int c0 = r % S.n0;
-    r /= S.n0;
-    int c1 = r % S.n1;
-    int c2 = r / S.n1;
+    int b, c0, c1, c2;
+    decode_site(S, i, b, c0, c1, c2);
     v3<T> ni = ld(n, i), vi = ld(v, i);
     v3<T> wi = vi - dot(vi, ni) * ni;
     v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
