@@ -513,6 +513,67 @@ def run_mc(args):
     return 0
 
 
+def run_square32(args):
+    """32x32 square lattice, open, J=1, interfacial D=0.3, K=0.1 z, B=1 T z,
+    mu_s=2: 1000 deterministic Depondt steps in FP64 (dt=1e-3 ps,
+    alpha=0.3) on the default path, with the other paths timed beside it
+    (single CTA, 27-point, generic; and FP32); the oracle on the host cores."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import binding as Bd
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    build.build()
+    cfg = I.cfg_square_32()
+    g, h, r = cfg["geometry"], cfg["hamiltonian"], cfg["run"]
+    kw = dict(solver=r["solver"], dt=r["dt"], alpha=r["alpha"])
+    S = r["n_steps"]
+    res = {}
+    st = torch.cuda.current_stream()
+    # default: FP64 per-spin kernels in small blocks over many SMs; cubic: the
+    # 27-point path; f32_*: the FP32 single-CTA path and the FP32 per-spin
+    # kernels with one launch per pass
+    for path in ("default", "cubic", "f32_single_cta", "f32_generic"):
+        c = Bd.Context(g, h, "f32" if path.startswith("f32") else "f64")
+        c.set_option("small_path", 1 if path in ("default", "f32_single_cta") else 0)
+        if path == "f32_generic":
+            c.set_option("generic_stencil", 1)
+        n = c.spins(I.random_spins(c.N, cfg["spin_seed"]))
+        for _ in range(args.warmup):
+            c.llg_step(n, S, **kw)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            ev[k][0].record(st)
+            c.llg_step(n, S, **kw)
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        res[path] = ms
+    N = 1024
+    out = {"metric": "LLG steps/s, 32x32 square lattice, FP64 Depondt (1000 steps per run)",
+           "value": S / (res["default"] / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["default"], "higher_is_better": True, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S},
+           "paths_ms_per_run": res, "spin_updates_per_s": N * S / (res["default"] / 1e3)}
+    if not args.no_cpu_baseline:
+        import oracle
+        o = oracle.System(g, h)
+        x = I.random_spins(N, cfg["spin_seed"])
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 5.0:
+            x = o.llg(x, 50, **kw)
+            k += 50
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k / sec, "unit": "steps/s", "cores": oracle.threads(), "kind": "oracle",
+                               "sample": "%d FP64 Depondt steps of the same lattice, %.1f s" % (k, sec)}
+    print(json.dumps(out))
+    return 0
+
+
 def run_hessian(args):
     """Covariant Hessian-vector products on a 2048x2048 hexagonal monolayer
     (FP32, interfacial DMI, anisotropy, field): product rate and HBM
@@ -712,7 +773,8 @@ def main():
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
     ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
-    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian"])
+    ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian",
+                                                        "square32"])
     ap.add_argument("--mc-sizes", default="10,15,20,30", help="mc30: lattice sides")
     ap.add_argument("--mc-thermal", type=int, default=10000, help="mc30: thermalisation sweeps")
     ap.add_argument("--mc-samples", type=int, default=100000, help="mc30: sampled sweeps")
@@ -744,6 +806,8 @@ def main():
         return run_mc(args)
     if args.workload == "hessian":
         return run_hessian(args)
+    if args.workload == "square32":
+        return run_square32(args)
     return run_gpu(args)
 
 

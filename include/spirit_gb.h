@@ -432,7 +432,14 @@ enum {
     /* value 1: evaluate the dipole field with the radix-2 shared-memory FFT
      * kernels even where the FP32 warp-FFT path (1024 x 1024 padded grid)
      * applies; 0: default */
-    SP_OPT_GENERIC_FFT = 4
+    SP_OPT_GENERIC_FFT = 4,
+    /* 1 (default): lattices of at most 2048 spins without the dipole term,
+     * stepped with Depondt, Heun or SIB, take the small-lattice paths: in
+     * FP32 one CTA keeps the lattice in shared memory and runs all steps of
+     * a call in the kernel; in FP64 the per-spin kernels run in small
+     * blocks spread over the SMs (both with the generic path's per-spin
+     * arithmetic); 0: never */
+    SP_OPT_SMALL_PATH = 5
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose SP_OPT_PLANES_PER_CTA by measurement: times the LLG predictor pass

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -335,6 +336,16 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
     bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
     LlgConst<T> k = llg_const<T>(c, p);
+    if (c->use_small && c->N <= kSmallMax && c->h.dipole == SP_DIPOLE_NONE && !rk4 && !c->prof.on) {
+        if (std::is_same<T, float>::value) {
+            // whole steps inside one CTA (the lattice fits in shared memory)
+            k.step = p->step0;
+            cudaError_t e = launch_llg_small(p->solver, *(const Stencil<float> *)&S, (float4 *)nn,
+                                             *(const LlgConst<float> *)&k, n_steps, st);
+            return e == cudaSuccess ? SP_OK : cuda_fail(c, e, "small-lattice LLG launch");
+        }
+        cub = false;  // FP64: per-spin kernels in small blocks over many SMs
+    }
     for (int s = 0; s < n_steps; ++s) {
         k.step = p->step0 + (uint64_t)s;
         const void *bd;
@@ -852,6 +863,10 @@ int sp_set_option(sp_ctx *c, int option, int value)
 {
     if (!c) return SP_ERR_ARG;
     switch (option) {
+    case SP_OPT_SMALL_PATH:
+        if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "small_path takes 0 or 1");
+        c->use_small = value == 1;
+        return SP_OK;
     case SP_OPT_GENERIC_STENCIL:
         c->use_cubic = value == 0;
         return SP_OK;
@@ -896,6 +911,9 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_GENERIC_FFT:
         *value = c->generic_fft ? 1 : 0;
+        return SP_OK;
+    case SP_OPT_SMALL_PATH:
+        *value = c->use_small ? 1 : 0;
         return SP_OK;
     default:
         return SP_ERR_ARG;

@@ -81,6 +81,39 @@ __device__ __forceinline__ v3<double> ldc(const dq4 *p, long i)
     double2 a = q[0], b = q[1];
     return {a.x, a.y, b.x};
 }
+// Records held in shared memory: distinct types so that ld/ldc/st resolve to
+// plain loads (never the read-only global path of ld above).
+struct sh4f {
+    float4 v;
+};
+struct sh4d {
+    double2 a, b;
+};
+template <typename T> struct ShRec;
+template <> struct ShRec<float> {
+    typedef sh4f type;
+};
+template <> struct ShRec<double> {
+    typedef sh4d type;
+};
+__device__ __forceinline__ v3<float> ld(const sh4f *p, long i)
+{
+    float4 v = p[i].v;
+    return {v.x, v.y, v.z};
+}
+__device__ __forceinline__ v3<double> ld(const sh4d *p, long i)
+{
+    double2 a = p[i].a, b = p[i].b;
+    return {a.x, a.y, b.x};
+}
+__device__ __forceinline__ v3<float> ldc(const sh4f *p, long i) { return ld(p, i); }
+__device__ __forceinline__ v3<double> ldc(const sh4d *p, long i) { return ld(p, i); }
+__device__ __forceinline__ void st(sh4f *p, long i, v3<float> v) { p[i].v = make_float4(v.x, v.y, v.z, 0.f); }
+__device__ __forceinline__ void st(sh4d *p, long i, v3<double> v)
+{
+    p[i].a = make_double2(v.x, v.y);
+    p[i].b = make_double2(v.z, 0.0);
+}
 __device__ __forceinline__ void st(float4 *p, long i, v3<float> v) { p[i] = make_float4(v.x, v.y, v.z, 0.f); }
 __device__ __forceinline__ void st(dq4 *p, long i, v3<double> v)
 {

@@ -106,6 +106,7 @@ struct sp_ctx {
     bool cubic = false;
     bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
     bool generic_fft = false;  // SP_OPT_GENERIC_FFT
+    bool use_small = true;     // SP_OPT_SMALL_PATH
     int zc = 0;             // units per CTA of the 27-point path; 0 = balanced (see cubic_per)
     int zc_auto = 0;        // balanced value, computed on first use
     CubicParams<float> Cf = {};

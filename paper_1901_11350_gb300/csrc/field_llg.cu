@@ -42,13 +42,12 @@ cudaError_t launch_field(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> 
 }
 
 // ---------------------------------------------------------------- LLG
-template <typename T, int SOLVER>
-__global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
-                                                     const rec_t<T> *__restrict__ Bdd, rec_t<T> *__restrict__ np,
-                                                     rec_t<T> *__restrict__ q, const LlgConst<T> c)
+// Per-spin bodies of the two passes, shared by the grid kernels (records in
+// global memory) and the single-CTA kernel (records in shared memory).
+template <typename T, int SOLVER, typename R>
+__device__ __forceinline__ void pred_spin(const Stencil<T> &S, const R *n, const rec_t<T> *Bdd, R *np, R *q,
+                                          const LlgConst<T> &c, int i)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.N) return;
     int b;
     v3<T> ni = ld(n, i);
     v3<T> B = local_field(S, n, i, ni, b);
@@ -74,13 +73,10 @@ __global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Ste
     }
 }
 
-template <typename T, int SOLVER>
-__global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ n,
-                                                     const rec_t<T> *__restrict__ np, const rec_t<T> *__restrict__ q,
-                                                     const rec_t<T> *__restrict__ Bdd, const LlgConst<T> c)
+template <typename T, int SOLVER, typename R>
+__device__ __forceinline__ void corr_spin(const Stencil<T> &S, R *n, const R *np, const R *q, const rec_t<T> *Bdd,
+                                          const LlgConst<T> &c, int i)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.N) return;
     int b;
     v3<T> p = ld(np, i);
     v3<T> B = local_field(S, np, i, p, b);
@@ -97,17 +93,91 @@ __global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Ste
     }
 }
 
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
+                                                     const rec_t<T> *__restrict__ Bdd, rec_t<T> *__restrict__ np,
+                                                     rec_t<T> *__restrict__ q, const LlgConst<T> c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    pred_spin<T, SOLVER>(S, n, Bdd, np, q, c, i);
+}
+
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ n,
+                                                     const rec_t<T> *__restrict__ np, const rec_t<T> *__restrict__ q,
+                                                     const rec_t<T> *__restrict__ Bdd, const LlgConst<T> c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.N) return;
+    corr_spin<T, SOLVER>(S, n, np, q, Bdd, c, i);
+}
+
+// Small FP32 lattices (N <= kSmallMax): one CTA keeps n, np and q in shared
+// memory and runs every step in the kernel, a CTA barrier between the passes
+// -- the same per-spin arithmetic as the two grid kernels, without 2 launches
+// per step.  (FP64 is not sent here: its rate per SM is low, and spreading
+// the spins over the SMs with small blocks is faster.)
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kSmallThreads) k_llg_small(const __grid_constant__ Stencil<T> S,
+                                                             rec_t<T> *__restrict__ ng, LlgConst<T> c, int n_steps)
+{
+    typedef typename ShRec<T>::type R;
+    extern __shared__ __align__(16) unsigned char smem_small[];
+    R *n = reinterpret_cast<R *>(smem_small);
+    R *np = n + S.N, *q = np + S.N;
+    for (int i = threadIdx.x; i < S.N; i += blockDim.x) st(n, i, ldc(ng, i));
+    __syncthreads();
+    const uint64_t step0 = c.step;
+    for (int s = 0; s < n_steps; ++s) {
+        c.step = step0 + (uint64_t)s;
+        for (int i = threadIdx.x; i < S.N; i += blockDim.x) pred_spin<T, SOLVER>(S, (const R *)n, nullptr, np, q, c, i);
+        __syncthreads();
+        for (int i = threadIdx.x; i < S.N; i += blockDim.x)
+            corr_spin<T, SOLVER>(S, n, (const R *)np, (const R *)q, nullptr, c, i);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < S.N; i += blockDim.x) st(ng, i, ld(n, i));
+}
+
+cudaError_t launch_llg_small(int solver, const Stencil<float> &S, float4 *n, const LlgConst<float> &c, int n_steps,
+                             cudaStream_t st)
+{
+    typedef float T;
+    if (S.N == 0 || n_steps == 0) return cudaSuccess;
+    size_t sm = 3 * sizeof(typename ShRec<T>::type) * (size_t)S.N;
+    static bool attr[3] = {false, false, false};
+    int slot = solver == SP_HEUN ? 0 : (solver == SP_SIB ? 1 : 2);
+    const void *fn = solver == SP_HEUN ? (const void *)k_llg_small<T, SP_HEUN>
+                                       : (solver == SP_SIB ? (const void *)k_llg_small<T, SP_SIB>
+                                                           : (const void *)k_llg_small<T, SP_DEPONDT>);
+    if (!attr[slot]) {
+        int max_sm = (int)(3 * sizeof(typename ShRec<T>::type) * kSmallMax);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_sm);
+        if (e != cudaSuccess) return e;
+        attr[slot] = true;
+    }
+    if (solver == SP_HEUN)
+        k_llg_small<T, SP_HEUN><<<1, kSmallThreads, sm, st>>>(S, n, c, n_steps);
+    else if (solver == SP_SIB)
+        k_llg_small<T, SP_SIB><<<1, kSmallThreads, sm, st>>>(S, n, c, n_steps);
+    else
+        k_llg_small<T, SP_DEPONDT><<<1, kSmallThreads, sm, st>>>(S, n, c, n_steps);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *np,
                             rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
+    int bs = llg_block(S.N);
     if (solver == SP_HEUN)
-        k_llg_pred<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_HEUN><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
     else if (solver == SP_SIB)
-        k_llg_pred<T, SP_SIB><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_SIB><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
     else
-        k_llg_pred<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_DEPONDT><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
     return cudaGetLastError();
 }
 
@@ -116,12 +186,13 @@ cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const 
                             const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
+    int bs = llg_block(S.N);
     if (solver == SP_HEUN)
-        k_llg_corr<T, SP_HEUN><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_HEUN><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
     else if (solver == SP_SIB)
-        k_llg_corr<T, SP_SIB><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_SIB><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
     else
-        k_llg_corr<T, SP_DEPONDT><<<blocks_for(S.N), kBlock, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_DEPONDT><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
     return cudaGetLastError();
 }
 

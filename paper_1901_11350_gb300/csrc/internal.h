@@ -16,11 +16,29 @@ template <typename T> struct LlgConst {
 };
 
 constexpr int kBlock = 256;
+// single-CTA LLG path for small FP32 lattices: threads of the CTA, largest
+// lattice (3 records of 16 B per spin in shared memory: 96 KB)
+constexpr int kSmallThreads = 512;
+constexpr int kSmallMax = 2048;
 inline int blocks_for(long n, int bs = kBlock) { return (int)((n + bs - 1) / bs); }
+// Threads per block of the per-spin LLG kernels: 256, or fewer for lattices
+// too small to give every SM of the device a block of 256 (at least 32), so
+// that the work spreads over the SMs -- it matters for FP64, whose rate per
+// SM is low.
+inline int llg_block(long n)
+{
+    const long sms = 152;
+    if (n >= sms * kBlock) return kBlock;
+    long per = (n + sms - 1) / sms;
+    int bs = (int)((per + 31) / 32 * 32);
+    return bs < 32 ? 32 : bs;
+}
 
 template <typename T>
 cudaError_t launch_field(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *out, T sign,
                          cudaStream_t st);
+cudaError_t launch_llg_small(int solver, const Stencil<float> &S, float4 *n, const LlgConst<float> &c, int n_steps,
+                             cudaStream_t st);
 template <typename T>
 cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *np,
                             rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st);

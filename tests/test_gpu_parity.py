@@ -97,9 +97,15 @@ CUBIC = ["square32_open", "sc_periodic_ragged", "sc_periodic_n2", "single_spin"]
 
 
 def _ctx(g, h, prec, path):
+    # "default": the library's choice (the single-CTA path for these small
+    # lattices); "generic": one launch per pass with the neighbour-table
+    # stencil; "cubic": the 27-point plane-streaming path
     c = B.Context(g, h, prec)
     if path == "generic":
         c.set_option("generic_stencil", 1)
+        c.set_option("small_path", 0)
+    elif path == "cubic":
+        c.set_option("small_path", 0)
     return c
 
 
@@ -112,10 +118,10 @@ def test_cubic_path_detection():
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("solver", ["depondt", "heun", "sib", "rk4"])
 @pytest.mark.parametrize("T", [0.0, 10.0])
-@pytest.mark.parametrize("path", ["default", "generic"])
+@pytest.mark.parametrize("path", ["default", "generic", "cubic"])
 def test_llg_step_fp64(name, solver, T, path):
-    if path == "generic" and name not in CUBIC:
-        pytest.skip("generic is the default path here")
+    if path == "cubic" and name not in CUBIC:
+        pytest.skip("no 27-point path for this lattice")
     g, h = CASES[name]
     o = _oracle(g, h)
     c = _ctx(g, h, "f64", path)
@@ -621,3 +627,22 @@ def test_mmf_matches_oracle(case):
     assert np.abs(_np(x) - xo).max() <= 1e-9
     assert abs(lam - lam_o) <= 1e-9 * max(1.0, abs(lam_o))
     assert abs(mf - np.linalg.norm(Fo, axis=1).max()) <= 1e-9 * max(1.0, mf)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("solver", ["depondt", "heun", "sib"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_small_lattice_path_equals_the_multi_launch_path(name, solver, prec):
+    # the single-CTA kernel runs the grid kernels' per-spin code from shared
+    # memory: the same bits after many steps, with and without the noise
+    g, h = CASES[name]
+    if h.get("dipole", "none") != "none":
+        pytest.skip("the dipole term is not on the single-CTA path")
+    for T in (0.0, 10.0):
+        a, b = _ctx(g, h, prec, "default"), _ctx(g, h, prec, "generic")
+        n0 = I.random_spins(a.N, 21)
+        kw = dict(solver=solver, dt=2e-3, alpha=0.2, T=T, seed=5, step0=77, replica=1)
+        x, y = a.spins(n0), b.spins(n0)
+        a.llg_step(x, 40, **kw)
+        b.llg_step(y, 40, **kw)
+        assert torch.equal(x, y), (name, solver, prec, T)
