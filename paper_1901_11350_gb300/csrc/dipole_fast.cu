@@ -187,10 +187,13 @@ __device__ __forceinline__ void cp16(void *smem, const void *gmem)
 
 __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, const float *__restrict__ Kt)
 {
+    // The transpose tiles are live only inside the transforms and the spectra
+    // only between them, so they share memory (barriers between the phases):
+    // 49 KB per block, four blocks per SM, all 513 columns in one wave.
     extern __shared__ float2 sm[];
-    float2 *spec = sm;                                  // [3][1024]
-    float2 *tr = sm + 3 * 1024 + (threadIdx.x / 32) * kTr;
-    float *ks = reinterpret_cast<float *>(sm + 3 * 1024 + 3 * kTr);  // [6][1024]
+    float2 *spec = sm;                                  // [3][1024], between the transforms
+    float2 *tr = sm + (threadIdx.x / 32) * kTr;         // [3][kTr], inside the transforms
+    float *ks = reinterpret_cast<float *>(sm + 3 * kTr);  // [6][1024]
     int c = threadIdx.x / 32, lane = threadIdx.x % 32;
     int kx = blockIdx.x;
     const float *K = Kt + (long)kx * 6 * 1024;
@@ -204,6 +207,7 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
         a[n2] = y < n1 ? col[y] : make_float2(0.f, 0.f);
     }
     fft1024<false>(a, tr, lane, twiddles(lane, false));
+    __syncthreads();  // every warp is done with its transpose tile
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) spec[c * 1024 + lane + 32 * k1] = a[k1];
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -219,6 +223,7 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
         float2 X = spec[ky], Y = spec[1024 + ky], Z = spec[2048 + ky];
         a[n2] = make_float2(r0 * X.x + r1 * Y.x + r2 * Z.x, r0 * X.y + r1 * Y.y + r2 * Z.y);
     }
+    __syncthreads();  // every warp has read the spectra before the tiles reuse them
     fft1024<true>(a, tr, lane, twiddles(lane, true));
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) {
@@ -279,7 +284,8 @@ __global__ void __launch_bounds__(64 * kRows) k_irows(int n0, int n1, const floa
 }
 
 constexpr size_t kRowSmem = sizeof(float2) * (3 * 513 * kRows + 2 * kRows * kTr) + sizeof(float) * kRows * 512;
-constexpr size_t kColSmem = sizeof(float2) * (3 * 1024 + 3 * kTr) + sizeof(float) * 6 * 1024;
+constexpr size_t kColSmem = sizeof(float2) * (3 * kTr) + sizeof(float) * 6 * 1024;
+static_assert(3 * kTr >= 3 * 1024, "the transpose tiles must cover the spectra they alias");
 
 }  // namespace
 
