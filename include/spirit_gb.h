@@ -442,14 +442,16 @@ enum {
     SP_OPT_SMALL_PATH = 5
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
-/* Choose SP_OPT_PLANES_PER_CTA by measurement: times the LLG predictor pass
- * of the 27-point path (Heun with the thermal field on; it reads n_dev and
- * writes only context scratch, so the spins are unchanged) with CUDA events
- * on `stream` for the balanced split, finer splits and a few fixed run
- * lengths, and keeps the fastest.  Allocates
+/* Choose the work per CTA of the 27-point path by measurement, for each pass
+ * separately (the passes have different register budgets and occupancy):
+ * times the LLG predictor and corrector passes (Heun with the thermal field
+ * on; they read n_dev and write only context scratch, so the spins are
+ * unchanged) with CUDA events on `stream` for the balanced split, finer
+ * splits and a few fixed run lengths, and keeps the fastest of each.  Allocates
  * the LLG scratch if needed and synchronises `stream`.  SP_OK without effect
  * when the 27-point path does not apply.  *chosen (host, may be NULL)
- * receives the value kept. */
+ * receives the predictor's value (SP_OPT_PLANES_PER_CTA reads it back;
+ * setting that option applies one value to both passes again). */
 int sp_autotune(sp_ctx *ctx, const void *n_dev, int *chosen, void *stream);
 int sp_get_option(const sp_ctx *ctx, int option, int *value);
 

@@ -272,6 +272,7 @@ void detect_cubic(sp_ctx *c)
     fill_cubic(c, J, D, Jc, c->Cf);
     fill_cubic(c, J, D, Jc, c->Cd);
     c->zc_auto = 0;  // recomputed for the new lattice on first use
+    c->zc_auto_corr = 0;
     c->cubic = true;
 }
 
@@ -371,7 +372,7 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
-        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, cubic_per(c), st)
+        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, cubic_per(c, 1), st)
                 : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
@@ -385,56 +386,69 @@ namespace {
 
 template <typename T> int autotune_run(sp_ctx *c, const void *n, int *chosen, cudaStream_t st)
 {
-    int rc = ensure(c, c->pred, 2 * sizeof(rec_t<T>) * (size_t)c->N);
+    // np, q, and the corrector's output (the caller's spins are only read)
+    int rc = ensure(c, c->pred, 3 * sizeof(rec_t<T>) * (size_t)c->N);
     if (rc) return rc;
     rec_t<T> *np = (rec_t<T> *)c->pred.p;
-    rec_t<T> *q = np + c->N;
+    rec_t<T> *q = np + c->N, *out = q + c->N;
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
     sp_llg_params p{SP_HEUN, 1e-3, 0.1, 10.0, 0, 0, 0};
     LlgConst<T> k = llg_const<T>(c, &p);
     k.step = 0;
-    // candidates: the balanced single-wave split and finer ones (more CTAs,
-    // shorter runs of planes), plus a few fixed run lengths
-    int user = c->zc;
-    c->zc = 0;
-    int bal = cubic_per(c);
-    c->zc = user;
-    std::vector<int> cands = {bal, (bal + 1) / 2, (bal + 2) / 3, (bal + 3) / 4, (bal + 5) / 6, 4, 8, 16, 32};
-    std::sort(cands.begin(), cands.end());
-    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, SP_ERR_CUDA, "cudaEventCreate");
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return fail(c, SP_ERR_CUDA, "cudaEventCreate");
     }
-    float best = 1e30f;
-    int best_per = bal;
+    auto launch = [&](int pass, int per) {
+        return pass == 0 ? launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st)
+                         : launch_cubic<T>(1, SP_HEUN, CP, np, nullptr, q, out, nullptr, k, per, st);
+    };
+    int user = c->zc, user_corr = c->zc_corr;
+    c->zc = 0;
+    c->zc_corr = 0;
+    int best_of[2] = {1, 1};
     cudaError_t e = cudaSuccess;
-    for (int per : cands) {
-        if (per < 1) continue;
-        e = launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st);  // warm-up
-        float t = 0;
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-            e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            t += ms;
-        }
-        if (e != cudaSuccess) break;
-        if (t < best) {
-            best = t;
-            best_per = per;
+    // each pass: the balanced single-wave split for its own occupancy and
+    // finer ones (more CTAs, shorter runs of planes), plus fixed run lengths
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        int bal = cubic_per(c, pass);
+        std::vector<int> cands = {bal, (bal + 1) / 2, (bal + 2) / 3, (bal + 3) / 4, (bal + 5) / 6, 4, 8, 16, 32};
+        std::sort(cands.begin(), cands.end());
+        cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+        if (pass == 1) e = launch(0, bal);  // the corrector reads the predictor's output
+        float best = 1e30f;
+        best_of[pass] = bal;
+        for (int per : cands) {
+            if (per < 1 || e != cudaSuccess) continue;
+            e = launch(pass, per);  // warm-up
+            float t = 0;
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = launch(pass, per);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                t += ms;
+            }
+            if (e == cudaSuccess && t < best) {
+                best = t;
+                best_of[pass] = per;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
-    c->zc = best_per;
-    if (chosen) *chosen = best_per;
+    if (e != cudaSuccess) {
+        c->zc = user;
+        c->zc_corr = user_corr;
+        return cuda_fail(c, e, "autotune");
+    }
+    c->zc = best_of[0];
+    c->zc_corr = best_of[1];
+    if (chosen) *chosen = best_of[0];
     return SP_OK;
 }
 
@@ -877,6 +891,7 @@ int sp_set_option(sp_ctx *c, int option, int value)
     case SP_OPT_PLANES_PER_CTA:
         if (value < 0) return fail(c, SP_ERR_ARG, "units per CTA must be >= 0 (0: balanced)");
         c->zc = value;
+        c->zc_corr = 0;  // the user's value applies to both passes
         return SP_OK;
     default:
         return fail(c, SP_ERR_ARG, "unknown option %d", option);

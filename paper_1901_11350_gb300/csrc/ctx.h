@@ -108,7 +108,9 @@ struct sp_ctx {
     bool generic_fft = false;  // SP_OPT_GENERIC_FFT
     bool use_small = true;     // SP_OPT_SMALL_PATH
     int zc = 0;             // units per CTA of the 27-point path; 0 = balanced (see cubic_per)
+    int zc_corr = 0;        // the corrector's, when the autotuner chose it separately
     int zc_auto = 0;        // balanced value, computed on first use
+    int zc_auto_corr = 0;   // the same for the corrector pass (its own occupancy)
     CubicParams<float> Cf = {};
     CubicParams<double> Cd = {};
     // device scratch (allocated on first use)
@@ -125,16 +127,18 @@ struct sp_ctx {
 
 // Units per CTA of the 27-point path: the user's choice, or the units spread
 // evenly over one wave of resident CTAs on the current device.
-inline int cubic_per(sp_ctx *c)
+inline int cubic_per(sp_ctx *c, int pass = 0)
 {
+    if (pass == 1 && c->zc_corr > 0) return c->zc_corr;
     if (c->zc > 0) return c->zc;
-    if (c->zc_auto <= 0) {
+    int &a = pass == 0 ? c->zc_auto : c->zc_auto_corr;
+    if (a <= 0) {
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
-        long slots = (long)nsm * cubic_resident_ctas(c->prec);
+        long slots = (long)nsm * cubic_resident_ctas(c->prec, pass);
         long units = cubic_units(c->nc[0], c->nc[1], c->nc[2]);
-        c->zc_auto = (int)std::max(1L, (units + slots - 1) / slots);
+        a = (int)std::max(1L, (units + slots - 1) / slots);
     }
-    return c->zc_auto;
+    return a;
 }

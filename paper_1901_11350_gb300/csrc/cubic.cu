@@ -29,6 +29,11 @@ namespace {
 #ifndef SPGB_CUBIC_MINB
 #define SPGB_CUBIC_MINB 3
 #endif
+// resident CTAs per SM the corrector pass is compiled for (its own register
+// budget: it has no thermal field to generate)
+#ifndef SPGB_CUBIC_MINB_CORR
+#define SPGB_CUBIC_MINB_CORR 4
+#endif
 
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
@@ -321,7 +326,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 // streamed as one segment.  With per = units / (SMs x resident CTAs) every SM
 // gets the same amount of work in a single wave.
 template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD>
-__global__ void __launch_bounds__(TX *TY, SPGB_CUBIC_MINB) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
+__global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
                                                   rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                                   const LlgConst<T> c, int per)
@@ -387,12 +392,16 @@ cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const re
 
 long cubic_units(int nx, int ny, int nz) { return (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz; }
 
-int cubic_resident_ctas(int prec)
+int cubic_resident_ctas(int prec, int pass)
 {
     int n = 0;
-    cudaError_t e = prec == SP_F64
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false>, TX * TY, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false>, TX * TY, 0);
+    cudaError_t e;
+    if (pass == 0)
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false>, TX * TY, 0);
+    else
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 1, 1, false>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false>, TX * TY, 0);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 

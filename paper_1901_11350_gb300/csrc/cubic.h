@@ -17,7 +17,7 @@ template <typename T> struct CubicParams {
 // Work units of the 27-point path: (32 x 8 column tile, plane) pairs.
 long cubic_units(int nx, int ny, int nz);
 // Resident 256-thread CTAs per SM of the 27-point kernels (occupancy query).
-int cubic_resident_ctas(int prec);
+int cubic_resident_ctas(int prec, int pass);
 
 // pass 0: predictor (stencil on src = n, writes np and q);
 // pass 1: corrector (stencil on src = np, reads q, writes nout = n).

@@ -74,7 +74,7 @@ template <typename T> int run_static(sp_ctx *c, void *n, const sp_llg_params *p,
         cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, nullptr, k, cubic_per(c), st)
                             : launch_llg_pred<T>(p->solver, S, nn, nullptr, np, q, k, st);
         if (e == cudaSuccess)
-            e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, nullptr, k, cubic_per(c), st)
+            e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, nullptr, k, cubic_per(c, 1), st)
                     : launch_llg_corr<T>(p->solver, S, nn, np, q, nullptr, k, st);
         if (e != cudaSuccess) {
             c->err = std::string("LLG launch: ") + cudaGetErrorString(e);
