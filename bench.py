@@ -214,7 +214,10 @@ def run_gpu(args):
     if args.generic:
         ctx.set_option("generic_stencil", 1)
     if args.zc:
-        ctx.set_option("planes_per_cta", args.zc)
+        zc = [int(x) for x in args.zc.split(",")]
+        ctx.set_option("planes_per_cta", zc[0])
+        if len(zc) > 1:
+            ctx.set_option("planes_per_cta_corr", zc[1])
     N = ctx.N
     host0 = torch.zeros((N, 4), dtype=torch.float32)
     host0[:, :3] = torch.from_numpy(I.random_spins(N, cfg["spin_seed"])).float()
@@ -307,6 +310,7 @@ def run_gpu(args):
                       "kernel_path": "generic" if args.generic else (
                           "cubic27" if ctx.get_option("has_cubic_path") else "generic"),
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
+                      "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
@@ -771,7 +775,8 @@ def main():
     ap.add_argument("--llg-steps", type=int, default=LLG_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--temperature", type=float, default=None, help="override T (profiling aid)")
-    ap.add_argument("--zc", type=int, default=0, help="planes per CTA of the 27-point path (profiling aid)")
+    ap.add_argument("--zc", default="", help="units per CTA of the 27-point path, P or P,C for predictor and "
+                    "corrector (profiling aid; default: chosen by sp_autotune)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
     ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian",
                                                         "square32"])

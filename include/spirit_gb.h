@@ -359,7 +359,10 @@ int sp_hessian_apply(sp_ctx *ctx, const void *n_dev, const void *v_dev, void *ou
 /* Lowest eigenvalue (*lambda, host) and unit eigenvector (mode_dev, N
  * records, in/out: a non-zero mode_dev is the start vector, zero selects a
  * fixed pseudo-random start) of the covariant Hessian at n_dev, by `krylov`
- * (1..256) Lanczos steps with full reorthogonalisation.  In exact arithmetic
+ * (1..256) Lanczos steps with full reorthogonalisation, at most 2N (the
+ * tangent space's dimension).  The iteration stops early at an invariant
+ * subspace: a residual below 1e-13 (FP64) or 1e-5 (FP32) of the running
+ * estimate of the tridiagonal matrix's norm.  In exact arithmetic
  * krylov >= 2N gives the exact lowest pair.  Synchronises `stream`. */
 int sp_lowest_mode(sp_ctx *ctx, const void *n_dev, void *mode_dev, int krylov, double *lambda, void *stream);
 
@@ -439,7 +442,14 @@ enum {
      * a call in the kernel; in FP64 the per-spin kernels run in small
      * blocks spread over the SMs (both with the generic path's per-spin
      * arithmetic); 0: never */
-    SP_OPT_SMALL_PATH = 5
+    SP_OPT_SMALL_PATH = 5,
+    /* the corrector pass's work per CTA of the 27-point path, in the units of
+     * SP_OPT_PLANES_PER_CTA (>= 1); 0: the corrector takes the value of
+     * SP_OPT_PLANES_PER_CTA (default; setting that option, or sp_autotune,
+     * overrides this one).  Reading returns the value the corrector uses:
+     * its own, else the shared user value, else its balanced split (the
+     * corrector keeps more CTAs resident than the predictor) */
+    SP_OPT_PLANES_PER_CTA_CORR = 6
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose the work per CTA of the 27-point path by measurement, for each pass
@@ -450,8 +460,9 @@ int sp_set_option(sp_ctx *ctx, int option, int value);
  * splits and a few fixed run lengths, and keeps the fastest of each.  Allocates
  * the LLG scratch if needed and synchronises `stream`.  SP_OK without effect
  * when the 27-point path does not apply.  *chosen (host, may be NULL)
- * receives the predictor's value (SP_OPT_PLANES_PER_CTA reads it back;
- * setting that option applies one value to both passes again). */
+ * receives the predictor's value (SP_OPT_PLANES_PER_CTA reads it back,
+ * SP_OPT_PLANES_PER_CTA_CORR the corrector's; setting SP_OPT_PLANES_PER_CTA
+ * applies one value to both passes again). */
 int sp_autotune(sp_ctx *ctx, const void *n_dev, int *chosen, void *stream);
 int sp_get_option(const sp_ctx *ctx, int option, int *value);
 

@@ -128,7 +128,8 @@ SIGNATURES = {
     "sp_conv3x3_wgrad": (_i, [_vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, C.c_longlong, _vp]),
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
-OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4, "small_path": 5}
+OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4, "small_path": 5,
+           "planes_per_cta_corr": 6}
 
 
 def library_path():

@@ -893,6 +893,10 @@ int sp_set_option(sp_ctx *c, int option, int value)
         c->zc = value;
         c->zc_corr = 0;  // the user's value applies to both passes
         return SP_OK;
+    case SP_OPT_PLANES_PER_CTA_CORR:
+        if (value < 0) return fail(c, SP_ERR_ARG, "units per CTA must be >= 0 (0: as the predictor)");
+        c->zc_corr = value;
+        return SP_OK;
     default:
         return fail(c, SP_ERR_ARG, "unknown option %d", option);
     }
@@ -929,6 +933,9 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_SMALL_PATH:
         *value = c->use_small ? 1 : 0;
+        return SP_OK;
+    case SP_OPT_PLANES_PER_CTA_CORR:
+        *value = c->zc_corr > 0 ? c->zc_corr : (c->zc > 0 ? c->zc : c->zc_auto_corr);
         return SP_OK;
     default:
         return SP_ERR_ARG;

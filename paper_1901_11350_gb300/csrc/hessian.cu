@@ -281,6 +281,13 @@ struct Ops {
         k_lin<T><<<nb, kHB, 0, st>>>(N, q(0), inv, q(0), 0.0, q(0));
         std::vector<double> alpha, beta, c(kMaxKrylov + 1);
         int used = 0;
+        // the Krylov space cannot outgrow the 2N-dimensional tangent space;
+        // a residual at the rounding level of the stored records (relative
+        // to the running estimate of |T|) is an invariant subspace, not a
+        // new direction: normalising it would add a dependent vector
+        m = (int)std::min<long long>(m, 2LL * N);
+        const double brk = sizeof(T) == 4 ? 1e-5 : 1e-13;
+        double tnorm = 0;
         for (int k = 0; k < m; ++k) {
             k_hvp<T><<<nb, kHB, 0, st>>>(S, n, q(k), w);
             // full reorthogonalisation, twice: w -= sum_j (q_j . w) q_j
@@ -294,7 +301,8 @@ struct Ops {
             double b2;
             if ((rc = dots(w, w, 1, &b2))) return rc;
             double b = sqrt(b2);
-            if (k == m - 1 || !(b > 1e-13 * (fabs(alpha[0]) + 1.0))) break;
+            tnorm = std::max(tnorm, fabs(alpha[k]) + b + (k ? beta[k - 1] : 0.0));
+            if (k == m - 1 || !(b > brk * tnorm)) break;
             beta.push_back(b);
             k_lin<T><<<nb, kHB, 0, st>>>(N, q(k + 1), 1.0 / b, w, 0.0, w);
         }

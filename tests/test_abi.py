@@ -136,3 +136,26 @@ def test_unet_layout_and_host_side_rejections():
     assert L.sp_conv3x3_forward(dummy, 32, 0, None, 32, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
     assert L.sp_conv3x3_forward(None, 32, 0, None, 0, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
     assert L.sp_conv3x3_wgrad(dummy, 32, 0, None, 0, dummy, 1, 16, 16, 32, dummy, None, dummy, 0, None) == -1
+
+
+def test_option_round_trip_and_rejections():
+    c = B.Context(I.simple_cubic(8), dict(J=[1.0, -0.2, 0.05], dmi_kind="bulk", D=[0.2]))
+    assert c.get_option("has_cubic_path") == 1
+    assert c.get_option("small_path") == 1
+    c.set_option("planes_per_cta", 7)
+    assert c.get_option("planes_per_cta") == 7 and c.get_option("planes_per_cta_corr") == 7
+    c.set_option("planes_per_cta_corr", 5)  # the corrector alone
+    assert c.get_option("planes_per_cta") == 7 and c.get_option("planes_per_cta_corr") == 5
+    c.set_option("planes_per_cta", 9)  # one value for both passes again
+    assert c.get_option("planes_per_cta_corr") == 9
+    for name, bad in (("planes_per_cta", -1), ("planes_per_cta_corr", -1), ("small_path", 2)):
+        with pytest.raises(B.SpinError) as e:
+            c.set_option(name, bad)
+        assert e.value.code == -1
+    h = c._h
+    assert B.lib().sp_set_option(h, 99, 1) == -1
+    v = C.c_int()
+    assert B.lib().sp_get_option(h, 99, C.byref(v)) == -1
+    c.set_option("generic_stencil", 1)
+    assert c.get_option("generic_stencil") == 1
+    c.close()
