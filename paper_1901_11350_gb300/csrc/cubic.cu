@@ -34,6 +34,18 @@ namespace {
 #ifndef SPGB_CUBIC_MINB_CORR
 #define SPGB_CUBIC_MINB_CORR 4
 #endif
+// plane buffers in shared memory per pass (planes are fetched NB - 1 ahead)
+// and how many planes ahead the corrector loads its folded term q (two
+// planes ahead costs the 64-register corrector spills and time)
+#ifndef SPGB_CUBIC_NB_PRED
+#define SPGB_CUBIC_NB_PRED 3
+#endif
+#ifndef SPGB_CUBIC_NB_CORR
+#define SPGB_CUBIC_NB_CORR 3
+#endif
+#ifndef SPGB_CUBIC_QAHEAD
+#define SPGB_CUBIC_QAHEAD 1
+#endif
 
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
@@ -235,56 +247,65 @@ template <typename T> __device__ __forceinline__ v3<T> onsite(const CubicParams<
 //     A(p+1) = e(p+1) + w(p) - c(p) x D_{+z} + onsite(c(p+1)),
 // so only A, w and c of one plane stay live between iterations.
 // PASS 0: predictor on n; PASS 1: corrector on np (q folded term, n out).
-template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD>
+// Plane p lives in tiles[(p - za + 1) % NB]; every fetch is one cp.async
+// group (empty past the segment's last plane), so that waiting for all but
+// the newest NB - 2 groups means "the plane needed next has landed".
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB>
 __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> *__restrict__ src,
                                         rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                         rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                         const LlgConst<T> &c, rec_t<T> (*tiles)[HN], int x0, int y0, int za, int zb)
 {
+    static_assert(NB >= 2 && NB <= 4, "2 to 4 plane buffers");
+    constexpr int QA = PASS == 1 ? SPGB_CUBIC_QAHEAD : 1;
+    static_assert(QA >= 1 && QA <= 2, "q is fetched 1 or 2 planes ahead");
     int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     int x = x0 + tx, y = y0 + ty;
     bool own = x < P.nx && y < P.ny;
     HaloSlot h0 = halo_slot(P, x0, y0, threadIdx.x), h1 = halo_slot(P, x0, y0, threadIdx.x + TX * TY);
-    // plane p lives in tiles[(p - za + 1) & 1]; plane p+2 is fetched while
-    // plane p is finished
-    load_plane<T>(P, src, tiles[0], h0, h1, za - 1);
-    cp_async_commit();
-    load_plane<T>(P, src, tiles[1], h0, h1, za);
-    cp_async_commit();
-    cp_async_wait<1>();
+    // planes za-1 .. za+NB-2 in flight
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (za - 1 + k <= zb) load_plane<T>(P, src, tiles[k], h0, h1, za - 1 + k);
+        cp_async_commit();
+    }
+    cp_async_wait<NB - 1>();
     __syncthreads();
     Plane<T> below = summarise<T, DM>(P, tiles[0], tx, ty);
     __syncthreads();
-    load_plane<T>(P, src, tiles[0], h0, h1, za + 1);
+    if (za + NB - 1 <= zb) load_plane<T>(P, src, tiles[0], h0, h1, za + NB - 1);
     cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait<NB - 1>();
     __syncthreads();
     Plane<T> cur = summarise<T, DM>(P, tiles[1], tx, ty);
     v3<T> acc = cur.e + below.w - zdmi<T, DM>(P, below.c) + onsite(P, cur.c);
     v3<T> wcur = cur.w, ccur = cur.c;
     const int plane_sz = P.nx * P.ny;  // N < 2^31
     int i = za * plane_sz + y * P.nx + x;
-    // per-spin global inputs of the plane being finished, fetched one plane
-    // ahead so that their latency overlaps the stencil of the current plane
-    v3<T> qn = mk(T(0), T(0), T(0)), bn = mk(T(0), T(0), T(0));
-    if (own) {
-        if (PASS == 1) qn = ld(q, i);
-        if (HAS_BDD) bn = ld(Bdd, i);
+    // per-spin global inputs of the planes being finished, fetched QA planes
+    // (Bdd: one plane) ahead so that their latency overlaps the stencils
+    v3<T> qa[QA], bn = mk(T(0), T(0), T(0));
+#pragma unroll
+    for (int k = 0; k < QA; ++k) {
+        qa[k] = mk(T(0), T(0), T(0));
+        if (PASS == 1 && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
     }
+    if (HAS_BDD && own) bn = ld(Bdd, i);
+    int s_next = 2 % NB, s_free = 1;  // slots of planes z+1 and z
     for (int z = za; z < zb; ++z, i += plane_sz) {
-        rec_t<T> *bnext = tiles[(z - za) & 1];      // plane z+1 (in flight)
-        rec_t<T> *bfree = tiles[(z - za + 1) & 1];  // plane z, already summarised
-        v3<T> qi = qn, bi = bn;
-        if (own && z + 1 < zb) {
-            if (PASS == 1) qn = ld(q, i + plane_sz);
-            if (HAS_BDD) bn = ld(Bdd, i + plane_sz);
-        }
-        cp_async_wait<0>();
+        rec_t<T> *bnext = tiles[s_next];  // plane z+1 (landed after the wait)
+        rec_t<T> *bfree = tiles[s_free];  // plane z, already summarised
+        s_next = s_next + 1 == NB ? 0 : s_next + 1;
+        s_free = s_free + 1 == NB ? 0 : s_free + 1;
+        v3<T> qi = qa[0], bi = bn;
+#pragma unroll
+        for (int k = 0; k + 1 < QA; ++k) qa[k] = qa[k + 1];
+        if (own && z + QA < zb && PASS == 1) qa[QA - 1] = ld(q, i + QA * plane_sz);
+        if (HAS_BDD && own && z + 1 < zb) bn = ld(Bdd, i + plane_sz);
+        cp_async_wait<NB - 2>();
         __syncthreads();
-        if (z + 2 <= zb) {
-            load_plane<T>(P, src, bfree, h0, h1, z + 2);
-            cp_async_commit();
-        }
+        if (z + NB <= zb) load_plane<T>(P, src, bfree, h0, h1, z + NB);
+        cp_async_commit();
         Plane<T> up = summarise<T, DM>(P, bnext, tx, ty);
         v3<T> B = acc + up.w + zdmi<T, DM>(P, up.c);
         acc = up.e + wcur - zdmi<T, DM>(P, ccur) + onsite(P, up.c);
@@ -318,6 +339,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
             }
         }
     }
+    cp_async_wait<0>();
     __syncthreads();  // the next segment reuses the tiles
 }
 
@@ -331,14 +353,15 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                                   const LlgConst<T> c, int per)
 {
-    __shared__ __align__(32) rec_t<T> tiles[2][HN];
+    constexpr int NB = PASS == 0 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
+    __shared__ __align__(32) rec_t<T> tiles[NB][HN];
     int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
     long total = (long)tiles_x * tiles_y * P.nz;
     long u = (long)blockIdx.x * per, u1 = min(u + per, total);
     while (u < u1) {
         int tile = (int)(u / P.nz), za = (int)(u % P.nz);
         int zb = (int)min((long)P.nz, za + (u1 - u));
-        segment<T, SOLVER, PASS, DM, HAS_BDD>(P, src, np, q, nout, Bdd, c, tiles, (tile % tiles_x) * TX,
+        segment<T, SOLVER, PASS, DM, HAS_BDD, NB>(P, src, np, q, nout, Bdd, c, tiles, (tile % tiles_x) * TX,
                                               (tile / tiles_x) * TY, za, zb);
         u += zb - za;
     }

@@ -135,10 +135,12 @@ def test_llg_step_fp64(name, solver, T, path):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("solver", ["depondt", "heun", "sib", "rk4"])
-@pytest.mark.parametrize("path", ["default", "generic"])
+@pytest.mark.parametrize("path", ["default", "generic", "cubic"])
 def test_llg_step_fp32_per_step(name, solver, path):
     if path == "generic" and name not in CUBIC:
         pytest.skip("generic is the default path here")
+    if path == "cubic" and name not in CUBIC:
+        pytest.skip("no 27-point path for this lattice")
     g, h = CASES[name]
     o = _oracle(g, h)
     c = _ctx(g, h, "f32", path)
@@ -179,10 +181,11 @@ def test_stochastic_heun_100_steps_fp64():
     assert np.abs(_np(n) - no).max() <= 1e-11
 
 
-@pytest.mark.parametrize("zc", [1, 2, 5, 7, 40, 1000])
-def test_cubic_plane_chunking_is_exact(zc):
+@pytest.mark.parametrize("zc,zcc", [(1, 0), (2, 1), (5, 3), (7, 0), (40, 2), (1000, 11)])
+def test_cubic_plane_chunking_is_exact(zc, zcc):
     # the result may not depend on how (tile, plane) units are split between
-    # CTAs, including runs that cross from one column tile to the next
+    # CTAs, including runs that cross from one column tile to the next, nor
+    # on the corrector taking a split of its own (zcc > 0)
     cfg = I.cfg_sc_128(4)
     g = dict(cfg["geometry"], n_cells=[37, 19, 23])
     c = B.Context(g, cfg["hamiltonian"], "f32")
@@ -191,6 +194,8 @@ def test_cubic_plane_chunking_is_exact(zc):
     a = c.spins(n0)
     c.llg_step(a, 3, **kw)
     c.set_option("planes_per_cta", zc)
+    c.set_option("planes_per_cta_corr", zcc)
+    assert c.get_option("planes_per_cta_corr") == (zcc or zc)
     b = c.spins(n0)
     c.llg_step(b, 3, **kw)
     assert torch.equal(a, b)
