@@ -236,6 +236,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
+// The same with the ten round keys given: rk[2r], rk[2r+1] = key after r
+// Weyl steps.
+__device__ __forceinline__ uint4 philox4x32_10_keyed(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 thermal_bits(uint64_t seed, uint64_t step, uint32_t replica, uint32_t i)
 {
     return philox4x32_10(make_uint4(i, (uint32_t)step, (uint32_t)(step >> 32), replica * 8u),

@@ -122,14 +122,13 @@ __device__ __forceinline__ v3<double> thermal_eta(uint4 x, double) { return box_
 // most two of them.  Their in-plane offsets (periodic wrap or "absent" for an
 // open edge) do not depend on z and are computed once per CTA.
 struct HaloSlot {
-    int off;  // gy * nx + gx
-    int ok;   // inside the lattice in-plane
+    int off;  // gy * nx + gx, or -1 outside the lattice in-plane
 };
 
 template <typename T>
 __device__ __forceinline__ HaloSlot halo_slot(const CubicParams<T> &P, int x0, int y0, int e)
 {
-    HaloSlot h{0, 0};
+    HaloSlot h{-1};
     if (e >= HN) return h;
     int hx = e % HX, hy = e / HX;
     int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
@@ -146,8 +145,7 @@ __device__ __forceinline__ HaloSlot halo_slot(const CubicParams<T> &P, int x0, i
     } else {
         in = in && gy >= 0 && gy < P.ny;
     }
-    h.off = gy * P.nx + gx;
-    h.ok = in;
+    h.off = in ? gy * P.nx + gx : -1;
     return h;
 }
 
@@ -172,12 +170,12 @@ __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<
     const rec_t<T> *plane = src + z * (P.nx * P.ny);
     int e0 = threadIdx.x, e1 = threadIdx.x + TX * TY;
     rec_t<T> zero{};
-    if (zin && h0.ok)
+    if (zin && h0.off >= 0)
         copy_rec<T>(tile + e0, plane + h0.off);
     else
         tile[e0] = zero;
     if (e1 < HN) {
-        if (zin && h1.ok)
+        if (zin && h1.off >= 0)
             copy_rec<T>(tile + e1, plane + h1.off);
         else
             tile[e1] = zero;
@@ -316,7 +314,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
             if (HAS_BDD) B = B + bi;
             if (PASS == 0) {
                 v3<T> Bth = mk(T(0), T(0), T(0));
-                if (c.thermal) Bth = c.sig[0] * thermal_eta(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+                if (c.thermal) Bth = c.sig[0] * thermal_eta(thermal_bits(c, (uint32_t)i), T(0));
                 v3<T> A = llg_A(c.cA[0], c.alpha, ni, B + Bth);
                 if (SOLVER == SP_HEUN) {
                     v3<T> f = cross(ni, A);

@@ -53,7 +53,7 @@ __device__ __forceinline__ void pred_spin(const Stencil<T> &S, const R *n, const
     v3<T> B = local_field(S, n, i, ni, b);
     if (Bdd) B = B + ld(Bdd, i);
     v3<T> Bth = mk(T(0), T(0), T(0));
-    if (c.thermal) Bth = c.sig[b] * box_muller(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+    if (c.thermal) Bth = c.sig[b] * box_muller(thermal_bits(c, (uint32_t)i), T(0));
     v3<T> A = llg_A(c.cA[b], c.alpha, ni, B + Bth);
     if (SOLVER == SP_HEUN) {
         v3<T> f = cross(ni, A);
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kBlock) k_rk4(const __grid_constant__ Stencil<
     v3<T> y = ld(src, i);
     v3<T> B = local_field(S, src, i, y, b);
     if (Bdd) B = B + ld(Bdd, i);
-    if (c.thermal) B = B + c.sig[b] * box_muller(thermal_bits(c.seed, c.step, c.replica, (uint32_t)i), T(0));
+    if (c.thermal) B = B + c.sig[b] * box_muller(thermal_bits(c, (uint32_t)i), T(0));
     v3<T> k = cross(y, llg_A(c.cA[b], c.alpha, y, B));
     v3<T> ni = ldc(n, i);
     if (STAGE == 0) {

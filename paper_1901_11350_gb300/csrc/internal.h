@@ -13,7 +13,27 @@ template <typename T> struct LlgConst {
     uint64_t seed, step;
     uint32_t replica;
     int thermal;
+    // Philox round keys (k0 + r W0, k1 + r W1), r = 0..9, of `seed`: the
+    // kernels read them as operands instead of stepping the key per spin
+    uint32_t rk[20];
 };
+
+template <typename T> inline void llg_set_seed(LlgConst<T> &k, uint64_t seed)
+{
+    k.seed = seed;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (uint32_t r = 0; r < 10; ++r) {
+        k.rk[2 * r] = k0 + r * 0x9E3779B9u;  // mod 2^32, as r successive Weyl steps
+        k.rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
+    }
+}
+
+// The thermal-field counter block of spin i at step c.step (the layout of
+// thermal_bits), through the precomputed round keys.
+template <typename T> __device__ __forceinline__ uint4 thermal_bits(const LlgConst<T> &c, uint32_t i)
+{
+    return philox4x32_10_keyed(make_uint4(i, (uint32_t)c.step, (uint32_t)(c.step >> 32), c.replica * 8u), c.rk);
+}
 
 constexpr int kBlock = 256;
 // single-CTA LLG path for small FP32 lattices: threads of the CTA, largest

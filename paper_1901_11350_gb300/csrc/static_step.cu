@@ -66,7 +66,7 @@ template <typename T> int run_static(sp_ctx *c, void *n, const sp_llg_params *p,
         k.cA[b] = (T)(-kGamma / ((1.0 + p->alpha * p->alpha) * mu));
         k.sig[b] = (T)std::sqrt(2.0 * p->alpha * kBoltzmann * p->T * mu / (kGamma * p->dt));
     }
-    k.seed = p->seed;
+    llg_set_seed(k, p->seed);
     k.replica = p->replica;
     k.thermal = (p->T > 0 && p->alpha > 0) ? 1 : 0;
     for (int s = 0; s < n_steps; ++s) {
