@@ -517,6 +517,112 @@ def run_mc(args):
     return 0
 
 
+def run_sllg(args):
+    """Stochastic LLG sampling of the simple-cubic ferromagnet (J = 1 meV,
+    periodic, B = 0; Appendix "Stochastic LLG"): every temperature of the grid
+    is a replica of one batch (sp_llg_step_replicas), stochastic Heun with
+    alpha = args.sllg_alpha and dt = args.sllg_dt; args.sllg_thermal steps,
+    then args.sllg_samples steps with the observables accumulated after
+    every args.sllg_every steps (sp_sample).  Reports spin-updates/s and the
+    critical temperature from the Binder-cumulant crossings of the sizes and
+    the susceptibility peak of the largest."""
+    import numpy as np
+    import torch
+    from paper_1901_11350_gb300 import binding as Bd
+    from paper_1901_11350_gb300 import build
+    from paper_1901_11350_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    build.build()
+    sizes = [int(v) for v in args.mc_sizes.split(",")]
+    T = np.round(np.arange(args.mc_tmin, args.mc_tmax + 1e-9, args.mc_dt), 6)
+    R = len(T)
+    kB = 0.08617333262
+    every = args.sllg_every
+    n_samp = args.sllg_samples // every
+    kw = dict(solver="heun", dt=args.sllg_dt, alpha=args.sllg_alpha)
+    res, tot_updates, tot_s = {}, 0.0, 0.0
+    st_cuda = torch.cuda.current_stream()
+    for L in sizes:
+        ctx = Bd.Context(I.simple_cubic(L, L, L, periodic=(True, True, True), mu_s=2.0), dict(J=[1.0]), "f32")
+        if args.generic:
+            ctx.set_option("generic_stencil", 1)
+        if args.zc:
+            zc = [int(v) for v in args.zc.split(",")]
+            ctx.set_option("planes_per_cta", zc[0])
+            if len(zc) > 1:
+                ctx.set_option("planes_per_cta_corr", zc[1])
+        N = ctx.N
+        x = ctx.spins(I.ferromagnet(N))[None].repeat(R, 1, 1).contiguous()
+        stats = torch.zeros((R, 8), dtype=torch.float64, device="cuda")
+        step = 0
+        ctx.llg_step_replicas(x, T, max(args.warmup, 1), seed=L, step0=step, **kw)
+        step += max(args.warmup, 1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(st_cuda)
+        ctx.llg_step_replicas(x, T, args.sllg_thermal, seed=L, step0=step, **kw)
+        step += args.sllg_thermal
+        e1.record(st_cuda)
+        for k in range(n_samp):
+            ctx.llg_step_replicas(x, T, every, seed=L, step0=step, **kw)
+            step += every
+            ctx.sample(x, stats)
+        e2.record(st_cuda)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e2) / 1e3
+        steps = args.sllg_thermal + n_samp * every
+        tot_updates += float(steps) * N * R
+        tot_s += secs
+        s = stats.cpu().numpy()
+        n = s[:, 5]
+        m, m2, m4, E, E2 = (s[:, k] / n for k in range(5))
+        res[L] = dict(N=N, seconds=secs, thermal_s=e0.elapsed_time(e1) / 1e3, m=m, m2=m2, m4=m4,
+                      U4=1 - m4 / (3 * m2 ** 2), chi=N * (m2 - m ** 2) / (kB * T), cv=(E2 - E ** 2) / (kB * T ** 2) / N,
+                      finite=bool(torch.isfinite(x).all().item()))
+    cross = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        d = res[a]["U4"] - res[b]["U4"]
+        for k in range(R - 1):
+            if d[k] < 0 <= d[k + 1] or d[k] > 0 >= d[k + 1]:
+                cross.append(float(T[k] + (T[k + 1] - T[k]) * d[k] / (d[k] - d[k + 1])))
+                break
+    Lmax = max(sizes)
+    chi = res[Lmax]["chi"]
+    k = int(np.argmax(chi))
+    tpk = float(T[k])
+    if 0 < k < R - 1:
+        y0, y1, y2 = chi[k - 1], chi[k], chi[k + 1]
+        den = y0 - 2 * y1 + y2
+        if den != 0:
+            tpk = float(T[k] + 0.5 * (T[1] - T[0]) * (y0 - y2) / den)
+    out = {"metric": "stochastic-LLG spin-updates/s, simple-cubic ferromagnet (Tc validation)",
+           "value": tot_updates / tot_s, "unit": "spin-updates/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32 field and steps, f64 observables", "data": "synthetic",
+           "config": {"workload": "sllg_sc_ferromagnet_tc", "sizes": sizes, "temperatures_K": [float(t) for t in T],
+                      "thermal_steps": args.sllg_thermal, "sample_steps": n_samp * every, "sample_every": every,
+                      "solver": "heun", "dt_ps": args.sllg_dt, "alpha": args.sllg_alpha, "J_meV": 1.0,
+                      "start": "ferromagnet along z", "thermal_rng": "philox4x32-10, one stream per replica"},
+           "tc_K": {"binder_crossings": cross, "binder_mean": float(np.mean(cross)) if cross else None,
+                    "chi_peak_L%d" % Lmax: tpk, "expected_high_T_series": 16.71, "paper_sllg": 16.92},
+           # method kernels: predictor + corrector per step of each size's batch, one observable pass per
+           # sample (the graph replays add one step-counter kernel per 32 steps, not counted)
+           "gpu_launches": sum(2 * (args.sllg_thermal + n_samp * every) + n_samp for _ in sizes),
+           "per_size": {str(L): {"seconds": r["seconds"], "spins": r["N"], "finite": r["finite"],
+                                 "m": [round(float(v), 5) for v in r["m"]], "U4": [round(float(v), 5) for v in r["U4"]],
+                                 "chi": [round(float(v), 3) for v in r["chi"]], "cv": [round(float(v), 5) for v in r["cv"]]}
+                        for L, r in res.items()}}
+    if not args.no_cpu_baseline:
+        # one replica of the largest lattice near Tc, stepped by the oracle
+        out["cpu_baseline"] = cpu_baseline(dict(
+            geometry=I.simple_cubic(Lmax, Lmax, Lmax, periodic=(True, True, True), mu_s=2.0),
+            hamiltonian=dict(J=[1.0]), spin_seed=1,
+            run=dict(solver="heun", dt=args.sllg_dt, alpha=args.sllg_alpha, T=16.5, seed=Lmax)), seconds=10.0,
+            max_steps=200)
+    print(json.dumps(out))
+    return 0
+
+
 def run_square32(args):
     """32x32 square lattice, open, J=1, interfacial D=0.3, K=0.1 z, B=1 T z,
     mu_s=2: 1000 deterministic Depondt steps in FP64 (dt=1e-3 ps,
@@ -779,13 +885,18 @@ def main():
                     "corrector (profiling aid; default: chosen by sp_autotune)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
     ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian",
-                                                        "square32"])
+                                                        "square32", "sllg30"])
     ap.add_argument("--mc-sizes", default="10,15,20,30", help="mc30: lattice sides")
     ap.add_argument("--mc-thermal", type=int, default=10000, help="mc30: thermalisation sweeps")
     ap.add_argument("--mc-samples", type=int, default=100000, help="mc30: sampled sweeps")
     ap.add_argument("--mc-tmin", type=float, default=10.0)
     ap.add_argument("--mc-tmax", type=float, default=24.0)
-    ap.add_argument("--mc-dt", type=float, default=0.5)
+    ap.add_argument("--mc-dt", type=float, default=0.5, help="mc30, sllg30: temperature step (K)")
+    ap.add_argument("--sllg-thermal", type=int, default=20000, help="sllg30: thermalisation steps")
+    ap.add_argument("--sllg-samples", type=int, default=100000, help="sllg30: sampled steps")
+    ap.add_argument("--sllg-every", type=int, default=10, help="sllg30: steps between samples")
+    ap.add_argument("--sllg-dt", type=float, default=1e-3, help="sllg30: time step (ps)")
+    ap.add_argument("--sllg-alpha", type=float, default=1.0, help="sllg30: damping")
     ap.add_argument("--systems", type=int, default=200, help="warmstart: held-out systems")
     ap.add_argument("--eval-max-iter", type=int, default=30000, help="warmstart: iteration cap per relaxation")
     ap.add_argument("--per-system", type=int, default=4, help="warmstart: systems timed in the one-system loop")
@@ -811,6 +922,8 @@ def main():
         return run_mc(args)
     if args.workload == "hessian":
         return run_hessian(args)
+    if args.workload == "sllg30":
+        return run_sllg(args)
     if args.workload == "square32":
         return run_square32(args)
     return run_gpu(args)

@@ -214,6 +214,32 @@ int sp_topological_charge(sp_ctx *ctx, const void *n_dev, double *Q_dev, void *s
  * per spin, 3 for RK4) on first use. */
 int sp_llg_step(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, void *stream);
 
+/* n_steps LLG steps of n_rep replicas of the context's system at once, for
+ * thermal averages by sampling the stochastic LLG over time (Appendix
+ * "Stochastic LLG": a temperature scan of one lattice).  Replica r sits at
+ * spins_dev + r N records (replica-major, the layout of sp_mc_sweeps), has
+ * temperature T[r] (K, host array) and the thermal stream p->replica + r
+ * (Philox counter word 3 = 8 (p->replica + r)); p->T is ignored.  Each
+ * replica's result is the one sp_llg_step gives that replica alone with
+ * p->T = T[r] and p->replica + r, bit for bit: the noise amplitudes are
+ * computed on the host in FP64 in the same way.  All replicas share one launch per
+ * pass (the 27-point path spreads all replicas' (tile, plane) units over the
+ * device; batches of two or more do not take the small-lattice single-CTA
+ * path, a batch of one is sp_llg_step at T[0]).  Where the 27-point split
+ * would give fewer than 8 planes per CTA (unless SP_OPT_PLANES_PER_CTA is
+ * set) the per-spin kernels run instead.  Runs of up to 32 steps are
+ * replayed from a CUDA graph captured on first use for the launch
+ * configuration (up to 4 kept per context; not while `stream` is being
+ * captured); their Philox step is read from a device counter the call sets.
+ * The kernel profiler does not bracket these launches.  Scratch: 2 (RK4:
+ * 3) records per spin and replica; the amplitudes are re-uploaded (with a
+ * synchronisation of `stream`) only when n_rep, T, dt or alpha change.
+ * SP_ERR_UNSUPPORTED with the dipole term; SP_ERR_ARG for n_rep < 1,
+ * n_rep N >= 2^31, a negative or non-finite T[r], p->replica + n_rep > 2^29
+ * and the checks of sp_llg_step. */
+int sp_llg_step_replicas(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const sp_llg_params *p,
+                         int n_steps, void *stream);
+
 /* ------------------------------------------------------------------------
  * Energy minimisation (Appendix D)
  * ------------------------------------------------------------------------ */
@@ -342,6 +368,15 @@ int sp_mc_colours(sp_ctx *ctx, int *n_colours);
  * after and before `stream` by events. */
 int sp_mc_sweeps(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const sp_mc_params *p, int n_sweeps,
                  double *cone_dev, double *stats_dev, void *stream);
+
+/* Accumulate the observables of n_rep replicas (n_rep x N records,
+ * replica-major) into stats_dev (DEVICE, n_rep x 8 doubles, the layout of
+ * sp_mc_sweeps): m, m^2, m^4, E, E^2 and one more sample; the acceptance
+ * slots 6 and 7 are not touched.  m = |sum_i n_i| / N and E the total energy
+ * of Eq. 1 without the dipole term, both summed in FP64 in a fixed order.
+ * Stream-ordered, no synchronisation.  SP_ERR_UNSUPPORTED with the dipole
+ * term. */
+int sp_sample(sp_ctx *ctx, const void *spins_dev, int n_rep, double *stats_dev, void *stream);
 
 /* ------------------------------------------------------------------------
  * Covariant Hessian, lowest mode and minimum mode following (Sec. MMF and

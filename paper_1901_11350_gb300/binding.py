@@ -90,6 +90,8 @@ SIGNATURES = {
     "sp_max_torque": (_i, [_vp, _vp, _vp, _vp]),
     "sp_topological_charge": (_i, [_vp, _vp, _vp, _vp]),
     "sp_llg_step": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
+    "sp_llg_step_replicas": (_i, [_vp, _vp, _i, C.POINTER(_d), C.POINTER(LLGParams), _i, _vp]),
+    "sp_sample": (_i, [_vp, _vp, _i, _vp, _vp]),
     "sp_minimise": (_i, [_vp, _vp, _vp, _d, _d, _d, _i, _i, C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
@@ -332,6 +334,34 @@ class Context:
         p = LLGParams(SOLVER[solver], float(dt), float(alpha), float(T), int(seed), int(step0), int(replica))
         self._check(lib().sp_llg_step(self._h, self._spin_arg(n, "n"), C.byref(p), int(n_steps), _stream()))
         return n
+
+    def llg_step_replicas(self, spins, T, n_steps=1, solver="heun", dt=1e-3, alpha=0.1, seed=0, step0=0, replica=0):
+        """LLG steps of replicas spins [R, N, 4] (CUDA, this context's dtype)
+        at temperatures T[R], replica r on the thermal stream replica + r."""
+        R = spins.shape[0]
+        if spins.dim() != 3 or spins.shape[1] != self.N:
+            raise ValueError("spins must be [replicas, N, 4]")
+        self._spin_arg(spins, "spins", R)
+        if len(T) != R:
+            raise ValueError("one temperature per replica")
+        Th = (C.c_double * R)(*[float(t) for t in T])
+        p = LLGParams(SOLVER[solver], float(dt), float(alpha), 0.0, int(seed), int(step0), int(replica))
+        self._check(lib().sp_llg_step_replicas(self._h, _ptr(spins), R, Th, C.byref(p), int(n_steps), _stream()))
+        return spins
+
+    def sample(self, spins, stats=None):
+        """Accumulate per-replica observables of spins [R, N, 4] into stats
+        [R, 8] (float64 CUDA, created when None): sums of m, m^2, m^4, E, E^2
+        and the sample count."""
+        R = spins.shape[0]
+        if spins.dim() != 3 or spins.shape[1] != self.N:
+            raise ValueError("spins must be [replicas, N, 4]")
+        self._spin_arg(spins, "spins", R)
+        stats = torch.zeros((R, 8), dtype=torch.float64, device=spins.device) if stats is None else stats
+        if not (stats.is_cuda and stats.dtype == torch.float64 and tuple(stats.shape) == (R, 8) and stats.is_contiguous()):
+            raise ValueError("stats must be a contiguous float64 CUDA tensor [R, 8]")
+        self._check(lib().sp_sample(self._h, _ptr(spins), R, _ptr(stats), _stream()))
+        return stats
 
     def minimise(self, n, v, dt=0.1, mass=1.0, tol=1e-6, max_iter=10000, check_every=64):
         it = C.c_int()

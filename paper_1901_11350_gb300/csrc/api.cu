@@ -325,18 +325,43 @@ template <typename T> LlgConst<T> llg_const(const sp_ctx *c, const sp_llg_params
     return k;
 }
 
+// Noise amplitudes of a batch of replicas at temperatures T[r] on the device
+// (c->rsig), uploaded when they differ from the last batch's.
+template <typename T> int replica_amplitudes(sp_ctx *c, const sp_llg_params *p, int n_rep, const double *temps,
+                                             cudaStream_t st)
+{
+    std::vector<double> key{(double)n_rep, (double)c->nb, (double)sizeof(T), p->dt, p->alpha};
+    key.insert(key.end(), temps, temps + n_rep);
+    if (c->rsig.p && key == c->rsig_key) return SP_OK;
+    std::vector<T> amp((size_t)n_rep * c->nb);
+    for (int r = 0; r < n_rep; ++r)
+        for (int b = 0; b < c->nb; ++b) {
+            double mu = c->mu_s[b] * kMuB;
+            amp[(size_t)r * c->nb + b] = (T)std::sqrt(2.0 * p->alpha * kBoltzmann * temps[r] * mu / (kGamma * p->dt));
+        }
+    int rc = ensure(c, c->rsig, sizeof(T) * amp.size());
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->rsig.p, amp.data(), sizeof(T) * amp.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // amp is freed on return
+    if (e != cudaSuccess) return cuda_fail(c, e, "replica noise amplitudes");
+    c->rsig_key.swap(key);
+    return SP_OK;
+}
+
 template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaStream_t st)
 {
     bool rk4 = p->solver == SP_RK4;
-    int rc = ensure(c, c->pred, (rk4 ? 3 : 2) * sizeof(rec_t<T>) * (size_t)c->N);
+    size_t NR = (size_t)c->N;
+    int rc = ensure(c, c->pred, (rk4 ? 3 : 2) * sizeof(rec_t<T>) * NR);
     if (rc) return rc;
     rec_t<T> *np = (rec_t<T> *)c->pred.p;
-    rec_t<T> *q = np + c->N;
+    rec_t<T> *q = np + NR;
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
     bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
     LlgConst<T> k = llg_const<T>(c, p);
+    int per0 = cub ? cubic_per(c) : 0, per1 = cub ? cubic_per(c, 1) : 0;
     if (c->use_small && c->N <= kSmallMax && c->h.dipole == SP_DIPOLE_NONE && !rk4 && !c->prof.on) {
         if (std::is_same<T, float>::value) {
             // whole steps inside one CTA (the lattice fits in shared memory)
@@ -352,7 +377,7 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         const void *bd;
         if (rk4) {
             // stage states ping-pong between np and q; acc follows them
-            rec_t<T> *acc = q + c->N;
+            rec_t<T> *acc = q + NR;
             const rec_t<T> *src[4] = {nn, np, q, np};
             rec_t<T> *dst[4] = {np, q, np, nn};
             for (int stg = 0; stg < 4; ++stg) {
@@ -366,16 +391,155 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         }
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
-        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, cubic_per(c), st)
+        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, per0, st)
                             : launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
-        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, cubic_per(c, 1), st)
+        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, per1, st)
                 : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
+    }
+    return SP_OK;
+}
+
+// ------------------------------------------------------------ replicas
+constexpr int kLlgGraphSteps = 32;  // steps per replayed graph of a replica batch
+constexpr int kCubicMinRun = 8;     // shortest balanced run (planes per CTA) worth the 27-point ring
+constexpr size_t kLlgGraphs = 4;    // instantiated graphs kept per context
+
+__global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
+__global__ void k_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
+
+// The instantiated graph of G steps of a replica batch for this key, captured
+// on first use: G steps whose kernels read the Philox step as *ctr + j, then
+// ctr += G.
+template <typename T, typename F>
+int replica_graph(sp_ctx *c, const std::vector<char> &key, int G, const LlgConst<T> &k, unsigned long long *ctr,
+                  F &&one_step, cudaGraphExec_t *out)
+{
+    for (auto &g : c->lg_graphs)
+        if (g.key == key) {
+            *out = g.exec;
+            return SP_OK;
+        }
+    cudaError_t e = cudaSuccess;
+    if (!c->lg_stream) e = cudaStreamCreateWithFlags(&c->lg_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->lg_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "replica graph capture");
+    for (int j = 0; j < G && e == cudaSuccess; ++j) {
+        LlgConst<T> kk = k;
+        kk.step = (uint64_t)j;
+        kk.step_base = ctr;
+        e = one_step(kk, c->lg_stream);
+    }
+    if (e == cudaSuccess) {
+        k_add_u64<<<1, 1, 0, c->lg_stream>>>(ctr, (unsigned long long)G);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->lg_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "replica graph");
+    if (c->lg_graphs.size() >= kLlgGraphs) {
+        cudaGraphExecDestroy(c->lg_graphs.front().exec);
+        c->lg_graphs.erase(c->lg_graphs.begin());
+    }
+    c->lg_graphs.push_back(LlgGraph{key, exec});
+    *out = exec;
+    return SP_OK;
+}
+
+// n_steps steps of n_rep > 1 replicas stored one after another at
+// temperatures temps[r] (sp_llg_step_replicas).  Runs of kLlgGraphSteps
+// steps are replayed from a CUDA graph (the step counter on the device),
+// the rest launched one step at a time.
+template <typename T>
+int replicas_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaStream_t st, int n_rep,
+                 const double *temps)
+{
+    bool rk4 = p->solver == SP_RK4;
+    size_t NR = (size_t)c->N * n_rep;
+    int rc = ensure(c, c->pred, (rk4 ? 3 : 2) * sizeof(rec_t<T>) * NR);
+    if (rc) return rc;
+    if ((rc = replica_amplitudes<T>(c, p, n_rep, temps, st))) return rc;
+    if ((rc = ensure(c, c->step_ctr, sizeof(unsigned long long)))) return rc;
+    rec_t<T> *np = (rec_t<T> *)c->pred.p, *q = np + NR, *acc = q + NR, *nn = (rec_t<T> *)n;
+    const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
+    const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
+    LlgConst<T> k = llg_const<T>(c, p);
+    k.n_rep = n_rep;
+    k.nb = c->nb;
+    k.rsig = (const T *)c->rsig.p;
+    bool hot = false;
+    for (int r = 0; r < n_rep; ++r) hot = hot || temps[r] > 0;
+    k.thermal = (hot && p->alpha > 0) ? 1 : 0;
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
+    int per0 = cub ? cubic_per_batch(c, 0, n_rep) : 0, per1 = cub ? cubic_per_batch(c, 1, n_rep) : 0;
+    // runs of a few planes per CTA are mostly the ring's prologue: the
+    // per-spin kernels are faster there (unless the user fixed the split)
+    if (cub && c->zc == 0 && per0 < kCubicMinRun) cub = false;
+    auto one_step = [&](const LlgConst<T> &kk, cudaStream_t s) -> cudaError_t {
+        if (rk4) {
+            const rec_t<T> *src[4] = {nn, np, q, np};
+            rec_t<T> *dst[4] = {np, q, np, nn};
+            for (int stg = 0; stg < 4; ++stg) {
+                cudaError_t e = launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, nullptr, kk, s);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, nullptr, kk, per0, s)
+                            : launch_llg_pred<T>(p->solver, S, nn, nullptr, np, q, kk, s);
+        if (e != cudaSuccess) return e;
+        return cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, nullptr, kk, per1, s)
+                   : launch_llg_corr<T>(p->solver, S, nn, np, q, nullptr, kk, s);
+    };
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream query");
+    int s = 0;
+    if (n_steps >= 2 && cap == cudaStreamCaptureStatusNone) {
+        int G = std::min(n_steps, kLlgGraphSteps);
+        unsigned long long *ctr = (unsigned long long *)c->step_ctr.p;
+        LlgConst<T> kk;
+        std::memcpy(&kk, &k, sizeof kk);  // byte copy: the key compares padding too
+        kk.step = 0;
+        kk.step_base = ctr;
+        struct Key {
+            const void *n, *pred, *ctr;
+            int n_rep, solver, cub, per0, per1, G;
+        } key;
+        std::memset(&key, 0, sizeof key);
+        key.n = nn;
+        key.pred = c->pred.p;
+        key.ctr = ctr;
+        key.n_rep = n_rep;
+        key.solver = p->solver;
+        key.cub = cub;
+        key.per0 = per0;
+        key.per1 = per1;
+        key.G = G;
+        std::vector<char> kb(sizeof key + sizeof kk + sizeof S + sizeof CP);
+        std::memcpy(kb.data(), &key, sizeof key);
+        std::memcpy(kb.data() + sizeof key, &kk, sizeof kk);
+        std::memcpy(kb.data() + sizeof key + sizeof kk, &S, sizeof S);
+        std::memcpy(kb.data() + sizeof key + sizeof kk + sizeof S, &CP, sizeof CP);
+        cudaGraphExec_t exec = nullptr;
+        if ((rc = replica_graph<T>(c, kb, G, k, ctr, one_step, &exec))) return rc;
+        k_set_u64<<<1, 1, 0, st>>>(ctr, (unsigned long long)p->step0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "step counter");
+        for (; s + G <= n_steps; s += G)
+            if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return cuda_fail(c, e, "replica graph launch");
+    }
+    for (; s < n_steps; ++s) {
+        k.step = p->step0 + (uint64_t)s;
+        if ((e = one_step(k, st)) != cudaSuccess) return cuda_fail(c, e, "LLG replica launch");
     }
     return SP_OK;
 }
@@ -479,6 +643,10 @@ int sp_destroy(sp_ctx *c)
     if (c->partials.p) cudaFree(c->partials.p);
     if (c->bdd.p) cudaFree(c->bdd.p);
     if (c->qbuf.p) cudaFree(c->qbuf.p);
+    if (c->rsig.p) cudaFree(c->rsig.p);
+    if (c->step_ctr.p) cudaFree(c->step_ctr.p);
+    for (auto &g : c->lg_graphs) cudaGraphExecDestroy(g.exec);
+    if (c->lg_stream) cudaStreamDestroy(c->lg_stream);
     mc_scratch_destroy(c->mc);
     hess_scratch_destroy(c->hess);
     dipole_destroy(c->dip);
@@ -656,6 +824,36 @@ int sp_llg_step(sp_ctx *c, void *n_dev, const sp_llg_params *p, int n_steps, voi
     if (n_steps == 0 || c->N == 0) return SP_OK;
     cudaStream_t st = (cudaStream_t)stream;
     return c->prec == SP_F64 ? llg_run<double>(c, n_dev, p, n_steps, st) : llg_run<float>(c, n_dev, p, n_steps, st);
+}
+
+int sp_llg_step_replicas(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const sp_llg_params *p, int n_steps,
+                         void *stream)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = check_spins(c, spins_dev, "spins"))) return rc;
+    if (!p || !T) return fail(c, SP_ERR_ARG, "NULL parameters or temperatures");
+    if (n_rep < 1) return fail(c, SP_ERR_ARG, "n_rep must be >= 1");
+    if (p->solver < SP_DEPONDT || p->solver > SP_RK4) return fail(c, SP_ERR_ARG, "unknown solver %d", p->solver);
+    if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(c, SP_ERR_ARG, "dt must be positive");
+    if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return fail(c, SP_ERR_ARG, "alpha must be >= 0");
+    for (int r = 0; r < n_rep; ++r)
+        if (!(T[r] >= 0) || !std::isfinite(T[r])) return fail(c, SP_ERR_ARG, "replica %d: T must be >= 0", r);
+    if (n_steps < 0) return fail(c, SP_ERR_ARG, "n_steps must be >= 0");
+    if ((long long)n_rep * c->N >= (1LL << 31)) return fail(c, SP_ERR_ARG, "replicas larger than 2^31 spins");
+    if ((unsigned long long)p->replica + (unsigned long long)n_rep > (1ULL << 29))
+        return fail(c, SP_ERR_ARG, "thermal streams replica .. replica + n_rep - 1 must stay below 2^29");
+    if (c->h.dipole != SP_DIPOLE_NONE) return fail(c, SP_ERR_UNSUPPORTED, "replicas with the dipole term");
+    if (n_steps == 0 || c->N == 0) return SP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_rep == 1) {  // one replica is a plain call at its own temperature
+        sp_llg_params one = *p;
+        one.T = T[0];
+        return c->prec == SP_F64 ? llg_run<double>(c, spins_dev, &one, n_steps, st)
+                                 : llg_run<float>(c, spins_dev, &one, n_steps, st);
+    }
+    return c->prec == SP_F64 ? replicas_run<double>(c, spins_dev, p, n_steps, st, n_rep, T)
+                             : replicas_run<float>(c, spins_dev, p, n_steps, st, n_rep, T);
 }
 
 int sp_minimise(sp_ctx *c, void *n_dev, void *v_dev, double dt, double mass, double tol, int max_iter, int check_every,

@@ -25,6 +25,13 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// An instantiated CUDA graph of a run of LLG steps of a replica batch and
+// the launch configuration it was captured for.
+struct LlgGraph {
+    std::vector<char> key;
+    cudaGraphExec_t exec;
+};
+
 // Pool of CUDA event pairs bracketing kernel launches (sp_profile_*).
 struct Profiler {
     static constexpr int kPairs = 4096;
@@ -118,12 +125,31 @@ struct sp_ctx {
     DevBuf partials;  // reduction partials
     DevBuf bdd;       // dipole field, 1 record per spin
     DevBuf qbuf;      // per-image topological charges of a path analysis
+    DevBuf rsig;      // noise amplitudes of the last batch of replicas
+    std::vector<double> rsig_key;  // what they were computed from
+    DevBuf step_ctr;               // Philox step base of replayed replica graphs
+    std::vector<LlgGraph> lg_graphs;
+    cudaStream_t lg_stream = nullptr;  // capture stream of those graphs
     DipolePlan *dip = nullptr;
     MinScratch *mins = nullptr;
     McScratch *mc = nullptr;
     HessScratch *hess = nullptr;
     Profiler prof;
 };
+
+// Units per CTA of the 27-point path for a batch of n_rep replicas: the
+// user's choice, or all replicas' units spread over one wave of resident CTAs.
+inline int cubic_per_batch(sp_ctx *c, int pass, int n_rep)
+{
+    if (pass == 1 && c->zc_corr > 0) return c->zc_corr;
+    if (c->zc > 0) return c->zc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+    long slots = (long)nsm * cubic_resident_ctas(c->prec, pass);
+    long units = cubic_units(c->nc[0], c->nc[1], c->nc[2]) * n_rep;
+    return (int)std::max(1L, (units + slots - 1) / slots);
+}
 
 // Units per CTA of the 27-point path: the user's choice, or the units spread
 // evenly over one wave of resident CTAs on the current device.

@@ -248,11 +248,14 @@ template <typename T> __device__ __forceinline__ v3<T> onsite(const CubicParams<
 // Plane p lives in tiles[(p - za + 1) % NB]; every fetch is one cp.async
 // group (empty past the segment's last plane), so that waiting for all but
 // the newest NB - 2 groups means "the plane needed next has landed".
-template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB>
+// REPL: the records belong to replica r of a batch (its noise amplitude and
+// thermal stream); otherwise r is 0 and the amplitude is c.sig[0].
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB, bool REPL>
 __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> *__restrict__ src,
                                         rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                         rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
-                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], int x0, int y0, int za, int zb)
+                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], int r, int x0, int y0, int za,
+                                        int zb)
 {
     static_assert(NB >= 2 && NB <= 4, "2 to 4 plane buffers");
     constexpr int QA = PASS == 1 ? SPGB_CUBIC_QAHEAD : 1;
@@ -290,6 +293,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
     }
     if (HAS_BDD && own) bn = ld(Bdd, i);
     int s_next = 2 % NB, s_free = 1;  // slots of planes z+1 and z
+    const uint64_t step = REPL && PASS == 0 ? llg_step_of(c) : c.step;  // Philox step of this launch
     for (int z = za; z < zb; ++z, i += plane_sz) {
         rec_t<T> *bnext = tiles[s_next];  // plane z+1 (landed after the wait)
         rec_t<T> *bfree = tiles[s_free];  // plane z, already summarised
@@ -314,7 +318,11 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
             if (HAS_BDD) B = B + bi;
             if (PASS == 0) {
                 v3<T> Bth = mk(T(0), T(0), T(0));
-                if (c.thermal) Bth = c.sig[0] * thermal_eta(thermal_bits(c, (uint32_t)i), T(0));
+                if (c.thermal)
+                    Bth = (REPL ? c.rsig[r] : c.sig[0]) *
+                          thermal_eta(REPL ? thermal_bits_at(c, step, (uint32_t)i, (uint32_t)r)
+                                           : thermal_bits_at(c, c.step, (uint32_t)i, 0u),
+                                      T(0));
                 v3<T> A = llg_A(c.cA[0], c.alpha, ni, B + Bth);
                 if (SOLVER == SP_HEUN) {
                     v3<T> f = cross(ni, A);
@@ -341,11 +349,12 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
     __syncthreads();  // the next segment reuses the tiles
 }
 
-// The work is the list of (column tile, plane) units, tile-major.  CTA b
+// The work is the list of (column tile, plane) units, tile-major (and
+// replica-major before that in a batch of replicas).  CTA b
 // takes units [b*per, (b+1)*per): a few contiguous runs of planes, each
 // streamed as one segment.  With per = units / (SMs x resident CTAs) every SM
 // gets the same amount of work in a single wave.
-template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD>
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, bool REPL>
 __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
                                                   rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
@@ -354,42 +363,51 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
     constexpr int NB = PASS == 0 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
     __shared__ __align__(32) rec_t<T> tiles[NB][HN];
     int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
-    long total = (long)tiles_x * tiles_y * P.nz;
+    long ntile = (long)tiles_x * tiles_y;
+    long total = ntile * P.nz * (REPL ? llg_reps(c) : 1);
     long u = (long)blockIdx.x * per, u1 = min(u + per, total);
     while (u < u1) {
-        int tile = (int)(u / P.nz), za = (int)(u % P.nz);
+        long tg = u / P.nz;  // tile over all replicas
+        int za = (int)(u % P.nz);
         int zb = (int)min((long)P.nz, za + (u1 - u));
-        segment<T, SOLVER, PASS, DM, HAS_BDD, NB>(P, src, np, q, nout, Bdd, c, tiles, (tile % tiles_x) * TX,
-                                              (tile / tiles_x) * TY, za, zb);
+        int r = REPL ? (int)(tg / ntile) : 0;
+        int tile = (int)(tg - (long)r * ntile);
+        size_t o = REPL ? (size_t)r * ((size_t)P.nx * P.ny * P.nz) : 0;
+        segment<T, SOLVER, PASS, DM, HAS_BDD, NB, REPL>(P, src + o, np ? np + o : np, q + o, nout ? nout + o : nout,
+                                                        Bdd, c, tiles, r, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
+                                                        za, zb);
         u += zb - za;
     }
 }
 
-template <typename T, int DM, bool HB>
+template <typename T, int DM, bool HB, bool RP>
 void launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
                 rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
 {
     if (pass == 0) {
         if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 0, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+            k_cubic<T, SP_HEUN, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
         else
-            k_cubic<T, SP_DEPONDT, 0, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+            k_cubic<T, SP_DEPONDT, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
     } else {
         if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 1, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+            k_cubic<T, SP_HEUN, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
         else
-            k_cubic<T, SP_DEPONDT, 1, DM, HB><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+            k_cubic<T, SP_DEPONDT, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
     }
 }
 
+// (a batch of replicas never carries the dipole field)
 template <typename T, int DM>
 void launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
                rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
 {
-    if (Bdd)
-        launch_dmb<T, DM, true>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    if (llg_reps(c) > 1)
+        launch_dmb<T, DM, false, true>(pass, solver, grid, P, src, np, q, nout, nullptr, c, per, st);
+    else if (Bdd)
+        launch_dmb<T, DM, true, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
     else
-        launch_dmb<T, DM, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+        launch_dmb<T, DM, false, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 }  // namespace
@@ -398,7 +416,7 @@ template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
                          rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
 {
-    long total = cubic_units(P.nx, P.ny, P.nz);
+    long total = cubic_units(P.nx, P.ny, P.nz) * llg_reps(c);
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
     int grid = (int)((total + per - 1) / per);
@@ -418,11 +436,11 @@ int cubic_resident_ctas(int prec, int pass)
     int n = 0;
     cudaError_t e;
     if (pass == 0)
-        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false>, TX * TY, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false>, TX * TY, 0);
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false, false>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false, false>, TX * TY, 0);
     else
-        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 1, 1, false>, TX * TY, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false>, TX * TY, 0);
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 1, 1, false, false>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false, false>, TX * TY, 0);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 

@@ -21,7 +21,8 @@ int cubic_resident_ctas(int prec, int pass);
 
 // pass 0: predictor (stencil on src = n, writes np and q);
 // pass 1: corrector (stencil on src = np, reads q, writes nout = n).
-// CTA b streams the units [b*per, (b+1)*per), tile-major.
+// CTA b streams the units [b*per, (b+1)*per), tile-major; with c.n_rep > 1
+// the units of all replicas (stored one after another), replica-major.
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
                          rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st);

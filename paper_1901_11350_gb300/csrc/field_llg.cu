@@ -44,16 +44,18 @@ cudaError_t launch_field(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> 
 // ---------------------------------------------------------------- LLG
 // Per-spin bodies of the two passes, shared by the grid kernels (records in
 // global memory) and the single-CTA kernel (records in shared memory).
+// (r: the replica within a batch, whose noise amplitudes and thermal stream
+// the predictor uses; the caller offsets the record pointers.)
 template <typename T, int SOLVER, typename R>
 __device__ __forceinline__ void pred_spin(const Stencil<T> &S, const R *n, const rec_t<T> *Bdd, R *np, R *q,
-                                          const LlgConst<T> &c, int i)
+                                          const LlgConst<T> &c, int i, int r = 0)
 {
     int b;
     v3<T> ni = ld(n, i);
     v3<T> B = local_field(S, n, i, ni, b);
     if (Bdd) B = B + ld(Bdd, i);
     v3<T> Bth = mk(T(0), T(0), T(0));
-    if (c.thermal) Bth = c.sig[b] * box_muller(thermal_bits(c, (uint32_t)i), T(0));
+    if (c.thermal) Bth = noise_amp(c, r, b) * box_muller(thermal_bits(c, (uint32_t)i, (uint32_t)r), T(0));
     v3<T> A = llg_A(c.cA[b], c.alpha, ni, B + Bth);
     if (SOLVER == SP_HEUN) {
         v3<T> f = cross(ni, A);
@@ -100,7 +102,9 @@ __global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Ste
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
-    pred_spin<T, SOLVER>(S, n, Bdd, np, q, c, i);
+    int r = blockIdx.y;  // replica
+    size_t o = (size_t)r * S.N;
+    pred_spin<T, SOLVER>(S, n + o, Bdd, np + o, q + o, c, i, r);
 }
 
 template <typename T, int SOLVER>
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Ste
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
-    corr_spin<T, SOLVER>(S, n, np, q, Bdd, c, i);
+    size_t o = (size_t)blockIdx.y * S.N;  // replica
+    corr_spin<T, SOLVER>(S, n + o, np + o, q + o, Bdd, c, i);
 }
 
 // Small FP32 lattices (N <= kSmallMax): one CTA keeps n, np and q in shared
@@ -171,13 +176,13 @@ cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, 
                             rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
-    int bs = llg_block(S.N);
+    int bs = llg_block((long)S.N * llg_reps(c));
     if (solver == SP_HEUN)
-        k_llg_pred<T, SP_HEUN><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_HEUN><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
     else if (solver == SP_SIB)
-        k_llg_pred<T, SP_SIB><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_SIB><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
     else
-        k_llg_pred<T, SP_DEPONDT><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, Bdd, np, q, c);
+        k_llg_pred<T, SP_DEPONDT><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
     return cudaGetLastError();
 }
 
@@ -186,13 +191,13 @@ cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const 
                             const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
-    int bs = llg_block(S.N);
+    int bs = llg_block((long)S.N * llg_reps(c));
     if (solver == SP_HEUN)
-        k_llg_corr<T, SP_HEUN><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_HEUN><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
     else if (solver == SP_SIB)
-        k_llg_corr<T, SP_SIB><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_SIB><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
     else
-        k_llg_corr<T, SP_DEPONDT><<<blocks_for(S.N, bs), bs, 0, st>>>(S, n, np, q, Bdd, c);
+        k_llg_corr<T, SP_DEPONDT><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
     return cudaGetLastError();
 }
 
@@ -209,11 +214,17 @@ __global__ void __launch_bounds__(kBlock) k_rk4(const __grid_constant__ Stencil<
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
+    int r = blockIdx.y;  // replica
+    size_t o = (size_t)r * S.N;
+    n += o;
+    src += o;
+    dst += o;
+    acc += o;
     int b;
     v3<T> y = ld(src, i);
     v3<T> B = local_field(S, src, i, y, b);
     if (Bdd) B = B + ld(Bdd, i);
-    if (c.thermal) B = B + c.sig[b] * box_muller(thermal_bits(c, (uint32_t)i), T(0));
+    if (c.thermal) B = B + noise_amp(c, r, b) * box_muller(thermal_bits(c, (uint32_t)i, (uint32_t)r), T(0));
     v3<T> k = cross(y, llg_A(c.cA[b], c.alpha, y, B));
     v3<T> ni = ldc(n, i);
     if (STAGE == 0) {
@@ -232,7 +243,7 @@ cudaError_t launch_rk4_stage(int stage, const Stencil<T> &S, rec_t<T> *n, const 
                              rec_t<T> *acc, const rec_t<T> *Bdd, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
-    int g = blocks_for(S.N);
+    dim3 g(blocks_for(S.N), llg_reps(c));
     switch (stage) {
     case 0: k_rk4<T, 0><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
     case 1: k_rk4<T, 1><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;

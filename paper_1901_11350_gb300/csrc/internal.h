@@ -16,7 +16,23 @@ template <typename T> struct LlgConst {
     // Philox round keys (k0 + r W0, k1 + r W1), r = 0..9, of `seed`: the
     // kernels read them as operands instead of stepping the key per spin
     uint32_t rk[20];
+    // a batch of replicas: n_rep > 1 copies of the lattice stored one after
+    // another; replica r has the noise amplitudes rsig[r * nb + b] (device)
+    // and the thermal stream replica + r.  n_rep 0 or 1 with rsig null: one
+    // lattice with the amplitudes sig[]
+    int n_rep, nb;
+    const T *rsig;
+    // step_base non-null (a batch of replicas replayed from a CUDA graph):
+    // the Philox step is *step_base + step, the base a device counter the
+    // graph advances
+    const unsigned long long *step_base;
 };
+
+template <typename T> __host__ __device__ inline int llg_reps(const LlgConst<T> &c) { return c.n_rep > 1 ? c.n_rep : 1; }
+template <typename T> __device__ __forceinline__ T noise_amp(const LlgConst<T> &c, int r, int b)
+{
+    return c.rsig ? c.rsig[r * c.nb + b] : c.sig[b];
+}
 
 template <typename T> inline void llg_set_seed(LlgConst<T> &k, uint64_t seed)
 {
@@ -28,11 +44,21 @@ template <typename T> inline void llg_set_seed(LlgConst<T> &k, uint64_t seed)
     }
 }
 
-// The thermal-field counter block of spin i at step c.step (the layout of
-// thermal_bits), through the precomputed round keys.
-template <typename T> __device__ __forceinline__ uint4 thermal_bits(const LlgConst<T> &c, uint32_t i)
+template <typename T> __device__ __forceinline__ uint64_t llg_step_of(const LlgConst<T> &c)
 {
-    return philox4x32_10_keyed(make_uint4(i, (uint32_t)c.step, (uint32_t)(c.step >> 32), c.replica * 8u), c.rk);
+    return c.step_base ? *c.step_base + c.step : c.step;
+}
+
+// The thermal-field counter block of spin i of replica c.replica + r at
+// `step` (the layout of thermal_bits), through the precomputed round keys.
+template <typename T>
+__device__ __forceinline__ uint4 thermal_bits_at(const LlgConst<T> &c, uint64_t step, uint32_t i, uint32_t r)
+{
+    return philox4x32_10_keyed(make_uint4(i, (uint32_t)step, (uint32_t)(step >> 32), (c.replica + r) * 8u), c.rk);
+}
+template <typename T> __device__ __forceinline__ uint4 thermal_bits(const LlgConst<T> &c, uint32_t i, uint32_t r = 0)
+{
+    return thermal_bits_at(c, llg_step_of(c), i, r);
 }
 
 constexpr int kBlock = 256;

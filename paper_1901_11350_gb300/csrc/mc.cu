@@ -329,6 +329,21 @@ int mfail(sp_ctx *c, int code, const char *msg)
     return code;
 }
 
+// Observables of n_rep replicas accumulated into stats (sp_sample).
+template <typename T>
+int sample_run(sp_ctx *c, const Stencil<T> &S, const void *spins, int n_rep, double *stats, cudaStream_t st)
+{
+    McScratch *&ms = c->mc;
+    if (!ms) ms = new McScratch;
+    int bpr = (S.N + kMcBlock - 1) / kMcBlock;
+    if (grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) || grow_buf(ms->cnt, sizeof(unsigned) * n_rep) ||
+        cudaMemsetAsync(ms->cnt.p, 0, sizeof(unsigned) * n_rep, st) != cudaSuccess)
+        return SP_ERR_CUDA;
+    k_mc_sample<T><<<(unsigned)(bpr * n_rep), kMcBlock, 0, st>>>(S, (const rec_t<T> *)spins, bpr, (double *)ms->part.p,
+                                                                 (unsigned *)ms->cnt.p, stats);
+    return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
+}
+
 }  // namespace
 
 void mc_scratch_destroy(McScratch *m)
@@ -373,6 +388,22 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
         return mfail(c, e, "lattice has no colouring (a neighbour beyond the next cell, or an odd periodic size not "
                            "divisible by 3)");
     if (e) return mfail(c, e, "Monte Carlo launch failed");
+    return SP_OK;
+}
+
+int sp_sample(sp_ctx *c, const void *spins_dev, int n_rep, double *stats_dev, void *stream)
+{
+    if (!c) return SP_ERR_ARG;
+    if (!c->have_geom || !c->have_ham) return mfail(c, SP_ERR_STATE, "context not configured");
+    if (!spins_dev || !stats_dev) return mfail(c, SP_ERR_ARG, "NULL argument");
+    if ((uintptr_t)spins_dev % (c->prec == SP_F64 ? 32 : 16)) return mfail(c, SP_ERR_ARG, "spins misaligned");
+    if (n_rep < 1) return mfail(c, SP_ERR_ARG, "n_rep must be >= 1");
+    if ((long long)n_rep * c->N >= (1LL << 31)) return mfail(c, SP_ERR_ARG, "more than 2^31 spins");
+    if (c->h.dipole != SP_DIPOLE_NONE) return mfail(c, SP_ERR_UNSUPPORTED, "observables with the dipole term");
+    if (c->N == 0) return SP_OK;
+    int e = c->prec == SP_F64 ? sample_run<double>(c, c->Sd, spins_dev, n_rep, stats_dev, (cudaStream_t)stream)
+                              : sample_run<float>(c, c->Sf, spins_dev, n_rep, stats_dev, (cudaStream_t)stream);
+    if (e) return mfail(c, e, "observable sampling launch failed");
     return SP_OK;
 }
 

@@ -159,3 +159,31 @@ def test_option_round_trip_and_rejections():
     c.set_option("generic_stencil", 1)
     assert c.get_option("generic_stencil") == 1
     c.close()
+
+
+def test_replica_and_sample_rejections():
+    c = B.Context(I.simple_cubic(6), dict(J=[1.0]), "f32")
+    L = B.lib()
+    h = c._h
+    p = B.LLGParams(1, 1e-3, 0.1, 0.0, 0, 0, 0)
+    T2 = (C.c_double * 2)(5.0, 10.0)
+    bad = (C.c_double * 2)(5.0, -1.0)
+    spins = C.c_void_p(256)  # never dereferenced: every call below fails or returns before a launch
+    assert L.sp_llg_step_replicas(h, spins, 0, T2, C.byref(p), 1, None) == -1
+    assert L.sp_llg_step_replicas(h, spins, 2, None, C.byref(p), 1, None) == -1
+    assert L.sp_llg_step_replicas(h, spins, 2, bad, C.byref(p), 1, None) == -1
+    assert b"replica 1" in L.sp_last_error(h)
+    assert L.sp_llg_step_replicas(h, spins, 2, T2, C.byref(p), -1, None) == -1
+    assert L.sp_llg_step_replicas(h, C.c_void_p(8), 2, T2, C.byref(p), 1, None) == -1  # misaligned
+    p.replica = (1 << 29) - 1
+    assert L.sp_llg_step_replicas(h, spins, 2, T2, C.byref(p), 1, None) == -1  # thermal stream overflow
+    p.replica = 0
+    assert L.sp_llg_step_replicas(h, spins, 2, T2, C.byref(p), 0, None) == 0  # nothing to do
+    assert L.sp_sample(h, spins, 2, None, None) == -1
+    assert L.sp_sample(h, spins, 0, C.c_void_p(512), None) == -1
+    assert L.sp_sample(h, C.c_void_p(8), 1, C.c_void_p(512), None) == -1
+    c.close()
+    d = B.Context(I.square(8, 8), dict(J=[1.0], dipole="fft"), "f32")
+    assert L.sp_llg_step_replicas(d._h, spins, 2, T2, C.byref(p), 1, None) == -4
+    assert L.sp_sample(d._h, spins, 1, C.c_void_p(512), None) == -4
+    d.close()
