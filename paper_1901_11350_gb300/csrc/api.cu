@@ -181,6 +181,11 @@ template <typename T> void fill_stencil(const sp_ctx *c, Stencil<T> &S)
                 E.Dx = (T)e.D[0];
                 E.Dy = (T)e.D[1];
                 E.Dz = (T)e.D[2];
+                // i = b + nb (c0 + n0 (c1 + n1 c2)), j the same with jb, c + d
+                E.lin = (e.jb - b) + c->nb * (e.d[0] + c->nc[0] * (e.d[1] + c->nc[1] * e.d[2]));
+                S.r0 = std::max(S.r0, std::abs(e.d[0]));
+                S.r1 = std::max(S.r1, std::abs(e.d[1]));
+                S.r2 = std::max(S.r2, std::abs(e.d[2]));
             }
     }
 }

@@ -127,6 +127,7 @@ __device__ __forceinline__ void st(dq4 *p, long i, v3<double> v)
 // DMI vector D_ij as seen from the centre atom.
 template <typename T> struct NbrEntry {
     int jb, d0, d1, d2;
+    int lin;  // j - i for a site whose neighbours need no wrap (see Stencil::r0)
     T J, Dx, Dy, Dz;
 };
 
@@ -161,6 +162,7 @@ __device__ __forceinline__ int fdiv(int n, const FastDiv &f)
 // by value as a __grid_constant__ kernel parameter (about 3-5 KB).
 template <typename T> struct Stencil {
     int nb, n0, n1, n2, per0, per1, per2, N;
+    int r0, r1, r2;             // largest |d| of the entries along each direction
     FastDiv fnb, fn0, fn1;      // division by nb, n0, n1
     int off[SP_MAX_BASIS + 1];  // entries of basis b: [off[b], off[b+1])
     T mu[SP_MAX_BASIS];         // mu_b mu_B, meV/T
@@ -195,6 +197,28 @@ __device__ __forceinline__ void decode_site(const Stencil<T> &S, int i, int &b, 
 
 // Local part of B_eff = -dH/dn at spin i (Eq. 1 without the dipole term):
 // mu_i B + 2 K (Khat.n_i) Khat + sum_j [J_ij n_j + n_j x D_ij].
+// Sites at least r0, r1, r2 cells from every edge take their neighbours at
+// the fixed offsets i + lin (the same indices the wrap gives).
+template <typename T>
+__device__ __forceinline__ bool interior_site(const Stencil<T> &S, int c0, int c1, int c2)
+{
+    return c0 >= S.r0 && c0 < S.n0 - S.r0 && c1 >= S.r1 && c1 < S.n1 - S.r1 && c2 >= S.r2 && c2 < S.n2 - S.r2;
+}
+
+// Index of the neighbour of entry E of site i = (b, c0, c1, c2), or -1
+// across an open edge.
+template <typename T>
+__device__ __forceinline__ int nbr_index(const Stencil<T> &S, const NbrEntry<T> &E, int i, bool inner, int c0, int c1,
+                                         int c2)
+{
+    if (inner) return i + E.lin;
+    int x0 = wrap(c0 + E.d0, S.n0, S.per0);
+    int x1 = wrap(c1 + E.d1, S.n1, S.per1);
+    int x2 = wrap(c2 + E.d2, S.n2, S.per2);
+    if ((x0 | x1 | x2) < 0) return -1;
+    return E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+}
+
 template <typename T, typename R>
 __device__ __forceinline__ v3<T> local_field(const Stencil<T> &S, const R *n, int i, v3<T> ni, int &b)
 {
@@ -203,13 +227,11 @@ __device__ __forceinline__ v3<T> local_field(const Stencil<T> &S, const R *n, in
     T kn = dot(mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]), ni);
     T k2 = T(2) * S.K[b] * kn;
     v3<T> B = mk(fma(k2, S.Kh[b][0], S.Bz[b][0]), fma(k2, S.Kh[b][1], S.Bz[b][1]), fma(k2, S.Kh[b][2], S.Bz[b][2]));
+    const bool inner = interior_site(S, c0, c1, c2);
     for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
         const NbrEntry<T> &E = S.e[q];
-        int x0 = wrap(c0 + E.d0, S.n0, S.per0);
-        int x1 = wrap(c1 + E.d1, S.n1, S.per1);
-        int x2 = wrap(c2 + E.d2, S.n2, S.per2);
-        if ((x0 | x1 | x2) < 0) continue;
-        int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+        int j = nbr_index(S, E, i, inner, c0, c1, c2);
+        if (j < 0) continue;
         v3<T> nj = ld(n, j);
         v3<T> c = cross(nj, mk(E.Dx, E.Dy, E.Dz));
         B = axpy(E.J, nj, B + c);

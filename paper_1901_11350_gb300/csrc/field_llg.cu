@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
     if (i < S.N) {
         int b, c0, c1, c2;
         decode_site(S, i, b, c0, c1, c2);
+        const bool inner = interior_site(S, c0, c1, c2);
         v3<T> ni = ld(n, i);
         v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
         v3<T> Kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
@@ -276,11 +277,8 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
         v3<T> Bx = mk(T(0), T(0), T(0)), Bd = mk(T(0), T(0), T(0));
         for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
             const NbrEntry<T> &E = S.e[q];
-            int x0 = wrap(c0 + E.d0, S.n0, S.per0);
-            int x1 = wrap(c1 + E.d1, S.n1, S.per1);
-            int x2 = wrap(c2 + E.d2, S.n2, S.per2);
-            if ((x0 | x1 | x2) < 0) continue;
-            int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+            int j = nbr_index(S, E, i, inner, c0, c1, c2);
+            if (j < 0) continue;
             v3<T> nj = ld(n, j);
             Bx = axpy(E.J, nj, Bx);
             Bd = Bd + cross(nj, mk(E.Dx, E.Dy, E.Dz));

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> 
     if (i >= S.N) return;
     int b, c0, c1, c2;
     decode_site(S, i, b, c0, c1, c2);
+    const bool inner = interior_site(S, c0, c1, c2);
     v3<T> ni = ld(n, i), vi = ld(v, i);
     v3<T> wi = vi - dot(vi, ni) * ni;
     v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
@@ -57,11 +58,8 @@ __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> 
     v3<T> Lw = (T(2) * S.K[b] * dot(kh, wi)) * kh;
     for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
         const NbrEntry<T> &E = S.e[q];
-        int x0 = wrap(c0 + E.d0, S.n0, S.per0);
-        int x1 = wrap(c1 + E.d1, S.n1, S.per1);
-        int x2 = wrap(c2 + E.d2, S.n2, S.per2);
-        if ((x0 | x1 | x2) < 0) continue;
-        int j = E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2));
+        int j = nbr_index(S, E, i, inner, c0, c1, c2);
+        if (j < 0) continue;
         v3<T> nj = ld(n, j), vj = ld(v, j);
         v3<T> wj = vj - dot(vj, nj) * nj;
         v3<T> D = mk(E.Dx, E.Dy, E.Dz);

@@ -15,6 +15,7 @@
 //           v.F', F'.F', max |F'|
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -33,8 +34,12 @@ struct BlkInfo {
     int g, t;
 };
 
-// per-image scalar slots (8 doubles per image)
-enum { kE = 0, kL2 = 1, kTT = 2, kGT = 3, kVF = 4, kFF = 5, kFMAX = 6, kLW = 7 };
+// per-image scalar slots (kS doubles per image): energy, squared geodesic
+// distance to the next image, |tau|^2, Pg.tau, v.F, F.F, max_i |F_i|^2,
+// energy-weighted segment length, tangent weights of the forward and
+// backward differences, force coefficient a (F = -Pg + a tau), velocity
+// projection coefficient v.F / F.F
+enum { kE = 0, kL2, kTT, kGT, kVF, kFF, kFMAX, kLW, kWP, kWM, kA, kC, kS = 16 };
 
 struct Buf {
     void *p = nullptr;
@@ -107,61 +112,115 @@ int grow_counters(Buf &b, size_t n, cudaStream_t st)
     return cudaMemsetAsync(b.p, 0, b.bytes, st) == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
 
+// An unevaluated sum hi + lo of two floats (about 48 significant bits):
+// FP32 sums whose result must match an FP64 sum without the FP64 pipe, which
+// is a small fraction of the FP32 rate on this part.  Knuth's TwoSum and
+// the FMA-exact product.
+struct f2sum {
+    float hi, lo;
+};
+__device__ __forceinline__ f2sum two_sum(float a, float b)
+{
+    float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2sum operator+(f2sum a, f2sum b)
+{
+    f2sum s = two_sum(a.hi, b.hi);
+    float lo = s.lo + (a.lo + b.lo), hi = s.hi + lo;
+    return {hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ bool operator>(f2sum a, f2sum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ f2sum exact_square(float a) { return {a * a, fmaf(a, a, -(a * a))}; }
+__device__ __forceinline__ f2sum exact_dot(v3<float> a, v3<float> b)
+{
+    float p0 = a.x * b.x, p1 = a.y * b.y, p2 = a.z * b.z;
+    return f2sum{p0, fmaf(a.x, b.x, -p0)} + f2sum{p1, fmaf(a.y, b.y, -p1)} + f2sum{p2, fmaf(a.z, b.z, -p2)};
+}
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ f2sum shfl_down(f2sum v, int o)
+{
+    return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double to_double(float v) { return v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(f2sum v) { return (double)v.hi + (double)v.lo; }
+
 template <int NV, typename V>
 __device__ __forceinline__ V combine(int k, unsigned maxmask, V a, V b)
 {
     return ((maxmask >> k) & 1u) ? (a > b ? a : b) : a + b;
 }
 
+struct NoPost {
+    __device__ void operator()(double *) const {}
+};
+
 // Deterministic per-image reduction of NV values (bit k of maxmask: max
-// instead of sum).  Every thread of every block of the image must call it.
-// The warp-level step runs in the values' own type V; warp results, block
-// partials and the image total are FP64.
-template <int NV, typename V>
+// instead of sum; maxima are of non-negative values, 0 is their identity).
+// Every thread of every block of the image must call it.  The warp-level
+// step runs in the values' own type V (float, double or f2sum); from the warp
+// results on everything is FP64.  After one barrier warps 1.. leave; warp 0
+// combines the warp results by a fixed shuffle tree into the block's partial
+// and takes a ticket; warp 0 of the image's last block sums the partials
+// (lane l takes partials l, l + 32, ..., then a shuffle tree), writes the
+// totals to out[] and calls post(out).
+template <int NV, typename V, typename Post = NoPost>
 __device__ void image_reduce(V (&v)[NV], unsigned maxmask, double *__restrict__ part, int blk, int blk0, int bpi,
-                             unsigned *counter, double *out)
+                             unsigned *counter, double *out, Post post = Post())
 {
-    __shared__ double sh[kBlock / 32][NV];
-    __shared__ double red[kBlock][NV];
-    __shared__ int last;
+    constexpr int NW = kBlock / 32;
+    static_assert(NW <= 32, "one warp combines the warp results");
+    __shared__ double sh[NW][NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] = combine<NV>(k, maxmask, v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+        for (int o = 16; o > 0; o >>= 1) v[k] = combine<NV>(k, maxmask, v[k], shfl_down(v[k], o));
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0)
-        for (int k = 0; k < NV; ++k) sh[w][k] = (double)v[k];
+        for (int k = 0; k < NV; ++k) sh[w][k] = to_double(v[k]);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NV; ++k) {
-            double a = sh[0][k];
-            for (int ww = 1; ww < kBlock / 32; ++ww) a = combine<NV, double>(k, maxmask, a, sh[ww][k]);
-            part[(size_t)blk * NV + k] = a;
-        }
+    if (w != 0) return;
+    double a[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        a[k] = l < NW ? sh[l][k] : 0.0;
+        for (int o = NW / 2; o > 0; o >>= 1) a[k] = combine<NV, double>(k, maxmask, a[k], shfl_down(a[k], o));
+    }
+    int last = 0;
+    if (l == 0) {
+        for (int k = 0; k < NV; ++k) part[(size_t)blk * NV + k] = a[k];
         __threadfence();
         unsigned ticket = atomicAdd(counter, 1u);
-        last = (ticket == (unsigned)(bpi - 1));
+        last = ticket == (unsigned)(bpi - 1);
     }
-    __syncthreads();
-    if (!last) return;
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
     __threadfence();
     double acc[NV];
+#pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int p = threadIdx.x; p < bpi; p += kBlock)
+    for (int p = l; p < bpi; p += 32)
         for (int k = 0; k < NV; ++k)
             acc[k] = combine<NV, double>(k, maxmask, acc[k], __ldcg(&part[(size_t)(blk0 + p) * NV + k]));
-    for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = acc[k];
-    __syncthreads();
-    for (int s = kBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < NV; ++k)
-                red[threadIdx.x][k] = combine<NV, double>(k, maxmask, red[threadIdx.x][k], red[threadIdx.x + s][k]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NV; ++k) out[k] = red[0][k];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] = combine<NV, double>(k, maxmask, acc[k], shfl_down(acc[k], o));
+    if (l == 0) {
+        for (int k = 0; k < NV; ++k) out[k] = acc[k];
+        post(out);
         atomicExch(counter, 0u);
     }
 }
+
+// After a force pass (out = scal + kS g + kVF): the projection coefficient
+// v.F / F.F (0 unless both are positive) of the next move.
+struct ProjectionPost {
+    __device__ void operator()(double *out) const
+    {
+        double vf = out[kVF - kVF], ff = out[kFF - kVF];
+        out[kC - kVF] = (vf > 0 && ff > 0) ? vf / ff : 0.0;
+    }
+};
 
 // ============================================================ VP minimiser
 // state (ints): [0] iterations performed, [1] active flag
@@ -171,7 +230,7 @@ __device__ void image_reduce(V (&v)[NV], unsigned maxmask, double *__restrict__ 
 // exactly max |F| in FP64)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ x,
-                                                     rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, double dth_m,
+                                                     rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, T dth_m,
                                                      int mode, double *part, unsigned *cnt, double *scal,
                                                      const int *state)
 {
@@ -198,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Ste
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
-                                                    const rec_t<T> *__restrict__ F, double dt, double dt2_2m, double tol,
+                                                    const rec_t<T> *__restrict__ F, T dt, T dt2_2m, double tol,
                                                     int k, int max_iter, const double *scal, int *state)
 {
     __shared__ T s_c;
@@ -240,23 +299,33 @@ __global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ 
     const Stencil<T> &St = S[im.chain];
     int i = bi.t * kBlock + threadIdx.x;
     const rec_t<T> *xb = x + im.spin0 + (long long)im.nu * im.N;
-    double r[2] = {0, 0};
+    // energy and squared angle sums: FP64, or float-float for FP32 (the
+    // same sums of the same products to ~1e-14, off the FP64 pipe)
+    using A = typename std::conditional<std::is_same<T, float>::value, f2sum, double>::type;
+    A r[2] = {A{}, A{}};
     if (i < im.N) {
         int b;
         v3<T> ni = ld(xb, i);
         v3<T> B = local_field(St, xb, i, ni, b);
         v3<T> Bz = mk(St.Bz[b][0], St.Bz[b][1], St.Bz[b][2]);
-        r[0] = -0.5 * ddot(ni, B + Bz);
         v3<T> pg = dot(B, ni) * ni - B;  // tangent-space part of dH/dn = -B
         st(G, im.spin0 + (long long)im.nu * im.N + i, pg);
+        T th = T(0);
         if (im.nu < im.M - 1) {
             v3<T> nj = ld(xb + im.N, i);
             v3<T> c = cross(ni, nj);
-            T th = atan2(sqrt(dot(c, c)), dot(ni, nj));
-            r[1] = (double)th * (double)th;
+            th = atan2(sqrt(dot(c, c)), dot(ni, nj));
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            f2sum e = exact_dot(ni, B + Bz);
+            r[0] = f2sum{-0.5f * e.hi, -0.5f * e.lo};
+            r[1] = exact_square(th);
+        } else {
+            r[0] = -0.5 * ddot(ni, B + Bz);
+            r[1] = th * th;
         }
     }
-    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kE);
+    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kE);
 }
 
 template <typename T>
@@ -269,51 +338,71 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
     ImgInfo im = img[bi.g];
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
-    double r[2] = {0, 0};
-    if (i < im.N && (im.nu == 0 || im.nu == im.M - 1)) {
+    bool end = im.nu == 0 || im.nu == im.M - 1;
+    // weights of the forward and backward differences (k_g_weights)
+    __shared__ T s_wp, s_wm;
+    if (threadIdx.x == 0 && !end) {
+        s_wp = (T)scal[kS * bi.g + kWP];
+        s_wm = (T)scal[kS * bi.g + kWM];
+    }
+    __syncthreads();
+    T r[2] = {0, 0};
+    if (i < im.N && end) {
         // endpoints: one-sided difference to the neighbouring image (only its
         // slope dE/dr is used, for the interpolated path energy)
         v3<T> xi = ld(x, p);
         v3<T> t = im.nu == 0 ? ld(x, p + im.N) - xi : xi - ld(x, p - im.N);
         t = t - dot(t, xi) * xi;
         st(Tau, p, t);
-        r[0] = (double)dot(t, t);
-        r[1] = (double)dot(ldc(G, p), t);
+        r[0] = dot(t, t);
+        r[1] = dot(ldc(G, p), t);
     } else if (i < im.N) {
-        double Ep = scal[8 * (bi.g + 1) + kE], E0 = scal[8 * bi.g + kE], Em = scal[8 * (bi.g - 1) + kE];
-        double wp, wm;
-        // improved tangent (Henkelman and Jonsson 2000)
-        if (Ep > E0 && E0 > Em) {
-            wp = 1;
-            wm = 0;
-        } else if (Ep < E0 && E0 < Em) {
-            wp = 0;
-            wm = 1;
-        } else {
-            double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
-            if (Ep > Em) {
-                wp = dmax;
-                wm = dmin;
-            } else {
-                wp = dmin;
-                wm = dmax;
-            }
-        }
         v3<T> xi = ld(x, p), xp = ld(x, p + im.N), xm = ld(x, p - im.N);
-        v3<T> t = axpy((T)wp, xp - xi, (T)wm * (xi - xm));
+        v3<T> t = axpy(s_wp, xp - xi, s_wm * (xi - xm));
         t = t - dot(t, xi) * xi;
         st(Tau, p, t);
-        r[0] = (double)dot(t, t);
-        r[1] = (double)dot(ldc(G, p), t);
+        r[0] = dot(t, t);
+        r[1] = dot(ldc(G, p), t);
     }
-    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kTT);
+    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kTT);
+}
+
+// Weights of the forward and backward differences in the improved tangent
+// (Henkelman and Jonsson 2000) of every interior image, from the energies of
+// the field pass; one thread per image.
+__global__ void k_g_weights(const ImgInfo *__restrict__ img, int n_img, double *scal)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_img) return;
+    ImgInfo im = img[g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    double Ep = scal[kS * (g + 1) + kE], E0 = scal[kS * g + kE], Em = scal[kS * (g - 1) + kE];
+    double wp, wm;
+    if (Ep > E0 && E0 > Em) {
+        wp = 1;
+        wm = 0;
+    } else if (Ep < E0 && E0 < Em) {
+        wp = 0;
+        wm = 1;
+    } else {
+        double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+        if (Ep > Em) {
+            wp = dmax;
+            wm = dmin;
+        } else {
+            wp = dmin;
+            wm = dmax;
+        }
+    }
+    scal[kS * g + kWP] = wp;
+    scal[kS * g + kWM] = wm;
 }
 
 // Slope dE/dr of image g along its normalised tangent.
 __device__ __forceinline__ double slope_of(const double *scal, int g)
 {
-    double tt = scal[8 * g + kTT];
-    return tt > 0 ? scal[8 * g + kGT] / sqrt(tt) : 0.0;
+    double tt = scal[kS * g + kTT];
+    return tt > 0 ? scal[kS * g + kGT] / sqrt(tt) : 0.0;
 }
 
 // Energy-weighted length of the segment from image a to a+1 (reading of the
@@ -367,76 +456,95 @@ __global__ void k_g_seglen(const ImgInfo *__restrict__ img, int n_img, double w,
     if (g >= n_img) return;
     ImgInfo im = img[g];
     if (im.nu >= im.M - 1) return;
-    scal[8 * g + kLW] = seg_length(scal[8 * g + kE], scal[8 * (g + 1) + kE], slope_of(scal, g), slope_of(scal, g + 1),
-                                   sqrt(scal[8 * g + kL2]), w);
+    scal[kS * g + kLW] = seg_length(scal[kS * g + kE], scal[kS * (g + 1) + kE], slope_of(scal, g), slope_of(scal, g + 1),
+                                   sqrt(scal[kS * g + kL2]), w);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
-                                                    rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
-                                                    const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
-                                                    double kspring, int climbing, int weighted, double dth_m, int mode,
-                                                    double *part, unsigned *cnt, double *scal)
+// The force coefficient a of every interior image (F = -Pg + a tau):
+// climbing image (the chain's highest interior image when climbing is on and
+// the image has no fixed kind): a = 2 Pg.tau / |tau|^2; falling image: 0;
+// otherwise (Pg.tau / |tau| + k (l_g - l_{g-1})) / |tau|, l the geodesic or
+// energy-weighted segment lengths.  One thread per image.
+__global__ void k_g_coef(const ImgInfo *__restrict__ img, int n_img, double kspring, int climbing, int weighted,
+                         double *scal)
 {
-    BlkInfo bi = blk[blockIdx.x];
-    ImgInfo im = img[bi.g];
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_img) return;
+    ImgInfo im = img[g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
     int ci = -1;
     if (climbing && im.kind < 0) {
         ci = 1;
-        double best = scal[8 * (im.g0 + 1) + kE];
+        double best = scal[kS * (im.g0 + 1) + kE];
         for (int nu = 2; nu < im.M - 1; ++nu) {
-            double e = scal[8 * (im.g0 + nu) + kE];
+            double e = scal[kS * (im.g0 + nu) + kE];
             if (e > best) {
                 best = e;
                 ci = nu;
             }
         }
     }
+    double tt = scal[kS * g + kTT];
+    double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
+    double gt = scal[kS * g + kGT] * inv;
+    double fs = weighted ? kspring * (scal[kS * g + kLW] - scal[kS * (g - 1) + kLW])
+                         : kspring * (sqrt(scal[kS * g + kL2]) - sqrt(scal[kS * (g - 1) + kL2]));
+    int kind = im.kind >= 0 ? im.kind : (im.nu == ci ? SP_IMAGE_CLIMBING : SP_IMAGE_NORMAL);
+    // climbing: tangential component inverted, no spring; falling: the full
+    // projected gradient, no spring (descends to a minimum along the path)
+    double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : gt + fs);
+    scal[kS * g + kA] = coef * inv;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                    rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
+                                                    const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
+                                                    T dth_m, int mode, double *part, unsigned *cnt, double *scal)
+{
+    BlkInfo bi = blk[blockIdx.x];
+    ImgInfo im = img[bi.g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    // the image's force is -G + a Tau (a from k_g_coef)
+    __shared__ T s_a;
+    if (threadIdx.x == 0) s_a = (T)scal[kS * bi.g + kA];
+    __syncthreads();
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
-    double r[3] = {0, 0, 0};
+    T r[3] = {0, 0, 0};
     if (i < im.N) {
-        double tt = scal[8 * bi.g + kTT];
-        double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
-        double gt = scal[8 * bi.g + kGT] * inv;
-        double fs = weighted ? kspring * (scal[8 * bi.g + kLW] - scal[8 * (bi.g - 1) + kLW])
-                             : kspring * (sqrt(scal[8 * bi.g + kL2]) - sqrt(scal[8 * (bi.g - 1) + kL2]));
-        int kind = im.kind >= 0 ? im.kind : (im.nu == ci ? SP_IMAGE_CLIMBING : SP_IMAGE_NORMAL);
-        // climbing: tangential component inverted, no spring; falling: the full
-        // projected gradient, no spring (descends to a minimum along the path)
-        double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : gt + fs);
-        v3<T> Fn = axpy((T)(coef * inv), ld(Tau, p), -ldc(G, p));
+        v3<T> Fn = axpy(s_a, ld(Tau, p), -ldc(G, p));
         if (mode == 1) {
             v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
             st(v, p, vi);
-            r[0] = (double)dot(vi, Fn);
+            r[0] = dot(vi, Fn);
         }
         st(F, p, Fn);
-        r[1] = (double)dot(Fn, Fn);
-        r[2] = sqrt(r[1]);
+        r[1] = dot(Fn, Fn);
+        r[2] = r[1];  // max |F|^2; the image's max |F| is its square root
     }
-    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kVF);
+    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kVF, ProjectionPost());
 }
 
 // mode 0: move; 1: project then move; 2: project only
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
                                                    rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
-                                                   const rec_t<T> *__restrict__ F, double dt, double dt2_2m, int mode,
+                                                   const rec_t<T> *__restrict__ F, T dt, T dt2_2m, int mode,
                                                    const double *scal)
 {
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
+    __shared__ T s_c;  // projection coefficient of the last force pass
+    if (threadIdx.x == 0 && mode >= 1) s_c = (T)scal[kS * bi.g + kC];
+    __syncthreads();
     int i = bi.t * kBlock + threadIdx.x;
     if (i >= im.N) return;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     v3<T> vi;
     if (mode >= 1) {
-        double vf = scal[8 * bi.g + kVF], ff = scal[8 * bi.g + kFF];
-        T c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
-        vi = c * ldc(F, p);
+        vi = s_c * ldc(F, p);
         st(v, p, vi);
     } else {
         vi = ldc(v, p);
@@ -447,12 +555,12 @@ __global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ b
 __global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const double *scal, double *E, double *fmax_out,
                            int n_chains)
 {
-    for (int g = threadIdx.x; g < n_img; g += blockDim.x) E[g] = scal[8 * g + kE];
+    for (int g = threadIdx.x; g < n_img; g += blockDim.x) E[g] = scal[kS * g + kE];
     for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
         double m = 0;
         for (int g = 0; g < n_img; ++g)
-            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = fmax(m, scal[8 * g + kFMAX]);
-        fmax_out[c] = m;
+            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = fmax(m, scal[kS * g + kFMAX]);
+        fmax_out[c] = sqrt(m);  // the slot holds max |F|^2
     }
 }
 
@@ -510,7 +618,7 @@ int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const Mi
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
                                                       const Stencil<T> *__restrict__ S, const rec_t<T> *__restrict__ x,
-                                                      rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, double dth_m,
+                                                      rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F, T dth_m,
                                                       int mode, double *part, unsigned *cnt, double *scal,
                                                       const int *state, int *proj)
 {
@@ -536,25 +644,24 @@ __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict_
         r[1] = dot(Fn, Fn);
         r[2] = r[1];
     }
-    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + 8 * bi.g + kVF);
+    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kVF, ProjectionPost());
     if (bi.t == 0 && threadIdx.x == 0) proj[bi.g] = mode;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_bvp_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
                                                      rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
-                                                     const rec_t<T> *__restrict__ F, double dt, double dt2_2m, double tol,
+                                                     const rec_t<T> *__restrict__ F, T dt, T dt2_2m, double tol,
                                                      int k, int max_iter, const double *scal, int *state,
                                                      const int *proj)
 {
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
-    const double *sc = scal + 8 * bi.g;
+    const double *sc = scal + kS * bi.g;
     __shared__ T s_c;
     __shared__ int s_done;
     if (threadIdx.x == 0) {
-        double vf = sc[kVF], ff = sc[kFF];
-        s_c = (vf > 0 && ff > 0) ? (T)(vf / ff) : T(0);
+        s_c = (T)sc[kC];
         s_done = (sqrt(sc[kFMAX]) < tol) || (k >= max_iter);
     }
     __syncthreads();
@@ -600,7 +707,7 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
     int n_full = (int)blk.size();
     size_t rb = sizeof(rec_t<T>) * (size_t)std::max(total, 1LL);
     // blk holds the full table followed by room for a compacted copy
-    if (grow(s->F, rb) || grow(s->scal, 8 * sizeof(double) * C) || grow(s->part, 3 * sizeof(double) * (size_t)n_full) ||
+    if (grow(s->F, rb) || grow(s->scal, kS * sizeof(double) * C) || grow(s->part, 3 * sizeof(double) * (size_t)n_full) ||
         grow_counters(s->cnt, C, st) || grow(s->blk, 2 * sizeof(BlkInfo) * n_full) ||
         grow(s->img, sizeof(ImgInfo) * C) || grow(s->sten, sizeof(Stencil<T>) * C) ||
         grow(s->state, sizeof(int) * 3 * C))
@@ -657,14 +764,14 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
     // final projection (where the last force pass updated the velocity)
     k_bvp_move<T><<<n_full, kBlock, 0, st>>>(Bfull, I, x, v, F, a.dt, dt2_2m, a.tol, a.max_iter, a.max_iter, scal, state,
                                              proj);
-    std::vector<double> hsc(8 * C);
+    std::vector<double> hsc(kS * C);
     if (cudaMemcpyAsync(hs.data(), state, sizeof(int) * 2 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(hsc.data(), scal, sizeof(double) * 8 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hsc.data(), scal, sizeof(double) * kS * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return SP_ERR_CUDA;
     for (int c = 0; c < C; ++c) {
         iters[c] = hs[2 * c];
-        max_torque[c] = sqrt(hsc[8 * c + kFMAX]);
+        max_torque[c] = sqrt(hsc[kS * c + kFMAX]);
     }
     return 0;
 }
@@ -696,7 +803,7 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     }
     int n_img = (int)img.size(), n_blk = (int)blk.size();
     size_t rb = sizeof(rec_t<T>) * (size_t)std::max(total, 1LL);
-    if (grow(s->F, rb) || grow(s->G, rb) || grow(s->Tau, rb) || grow(s->scal, 8 * sizeof(double) * n_img) ||
+    if (grow(s->F, rb) || grow(s->G, rb) || grow(s->Tau, rb) || grow(s->scal, kS * sizeof(double) * n_img) ||
         grow(s->part, 3 * sizeof(double) * (size_t)n_blk) || grow_counters(s->cnt, n_img, st) ||
         grow(s->blk, sizeof(BlkInfo) * n_blk) || grow(s->img, sizeof(ImgInfo) * n_img) ||
         grow(s->sten, sizeof(Stencil<T>) * C))
@@ -726,12 +833,14 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     unsigned *cnt = (unsigned *)s->cnt.p;
     double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
     const int weighted = a.w != 0.0;
+    const int ib = (n_img + 127) / 128;
     auto forces = [&](int mode, cudaStream_t ss) {
         k_g_field<T><<<n_blk, kBlock, 0, ss>>>(B, I, Sd, x, G, part, cnt, scal);
+        k_g_weights<<<ib, 128, 0, ss>>>(I, n_img, scal);
         k_g_tangent<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, G, Tau, part, cnt, scal);
-        if (weighted) k_g_seglen<<<(n_img + 127) / 128, 128, 0, ss>>>(I, n_img, a.w, scal);
-        k_g_force<T><<<n_blk, kBlock, 0, ss>>>(B, I, v, F, G, Tau, a.k, a.climbing, weighted, dth_m, mode, part, cnt,
-                                              scal);
+        if (weighted) k_g_seglen<<<ib, 128, 0, ss>>>(I, n_img, a.w, scal);
+        k_g_coef<<<ib, 128, 0, ss>>>(I, n_img, a.k, a.climbing, weighted, scal);
+        k_g_force<T><<<n_blk, kBlock, 0, ss>>>(B, I, v, F, G, Tau, dth_m, mode, part, cnt, scal);
     };
     auto iteration = [&](cudaStream_t ss) {
         k_g_move<T><<<n_blk, kBlock, 0, ss>>>(B, I, x, v, F, a.dt, dt2_2m, 1, scal);
@@ -810,15 +919,15 @@ int gneb_path_scalars(MinScratch **sp, const Stencil<T> &S, const void *chain, i
     rc = gneb_batch_run<T>(sp, sv, std::vector<int>{M}, std::vector<long long>{0}, const_cast<void *>(chain),
                            const_cast<void *>(chain), a, Ed, Ed + M, st);
     if (rc) return rc;
-    std::vector<double> sc(8 * (size_t)M);
-    if (cudaMemcpyAsync(sc.data(), (*sp)->scal.p, sizeof(double) * 8 * M, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    std::vector<double> sc(kS * (size_t)M);
+    if (cudaMemcpyAsync(sc.data(), (*sp)->scal.p, sizeof(double) * kS * M, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return SP_ERR_CUDA;
     for (int g = 0; g < M; ++g) {
-        E[g] = sc[8 * g + kE];
-        if (g + 1 < M) dist[g] = sqrt(sc[8 * g + kL2]);
-        double tt = sc[8 * g + kTT];
-        slope[g] = tt > 0 ? sc[8 * g + kGT] / sqrt(tt) : 0.0;
+        E[g] = sc[kS * g + kE];
+        if (g + 1 < M) dist[g] = sqrt(sc[kS * g + kL2]);
+        double tt = sc[kS * g + kTT];
+        slope[g] = tt > 0 ? sc[kS * g + kGT] / sqrt(tt) : 0.0;
     }
     return 0;
 }
