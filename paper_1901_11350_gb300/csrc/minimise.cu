@@ -137,6 +137,17 @@ __device__ __forceinline__ f2sum exact_dot(v3<float> a, v3<float> b)
     float p0 = a.x * b.x, p1 = a.y * b.y, p2 = a.z * b.z;
     return f2sum{p0, fmaf(a.x, b.x, -p0)} + f2sum{p1, fmaf(a.y, b.y, -p1)} + f2sum{p2, fmaf(a.z, b.z, -p2)};
 }
+// Per-image dot-product accumulators: float-float for FP32 (the FP64 sum of
+// the same exact products to ~1e-14), plain FP64 for FP64.
+template <typename T> struct Acc {
+    using type = double;
+};
+template <> struct Acc<float> {
+    using type = f2sum;
+};
+__device__ __forceinline__ f2sum acc_dot(v3<float> a, v3<float> b) { return exact_dot(a, b); }
+__device__ __forceinline__ double acc_dot(v3<double> a, v3<double> b) { return dot(a, b); }
+
 __device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ f2sum shfl_down(f2sum v, int o)
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Ste
         v3<T> B = local_field(S, x, i, ni, b);
         v3<T> Fn = B - dot(B, ni) * ni;
         if (mode == 1) {
-            v3<T> vi = axpy((T)dth_m, ldc(F, i) + Fn, ldc(v, i));
+            v3<T> vi = axpy(dth_m, ldc(F, i) + Fn, ldc(v, i));
             st(v, i, vi);
             r[0] = dot(vi, Fn);
         }
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict_
         } else {
             vi = ldc(v, i);
         }
-        if (!done) st(x, i, normalised(axpy((T)dt2_2m, ldc(F, i), axpy((T)dt, vi, ldc(x, i)))));
+        if (!done) st(x, i, normalised(axpy(dt2_2m, ldc(F, i), axpy(dt, vi, ldc(x, i)))));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         state[1] = done ? 0 : 1;
@@ -301,7 +312,7 @@ __global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ 
     const rec_t<T> *xb = x + im.spin0 + (long long)im.nu * im.N;
     // energy and squared angle sums: FP64, or float-float for FP32 (the
     // same sums of the same products to ~1e-14, off the FP64 pipe)
-    using A = typename std::conditional<std::is_same<T, float>::value, f2sum, double>::type;
+    using A = typename Acc<T>::type;
     A r[2] = {A{}, A{}};
     if (i < im.N) {
         int b;
@@ -346,7 +357,8 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
         s_wm = (T)scal[kS * bi.g + kWM];
     }
     __syncthreads();
-    T r[2] = {0, 0};
+    using A = typename Acc<T>::type;
+    A r[2] = {A{}, A{}};
     if (i < im.N && end) {
         // endpoints: one-sided difference to the neighbouring image (only its
         // slope dE/dr is used, for the interpolated path energy)
@@ -354,15 +366,15 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
         v3<T> t = im.nu == 0 ? ld(x, p + im.N) - xi : xi - ld(x, p - im.N);
         t = t - dot(t, xi) * xi;
         st(Tau, p, t);
-        r[0] = dot(t, t);
-        r[1] = dot(ldc(G, p), t);
+        r[0] = acc_dot(t, t);
+        r[1] = acc_dot(ldc(G, p), t);
     } else if (i < im.N) {
         v3<T> xi = ld(x, p), xp = ld(x, p + im.N), xm = ld(x, p - im.N);
         v3<T> t = axpy(s_wp, xp - xi, s_wm * (xi - xm));
         t = t - dot(t, xi) * xi;
         st(Tau, p, t);
-        r[0] = dot(t, t);
-        r[1] = dot(ldc(G, p), t);
+        r[0] = acc_dot(t, t);
+        r[1] = acc_dot(ldc(G, p), t);
     }
     image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kTT);
 }
@@ -511,16 +523,17 @@ __global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ 
     __syncthreads();
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
-    T r[3] = {0, 0, 0};
+    using A = typename Acc<T>::type;
+    A r[3] = {A{}, A{}, A{}};
     if (i < im.N) {
         v3<T> Fn = axpy(s_a, ld(Tau, p), -ldc(G, p));
         if (mode == 1) {
-            v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
+            v3<T> vi = axpy(dth_m, ldc(F, p) + Fn, ldc(v, p));
             st(v, p, vi);
-            r[0] = dot(vi, Fn);
+            r[0] = acc_dot(vi, Fn);
         }
         st(F, p, Fn);
-        r[1] = dot(Fn, Fn);
+        r[1] = acc_dot(Fn, Fn);
         r[2] = r[1];  // max |F|^2; the image's max |F| is its square root
     }
     image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kVF, ProjectionPost());
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ b
     } else {
         vi = ldc(v, p);
     }
-    if (mode <= 1) st(x, p, normalised(axpy((T)dt2_2m, ldc(F, p), axpy((T)dt, vi, ldc(x, p)))));
+    if (mode <= 1) st(x, p, normalised(axpy(dt2_2m, ldc(F, p), axpy(dt, vi, ldc(x, p)))));
 }
 
 __global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const double *scal, double *E, double *fmax_out,
@@ -636,7 +649,7 @@ __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict_
         v3<T> B = local_field(St, xb, i, ni, b);
         v3<T> Fn = B - dot(B, ni) * ni;
         if (mode == 1) {
-            v3<T> vi = axpy((T)dth_m, ldc(F, p) + Fn, ldc(v, p));
+            v3<T> vi = axpy(dth_m, ldc(F, p) + Fn, ldc(v, p));
             st(v, p, vi);
             r[0] = dot(vi, Fn);
         }
@@ -677,7 +690,7 @@ __global__ void __launch_bounds__(kBlock) k_bvp_move(const BlkInfo *__restrict__
         } else {
             vi = ldc(v, p);
         }
-        if (!done) st(x, p, normalised(axpy((T)dt2_2m, ldc(F, p), axpy((T)dt, vi, ldc(x, p)))));
+        if (!done) st(x, p, normalised(axpy(dt2_2m, ldc(F, p), axpy(dt, vi, ldc(x, p)))));
     }
     if (bi.t == 0 && threadIdx.x == 0) {
         state[2 * bi.g + 1] = done ? 0 : 1;
