@@ -46,6 +46,12 @@ namespace {
 #ifndef SPGB_CUBIC_QAHEAD
 #define SPGB_CUBIC_QAHEAD 1
 #endif
+// 1: the Heun corrector's folded term q travels with the plane ring (q of
+// plane p - 1 in the cp.async group of plane p), read from shared memory;
+// 0: loaded from global memory QAHEAD planes ahead into registers
+#ifndef SPGB_CUBIC_QSMEM
+#define SPGB_CUBIC_QSMEM 1
+#endif
 
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
@@ -254,9 +260,10 @@ template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB, bool R
 __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> *__restrict__ src,
                                         rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                         rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
-                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], int r, int x0, int y0, int za,
-                                        int zb)
+                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], rec_t<T> (*qt)[TX * TY], int r,
+                                        int x0, int y0, int za, int zb)
 {
+    constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     static_assert(NB >= 2 && NB <= 4, "2 to 4 plane buffers");
     constexpr int QA = PASS == 1 ? SPGB_CUBIC_QAHEAD : 1;
     static_assert(QA >= 1 && QA <= 2, "q is fetched 1 or 2 planes ahead");
@@ -264,24 +271,28 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
     int x = x0 + tx, y = y0 + ty;
     bool own = x < P.nx && y < P.ny;
     HaloSlot h0 = halo_slot(P, x0, y0, threadIdx.x), h1 = halo_slot(P, x0, y0, threadIdx.x + TX * TY);
+    const int plane_sz = P.nx * P.ny;  // N < 2^31
+    // one cp.async group per ring slot: plane p of src (and, QS, q of plane
+    // p - 1 at this thread's column)
+    auto load = [&](int slot, int p) {
+        if (p <= zb) load_plane<T>(P, src, tiles[slot], h0, h1, p);
+        if (QS && own && p - 1 >= za && p - 1 < zb)
+            copy_rec<T>(&qt[slot][threadIdx.x], q + (size_t)(p - 1) * plane_sz + y * P.nx + x);
+        cp_async_commit();
+    };
     // planes za-1 .. za+NB-2 in flight
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        if (za - 1 + k <= zb) load_plane<T>(P, src, tiles[k], h0, h1, za - 1 + k);
-        cp_async_commit();
-    }
+    for (int k = 0; k < NB; ++k) load(k, za - 1 + k);
     cp_async_wait<NB - 1>();
     __syncthreads();
     Plane<T> below = summarise<T, DM>(P, tiles[0], tx, ty);
     __syncthreads();
-    if (za + NB - 1 <= zb) load_plane<T>(P, src, tiles[0], h0, h1, za + NB - 1);
-    cp_async_commit();
+    load(0, za + NB - 1);
     cp_async_wait<NB - 1>();
     __syncthreads();
     Plane<T> cur = summarise<T, DM>(P, tiles[1], tx, ty);
     v3<T> acc = cur.e + below.w - zdmi<T, DM>(P, below.c) + onsite(P, cur.c);
     v3<T> wcur = cur.w, ccur = cur.c;
-    const int plane_sz = P.nx * P.ny;  // N < 2^31
     int i = za * plane_sz + y * P.nx + x;
     // per-spin global inputs of the planes being finished, fetched QA planes
     // (Bdd: one plane) ahead so that their latency overlaps the stencils
@@ -289,26 +300,25 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 #pragma unroll
     for (int k = 0; k < QA; ++k) {
         qa[k] = mk(T(0), T(0), T(0));
-        if (PASS == 1 && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
+        if (PASS == 1 && !QS && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
     }
     if (HAS_BDD && own) bn = ld(Bdd, i);
     int s_next = 2 % NB, s_free = 1;  // slots of planes z+1 and z
     const uint64_t step = REPL && PASS == 0 ? llg_step_of(c) : c.step;  // Philox step of this launch
     for (int z = za; z < zb; ++z, i += plane_sz) {
-        rec_t<T> *bnext = tiles[s_next];  // plane z+1 (landed after the wait)
-        rec_t<T> *bfree = tiles[s_free];  // plane z, already summarised
+        const int sn = s_next, sf = s_free;  // plane z+1 (landed after the wait); plane z, summarised
         s_next = s_next + 1 == NB ? 0 : s_next + 1;
         s_free = s_free + 1 == NB ? 0 : s_free + 1;
         v3<T> qi = qa[0], bi = bn;
 #pragma unroll
         for (int k = 0; k + 1 < QA; ++k) qa[k] = qa[k + 1];
-        if (own && z + QA < zb && PASS == 1) qa[QA - 1] = ld(q, i + QA * plane_sz);
+        if (own && z + QA < zb && PASS == 1 && !QS) qa[QA - 1] = ld(q, i + QA * plane_sz);
         if (HAS_BDD && own && z + 1 < zb) bn = ld(Bdd, i + plane_sz);
         cp_async_wait<NB - 2>();
         __syncthreads();
-        if (z + NB <= zb) load_plane<T>(P, src, bfree, h0, h1, z + NB);
-        cp_async_commit();
-        Plane<T> up = summarise<T, DM>(P, bnext, tx, ty);
+        if (QS && own) qi = ldc(qt[sn], threadIdx.x);  // q of plane z, landed with plane z+1
+        load(sf, z + NB);
+        Plane<T> up = summarise<T, DM>(P, tiles[sn], tx, ty);
         v3<T> B = acc + up.w + zdmi<T, DM>(P, up.c);
         acc = up.e + wcur - zdmi<T, DM>(P, ccur) + onsite(P, up.c);
         v3<T> ni = ccur;
@@ -361,7 +371,9 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
                                                   const LlgConst<T> c, int per)
 {
     constexpr int NB = PASS == 0 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
+    constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     __shared__ __align__(32) rec_t<T> tiles[NB][HN];
+    __shared__ __align__(32) rec_t<T> qtiles[QS ? NB : 1][QS ? TX * TY : 1];
     int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
     long ntile = (long)tiles_x * tiles_y;
     long total = ntile * P.nz * (REPL ? llg_reps(c) : 1);
@@ -374,8 +386,8 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
         int tile = (int)(tg - (long)r * ntile);
         size_t o = REPL ? (size_t)r * ((size_t)P.nx * P.ny * P.nz) : 0;
         segment<T, SOLVER, PASS, DM, HAS_BDD, NB, REPL>(P, src + o, np ? np + o : np, q + o, nout ? nout + o : nout,
-                                                        Bdd, c, tiles, r, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
-                                                        za, zb);
+                                                        Bdd, c, tiles, (rec_t<T>(*)[TX * TY])qtiles, r,
+                                                        (tile % tiles_x) * TX, (tile / tiles_x) * TY, za, zb);
         u += zb - za;
     }
 }
