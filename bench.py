@@ -35,7 +35,17 @@ LLG_STEPS = 10000
 # algorithmic bytes per spin and launch (FP32 records of 16 B):
 #   predictor: read n, write predictor state and folded corrector term (3 x 16)
 #   corrector: read predictor state and folded term, write n          (3 x 16)
-BYTES_PER_SPIN = {"llg_predictor": 48, "llg_corrector": 48}
+# algorithmic bytes per spin and launch of the two LLG kernel classes (FP32
+# records): Heun reads n, writes np and q; reads np and q, writes n.  Depondt
+# and SIB correctors also read n.  RK4: stage 0 (counted as the predictor)
+# reads n, writes acc and the stage state; stages 1-2 read the stage state,
+# n and acc and write acc and the next state; stage 3 reads the stage state,
+# n and acc and writes n (the three counted as the corrector).
+SOLVER_BYTES = {"heun": {"llg_predictor": 48, "llg_corrector": 48},
+                "depondt": {"llg_predictor": 48, "llg_corrector": 64},
+                "sib": {"llg_predictor": 48, "llg_corrector": 64},
+                "rk4": {"llg_predictor": 48, "llg_corrector": (80 + 80 + 64) / 3}}
+CORRECTOR_LAUNCHES = {"heun": 1, "depondt": 1, "sib": 1, "rk4": 3}
 KERNEL_SOURCES = ["paper_1901_11350_gb300/csrc/field_llg.cu", "paper_1901_11350_gb300/csrc/cubic.cu",
                   "paper_1901_11350_gb300/csrc/common.cuh"]
 
@@ -159,8 +169,22 @@ def cpu_baseline(cfg, seconds=12.0, max_steps=64):
     n = o.llg(n, steps, step0=1, **kw)
     el = time.perf_counter() - t0
     return {"value": o.N * steps / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d FP64 stochastic-Heun steps of the full %s lattice (%d spins), %.1f s" % (
-                steps, "x".join(str(x) for x in g["n_cells"]), o.N, el)}
+            "sample": "%d FP64 %s steps (T = %g K) of the full %s lattice (%d spins), %.1f s" % (
+                steps, r["solver"], r["T"], "x".join(str(x) for x in g["n_cells"]), o.N, el)}
+
+
+def oracle_rate(step, units_per_call, seconds=10.0, max_calls=1000):
+    """Units per second of `step()` (one oracle call doing units_per_call
+    units of work), timed for about `seconds` on the host cores."""
+    t0 = time.perf_counter()
+    step()
+    t1 = time.perf_counter() - t0
+    calls = max(1, min(max_calls, int(seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        step()
+    el = time.perf_counter() - t0
+    return units_per_call * calls / el, calls, el
 
 
 def run_reference(args):
@@ -223,8 +247,10 @@ def run_gpu(args):
     host0[:, :3] = torch.from_numpy(I.random_spins(N, cfg["spin_seed"])).float()
     host0 = host0.pin_memory()
     n = host0.to("cuda")
-    kw = dict(solver="heun", dt=r["dt"], alpha=r["alpha"], T=r["T"] if args.temperature is None else args.temperature,
-              seed=r["seed"], replica=rank)
+    kw = dict(solver=args.solver, dt=r["dt"], alpha=r["alpha"],
+              T=r["T"] if args.temperature is None else args.temperature, seed=r["seed"], replica=rank)
+    bps = SOLVER_BYTES[args.solver]
+    bytes_per_step = bps["llg_predictor"] + CORRECTOR_LAUNCHES[args.solver] * bps["llg_corrector"]
     if not args.zc and not args.generic:
         ctx.autotune(n)  # planes per CTA, chosen by timing before the timed region
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -289,14 +315,15 @@ def run_gpu(args):
     dom = max(kern, key=lambda k: kern[k][0])
     ms, cnt = kern[dom]
     avg_s = ms / max(cnt, 1) / 1e3
-    achieved = BYTES_PER_SPIN[dom] * N / avg_s / 1e9
+    achieved = bps[dom] * N / avg_s / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(dom), "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": BYTES_PER_SPIN[dom] * N, "avg_launch_us": avg_s * 1e6,
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": ncu_traffic(dom) if args.solver == "heun" and not args.generic else None,
+            "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": bps[dom] * N, "avg_launch_us": avg_s * 1e6,
             "launches": cnt, "kernel_timing": "CUDA events around each launch, %d profiled steps after the timed region"
             % prof_steps,
-            "pair_frac_timed_region": sum(BYTES_PER_SPIN.values()) * N * S * args.steps / (el_ms / 1e3) / 1e9
-            / peaks["hbm_gbs"],
+            "pair_frac_timed_region": bytes_per_step * N * S * args.steps / (el_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
             "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kern.items()}}
     clocks = clk.summary()
     if world > 1:
@@ -306,17 +333,18 @@ def run_gpu(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S, "solver": "heun",
-                      "kernel_path": "generic" if args.generic else (
+           "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S, "solver": args.solver,
+                      "kernel_path": "generic" if args.generic or args.solver == "rk4" else (
                           "cubic27" if ctx.get_option("has_cubic_path") else "generic"),
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
-           "gpu_launches": 2 * S * args.steps, "roofline": roof, "clocks": clocks, "finite": finite}
+           "gpu_launches": (1 + CORRECTOR_LAUNCHES[args.solver]) * S * args.steps, "roofline": roof, "clocks": clocks,
+           "finite": finite}
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(cfg)
+        out["cpu_baseline"] = cpu_baseline(dict(cfg, run=dict(r, solver=args.solver)))
     print(json.dumps(out))
     return 0
 
@@ -371,6 +399,50 @@ def run_gneb(args):
            "barrier_rel_diff_f32_batch_vs_f64": {"max": float(np.max(np.abs(bar32 - bar64) / np.abs(bar64))),
                                                  "median": float(np.median(np.abs(bar32 - bar64) / np.abs(bar64)))},
            "setup_s": prep_s}
+    # per-iteration roofline over the full batch: algorithmic bytes per spin
+    # and iteration (FP32 records): move 80 (read F, v, x; write v, x), field
+    # 48 (x, next image; write Pg), tangent 80 (three images, Pg; write tau),
+    # force 96 (tau, Pg, F, v; write v, F)
+    import torch
+    offs, Ms, ctxs, off = [], [], [], 0
+    for ch in chains:
+        offs.append(off)
+        Ms.append(ch.M)
+        ctxs.append(ch.ctx)
+        off += ch.M * ch.N
+    x = torch.cat([ch.ctx.spins(ch.chain0).reshape(-1, 4) for ch in chains])
+    v = torch.zeros_like(x)
+    Bd.gneb_batch_step(ctxs, x, v, offs, Ms, n_iter=16, k_spring=1.0, climbing=True, dt=kw["dt"])
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    Bd.gneb_batch_step(ctxs, x, v, offs, Ms, n_iter=64, k_spring=1.0, climbing=True, dt=kw["dt"])
+    e1.record(st)
+    torch.cuda.synchronize()
+    it_s = e0.elapsed_time(e1) / 64 / 1e3
+    peaks, pk = measured_peaks()
+    gbs = 304 * off / it_s / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "one GNEB iteration of all chains (move, field, tangent, force)",
+                       "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                       "traffic": None, "peak_source": pk, "algorithmic_bytes_per_spin_iteration": 304,
+                       "ms_per_iteration": it_s * 1e3}
+    # the oracle on the largest chain, scaled to the spin-iterations this run needed
+    import oracle
+    big = max(range(len(chains)), key=lambda k: chains[k].M * chains[k].N)
+    ch = chains[big]
+    o = oracle.System(ch.draw["geometry"], ch.draw["hamiltonian"])
+    ost = {"x": ch.chain0, "v": None}
+
+    def oiter():
+        ost["x"], ost["v"], _, _, _ = o.gneb(ost["x"], ost["v"], n_iter=1, k_spring=1.0, climbing=True, dt=kw["dt"])
+
+    rate, calls, el = oracle_rate(oiter, ch.M * ch.N)
+    work = sum(state[k]["iters"] * chains[k].M * chains[k].N for k in state)
+    out["cpu_baseline"] = {"value": work / rate, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
+                           "sample": "%d FP64 GNEB iterations of the largest chain (%d images x %d spins) in %.1f s; "
+                                     "%.3g spin-iterations/s, scaled to the %.3g spin-iterations of the batched run"
+                                     % (calls, ch.M, ch.N, el, rate, work)}
     print(json.dumps(out))
     return 0
 
@@ -434,6 +506,15 @@ def run_hex_dipole(args):
            "dipole": {"us_per_evaluation": 1e3 * dip_ms / max(dip_n, 1), "algorithmic_bytes": dip_bytes,
                       "achieved_GBs": dip_bytes / (dip_ms / max(dip_n, 1) / 1e3) / 1e9, "peak_GBs": peaks["hbm_gbs"]},
            "finite": bool(torch.isfinite(n).all().item())}
+    dip_gbs = dip_bytes / (dip_ms / max(dip_n, 1) / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "dipole_field (row, column x kernel, inverse-row FFT passes)",
+                       "achieved": dip_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": dip_gbs / peaks["hbm_gbs"], "traffic": None,
+                       "algorithmic_bytes_per_launch": dip_bytes,
+                       "note": "per dipole evaluation (the largest share of a step); its 46 MB working set stays "
+                               "in L2, so the passes are latency-bound rather than DRAM-bound"}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, seconds=10.0, max_steps=50)
     print(json.dumps(out))
     return 0
 
@@ -517,6 +598,27 @@ def run_mc(args):
                                  "chi": [round(float(v), 3) for v in r["chi"]], "cv": [round(float(v), 5) for v in r["cv"]],
                                  "accept": [round(float(v), 3) for v in r["accept"]]}
                         for L, r in res.items()}}
+    peaks, kind = measured_peaks()
+    # algorithmic bytes of a trial: the spin's record read and written (the
+    # neighbours' records come from L2 within a colour sweep)
+    gbs = 32 * out["value"] / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "k_mc_colour", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                       "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": kind,
+                       "algorithmic_bytes_per_trial": 32,
+                       "note": "latency-bound: a colour launch of these lattices fills a third of the device"}
+    if not args.no_cpu_baseline:
+        import oracle
+        Lm = max(sizes)
+        o = oracle.System(I.simple_cubic(Lm, Lm, Lm, periodic=(True, True, True), mu_s=2.0), dict(J=[1.0]))
+        x0 = I.ferromagnet(o.N)[None]
+        state = {"x": x0}
+
+        def sweep():
+            state["x"], _, _ = o.mc(state["x"], [16.5], 1, seed=1, target_accept=0.5, sample=True)
+
+        v, calls, el = oracle_rate(sweep, o.N)
+        out["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": oracle.threads(), "kind": "oracle",
+                               "sample": "%d Metropolis sweeps of one %d^3 replica at 16.5 K, %.1f s" % (calls, Lm, el)}
     print(json.dumps(out))
     return 0
 
@@ -612,6 +714,12 @@ def run_sllg(args):
            # method kernels: predictor + corrector per step of each size's batch, one observable pass per
            # sample (the graph replays add one step-counter kernel per 32 steps, not counted)
            "gpu_launches": sum(2 * (args.sllg_thermal + n_samp * every) + n_samp for _ in sizes),
+           # algorithmic bytes of a spin update: the two LLG passes, 48 B each
+           "roofline": {"bound": "hbm", "kernel": "LLG predictor + corrector, all replica batches",
+                        "achieved": 96 * tot_updates / tot_s / 1e9, "peak": measured_peaks()[0]["hbm_gbs"],
+                        "unit": "GB/s", "frac": 96 * tot_updates / tot_s / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                        "traffic": None, "algorithmic_bytes_per_update": 96,
+                        "note": "includes the observable passes and the small lattices' launch latency"},
            "per_size": {str(L): {"seconds": r["seconds"], "spins": r["N"], "finite": r["finite"],
                                  "m": [round(float(v), 5) for v in r["m"]], "U4": [round(float(v), 5) for v in r["U4"]],
                                  "chi": [round(float(v), 3) for v in r["chi"]], "cv": [round(float(v), 5) for v in r["cv"]]}
@@ -744,6 +852,17 @@ def run_hessian(args):
                           "algorithmic_bytes_per_launch": 48 * N},
              "lanczos": {"lattice": [128, 128], "state": "relaxed Neel skyrmion", "krylov": 64,
                          "seconds": lanczos_s, "lowest_eigenvalue_meV": lam}}
+    if not args.no_cpu_baseline:
+        # the oracle's product on a 512x512 crop of the workload (the full
+        # lattice's products are independent per spin: the rate carries over)
+        import oracle
+        gs = I.hexagonal(512, 512, periodic=(True, True), mu_s=2.0)
+        o = oracle.System(gs, h)
+        ns, vs = I.random_spins(o.N, 1), I.random_spins(o.N, 2)
+        rate, calls, el = oracle_rate(lambda: o.hessian_apply(ns, vs), o.N)
+        out_j["cpu_baseline"] = {"value": rate / N, "unit": "products/s", "cores": oracle.threads(), "kind": "oracle",
+                                 "sample": "%d FP64 products on a 512x512 lattice in %.1f s (%.3g spins/s), "
+                                           "scaled to the 2048x2048 lattice" % (calls, el, rate)}
     print(json.dumps(out_j))
     return 0
 
@@ -888,6 +1007,8 @@ def main():
     ap.add_argument("--zc", default="", help="units per CTA of the 27-point path, P or P,C for predictor and "
                     "corrector (profiling aid; default: chosen by sp_autotune)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
+    ap.add_argument("--solver", default="heun", choices=["heun", "depondt", "sib", "rk4"],
+                    help="sc128: LLG solver (the workload is stochastic Heun; the others for comparison)")
     ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian",
                                                         "square32", "sllg30"])
     ap.add_argument("--mc-sizes", default="10,15,20,30", help="mc30: lattice sides")

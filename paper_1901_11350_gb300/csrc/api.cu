@@ -364,7 +364,7 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
-    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB);
     LlgConst<T> k = llg_const<T>(c, p);
     int per0 = cub ? cubic_per(c) : 0, per1 = cub ? cubic_per(c, 1) : 0;
     if (c->use_small && c->N <= kSmallMax && c->h.dipole == SP_DIPOLE_NONE && !rk4 && !c->prof.on) {
@@ -484,7 +484,7 @@ int replicas_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaSt
     bool hot = false;
     for (int r = 0; r < n_rep; ++r) hot = hot || temps[r] > 0;
     k.thermal = (hot && p->alpha > 0) ? 1 : 0;
-    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB);
     int per0 = cub ? cubic_per_batch(c, 0, n_rep) : 0, per1 = cub ? cubic_per_batch(c, 1, n_rep) : 0;
     // runs of a few planes per CTA are mostly the ring's prologue: the
     // per-spin kernels are faster there (unless the user fixed the split)

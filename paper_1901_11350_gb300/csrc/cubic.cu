@@ -340,6 +340,11 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
                     v3<T> g = cross(p, llg_A(c.cA[0], c.alpha, p, Bth));
                     st(np, i, p);
                     st(q, i, axpy(T(0.5) * c.dt, f + g, ni));
+                } else if (SOLVER == SP_SIB) {
+                    // np holds the midpoint (n + x_p)/2, q the thermal part of A there
+                    v3<T> m = T(0.5) * (ni + sib_solve(ni, A, c.dt));
+                    st(np, i, m);
+                    st(q, i, llg_A(c.cA[0], c.alpha, m, Bth));
                 } else {
                     v3<T> p = rotate(ni, A, c.dt);
                     st(np, i, p);
@@ -349,6 +354,8 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
                 v3<T> Ap = llg_A(c.cA[0], c.alpha, ni, B);
                 if (SOLVER == SP_HEUN) {
                     st(nout, i, normalised(axpy(T(0.5) * c.dt, cross(ni, Ap), qi)));
+                } else if (SOLVER == SP_SIB) {
+                    st(nout, i, sib_solve(ldc(nout, i), Ap + qi, c.dt));
                 } else {
                     st(nout, i, rotate(ldc(nout, i), axpy(T(0.5), Ap, qi), c.dt));
                 }
@@ -399,11 +406,15 @@ void launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const r
     if (pass == 0) {
         if (solver == SP_HEUN)
             k_cubic<T, SP_HEUN, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+        else if (solver == SP_SIB)
+            k_cubic<T, SP_SIB, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
         else
             k_cubic<T, SP_DEPONDT, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
     } else {
         if (solver == SP_HEUN)
             k_cubic<T, SP_HEUN, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+        else if (solver == SP_SIB)
+            k_cubic<T, SP_SIB, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
         else
             k_cubic<T, SP_DEPONDT, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
     }

@@ -1,5 +1,5 @@
 // field_llg.cu -- effective field, energy/torque reductions and the two-pass
-// LLG step (Heun and Depondt) for any lattice with a neighbour stencil.
+// LLG step (Depondt, Heun, SIB, RK4) for any lattice with a neighbour stencil.
 //
 // Heun (Appendix B) with the thermal field of Eq. 4, one step in two passes:
 //   pass 1 (predictor), per spin i:

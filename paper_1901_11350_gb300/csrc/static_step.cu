@@ -57,7 +57,7 @@ template <typename T> int run_static(sp_ctx *c, void *n, const sp_llg_params *p,
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
-    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT);
+    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB);
     LlgConst<T> k{};
     k.dt = (T)p->dt;
     k.alpha = (T)p->alpha;
