@@ -199,10 +199,14 @@ __device__ __forceinline__ void decode_site(const Stencil<T> &S, int i, int &b, 
 // mu_i B + 2 K (Khat.n_i) Khat + sum_j [J_ij n_j + n_j x D_ij].
 // Sites at least r0, r1, r2 cells from every edge take their neighbours at
 // the fixed offsets i + lin (the same indices the wrap gives).
+// The decision is taken per warp (all active lanes interior), so that a warp
+// never runs both index paths: on small lattices most warps touch an edge.
 template <typename T>
 __device__ __forceinline__ bool interior_site(const Stencil<T> &S, int c0, int c1, int c2)
 {
-    return c0 >= S.r0 && c0 < S.n0 - S.r0 && c1 >= S.r1 && c1 < S.n1 - S.r1 && c2 >= S.r2 && c2 < S.n2 - S.r2;
+    const bool in = c0 >= S.r0 && c0 < S.n0 - S.r0 && c1 >= S.r1 && c1 < S.n1 - S.r1 && c2 >= S.r2 &&
+                    c2 < S.n2 - S.r2;
+    return __all_sync(__activemask(), in);
 }
 
 // Index of the neighbour of entry E of site i = (b, c0, c1, c2), or -1
@@ -237,6 +241,43 @@ __device__ __forceinline__ v3<T> local_field(const Stencil<T> &S, const R *n, in
         B = axpy(E.J, nj, B + c);
     }
     return B;
+}
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch: a kernel lets the next one on its stream be
+// scheduled while it runs (the next kernel's blocks take SMs as they free up
+// and do their independent prologue), and a kernel waits for the previous
+// one's completion and memory before it reads what that one wrote.  Without
+// the launch attribute both are no-ops.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void wait_prerequisite() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launch a kernel that calls wait_prerequisite() before it reads anything
+// written earlier on the stream, with programmatic stream serialisation --
+// except into a CUDA graph being captured, where kernel-to-kernel edges are
+// already short and programmatic ones measured slower.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap != cudaStreamCaptureStatusNone) {
+        kern<<<grid, block, smem, st>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kern, args...);
 }
 
 // ---------------------------------------------------------------- Philox

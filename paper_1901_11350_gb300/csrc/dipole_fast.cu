@@ -39,6 +39,7 @@ __device__ __forceinline__ float2 ca(float2 a, float2 b) { return make_float2(a.
 __device__ __forceinline__ float2 cs(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cj(float2 a) { return make_float2(a.x, -a.y); }
 
+
 constexpr int rev5(int i)
 {
     return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
@@ -135,7 +136,9 @@ __global__ void __launch_bounds__(64 * kRows) k_rows(int n0, int n1, const float
     int w = wid >> 1, part = wid & 1;  // row in block; 0: z, 1: x + i y
     int y0 = blockIdx.x * kRows, y = y0 + w;
     bool row = y < n1;
+    allow_dependents();
     Tw tw = twiddles(lane, false);
+    wait_prerequisite();  // the spins may come from the pass just before
     float2 a[32];
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) {
@@ -197,8 +200,11 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
     int c = threadIdx.x / 32, lane = threadIdx.x % 32;
     int kx = blockIdx.x;
     const float *K = Kt + (long)kx * 6 * 1024;
+    allow_dependents();
     for (int t = threadIdx.x; t < 6 * 1024 / 4; t += blockDim.x) cp16(ks + 4 * t, K + 4 * t);
     asm volatile("cp.async.commit_group;\n" ::);
+    Tw twf = twiddles(lane, false);
+    wait_prerequisite();  // the row spectra
     float2 *col = ST + ((long)c * 513 + kx) * n1;
     float2 a[32];
 #pragma unroll
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
         int y = 32 * n2 + lane;
         a[n2] = y < n1 ? col[y] : make_float2(0.f, 0.f);
     }
-    fft1024<false>(a, tr, lane, twiddles(lane, false));
+    fft1024<false>(a, tr, lane, twf);
     __syncthreads();  // every warp is done with its transpose tile
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) spec[c * 1024 + lane + 32 * k1] = a[k1];
@@ -244,12 +250,14 @@ __global__ void __launch_bounds__(64 * kRows) k_irows(int n0, int n1, const floa
     int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
     int w = wid >> 1, part = wid & 1;
     int y0 = blockIdx.x * kRows, y = y0 + w;
+    allow_dependents();
+    Tw tw = twiddles(lane, true);
+    wait_prerequisite();  // the column pass's spectra
     for (int t = threadIdx.x; t < 3 * 513 * kRows; t += blockDim.x) {
         int r = t % kRows, ck = t / kRows;
         stage[t] = (y0 + r < n1) ? ST[(long)ck * n1 + y0 + r] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    Tw tw = twiddles(lane, true);
     float2 a[32];
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) {
@@ -300,10 +308,10 @@ cudaError_t dipole_fast_setup()
 cudaError_t dipole_fast_run(int n0, int n1, const float4 *n, float2 *ST, const float *Kt, float4 *out, cudaStream_t st)
 {
     int rb = (n1 + kRows - 1) / kRows;
-    k_rows<<<rb, 64 * kRows, kRowSmem, st>>>(n0, n1, n, ST);
-    k_cols<<<513, 96, kColSmem, st>>>(n1, ST, Kt);
-    k_irows<<<rb, 64 * kRows, kRowSmem, st>>>(n0, n1, ST, out);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_rows, dim3(rb), dim3(64 * kRows), kRowSmem, st, n0, n1, n, ST);
+    if (e == cudaSuccess) e = launch_pdl(k_cols, dim3(513), dim3(96), kColSmem, st, n1, ST, Kt);
+    if (e == cudaSuccess) e = launch_pdl(k_irows, dim3(rb), dim3(64 * kRows), kRowSmem, st, n0, n1, (const float2 *)ST, out);
+    return e;
 }
 
 }  // namespace spgb

@@ -16,6 +16,11 @@
 // for Depondt), write n -- 6 (7) records per spin.
 #include "internal.h"
 
+// 1: the per-spin LLG passes are launched with programmatic dependent launch
+#ifndef SPGB_LLG_PDL
+#define SPGB_LLG_PDL 1
+#endif
+
 namespace spgb {
 
 // ---------------------------------------------------------------- field
@@ -100,6 +105,8 @@ __global__ void __launch_bounds__(kBlock) k_llg_pred(const __grid_constant__ Ste
                                                      const rec_t<T> *__restrict__ Bdd, rec_t<T> *__restrict__ np,
                                                      rec_t<T> *__restrict__ q, const LlgConst<T> c)
 {
+    allow_dependents();
+    wait_prerequisite();  // n (and Bdd) come from the kernels before
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
     int r = blockIdx.y;  // replica
@@ -112,6 +119,8 @@ __global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Ste
                                                      const rec_t<T> *__restrict__ np, const rec_t<T> *__restrict__ q,
                                                      const rec_t<T> *__restrict__ Bdd, const LlgConst<T> c)
 {
+    allow_dependents();
+    wait_prerequisite();  // np, q (and Bdd) come from the kernels before
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
     size_t o = (size_t)blockIdx.y * S.N;  // replica
@@ -171,19 +180,31 @@ cudaError_t launch_llg_small(int solver, const Stencil<float> &S, float4 *n, con
     return cudaGetLastError();
 }
 
+template <typename... KArgs, typename... Args>
+cudaError_t launch_llg_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+#if SPGB_LLG_PDL
+    return launch_pdl(kern, grid, block, smem, st, args...);
+#else
+    kern<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+#endif
+}
+
 template <typename T>
 cudaError_t launch_llg_pred(int solver, const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, rec_t<T> *np,
                             rec_t<T> *q, const LlgConst<T> &c, cudaStream_t st)
 {
     if (S.N == 0) return cudaSuccess;
     int bs = llg_block((long)S.N * llg_reps(c));
+    cudaError_t e;
     if (solver == SP_HEUN)
-        k_llg_pred<T, SP_HEUN><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
+        e = launch_llg_kernel(k_llg_pred<T, SP_HEUN>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, Bdd, np, q, c);
     else if (solver == SP_SIB)
-        k_llg_pred<T, SP_SIB><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
+        e = launch_llg_kernel(k_llg_pred<T, SP_SIB>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, Bdd, np, q, c);
     else
-        k_llg_pred<T, SP_DEPONDT><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, Bdd, np, q, c);
-    return cudaGetLastError();
+        e = launch_llg_kernel(k_llg_pred<T, SP_DEPONDT>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, Bdd, np, q, c);
+    return e;
 }
 
 template <typename T>
@@ -192,13 +213,14 @@ cudaError_t launch_llg_corr(int solver, const Stencil<T> &S, rec_t<T> *n, const 
 {
     if (S.N == 0) return cudaSuccess;
     int bs = llg_block((long)S.N * llg_reps(c));
+    cudaError_t e;
     if (solver == SP_HEUN)
-        k_llg_corr<T, SP_HEUN><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
+        e = launch_llg_kernel(k_llg_corr<T, SP_HEUN>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, np, q, Bdd, c);
     else if (solver == SP_SIB)
-        k_llg_corr<T, SP_SIB><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
+        e = launch_llg_kernel(k_llg_corr<T, SP_SIB>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, np, q, Bdd, c);
     else
-        k_llg_corr<T, SP_DEPONDT><<<dim3(blocks_for(S.N, bs), llg_reps(c)), bs, 0, st>>>(S, n, np, q, Bdd, c);
-    return cudaGetLastError();
+        e = launch_llg_kernel(k_llg_corr<T, SP_DEPONDT>, dim3(blocks_for(S.N, bs), llg_reps(c)), dim3(bs), 0, st, S, n, np, q, Bdd, c);
+    return e;
 }
 
 // ---------------------------------------------------------------- RK4
@@ -212,6 +234,8 @@ __global__ void __launch_bounds__(kBlock) k_rk4(const __grid_constant__ Stencil<
                                                 rec_t<T> *__restrict__ acc, const rec_t<T> *__restrict__ Bdd,
                                                 const LlgConst<T> c)
 {
+    allow_dependents();
+    wait_prerequisite();  // the stage inputs come from the kernels before
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.N) return;
     int r = blockIdx.y;  // replica
