@@ -52,6 +52,11 @@ namespace {
 #ifndef SPGB_CUBIC_QSMEM
 #define SPGB_CUBIC_QSMEM 1
 #endif
+// 1: programmatic dependent launch of the passes (each waits for the one
+// before it ahead of any global access; the launch overlaps its drain)
+#ifndef SPGB_CUBIC_PDL
+#define SPGB_CUBIC_PDL 1
+#endif
 
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
@@ -381,6 +386,8 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
     constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     __shared__ __align__(32) rec_t<T> tiles[NB][HN];
     __shared__ __align__(32) rec_t<T> qtiles[QS ? NB : 1][QS ? TX * TY : 1];
+    allow_dependents();
+    wait_prerequisite();  // the previous pass reads what this one overwrites
     int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
     long ntile = (long)tiles_x * tiles_y;
     long total = ntile * P.nz * (REPL ? llg_reps(c) : 1);
@@ -399,38 +406,47 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUB
     }
 }
 
+template <typename K, typename T>
+cudaError_t launch_one(K kern, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
+                       rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
+{
+#if SPGB_CUBIC_PDL
+    return launch_pdl(kern, dim3(grid), dim3(TX * TY), 0, st, P, src, np, q, nout, Bdd, c, per);
+#else
+    kern<<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+    return cudaGetLastError();
+#endif
+}
+
 template <typename T, int DM, bool HB, bool RP>
-void launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
-                rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
+cudaError_t launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
+                       rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per,
+                       cudaStream_t st)
 {
     if (pass == 0) {
         if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
-        else if (solver == SP_SIB)
-            k_cubic<T, SP_SIB, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
-        else
-            k_cubic<T, SP_DEPONDT, 0, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
-    } else {
-        if (solver == SP_HEUN)
-            k_cubic<T, SP_HEUN, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
-        else if (solver == SP_SIB)
-            k_cubic<T, SP_SIB, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
-        else
-            k_cubic<T, SP_DEPONDT, 1, DM, HB, RP><<<grid, TX * TY, 0, st>>>(P, src, np, q, nout, Bdd, c, per);
+            return launch_one(k_cubic<T, SP_HEUN, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+        if (solver == SP_SIB)
+            return launch_one(k_cubic<T, SP_SIB, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_one(k_cubic<T, SP_DEPONDT, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
     }
+    if (solver == SP_HEUN)
+        return launch_one(k_cubic<T, SP_HEUN, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+    if (solver == SP_SIB)
+        return launch_one(k_cubic<T, SP_SIB, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+    return launch_one(k_cubic<T, SP_DEPONDT, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 // (a batch of replicas never carries the dipole field)
 template <typename T, int DM>
-void launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-               rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
+cudaError_t launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
+                      rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per,
+                      cudaStream_t st)
 {
     if (llg_reps(c) > 1)
-        launch_dmb<T, DM, false, true>(pass, solver, grid, P, src, np, q, nout, nullptr, c, per, st);
-    else if (Bdd)
-        launch_dmb<T, DM, true, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    else
-        launch_dmb<T, DM, false, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_dmb<T, DM, false, true>(pass, solver, grid, P, src, np, q, nout, nullptr, c, per, st);
+    if (Bdd) return launch_dmb<T, DM, true, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    return launch_dmb<T, DM, false, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 }  // namespace
@@ -443,13 +459,9 @@ cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const re
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
     int grid = (int)((total + per - 1) / per);
-    if (P.dmi_mode == 0)
-        launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    else if (P.dmi_mode == 1)
-        launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    else
-        launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    return cudaGetLastError();
+    if (P.dmi_mode == 0) return launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    if (P.dmi_mode == 1) return launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    return launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 long cubic_units(int nx, int ny, int nz) { return (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz; }
