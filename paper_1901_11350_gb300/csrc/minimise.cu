@@ -245,6 +245,8 @@ __global__ void __launch_bounds__(kBlock) k_vp_force(const __grid_constant__ Ste
                                                      int mode, double *part, unsigned *cnt, double *scal,
                                                      const int *state)
 {
+    allow_dependents();
+    wait_prerequisite();  // state, scalars and records come from the kernels before
     if (mode == 1 && state[1] == 0) return;
     int i = blockIdx.x * kBlock + threadIdx.x;
     T r[3] = {0, 0, 0};
@@ -271,6 +273,8 @@ __global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict_
                                                     const rec_t<T> *__restrict__ F, T dt, T dt2_2m, double tol,
                                                     int k, int max_iter, const double *scal, int *state)
 {
+    allow_dependents();
+    wait_prerequisite();  // state, scalars and records come from the kernels before
     __shared__ T s_c;
     __shared__ int s_done;
     if (threadIdx.x == 0) {
@@ -599,13 +603,14 @@ int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const Mi
     int *state = (int *)s->state.p;
     double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
     if (cudaMemsetAsync(state, 0, 4 * sizeof(int), st) != cudaSuccess) return SP_ERR_CUDA;
-    k_vp_force<T><<<nblk, kBlock, 0, st>>>(S, x, vv, F, dth_m, 0, part, cnt, scal, state);
+    launch_pdl(k_vp_force<T>, dim3(nblk), dim3(kBlock), 0, st, S, x, vv, F, (T)dth_m, 0, part, cnt, scal, (const int *)state);
     int k = 0;
     while (k < a.max_iter) {
         int chunk = std::min(a.check_every, a.max_iter - k);
         for (int c = 0; c < chunk; ++c, ++k) {
-            k_vp_move<T><<<nblk, kBlock, 0, st>>>(N, x, vv, F, a.dt, dt2_2m, a.tol, k, a.max_iter, scal, state);
-            k_vp_force<T><<<nblk, kBlock, 0, st>>>(S, x, vv, F, dth_m, 1, part, cnt, scal, state);
+            launch_pdl(k_vp_move<T>, dim3(nblk), dim3(kBlock), 0, st, N, x, vv, (const rec_t<T> *)F, (T)a.dt, (T)dt2_2m, a.tol, k,
+                       a.max_iter, (const double *)scal, state);
+            launch_pdl(k_vp_force<T>, dim3(nblk), dim3(kBlock), 0, st, S, x, vv, F, (T)dth_m, 1, part, cnt, scal, (const int *)state);
         }
         if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
         if (cudaMemcpyAsync(s->host_state, state, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -614,7 +619,8 @@ int vp_minimise(MinScratch **sp, const Stencil<T> &S, void *n, void *v, const Mi
         if (s->host_state[1] == 0) break;
     }
     // final projection of the velocity (or nothing when no iteration ran)
-    k_vp_move<T><<<nblk, kBlock, 0, st>>>(N, x, vv, F, a.dt, dt2_2m, a.tol, a.max_iter, a.max_iter, scal, state);
+    launch_pdl(k_vp_move<T>, dim3(nblk), dim3(kBlock), 0, st, N, x, vv, (const rec_t<T> *)F, (T)a.dt, (T)dt2_2m, a.tol,
+               a.max_iter, a.max_iter, (const double *)scal, state);
     if (cudaMemcpyAsync(s->host_state, state, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(s->host_fmax, scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -635,6 +641,8 @@ __global__ void __launch_bounds__(kBlock) k_bvp_force(const BlkInfo *__restrict_
                                                       int mode, double *part, unsigned *cnt, double *scal,
                                                       const int *state, int *proj)
 {
+    allow_dependents();
+    wait_prerequisite();  // state, scalars and records come from the kernels before
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
     if (mode == 1 && state[2 * bi.g + 1] == 0) return;
@@ -668,6 +676,8 @@ __global__ void __launch_bounds__(kBlock) k_bvp_move(const BlkInfo *__restrict__
                                                      int k, int max_iter, const double *scal, int *state,
                                                      const int *proj)
 {
+    allow_dependents();
+    wait_prerequisite();  // state, scalars and records come from the kernels before
     BlkInfo bi = blk[blockIdx.x];
     ImgInfo im = img[bi.g];
     const double *sc = scal + kS * bi.g;
@@ -742,14 +752,17 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
     int *state = (int *)s->state.p, *proj = state + 2 * C;
     double dth_m = a.dt / (2.0 * a.mass), dt2_2m = a.dt * a.dt / (2.0 * a.mass);
     std::vector<int> hs(2 * C);
-    k_bvp_force<T><<<n_full, kBlock, 0, st>>>(Bfull, I, Sd, x, v, F, dth_m, 0, part, cnt, scal, state, proj);
+    launch_pdl(k_bvp_force<T>, dim3(n_full), dim3(kBlock), 0, st, (const BlkInfo *)Bfull, (const ImgInfo *)I, Sd,
+               (const rec_t<T> *)x, v, F, (T)dth_m, 0, part, cnt, scal, (const int *)state, proj);
     int k = 0, n_act = n_full;
     while (k < a.max_iter) {
         int chunk = std::min(a.check_every, a.max_iter - k);
         for (int c = 0; c < chunk; ++c, ++k) {
-            k_bvp_move<T><<<n_act, kBlock, 0, st>>>(Bact, I, x, v, F, a.dt, dt2_2m, a.tol, k, a.max_iter, scal, state,
-                                                    proj);
-            k_bvp_force<T><<<n_act, kBlock, 0, st>>>(Bact, I, Sd, x, v, F, dth_m, 1, part, cnt, scal, state, proj);
+            launch_pdl(k_bvp_move<T>, dim3(n_act), dim3(kBlock), 0, st, (const BlkInfo *)Bact, (const ImgInfo *)I, x, v,
+                       (const rec_t<T> *)F, (T)a.dt, (T)dt2_2m, a.tol, k, a.max_iter, (const double *)scal, state,
+                       (const int *)proj);
+            launch_pdl(k_bvp_force<T>, dim3(n_act), dim3(kBlock), 0, st, (const BlkInfo *)Bact, (const ImgInfo *)I, Sd,
+                       (const rec_t<T> *)x, v, F, (T)dth_m, 1, part, cnt, scal, (const int *)state, proj);
         }
         if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
         if (cudaMemcpyAsync(hs.data(), state, sizeof(int) * 2 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -775,8 +788,9 @@ int vp_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, const
         }
     }
     // final projection (where the last force pass updated the velocity)
-    k_bvp_move<T><<<n_full, kBlock, 0, st>>>(Bfull, I, x, v, F, a.dt, dt2_2m, a.tol, a.max_iter, a.max_iter, scal, state,
-                                             proj);
+    launch_pdl(k_bvp_move<T>, dim3(n_full), dim3(kBlock), 0, st, (const BlkInfo *)Bfull, (const ImgInfo *)I, x, v,
+               (const rec_t<T> *)F, (T)a.dt, (T)dt2_2m, a.tol, a.max_iter, a.max_iter, (const double *)scal, state,
+               (const int *)proj);
     std::vector<double> hsc(kS * C);
     if (cudaMemcpyAsync(hs.data(), state, sizeof(int) * 2 * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(hsc.data(), scal, sizeof(double) * kS * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
