@@ -46,6 +46,8 @@ template <typename T>
 __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
                                              const rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ out)
 {
+    allow_dependents();
+    wait_prerequisite();  // n and v may come from the kernels before
     int i = blockIdx.x * kHB + threadIdx.x;
     if (i >= S.N) return;
     int b, c0, c1, c2;
@@ -457,11 +459,11 @@ int sp_hessian_apply(sp_ctx *c, const void *n_dev, const void *v_dev, void *out_
     if (v_dev == out_dev) return hfail(c, SP_ERR_ARG, "v and out must differ");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned nb = hblocks(c->N);
-    if (c->prec == SP_F64)
-        k_hvp<double><<<nb, kHB, 0, st>>>(c->Sd, (const dq4 *)n_dev, (const dq4 *)v_dev, (dq4 *)out_dev);
-    else
-        k_hvp<float><<<nb, kHB, 0, st>>>(c->Sf, (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev);
-    return cudaGetLastError() == cudaSuccess ? SP_OK : hfail(c, SP_ERR_CUDA, "Hessian launch failed");
+    cudaError_t e = c->prec == SP_F64 ? launch_pdl(k_hvp<double>, dim3(nb), dim3(kHB), 0, st, c->Sd, (const dq4 *)n_dev,
+                                                   (const dq4 *)v_dev, (dq4 *)out_dev)
+                                      : launch_pdl(k_hvp<float>, dim3(nb), dim3(kHB), 0, st, c->Sf,
+                                                   (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev);
+    return e == cudaSuccess ? SP_OK : hfail(c, SP_ERR_CUDA, "Hessian launch failed");
 }
 
 int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, double *lambda, void *stream)
