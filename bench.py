@@ -334,7 +334,7 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": cfg["name"], "spins": N, "llg_steps_per_bench_step": S, "solver": args.solver,
-                      "kernel_path": "generic" if args.generic or args.solver == "rk4" else (
+                      "kernel_path": "generic" if args.generic else (
                           "cubic27" if ctx.get_option("has_cubic_path") else "generic"),
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),

@@ -459,8 +459,7 @@ enum {
      * when the shell-symmetric 27-point plane-streaming path applies (one
      * basis atom, bonds within the 3x3x3 cell neighbourhood, one exchange
      * constant per face/edge/corner class, DMI on faces only; LLG steps with
-     * Depondt, Heun or SIB -- RK4 always takes the generic kernels); 0:
-     * default */
+     * any solver, RK4 only without the dipole term); 0: default */
     SP_OPT_GENERIC_STENCIL = 1,
     /* work of one CTA of the 27-point path, in (32 x 8 column tile, plane)
      * units taken in tile-major order (>= 1); 0 (default): the units spread

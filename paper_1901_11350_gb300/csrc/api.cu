@@ -364,7 +364,9 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
     rec_t<T> *nn = (rec_t<T> *)n;
     const Stencil<T> &S = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
     const CubicParams<T> &CP = *(const CubicParams<T> *)(c->prec == SP_F64 ? (const void *)&c->Cd : (const void *)&c->Cf);
-    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB);
+    bool cub = c->cubic && c->use_cubic &&
+               (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB ||
+                (p->solver == SP_RK4 && c->h.dipole == SP_DIPOLE_NONE));
     LlgConst<T> k = llg_const<T>(c, p);
     int per0 = cub ? cubic_per(c) : 0, per1 = cub ? cubic_per(c, 1) : 0;
     if (c->use_small && c->N <= kSmallMax && c->h.dipole == SP_DIPOLE_NONE && !rk4 && !c->prof.on) {
@@ -388,7 +390,9 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
             for (int stg = 0; stg < 4; ++stg) {
                 if ((rc = dipole(c, src[stg], &bd, st))) return rc;
                 int pr = c->prof.begin(stg == 0 ? SP_PROF_LLG_PREDICTOR : SP_PROF_LLG_CORRECTOR, st);
-                cudaError_t e = launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, (const rec_t<T> *)bd, k, st);
+                cudaError_t e = cub ? launch_cubic<T>(stg, SP_RK4, CP, src[stg], dst[stg], acc, nn, nullptr, k, per0, st)
+                                    : launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, (const rec_t<T> *)bd, k,
+                                                          st);
                 c->prof.end(pr, st);
                 if (e != cudaSuccess) return cuda_fail(c, e, "RK4 stage launch");
             }
@@ -484,7 +488,7 @@ int replicas_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaSt
     bool hot = false;
     for (int r = 0; r < n_rep; ++r) hot = hot || temps[r] > 0;
     k.thermal = (hot && p->alpha > 0) ? 1 : 0;
-    bool cub = c->cubic && c->use_cubic && (p->solver == SP_HEUN || p->solver == SP_DEPONDT || p->solver == SP_SIB);
+    bool cub = c->cubic && c->use_cubic;  // all four solvers (a batch has no dipole term)
     int per0 = cub ? cubic_per_batch(c, 0, n_rep) : 0, per1 = cub ? cubic_per_batch(c, 1, n_rep) : 0;
     // runs of a few planes per CTA are mostly the ring's prologue: the
     // per-spin kernels are faster there (unless the user fixed the split)
@@ -494,7 +498,8 @@ int replicas_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaSt
             const rec_t<T> *src[4] = {nn, np, q, np};
             rec_t<T> *dst[4] = {np, q, np, nn};
             for (int stg = 0; stg < 4; ++stg) {
-                cudaError_t e = launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, nullptr, kk, s);
+                cudaError_t e = cub ? launch_cubic<T>(stg, SP_RK4, CP, src[stg], dst[stg], acc, nn, nullptr, kk, per0, s)
+                                    : launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, nullptr, kk, s);
                 if (e != cudaSuccess) return e;
             }
             return cudaSuccess;

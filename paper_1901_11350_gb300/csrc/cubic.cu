@@ -270,7 +270,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 {
     constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     static_assert(NB >= 2 && NB <= 4, "2 to 4 plane buffers");
-    constexpr int QA = PASS == 1 ? SPGB_CUBIC_QAHEAD : 1;
+    constexpr int QA = PASS == 1 && SOLVER != SP_RK4 ? SPGB_CUBIC_QAHEAD : 1;
     static_assert(QA >= 1 && QA <= 2, "q is fetched 1 or 2 planes ahead");
     int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     int x = x0 + tx, y = y0 + ty;
@@ -305,11 +305,11 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 #pragma unroll
     for (int k = 0; k < QA; ++k) {
         qa[k] = mk(T(0), T(0), T(0));
-        if (PASS == 1 && !QS && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
+        if (PASS == 1 && SOLVER != SP_RK4 && !QS && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
     }
     if (HAS_BDD && own) bn = ld(Bdd, i);
     int s_next = 2 % NB, s_free = 1;  // slots of planes z+1 and z
-    const uint64_t step = REPL && PASS == 0 ? llg_step_of(c) : c.step;  // Philox step of this launch
+    const uint64_t step = REPL && (PASS == 0 || SOLVER == SP_RK4) ? llg_step_of(c) : c.step;  // Philox step
     for (int z = za; z < zb; ++z, i += plane_sz) {
         const int sn = s_next, sf = s_free;  // plane z+1 (landed after the wait); plane z, summarised
         s_next = s_next + 1 == NB ? 0 : s_next + 1;
@@ -317,7 +317,7 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
         v3<T> qi = qa[0], bi = bn;
 #pragma unroll
         for (int k = 0; k + 1 < QA; ++k) qa[k] = qa[k + 1];
-        if (own && z + QA < zb && PASS == 1 && !QS) qa[QA - 1] = ld(q, i + QA * plane_sz);
+        if (own && z + QA < zb && PASS == 1 && SOLVER != SP_RK4 && !QS) qa[QA - 1] = ld(q, i + QA * plane_sz);
         if (HAS_BDD && own && z + 1 < zb) bn = ld(Bdd, i + plane_sz);
         cp_async_wait<NB - 2>();
         __syncthreads();
@@ -331,13 +331,31 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
         ccur = up.c;
         if (own) {
             if (HAS_BDD) B = B + bi;
-            if (PASS == 0) {
-                v3<T> Bth = mk(T(0), T(0), T(0));
-                if (c.thermal)
-                    Bth = (REPL ? c.rsig[r] : c.sig[0]) *
-                          thermal_eta(REPL ? thermal_bits_at(c, step, (uint32_t)i, (uint32_t)r)
-                                           : thermal_bits_at(c, c.step, (uint32_t)i, 0u),
-                                      T(0));
+            v3<T> Bth = mk(T(0), T(0), T(0));
+            if ((PASS == 0 || SOLVER == SP_RK4) && c.thermal)
+                Bth = (REPL ? c.rsig[r] : c.sig[0]) *
+                      thermal_eta(REPL ? thermal_bits_at(c, step, (uint32_t)i, (uint32_t)r)
+                                       : thermal_bits_at(c, c.step, (uint32_t)i, 0u),
+                                  T(0));
+            if (SOLVER == SP_RK4) {
+                // stage PASS of the fourth-order Runge-Kutta step (the same
+                // thermal field in every stage): np = next stage state, q =
+                // accumulator k1 + 2 k2 + 2 k3, nout = n (read by stages 1-3,
+                // written by stage 3)
+                v3<T> k = cross(ni, llg_A(c.cA[0], c.alpha, ni, B + Bth));
+                if (PASS == 0) {
+                    st(q, i, k);
+                    st(np, i, axpy(T(0.5) * c.dt, k, ni));
+                } else {
+                    v3<T> n0 = ldc(nout, i);
+                    if (PASS < 3) {
+                        st(q, i, axpy(T(2), k, ldc(q, i)));
+                        st(np, i, axpy((PASS == 1 ? T(0.5) : T(1)) * c.dt, k, n0));
+                    } else {
+                        st(nout, i, normalised(axpy(c.dt / T(6), ldc(q, i) + k, n0)));
+                    }
+                }
+            } else if (PASS == 0) {
                 v3<T> A = llg_A(c.cA[0], c.alpha, ni, B + Bth);
                 if (SOLVER == SP_HEUN) {
                     v3<T> f = cross(ni, A);
@@ -377,12 +395,12 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 // streamed as one segment.  With per = units / (SMs x resident CTAs) every SM
 // gets the same amount of work in a single wave.
 template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, bool REPL>
-__global__ void __launch_bounds__(TX *TY, PASS == 0 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
+__global__ void __launch_bounds__(TX *TY, PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
                                                   rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                                   const LlgConst<T> c, int per)
 {
-    constexpr int NB = PASS == 0 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
+    constexpr int NB = PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
     constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     __shared__ __align__(32) rec_t<T> tiles[NB][HN];
     __shared__ __align__(32) rec_t<T> qtiles[QS ? NB : 1][QS ? TX * TY : 1];
@@ -423,6 +441,18 @@ cudaError_t launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, 
                        rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per,
                        cudaStream_t st)
 {
+    if (solver == SP_RK4) {  // stages 0..3, without the dipole term
+        if constexpr (HB) {
+            return cudaErrorNotSupported;
+        } else {
+            switch (pass) {
+            case 0: return launch_one(k_cubic<T, SP_RK4, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            case 1: return launch_one(k_cubic<T, SP_RK4, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            case 2: return launch_one(k_cubic<T, SP_RK4, 2, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            default: return launch_one(k_cubic<T, SP_RK4, 3, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            }
+        }
+    }
     if (pass == 0) {
         if (solver == SP_HEUN)
             return launch_one(k_cubic<T, SP_HEUN, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);

@@ -269,12 +269,11 @@ cudaError_t launch_rk4_stage(int stage, const Stencil<T> &S, rec_t<T> *n, const 
     if (S.N == 0) return cudaSuccess;
     dim3 g(blocks_for(S.N), llg_reps(c));
     switch (stage) {
-    case 0: k_rk4<T, 0><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
-    case 1: k_rk4<T, 1><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
-    case 2: k_rk4<T, 2><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
-    default: k_rk4<T, 3><<<g, kBlock, 0, st>>>(S, n, src, dst, acc, Bdd, c); break;
+    case 0: return launch_llg_kernel(k_rk4<T, 0>, g, dim3(kBlock), 0, st, S, n, src, dst, acc, Bdd, c);
+    case 1: return launch_llg_kernel(k_rk4<T, 1>, g, dim3(kBlock), 0, st, S, n, src, dst, acc, Bdd, c);
+    case 2: return launch_llg_kernel(k_rk4<T, 2>, g, dim3(kBlock), 0, st, S, n, src, dst, acc, Bdd, c);
+    default: return launch_llg_kernel(k_rk4<T, 3>, g, dim3(kBlock), 0, st, S, n, src, dst, acc, Bdd, c);
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- energy
