@@ -542,6 +542,7 @@ def run_mc(args):
     st_cuda = torch.cuda.current_stream()
     for L in sizes:
         ctx = Bd.Context(I.simple_cubic(L, L, L, periodic=(True, True, True), mu_s=2.0), dict(J=[1.0]), "f32")
+        ctx.set_option("mc_resident", args.mc_resident)
         N = ctx.N
         x = ctx.spins(I.ferromagnet(N))[None].repeat(R, 1, 1).contiguous()
         cone = torch.full((R,), 0.5, dtype=torch.float64, device="cuda")
@@ -565,7 +566,8 @@ def run_mc(args):
         s = stats.cpu().numpy()
         n = s[:, 5]
         m, m2, m4, E, E2 = (s[:, k] / n for k in range(5))
-        res[L] = dict(N=N, seconds=secs, thermal_s=e0.elapsed_time(e1) / 1e3, m=m, m2=m2, m4=m4,
+        res[L] = dict(N=N, colours=ctx.mc_colours(), resident=ctx.get_option("mc_resident") == 1 and N <= 2048,
+                      seconds=secs, thermal_s=e0.elapsed_time(e1) / 1e3, m=m, m2=m2, m4=m4,
                       U4=1 - m4 / (3 * m2 ** 2), chi=N * (m2 - m ** 2) / (kB * T), cv=(E2 - E ** 2) / (kB * T ** 2) / N,
                       accept=s[:, 6] / s[:, 7], cone=cone.cpu().numpy())
     # Binder-cumulant crossings of consecutive sizes (linear interpolation)
@@ -590,10 +592,15 @@ def run_mc(args):
            "dtype": "f32 field and trials, f64 observables", "data": "synthetic",
            "config": {"workload": "mc_sc_ferromagnet_tc", "sizes": sizes, "temperatures_K": [float(t) for t in T],
                       "thermal_sweeps": args.mc_thermal, "sample_sweeps": args.mc_samples, "J_meV": 1.0,
-                      "target_accept": 0.5, "colours": 8},
+                      "target_accept": 0.5, "colours": {str(L): r["colours"] for L, r in res.items()},
+                      "l2": "inputs resident in L2 (at most 29 x 30^3 x 16 B = 12.5 MB): a sweep's cost is "
+                            "instruction issue, not DRAM"},
            "tc_K": {"binder_crossings": cross, "binder_mean": float(np.mean(cross)) if cross else None,
                     "chi_peak_L%d" % Lmax: tpk, "expected_high_T_series": 16.71, "paper_mc": 16.60},
            "per_size": {str(L): {"seconds": r["seconds"], "spins": r["N"],
+                                 "kernel": "k_mc_resident" if r["resident"] else "k_mc_colour",
+                                 "us_per_sweep_adaptive": 1e6 * r["thermal_s"] / max(args.mc_thermal, 1),
+                                 "us_per_sweep_sampled": 1e6 * (r["seconds"] - r["thermal_s"]) / max(args.mc_samples, 1),
                                  "m": [round(float(v), 5) for v in r["m"]], "U4": [round(float(v), 5) for v in r["U4"]],
                                  "chi": [round(float(v), 3) for v in r["chi"]], "cv": [round(float(v), 5) for v in r["cv"]],
                                  "accept": [round(float(v), 3) for v in r["accept"]]}
@@ -605,7 +612,8 @@ def run_mc(args):
     out["roofline"] = {"bound": "hbm", "kernel": "k_mc_colour", "achieved": gbs, "peak": peaks["hbm_gbs"],
                        "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": kind,
                        "algorithmic_bytes_per_trial": 32,
-                       "note": "latency-bound: a colour launch of these lattices fills a third of the device"}
+                       "note": "bound by instruction issue, not DRAM: the neighbour records come from L2 or "
+                               "shared memory; ncu of the resident kernel shows the issue slots of its SMs 80% busy"}
     if not args.no_cpu_baseline:
         import oracle
         Lm = max(sizes)
@@ -1017,6 +1025,8 @@ def main():
     ap.add_argument("--mc-tmin", type=float, default=10.0)
     ap.add_argument("--mc-tmax", type=float, default=24.0)
     ap.add_argument("--mc-dt", type=float, default=0.5, help="mc30, sllg30: temperature step (K)")
+    ap.add_argument("--mc-resident", type=int, default=1, choices=[0, 1],
+                    help="mc30: 0 forces one launch per colour on every size")
     ap.add_argument("--sllg-thermal", type=int, default=20000, help="sllg30: thermalisation steps")
     ap.add_argument("--sllg-samples", type=int, default=100000, help="sllg30: sampled steps")
     ap.add_argument("--sllg-every", type=int, default=10, help="sllg30: steps between samples")

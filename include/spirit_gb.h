@@ -345,7 +345,12 @@ typedef struct {
 
 /* Number of colours of this context's Monte Carlo sweep (0: the lattice has
  * no colouring -- a neighbour more than one cell away, a periodic direction
- * of odd size not divisible by 3, or offsets along a direction of one cell). */
+ * of odd size not divisible by 3, or offsets along a direction of one cell).
+ * 2 for the checkerboard: one basis atom, every pair offset of odd
+ * coordinate sum, every periodic direction of even size and an even first
+ * direction; colour = (c0 + c1 + c2) mod 2.  Otherwise colour = basis atom
+ * and, per direction, the cell index mod 2 (mod 3 for a periodic direction
+ * of odd size divisible by 3). */
 int sp_mc_colours(sp_ctx *ctx, int *n_colours);
 
 /* n_sweeps Metropolis sweeps of n_rep replicas of the context's system,
@@ -485,7 +490,14 @@ enum {
      * overrides this one).  Reading returns the value the corrector uses:
      * its own, else the shared user value, else its balanced split (the
      * corrector keeps more CTAs resident than the predictor) */
-    SP_OPT_PLANES_PER_CTA_CORR = 6
+    SP_OPT_PLANES_PER_CTA_CORR = 6,
+    /* 1 (default): sp_mc_sweeps on a lattice of at most 2048 spins with at
+     * most 32 colours runs one CTA per replica, the replica held in shared
+     * memory for all sweeps of the call; 0: one launch per colour over all
+     * replicas (always taken for larger lattices, where it is faster).  Both
+     * give the same spins, cones and counts; the observable sums differ in
+     * rounding order. */
+    SP_OPT_MC_RESIDENT = 7
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose the work per CTA of the 27-point path by measurement, for each pass

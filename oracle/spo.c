@@ -1259,11 +1259,16 @@ int spo_topological_charge(const spo_system *s, const double *n, double *Q)
 /* ------------------------------------------------------------------ */
 /* Reading of the sweep: the paper visits every spin once per iteration in a
  * random sequential order; here the sweep visits the colours of a lattice
- * colouring in order (colour = basis atom and, per direction, the cell index
- * modulo 2, or modulo 3 for a periodic direction of odd size divisible by 3),
- * so that spins of one colour never interact and may be updated in any order.
- * Every update is still a Metropolis step with the rest of the system fixed,
- * so the sampled distribution is the same Boltzmann distribution. */
+ * colouring in order, so that spins of one colour never interact and may be
+ * updated in any order.  Every update is still a Metropolis step with the
+ * rest of the system fixed, so the sampled distribution is the same
+ * Boltzmann distribution.  Two colourings:
+ *  - the sum colouring, colour = (c0 + c1 + c2) mod k (mc_sum_modulus);
+ *  - the product colouring, colour = basis atom and, per direction, the cell
+ *    index modulo 2, or modulo 3 for a periodic direction of odd size
+ *    divisible by 3 (mc_moduli).
+ * The sum colouring is taken where it exists with no more colours than the
+ * product colouring (or where the product colouring does not exist). */
 static int mc_moduli(const spo_system *s, int m[3])
 {
     for (int d = 0; d < 3; ++d) {
@@ -1288,11 +1293,48 @@ static int mc_moduli(const spo_system *s, int m[3])
     return 1;
 }
 
+/* The smallest k >= 2 for which (c0 + c1 + c2) mod k is a colouring, 0 if
+ * there is none.  Conditions: one basis atom; no bond with d0 + d1 + d2
+ * divisible by k (a bond changes the sum by d0 + d1 + d2); every periodic
+ * direction a bond crosses has an extent divisible by k (the wrap then
+ * changes the sum by a multiple of k); and k divides the first extent, so
+ * that every row (c1, c2) holds n0 / k sites of each colour. */
+static int mc_sum_modulus(const spo_system *s)
+{
+    if (s->nb != 1) return 0;
+    for (int k = 2; k <= s->nc[0]; ++k) {
+        if (s->nc[0] % k) continue;
+        int ok = 1;
+        for (int e = 0; e < s->n_nbr[0]; ++e) {
+            const int *d = s->nbr[0][e].d;
+            if ((d[0] + d[1] + d[2]) % k == 0) ok = 0;
+            for (int a = 0; a < 3; ++a)
+                if (d[a] != 0 && s->per[a] && s->nc[a] % k) ok = 0;
+        }
+        if (ok) return k;
+    }
+    return 0;
+}
+
+/* Colours of the sweep; *k = the sum colouring's modulus, 0 for the product
+ * colouring with moduli m. */
+static int mc_colouring(const spo_system *s, int *k, int m[3])
+{
+    int ks = mc_sum_modulus(s);
+    int prod = mc_moduli(s, m) ? s->nb * m[0] * m[1] * m[2] : 0;
+    if (ks && (!prod || ks <= prod)) {
+        *k = ks;
+        return ks;
+    }
+    *k = 0;
+    return prod;
+}
+
 int spo_mc_colours(const spo_system *s)
 {
-    int m[3];
-    if (!s || !s->have_ham || !mc_moduli(s, m)) return 0;
-    return s->nb * m[0] * m[1] * m[2];
+    int k, m[3];
+    if (!s || !s->have_ham) return 0;
+    return mc_colouring(s, &k, m);
 }
 
 /* Field terms linear in n_i: Zeeman, exchange and DMI. */
@@ -1325,9 +1367,9 @@ int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const
 {
     if (!s || !s->have_ham || !spins || n_rep < 1 || !T || !p || n_sweeps < 0 || !cone || !stats) return SPO_ERR_ARG;
     if (s->h.dipole != SPO_DIPOLE_NONE) return SPO_ERR_ARG;
-    int m[3];
-    if (!mc_moduli(s, m)) return SPO_ERR_ARG;
-    int n_col = s->nb * m[0] * m[1] * m[2];
+    int k, m[3];
+    const int n_col = mc_colouring(s, &k, m);
+    if (!n_col) return SPO_ERR_ARG;
     long N = s->N;
     double *Bs = (double *)malloc(sizeof(double) * 3 * N);
     if (!Bs) return SPO_ERR_STATE;
@@ -1342,7 +1384,8 @@ int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const
                 for (long i = 0; i < N; ++i) {
                     int b, c[3];
                     decode(s, (int)i, &b, c);
-                    int cc = b + s->nb * (c[0] % m[0] + m[0] * (c[1] % m[1] + m[1] * (c[2] % m[2])));
+                    int cc = k ? (c[0] + c[1] + c[2]) % k
+                               : b + s->nb * (c[0] % m[0] + m[0] * (c[1] % m[1] + m[1] * (c[2] % m[2])));
                     if (cc != col) continue;
                     /* three uniforms in (0, 1) from Philox: azimuth, cone, acceptance */
                     uint32_t ctr[4] = {(uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)r + 1u};

@@ -156,9 +156,8 @@ typedef struct {
     int sample;             /* 1: accumulate observables after every sweep */
 } spo_mc_params;
 
-/* Number of colours of the sweep (0 when the lattice cannot be coloured:
- * a neighbour more than one cell away, or a periodic direction whose size
- * is odd and not a multiple of 3, or a one-cell direction with offsets). */
+/* Number of colours of the sweep: k for the sum colouring (c0 + c1 + c2)
+ * mod k, else the product colouring's count; 0 when neither applies. */
 int spo_mc_colours(const spo_system *s);
 /* n_sweeps Metropolis sweeps of n_rep replicas of the system (spins
  * n_rep x N x 3, replica r at temperature T[r] K).  cone[r] (radians,

@@ -1105,6 +1105,10 @@ int sp_set_option(sp_ctx *c, int option, int value)
         if (value < 0) return fail(c, SP_ERR_ARG, "units per CTA must be >= 0 (0: as the predictor)");
         c->zc_corr = value;
         return SP_OK;
+    case SP_OPT_MC_RESIDENT:
+        if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "mc_resident takes 0 or 1");
+        c->use_mc_resident = value == 1;
+        return SP_OK;
     default:
         return fail(c, SP_ERR_ARG, "unknown option %d", option);
     }
@@ -1144,6 +1148,9 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_PLANES_PER_CTA_CORR:
         *value = c->zc_corr > 0 ? c->zc_corr : (c->zc > 0 ? c->zc : c->zc_auto_corr);
+        return SP_OK;
+    case SP_OPT_MC_RESIDENT:
+        *value = c->use_mc_resident ? 1 : 0;
         return SP_OK;
     default:
         return SP_ERR_ARG;

@@ -122,6 +122,42 @@ __device__ __forceinline__ void st(dq4 *p, long i, v3<double> v)
     q[1] = make_double2(v.z, 0.0);
 }
 
+// ---------------------------------------------------------------- float-float
+// An unevaluated sum hi + lo of two floats (about 48 significant bits):
+// FP32 sums whose result must match an FP64 sum without the FP64 pipe, which
+// is a small fraction of the FP32 rate on this part.  Knuth's TwoSum and
+// the FMA-exact product.
+struct f2sum {
+    float hi, lo;
+};
+__device__ __forceinline__ f2sum two_sum(float a, float b)
+{
+    float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2sum operator+(f2sum a, f2sum b)
+{
+    f2sum s = two_sum(a.hi, b.hi);
+    float lo = s.lo + (a.lo + b.lo), hi = s.hi + lo;
+    return {hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ bool operator>(f2sum a, f2sum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ f2sum exact_square(float a) { return {a * a, fmaf(a, a, -(a * a))}; }
+__device__ __forceinline__ f2sum exact_dot(v3<float> a, v3<float> b)
+{
+    float p0 = a.x * b.x, p1 = a.y * b.y, p2 = a.z * b.z;
+    return f2sum{p0, fmaf(a.x, b.x, -p0)} + f2sum{p1, fmaf(a.y, b.y, -p1)} + f2sum{p2, fmaf(a.z, b.z, -p2)};
+}
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ f2sum shfl_down(f2sum v, int o)
+{
+    return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double to_double(float v) { return v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(f2sum v) { return (double)v.hi + (double)v.lo; }
+
 // ---------------------------------------------------------------- stencil
 // One directed neighbour entry: basis atom jb in cell c + d, exchange J and
 // DMI vector D_ij as seen from the centre atom.

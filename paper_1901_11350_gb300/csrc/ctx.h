@@ -114,6 +114,7 @@ struct sp_ctx {
     bool use_cubic = true;  // cleared by SP_OPT_GENERIC_STENCIL
     bool generic_fft = false;  // SP_OPT_GENERIC_FFT
     bool use_small = true;     // SP_OPT_SMALL_PATH
+    bool use_mc_resident = true;  // SP_OPT_MC_RESIDENT
     int zc = 0;             // units per CTA of the 27-point path; 0 = balanced (see cubic_per)
     int zc_corr = 0;        // the corrector's, when the autotuner chose it separately
     int zc_auto = 0;        // balanced value, computed on first use

@@ -148,7 +148,10 @@ def test_option_round_trip_and_rejections():
     assert c.get_option("planes_per_cta") == 7 and c.get_option("planes_per_cta_corr") == 5
     c.set_option("planes_per_cta", 9)  # one value for both passes again
     assert c.get_option("planes_per_cta_corr") == 9
-    for name, bad in (("planes_per_cta", -1), ("planes_per_cta_corr", -1), ("small_path", 2)):
+    assert c.get_option("mc_resident") == 1
+    c.set_option("mc_resident", 0)
+    assert c.get_option("mc_resident") == 0
+    for name, bad in (("planes_per_cta", -1), ("planes_per_cta_corr", -1), ("small_path", 2), ("mc_resident", 3)):
         with pytest.raises(B.SpinError) as e:
             c.set_option(name, bad)
         assert e.value.code == -1

@@ -519,13 +519,23 @@ MC_CASES = [
     ("hex9", I.hexagonal(9, 9, periodic=(True, True), mu_s=2.0),
      dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0, 1.0]), 9),
     ("hex6open", I.hexagonal(6, 5, periodic=(True, False), mu_s=3.0), dict(J=[1.0], B=[0.2, 0, 0.5]), 4),
+    # nearest-neighbour bonds only: the two-colour checkerboard
+    ("sc6nn", I.simple_cubic(6, 4, 4), dict(J=[1.0], dmi_kind="bulk", D=[0.25], K=[0.1], Khat=[[0, 0, 1]],
+                                           B=[0, 0.3, 0.8]), 2),
+    ("sq6x5open", I.square(6, 5, periodic=(True, False), mu_s=2.0), dict(J=[1.0], B=[0, 0, 0.4]), 2),
+    # odd periodic extents: (c0 + c1 + c2) mod 3 (the product colouring has 27)
+    ("sc9x3x3nn", I.simple_cubic(9, 3, 3), dict(J=[1.0], K=[0.1], Khat=[[0, 0, 1]], B=[0.2, 0, 0.5]), 3),
+    # mod 5: no product colouring exists
+    ("sc5nn", I.simple_cubic(5, 5, 5), dict(J=[1.0], dmi_kind="bulk", D=[0.2], B=[0, 0, 0.3]), 5),
 ]
 
 
+@pytest.mark.parametrize("resident", [1, 0], ids=["resident", "per_colour"])
 @pytest.mark.parametrize("name,g,h,ncol", MC_CASES, ids=[c[0] for c in MC_CASES])
-def test_mc_sweeps_fp64_match_oracle(name, g, h, ncol):
+def test_mc_sweeps_fp64_match_oracle(name, g, h, ncol, resident):
     o = _oracle(g, h)
     c = B.Context(g, h, "f64")
+    c.set_option("mc_resident", resident)
     assert c.mc_colours() == ncol == o.mc_colours()
     R = 3
     T = [2.0, 8.0, 30.0]
@@ -543,10 +553,13 @@ def test_mc_sweeps_fp64_match_oracle(name, g, h, ncol):
     assert np.allclose(st[:, :5], so[:, :5], rtol=1e-10, atol=1e-12)
 
 
-def test_mc_graph_replay_and_resume_are_bit_exact():
-    # 40 sweeps in one call (graph replay) equal 40 single-sweep calls
+@pytest.mark.parametrize("resident", [1, 0], ids=["resident", "per_colour"])
+def test_mc_graph_replay_and_resume_are_bit_exact(resident):
+    # 40 sweeps in one call (one resident launch, or graph replay) equal 40
+    # single-sweep calls
     g, h = MC_CASES[0][1], MC_CASES[0][2]
     c = B.Context(g, h, "f64")
+    c.set_option("mc_resident", resident)
     x0 = c.spins(I.random_spins(c.N, 5))[None].repeat(2, 1, 1).contiguous()
     x1 = x0.clone()
     ca, sa = c.mc_sweeps(x0, [4.0, 9.0], 40, seed=3, target_accept=0.5)
@@ -554,6 +567,32 @@ def test_mc_graph_replay_and_resume_are_bit_exact():
     for k in range(40):
         cb, sb = c.mc_sweeps(x1, [4.0, 9.0], 1, seed=3, sweep0=k, target_accept=0.5, cone=cb, stats=sb)
     assert torch.equal(x0, x1) and torch.equal(ca, cb) and torch.equal(sa, sb)
+
+
+@pytest.mark.parametrize("dims,prec", [((10, 10, 10), "f32"), ((10, 10, 10), "f64"), ((12, 12, 12), "f32"),
+                                       ((16, 16, 8), "f32"), ((9, 9, 9), "f32")])
+def test_mc_resident_equals_per_colour_launches(dims, prec):
+    # 29 replicas as in the Tc workload (10^3 is its smallest lattice; 16 x
+    # 16 x 8 the largest the resident kernel takes; 9^3 has three colours):
+    # one resident CTA per replica gives the spins, cones and counts of the
+    # per-colour launches; the observable sums differ only in summation order
+    g = I.simple_cubic(*dims, periodic=(True, True, True), mu_s=2.0)
+    h = dict(J=[1.0])
+    temps = list(np.round(np.arange(10.0, 24.0 + 1e-9, 0.5), 6))
+    R = len(temps)
+    x0 = np.stack([I.random_spins(int(np.prod(dims)), 300 + r) for r in range(R)])
+    out = []
+    for resident in (1, 0):
+        c = B.Context(g, h, prec)
+        c.set_option("mc_resident", resident)
+        x = torch.stack([c.spins(x0[r]) for r in range(R)])
+        cone, st = c.mc_sweeps(x, temps, 37, seed=4, target_accept=0.5, sample=True)
+        cone, st = c.mc_sweeps(x, temps, 21, seed=4, sweep0=37, target_accept=0.0, cone=cone, stats=st)
+        out.append((x, cone, st))
+    (xa, ca, sa), (xb, cb, sb) = out
+    assert torch.equal(xa, xb) and torch.equal(ca, cb)
+    assert torch.equal(sa[:, 5:], sb[:, 5:])
+    assert torch.allclose(sa[:, :5], sb[:, :5], rtol=1e-12, atol=0)
 
 
 def test_mc_fp32_samples_the_same_distribution():

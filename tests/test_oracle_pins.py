@@ -883,9 +883,45 @@ def test_mc_exchange_dimer_is_langevin_in_j_over_kt():
     assert abs(-st[:, 3].sum() / st[:, 5].sum() / J - _langevin(x)) < 6e-3
 
 
+def test_mc_heisenberg_ring_energy_is_the_transfer_matrix_value():
+    # classical Heisenberg ring of 5 spins: exp(K n.m) has the eigenvalues
+    # 4 pi i_l(K) (multiplicity 2l + 1, i_l the modified spherical Bessel
+    # function), so Z = (4 pi)^5 sum_l (2l+1) i_l(K)^5 and
+    # <E> = -J d ln Z / dK, K = J / kT.  Five colours (c0 mod 5): the sweep
+    # visits the ring sequentially
+    from scipy.special import spherical_in
+    J, T = 1.0, 7.5
+    s = oracle.System(I.square(5, 1, periodic=(True, False), mu_s=2.0), dict(J=[J]))
+    assert s.mc_colours() == 5
+    K = J / (oracle.K_B * T)
+    ls = np.arange(0, 40)
+    i_l = spherical_in(ls, K)
+    di_l = spherical_in(ls, K, derivative=True)
+    dlnZ = np.sum((2 * ls + 1) * 5 * i_l ** 4 * di_l) / np.sum((2 * ls + 1) * i_l ** 5)
+    R = 64
+    _, _, st = _mc_run(s, R, [T] * R, 200, 3000, seed=14)
+    E = st[:, 3].sum() / st[:, 5].sum()
+    # the standard error is ~0.006 J; the open chain (-5 J L(K)) lies 0.13 J away
+    assert abs(E - (-J * dlnZ)) < 0.03 * J, (E, -J * dlnZ)
+
+
+@pytest.mark.parametrize("geom,ham,ncol", [
+    (I.simple_cubic(6, 4, 4), dict(J=[1.0]), 2),          # (c0 + c1 + c2) mod 2
+    (I.simple_cubic(9, 3, 3), dict(J=[1.0]), 3),          # odd periodic extents: mod 3 (product: 27)
+    (I.simple_cubic(5, 5, 5), dict(J=[1.0]), 5),          # no product colouring
+    (I.simple_cubic(4, 4, 4), dict(J=[1.0, -0.2]), 8),    # second shell: d0 + d1 + d2 = 0 bonds
+    (I.hexagonal(9, 9, periodic=(True, True), mu_s=2.0), dict(J=[1.0]), 9),
+    (I.simple_cubic(7, 7, 7), dict(J=[1.0, -0.2]), 0),    # neither colouring
+])
+def test_mc_colour_counts(geom, ham, ncol):
+    assert oracle.System(geom, ham).mc_colours() == ncol
+
+
 def test_mc_cone_adapts_to_the_target_acceptance_and_limits():
-    s = oracle.System(I.simple_cubic(4, 4, 4), dict(J=[1.0], B=[0, 0, 0.5]))
-    assert s.mc_colours() == 8
+    # 8^3 spins: a sweep's acceptance fluctuates by ~2% (on 4^3 by ~6%, and the
+    # multiplicative feedback turns that into a random walk of the cone)
+    s = oracle.System(I.simple_cubic(8, 8, 8), dict(J=[1.0], B=[0, 0, 0.5]))
+    assert s.mc_colours() == 2  # nearest neighbours only: (c0 + c1 + c2) mod 2
     x0 = np.tile(I.random_spins(s.N, 3)[None], (3, 1, 1))
     x, cone, st = s.mc(x0, [5.0, 12.0, 60.0], 400, seed=5, target_accept=0.4, sample=False)
     # acceptance of the next 100 sweeps at the adapted cone
