@@ -30,6 +30,8 @@
 #include "ctx.h"
 
 struct McScratch {
+    // T: the replicas' temperature factors and cosc the cosines of their
+    // cones, both in the compute type; acc: accepted trials of the sweep
     DevBuf T, acc, sweep, part, cnt, cosc;
     cudaStream_t gs = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -46,6 +48,7 @@ struct McColour {
     int k, res;            // sum colouring: (c0 + c1 + c2) mod k == res; k = 0: the product colouring
     int nk;                // sum colouring: sites of the colour per row (c1, c2), n0 / k
     FastDiv fk;            // division by nk
+    FastDiv fkk;           // division by k
     int m0, m1, m2;        // product colouring: moduli per direction
     int off0, off1, off2;  // this colour's residues
     int s0, s1, s2;        // cells of this colour per direction
@@ -66,30 +69,66 @@ struct McColourSet {
     McColour c[kMcMaxResColours];
 };
 
-// Spin index of the q-th site of colour col (q < col.per).
-template <typename T>
-__device__ __forceinline__ int mc_site(const Stencil<T> &S, const McColour &col, int q)
+// Philox round keys of the trial stream: key (seed lo, seed hi) advanced by
+// the Weyl constants, round r at 2r, 2r + 1 (philox4x32_10_keyed).
+struct McKeys {
+    uint32_t rk[20];
+};
+inline McKeys mc_keys(uint64_t seed)
 {
-    int c0, c1, c2;
+    McKeys k;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (uint32_t r = 0; r < 10; ++r) {
+        k.rk[2 * r] = k0 + r * 0x9E3779B9u;
+        k.rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
+    }
+    return k;
+}
+
+// Spin index of the q-th site of colour col (q < col.per), and its basis
+// atom and cell.
+template <typename T>
+__device__ __forceinline__ int mc_site(const Stencil<T> &S, const McColour &col, int q, int &b, int &c0, int &c1,
+                                       int &c2)
+{
     if (col.k) {
         const int row = fdiv(q, col.fk);
         c2 = fdiv(row, S.fn1);
         c1 = row - c2 * S.n1;
-        int first = col.res - (c1 + c2) % col.k;
+        const int s = c1 + c2;
+        int first = col.res - (s - col.k * fdiv(s, col.fkk));
         first += first < 0 ? col.k : 0;
         c0 = first + col.k * (q - row * col.nk);
+        b = 0;
     } else {
         c0 = col.off0 + col.m0 * (q % col.s0);
         q /= col.s0;
         c1 = col.off1 + col.m1 * (q % col.s1);
         q /= col.s1;
         c2 = col.off2 + col.m2 * q;
+        b = col.b;
     }
-    return col.b + S.nb * (c0 + S.n0 * (c1 + S.n1 * c2));
+    return b + S.nb * (c0 + S.n0 * (c1 + S.n1 * c2));
 }
 
-// One Metropolis trial of spin i of replica rep (records xr: global or
-// shared memory); stores the trial direction when accepted.
+// B0 + sum_j [J_ij n_j + n_j x D_ij] over the stencil entries of basis atom
+// b at cell (c0, c1, c2), neighbours wrapped (periodic) or skipped (open).
+// DMI = false when every D_ij of the stencil vanishes.
+template <bool DMI, typename T, typename R>
+__device__ __forceinline__ v3<T> mc_field(const Stencil<T> &S, const R *n, int b, int c0, int c1, int c2, v3<T> B)
+{
+    for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
+        const NbrEntry<T> &E = S.e[q];
+        const int x0 = wrap(c0 + E.d0, S.n0, S.per0), x1 = wrap(c1 + E.d1, S.n1, S.per1),
+                  x2 = wrap(c2 + E.d2, S.n2, S.per2);
+        if ((x0 | x1 | x2) < 0) continue;
+        const v3<T> nj = ld(n, E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2)));
+        if (DMI) B = B + cross(nj, mk(E.Dx, E.Dy, E.Dz));
+        B = axpy(E.J, nj, B);
+    }
+    return B;
+}
+
 // The temperature as the trial uses it, 0 for T = 0 (accept only moves that
 // lower the energy): FP64 takes kT = k_B T and exp(-dE / kT); FP32 takes
 // log2(e) / kT and exp2(-dE log2(e) / kT), the same probability without a
@@ -120,20 +159,20 @@ __device__ __forceinline__ void mc_azimuth(double u0, double *s, double *c)
 }
 __device__ __forceinline__ void mc_azimuth(float u0, float *s, float *c) { sincospif(2.f * u0, s, c); }
 
-template <typename T, typename R>
-__device__ __forceinline__ bool mc_trial(const Stencil<T> &S, R *xr, int i, int rep, uint64_t sweep, uint64_t seed,
-                                         T ct, T temp)
+// One Metropolis trial of spin i = (b, c0, c1, c2) of replica rep (records
+// xr: global or shared memory); stores the trial direction when accepted.
+// The energy change takes the field's terms linear in n_i (Zeeman, exchange,
+// DMI) and the anisotropy exactly.
+template <bool DMI, typename T, typename R>
+__device__ __forceinline__ bool mc_trial(const Stencil<T> &S, R *xr, int i, int b, int c0, int c1, int c2, int rep,
+                                         uint64_t sweep, const McKeys &keys, T ct, T temp)
 {
-    v3<T> ni = ld(xr, i);
-    int b;
-    v3<T> B = local_field(S, xr, i, ni, b);
-    // the field's terms linear in n_i (Zeeman, exchange, DMI): remove the
-    // anisotropy part, whose energy change is taken exactly below
-    v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
-    T kn = dot(kh, ni);
-    v3<T> Bl = B - (T(2) * S.K[b] * kn) * kh;
-    uint4 o = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)rep + 1u),
-                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const v3<T> ni = ld(xr, i);
+    const v3<T> Bl = mc_field<DMI>(S, xr, b, c0, c1, c2, mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]));
+    const v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
+    const T kn = dot(kh, ni);
+    uint4 o = philox4x32_10_keyed(
+        make_uint4((uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)rep + 1u), keys.rk);
     const T scale = T(2.3283064365386963e-10);
     T u0 = ((T)o.x + T(0.5)) * scale, u1 = ((T)o.y + T(0.5)) * scale, u2 = ((T)o.z + T(0.5)) * scale;
     T cth = T(1) - u1 * (T(1) - ct);
@@ -151,12 +190,13 @@ __device__ __forceinline__ bool mc_trial(const Stencil<T> &S, R *xr, int i, int 
     return ok;
 }
 
-template <typename T>
+template <typename T, bool DMI>
 __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ x,
-                                                        int n_rep, McColour col, const double *__restrict__ TK,
-                                                        const double *__restrict__ cosc,
+                                                        int n_rep, McColour col, const T *__restrict__ temps,
+                                                        const T *__restrict__ cosc,
                                                         const unsigned long long *__restrict__ sweep_dev,
-                                                        uint64_t seed, unsigned long long *__restrict__ acc)
+                                                        const __grid_constant__ McKeys keys,
+                                                        unsigned long long *__restrict__ acc)
 {
     __shared__ unsigned cnt[kMcBlock];
     cnt[threadIdx.x] = 0;
@@ -166,9 +206,12 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
     int rep0 = (int)(t0 / col.per);
     if (t < col.per * n_rep) {
         int rep = (int)(t / col.per);
-        int i = mc_site(S, col, (int)(t - (long long)rep * col.per));
-        // the replica's cone enters as cos, computed once per sweep in FP64
-        if (mc_trial(S, x + (long long)rep * S.N, i, rep, *sweep_dev, seed, (T)cosc[rep], mc_temp<T>(TK[rep])))
+        int b, c0, c1, c2;
+        int i = mc_site(S, col, (int)(t - (long long)rep * col.per), b, c0, c1, c2);
+        // per replica: the cone as its cosine (once per sweep, from FP64) and
+        // the temperature factor (once per call): no FP64 work per trial
+        if (mc_trial<DMI>(S, x + (long long)rep * S.N, i, b, c0, c1, c2, rep, *sweep_dev, keys, cosc[rep],
+                          temps[rep]))
             atomicAdd(&cnt[rep - rep0], 1u);
     }
     __syncthreads();
@@ -178,24 +221,38 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
 
 // After a sweep: acceptance into the statistics, the cone's feedback
 // (theta <- theta exp(ratio - target), kept in [1e-4, pi]) and the sweep
-// counter.
-__global__ void k_mc_cone(int n_rep, long long N, unsigned long long *acc, double *cone, double *cosc, double target,
-                          double *stats, unsigned long long *sweep_dev)
+// counter -- a kernel of its own, or the end of k_mc_sample in sampled
+// sweeps (one launch fewer per sweep).
+template <typename T> struct McCone {
+    unsigned long long *acc;  // accepted trials of the sweep per replica (reset here)
+    double *cone;             // cone half-angles
+    T *cosc;                  // their cosines in the compute type
+    double target;            // target acceptance; 0: the cone stays
+    unsigned long long *sweep;
+};
+
+template <typename T>
+__device__ __forceinline__ void mc_cone_update(const McCone<T> &c, int r, long long N, double *stats)
 {
-    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) {
-        double a = (double)acc[r];
-        stats[8 * r + 6] += a;
-        stats[8 * r + 7] += (double)N;
-        if (target > 0) cone[r] = fmin(3.141592653589793, fmax(1e-4, cone[r] * exp(a / (double)N - target)));
-        cosc[r] = cos(cone[r]);
-        acc[r] = 0;
-    }
-    if (threadIdx.x == 0) *sweep_dev += 1;
+    double a = (double)c.acc[r];
+    stats[8 * r + 6] += a;
+    stats[8 * r + 7] += (double)N;
+    if (c.target > 0) c.cone[r] = fmin(3.141592653589793, fmax(1e-4, c.cone[r] * exp(a / (double)N - c.target)));
+    c.cosc[r] = (T)cos(c.cone[r]);
+    c.acc[r] = 0;
 }
 
-__global__ void k_mc_cos(int n_rep, const double *cone, double *cosc)
+template <typename T>
+__global__ void k_mc_cone(int n_rep, long long N, const McCone<T> c, double *stats)
 {
-    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) cosc[r] = cos(cone[r]);
+    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) mc_cone_update(c, r, N, stats);
+    if (threadIdx.x == 0) *c.sweep += 1;
+}
+
+template <typename T>
+__global__ void k_mc_cos(int n_rep, const double *cone, T *cosc)
+{
+    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) cosc[r] = (T)cos(cone[r]);
 }
 
 // Per-spin observable sums: float-float in FP32 (TwoSum, FMA-exact
@@ -217,36 +274,43 @@ __device__ __forceinline__ f2sum mc_energy(v3<float> n, v3<float> b)
 }
 __device__ __forceinline__ double mc_energy(v3<double> n, v3<double> b) { return -0.5 * dot(n, b); }
 
-// Observables of spin i: sum of n (3 components) and its energy.
-template <typename T, typename R, typename A>
+// Observables of spin i: sum of n (3 components) and its energy, B the
+// local part of B_eff (Eq. 1 without the dipole term).
+template <bool DMI, typename T, typename R, typename A>
 __device__ __forceinline__ void mc_observe(const Stencil<T> &S, const R *xr, int i, A v[4])
 {
-    v3<T> ni = ld(xr, i);
-    int b;
-    v3<T> B = local_field(S, xr, i, ni, b);
-    v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
+    const v3<T> ni = ld(xr, i);
+    int b, c0, c1, c2;
+    decode_site(S, i, b, c0, c1, c2);
+    const v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
+    const T k2 = T(2) * S.K[b] * dot(mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]), ni);
+    const v3<T> B = mc_field<DMI>(S, xr, b, c0, c1, c2,
+                                  mk(fma(k2, S.Kh[b][0], Bz.x), fma(k2, S.Kh[b][1], Bz.y), fma(k2, S.Kh[b][2], Bz.z)));
     v[0] = v[0] + mc_term(ni.x);
     v[1] = v[1] + mc_term(ni.y);
     v[2] = v[2] + mc_term(ni.z);
     v[3] = v[3] + mc_energy(ni, B + Bz);
 }
 
-// Observables of every replica: per block the sums of mc_observe, the last
-// block of a replica reduces the partials (warp 0, a fixed order) and
-// accumulates m, m^2, m^4, E, E^2 and the sample count (FP64).
-template <typename T>
+// Observables of every replica: bpr blocks per replica, each summing
+// mc_observe over a strided share of its spins (a few per thread: the
+// reductions are the cost otherwise); the last block of a replica reduces
+// the partials (warp 0, a fixed order) and accumulates m, m^2, m^4, E, E^2
+// and the sample count (FP64); with cone.acc set it then takes the sweep's
+// cone step of that replica (k_mc_cone).
+template <typename T, bool DMI>
 __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ Stencil<T> S,
                                                         const rec_t<T> *__restrict__ x, int bpr, double *part,
-                                                        unsigned *tickets, double *stats)
+                                                        unsigned *tickets, double *stats, const McCone<T> cone)
 {
     using A = typename McAcc<T>::type;
     __shared__ double sh[kMcBlock / 32][4];
     __shared__ int last;
     int rep = blockIdx.x / bpr, blk = blockIdx.x - rep * bpr;
-    int i = blk * kMcBlock + threadIdx.x;
     const rec_t<T> *xr = x + (long long)rep * S.N;
+    // block blk of the replica takes spins blk * kMcBlock + t + k bpr kMcBlock
     A v[4] = {};
-    if (i < S.N) mc_observe(S, xr, i, v);
+    for (int i = blk * kMcBlock + threadIdx.x; i < S.N; i += bpr * kMcBlock) mc_observe<DMI>(S, xr, i, v);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] = v[k] + shfl_down(v[k], o);
@@ -256,15 +320,20 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ 
         for (int k = 0; k < 4; ++k) sh[w][k] = to_double(v[k]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
+        double s[4];
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double s = 0;
-            for (int ww = 0; ww < kMcBlock / 32; ++ww) s += sh[ww][k];
-            part[4 * (size_t)blockIdx.x + k] = s;
+            s[k] = l < kMcBlock / 32 ? sh[l][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
         }
-        __threadfence();
-        unsigned tk = atomicAdd(&tickets[rep], 1u);
-        last = tk == (unsigned)(bpr - 1);
+        if (l == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[4 * (size_t)blockIdx.x + k] = s[k];
+            __threadfence();
+            unsigned tk = atomicAdd(&tickets[rep], 1u);
+            last = tk == (unsigned)(bpr - 1);
+        }
     }
     __syncthreads();
     if (!last || w != 0) return;
@@ -288,6 +357,10 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ 
     st[4] += M[3] * M[3];
     st[5] += 1;
     tickets[rep] = 0;
+    if (cone.acc) {  // the sweep's cone step for this replica
+        mc_cone_update(cone, rep, (long long)S.N, stats);
+        if (rep == 0) *cone.sweep += 1;
+    }
 }
 
 // Resident sweeps: CTA r holds replica r in shared memory and runs n_sweeps
@@ -298,12 +371,13 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ 
 // statistics (FP64, kept in registers between sweeps).  With the cone fixed
 // (target 0) the next sweep needs nothing from that update, so the other
 // warps go on while lane 0 finishes it.
-template <typename T>
+template <typename T, bool DMI>
 __global__ void __launch_bounds__(kMcResBlock<T>) k_mc_resident(const __grid_constant__ Stencil<T> S,
                                                              rec_t<T> *__restrict__ x,
                                                              const __grid_constant__ McColourSet cs,
-                                                             const double *__restrict__ TK, double *__restrict__ cone,
-                                                             double *__restrict__ stats, uint64_t seed,
+                                                             const T *__restrict__ temps, double *__restrict__ cone,
+                                                             double *__restrict__ stats,
+                                                             const __grid_constant__ McKeys keys,
                                                              unsigned long long sweep0, int n_sweeps, double target,
                                                              int sample)
 {
@@ -318,7 +392,7 @@ __global__ void __launch_bounds__(kMcResBlock<T>) k_mc_resident(const __grid_con
     const int rep = blockIdx.x;
     rec_t<T> *xr = x + (long long)rep * S.N;
     for (int i = threadIdx.x; i < S.N; i += kB) st(sh, i, ld(xr, i));
-    const T temp = mc_temp<T>(TK[rep]);
+    const T temp = temps[rep];
     double cn = 0, acc6 = 0, acc7 = 0, st0 = 0, st1 = 0, st2 = 0, st3 = 0, st4 = 0, st5 = 0;
     if (threadIdx.x == 0) {
         const double *sr = stats + 8 * (size_t)rep;
@@ -335,13 +409,16 @@ __global__ void __launch_bounds__(kMcResBlock<T>) k_mc_resident(const __grid_con
         for (int c = 0; c < cs.n; ++c) {
             const McColour &col = cs.c[c];
             const int per = (int)col.per;
-            for (int q = threadIdx.x; q < per; q += kB)
-                accepted += mc_trial(S, sh, mc_site(S, col, q), rep, sweep, seed, ct, temp) ? 1u : 0u;
+            for (int q = threadIdx.x; q < per; q += kB) {
+                int b, c0, c1, c2;
+                const int i = mc_site(S, col, q, b, c0, c1, c2);
+                accepted += mc_trial<DMI>(S, sh, i, b, c0, c1, c2, rep, sweep, keys, ct, temp) ? 1u : 0u;
+            }
             __syncthreads();
         }
         A v[4] = {};
         if (sample)
-            for (int i = threadIdx.x; i < S.N; i += kB) mc_observe(S, sh, i, v);
+            for (int i = threadIdx.x; i < S.N; i += kB) mc_observe<DMI>(S, sh, i, v);
         accepted = __reduce_add_sync(0xffffffffu, accepted);
         if (sample) {
 #pragma unroll
@@ -474,6 +551,7 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
             c.res = r;
             c.nk = S.n0 / k;
             c.fk = make_fastdiv(c.nk);
+            c.fkk = make_fastdiv(k);
             c.s0 = c.s1 = c.s2 = 1;
             c.per = (long long)S.N / k;
             out.push_back(c);
@@ -506,6 +584,28 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
 
 // Shared memory of the resident kernel for one replica; 0 when it does not
 // fit (or the colouring is too long for its parameter block).
+// Blocks per replica of k_mc_sample: all blocks of all replicas resident at
+// once (one wave, the SMs within one block of each other), at most one per
+// kMcBlock spins.
+template <typename T, bool DMI>
+int mc_sample_blocks(int N, int n_rep)
+{
+    static int cap = 0;  // resident blocks of the kernel on the device
+    if (!cap) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_sample<T, DMI>, kMcBlock, 0) != cudaSuccess ||
+            per < 1)
+            per = 1;
+        cap = sms * per;
+    }
+    const int want = cap / n_rep > 0 ? cap / n_rep : 1;
+    const int most = (N + kMcBlock - 1) / kMcBlock;
+    return want < most ? want : most;
+}
+
 template <typename T>
 size_t mc_resident_bytes(const Stencil<T> &S, size_t n_colours)
 {
@@ -527,7 +627,16 @@ size_t mc_resident_bytes(const Stencil<T> &S, size_t n_colours)
     return bytes;
 }
 
+// True when some pair of the stencil carries a DMI vector.
 template <typename T>
+bool mc_has_dmi(const Stencil<T> &S)
+{
+    for (int q = 0; q < S.off[S.nb]; ++q)
+        if (S.e[q].Dx != T(0) || S.e[q].Dy != T(0) || S.e[q].Dz != T(0)) return true;
+    return false;
+}
+
+template <typename T, bool DMI>
 int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double *T_host, const sp_mc_params *p,
            int n_sweeps, double *cone, double *stats, cudaStream_t st)
 {
@@ -535,49 +644,56 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
     if (!ms) ms = new McScratch;
     std::vector<McColour> cols = mc_colours(S);
     if (cols.empty()) return SP_ERR_UNSUPPORTED;
-    int bpr = (S.N + kMcBlock - 1) / kMcBlock;
-    if (grow_buf(ms->T, sizeof(double) * n_rep) || grow_buf(ms->acc, sizeof(unsigned long long) * (n_rep + kMcBlock)) ||
+    const int bpr = mc_sample_blocks<T, DMI>(S.N, n_rep);
+    if (grow_buf(ms->T, sizeof(T) * n_rep) || grow_buf(ms->acc, sizeof(unsigned long long) * (n_rep + kMcBlock)) ||
         grow_buf(ms->sweep, sizeof(unsigned long long)) || grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) ||
-        grow_buf(ms->cnt, sizeof(unsigned) * n_rep) || grow_buf(ms->cosc, sizeof(double) * n_rep))
+        grow_buf(ms->cnt, sizeof(unsigned) * n_rep) || grow_buf(ms->cosc, sizeof(T) * n_rep))
         return SP_ERR_CUDA;
     unsigned long long s0 = p->sweep0;
-    if (cudaMemcpyAsync(ms->T.p, T_host, sizeof(double) * n_rep, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    // the trial's temperature factors, once per call on the host
+    std::vector<T> temps_host(n_rep);
+    for (int r = 0; r < n_rep; ++r) temps_host[r] = mc_temp<T>(T_host[r]);
+    if (cudaMemcpyAsync(ms->T.p, temps_host.data(), sizeof(T) * n_rep, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(ms->sweep.p, &s0, sizeof s0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(ms->acc.p, 0, sizeof(unsigned long long) * (n_rep + kMcBlock), st) != cudaSuccess ||
         cudaMemsetAsync(ms->cnt.p, 0, sizeof(unsigned) * n_rep, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)  // the host values above must outlive the copies
         return SP_ERR_CUDA;
     rec_t<T> *x = (rec_t<T> *)spins;
-    const double *TK = (const double *)ms->T.p;
+    const T *temps = (const T *)ms->T.p;
+    const McKeys keys = mc_keys(p->seed);
     const size_t res_bytes = c->use_mc_resident ? mc_resident_bytes(S, cols.size()) : 0;
     if (res_bytes && n_sweeps > 0) {
         McColourSet set{};
         set.n = (int)cols.size();
         for (int k = 0; k < set.n; ++k) set.c[k] = cols[k];
-        if (cudaFuncSetAttribute(k_mc_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_mc_resident<T, DMI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)res_bytes) != cudaSuccess)
             return SP_ERR_CUDA;
         for (int k = 0; k < n_sweeps; k += kMcResMaxSweeps) {
             const int ns = n_sweeps - k < kMcResMaxSweeps ? n_sweeps - k : kMcResMaxSweeps;
-            k_mc_resident<T><<<(unsigned)n_rep, kMcResBlock<T>, res_bytes, st>>>(S, x, set, TK, cone, stats, p->seed,
+            k_mc_resident<T, DMI><<<(unsigned)n_rep, kMcResBlock<T>, res_bytes, st>>>(S, x, set, temps, cone, stats, keys,
                                                                               s0 + (unsigned long long)k, ns,
                                                                               p->target_accept, p->sample);
         }
         return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
     }
-    double *cosc = (double *)ms->cosc.p;
-    k_mc_cos<<<1, 256, 0, st>>>(n_rep, cone, cosc);
+    T *cosc = (T *)ms->cosc.p;
+    k_mc_cos<T><<<1, 256, 0, st>>>(n_rep, cone, cosc);
     unsigned long long *acc = (unsigned long long *)ms->acc.p, *sw = (unsigned long long *)ms->sweep.p;
     double *part = (double *)ms->part.p;
     unsigned *tk = (unsigned *)ms->cnt.p;
     auto sweep = [&](cudaStream_t ss) {
         for (const McColour &col : cols) {
             long long work = col.per * n_rep;
-            k_mc_colour<T><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(S, x, n_rep, col, TK, cosc,
-                                                                                            sw, p->seed, acc);
+            k_mc_colour<T, DMI><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(
+                S, x, n_rep, col, temps, cosc, sw, keys, acc);
         }
-        k_mc_cone<<<1, 256, 0, ss>>>(n_rep, (long long)S.N, acc, cone, cosc, p->target_accept, stats, sw);
-        if (p->sample) k_mc_sample<T><<<(unsigned)(bpr * n_rep), kMcBlock, 0, ss>>>(S, x, bpr, part, tk, stats);
+        const McCone<T> cc{acc, cone, cosc, p->target_accept, sw};
+        if (p->sample)
+            k_mc_sample<T, DMI><<<(unsigned)(bpr * n_rep), kMcBlock, 0, ss>>>(S, x, bpr, part, tk, stats, cc);
+        else
+            k_mc_cone<T><<<1, 256, 0, ss>>>(n_rep, (long long)S.N, cc, stats);
     };
     int k = 0;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -594,7 +710,7 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
             uint64_t seed;
             double target;
             int sample, n_rep, prec;
-        } key{x, cone, stats, TK, acc, sw, part, tk, cosc, p->seed, p->target_accept, p->sample, n_rep, (int)sizeof(T)};
+        } key{x, cone, stats, temps, acc, sw, part, tk, cosc, p->seed, p->target_accept, p->sample, n_rep, (int)sizeof(T)};
         std::vector<char> gk(sizeof key + sizeof(Stencil<T>));
         memcpy(gk.data(), &key, sizeof key);
         memcpy(gk.data() + sizeof key, &S, sizeof(Stencil<T>));
@@ -633,12 +749,14 @@ int sample_run(sp_ctx *c, const Stencil<T> &S, const void *spins, int n_rep, dou
 {
     McScratch *&ms = c->mc;
     if (!ms) ms = new McScratch;
-    int bpr = (S.N + kMcBlock - 1) / kMcBlock;
+    const bool dmi = mc_has_dmi(S);
+    const int bpr = dmi ? mc_sample_blocks<T, true>(S.N, n_rep) : mc_sample_blocks<T, false>(S.N, n_rep);
     if (grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) || grow_buf(ms->cnt, sizeof(unsigned) * n_rep) ||
         cudaMemsetAsync(ms->cnt.p, 0, sizeof(unsigned) * n_rep, st) != cudaSuccess)
         return SP_ERR_CUDA;
-    k_mc_sample<T><<<(unsigned)(bpr * n_rep), kMcBlock, 0, st>>>(S, (const rec_t<T> *)spins, bpr, (double *)ms->part.p,
-                                                                 (unsigned *)ms->cnt.p, stats);
+    auto kern = dmi ? k_mc_sample<T, true> : k_mc_sample<T, false>;
+    kern<<<(unsigned)(bpr * n_rep), kMcBlock, 0, st>>>(S, (const rec_t<T> *)spins, bpr, (double *)ms->part.p,
+                                                       (unsigned *)ms->cnt.p, stats, McCone<T>{});
     return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
 
@@ -680,8 +798,10 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
         if (!(T[r] >= 0)) return mfail(c, SP_ERR_ARG, "temperatures must be >= 0");
     if (c->h.dipole != SP_DIPOLE_NONE) return mfail(c, SP_ERR_UNSUPPORTED, "Monte Carlo with the dipole term");
     int e = c->prec == SP_F64
-                ? mc_run<double>(c, c->Sd, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream)
-                : mc_run<float>(c, c->Sf, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream);
+                ? (mc_has_dmi(c->Sd) ? mc_run<double, true> : mc_run<double, false>)(
+                      c, c->Sd, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream)
+                : (mc_has_dmi(c->Sf) ? mc_run<float, true> : mc_run<float, false>)(
+                      c, c->Sf, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream);
     if (e == SP_ERR_UNSUPPORTED)
         return mfail(c, e, "lattice has no colouring (neither (c0 + c1 + c2) mod k nor the product colouring "
                            "applies)");
