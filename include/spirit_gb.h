@@ -343,14 +343,18 @@ typedef struct {
     int sample;             /* 1: accumulate observables after every sweep */
 } sp_mc_params;
 
-/* Number of colours of this context's Monte Carlo sweep (0: the lattice has
- * no colouring -- a neighbour more than one cell away, a periodic direction
- * of odd size not divisible by 3, or offsets along a direction of one cell).
- * 2 for the checkerboard: one basis atom, every pair offset of odd
- * coordinate sum, every periodic direction of even size and an even first
- * direction; colour = (c0 + c1 + c2) mod 2.  Otherwise colour = basis atom
- * and, per direction, the cell index mod 2 (mod 3 for a periodic direction
- * of odd size divisible by 3). */
+/* Number of colours of this context's Monte Carlo sweep (the sweep visits
+ * them in order; spins of one colour never interact).  Two colourings:
+ *  - sum: colour = (c0 + c1 + c2) mod k for the smallest k >= 2 with one
+ *    basis atom, k | n0, no pair offset whose coordinate sum k divides, and
+ *    k dividing every periodic extent a pair offset crosses (2 for the
+ *    nearest neighbours of an even cubic or square lattice, 3 for 15^3);
+ *  - product: colour = basis atom and, per direction, the cell index mod 2
+ *    (mod 3 for a periodic direction of odd size divisible by 3), when no
+ *    offset reaches beyond the next cell and no offset runs along a
+ *    direction of one cell.
+ * The sum colouring is taken when it exists with no more colours than the
+ * product colouring; 0 when neither exists. */
 int sp_mc_colours(sp_ctx *ctx, int *n_colours);
 
 /* n_sweeps Metropolis sweeps of n_rep replicas of the context's system,

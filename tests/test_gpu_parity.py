@@ -519,7 +519,7 @@ MC_CASES = [
     ("hex9", I.hexagonal(9, 9, periodic=(True, True), mu_s=2.0),
      dict(J=[1.0], dmi_kind="interfacial", D=[0.3], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0, 1.0]), 9),
     ("hex6open", I.hexagonal(6, 5, periodic=(True, False), mu_s=3.0), dict(J=[1.0], B=[0.2, 0, 0.5]), 4),
-    # nearest-neighbour bonds only: the two-colour checkerboard
+    # nearest-neighbour bonds only: (c0 + c1 + c2) mod 2
     ("sc6nn", I.simple_cubic(6, 4, 4), dict(J=[1.0], dmi_kind="bulk", D=[0.25], K=[0.1], Khat=[[0, 0, 1]],
                                            B=[0, 0.3, 0.8]), 2),
     ("sq6x5open", I.square(6, 5, periodic=(True, False), mu_s=2.0), dict(J=[1.0], B=[0, 0, 0.4]), 2),

@@ -177,3 +177,28 @@ def test_independent_moments_reach_the_langevin_magnetisation():
         L = 1.0 / math.tanh(xx) - 1.0 / xx
         m = st[r, 0] / st[r, 5]
         assert abs(m - L) < 0.01, (T, m, L)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("R", [1, 29])
+def test_sample_of_large_lattices_is_the_definition(prec, R):
+    # 30^3 with bulk DMI: with 29 replicas each thread of the observables
+    # kernel sums a strided share of several spins; with one replica the
+    # blocks cover one spin per thread
+    g = I.simple_cubic(30, 30, 30, periodic=(True, True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="bulk", D=[0.2], K=[0.05], Khat=[[0, 0, 1]], B=[0, 0.1, 0.4])
+    o = oracle.System(g, h)
+    c = B.Context(g, h, prec)
+    n0 = np.stack([I.random_spins(c.N, 600 + r) for r in range(R)])
+    n0[:, :, 2] += 0.5  # a net magnetisation well above the sampling noise
+    n0 /= np.linalg.norm(n0, axis=2, keepdims=True)
+    if prec == "f32":
+        n0 = n0.astype(np.float32).astype(np.float64)
+    st = c.sample(c.spins(n0)).cpu().numpy()
+    tol = 1e-12 if prec == "f64" else 1e-6
+    for r in sorted({0, R // 2, R - 1}):
+        m = np.linalg.norm(n0[r].sum(axis=0)) / c.N
+        E = o.energy(n0[r])[0]
+        assert abs(st[r, 0] - m) <= tol * m, r
+        assert abs(st[r, 3] - E) <= tol * abs(E), r
+        assert st[r, 5] == 1
