@@ -19,10 +19,11 @@
 // Two launch shapes give the same spins, cones and counts:
 //  - resident: one CTA per replica keeps the replica in shared memory for all
 //    sweeps of a call (colours separated by block barriers, the cone and the
-//    observables updated in the kernel) -- lattices that fit shared memory;
+//    observables updated in the kernel) -- replicas of at most 2048 spins;
 //  - one launch per colour over all replicas, then one for the cone feedback
-//    and one for the observables; the sweep index lives in device memory and
-//    is advanced by the cone kernel, so runs of sweeps replay from a CUDA
+//    (adaptive sweeps) or one for the observables that ends with the cone
+//    step (sampled sweeps); the sweep index lives in device memory and is
+//    advanced by that last launch, so runs of sweeps replay from a CUDA
 //    graph.
 #include <cmath>
 #include <vector>
