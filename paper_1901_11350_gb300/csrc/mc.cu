@@ -55,6 +55,7 @@ struct McColour {
     int s0, s1, s2;        // cells of this colour per direction
     int b;                 // basis atom
     long long per;         // spins of this colour per replica
+    FastDiv fper;          // division by per (per * replicas < 2^31)
 };
 
 // threads of the resident kernel's CTA (FP64: fewer, for the registers)
@@ -202,13 +203,15 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
     __shared__ unsigned cnt[kMcBlock];
     cnt[threadIdx.x] = 0;
     __syncthreads();
-    long long t0 = (long long)blockIdx.x * kMcBlock;
-    long long t = t0 + threadIdx.x;
-    int rep0 = (int)(t0 / col.per);
-    if (t < col.per * n_rep) {
-        int rep = (int)(t / col.per);
+    // replicas x spins of a colour stay below 2^31 (checked on the host):
+    // 32-bit indices, multiply-high divisions
+    const int t0 = (int)blockIdx.x * kMcBlock;  // < total: the grid covers total exactly
+    const unsigned t = (unsigned)t0 + threadIdx.x;
+    const int rep0 = fdiv(t0, col.fper);
+    if (t < (unsigned)col.per * (unsigned)n_rep) {
+        const int rep = fdiv((int)t, col.fper);
         int b, c0, c1, c2;
-        int i = mc_site(S, col, (int)(t - (long long)rep * col.per), b, c0, c1, c2);
+        int i = mc_site(S, col, (int)t - rep * (int)col.per, b, c0, c1, c2);
         // per replica: the cone as its cosine (once per sweep, from FP64) and
         // the temperature factor (once per call): no FP64 work per trial
         if (mc_trial<DMI>(S, x + (long long)rep * S.N, i, b, c0, c1, c2, rep, *sweep_dev, keys, cosc[rep],
@@ -555,6 +558,7 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
             c.fkk = make_fastdiv(k);
             c.s0 = c.s1 = c.s2 = 1;
             c.per = (long long)S.N / k;
+            c.fper = make_fastdiv((int)c.per);
             out.push_back(c);
         }
         return out;
@@ -578,6 +582,7 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
                     c.s2 = (n[2] - r2 + m[2] - 1) / m[2];
                     c.b = b;
                     c.per = (long long)c.s0 * c.s1 * c.s2;
+                    c.fper = make_fastdiv((int)c.per);
                     out.push_back(c);
                 }
     return out;
