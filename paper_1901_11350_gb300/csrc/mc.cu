@@ -113,20 +113,46 @@ __device__ __forceinline__ int mc_site(const Stencil<T> &S, const McColour &col,
     return b + S.nb * (c0 + S.n0 * (c1 + S.n1 * c2));
 }
 
+// The six face bonds of a one-atom lattice whose stencil is exactly the
+// faces (+-1 along each direction), in the order +0, -0, +1, -1, +2, -2.
+template <typename T> struct McFaces {
+    T J[6], D[6][3];
+};
+
 // B0 + sum_j [J_ij n_j + n_j x D_ij] over the stencil entries of basis atom
-// b at cell (c0, c1, c2), neighbours wrapped (periodic) or skipped (open).
-// DMI = false when every D_ij of the stencil vanishes.
-template <bool DMI, typename T, typename R>
-__device__ __forceinline__ v3<T> mc_field(const Stencil<T> &S, const R *n, int b, int c0, int c1, int c2, v3<T> B)
+// b at cell (c0, c1, c2) = spin i, neighbours wrapped (periodic) or skipped
+// (open).  DMI = false when every D_ij of the stencil vanishes; FACES: the
+// stencil is the six faces of F, whose neighbour indices follow from i and
+// the strides without the per-entry offsets.
+template <bool DMI, bool FACES, typename T, typename R>
+__device__ __forceinline__ v3<T> mc_field(const Stencil<T> &S, const McFaces<T> &F, const R *n, int i, int b, int c0,
+                                          int c1, int c2, v3<T> B)
 {
-    for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
-        const NbrEntry<T> &E = S.e[q];
-        const int x0 = wrap(c0 + E.d0, S.n0, S.per0), x1 = wrap(c1 + E.d1, S.n1, S.per1),
-                  x2 = wrap(c2 + E.d2, S.n2, S.per2);
-        if ((x0 | x1 | x2) < 0) continue;
-        const v3<T> nj = ld(n, E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2)));
-        if (DMI) B = B + cross(nj, mk(E.Dx, E.Dy, E.Dz));
-        B = axpy(E.J, nj, B);
+    if constexpr (FACES) {
+        const int s1 = S.n0, s2 = S.n0 * S.n1;
+        const int j[6] = {c0 + 1 < S.n0 ? i + 1 : (S.per0 ? i - (S.n0 - 1) : -1),
+                          c0 > 0 ? i - 1 : (S.per0 ? i + (S.n0 - 1) : -1),
+                          c1 + 1 < S.n1 ? i + s1 : (S.per1 ? i - (S.n1 - 1) * s1 : -1),
+                          c1 > 0 ? i - s1 : (S.per1 ? i + (S.n1 - 1) * s1 : -1),
+                          c2 + 1 < S.n2 ? i + s2 : (S.per2 ? i - (S.n2 - 1) * s2 : -1),
+                          c2 > 0 ? i - s2 : (S.per2 ? i + (S.n2 - 1) * s2 : -1)};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (j[f] < 0) continue;
+            const v3<T> nj = ld(n, j[f]);
+            if (DMI) B = B + cross(nj, mk(F.D[f][0], F.D[f][1], F.D[f][2]));
+            B = axpy(F.J[f], nj, B);
+        }
+    } else {
+        for (int q = S.off[b]; q < S.off[b + 1]; ++q) {
+            const NbrEntry<T> &E = S.e[q];
+            const int x0 = wrap(c0 + E.d0, S.n0, S.per0), x1 = wrap(c1 + E.d1, S.n1, S.per1),
+                      x2 = wrap(c2 + E.d2, S.n2, S.per2);
+            if ((x0 | x1 | x2) < 0) continue;
+            const v3<T> nj = ld(n, E.jb + S.nb * (x0 + S.n0 * (x1 + S.n1 * x2)));
+            if (DMI) B = B + cross(nj, mk(E.Dx, E.Dy, E.Dz));
+            B = axpy(E.J, nj, B);
+        }
     }
     return B;
 }
@@ -165,12 +191,12 @@ __device__ __forceinline__ void mc_azimuth(float u0, float *s, float *c) { sinco
 // xr: global or shared memory); stores the trial direction when accepted.
 // The energy change takes the field's terms linear in n_i (Zeeman, exchange,
 // DMI) and the anisotropy exactly.
-template <bool DMI, typename T, typename R>
-__device__ __forceinline__ bool mc_trial(const Stencil<T> &S, R *xr, int i, int b, int c0, int c1, int c2, int rep,
-                                         uint64_t sweep, const McKeys &keys, T ct, T temp)
+template <bool DMI, bool FACES, typename T, typename R>
+__device__ __forceinline__ bool mc_trial(const Stencil<T> &S, const McFaces<T> &F, R *xr, int i, int b, int c0, int c1,
+                                         int c2, int rep, uint64_t sweep, const McKeys &keys, T ct, T temp)
 {
     const v3<T> ni = ld(xr, i);
-    const v3<T> Bl = mc_field<DMI>(S, xr, b, c0, c1, c2, mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]));
+    const v3<T> Bl = mc_field<DMI, FACES>(S, F, xr, i, b, c0, c1, c2, mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]));
     const v3<T> kh = mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]);
     const T kn = dot(kh, ni);
     uint4 o = philox4x32_10_keyed(
@@ -192,8 +218,9 @@ __device__ __forceinline__ bool mc_trial(const Stencil<T> &S, R *xr, int i, int 
     return ok;
 }
 
-template <typename T, bool DMI>
-__global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ Stencil<T> S, rec_t<T> *__restrict__ x,
+template <typename T, bool DMI, bool FACES>
+__global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ Stencil<T> S,
+                                                        const __grid_constant__ McFaces<T> F, rec_t<T> *__restrict__ x,
                                                         int n_rep, McColour col, const T *__restrict__ temps,
                                                         const T *__restrict__ cosc,
                                                         const unsigned long long *__restrict__ sweep_dev,
@@ -214,7 +241,7 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_colour(const __grid_constant__ 
         int i = mc_site(S, col, (int)t - rep * (int)col.per, b, c0, c1, c2);
         // per replica: the cone as its cosine (once per sweep, from FP64) and
         // the temperature factor (once per call): no FP64 work per trial
-        if (mc_trial<DMI>(S, x + (long long)rep * S.N, i, b, c0, c1, c2, rep, *sweep_dev, keys, cosc[rep],
+        if (mc_trial<DMI, FACES>(S, F, x + (long long)rep * S.N, i, b, c0, c1, c2, rep, *sweep_dev, keys, cosc[rep],
                           temps[rep]))
             atomicAdd(&cnt[rep - rep0], 1u);
     }
@@ -280,16 +307,17 @@ __device__ __forceinline__ double mc_energy(v3<double> n, v3<double> b) { return
 
 // Observables of spin i: sum of n (3 components) and its energy, B the
 // local part of B_eff (Eq. 1 without the dipole term).
-template <bool DMI, typename T, typename R, typename A>
-__device__ __forceinline__ void mc_observe(const Stencil<T> &S, const R *xr, int i, A v[4])
+template <bool DMI, bool FACES, typename T, typename R, typename A>
+__device__ __forceinline__ void mc_observe(const Stencil<T> &S, const McFaces<T> &F, const R *xr, int i, A v[4])
 {
     const v3<T> ni = ld(xr, i);
     int b, c0, c1, c2;
     decode_site(S, i, b, c0, c1, c2);
     const v3<T> Bz = mk(S.Bz[b][0], S.Bz[b][1], S.Bz[b][2]);
     const T k2 = T(2) * S.K[b] * dot(mk(S.Kh[b][0], S.Kh[b][1], S.Kh[b][2]), ni);
-    const v3<T> B = mc_field<DMI>(S, xr, b, c0, c1, c2,
-                                  mk(fma(k2, S.Kh[b][0], Bz.x), fma(k2, S.Kh[b][1], Bz.y), fma(k2, S.Kh[b][2], Bz.z)));
+    const v3<T> B = mc_field<DMI, FACES>(
+        S, F, xr, i, b, c0, c1, c2,
+        mk(fma(k2, S.Kh[b][0], Bz.x), fma(k2, S.Kh[b][1], Bz.y), fma(k2, S.Kh[b][2], Bz.z)));
     v[0] = v[0] + mc_term(ni.x);
     v[1] = v[1] + mc_term(ni.y);
     v[2] = v[2] + mc_term(ni.z);
@@ -302,8 +330,9 @@ __device__ __forceinline__ void mc_observe(const Stencil<T> &S, const R *xr, int
 // the partials (warp 0, a fixed order) and accumulates m, m^2, m^4, E, E^2
 // and the sample count (FP64); with cone.acc set it then takes the sweep's
 // cone step of that replica (k_mc_cone).
-template <typename T, bool DMI>
+template <typename T, bool DMI, bool FACES>
 __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ Stencil<T> S,
+                                                        const __grid_constant__ McFaces<T> F,
                                                         const rec_t<T> *__restrict__ x, int bpr, double *part,
                                                         unsigned *tickets, double *stats, const McCone<T> cone)
 {
@@ -314,7 +343,8 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ 
     const rec_t<T> *xr = x + (long long)rep * S.N;
     // block blk of the replica takes spins blk * kMcBlock + t + k bpr kMcBlock
     A v[4] = {};
-    for (int i = blk * kMcBlock + threadIdx.x; i < S.N; i += bpr * kMcBlock) mc_observe<DMI>(S, xr, i, v);
+    for (int i = blk * kMcBlock + threadIdx.x; i < S.N; i += bpr * kMcBlock)
+        mc_observe<DMI, FACES>(S, F, xr, i, v);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] = v[k] + shfl_down(v[k], o);
@@ -375,8 +405,9 @@ __global__ void __launch_bounds__(kMcBlock) k_mc_sample(const __grid_constant__ 
 // statistics (FP64, kept in registers between sweeps).  With the cone fixed
 // (target 0) the next sweep needs nothing from that update, so the other
 // warps go on while lane 0 finishes it.
-template <typename T, bool DMI>
+template <typename T, bool DMI, bool FACES>
 __global__ void __launch_bounds__(kMcResBlock<T>) k_mc_resident(const __grid_constant__ Stencil<T> S,
+                                                             const __grid_constant__ McFaces<T> F,
                                                              rec_t<T> *__restrict__ x,
                                                              const __grid_constant__ McColourSet cs,
                                                              const T *__restrict__ temps, double *__restrict__ cone,
@@ -416,13 +447,13 @@ __global__ void __launch_bounds__(kMcResBlock<T>) k_mc_resident(const __grid_con
             for (int q = threadIdx.x; q < per; q += kB) {
                 int b, c0, c1, c2;
                 const int i = mc_site(S, col, q, b, c0, c1, c2);
-                accepted += mc_trial<DMI>(S, sh, i, b, c0, c1, c2, rep, sweep, keys, ct, temp) ? 1u : 0u;
+                accepted += mc_trial<DMI, FACES>(S, F, sh, i, b, c0, c1, c2, rep, sweep, keys, ct, temp) ? 1u : 0u;
             }
             __syncthreads();
         }
         A v[4] = {};
         if (sample)
-            for (int i = threadIdx.x; i < S.N; i += kB) mc_observe<DMI>(S, sh, i, v);
+            for (int i = threadIdx.x; i < S.N; i += kB) mc_observe<DMI, FACES>(S, F, sh, i, v);
         accepted = __reduce_add_sync(0xffffffffu, accepted);
         if (sample) {
 #pragma unroll
@@ -593,7 +624,7 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
 // Blocks per replica of k_mc_sample: all blocks of all replicas resident at
 // once (one wave, the SMs within one block of each other), at most one per
 // kMcBlock spins.
-template <typename T, bool DMI>
+template <typename T, bool DMI, bool FACES>
 int mc_sample_blocks(int N, int n_rep)
 {
     static int cap = 0;  // resident blocks of the kernel on the device
@@ -602,7 +633,8 @@ int mc_sample_blocks(int N, int n_rep)
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_sample<T, DMI>, kMcBlock, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_sample<T, DMI, FACES>, kMcBlock, 0) !=
+                cudaSuccess ||
             per < 1)
             per = 1;
         cap = sms * per;
@@ -642,7 +674,34 @@ bool mc_has_dmi(const Stencil<T> &S)
     return false;
 }
 
-template <typename T, bool DMI>
+// The face bonds in the order of McFaces when the stencil is exactly the six
+// faces of a one-atom lattice; false otherwise.
+template <typename T>
+bool mc_faces(const Stencil<T> &S, McFaces<T> &F)
+{
+    F = McFaces<T>{};
+    if (S.nb != 1 || S.off[1] != 6) return false;
+    bool seen[6] = {false, false, false, false, false, false};
+    for (int q = 0; q < 6; ++q) {
+        const NbrEntry<T> &E = S.e[q];
+        const int d[3] = {E.d0, E.d1, E.d2};
+        int f = -1, nz = 0;
+        for (int a = 0; a < 3; ++a)
+            if (d[a]) {
+                ++nz;
+                f = d[a] == 1 ? 2 * a : (d[a] == -1 ? 2 * a + 1 : -1);
+            }
+        if (E.jb != 0 || nz != 1 || f < 0 || seen[f]) return false;
+        seen[f] = true;
+        F.J[f] = E.J;
+        F.D[f][0] = E.Dx;
+        F.D[f][1] = E.Dy;
+        F.D[f][2] = E.Dz;
+    }
+    return true;
+}
+
+template <typename T, bool DMI, bool FACES>
 int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double *T_host, const sp_mc_params *p,
            int n_sweeps, double *cone, double *stats, cudaStream_t st)
 {
@@ -650,7 +709,9 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
     if (!ms) ms = new McScratch;
     std::vector<McColour> cols = mc_colours(S);
     if (cols.empty()) return SP_ERR_UNSUPPORTED;
-    const int bpr = mc_sample_blocks<T, DMI>(S.N, n_rep);
+    McFaces<T> F;
+    mc_faces(S, F);
+    const int bpr = mc_sample_blocks<T, DMI, FACES>(S.N, n_rep);
     if (grow_buf(ms->T, sizeof(T) * n_rep) || grow_buf(ms->acc, sizeof(unsigned long long) * (n_rep + kMcBlock)) ||
         grow_buf(ms->sweep, sizeof(unsigned long long)) || grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) ||
         grow_buf(ms->cnt, sizeof(unsigned) * n_rep) || grow_buf(ms->cosc, sizeof(T) * n_rep))
@@ -673,12 +734,13 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
         McColourSet set{};
         set.n = (int)cols.size();
         for (int k = 0; k < set.n; ++k) set.c[k] = cols[k];
-        if (cudaFuncSetAttribute(k_mc_resident<T, DMI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_mc_resident<T, DMI, FACES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)res_bytes) != cudaSuccess)
             return SP_ERR_CUDA;
         for (int k = 0; k < n_sweeps; k += kMcResMaxSweeps) {
             const int ns = n_sweeps - k < kMcResMaxSweeps ? n_sweeps - k : kMcResMaxSweeps;
-            k_mc_resident<T, DMI><<<(unsigned)n_rep, kMcResBlock<T>, res_bytes, st>>>(S, x, set, temps, cone, stats, keys,
+            k_mc_resident<T, DMI, FACES><<<(unsigned)n_rep, kMcResBlock<T>, res_bytes, st>>>(S, F, x, set, temps, cone,
+                                                                                     stats, keys,
                                                                               s0 + (unsigned long long)k, ns,
                                                                               p->target_accept, p->sample);
         }
@@ -692,12 +754,12 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
     auto sweep = [&](cudaStream_t ss) {
         for (const McColour &col : cols) {
             long long work = col.per * n_rep;
-            k_mc_colour<T, DMI><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(
-                S, x, n_rep, col, temps, cosc, sw, keys, acc);
+            k_mc_colour<T, DMI, FACES><<<(unsigned)((work + kMcBlock - 1) / kMcBlock), kMcBlock, 0, ss>>>(
+                S, F, x, n_rep, col, temps, cosc, sw, keys, acc);
         }
         const McCone<T> cc{acc, cone, cosc, p->target_accept, sw};
         if (p->sample)
-            k_mc_sample<T, DMI><<<(unsigned)(bpr * n_rep), kMcBlock, 0, ss>>>(S, x, bpr, part, tk, stats, cc);
+            k_mc_sample<T, DMI, FACES><<<(unsigned)(bpr * n_rep), kMcBlock, 0, ss>>>(S, F, x, bpr, part, tk, stats, cc);
         else
             k_mc_cone<T><<<1, 256, 0, ss>>>(n_rep, (long long)S.N, cc, stats);
     };
@@ -743,6 +805,18 @@ int mc_run(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double 
     return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
 
+// mc_run for the field variant the stencil allows.
+template <typename T>
+int mc_dispatch(sp_ctx *c, const Stencil<T> &S, void *spins, int n_rep, const double *T_host, const sp_mc_params *p,
+                int n_sweeps, double *cone, double *stats, cudaStream_t st)
+{
+    McFaces<T> F;
+    const bool dmi = mc_has_dmi(S), faces = mc_faces(S, F);
+    auto run = dmi ? (faces ? mc_run<T, true, true> : mc_run<T, true, false>)
+                   : (faces ? mc_run<T, false, true> : mc_run<T, false, false>);
+    return run(c, S, spins, n_rep, T_host, p, n_sweeps, cone, stats, st);
+}
+
 int mfail(sp_ctx *c, int code, const char *msg)
 {
     c->err = msg;
@@ -756,12 +830,17 @@ int sample_run(sp_ctx *c, const Stencil<T> &S, const void *spins, int n_rep, dou
     McScratch *&ms = c->mc;
     if (!ms) ms = new McScratch;
     const bool dmi = mc_has_dmi(S);
-    const int bpr = dmi ? mc_sample_blocks<T, true>(S.N, n_rep) : mc_sample_blocks<T, false>(S.N, n_rep);
+    McFaces<T> F;
+    const bool faces = mc_faces(S, F);
+    const int bpr = dmi ? (faces ? mc_sample_blocks<T, true, true>(S.N, n_rep) : mc_sample_blocks<T, true, false>(S.N, n_rep))
+                        : (faces ? mc_sample_blocks<T, false, true>(S.N, n_rep)
+                                 : mc_sample_blocks<T, false, false>(S.N, n_rep));
     if (grow_buf(ms->part, 4 * sizeof(double) * (size_t)bpr * n_rep) || grow_buf(ms->cnt, sizeof(unsigned) * n_rep) ||
         cudaMemsetAsync(ms->cnt.p, 0, sizeof(unsigned) * n_rep, st) != cudaSuccess)
         return SP_ERR_CUDA;
-    auto kern = dmi ? k_mc_sample<T, true> : k_mc_sample<T, false>;
-    kern<<<(unsigned)(bpr * n_rep), kMcBlock, 0, st>>>(S, (const rec_t<T> *)spins, bpr, (double *)ms->part.p,
+    auto kern = dmi ? (faces ? k_mc_sample<T, true, true> : k_mc_sample<T, true, false>)
+                    : (faces ? k_mc_sample<T, false, true> : k_mc_sample<T, false, false>);
+    kern<<<(unsigned)(bpr * n_rep), kMcBlock, 0, st>>>(S, F, (const rec_t<T> *)spins, bpr, (double *)ms->part.p,
                                                        (unsigned *)ms->cnt.p, stats, McCone<T>{});
     return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
@@ -804,10 +883,10 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
         if (!(T[r] >= 0)) return mfail(c, SP_ERR_ARG, "temperatures must be >= 0");
     if (c->h.dipole != SP_DIPOLE_NONE) return mfail(c, SP_ERR_UNSUPPORTED, "Monte Carlo with the dipole term");
     int e = c->prec == SP_F64
-                ? (mc_has_dmi(c->Sd) ? mc_run<double, true> : mc_run<double, false>)(
-                      c, c->Sd, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream)
-                : (mc_has_dmi(c->Sf) ? mc_run<float, true> : mc_run<float, false>)(
-                      c, c->Sf, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev, (cudaStream_t)stream);
+                ? mc_dispatch<double>(c, c->Sd, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev,
+                                      (cudaStream_t)stream)
+                : mc_dispatch<float>(c, c->Sf, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev,
+                                     (cudaStream_t)stream);
     if (e == SP_ERR_UNSUPPORTED)
         return mfail(c, e, "lattice has no colouring (neither (c0 + c1 + c2) mod k nor the product colouring "
                            "applies)");
