@@ -7,6 +7,7 @@ import re
 
 import pytest
 
+import oracle
 from paper_1901_11350_gb300 import binding as B
 from paper_1901_11350_gb300 import build
 from paper_1901_11350_gb300 import inputs as I
@@ -190,3 +191,45 @@ def test_replica_and_sample_rejections():
     assert L.sp_llg_step_replicas(d._h, spins, 2, T2, C.byref(p), 1, None) == -4
     assert L.sp_sample(d._h, spins, 1, C.c_void_p(512), None) == -4
     d.close()
+
+
+MC_COLOURINGS = [
+    # (geometry, hamiltonian, colours) -- sum colouring (c0 + c1 + c2) mod k
+    (I.simple_cubic(2), dict(J=[1.0]), 2),
+    (I.simple_cubic(3), dict(J=[1.0]), 3),
+    (I.simple_cubic(6, 4, 4), dict(J=[1.0], dmi_kind="bulk", D=[0.2]), 2),
+    (I.simple_cubic(5), dict(J=[1.0]), 5),
+    (I.simple_cubic(7), dict(J=[1.0]), 7),
+    (I.simple_cubic(15), dict(J=[1.0]), 3),
+    (I.simple_cubic(5, periodic=(False, False, False)), dict(J=[1.0]), 5),
+    # no sum colouring (2 does not divide 9, 3 not 4, 6 not 9): the product, 2 x 3 x 2
+    (I.simple_cubic(6, 9, 4), dict(J=[1.0]), 12),
+    (I.square(7, 4, periodic=(True, False)), dict(J=[1.0]), 7),
+    (I.square(1, 1), dict(B=[0, 0, 1.0]), 1),
+    # the product colouring
+    (I.simple_cubic(4), dict(J=[1.0, -0.2]), 8),
+    (I.simple_cubic(9), dict(J=[1.0, -0.2]), 27),
+    (I.hexagonal(9, 9, periodic=(True, True)), dict(J=[1.0]), 9),
+    (I.hexagonal(6, 6, periodic=(True, True)), dict(J=[1.0], dmi_kind="interfacial", D=[0.3]), 4),
+    (I.hexagonal(6, 5, periodic=(True, False)), dict(J=[1.0]), 4),
+    (dict(bravais=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], basis=[[0, 0, 0], [0.5, 0.5, 0.5]], n_cells=[4, 4, 4],
+          periodic=[1, 1, 1], lattice_constant=1.0, mu_s=[2.0, 1.0]),
+     dict(pairs=[(0, 1, (0, 0, 0), 1.0, (0, 0, 0)), (1, 0, (1, 1, 1), 0.5, (0, 0, 0))]), 16),
+    # neither: a second-shell bond with an odd periodic extent not divisible by 3
+    (I.simple_cubic(7), dict(J=[1.0, -0.2]), 0),
+    # a bond two cells long: no product colouring; (c0 + c1 + c2) mod 3
+    (I.square(6, 6, periodic=(True, True)), dict(pairs=[(0, 0, (1, 0, 0), 1.0, (0, 0, 0)),
+                                                        (0, 0, (0, 1, 0), 1.0, (0, 0, 0)),
+                                                        (0, 0, (2, 0, 0), 0.3, (0, 0, 0))]), 3),
+]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("case", range(len(MC_COLOURINGS)))
+def test_mc_colouring_host_logic_agrees_with_the_oracle(case, prec):
+    # the library's colouring choice (host code, no GPU) against the
+    # oracle's independent implementation and the expected count
+    g, h, n = MC_COLOURINGS[case]
+    c = B.Context(g, h, prec)
+    assert c.mc_colours() == oracle.System(g, h).mc_colours() == n
+    c.close()
