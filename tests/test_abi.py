@@ -233,3 +233,27 @@ def test_mc_colouring_host_logic_agrees_with_the_oracle(case, prec):
     c = B.Context(g, h, prec)
     assert c.mc_colours() == oracle.System(g, h).mc_colours() == n
     c.close()
+
+
+CUBIC_PATH = [
+    # one basis atom, bonds within the 3x3x3 cell neighbourhood, one exchange
+    # constant per face / edge / corner class, DMI on face bonds only
+    (I.simple_cubic(8), dict(J=[1.0, -0.2, 0.05], dmi_kind="bulk", D=[0.2], K=[0.05], Khat=[[0, 0, 1]]), 1),
+    (I.simple_cubic(8), dict(J=[1.0]), 1),
+    (I.simple_cubic(8), dict(J=[1.0], dmi_kind="interfacial", D=[0.3]), 1),
+    (I.square(8, 8, periodic=(True, True)), dict(J=[1.0], dmi_kind="interfacial", D=[0.3]), 1),
+    (I.simple_cubic(8), dict(J=[1.0, 0.2], dmi_kind="bulk", D=[0.2, 0.1]), 0),   # DMI on edge bonds
+    (I.simple_cubic(8), dict(J=[1.0, 0.1, 0.1, 0.05]), 0),                        # a bond two cells long
+    (I.hexagonal(8, 8, periodic=(True, True)), dict(J=[1.0]), 0),                 # (1, -1) without (1, 1)
+    (dict(bravais=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], basis=[[0, 0, 0], [0.5, 0.5, 0.5]], n_cells=[4, 4, 4],
+          periodic=[1, 1, 1], lattice_constant=1.0, mu_s=[2.0, 1.0]), dict(J=[1.0]), 0),  # two basis atoms
+]
+
+
+@pytest.mark.parametrize("case", range(len(CUBIC_PATH)))
+def test_27_point_path_detection(case):
+    g, h, expect = CUBIC_PATH[case]
+    for prec in ("f32", "f64"):
+        c = B.Context(g, h, prec)
+        assert c.get_option("has_cubic_path") == expect
+        c.close()
