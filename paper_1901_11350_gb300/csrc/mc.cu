@@ -627,8 +627,8 @@ std::vector<McColour> mc_colours(const Stencil<T> &S)
 template <typename T, bool DMI, bool FACES>
 int mc_sample_blocks(int N, int n_rep)
 {
-    static int cap = 0;  // resident blocks of the kernel on the device
-    if (!cap) {
+    // resident blocks of the kernel on the device (computed once, thread-safe)
+    static const int cap = [] {
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
@@ -637,8 +637,8 @@ int mc_sample_blocks(int N, int n_rep)
                 cudaSuccess ||
             per < 1)
             per = 1;
-        cap = sms * per;
-    }
+        return sms * per;
+    }();
     const int want = cap / n_rep > 0 ? cap / n_rep : 1;
     const int most = (N + kMcBlock - 1) / kMcBlock;
     return want < most ? want : most;
@@ -647,13 +647,14 @@ int mc_sample_blocks(int N, int n_rep)
 template <typename T>
 size_t mc_resident_bytes(const Stencil<T> &S, size_t n_colours)
 {
-    static int optin = -1;
-    if (optin < 0) {
-        int dev = 0;
+    // opt-in shared memory per block (computed once, thread-safe)
+    static const int optin = [] {
+        int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-            optin = 0;
-    }
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 0;
+        return v;
+    }();
     const size_t bytes = sizeof(typename ShRec<T>::type) * (size_t)S.N;
     const size_t reserve = 2048;  // the kernel's static shared memory
     if (n_colours > (size_t)kMcMaxResColours || bytes == 0 || bytes + reserve > (size_t)optin) return 0;
