@@ -372,7 +372,11 @@ int sp_mc_colours(sp_ctx *ctx, int *n_colours);
  *              m^2, m^4, E, E^2 (m = |sum_i n_i| / N, E total energy in meV,
  *              each after every sweep when p->sample), the number of samples,
  *              accepted trials and trials
- * SP_ERR_UNSUPPORTED for the dipole term or a lattice without colouring.
+ * SP_ERR_ARG for NULL or misaligned pointers (records 16 B aligned in FP32,
+ * 32 B in FP64; cone and stats 8 B), n_rep < 1, n_sweeps < 0, more than
+ * 2^31 spins over all replicas, target_accept outside [0, 1) or a negative
+ * temperature; SP_ERR_UNSUPPORTED for the dipole term or a lattice without
+ * colouring.
  * Runs of sweeps are replayed from a CUDA graph on a private stream ordered
  * after and before `stream` by events. */
 int sp_mc_sweeps(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const sp_mc_params *p, int n_sweeps,

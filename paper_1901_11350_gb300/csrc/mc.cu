@@ -877,6 +877,8 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
     if (!c) return SP_ERR_ARG;
     if (!c->have_geom || !c->have_ham) return mfail(c, SP_ERR_STATE, "context not configured");
     if (!spins_dev || !T || !p || !cone_dev || !stats_dev) return mfail(c, SP_ERR_ARG, "NULL argument");
+    if ((uintptr_t)spins_dev % (c->prec == SP_F64 ? 32 : 16)) return mfail(c, SP_ERR_ARG, "spins misaligned");
+    if ((uintptr_t)cone_dev % 8 || (uintptr_t)stats_dev % 8) return mfail(c, SP_ERR_ARG, "cone or stats misaligned");
     if (n_rep < 1 || n_sweeps < 0) return mfail(c, SP_ERR_ARG, "n_rep >= 1 and n_sweeps >= 0 required");
     if ((long long)n_rep * c->N >= (1LL << 31)) return mfail(c, SP_ERR_ARG, "more than 2^31 spins");
     if (!(p->target_accept >= 0 && p->target_accept < 1)) return mfail(c, SP_ERR_ARG, "target_accept in [0, 1) required");

@@ -193,6 +193,36 @@ def test_replica_and_sample_rejections():
     d.close()
 
 
+def test_mc_sweep_rejections():
+    c = B.Context(I.simple_cubic(6), dict(J=[1.0]), "f32")
+    L = B.lib()
+    h = c._h
+    T2 = (C.c_double * 2)(5.0, 10.0)
+    bad = (C.c_double * 2)(5.0, -1.0)
+    ok = B.MCParams(1, 0, 0.5, 1)
+    spins, cone, stats = C.c_void_p(256), C.c_void_p(4096), C.c_void_p(8192)  # never dereferenced
+    assert L.sp_mc_sweeps(h, None, 2, T2, C.byref(ok), 1, cone, stats, None) == -1
+    assert L.sp_mc_sweeps(h, spins, 2, None, C.byref(ok), 1, cone, stats, None) == -1
+    assert L.sp_mc_sweeps(h, spins, 2, T2, None, 1, cone, stats, None) == -1
+    assert L.sp_mc_sweeps(h, C.c_void_p(264), 2, T2, C.byref(ok), 1, cone, stats, None) == -1
+    assert b"misaligned" in L.sp_last_error(h)
+    assert L.sp_mc_sweeps(h, spins, 2, T2, C.byref(ok), 1, C.c_void_p(4100), stats, None) == -1
+    assert L.sp_mc_sweeps(h, spins, 0, T2, C.byref(ok), 1, cone, stats, None) == -1
+    assert L.sp_mc_sweeps(h, spins, 2, T2, C.byref(ok), -1, cone, stats, None) == -1
+    assert L.sp_mc_sweeps(h, spins, 2, bad, C.byref(ok), 1, cone, stats, None) == -1
+    assert b"temperature" in L.sp_last_error(h)
+    for t in (-0.1, 1.0, float("nan")):
+        assert L.sp_mc_sweeps(h, spins, 2, T2, C.byref(B.MCParams(1, 0, t, 1)), 1, cone, stats, None) == -1
+    c.close()
+    d = B.Context(I.square(8, 8), dict(J=[1.0], dipole="fft"), "f32")
+    assert L.sp_mc_sweeps(d._h, spins, 2, T2, C.byref(ok), 1, cone, stats, None) == -4
+    d.close()
+    e = B.Context(I.simple_cubic(7), dict(J=[1.0, -0.2]), "f64")  # no colouring
+    assert L.sp_mc_sweeps(e._h, spins, 2, T2, C.byref(ok), 1, cone, stats, None) == -4
+    assert b"colouring" in L.sp_last_error(e._h)
+    e.close()
+
+
 MC_COLOURINGS = [
     # (geometry, hamiltonian, colours) -- sum colouring (c0 + c1 + c2) mod k
     (I.simple_cubic(2), dict(J=[1.0]), 2),
