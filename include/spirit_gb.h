@@ -386,14 +386,18 @@ int sp_mc_sweeps(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const
  * replica-major) into stats_dev (DEVICE, n_rep x 8 doubles, the layout of
  * sp_mc_sweeps): m, m^2, m^4, E, E^2 and one more sample; the acceptance
  * slots 6 and 7 are not touched.  m = |sum_i n_i| / N and E the total energy
- * of Eq. 1 without the dipole term, both summed in FP64 in a fixed order.
- * Stream-ordered, no synchronisation.  SP_ERR_UNSUPPORTED with the dipole
- * term. */
+ * of Eq. 1 without the dipole term, both summed in a fixed order to FP64
+ * accuracy (FP32 contexts: float-float within a thread and a warp, FP64
+ * across warps and blocks).  Stream-ordered, no synchronisation.
+ * SP_ERR_ARG for NULL or misaligned pointers; SP_ERR_UNSUPPORTED with the
+ * dipole term. */
 int sp_sample(sp_ctx *ctx, const void *spins_dev, int n_rep, double *stats_dev, void *stream);
 
 /* ------------------------------------------------------------------------
  * Covariant Hessian, lowest mode and minimum mode following (Sec. MMF and
- * the appendix on the manifold of constant-length spins)
+ * the appendix on the manifold of constant-length spins).  All three return
+ * SP_ERR_ARG for NULL pointers or record arrays off a record boundary (16 B
+ * in FP32, 32 B in FP64) and SP_ERR_UNSUPPORTED with the dipole term.
  * ------------------------------------------------------------------------ */
 
 /* out = H v: the covariant Hessian of the energy at the configuration n_dev

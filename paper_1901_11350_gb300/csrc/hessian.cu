@@ -14,6 +14,7 @@
 // eigenvalue is not negative) by the velocity projection of Appendix D.
 #include <algorithm>
 #include <cmath>
+#include <initializer_list>
 #include <vector>
 
 #include "ctx.h"
@@ -438,6 +439,15 @@ int hcheck(sp_ctx *c)
     return SP_OK;
 }
 
+// Device record arrays start on a record boundary (16 B in FP32, 32 B in FP64).
+bool hrecords_aligned(const sp_ctx *c, std::initializer_list<const void *> ptrs)
+{
+    const uintptr_t a = c->prec == SP_F64 ? 32 : 16;
+    for (const void *p : ptrs)
+        if ((uintptr_t)p % a) return false;
+    return true;
+}
+
 }  // namespace
 
 void hess_scratch_destroy(HessScratch *h)
@@ -457,6 +467,7 @@ int sp_hessian_apply(sp_ctx *c, const void *n_dev, const void *v_dev, void *out_
     if (rc) return rc;
     if (!n_dev || !v_dev || !out_dev) return hfail(c, SP_ERR_ARG, "NULL argument");
     if (v_dev == out_dev) return hfail(c, SP_ERR_ARG, "v and out must differ");
+    if (!hrecords_aligned(c, {n_dev, v_dev, out_dev})) return hfail(c, SP_ERR_ARG, "misaligned record array");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned nb = hblocks(c->N);
     cudaError_t e = c->prec == SP_F64 ? launch_pdl(k_hvp<double>, dim3(nb), dim3(kHB), 0, st, c->Sd, (const dq4 *)n_dev,
@@ -472,6 +483,7 @@ int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, dou
     if (rc) return rc;
     if (!n_dev || !mode_dev || !lambda) return hfail(c, SP_ERR_ARG, "NULL argument");
     if (krylov < 1 || krylov > kMaxKrylov) return hfail(c, SP_ERR_ARG, "krylov must be in 1..256");
+    if (!hrecords_aligned(c, {n_dev, mode_dev})) return hfail(c, SP_ERR_ARG, "misaligned record array");
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? lowest_mode_run<double>(c, c->Sd, n_dev, mode_dev, krylov, lambda, st)
                            : lowest_mode_run<float>(c, c->Sf, n_dev, mode_dev, krylov, lambda, st);
@@ -486,6 +498,7 @@ int sp_mmf(sp_ctx *c, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf_p
     if (!n_dev || !vel_dev || !mode_dev || !p || !max_force || !lambda) return hfail(c, SP_ERR_ARG, "NULL argument");
     if (!(p->dt > 0) || !(p->mass > 0) || p->krylov < 1 || p->krylov > kMaxKrylov || n_iter < 0)
         return hfail(c, SP_ERR_ARG, "bad MMF parameters");
+    if (!hrecords_aligned(c, {n_dev, vel_dev, mode_dev})) return hfail(c, SP_ERR_ARG, "misaligned record array");
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? mmf_run<double>(c, c->Sd, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st)
                            : mmf_run<float>(c, c->Sf, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st);

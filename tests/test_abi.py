@@ -223,6 +223,25 @@ def test_mc_sweep_rejections():
     e.close()
 
 
+def test_hessian_rejections():
+    c = B.Context(I.square(8, 8, periodic=(True, True)), dict(J=[1.0], K=[0.1], Khat=[[0, 0, 1]]), "f64")
+    L = B.lib()
+    h = c._h
+    n, v, out = C.c_void_p(512), C.c_void_p(1024), C.c_void_p(2048)  # never dereferenced
+    lam = C.c_double()
+    assert L.sp_hessian_apply(h, None, v, out, None) == -1
+    assert L.sp_hessian_apply(h, n, v, v, None) == -1
+    assert L.sp_hessian_apply(h, n, C.c_void_p(1040), out, None) == -1  # 16 B: not an FP64 record boundary
+    assert b"misaligned" in L.sp_last_error(h)
+    assert L.sp_lowest_mode(h, n, out, 0, C.byref(lam), None) == -1
+    assert L.sp_lowest_mode(h, n, out, 257, C.byref(lam), None) == -1
+    assert L.sp_lowest_mode(h, C.c_void_p(520), out, 8, C.byref(lam), None) == -1
+    c.close()
+    d = B.Context(I.square(8, 8), dict(J=[1.0], dipole="fft"), "f32")
+    assert L.sp_hessian_apply(d._h, n, v, out, None) == -4
+    d.close()
+
+
 MC_COLOURINGS = [
     # (geometry, hamiltonian, colours) -- sum colouring (c0 + c1 + c2) mod k
     (I.simple_cubic(2), dict(J=[1.0]), 2),
