@@ -45,6 +45,14 @@ SOLVER_BYTES = {"heun": {"llg_predictor": 48, "llg_corrector": 48},
                 "depondt": {"llg_predictor": 48, "llg_corrector": 64},
                 "sib": {"llg_predictor": 48, "llg_corrector": 64},
                 "rk4": {"llg_predictor": 48, "llg_corrector": (80 + 80 + 64) / 3}}
+# the method's own algorithmic bytes per spin and time step (FP32 records),
+# which the roofline fraction is charged with: a two-stage step reads n and
+# writes the predictor n^p (32 B), then reads n and n^p and writes n' (48 B);
+# the field and the thermal noise are recomputed, not stored.  (The kernels
+# above move 96 B for Heun because they store the folded corrector term q in
+# place of recomputing the stencil on n and the noise.)  RK4 has no two-stage
+# figure and is charged with the design's bytes.
+METHOD_STEP_BYTES = {"heun": 80, "depondt": 80, "sib": 80}
 CORRECTOR_LAUNCHES = {"heun": 1, "depondt": 1, "sib": 1, "rk4": 3}
 KERNEL_SOURCES = ["paper_1901_11350_gb300/csrc/field_llg.cu", "paper_1901_11350_gb300/csrc/cubic.cu",
                   "paper_1901_11350_gb300/csrc/common.cuh"]
@@ -312,19 +320,27 @@ def run_gpu(args):
     e2e_value = whole_job_rate(world, N * S * args.steps, max_over_ranks(e0.elapsed_time(e1), "cuda"))
 
     peaks, peak_kind = measured_peaks()
-    dom = max(kern, key=lambda k: kern[k][0])
-    ms, cnt = kern[dom]
-    avg_s = ms / max(cnt, 1) / 1e3
-    achieved = bps[dom] * N / avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"],
-            "traffic": ncu_traffic(dom) if args.solver == "heun" and not args.generic else None,
-            "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bps[dom] * N, "avg_launch_us": avg_s * 1e6,
-            "launches": cnt, "kernel_timing": "CUDA events around each launch, %d profiled steps after the timed region"
-            % prof_steps,
-            "pair_frac_timed_region": bytes_per_step * N * S * args.steps / (el_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-            "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kern.items()}}
+    # the roofline unit is one LLG time step (its predictor and corrector
+    # launches together), timed by the CUDA events around the timed region:
+    # per-launch events would serialise the two passes' overlap
+    step_s = el_ms / 1e3 / (S * args.steps) * world
+    method_bytes = METHOD_STEP_BYTES.get(args.solver, bytes_per_step)
+    achieved = method_bytes * N / step_s / 1e9
+    tr = [ncu_traffic(k) for k in ("llg_predictor", "llg_corrector")] if args.solver == "heun" and not args.generic \
+        else [None]
+    tot_ms = sum(v[0] for v in kern.values())
+    roof = {"bound": "hbm", "kernel": "llg_step (predictor + corrector launch of one time step)",
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": None if None in tr else sum(tr), "peak_source": peak_kind,
+            "algorithmic_bytes_per_spin_step": method_bytes,
+            "algorithmic_bytes_per_step": method_bytes * N, "us_per_step": step_s * 1e6,
+            "timing": "CUDA events around the timed region, %d LLG steps" % (S * args.steps),
+            "design_bytes_per_spin_step": bytes_per_step,
+            "design_frac": bytes_per_step * N / step_s / 1e9 / peaks["hbm_gbs"],
+            "kernel_share": {k: {"share": v[0] / tot_ms if tot_ms else None, "launches": v[1],
+                                 "avg_launch_us": 1e3 * v[0] / max(v[1], 1)} for k, v in kern.items()},
+            "kernel_share_timing": "serialised: CUDA events around every launch, %d profiled bench steps after "
+                                   "the timed region (shares, not the kernels' speed inside the step)" % prof_steps}
     clocks = clk.summary()
     if world > 1:
         dist.destroy_process_group()
@@ -341,15 +357,25 @@ def run_gpu(args):
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
-           "gpu_launches": (1 + CORRECTOR_LAUNCHES[args.solver]) * S * args.steps, "roofline": roof, "clocks": clocks,
+           "gpu_launches": ((1 + CORRECTOR_LAUNCHES[args.solver]) * S + 1) * args.steps, "roofline": roof, "clocks": clocks,
            "finite": finite}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(dict(cfg, run=dict(r, solver=args.solver)))
+    if world == 1 and not args.no_relax:
+        # the metric's second half: time to converge relaxations, against the
+        # plain FP64 method on the same GPU
+        out["relaxation"] = {"gneb": gneb_result(args, compact=True),
+                             "warm_start": warmstart_result(args, args.relax_systems, compact=True)}
     print(json.dumps(out))
     return 0
 
 
 def run_gneb(args):
+    print(json.dumps(gneb_result(args)))
+    return 0
+
+
+def gneb_result(args, compact=False):
     """Batched GNEB workload (48 skyrmion-collapse chains): device seconds to
     max force < 1e-5 meV/rad, batched FP32 against the plain FP64 loop over
     chains through the single-chain entry point, on the same GPU."""
@@ -358,7 +384,7 @@ def run_gneb(args):
     from paper_1901_11350_gb300 import build
     from paper_1901_11350_gb300 import gneb_batch as G
 
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(torch.cuda.current_device())
     build.build()
     t0 = time.perf_counter()
     chains = G.prepare(n_chains=args.chains, seed=4, precision="f32")
@@ -367,9 +393,8 @@ def run_gneb(args):
     G.run_batched(chains[:2], **dict(kw, chunk=10, tol=0.0, max_iter=10))  # warm-up (graph, tables)
     state, batch_s = G.run_batched(chains, **kw)
     if args.gneb_no_reference:  # profiling aid: the batched run alone
-        print(json.dumps({"metric": "GNEB device seconds to max force < 1e-5 meV/rad, all chains", "value": batch_s,
-                          "unit": "s", "higher_is_better": False, "reference": None}))
-        return 0
+        return {"metric": "GNEB device seconds to max force < 1e-5 meV/rad, all chains", "value": batch_s,
+                "unit": "s", "higher_is_better": False, "reference": None}
     ref, ref_s = G.run_per_chain(chains, precision="f64", **kw)
     from paper_1901_11350_gb300 import binding as Bd
     # barrier heights in FP64: image energies of the converged FP32 chains
@@ -437,14 +462,16 @@ def run_gneb(args):
     def oiter():
         ost["x"], ost["v"], _, _, _ = o.gneb(ost["x"], ost["v"], n_iter=1, k_spring=1.0, climbing=True, dt=kw["dt"])
 
-    rate, calls, el = oracle_rate(oiter, ch.M * ch.N)
+    rate, calls, el = oracle_rate(oiter, ch.M * ch.N, seconds=6.0 if compact else 10.0)
     work = sum(state[k]["iters"] * chains[k].M * chains[k].N for k in state)
     out["cpu_baseline"] = {"value": work / rate, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
                            "sample": "%d FP64 GNEB iterations of the largest chain (%d images x %d spins) in %.1f s; "
                                      "%.3g spin-iterations/s, scaled to the %.3g spin-iterations of the batched run"
                                      % (calls, ch.M, ch.N, el, rate, work)}
-    print(json.dumps(out))
-    return 0
+    if compact:
+        for k in ("images", "sides"):
+            out["config"].pop(k)
+    return out
 
 
 def run_hex_dipole(args):
@@ -946,6 +973,11 @@ def run_unet(args):
 
 
 def run_warmstart(args):
+    print(json.dumps(warmstart_result(args, args.systems)))
+    return 0
+
+
+def warmstart_result(args, systems, compact=False):
     """Learned warm start (BF16 U-Net, 128x128 periodic hexagonal lattices):
     device seconds until every held-out system has FP64 max torque < 1e-6 meV,
     for the unaided FP64 minimiser and for network prediction + FP32 + FP64,
@@ -958,7 +990,7 @@ def run_warmstart(args):
     from paper_1901_11350_gb300 import unet as UN
     from paper_1901_11350_gb300 import warmstart as W
 
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(torch.cuda.current_device())
     build.build()
     params = W.load_params(args.weights)
     L, bm = 128, 64
@@ -980,14 +1012,14 @@ def run_warmstart(args):
     peaks, kind = measured_peaks()
     tf_pred = bm * flops / times["predict"] / 1e12
     tf_train = 3 * bm * flops / times["train_step"] / 1e12
-    rep = W.evaluate(net, I.WARMSTART_SEEDS["heldout"], args.systems, L, max_iter=args.eval_max_iter,
-                     polish_max_iter=5000, chunk=args.systems, per_system=args.per_system, log=lambda m: None)
+    rep = W.evaluate(net, I.WARMSTART_SEEDS["heldout"], systems, L, max_iter=args.eval_max_iter,
+                     polish_max_iter=5000, chunk=systems, per_system=args.per_system, log=lambda m: None)
     warm, una = rep["warm"], rep["unaided"]
     loop = rep["unaided_per_system_loop"]
     out = {"metric": "device seconds to FP64 max torque < 1e-6 meV for all systems, warm start vs unaided FP64",
            "value": warm["batched_seconds"], "unit": "s", "higher_is_better": False,
            "dtype": "bf16 network, f32 then f64 minimiser", "data": "synthetic", "n_gpus": 1,
-           "config": {"workload": "warmstart_hex128", "systems": args.systems, "lattice": [L, L],
+           "config": {"workload": "warmstart_hex128", "systems": systems, "lattice": [L, L],
                       "max_iter": args.eval_max_iter, "params": os.path.basename(args.weights)},
            "unaided_fp64": {"batched_seconds": una["batched_seconds"], "per_system_loop_seconds_est":
                             loop["est_seconds_all"], "per_system_loop_sample": loop},
@@ -999,8 +1031,11 @@ def run_warmstart(args):
                                     "unit": "TFLOP/s", "frac": tf_pred / peaks["bf16_tflops"], "traffic": None,
                                     "peak_kind": kind + " bf16 burst"},
                        "train_tflops": tf_train}}
-    print(json.dumps(out))
-    return 0
+    if compact:
+        out["arms"] = {k: {kk: rep[k][kk] for kk in ("converged", "matched", "mean_iterations", "batched_seconds")
+                           if kk in rep[k]} for k in ("unaided", "batched", "warm", "uniform")}
+        out["unaided_fp64"].pop("per_system_loop_sample")
+    return out
 
 
 def main():
@@ -1041,6 +1076,10 @@ def main():
     ap.add_argument("--gneb-chunk", type=int, default=50)
     ap.add_argument("--gneb-no-reference", action="store_true", help="gneb48: skip the FP64 per-chain loop (profiling aid)")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
+    ap.add_argument("--no-relax", action="store_true",
+                    help="sc128: skip the relaxation half of the metric (GNEB batch, warm start)")
+    ap.add_argument("--relax-systems", type=int, default=64,
+                    help="sc128: held-out systems of the warm-start part of the relaxation half")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -38,6 +38,28 @@
  * Errors: every call returns SP_OK (0) or a negative SP_ERR_* code, and
  * sp_last_error() returns a message for the last failure on that context.
  * Argument errors are detected on the host before anything is launched.
+ *
+ * Device status word (the boundary's error path for what only the device
+ * sees): each context owns a small status word in mapped, pinned host memory
+ * (4 words, allocated by the first call that checks a result).  Every
+ * stream-ordered compute call enqueues, after its own kernels, a check of
+ * what it produced -- the spin state of sp_llg_step, sp_llg_step_replicas
+ * and sp_mc_sweeps, the field of sp_effective_field and sp_gradient, the
+ * values of sp_energy, sp_max_torque, sp_topological_charge and sp_sample,
+ * the image energies and forces of sp_gneb_step and sp_gneb_batch_step (the
+ * first chain's context), the product of sp_hessian_apply -- and a non-finite
+ * value (NaN or infinity; the padding lane of a record is not looked at)
+ * sets a bit in the word.  The word is surfaced as SP_ERR_NAN (SP_ERR_TIMEOUT
+ * for a bounded device-side wait that gave up):
+ *   - by the next compute call on the context that finds it set: that call
+ *     clears the word, launches nothing and returns the error, with the
+ *     kind of result that was bad in sp_last_error.  The host reads the word
+ *     without waiting, so a call issued before the GPU has reached the
+ *     check does not see it yet;
+ *   - deterministically by sp_sync_status(ctx), which waits for the device.
+ * Calls that return host results (sp_minimise, sp_minimise_batch,
+ * sp_gneb_path, sp_lowest_mode, sp_mmf) check those and return SP_ERR_NAN
+ * themselves.  The allocation-free sp_llg_step_static takes no part in it.
  */
 #ifndef SPIRIT_GB_H
 #define SPIRIT_GB_H
@@ -140,6 +162,13 @@ int sp_destroy(sp_ctx *ctx);
 /* Message of the last error on ctx (owned by ctx, valid until the next call
  * on it); a static string for ctx == NULL. */
 const char *sp_last_error(const sp_ctx *ctx);
+
+/* Waits for the context's device (cudaDeviceSynchronize, with that device
+ * current), then reads and clears the context's status word (see the top of
+ * this header): SP_OK, SP_ERR_NAN if an earlier call produced a non-finite
+ * value, SP_ERR_TIMEOUT if a bounded device-side wait gave up, SP_ERR_CUDA
+ * if the synchronisation reported an error. */
+int sp_sync_status(sp_ctx *ctx);
 
 /* Geometry (Sec. "Hamiltonian": arbitrary Bravais vectors and basis cells,
  * open or periodic boundaries per direction).
@@ -449,8 +478,11 @@ int sp_mmf(sp_ctx *ctx, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf
  * 2 * 32 * SP_STATIC_MAX_SPINS bytes (4 MiB) that every GPU loading the
  * library holds until the process exits.
  *
- * Same arguments, same arithmetic and same results as sp_llg_step.  Limits
- * and behaviour:
+ * Same arguments and the same per-spin arithmetic as sp_llg_step's
+ * two-pass launches: bit for bit the result of sp_llg_step whenever that
+ * call takes them too (lattices above 2048 spins, or SP_OPT_SMALL_PATH = 0);
+ * where sp_llg_step takes its small-lattice path instead, the two agree
+ * within the precision's tolerance.  Limits and behaviour:
  *   - N > SP_STATIC_MAX_SPINS: SP_ERR_ARG with a message, nothing launched;
  *   - a Hamiltonian with the dipole term, or the RK4 solver (3 records per
  *     spin): SP_ERR_UNSUPPORTED;
@@ -462,7 +494,9 @@ int sp_mmf(sp_ctx *ctx, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf
  *     array, which keeps the last call's contents (nothing in it needs to
  *     start at zero): calls that overlap on the GPU race and give wrong
  *     results, so serialise them (one stream, or events between streams);
- *   - kernel timing (sp_profile_enable) does not apply to this call. */
+ *   - kernel timing (sp_profile_enable) and the device status word (a
+ *     result check would need the status word's allocation) do not apply
+ *     to this call. */
 #define SP_STATIC_MAX_SPINS 65536
 int sp_llg_step_static(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, void *stream);
 
@@ -509,7 +543,13 @@ enum {
      * replicas (always taken for larger lattices, where it is faster).  Both
      * give the same spins, cones and counts; the observable sums differ in
      * rounding order. */
-    SP_OPT_MC_RESIDENT = 7
+    SP_OPT_MC_RESIDENT = 7,
+    /* read only: device memory the context's own buffers hold, in KiB rounded
+     * up -- the LLG predictor scratch, reduction partials, dipole field,
+     * path-analysis charges, replica noise amplitudes and step counter (not
+     * the dipole plan, minimiser, Monte Carlo or Hessian workspaces).  0 on a
+     * context that has allocated none of them */
+    SP_OPT_SCRATCH_KIB = 8
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose the work per CTA of the 27-point path by measurement, for each pass

@@ -81,6 +81,7 @@ SIGNATURES = {
     "sp_create": (_i, [C.POINTER(_vp), _i]),
     "sp_destroy": (_i, [_vp]),
     "sp_last_error": (C.c_char_p, [_vp]),
+    "sp_sync_status": (_i, [_vp]),
     "sp_set_geometry": (_i, [_vp, C.POINTER(_d), _i, C.POINTER(_d), C.POINTER(_i), C.POINTER(_i), _d, C.POINTER(_d)]),
     "sp_set_hamiltonian": (_i, [_vp, C.POINTER(Hamiltonian)]),
     "sp_n_spins": (_i, [_vp, C.POINTER(_i)]),
@@ -131,7 +132,7 @@ SIGNATURES = {
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
 OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4, "small_path": 5,
-           "planes_per_cta_corr": 6, "mc_resident": 7}
+           "planes_per_cta_corr": 6, "mc_resident": 7, "scratch_kib": 8}
 
 
 def library_path():
@@ -221,6 +222,12 @@ class Context:
     def _check(self, rc):
         if rc:
             raise SpinError(rc, lib().sp_last_error(self._h).decode())
+
+    def sync_status(self):
+        """Wait for the device and return (code, message) of the context's
+        status word, cleared (code 0 when nothing was flagged)."""
+        rc = lib().sp_sync_status(self._h)
+        return rc, (lib().sp_last_error(self._h).decode() if rc else "")
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -290,6 +290,13 @@ int ready(sp_ctx *c)
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// A compute call on a configured context: surfaces a pending status first.
+int enter(sp_ctx *c)
+{
+    int rc = ready(c);
+    return rc ? rc : status_enter(c);
+}
+
 int check_spins(sp_ctx *c, const void *p, const char *what)
 {
     if (!p) return fail(c, SP_ERR_ARG, "%s is NULL", what);
@@ -628,6 +635,70 @@ template <typename T> int autotune_run(sp_ctx *c, const void *n, int *chosen, cu
 
 }  // namespace
 
+// ===================================================================== status word
+unsigned *status_word(sp_ctx *c)
+{
+    if (c->status_d) return c->status_d;
+    void *h = nullptr, *d = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, 4 * sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        std::memset(h, 0, 4 * sizeof(unsigned));
+        e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) cudaFreeHost(h);
+    }
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "status word allocation");
+        return nullptr;
+    }
+    c->status_h = (unsigned *)h;
+    c->status_d = (unsigned *)d;
+    return c->status_d;
+}
+
+namespace {
+std::string site_names(unsigned bits)
+{
+    static const char *names[] = {"spin state", "effective field", "energy or torque", "GNEB energies or forces",
+                                  "observables", "Hessian product"};
+    std::string s;
+    for (int k = 0; k < 6; ++k)
+        if (bits & (1u << k)) s += std::string(s.empty() ? "" : ", ") + names[k];
+    return s.empty() ? std::string("unknown") : s;
+}
+
+// Read and clear the status word; the error it stands for (SP_OK if clear).
+int status_take(sp_ctx *c)
+{
+    if (!c->status_h) return SP_OK;
+    volatile unsigned *w = c->status_h;
+    unsigned nan = w[0], tmo = w[1];
+    if (!nan && !tmo) return SP_OK;
+    w[0] = 0;
+    w[1] = 0;
+    if (tmo) return fail(c, SP_ERR_TIMEOUT, "a bounded device-side wait gave up (sites 0x%x)", tmo);
+    return fail(c, SP_ERR_NAN, "a non-finite value was detected in the %s of an earlier call", site_names(nan).c_str());
+}
+}  // namespace
+
+int status_enter(sp_ctx *c) { return status_take(c); }
+
+int status_check_records(sp_ctx *c, const void *recs, long n_rec, unsigned site, cudaStream_t st)
+{
+    unsigned *w = status_word(c);
+    if (!w) return SP_ERR_CUDA;
+    cudaError_t e = c->prec == SP_F64 ? launch_check_records<double>((const dq4 *)recs, n_rec, w, site, st)
+                                      : launch_check_records<float>((const float4 *)recs, n_rec, w, site, st);
+    return e == cudaSuccess ? SP_OK : cuda_fail(c, e, "finiteness check launch");
+}
+
+int status_check_doubles(sp_ctx *c, const double *v, long n_val, unsigned site, cudaStream_t st)
+{
+    unsigned *w = status_word(c);
+    if (!w) return SP_ERR_CUDA;
+    cudaError_t e = launch_check_doubles(v, n_val, w, site, st);
+    return e == cudaSuccess ? SP_OK : cuda_fail(c, e, "finiteness check launch");
+}
+
 // ===================================================================== C ABI
 extern "C" {
 
@@ -655,6 +726,7 @@ int sp_destroy(sp_ctx *c)
     if (c->qbuf.p) cudaFree(c->qbuf.p);
     if (c->rsig.p) cudaFree(c->rsig.p);
     if (c->step_ctr.p) cudaFree(c->step_ctr.p);
+    if (c->status_h) cudaFreeHost(c->status_h);
     for (auto &g : c->lg_graphs) cudaGraphExecDestroy(g.exec);
     if (c->lg_stream) cudaStreamDestroy(c->lg_stream);
     mc_scratch_destroy(c->mc);
@@ -767,7 +839,7 @@ int sp_n_spins(const sp_ctx *c, int *n)
 
 static int field_common(sp_ctx *c, const void *n, void *out, double sign, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, n, "spins")) || (rc = check_spins(c, out, "output"))) return rc;
     if (n == out) return fail(c, SP_ERR_ARG, "input and output must not overlap");
@@ -778,7 +850,7 @@ static int field_common(sp_ctx *c, const void *n, void *out, double sign, void *
                         ? launch_field<double>(c->Sd, (const dq4 *)n, (const dq4 *)bd, (dq4 *)out, sign, st)
                         : launch_field<float>(c->Sf, (const float4 *)n, (const float4 *)bd, (float4 *)out, (float)sign, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "field launch");
-    return SP_OK;
+    return status_check_records(c, out, c->N, SITE_FIELD, st);
 }
 
 int sp_effective_field(sp_ctx *c, const void *n_dev, void *B_dev, void *stream)
@@ -793,7 +865,7 @@ int sp_gradient(sp_ctx *c, const void *n_dev, void *grad_dev, void *stream)
 
 static int energy_common(sp_ctx *c, const void *n, double *e_out, double *t_out, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, n, "spins"))) return rc;
     if (!e_out && !t_out) return fail(c, SP_ERR_ARG, "NULL output");
@@ -805,7 +877,7 @@ static int energy_common(sp_ctx *c, const void *n, double *e_out, double *t_out,
                         ? launch_energy<double>(c->Sd, (const dq4 *)n, (const dq4 *)bd, (double *)c->partials.p, e_out, t_out, st)
                         : launch_energy<float>(c->Sf, (const float4 *)n, (const float4 *)bd, (double *)c->partials.p, e_out, t_out, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "energy launch");
-    return SP_OK;
+    return e_out ? status_check_doubles(c, e_out, 6, SITE_ENERGY, st) : status_check_doubles(c, t_out, 1, SITE_ENERGY, st);
 }
 
 int sp_energy(sp_ctx *c, const void *n_dev, double *e_dev, void *stream)
@@ -822,7 +894,7 @@ int sp_max_torque(sp_ctx *c, const void *n_dev, double *torque_dev, void *stream
 
 int sp_llg_step(sp_ctx *c, void *n_dev, const sp_llg_params *p, int n_steps, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, n_dev, "spins"))) return rc;
     if (!p) return fail(c, SP_ERR_ARG, "NULL parameters");
@@ -833,13 +905,14 @@ int sp_llg_step(sp_ctx *c, void *n_dev, const sp_llg_params *p, int n_steps, voi
     if (n_steps < 0) return fail(c, SP_ERR_ARG, "n_steps must be >= 0");
     if (n_steps == 0 || c->N == 0) return SP_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    return c->prec == SP_F64 ? llg_run<double>(c, n_dev, p, n_steps, st) : llg_run<float>(c, n_dev, p, n_steps, st);
+    rc = c->prec == SP_F64 ? llg_run<double>(c, n_dev, p, n_steps, st) : llg_run<float>(c, n_dev, p, n_steps, st);
+    return rc ? rc : status_check_records(c, n_dev, c->N, SITE_STATE, st);
 }
 
 int sp_llg_step_replicas(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const sp_llg_params *p, int n_steps,
                          void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, spins_dev, "spins"))) return rc;
     if (!p || !T) return fail(c, SP_ERR_ARG, "NULL parameters or temperatures");
@@ -859,17 +932,19 @@ int sp_llg_step_replicas(sp_ctx *c, void *spins_dev, int n_rep, const double *T,
     if (n_rep == 1) {  // one replica is a plain call at its own temperature
         sp_llg_params one = *p;
         one.T = T[0];
-        return c->prec == SP_F64 ? llg_run<double>(c, spins_dev, &one, n_steps, st)
-                                 : llg_run<float>(c, spins_dev, &one, n_steps, st);
+        rc = c->prec == SP_F64 ? llg_run<double>(c, spins_dev, &one, n_steps, st)
+                               : llg_run<float>(c, spins_dev, &one, n_steps, st);
+    } else {
+        rc = c->prec == SP_F64 ? replicas_run<double>(c, spins_dev, p, n_steps, st, n_rep, T)
+                               : replicas_run<float>(c, spins_dev, p, n_steps, st, n_rep, T);
     }
-    return c->prec == SP_F64 ? replicas_run<double>(c, spins_dev, p, n_steps, st, n_rep, T)
-                             : replicas_run<float>(c, spins_dev, p, n_steps, st, n_rep, T);
+    return rc ? rc : status_check_records(c, spins_dev, (long)n_rep * c->N, SITE_STATE, st);
 }
 
 int sp_minimise(sp_ctx *c, void *n_dev, void *v_dev, double dt, double mass, double tol, int max_iter, int check_every,
                 int *iters, double *max_torque, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, n_dev, "spins")) || (rc = check_spins(c, v_dev, "velocities"))) return rc;
     if (n_dev == v_dev) return fail(c, SP_ERR_ARG, "spins and velocities must not overlap");
@@ -886,13 +961,14 @@ int sp_minimise(sp_ctx *c, void *n_dev, void *v_dev, double dt, double mass, dou
     if (e) return fail(c, e, "minimisation failed (%s)", e == SP_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "");
     if (iters) *iters = it;
     if (max_torque) *max_torque = mt;
+    if (!std::isfinite(mt)) return fail(c, SP_ERR_NAN, "minimisation: the max torque is not finite");
     return SP_OK;
 }
 
 int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const sp_gneb_params *p, int n_iter,
                  double *energies_dev, double *max_force_dev, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, chain_dev, "chain")) || (rc = check_spins(c, vel_dev, "velocities"))) return rc;
     if (!p) return fail(c, SP_ERR_ARG, "NULL parameters");
@@ -912,13 +988,14 @@ int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const 
                 ? gneb_run<double>(&c->mins, c->Sd, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream)
                 : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
     if (e) return fail(c, e, "GNEB failed");
-    return SP_OK;
+    if ((rc = status_check_doubles(c, energies_dev, n_images, SITE_RELAX, (cudaStream_t)stream))) return rc;
+    return status_check_doubles(c, max_force_dev, 1, SITE_RELAX, (cudaStream_t)stream);
 }
 
 int sp_gneb_path(sp_ctx *c, const void *chain_dev, int n_images, int n_interp, double *r, double *E, double *slope,
                  double *Q, double *r_interp, double *E_interp, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, chain_dev, "chain"))) return rc;
     if (n_images < 2) return fail(c, SP_ERR_ARG, "a chain needs at least 2 images");
@@ -958,13 +1035,18 @@ int sp_gneb_path(sp_ctx *c, const void *chain_dev, int n_images, int n_interp, d
         cudaError_t ce = cudaMemcpyAsync(Q, c->qbuf.p, sizeof(double) * n_images, cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "topological charge copy");
+        for (int v = 0; v < n_images; ++v)
+            if (!std::isfinite(Q[v])) return fail(c, SP_ERR_NAN, "path analysis: image %d has a non-finite charge", v);
     }
+    for (int v = 0; v < n_images; ++v)
+        if (!std::isfinite(E[v]) || !std::isfinite(r[v]) || !std::isfinite(slope[v]))
+            return fail(c, SP_ERR_NAN, "path analysis: image %d has a non-finite energy, distance or slope", v);
     return SP_OK;
 }
 
 int sp_topological_charge(sp_ctx *c, const void *n_dev, double *Q_dev, void *stream)
 {
-    int rc = ready(c);
+    int rc = enter(c);
     if (rc) return rc;
     if ((rc = check_spins(c, n_dev, "spins"))) return rc;
     if (!Q_dev) return fail(c, SP_ERR_ARG, "NULL output");
@@ -976,7 +1058,7 @@ int sp_topological_charge(sp_ctx *c, const void *n_dev, double *Q_dev, void *str
                         ? launch_topo<double>(c->Sd, (const dq4 *)n_dev, cz < 0, (double *)c->partials.p, Q_dev, st)
                         : launch_topo<float>(c->Sf, (const float4 *)n_dev, cz < 0, (double *)c->partials.p, Q_dev, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "topological charge launch");
-    return SP_OK;
+    return status_check_doubles(c, Q_dev, 1, SITE_SAMPLE, st);
 }
 
 int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel_dev, const long long *offsets,
@@ -986,7 +1068,8 @@ int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel
     if (!ctxs || n_sys < 1 || !ctxs[0]) return SP_ERR_ARG;
     sp_ctx *c0 = ctxs[0];
     if (!offsets || !iters || !max_torque) return fail(c0, SP_ERR_ARG, "NULL batch argument");
-    int rc;
+    int rc = status_enter(c0);
+    if (rc) return rc;
     if ((rc = check_spins(c0, spins_dev, "spins")) || (rc = check_spins(c0, vel_dev, "velocities"))) return rc;
     if (spins_dev == vel_dev) return fail(c0, SP_ERR_ARG, "spins and velocities must not overlap");
     if (!(dt > 0) || !(mass > 0) || !(tol >= 0) || max_iter < 0 || check_every < 1)
@@ -1018,6 +1101,9 @@ int sp_minimise_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, void *vel
         e = vp_batch_run<float>(&c0->mins, S, off, spins_dev, vel_dev, a, iters, max_torque, (cudaStream_t)stream);
     }
     if (e) return fail(c0, e, "batched minimisation failed");
+    for (int k = 0; k < n_sys; ++k)
+        if (!std::isfinite(max_torque[k]))
+            return fail(c0, SP_ERR_NAN, "batched minimisation: system %d has a non-finite max torque", k);
     return SP_OK;
 }
 
@@ -1029,7 +1115,8 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
     sp_ctx *c0 = ctxs[0];
     if (!offsets || !n_images || !p) return fail(c0, SP_ERR_ARG, "NULL batch description");
     if (!energies_dev || !max_force_dev) return fail(c0, SP_ERR_ARG, "NULL output");
-    int rc;
+    int rc = status_enter(c0);
+    if (rc) return rc;
     if ((rc = check_spins(c0, chains_dev, "chains")) || (rc = check_spins(c0, vel_dev, "velocities"))) return rc;
     if (n_iter < 0 || !(p->dt > 0) || !(p->mass > 0)) return fail(c0, SP_ERR_ARG, "bad iteration parameters");
     struct Span {
@@ -1078,7 +1165,22 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
                                   (cudaStream_t)stream);
     }
     if (e) return fail(c0, e, "batched GNEB failed");
-    return SP_OK;
+    long long tot = 0;
+    for (int k = 0; k < n_chains; ++k) tot += n_images[k];
+    if ((rc = status_check_doubles(c0, energies_dev, (long)tot, SITE_RELAX, (cudaStream_t)stream))) return rc;
+    return status_check_doubles(c0, max_force_dev, n_chains, SITE_RELAX, (cudaStream_t)stream);
+}
+
+int sp_sync_status(sp_ctx *c)
+{
+    if (!c) return SP_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev != c->device) e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (dev != c->device) cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device synchronisation");
+    return status_take(c);
 }
 
 int sp_set_option(sp_ctx *c, int option, int value)
@@ -1152,6 +1254,11 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
     case SP_OPT_MC_RESIDENT:
         *value = c->use_mc_resident ? 1 : 0;
         return SP_OK;
+    case SP_OPT_SCRATCH_KIB: {
+        size_t b = c->pred.bytes + c->partials.bytes + c->bdd.bytes + c->qbuf.bytes + c->rsig.bytes + c->step_ctr.bytes;
+        *value = (int)std::min<size_t>((b + 1023) / 1024, 0x7fffffff);
+        return SP_OK;
+    }
     default:
         return SP_ERR_ARG;
     }

@@ -50,6 +50,10 @@ template <typename T> __device__ __forceinline__ v3<T> axpy(T s, v3<T> a, v3<T> 
 {
     return {fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z)};
 }
+// Maximum that keeps a NaN (fmax drops it): reductions of max torque and
+// max force must carry a non-finite value through to the status check.
+template <typename T> __device__ __forceinline__ T nan_max(T a, T b) { return (a > b || a != a) ? a : b; }
+
 __device__ __forceinline__ float rnorm(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rnorm(double x) { return rsqrt(x); }
 template <typename T> __device__ __forceinline__ v3<T> normalised(v3<T> a)
@@ -142,6 +146,7 @@ __device__ __forceinline__ f2sum operator+(f2sum a, f2sum b)
     return {hi, lo - (hi - s.hi)};
 }
 __device__ __forceinline__ bool operator>(f2sum a, f2sum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ f2sum nan_max(f2sum a, f2sum b) { return (a > b || a.hi != a.hi) ? a : b; }
 __device__ __forceinline__ f2sum exact_square(float a) { return {a * a, fmaf(a, a, -(a * a))}; }
 __device__ __forceinline__ f2sum exact_dot(v3<float> a, v3<float> b)
 {

@@ -131,12 +131,36 @@ struct sp_ctx {
     DevBuf step_ctr;               // Philox step base of replayed replica graphs
     std::vector<LlgGraph> lg_graphs;
     cudaStream_t lg_stream = nullptr;  // capture stream of those graphs
+    // device status word (mapped pinned host memory, allocated on first use;
+    // status_d is its device address): word 0 collects the SITE_* bits of
+    // non-finite results, word 1 those of bounded waits that gave up
+    unsigned *status_h = nullptr, *status_d = nullptr;
     DipolePlan *dip = nullptr;
     MinScratch *mins = nullptr;
     McScratch *mc = nullptr;
     HessScratch *hess = nullptr;
     Profiler prof;
 };
+
+// Where a non-finite value was seen (bits of status word 0).
+enum {
+    SITE_STATE = 1,    // spins after LLG steps or Monte Carlo sweeps
+    SITE_FIELD = 2,    // effective field or gradient
+    SITE_ENERGY = 4,   // energies or max torque
+    SITE_RELAX = 8,    // GNEB image energies or forces
+    SITE_SAMPLE = 16,  // sampled observables or topological charge
+    SITE_HESSIAN = 32  // Hessian-vector product
+};
+// Device address of ctx's status word (allocated on first use), or null
+// with an error set on ctx.
+unsigned *status_word(sp_ctx *c);
+// SP_OK, or the error a pending status word stands for (the word is read
+// without waiting for the device and cleared).
+int status_enter(sp_ctx *c);
+// Enqueue the finiteness check of n_rec records (spins, fields) or n_val
+// doubles (energies, forces) on st.
+int status_check_records(sp_ctx *c, const void *recs, long n_rec, unsigned site, cudaStream_t st);
+int status_check_doubles(sp_ctx *c, const double *v, long n_val, unsigned site, cudaStream_t st);
 
 // Units per CTA of the 27-point path for a batch of n_rep replicas: the
 // user's choice, or all replicas' units spread over one wave of resident CTAs.

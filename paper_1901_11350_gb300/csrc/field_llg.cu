@@ -14,6 +14,8 @@
 // way: h_i = A_i/2 + A(np_i, Bth_i)/2 and n_i <- R(h_i + A(np_i, B_i(np))/2) n_i.
 // Memory per step: read n, write np and q; read np (stencil) and q (and n
 // for Depondt), write n -- 6 (7) records per spin.
+#include <algorithm>
+
 #include "internal.h"
 
 // 1: the per-spin LLG passes are launched with programmatic dependent launch
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
     __shared__ double sh[kBlock / 32][7];
     for (int k = 0; k < 6; ++k)
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-    for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_down_sync(0xffffffffu, tmax, o));
+    for (int o = 16; o > 0; o >>= 1) tmax = nan_max(tmax, __shfl_down_sync(0xffffffffu, tmax, o));
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
         for (int k = 0; k < 6; ++k) sh[w][k] = acc[k];
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_energy(const __grid_constant__ Stenc
     if (threadIdx.x < 7) {
         int k = threadIdx.x;
         double v = sh[0][k];
-        for (int ww = 1; ww < kBlock / 32; ++ww) v = (k == 6) ? fmax(v, sh[ww][k]) : v + sh[ww][k];
+        for (int ww = 1; ww < kBlock / 32; ++ww) v = (k == 6) ? nan_max(v, sh[ww][k]) : v + sh[ww][k];
         partials[8 * blockIdx.x + k] = v;
     }
 }
@@ -345,14 +347,14 @@ __global__ void __launch_bounds__(kBlock) k_energy_final(const double *__restric
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int p = threadIdx.x; p < nblk; p += kBlock) {
         for (int k = 0; k < 6; ++k) acc[k] += partials[8 * p + k];
-        acc[6] = fmax(acc[6], partials[8 * p + 6]);
+        acc[6] = nan_max(acc[6], partials[8 * p + 6]);
     }
     for (int k = 0; k < 7; ++k) sh[threadIdx.x][k] = acc[k];
     __syncthreads();
     for (int s = kBlock / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)
             for (int k = 0; k < 7; ++k)
-                sh[threadIdx.x][k] = (k == 6) ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                sh[threadIdx.x][k] = (k == 6) ? nan_max(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
                                               : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
         __syncthreads();
     }
@@ -373,6 +375,54 @@ cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T>
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- status
+// One wave of blocks strides over the values; a block that saw a non-finite
+// one ORs its site bit into the status word (system scope: the word lives in
+// mapped host memory that the host reads between calls).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_check_records(const rec_t<T> *__restrict__ n, long n_rec,
+                                                          unsigned *flag, unsigned site)
+{
+    int bad = 0;
+    for (long i = (long)blockIdx.x * kBlock + threadIdx.x; i < n_rec; i += (long)gridDim.x * kBlock) {
+        v3<T> v = ld(n, i);
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr_system(flag, site);
+}
+
+__global__ void __launch_bounds__(kBlock) k_check_doubles(const double *__restrict__ v, long n_val, unsigned *flag,
+                                                          unsigned site)
+{
+    int bad = 0;
+    for (long i = (long)blockIdx.x * kBlock + threadIdx.x; i < n_val; i += (long)gridDim.x * kBlock)
+        bad |= !isfinite(v[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr_system(flag, site);
+}
+
+namespace {
+int check_grid(long n)
+{
+    long b = (n + kBlock - 1) / kBlock;
+    return (int)std::max(1L, std::min(b, 152L * 4));
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_check_records(const rec_t<T> *n, long n_rec, unsigned *flag, unsigned site, cudaStream_t st)
+{
+    if (n_rec <= 0) return cudaSuccess;
+    k_check_records<T><<<check_grid(n_rec), kBlock, 0, st>>>(n, n_rec, flag, site);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_doubles(const double *v, long n_val, unsigned *flag, unsigned site, cudaStream_t st)
+{
+    if (n_val <= 0) return cudaSuccess;
+    k_check_doubles<<<check_grid(n_val), kBlock, 0, st>>>(v, n_val, flag, site);
+    return cudaGetLastError();
+}
+
 #define SPGB_INST(T)                                                                                                   \
     template cudaError_t launch_field<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, rec_t<T> *, T,         \
                                          cudaStream_t);                                                                \
@@ -383,7 +433,8 @@ cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T>
     template cudaError_t launch_rk4_stage<T>(int, const Stencil<T> &, rec_t<T> *, const rec_t<T> *, rec_t<T> *,        \
                                              rec_t<T> *, const rec_t<T> *, const LlgConst<T> &, cudaStream_t);         \
     template cudaError_t launch_energy<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, double *, double *,   \
-                                          double *, cudaStream_t);
+                                          double *, cudaStream_t);                                            \
+    template cudaError_t launch_check_records<T>(const rec_t<T> *, long, unsigned *, unsigned, cudaStream_t);
 SPGB_INST(float)
 SPGB_INST(double)
 

@@ -436,7 +436,7 @@ int hcheck(sp_ctx *c)
     if (!c) return SP_ERR_ARG;
     if (!c->have_geom || !c->have_ham) return hfail(c, SP_ERR_STATE, "context not configured");
     if (c->h.dipole != SP_DIPOLE_NONE) return hfail(c, SP_ERR_UNSUPPORTED, "Hessian with the dipole term");
-    return SP_OK;
+    return status_enter(c);
 }
 
 // Device record arrays start on a record boundary (16 B in FP32, 32 B in FP64).
@@ -474,7 +474,8 @@ int sp_hessian_apply(sp_ctx *c, const void *n_dev, const void *v_dev, void *out_
                                                    (const dq4 *)v_dev, (dq4 *)out_dev)
                                       : launch_pdl(k_hvp<float>, dim3(nb), dim3(kHB), 0, st, c->Sf,
                                                    (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev);
-    return e == cudaSuccess ? SP_OK : hfail(c, SP_ERR_CUDA, "Hessian launch failed");
+    if (e != cudaSuccess) return hfail(c, SP_ERR_CUDA, "Hessian launch failed");
+    return status_check_records(c, out_dev, c->N, SITE_HESSIAN, st);
 }
 
 int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, double *lambda, void *stream)
@@ -487,7 +488,8 @@ int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, dou
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? lowest_mode_run<double>(c, c->Sd, n_dev, mode_dev, krylov, lambda, st)
                            : lowest_mode_run<float>(c, c->Sf, n_dev, mode_dev, krylov, lambda, st);
-    return rc ? hfail(c, rc, "Lanczos failed") : SP_OK;
+    if (rc) return hfail(c, rc, "Lanczos failed");
+    return std::isfinite(*lambda) ? SP_OK : hfail(c, SP_ERR_NAN, "lowest mode: the eigenvalue is not finite");
 }
 
 int sp_mmf(sp_ctx *c, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf_params *p, int n_iter,
@@ -502,7 +504,10 @@ int sp_mmf(sp_ctx *c, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf_p
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? mmf_run<double>(c, c->Sd, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st)
                            : mmf_run<float>(c, c->Sf, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st);
-    return rc ? hfail(c, rc, "minimum mode following failed") : SP_OK;
+    if (rc) return hfail(c, rc, "minimum mode following failed");
+    return std::isfinite(*max_force) && std::isfinite(*lambda)
+               ? SP_OK
+               : hfail(c, SP_ERR_NAN, "minimum mode following: the force or eigenvalue is not finite");
 }
 
 }  // extern "C"

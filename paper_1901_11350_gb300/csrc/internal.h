@@ -101,6 +101,13 @@ template <typename T>
 cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, double *partials, double *e_out,
                           double *torque_out, cudaStream_t st);
 
+// Finiteness check of results (the device status word): records n[0..n_rec)
+// (x, y, z; the padding lane is not looked at) or plain doubles v[0..n_val);
+// any non-finite value ORs `site` into *flag, a word of mapped host memory.
+template <typename T>
+cudaError_t launch_check_records(const rec_t<T> *n, long n_rec, unsigned *flag, unsigned site, cudaStream_t st);
+cudaError_t launch_check_doubles(const double *v, long n_val, unsigned *flag, unsigned site, cudaStream_t st);
+
 // Topological charge of a 2D one-atom lattice; flip swaps the triangle
 // orientation (for left-handed in-plane lattice vectors); partials needs
 // blocks_for(n0 * n1) doubles.

@@ -885,6 +885,7 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
     for (int r = 0; r < n_rep; ++r)
         if (!(T[r] >= 0)) return mfail(c, SP_ERR_ARG, "temperatures must be >= 0");
     if (c->h.dipole != SP_DIPOLE_NONE) return mfail(c, SP_ERR_UNSUPPORTED, "Monte Carlo with the dipole term");
+    if (int rc = status_enter(c)) return rc;
     int e = c->prec == SP_F64
                 ? mc_dispatch<double>(c, c->Sd, spins_dev, n_rep, T, p, n_sweeps, cone_dev, stats_dev,
                                       (cudaStream_t)stream)
@@ -894,7 +895,7 @@ int sp_mc_sweeps(sp_ctx *c, void *spins_dev, int n_rep, const double *T, const s
         return mfail(c, e, "lattice has no colouring (neither (c0 + c1 + c2) mod k nor the product colouring "
                            "applies)");
     if (e) return mfail(c, e, "Monte Carlo launch failed");
-    return SP_OK;
+    return status_check_records(c, spins_dev, (long)n_rep * c->N, SITE_STATE, (cudaStream_t)stream);
 }
 
 int sp_sample(sp_ctx *c, const void *spins_dev, int n_rep, double *stats_dev, void *stream)
@@ -907,10 +908,11 @@ int sp_sample(sp_ctx *c, const void *spins_dev, int n_rep, double *stats_dev, vo
     if ((long long)n_rep * c->N >= (1LL << 31)) return mfail(c, SP_ERR_ARG, "more than 2^31 spins");
     if (c->h.dipole != SP_DIPOLE_NONE) return mfail(c, SP_ERR_UNSUPPORTED, "observables with the dipole term");
     if (c->N == 0) return SP_OK;
+    if (int rc = status_enter(c)) return rc;
     int e = c->prec == SP_F64 ? sample_run<double>(c, c->Sd, spins_dev, n_rep, stats_dev, (cudaStream_t)stream)
                               : sample_run<float>(c, c->Sf, spins_dev, n_rep, stats_dev, (cudaStream_t)stream);
     if (e) return mfail(c, e, "observable sampling launch failed");
-    return SP_OK;
+    return status_check_doubles(c, stats_dev, 8L * n_rep, SITE_SAMPLE, (cudaStream_t)stream);
 }
 
 }  // extern "C"

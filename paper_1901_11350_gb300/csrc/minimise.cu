@@ -126,7 +126,7 @@ __device__ __forceinline__ double acc_dot(v3<double> a, v3<double> b) { return d
 template <int NV, typename V>
 __device__ __forceinline__ V combine(int k, unsigned maxmask, V a, V b)
 {
-    return ((maxmask >> k) & 1u) ? (a > b ? a : b) : a + b;
+    return ((maxmask >> k) & 1u) ? nan_max(a, b) : a + b;
 }
 
 struct NoPost {
@@ -541,7 +541,7 @@ __global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const dou
     for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
         double m = 0;
         for (int g = 0; g < n_img; ++g)
-            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = fmax(m, scal[kS * g + kFMAX]);
+            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = nan_max(m, scal[kS * g + kFMAX]);
         fmax_out[c] = sqrt(m);  // the slot holds max |F|^2
     }
 }
