@@ -466,6 +466,59 @@ int sp_mmf(sp_ctx *ctx, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf
            double *max_force, double *lambda, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Harmonic transition-state theory (Sec. "Harmonic Transition-State Theory",
+ * appendix on the curved manifold).  SP_F64 contexts without the dipole term,
+ * 1..SP_HTST_MAX_SPINS spins; SP_ERR_UNSUPPORTED for SP_F32 or the dipole
+ * term, SP_ERR_ARG for larger lattices or NULL/misaligned pointers.
+ * ------------------------------------------------------------------------ */
+#define SP_HTST_MAX_SPINS 2048
+
+/* All 2N eigenvalues of the covariant Hessian at n_dev (the operator of
+ * sp_hessian_apply in the 2N-dimensional tangent space), ascending, into the
+ * HOST array eig[2N].  Lanczos over the whole tangent space with classical
+ * Gram-Schmidt reorthogonalisation done twice against every stored vector,
+ * restarted from a new pseudo-random tangent field where the Krylov space
+ * closes (so degenerate eigenvalues appear with their multiplicity), then
+ * bisection on Sturm counts of the resulting tridiagonal matrix.  Device
+ * scratch: (2N + 1) N records of 32 B and small buffers (268 MB at 2048
+ * spins), kept by the context.  Synchronises `stream`. */
+int sp_hessian_spectrum(sp_ctx *ctx, const void *n_dev, double *eig, void *stream);
+
+typedef struct {
+    double zero_tol;  /* eigenvalues with |lambda| <= zero_tol (meV) count as zero modes (>= 0) */
+    double V_min;     /* phase-space volume of the zero modes at the minimum (1 without any) */
+    double V_sad;     /* the same at the saddle point */
+} sp_htst_params;
+
+typedef struct {
+    double E_min, E_sad, dE;          /* energies (meV, FP64 sums) and barrier dE = E_sad - E_min */
+    double log_det_min, log_det_sad;  /* sum of ln(lambda) over the eigenvalues above zero_tol */
+    double omega0;                    /* Omega_0 = sqrt(prod' lambda^M / prod' lambda^S) */
+    double v;                         /* sqrt(sum' a_i^2 / lambda^S_i), a_i the dynamical
+                                         matrix's unstable-mode row in the eigenbasis */
+    double lambda_unstable;           /* lowest eigenvalue at the saddle point (meV) */
+    double prefactor;                 /* v / (2 pi) Omega_0 V_sad / V_min */
+    int n_zero_min, n_zero_sad;       /* zero modes N0^M, N0^S */
+    int n_neg_min, n_neg_sad;         /* eigenvalues below -zero_tol (0 and 1 for a minimum
+                                         and a first-order saddle) */
+} sp_htst_result;
+
+/* HTST rate prefactor of the transition from the minimum n_min_dev over the
+ * first-order saddle point n_sad_dev (N records each, device):
+ *   Gamma = prefactor (2 pi kB T)^((N0^M - N0^S)/2) exp(-dE / kB T),
+ * prefactor = v / (2 pi) Omega_0 V^S / V^M (1/ps when both states have the
+ * same number of zero modes).  Omega_0 from the two spectra of
+ * sp_hessian_spectrum.  v from the linearised precession without damping,
+ * d(dn_i)/dt = (gamma / mu_i) n_i x (H dn)_i (gamma = 0.176085963023
+ * rad/(ps T), mu_i = mu_s mu_B): with e_1 the saddle's unstable eigenvector
+ * (Ritz vector of the lowest eigenvalue) and u_i = (gamma / mu_i) n_i x e_1,i,
+ * v^2 = u . H u at the saddle, which equals sum' a_i^2 / lambda_i up to the
+ * zero modes' share (|lambda| <= zero_tol; at most zero_tol |u|^2).  Result
+ * in *out (host).  Synchronises `stream`. */
+int sp_htst(sp_ctx *ctx, const void *n_min_dev, const void *n_sad_dev, const sp_htst_params *p, sp_htst_result *out,
+            void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free LLG stepping
  * ------------------------------------------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

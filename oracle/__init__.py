@@ -116,6 +116,7 @@ def lib():
         L.spo_hessian_apply.argtypes = [C.c_void_p, d, d, d]
         L.spo_hessian_dense.argtypes = [C.c_void_p, d, d, d]
         L.spo_mc.argtypes = [C.c_void_p, d, C.c_int, d, P(_MC), C.c_int, d, d]
+        L.spo_mc_coloured.argtypes = [C.c_void_p, d, C.c_int, d, P(_MC), C.c_int, d, d]
         L.spo_mc_colours.argtypes = [C.c_void_p]
         L.spo_segment_length.argtypes = [C.c_double] * 6
         L.spo_segment_length.restype = C.c_double
@@ -174,6 +175,7 @@ class System:
         _check(L.spo_set_geometry(self._h, _dp(brav), nb, _dp(basis.reshape(-1)), nc, per,
                                   float(g.get("lattice_constant", 1.0)), _dp(mu)), "set_geometry")
         self.n_basis = nb
+        self.mu_s = mu.copy()
         self.N = L.spo_n_spins(self._h)
         h = hamiltonian
         H = _Ham()
@@ -346,6 +348,59 @@ class System:
         mode = np.einsum("ikc,ic->ik", T, V[:, 0].reshape(-1, 2))
         return w[0], mode / np.linalg.norm(mode)
 
+    def hessian_eigen(self, n):
+        """All 2N eigenvalues (ascending) and eigenvectors (columns, in the
+        tangent basis T) of the covariant Hessian at n, by dense
+        eigen-decomposition."""
+        H, T = self.hessian_dense(n)
+        lam, vec = np.linalg.eigh(0.5 * (H + H.T))
+        return lam, vec, T
+
+    def htst(self, n_min, n_sad, zero_tol=1e-6, V_min=1.0, V_sad=1.0):
+        """Harmonic transition-state theory rate prefactor (Sec. HTST) of the
+        transition from the minimum n_min over the first-order saddle n_sad:
+        Gamma = v/(2 pi) Omega_0 exp(-dE/kB T), with
+          Omega_0 = sqrt(prod' lambda^M / prod' lambda^S)   (eigenvalues above zero_tol),
+          v = (2 pi kB T)^((N0^M - N0^S)/2) V^S/V^M sqrt(sum'_i a_i^2 / lambda^S_i),
+        a_i the first row (the unstable mode's) of the dynamical matrix in the
+        Hessian's eigenbasis, V|2N = Lambda^T T^T V|3N T Lambda.  The dynamical
+        matrix is the linearisation at the saddle of the precession without
+        damping, dn_i/dt = (gamma/mu_i) n_i x grad_i H, i.e. V|3N = G H|3N with
+        G_ii = (gamma/mu_i) [n_i]_x; in the eigenbasis its first row is
+        (Lambda^T T^T G T Lambda)_1k lambda_k.  Returns a dict with the fields
+        of the C result (prefactor = v/(2 pi) Omega_0 V^S/V^M without the
+        (2 pi kB T) factor) and the eigenvalues."""
+        out = {}
+        spec = {}
+        for tag, n in (("min", n_min), ("sad", n_sad)):
+            lam, vec, T = self.hessian_eigen(n)
+            pos = lam > zero_tol
+            spec[tag] = (lam, vec, T)
+            out["log_det_" + tag] = float(np.sum(np.log(lam[pos])))
+            out["n_zero_" + tag] = int(np.sum(np.abs(lam) <= zero_tol))
+            out["n_neg_" + tag] = int(np.sum(lam < -zero_tol))
+            out["E_" + tag] = float(self.energy(n)[0])
+            out["eig_" + tag] = lam
+        out["dE"] = out["E_sad"] - out["E_min"]
+        lam, vec, T = spec["sad"]
+        n = self._spins(n_sad)
+        # G in the tangent basis, 2 x 2 per spin: T_i^T (gamma/mu_i) [n_i]_x T_i
+        W = np.zeros((2 * self.N, 2 * self.N))
+        for i in range(self.N):
+            x = n[i]
+            nx = np.array([[0.0, -x[2], x[1]], [x[2], 0.0, -x[0]], [-x[1], x[0], 0.0]])
+            mu = self.mu_s[i % self.n_basis] * MU_B
+            W[2 * i:2 * i + 2, 2 * i:2 * i + 2] = (GAMMA / mu) * (T[i].T @ nx @ T[i])
+        Vd = (vec.T @ W @ vec) * lam[None, :]  # the dynamical matrix in the eigenbasis
+        a = Vd[0, :]                            # the unstable mode's row
+        pos = lam > zero_tol
+        out["a"] = a
+        out["lambda_unstable"] = float(lam[0])
+        out["v"] = float(np.sqrt(np.sum(a[pos] ** 2 / lam[pos])))
+        out["omega0"] = float(np.exp(0.5 * (out["log_det_min"] - out["log_det_sad"])))
+        out["prefactor"] = out["v"] / (2.0 * np.pi) * out["omega0"] * V_sad / V_min
+        return out
+
     def mmf(self, n, n_iter, dt=0.1, mass=1.0, vel=None):
         """Minimum mode following (Sec. MMF): velocity projection (Appendix D)
         with the effective force F - 2 (F.l) l, l the lowest mode; where the
@@ -377,16 +432,21 @@ class System:
     def mc_colours(self):
         return lib().spo_mc_colours(self._h)
 
-    def mc(self, spins, T, n_sweeps, seed=0, sweep0=0, target_accept=0.5, sample=True, cone=None, stats=None):
+    def mc(self, spins, T, n_sweeps, seed=0, sweep0=0, target_accept=0.5, sample=True, cone=None, stats=None,
+           order="random"):
         """Metropolis sweeps of replicas spins [R, N, 3] at temperatures T[R];
-        returns (spins, cone[R], stats[R, 8])."""
+        returns (spins, cone[R], stats[R, 8]).  order "random": each sweep
+        visits the spins in a fresh random order (the method's sweep);
+        "coloured": colour by colour of the lattice colouring (a check of a
+        colour-parallel decomposition)."""
         x = np.ascontiguousarray(np.asarray(spins, dtype=np.float64)[..., :3]).copy()
         R = x.shape[0]
         Tk = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(R))
         cn = np.full(R, 0.5) if cone is None else np.ascontiguousarray(np.asarray(cone, dtype=np.float64)).copy()
         st = np.zeros((R, 8)) if stats is None else np.ascontiguousarray(np.asarray(stats, dtype=np.float64)).copy()
         p = _MC(int(seed), int(sweep0), float(target_accept), int(bool(sample)))
-        _check(lib().spo_mc(self._h, _dp(x), R, _dp(Tk), C.byref(p), int(n_sweeps), _dp(cn), _dp(st)), "mc")
+        fn = {"random": lib().spo_mc, "coloured": lib().spo_mc_coloured}[order]
+        _check(fn(self._h, _dp(x), R, _dp(Tk), C.byref(p), int(n_sweeps), _dp(cn), _dp(st)), "mc")
         return x, cn, st
 
     def topological_charge(self, n):

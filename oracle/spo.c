@@ -1257,12 +1257,17 @@ int spo_topological_charge(const spo_system *s, const double *n, double *Q)
 /* ------------------------------------------------------------------ */
 /* Metropolis Monte Carlo (Sec. Monte Carlo)                            */
 /* ------------------------------------------------------------------ */
-/* Reading of the sweep: the paper visits every spin once per iteration in a
- * random sequential order; here the sweep visits the colours of a lattice
- * colouring in order, so that spins of one colour never interact and may be
- * updated in any order.  Every update is still a Metropolis step with the
- * rest of the system fixed, so the sampled distribution is the same
- * Boltzmann distribution.  Two colourings:
+/* The sweep (Sec. Monte Carlo): every spin is visited once per iteration,
+ * sequentially, in a random order -- spo_mc draws a fresh permutation of the
+ * spins for every sweep of every replica by a Fisher-Yates shuffle.  Each
+ * visit is a Metropolis step with the rest of the system fixed: a cone trial
+ * move accepted with probability min(1, exp(-dE / kB T)).
+ *
+ * spo_mc_coloured is a second, separately named sweep order that serves as a
+ * check of a parallel decomposition, not as the definition: it visits the
+ * colours of a lattice colouring one after the other (spins of one colour
+ * never interact, so a colour may be updated in any order).  It samples the
+ * same Boltzmann distribution.  Two colourings:
  *  - the sum colouring, colour = (c0 + c1 + c2) mod k (mc_sum_modulus);
  *  - the product colouring, colour = basis atom and, per direction, the cell
  *    index modulo 2, or modulo 3 for a periodic direction of odd size
@@ -1362,17 +1367,134 @@ static double mc_self_energy(const spo_system *s, int b, const double *ni)
     return -s->h.K[b] * kn * kn + gauss_terms(s, ni, dummy);
 }
 
-int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
-           double *cone, double *stats)
+/* One Metropolis visit of spin i of replica r (spins x) in sweep `sweep`:
+ * three uniforms in (0, 1) from Philox (counter (i, sweep lo, sweep hi,
+ * 8 r + 1)) give the azimuth, the cone angle and the acceptance test.
+ * Returns 1 if the trial was accepted. */
+static int mc_visit(const spo_system *s, double *x, long i, uint64_t sweep, int r, double ct, double T,
+                    const uint32_t key[2])
+{
+    int b, c[3];
+    decode(s, (int)i, &b, c);
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)r + 1u};
+    uint32_t o[4];
+    spo_philox4x32_10(ctr, key, o);
+    double u0 = (o[0] + 0.5) * 2.3283064365386963e-10;
+    double u1 = (o[1] + 0.5) * 2.3283064365386963e-10;
+    double u2 = (o[2] + 0.5) * 2.3283064365386963e-10;
+    /* trial direction: uniform on the cap of half-angle theta_cone around
+     * n_i (cos theta uniform in [cos theta_cone, 1]) */
+    double *ni = x + 3 * i;
+    double cth = 1.0 - u1 * (1.0 - ct), sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+    double ph = 2.0 * M_PI * u0;
+    double a[3] = {1, 0, 0};
+    if (fabs(ni[0]) >= 0.9) { a[0] = 0; a[1] = 1; }
+    double an = dot3(a, ni), e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) e1[k] = a[k] - an * ni[k];
+    normalise3(e1);
+    cross3(ni, e1, e2);
+    double nt[3];
+    for (int k = 0; k < 3; ++k) nt[k] = cth * ni[k] + sth * (cos(ph) * e1[k] + sin(ph) * e2[k]);
+    normalise3(nt);
+    double Bl[3];
+    mc_linear_field(s, x, (int)i, Bl);
+    double dE = -(dot3(nt, Bl) - dot3(ni, Bl)) + mc_self_energy(s, b, nt) - mc_self_energy(s, b, ni);
+    int acc = T > 0 ? (u2 < exp(-dE / (K_B * T))) : (dE < 0);
+    if (acc)
+        for (int k = 0; k < 3; ++k) ni[k] = nt[k];
+    return acc;
+}
+
+/* After a sweep of replica r: acceptance counts, the adaptive cone and the
+ * sampled observables. */
+static void mc_sweep_end(const spo_system *s, const double *x, int r, double accepted, const spo_mc_params *p,
+                         double *cone, double *stats)
+{
+    long N = s->N;
+    double *st = stats + 8 * (size_t)r;
+    st[6] += accepted;
+    st[7] += (double)N;
+    /* reading of the adaptive cone: multiplicative feedback towards the
+     * target acceptance ratio, theta <- theta exp(ratio - target), kept in
+     * [1e-4, pi] */
+    if (p->target_accept > 0) {
+        double th = cone[r] * exp(accepted / (double)N - p->target_accept);
+        cone[r] = fmin(M_PI, fmax(1e-4, th));
+    }
+    if (p->sample) {
+        double M[3] = {0, 0, 0};
+        for (long i = 0; i < N; ++i)
+            for (int k = 0; k < 3; ++k) M[k] += x[3 * i + k];
+        double mm = sqrt(dot3(M, M)) / (double)N;
+        double e[6];
+        spo_energy(s, x, e);
+        st[0] += mm;
+        st[1] += mm * mm;
+        st[2] += mm * mm * mm * mm;
+        st[3] += e[0];
+        st[4] += e[0] * e[0];
+        st[5] += 1;
+    }
+}
+
+static int mc_check(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p,
+                    int n_sweeps, double *cone, double *stats)
 {
     if (!s || !s->have_ham || !spins || n_rep < 1 || !T || !p || n_sweeps < 0 || !cone || !stats) return SPO_ERR_ARG;
     if (s->h.dipole != SPO_DIPOLE_NONE) return SPO_ERR_ARG;
+    return SPO_OK;
+}
+
+int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
+           double *cone, double *stats)
+{
+    int rc = mc_check(s, spins, n_rep, T, p, n_sweeps, cone, stats);
+    if (rc) return rc;
+    long N = s->N;
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    int bad = 0;
+    /* replicas are independent Markov chains: one per thread */
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int r = 0; r < n_rep; ++r) {
+        long *order = (long *)malloc(sizeof(long) * (size_t)(N > 0 ? N : 1));
+        if (!order) {
+            bad = 1;
+            continue;
+        }
+        double *x = spins + 3 * N * (size_t)r;
+        for (int sw = 0; sw < n_sweeps; ++sw) {
+            uint64_t sweep = p->sweep0 + (uint64_t)sw;
+            /* the visiting order: a uniformly random permutation (Fisher-Yates,
+             * uniforms from Philox counter (k, sweep lo, sweep hi, 8 r + 2)) */
+            for (long i = 0; i < N; ++i) order[i] = i;
+            for (long k = N - 1; k > 0; --k) {
+                uint32_t ctr[4] = {(uint32_t)k, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)r + 2u};
+                uint32_t o[4];
+                spo_philox4x32_10(ctr, key, o);
+                long j = (long)((((uint64_t)o[0] << 32) | o[1]) % (uint64_t)(k + 1));
+                long t = order[k];
+                order[k] = order[j];
+                order[j] = t;
+            }
+            double ct = cos(cone[r]);
+            double accepted = 0;
+            for (long q = 0; q < N; ++q) accepted += mc_visit(s, x, order[q], sweep, r, ct, T[r], key);
+            mc_sweep_end(s, x, r, accepted, p, cone, stats);
+        }
+        free(order);
+    }
+    return bad ? SPO_ERR_STATE : SPO_OK;
+}
+
+int spo_mc_coloured(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p,
+                    int n_sweeps, double *cone, double *stats)
+{
+    int rc = mc_check(s, spins, n_rep, T, p, n_sweeps, cone, stats);
+    if (rc) return rc;
     int k, m[3];
     const int n_col = mc_colouring(s, &k, m);
     if (!n_col) return SPO_ERR_ARG;
     long N = s->N;
-    double *Bs = (double *)malloc(sizeof(double) * 3 * N);
-    if (!Bs) return SPO_ERR_STATE;
     uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
     for (int sw = 0; sw < n_sweeps; ++sw) {
         uint64_t sweep = p->sweep0 + (uint64_t)sw;
@@ -1386,64 +1508,11 @@ int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const
                     decode(s, (int)i, &b, c);
                     int cc = k ? (c[0] + c[1] + c[2]) % k
                                : b + s->nb * (c[0] % m[0] + m[0] * (c[1] % m[1] + m[1] * (c[2] % m[2])));
-                    if (cc != col) continue;
-                    /* three uniforms in (0, 1) from Philox: azimuth, cone, acceptance */
-                    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)sweep, (uint32_t)(sweep >> 32), 8u * (uint32_t)r + 1u};
-                    uint32_t o[4];
-                    spo_philox4x32_10(ctr, key, o);
-                    double u0 = (o[0] + 0.5) * 2.3283064365386963e-10;
-                    double u1 = (o[1] + 0.5) * 2.3283064365386963e-10;
-                    double u2 = (o[2] + 0.5) * 2.3283064365386963e-10;
-                    /* trial direction: uniform on the cap of half-angle theta_cone
-                     * around n_i (cos theta uniform in [cos theta_cone, 1]) */
-                    double *ni = x + 3 * i;
-                    double cth = 1.0 - u1 * (1.0 - ct), sth = sqrt(fmax(0.0, 1.0 - cth * cth));
-                    double ph = 2.0 * M_PI * u0;
-                    double a[3] = {1, 0, 0};
-                    if (fabs(ni[0]) >= 0.9) { a[0] = 0; a[1] = 1; }
-                    double an = dot3(a, ni), e1[3], e2[3];
-                    for (int k = 0; k < 3; ++k) e1[k] = a[k] - an * ni[k];
-                    normalise3(e1);
-                    cross3(ni, e1, e2);
-                    double nt[3];
-                    for (int k = 0; k < 3; ++k) nt[k] = cth * ni[k] + sth * (cos(ph) * e1[k] + sin(ph) * e2[k]);
-                    normalise3(nt);
-                    double Bl[3];
-                    mc_linear_field(s, x, (int)i, Bl);
-                    double dE = -(dot3(nt, Bl) - dot3(ni, Bl)) + mc_self_energy(s, b, nt) - mc_self_energy(s, b, ni);
-                    int acc = T[r] > 0 ? (u2 < exp(-dE / (K_B * T[r]))) : (dE < 0);
-                    if (acc) {
-                        for (int k = 0; k < 3; ++k) ni[k] = nt[k];
-                        accepted += 1;
-                    }
+                    if (cc == col) accepted += mc_visit(s, x, i, sweep, r, ct, T[r], key);
                 }
-            double *st = stats + 8 * (size_t)r;
-            st[6] += accepted;
-            st[7] += (double)N;
-            /* reading of the adaptive cone: multiplicative feedback towards
-             * the target acceptance ratio, theta <- theta exp(ratio - target),
-             * kept in [1e-4, pi] */
-            if (p->target_accept > 0) {
-                double th = cone[r] * exp(accepted / (double)N - p->target_accept);
-                cone[r] = fmin(M_PI, fmax(1e-4, th));
-            }
-            if (p->sample) {
-                double M[3] = {0, 0, 0};
-                for (long i = 0; i < N; ++i)
-                    for (int k = 0; k < 3; ++k) M[k] += x[3 * i + k];
-                double mm = sqrt(dot3(M, M)) / (double)N;
-                double e[6];
-                spo_energy(s, x, e);
-                st[0] += mm;
-                st[1] += mm * mm;
-                st[2] += mm * mm * mm * mm;
-                st[3] += e[0];
-                st[4] += e[0] * e[0];
-                st[5] += 1;
-            }
+            mc_sweep_end(s, x, r, accepted, p, cone, stats);
         }
     }
-    free(Bs);
     return SPO_OK;
 }
 

@@ -160,12 +160,19 @@ typedef struct {
  * mod k, else the product colouring's count; 0 when neither applies. */
 int spo_mc_colours(const spo_system *s);
 /* n_sweeps Metropolis sweeps of n_rep replicas of the system (spins
- * n_rep x N x 3, replica r at temperature T[r] K).  cone[r] (radians,
- * in/out) is the trial cone's half-angle.  stats[r*8 + k] accumulates
- * (sum m, m^2, m^4, E, E^2, samples, accepted, trials), m = |sum n_i|/N,
- * E the total energy (meV). */
+ * n_rep x N x 3, replica r at temperature T[r] K), each sweep visiting every
+ * spin once in a fresh uniformly random order (Sec. Monte Carlo).  cone[r]
+ * (radians, in/out) is the trial cone's half-angle.  stats[r*8 + k]
+ * accumulates (sum m, m^2, m^4, E, E^2, samples, accepted, trials),
+ * m = |sum n_i|/N, E the total energy (meV). */
 int spo_mc(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p, int n_sweeps,
            double *cone, double *stats);
+/* The same Metropolis visits in another sweep order: the colours of the
+ * lattice colouring (spo_mc_colours) one after the other, each colour in
+ * index order.  A check of a colour-parallel decomposition; SPO_ERR_ARG for
+ * a lattice without colouring. */
+int spo_mc_coloured(const spo_system *s, double *spins, int n_rep, const double *T, const spo_mc_params *p,
+                    int n_sweeps, double *cone, double *stats);
 
 /* Covariant Hessian (Sec. MMF and its appendix on the spin manifold): the
  * action on v (N x 3, projected onto each spin's tangent plane first) of

@@ -59,6 +59,17 @@ class MMFParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("mass", C.c_double), ("krylov", C.c_int)]
 
 
+class HTSTParams(C.Structure):
+    _fields_ = [("zero_tol", C.c_double), ("V_min", C.c_double), ("V_sad", C.c_double)]
+
+
+class HTSTResult(C.Structure):
+    _fields_ = [("E_min", C.c_double), ("E_sad", C.c_double), ("dE", C.c_double), ("log_det_min", C.c_double),
+                ("log_det_sad", C.c_double), ("omega0", C.c_double), ("v", C.c_double),
+                ("lambda_unstable", C.c_double), ("prefactor", C.c_double), ("n_zero_min", C.c_int),
+                ("n_zero_sad", C.c_int), ("n_neg_min", C.c_int), ("n_neg_sad", C.c_int)]
+
+
 class MCParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("sweep0", C.c_uint64), ("target_accept", C.c_double), ("sample", C.c_int)]
 
@@ -100,6 +111,8 @@ SIGNATURES = {
     "sp_hessian_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "sp_lowest_mode": (_i, [_vp, _vp, _vp, _i, C.POINTER(_d), _vp]),
     "sp_mmf": (_i, [_vp, _vp, _vp, _vp, C.POINTER(MMFParams), _i, C.POINTER(_d), C.POINTER(_d), _vp]),
+    "sp_hessian_spectrum": (_i, [_vp, _vp, _vp, _vp]),
+    "sp_htst": (_i, [_vp, _vp, _vp, C.POINTER(HTSTParams), C.POINTER(HTSTResult), _vp]),
     "sp_mc_colours": (_i, [_vp, C.POINTER(_i)]),
     "sp_mc_sweeps": (_i, [_vp, _vp, _i, C.POINTER(_d), C.POINTER(MCParams), _i, _vp, _vp, _vp]),
     "sp_gneb_path": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -301,6 +314,21 @@ class Context:
         self._check(lib().sp_lowest_mode(self._h, self._spin_arg(n, "n"), self._spin_arg(mode, "mode"), int(krylov),
                                          C.byref(lam), _stream()))
         return lam.value, mode
+
+    def hessian_spectrum(self, n):
+        """All 2N eigenvalues of the covariant Hessian at n (FP64 contexts), ascending."""
+        eig = np.zeros(2 * self.N)
+        self._check(lib().sp_hessian_spectrum(self._h, self._spin_arg(n, "n"), eig.ctypes.data_as(C.c_void_p),
+                                              _stream()))
+        return eig
+
+    def htst(self, n_min, n_sad, zero_tol=1e-6, V_min=1.0, V_sad=1.0):
+        """HTST rate prefactor of the transition n_min -> over n_sad, as a dict."""
+        p = HTSTParams(float(zero_tol), float(V_min), float(V_sad))
+        r = HTSTResult()
+        self._check(lib().sp_htst(self._h, self._spin_arg(n_min, "n_min"), self._spin_arg(n_sad, "n_sad"),
+                                  C.byref(p), C.byref(r), _stream()))
+        return {name: getattr(r, name) for name, _ in HTSTResult._fields_}
 
     def mmf(self, n, vel, mode, n_iter, dt=0.1, mass=1.0, krylov=64):
         """Minimum mode following in place; returns (max |F|, lowest eigenvalue)."""

@@ -718,7 +718,7 @@ int sp_create(sp_ctx **out, int precision)
 int sp_destroy(sp_ctx *c)
 {
     if (!c) return SP_OK;
-    bool any = c->pred.p || c->partials.p || c->bdd.p || c->dip || c->mins;
+    bool any = c->pred.p || c->partials.p || c->bdd.p || c->dip || c->mins || c->hess || c->htst || c->mc;
     if (any) cudaDeviceSynchronize();
     if (c->pred.p) cudaFree(c->pred.p);
     if (c->partials.p) cudaFree(c->partials.p);
@@ -731,6 +731,7 @@ int sp_destroy(sp_ctx *c)
     if (c->lg_stream) cudaStreamDestroy(c->lg_stream);
     mc_scratch_destroy(c->mc);
     hess_scratch_destroy(c->hess);
+    htst_scratch_destroy(c->htst);
     dipole_destroy(c->dip);
     min_scratch_destroy(c->mins);
     delete c;

@@ -89,6 +89,8 @@ struct McScratch;  // Monte Carlo scratch (mc.cu)
 void mc_scratch_destroy(McScratch *m);
 struct HessScratch;  // Hessian / Lanczos / MMF scratch (hessian.cu)
 void hess_scratch_destroy(HessScratch *h);
+struct HtstScratch;  // full-spectrum Lanczos scratch (htst.cu)
+void htst_scratch_destroy(HtstScratch *h);
 
 struct sp_ctx {
     int prec = SP_F32;
@@ -139,6 +141,7 @@ struct sp_ctx {
     MinScratch *mins = nullptr;
     McScratch *mc = nullptr;
     HessScratch *hess = nullptr;
+    HtstScratch *htst = nullptr;
     Profiler prof;
 };
 

@@ -450,6 +450,18 @@ bool hrecords_aligned(const sp_ctx *c, std::initializer_list<const void *> ptrs)
 
 }  // namespace
 
+namespace spgb {
+template <typename T>
+cudaError_t launch_hvp(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *v, rec_t<T> *out, cudaStream_t st)
+{
+    if (S.N <= 0) return cudaSuccess;
+    k_hvp<T><<<hblocks(S.N), kHB, 0, st>>>(S, n, v, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_hvp<float>(const Stencil<float> &, const float4 *, const float4 *, float4 *, cudaStream_t);
+template cudaError_t launch_hvp<double>(const Stencil<double> &, const dq4 *, const dq4 *, dq4 *, cudaStream_t);
+}  // namespace spgb
+
 void hess_scratch_destroy(HessScratch *h)
 {
     if (!h) return;

@@ -101,6 +101,11 @@ template <typename T>
 cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *Bdd, double *partials, double *e_out,
                           double *torque_out, cudaStream_t st);
 
+// Covariant Hessian-vector product out = H v at the configuration n (v is
+// projected onto the tangent planes first).
+template <typename T>
+cudaError_t launch_hvp(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *v, rec_t<T> *out, cudaStream_t st);
+
 // Finiteness check of results (the device status word): records n[0..n_rec)
 // (x, y, z; the padding lane is not looked at) or plain doubles v[0..n_val);
 // any non-finite value ORs `site` into *flag, a word of mapped host memory.

@@ -78,7 +78,7 @@ def test_mc30_sweep_full_size_fp64():
     cone = torch.full((R,), 0.6, dtype=torch.float64, device="cuda")
     x = c.spins(n0)
     cone_g, st = c.mc_sweeps(x, TEMPS, 1, seed=7, target_accept=0.5, cone=cone)
-    xo, co, sto = o.mc(n0, TEMPS, 1, seed=7, target_accept=0.5, cone=np.full(R, 0.6))
+    xo, co, sto = o.mc(n0, TEMPS, 1, seed=7, target_accept=0.5, cone=np.full(R, 0.6), order="coloured")
     for r in (0, 14, 28):
         assert np.abs(_np(x[r]) - xo[r]).max() <= 1e-12, r
     assert np.allclose(cone_g.cpu().numpy(), co, rtol=0, atol=1e-12)

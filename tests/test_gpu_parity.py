@@ -544,8 +544,9 @@ def test_mc_sweeps_fp64_match_oracle(name, g, h, ncol, resident):
     # thermalisation with the adaptive cone, then sampling with the cone fixed
     cone, stats = c.mc_sweeps(x, T, 20, seed=9, target_accept=0.4, sample=False)
     cone, stats = c.mc_sweeps(x, T, 20, seed=9, sweep0=20, target_accept=0.0, sample=True, cone=cone, stats=stats)
-    xo, co, so = o.mc(x0, T, 20, seed=9, target_accept=0.4, sample=False)
-    xo, co, so = o.mc(xo, T, 20, seed=9, sweep0=20, target_accept=0.0, sample=True, cone=co, stats=so)
+    xo, co, so = o.mc(x0, T, 20, seed=9, target_accept=0.4, sample=False, order="coloured")
+    xo, co, so = o.mc(xo, T, 20, seed=9, sweep0=20, target_accept=0.0, sample=True, cone=co, stats=so,
+                      order="coloured")
     assert np.abs(_np(x) - xo).max() <= 1e-11
     assert np.abs(cone.cpu().numpy() - co).max() <= 1e-12
     st = stats.cpu().numpy()

@@ -15,8 +15,9 @@ forces), not only with other FP32 runs:
 * image energies of one chain state: the FP32 field with float-float sums
   against the oracle's FP64 energies, 1e-8 relative of the image energy (the
   FP32 rounding of the per-spin terms, not of the sum, is what remains);
-* converged relaxations: the FP32 minimiser's final energy against the
-  oracle's to 1e-8 relative, the FP32 chain's barrier against the oracle's.
+* converged relaxations: the FP32 minimiser's final energy (max torque
+  below 1e-6) against the oracle's to 1e-8 relative, the FP32 chain's
+  barrier against the oracle's.
 """
 import numpy as np
 import pytest
@@ -96,14 +97,19 @@ def test_vp_fp32_ten_iterations_and_convergence_against_oracle():
     # relaxed energy (the energy is stationary at the minimum: second order).
     # The start is a perturbed ferromagnet along the field, which relaxes to
     # one minimum (from random starts FP32 and FP64 may end in different ones)
+    # The energy error of a state relaxed to max torque tau is of order
+    # tau^2 / (softest curvature) per spin: at tau = 1e-4 it was measured at
+    # 5.7e-8 relative, so the FP32 path relaxes to 1e-6 here (its forces
+    # resolve ~1e-7 meV), where the bound is 1e-8 relative (the final-energy
+    # contract)
     n1 = _f32(I.perturbed(I.ferromagnet(o.N), 0.4, 7))
     x, v = c.spins(n1), c.spins(np.zeros_like(n1))
-    it, mt = c.minimise(x, v, dt=0.1, tol=1e-4, max_iter=20000, check_every=50)
-    no, _, ito, mto = o.minimise(n1, dt=0.1, tol=1e-8, max_iter=20000)
-    assert mt < 1e-4 and mto < 1e-8
+    it, mt = c.minimise(x, v, dt=0.1, tol=1e-6, max_iter=40000, check_every=50)
+    no, _, ito, mto = o.minimise(n1, dt=0.1, tol=1e-8, max_iter=40000)
+    assert mt < 1e-6 and mto < 1e-8
     e32 = o.energy(_np(x))[0]
     e64 = o.energy(no)[0]
-    print("VP FP32 relaxed energy vs oracle: %.3g relative" % (abs(e32 - e64) / abs(e64)))
+    print("VP FP32 relaxed energy vs oracle: %.3g relative (FP32 %d iterations)" % (abs(e32 - e64) / abs(e64), it))
     assert abs(e32 - e64) <= 1e-8 * abs(e64)
 
 

@@ -917,6 +917,27 @@ def test_mc_colour_counts(geom, ham, ncol):
     assert oracle.System(geom, ham).mc_colours() == ncol
 
 
+def test_mc_random_order_sweep_visits_every_spin_once():
+    # the method's sweep visits each spin once per iteration in a random
+    # order.  At a temperature where every trial is accepted, one sweep moves
+    # every spin exactly once: each spin's move is the trial drawn for it, so
+    # the coloured order (a different visiting order) gives the same state,
+    # and a permutation that missed a spin would leave it where it was
+    s = oracle.System(I.simple_cubic(6, 6, 4), dict(J=[1.0], B=[0, 0, 0.5]))
+    x0 = I.random_spins(s.N, 8)[None]
+    x, _, st = s.mc(x0, [1e12], 1, seed=3, target_accept=0.0, sample=False, cone=[0.7])
+    y, _, _ = s.mc(x0, [1e12], 1, seed=3, target_accept=0.0, sample=False, cone=[0.7], order="coloured")
+    assert st[0, 6] == st[0, 7] == s.N
+    assert np.all(np.linalg.norm(x[0] - x0[0], axis=1) > 0)
+    assert np.abs(x - y).max() < 1e-15
+    # at a finite temperature the visiting order matters (the field of a
+    # spin depends on which neighbours moved before it): the two orders give
+    # different chains
+    x, _, _ = s.mc(x0, [3.0], 3, seed=3, target_accept=0.0, sample=False, cone=[0.7])
+    y, _, _ = s.mc(x0, [3.0], 3, seed=3, target_accept=0.0, sample=False, cone=[0.7], order="coloured")
+    assert np.abs(x - y).max() > 1e-3
+
+
 def test_mc_cone_adapts_to_the_target_acceptance_and_limits():
     # 8^3 spins: a sweep's acceptance fluctuates by ~2% (on 4^3 by ~6%, and the
     # multiplicative feedback turns that into a random walk of the cone)
@@ -1005,3 +1026,110 @@ def test_mmf_single_spin_climbs_onto_a_first_order_saddle():
         y = _retract(y, np.einsum("ikc,ic->ik", Ty, step.reshape(-1, 2)), 1.0)
     assert np.linalg.norm(y - x) < 1e-8
     assert s.energy(x)[0] > s.energy(x0)[0]
+
+
+# ----------------------------------------------------------------------------
+# Harmonic transition-state theory (Sec. HTST, appendix on the manifold)
+# ----------------------------------------------------------------------------
+def _single_spin_stationary(mu_s, K, Bx, Bz):
+    """Stationary points of one spin with easy axis z and field (Bx, 0, Bz) on
+    the great circle n = (sin psi, 0, cos psi), found here independently of
+    the oracle: (psi_min, psi_saddle) and the closed-form curvatures
+    lambda_psi = E''(psi), lambda_y = 2 K n_z^2 + mu (Bx n_x + Bz n_z) (the
+    second derivative along the geodesic towards y, which does not couple to
+    psi by the mirror symmetry y -> -y)."""
+    from scipy.optimize import brentq
+    mu = mu_s * oracle.MU_B
+    dE = lambda p: 2 * K * math.cos(p) * math.sin(p) - mu * (Bx * math.cos(p) - Bz * math.sin(p))  # noqa: E731
+    d2E = lambda p: 2 * K * math.cos(2 * p) + mu * (Bx * math.sin(p) + Bz * math.cos(p))  # noqa: E731
+    grid = np.linspace(-math.pi, math.pi, 4001)
+    roots = [brentq(dE, a, b, xtol=1e-15) for a, b in zip(grid[:-1], grid[1:]) if dE(a) * dE(b) < 0]
+
+    def lam(p):
+        nx, nz = math.sin(p), math.cos(p)
+        return d2E(p), 2 * K * nz * nz + mu * (Bx * nx + Bz * nz)
+
+    mins = [p for p in roots if min(lam(p)) > 0]
+    sads = [p for p in roots if lam(p)[0] < 0 < lam(p)[1]]
+    # the metastable minimum (the higher of the two) and the saddle
+    E = lambda p: -K * math.cos(p) ** 2 - mu * (Bx * math.sin(p) + Bz * math.cos(p))  # noqa: E731
+    pm = max(mins, key=E)
+    return pm, sads[0], lam(pm), lam(sads[0]), mu
+
+
+def test_htst_single_spin_prefactor_is_the_precession_frequency():
+    # one spin: the saddle's positive curvature cancels between Omega_0 and
+    # v, and the prefactor is the precession frequency at the minimum over
+    # 2 pi, gamma / (2 pi mu) sqrt(lambda_1^M lambda_2^M)
+    mu_s, K, Bx, Bz = 2.0, 1.0, 1.5, 3.0
+    pm, ps, lm, ls, mu = _single_spin_stationary(mu_s, K, Bx, Bz)
+    s = oracle.System(I.square(1, 1, mu_s=mu_s), dict(B=[Bx, 0, Bz], K=[K], Khat=[[0, 0, 1]]))
+    nm = np.array([[math.sin(pm), 0.0, math.cos(pm)]])
+    ns = np.array([[math.sin(ps), 0.0, math.cos(ps)]])
+    r = s.htst(nm, ns, zero_tol=1e-9)
+    assert r["n_neg_min"] == 0 and r["n_neg_sad"] == 1 and r["n_zero_min"] == r["n_zero_sad"] == 0
+    assert np.allclose(np.sort(r["eig_min"]), np.sort(lm), rtol=1e-12)
+    assert np.allclose(np.sort(r["eig_sad"]), np.sort(ls), rtol=1e-12)
+    assert abs(r["omega0"] - math.sqrt(lm[0] * lm[1] / ls[1])) <= 1e-12 * r["omega0"]
+    assert abs(r["v"] - oracle.GAMMA / mu * math.sqrt(ls[1])) <= 1e-12 * r["v"]
+    freq = oracle.GAMMA / (2 * math.pi * mu) * math.sqrt(lm[0] * lm[1])
+    assert abs(r["prefactor"] - freq) <= 1e-12 * freq
+    E = lambda p: -K * math.cos(p) ** 2 - mu * (Bx * math.sin(p) + Bz * math.cos(p))  # noqa: E731
+    assert abs(r["dE"] - (E(ps) - E(pm))) <= 1e-12 * abs(E(pm))
+
+
+def test_htst_axial_single_spin_has_a_zero_mode_at_the_saddle():
+    # field along the easy axis: the saddle is a ring (cos theta = -h), one
+    # zero mode there and none at the minimum; no positive saddle mode is
+    # left, so the velocity factor of the primed sum vanishes
+    mu_s, K, Bz = 2.0, 1.0, 3.0
+    mu = mu_s * oracle.MU_B
+    h = mu * Bz / (2 * K)
+    s = oracle.System(I.square(1, 1, mu_s=mu_s), dict(B=[0, 0, Bz], K=[K], Khat=[[0, 0, 1]]))
+    th = math.acos(-h)
+    r = s.htst(np.array([[0.0, 0.0, -1.0]]), np.array([[math.sin(th), 0.0, math.cos(th)]]), zero_tol=1e-9)
+    assert r["n_zero_sad"] == 1 and r["n_neg_sad"] == 1 and r["n_zero_min"] == 0
+    assert abs(r["dE"] - K * (1 - h) ** 2) < 1e-12
+    assert r["v"] == 0.0
+
+
+def test_htst_velocity_equals_the_turned_mode_curvature():
+    # the identity the GPU path computes v with: for W antisymmetric per
+    # spin, sum over positive modes of a_i^2 / lambda_i = u . H u with
+    # u_i = (gamma / mu_i) n_i x e_1,i (e_1 the unstable eigenvector), when
+    # no zero modes are present.  Checked on a random "saddle" of a small
+    # interacting system: the lowest eigenvalue is negative there.
+    g = I.hexagonal(3, 3, periodic=(True, True), mu_s=[2.0])
+    g["basis"] = [[0, 0, 0], [0.5, 0.3, 0]]
+    g["mu_s"] = [2.0, 1.3]
+    h = dict(J=[1.0, 0.3], dmi_kind="interfacial", D=[0.4], K=[0.3, 0.1], Khat=[[0, 0, 1], [1, 0, 0]], B=[0.1, 0, 0.9])
+    s = oracle.System(g, h)
+    n = I.random_spins(s.N, 4)
+    r = s.htst(n, n, zero_tol=1e-9)
+    lam, vec, T = s.hessian_eigen(n)
+    assert lam[0] < 0
+    e1 = np.einsum("ikc,ic->ik", T, vec[:, 0].reshape(-1, 2))
+    mu = np.array([s.mu_s[i % 2] for i in range(s.N)]) * oracle.MU_B
+    u = (oracle.GAMMA / mu)[:, None] * np.cross(n, e1)
+    uHu = np.sum(u * s.hessian_apply(n, u))
+    neg = lam < -1e-9
+    # the primed sum leaves out every non-positive mode; u.Hu keeps the
+    # other negative ones, whose share is subtracted here
+    a = r["a"]
+    extra = np.sum(a[neg][1:] ** 2 / lam[neg][1:])
+    assert abs((uHu - extra) - r["v"] ** 2) <= 1e-10 * r["v"] ** 2
+
+
+def test_htst_log_determinant_of_the_ferromagnet_is_the_magnon_product():
+    # ferromagnet along z on a periodic square lattice (B, K along z): the
+    # Hessian's eigenvalues are mu B + 2K + J (4 - 2 cos qx - 2 cos qy), each
+    # twice, so log det = 2 sum_q log(...)
+    L, mu_s, Bz, K, J = 6, 2.0, 0.7, 0.2, 1.0
+    s = oracle.System(I.square(L, L, periodic=(True, True), mu_s=mu_s), dict(J=[J], K=[K], Khat=[[0, 0, 1]],
+                                                                              B=[0, 0, Bz]))
+    n = I.ferromagnet(s.N)
+    q = 2 * math.pi * np.arange(L) / L
+    w = mu_s * oracle.MU_B * Bz + 2 * K + J * (4 - 2 * np.cos(q)[:, None] - 2 * np.cos(q)[None, :])
+    r = s.htst(n, n, zero_tol=1e-9)
+    assert abs(r["log_det_min"] - 2 * np.sum(np.log(w))) <= 1e-12 * abs(r["log_det_min"])
+    assert r["n_neg_min"] == 0 and r["n_zero_min"] == 0
