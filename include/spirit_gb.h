@@ -602,7 +602,21 @@ enum {
      * path-analysis charges, replica noise amplitudes and step counter (not
      * the dipole plan, minimiser, Monte Carlo or Hessian workspaces).  0 on a
      * context that has allocated none of them */
-    SP_OPT_SCRATCH_KIB = 8
+    SP_OPT_SCRATCH_KIB = 8,
+    /* value 1: the iterations of an sp_gneb_step / sp_gneb_batch_step call
+     * (the batch reads the option of its first chain's context) run in one
+     * persistent cooperative launch -- every image of every chain, the
+     * passes separated by grid-wide barriers, tangent weights and force
+     * coefficients computed per work block -- instead of one launch per pass
+     * replayed from a CUDA graph; the iterates are bit-identical.  A barrier
+     * wait that exceeds SP_OPT_WAIT_LIMIT polls gives up: every block then
+     * leaves the kernel, the chain is left part-way through an iteration, and
+     * the context's status word reports SP_ERR_TIMEOUT (sp_sync_status or the
+     * next call).  0 (default): one launch per pass */
+    SP_OPT_GNEB_PERSISTENT = 9,
+    /* polls (about 0.1-0.5 us each) a grid-barrier wait of the persistent
+     * GNEB kernel makes before it gives up (>= 1); 0: the default, 2^21 */
+    SP_OPT_WAIT_LIMIT = 10
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose the work per CTA of the 27-point path by measurement, for each pass

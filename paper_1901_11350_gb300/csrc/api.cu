@@ -985,6 +985,9 @@ int sp_gneb_step(sp_ctx *c, void *chain_dev, void *vel_dev, int n_images, const 
             if (p->image_types[v] < SP_IMAGE_NORMAL || p->image_types[v] > SP_IMAGE_FALLING)
                 return fail(c, SP_ERR_ARG, "image %d: unknown image type %d", v, p->image_types[v]);
     GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, n_images, n_iter, p->image_types, p->energy_weight};
+    a.persistent = c->gneb_persistent;
+    a.wait_limit = c->wait_limit;
+    if (a.persistent && !(a.status = status_word(c))) return SP_ERR_CUDA;
     int e = c->prec == SP_F64
                 ? gneb_run<double>(&c->mins, c->Sd, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream)
                 : gneb_run<float>(&c->mins, c->Sf, chain_dev, vel_dev, a, energies_dev, max_force_dev, (cudaStream_t)stream);
@@ -1153,6 +1156,9 @@ int sp_gneb_batch_step(sp_ctx *const *ctxs, int n_chains, void *chains_dev, void
                 return fail(c0, SP_ERR_ARG, "image %lld: unknown image type %d", g, p->image_types[g]);
     }
     GnebArgs a{p->dt, p->mass, p->k_spring, p->climbing ? 1 : 0, 0, n_iter, p->image_types, p->energy_weight};
+    a.persistent = c0->gneb_persistent;
+    a.wait_limit = c0->wait_limit;
+    if (a.persistent && !(a.status = status_word(c0))) return SP_ERR_CUDA;
     int e;
     if (c0->prec == SP_F64) {
         std::vector<Stencil<double>> S;
@@ -1212,6 +1218,14 @@ int sp_set_option(sp_ctx *c, int option, int value)
         if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "mc_resident takes 0 or 1");
         c->use_mc_resident = value == 1;
         return SP_OK;
+    case SP_OPT_GNEB_PERSISTENT:
+        if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "gneb_persistent takes 0 or 1");
+        c->gneb_persistent = value;
+        return SP_OK;
+    case SP_OPT_WAIT_LIMIT:
+        if (value < 0) return fail(c, SP_ERR_ARG, "wait limit must be >= 0 (0: default)");
+        c->wait_limit = value;
+        return SP_OK;
     default:
         return fail(c, SP_ERR_ARG, "unknown option %d", option);
     }
@@ -1254,6 +1268,12 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_MC_RESIDENT:
         *value = c->use_mc_resident ? 1 : 0;
+        return SP_OK;
+    case SP_OPT_GNEB_PERSISTENT:
+        *value = c->gneb_persistent;
+        return SP_OK;
+    case SP_OPT_WAIT_LIMIT:
+        *value = c->wait_limit;
         return SP_OK;
     case SP_OPT_SCRATCH_KIB: {
         size_t b = c->pred.bytes + c->partials.bytes + c->bdd.bytes + c->qbuf.bytes + c->rsig.bytes + c->step_ctr.bytes;

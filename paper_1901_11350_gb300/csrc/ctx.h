@@ -117,6 +117,8 @@ struct sp_ctx {
     bool generic_fft = false;  // SP_OPT_GENERIC_FFT
     bool use_small = true;     // SP_OPT_SMALL_PATH
     bool use_mc_resident = true;  // SP_OPT_MC_RESIDENT
+    int gneb_persistent = 0;      // SP_OPT_GNEB_PERSISTENT
+    int wait_limit = 0;           // SP_OPT_WAIT_LIMIT (0: default)
     int zc = 0;             // units per CTA of the 27-point path; 0 = balanced (see cubic_per)
     int zc_corr = 0;        // the corrector's, when the autotuner chose it separately
     int zc_auto = 0;        // balanced value, computed on first use

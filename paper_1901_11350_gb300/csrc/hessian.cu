@@ -277,6 +277,7 @@ struct Ops {
         double nrm2;
         int rc = dots(q(0), q(0), 1, &nrm2);
         if (rc) return rc;
+        if (nrm2 != nrm2) return SP_ERR_NAN;  // a non-finite state or start vector
         if (!(nrm2 > 0)) return SP_ERR_ARG;
         double inv = 1.0 / sqrt(nrm2);
         k_lin<T><<<nb, kHB, 0, st>>>(N, q(0), inv, q(0), 0.0, q(0));
@@ -500,6 +501,7 @@ int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, dou
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? lowest_mode_run<double>(c, c->Sd, n_dev, mode_dev, krylov, lambda, st)
                            : lowest_mode_run<float>(c, c->Sf, n_dev, mode_dev, krylov, lambda, st);
+    if (rc == SP_ERR_NAN) return hfail(c, rc, "lowest mode: a non-finite value in the state or the start vector");
     if (rc) return hfail(c, rc, "Lanczos failed");
     return std::isfinite(*lambda) ? SP_OK : hfail(c, SP_ERR_NAN, "lowest mode: the eigenvalue is not finite");
 }
@@ -516,6 +518,7 @@ int sp_mmf(sp_ctx *c, void *n_dev, void *vel_dev, void *mode_dev, const sp_mmf_p
     cudaStream_t st = (cudaStream_t)stream;
     rc = c->prec == SP_F64 ? mmf_run<double>(c, c->Sd, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st)
                            : mmf_run<float>(c, c->Sf, n_dev, vel_dev, mode_dev, p, n_iter, max_force, lambda, st);
+    if (rc == SP_ERR_NAN) return hfail(c, rc, "minimum mode following: a non-finite value");
     if (rc) return hfail(c, rc, "minimum mode following failed");
     return std::isfinite(*max_force) && std::isfinite(*lambda)
                ? SP_OK

@@ -60,7 +60,7 @@ int grow(Buf &b, size_t bytes)
 }  // namespace
 
 struct MinScratch {
-    Buf F, G, Tau, scal, part, cnt, blk, img, sten, state, aux;
+    Buf F, G, Tau, scal, part, cnt, blk, img, sten, state, aux, sync;
     int *host_state = nullptr;  // pinned: iters, active
     double *host_fmax = nullptr;
     // batch layout last uploaded (block/image tables and stencils)
@@ -78,7 +78,8 @@ constexpr int kGraphIters = 8;
 void min_scratch_destroy(MinScratch *s)
 {
     if (!s) return;
-    Buf *bufs[] = {&s->F, &s->G, &s->Tau, &s->scal, &s->part, &s->cnt, &s->blk, &s->img, &s->sten, &s->state, &s->aux};
+    Buf *bufs[] = {&s->F, &s->G, &s->Tau, &s->scal, &s->part, &s->cnt, &s->blk, &s->img, &s->sten, &s->state, &s->aux,
+                   &s->sync};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (s->host_state) cudaFreeHost(s->host_state);
@@ -269,16 +270,23 @@ __global__ void __launch_bounds__(kBlock) k_vp_move(int N, rec_t<T> *__restrict_
 }
 
 // ============================================================ GNEB
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
-                                                    const Stencil<T> *__restrict__ S, const rec_t<T> *__restrict__ x,
-                                                    rec_t<T> *__restrict__ G, double *part, unsigned *cnt, double *scal)
+// The GNEB passes are written as bodies for one work block `vb` (an entry of
+// the block table), so that the per-pass kernels (vb = blockIdx.x) and the
+// persistent kernel (a CTA takes several vb in turn) run the same code.
+// R: the record type the mutable buffers are read through -- rec_t<T> (the
+// per-pass kernels: spins by the read-only path) or the plain-load record
+// type of ShRec<T> (the persistent kernel, which reads what other blocks
+// wrote earlier in the same launch).
+template <typename T, typename R>
+__device__ __forceinline__ void g_field_body(int vb, const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                             const Stencil<T> *__restrict__ S, const R *x, R *G, double *part,
+                                             unsigned *cnt, double *scal)
 {
-    BlkInfo bi = blk[blockIdx.x];
+    BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
     const Stencil<T> &St = S[im.chain];
     int i = bi.t * kBlock + threadIdx.x;
-    const rec_t<T> *xb = x + im.spin0 + (long long)im.nu * im.N;
+    const R *xb = x + im.spin0 + (long long)im.nu * im.N;
     // energy and squared angle sums: FP64, or float-float for FP32 (the
     // same sums of the same products to ~1e-14, off the FP64 pipe)
     using A = typename Acc<T>::type;
@@ -305,25 +313,69 @@ __global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ 
             r[1] = th * th;
         }
     }
-    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kE);
+    image_reduce<2>(r, 0u, part, vb, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kE);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
-                                                      const rec_t<T> *__restrict__ x, const rec_t<T> *__restrict__ G,
-                                                      rec_t<T> *__restrict__ Tau, double *part, unsigned *cnt,
-                                                      double *scal)
+__global__ void __launch_bounds__(kBlock) k_g_field(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                    const Stencil<T> *__restrict__ S, const rec_t<T> *__restrict__ x,
+                                                    rec_t<T> *__restrict__ G, double *part, unsigned *cnt, double *scal)
 {
-    BlkInfo bi = blk[blockIdx.x];
+    g_field_body<T>(blockIdx.x, blk, img, S, x, G, part, cnt, scal);
+}
+
+// Weights (w+, w-) of the forward and backward differences in the improved
+// tangent (Henkelman and Jonsson 2000) of interior image g, from the image
+// energies of the field pass.
+__device__ __forceinline__ void tangent_weights(const double *scal, int g, double *wp_out, double *wm_out)
+{
+    double Ep = scal[kS * (g + 1) + kE], E0 = scal[kS * g + kE], Em = scal[kS * (g - 1) + kE];
+    double wp, wm;
+    if (Ep > E0 && E0 > Em) {
+        wp = 1;
+        wm = 0;
+    } else if (Ep < E0 && E0 < Em) {
+        wp = 0;
+        wm = 1;
+    } else {
+        double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+        if (Ep > Em) {
+            wp = dmax;
+            wm = dmin;
+        } else {
+            wp = dmin;
+            wm = dmax;
+        }
+    }
+    *wp_out = wp;
+    *wm_out = wm;
+}
+
+// LOCALW: the weights are computed here from the energies (persistent
+// kernel) instead of read from the slots k_g_weights filled -- the same
+// function of the same values.
+template <typename T, bool LOCALW, typename R>
+__device__ __forceinline__ void g_tangent_body(int vb, const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                               const R *x, const R *G, R *Tau, double *part, unsigned *cnt,
+                                               double *scal)
+{
+    BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     bool end = im.nu == 0 || im.nu == im.M - 1;
-    // weights of the forward and backward differences (k_g_weights)
+    // weights of the forward and backward differences
     __shared__ T s_wp, s_wm;
     if (threadIdx.x == 0 && !end) {
-        s_wp = (T)scal[kS * bi.g + kWP];
-        s_wm = (T)scal[kS * bi.g + kWM];
+        if (LOCALW) {
+            double wp, wm;
+            tangent_weights(scal, bi.g, &wp, &wm);
+            s_wp = (T)wp;
+            s_wm = (T)wm;
+        } else {
+            s_wp = (T)scal[kS * bi.g + kWP];
+            s_wm = (T)scal[kS * bi.g + kWM];
+        }
     }
     __syncthreads();
     using A = typename Acc<T>::type;
@@ -345,38 +397,26 @@ __global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict_
         r[0] = acc_dot(t, t);
         r[1] = acc_dot(ldc(G, p), t);
     }
-    image_reduce<2>(r, 0u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kTT);
+    image_reduce<2>(r, 0u, part, vb, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kTT);
 }
 
-// Weights of the forward and backward differences in the improved tangent
-// (Henkelman and Jonsson 2000) of every interior image, from the energies of
-// the field pass; one thread per image.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_tangent(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                      const rec_t<T> *__restrict__ x, const rec_t<T> *__restrict__ G,
+                                                      rec_t<T> *__restrict__ Tau, double *part, unsigned *cnt,
+                                                      double *scal)
+{
+    g_tangent_body<T, false>(blockIdx.x, blk, img, x, G, Tau, part, cnt, scal);
+}
+
+// Tangent weights of every interior image into its slots; one thread per image.
 __global__ void k_g_weights(const ImgInfo *__restrict__ img, int n_img, double *scal)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_img) return;
     ImgInfo im = img[g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
-    double Ep = scal[kS * (g + 1) + kE], E0 = scal[kS * g + kE], Em = scal[kS * (g - 1) + kE];
-    double wp, wm;
-    if (Ep > E0 && E0 > Em) {
-        wp = 1;
-        wm = 0;
-    } else if (Ep < E0 && E0 < Em) {
-        wp = 0;
-        wm = 1;
-    } else {
-        double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
-        if (Ep > Em) {
-            wp = dmax;
-            wm = dmin;
-        } else {
-            wp = dmin;
-            wm = dmax;
-        }
-    }
-    scal[kS * g + kWP] = wp;
-    scal[kS * g + kWM] = wm;
+    tangent_weights(scal, g, &scal[kS * g + kWP], &scal[kS * g + kWM]);
 }
 
 // Slope dE/dr of image g along its normalised tangent.
@@ -430,6 +470,13 @@ __device__ double seg_length(double Ea, double Eb, double da, double db, double 
     return total;
 }
 
+// Energy-weighted length of segment (g, g+1) from the image slots.
+__device__ __forceinline__ double segment_of(const double *scal, int g, double w)
+{
+    return seg_length(scal[kS * g + kE], scal[kS * (g + 1) + kE], slope_of(scal, g), slope_of(scal, g + 1),
+                      sqrt(scal[kS * g + kL2]), w);
+}
+
 // scal[8g + kLW] = energy-weighted length of segment (g, g+1), one thread per image.
 __global__ void k_g_seglen(const ImgInfo *__restrict__ img, int n_img, double w, double *scal)
 {
@@ -437,8 +484,7 @@ __global__ void k_g_seglen(const ImgInfo *__restrict__ img, int n_img, double w,
     if (g >= n_img) return;
     ImgInfo im = img[g];
     if (im.nu >= im.M - 1) return;
-    scal[kS * g + kLW] = seg_length(scal[kS * g + kE], scal[kS * (g + 1) + kE], slope_of(scal, g), slope_of(scal, g + 1),
-                                   sqrt(scal[kS * g + kL2]), w);
+    scal[kS * g + kLW] = segment_of(scal, g, w);
 }
 
 // The force coefficient a of every interior image (F = -Pg + a tau):
@@ -446,13 +492,11 @@ __global__ void k_g_seglen(const ImgInfo *__restrict__ img, int n_img, double w,
 // the image has no fixed kind): a = 2 Pg.tau / |tau|^2; falling image: 0;
 // otherwise (Pg.tau / |tau| + k (l_g - l_{g-1})) / |tau|, l the geodesic or
 // energy-weighted segment lengths.  One thread per image.
-__global__ void k_g_coef(const ImgInfo *__restrict__ img, int n_img, double kspring, int climbing, int weighted,
-                         double *scal)
+// lw_g, lw_gm: the energy-weighted lengths of segments (g, g+1) and
+// (g-1, g) (used when `weighted`).
+__device__ __forceinline__ double force_coef(const ImgInfo &im, int g, double kspring, int climbing, int weighted,
+                                             const double *scal, double lw_g, double lw_gm)
 {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_img) return;
-    ImgInfo im = img[g];
-    if (im.nu == 0 || im.nu == im.M - 1) return;
     int ci = -1;
     if (climbing && im.kind < 0) {
         ci = 1;
@@ -468,27 +512,55 @@ __global__ void k_g_coef(const ImgInfo *__restrict__ img, int n_img, double kspr
     double tt = scal[kS * g + kTT];
     double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
     double gt = scal[kS * g + kGT] * inv;
-    double fs = weighted ? kspring * (scal[kS * g + kLW] - scal[kS * (g - 1) + kLW])
+    double fs = weighted ? kspring * (lw_g - lw_gm)
                          : kspring * (sqrt(scal[kS * g + kL2]) - sqrt(scal[kS * (g - 1) + kL2]));
     int kind = im.kind >= 0 ? im.kind : (im.nu == ci ? SP_IMAGE_CLIMBING : SP_IMAGE_NORMAL);
     // climbing: tangential component inverted, no spring; falling: the full
     // projected gradient, no spring (descends to a minimum along the path)
     double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : gt + fs);
-    scal[kS * g + kA] = coef * inv;
+    return coef * inv;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
-                                                    rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
-                                                    const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
-                                                    T dth_m, int mode, double *part, unsigned *cnt, double *scal)
+__global__ void k_g_coef(const ImgInfo *__restrict__ img, int n_img, double kspring, int climbing, int weighted,
+                         double *scal)
 {
-    BlkInfo bi = blk[blockIdx.x];
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_img) return;
+    ImgInfo im = img[g];
+    if (im.nu == 0 || im.nu == im.M - 1) return;
+    scal[kS * g + kA] = force_coef(im, g, kspring, climbing, weighted, scal, weighted ? scal[kS * g + kLW] : 0.0,
+                                   weighted ? scal[kS * (g - 1) + kLW] : 0.0);
+}
+
+// Coefficients of the force pass when computed in place (persistent kernel).
+struct CoefArgs {
+    double kspring, w;
+    int climbing, weighted;
+};
+
+template <typename T, bool LOCALC, typename R>
+__device__ __forceinline__ void g_force_body(int vb, const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                             R *v, R *F, const R *G, const R *Tau, T dth_m, int mode, double *part,
+                                             unsigned *cnt, double *scal, CoefArgs ca)
+{
+    BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
-    // the image's force is -G + a Tau (a from k_g_coef)
+    // the image's force is -G + a Tau (a from k_g_coef, or computed here from
+    // the same slots by the same function)
     __shared__ T s_a;
-    if (threadIdx.x == 0) s_a = (T)scal[kS * bi.g + kA];
+    if (threadIdx.x == 0) {
+        if (LOCALC) {
+            double lw = 0, lwm = 0;
+            if (ca.weighted) {
+                lw = segment_of(scal, bi.g, ca.w);
+                lwm = segment_of(scal, bi.g - 1, ca.w);
+            }
+            s_a = (T)force_coef(im, bi.g, ca.kspring, ca.climbing, ca.weighted, scal, lw, lwm);
+        } else {
+            s_a = (T)scal[kS * bi.g + kA];
+        }
+    }
     __syncthreads();
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
@@ -505,17 +577,24 @@ __global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ 
         r[1] = acc_dot(Fn, Fn);
         r[2] = r[1];  // max |F|^2; the image's max |F| is its square root
     }
-    image_reduce<3>(r, 4u, part, blockIdx.x, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kVF, ProjectionPost());
+    image_reduce<3>(r, 4u, part, vb, im.blk0, im.bpi, cnt + bi.g, scal + kS * bi.g + kVF, ProjectionPost());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_force(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                    rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ F,
+                                                    const rec_t<T> *__restrict__ G, const rec_t<T> *__restrict__ Tau,
+                                                    T dth_m, int mode, double *part, unsigned *cnt, double *scal)
+{
+    g_force_body<T, false>(blockIdx.x, blk, img, v, F, G, Tau, dth_m, mode, part, cnt, scal, CoefArgs{});
 }
 
 // mode 0: move; 1: project then move; 2: project only
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
-                                                   rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
-                                                   const rec_t<T> *__restrict__ F, T dt, T dt2_2m, int mode,
-                                                   const double *scal)
+template <typename T, typename R>
+__device__ __forceinline__ void g_move_body(int vb, const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                            R *x, R *v, const R *F, T dt, T dt2_2m, int mode, const double *scal)
 {
-    BlkInfo bi = blk[blockIdx.x];
+    BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
     __shared__ T s_c;  // projection coefficient of the last force pass
@@ -532,6 +611,111 @@ __global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ b
         vi = ldc(v, p);
     }
     if (mode <= 1) st(x, p, normalised(axpy(dt2_2m, ldc(F, p), axpy(dt, vi, ldc(x, p)))));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_move(const BlkInfo *__restrict__ blk, const ImgInfo *__restrict__ img,
+                                                   rec_t<T> *__restrict__ x, rec_t<T> *__restrict__ v,
+                                                   const rec_t<T> *__restrict__ F, T dt, T dt2_2m, int mode,
+                                                   const double *scal)
+{
+    g_move_body<T>(blockIdx.x, blk, img, x, v, F, dt, dt2_2m, mode, scal);
+}
+
+// ------------------------------------------------------------ persistent GNEB
+// Grid-wide barrier of a cooperative launch, with a bounded wait: the arrival
+// counter *bar only grows (by gridDim.x per barrier; the host zeroes it before
+// the launch).  A block polls at most `limit` times; a block that gives up
+// raises *abort_flag and ORs `site` into status[1] (the context's status word,
+// timeouts), and every block that sees the abort flag while waiting leaves
+// too, so no block waits unboundedly.  Returns false when the kernel must
+// return.
+__device__ bool grid_sync(unsigned *bar, unsigned *abort_flag, unsigned &gen, long long limit, unsigned *status,
+                          unsigned site)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gen += 1;
+        const unsigned target = gen * gridDim.x;
+        __threadfence();  // this block's writes before its arrival
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        long long polls = 0;
+        while (*(volatile unsigned *)bar < target) {
+            if (*(volatile unsigned *)abort_flag) {
+                ok = 0;
+                break;
+            }
+            if (++polls > limit) {
+                ok = 0;
+                atomicExch(abort_flag, 1u);
+                if (status) atomicOr_system(status + 1, site);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();  // the other blocks' writes after the barrier
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T> struct PersistArgs {
+    const BlkInfo *blk;
+    const ImgInfo *img;
+    const Stencil<T> *S;
+    rec_t<T> *x, *v, *F, *G, *Tau;
+    double *part, *scal;
+    unsigned *cnt;
+    T dt, dt2_2m, dth_m;
+    int n_blk, n_iter, first_mode;  // first_mode: move mode of the first iteration (0 or 1)
+    CoefArgs ca;
+    unsigned *bar, *abort_flag, *status;
+    long long limit;
+};
+
+// n_iter GNEB iterations (move, field, tangent, force) of every image of
+// every chain in one cooperative launch: each pass is a grid-stride loop over
+// the block table, the passes are separated by grid barriers, and the
+// per-image tangent weights and force coefficients are computed by each work
+// block from the slots the previous pass filled (the same functions of the
+// same values as the per-pass kernels, so the iterates are bit-identical).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_g_persistent(const __grid_constant__ PersistArgs<T> a)
+{
+    // every spin, velocity and pass buffer is read with plain (coherent)
+    // loads: other blocks wrote them earlier in this launch
+    using R = typename ShRec<T>::type;
+    static_assert(sizeof(R) == sizeof(rec_t<T>), "plain-load records have the record layout");
+    R *x = reinterpret_cast<R *>(a.x), *v = reinterpret_cast<R *>(a.v), *F = reinterpret_cast<R *>(a.F),
+      *G = reinterpret_cast<R *>(a.G), *Tau = reinterpret_cast<R *>(a.Tau);
+    unsigned gen = 0;
+    for (int it = 0; it < a.n_iter; ++it) {
+        const int mode = it == 0 ? a.first_mode : 1;
+        for (int vb = blockIdx.x; vb < a.n_blk; vb += gridDim.x) {
+            g_move_body<T>(vb, a.blk, a.img, x, v, (const R *)F, a.dt, a.dt2_2m, mode, a.scal);
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.abort_flag, gen, a.limit, a.status, 1u)) return;
+        for (int vb = blockIdx.x; vb < a.n_blk; vb += gridDim.x) {
+            g_field_body<T>(vb, a.blk, a.img, a.S, (const R *)x, G, a.part, a.cnt, a.scal);
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.abort_flag, gen, a.limit, a.status, 1u)) return;
+        for (int vb = blockIdx.x; vb < a.n_blk; vb += gridDim.x) {
+            g_tangent_body<T, true>(vb, a.blk, a.img, (const R *)x, (const R *)G, Tau, a.part, a.cnt, a.scal);
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.abort_flag, gen, a.limit, a.status, 1u)) return;
+        for (int vb = blockIdx.x; vb < a.n_blk; vb += gridDim.x) {
+            g_force_body<T, true>(vb, a.blk, a.img, v, F, (const R *)G, (const R *)Tau, a.dth_m, 1, a.part, a.cnt,
+                                  a.scal, a.ca);
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.abort_flag, gen, a.limit, a.status, 1u)) return;
+    }
 }
 
 __global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const double *scal, double *E, double *fmax_out,
@@ -840,6 +1024,31 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     };
     forces(0, st);
     int remaining = a.n_iter;
+    if (remaining > 0 && a.persistent) {
+        // every iteration of the call in one cooperative launch; the barrier
+        // counter, abort flag and the image tickets start at zero (a launch
+        // that gave up may have left tickets behind)
+        if (grow(s->sync, 4 * sizeof(unsigned))) return SP_ERR_CUDA;
+        int dev = 0, nsm = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_g_persistent<T>, kBlock, 0) != cudaSuccess ||
+            per_sm < 1)
+            return SP_ERR_CUDA;
+        int grid = (int)std::min<long long>((long long)nsm * per_sm, n_blk);
+        PersistArgs<T> pa{B, I, Sd, x, v, F, G, Tau, part, scal, cnt, (T)a.dt, (T)dt2_2m, (T)dth_m, n_blk, remaining,
+                          0, CoefArgs{a.k, a.w, a.climbing, weighted}, (unsigned *)s->sync.p,
+                          (unsigned *)s->sync.p + 1, a.status, a.wait_limit > 0 ? a.wait_limit : (1LL << 21)};
+        void *args[] = {&pa};
+        if (cudaMemsetAsync(s->sync.p, 0, 4 * sizeof(unsigned), st) != cudaSuccess ||
+            cudaMemsetAsync(cnt, 0, sizeof(unsigned) * n_img, st) != cudaSuccess ||
+            cudaLaunchCooperativeKernel((const void *)k_g_persistent<T>, dim3(grid), dim3(kBlock), args, 0, st) !=
+                cudaSuccess)
+            return SP_ERR_CUDA;
+        // leave the tickets at zero for the next call whatever happened
+        if (cudaMemsetAsync(cnt, 0, sizeof(unsigned) * n_img, st) != cudaSuccess) return SP_ERR_CUDA;
+        remaining = 0;
+    }
     if (remaining > 0) {
         k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, 0, scal);
         forces(1, st);

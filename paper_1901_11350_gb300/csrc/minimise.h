@@ -21,6 +21,11 @@ struct GnebArgs {
     int climbing, M, n_iter;
     const int *kinds;  // host, one SP_IMAGE_* per image of all chains, or NULL
     double w;          // energy weight of the spring lengths (0: geodesic)
+    // 1: the iterations of a call run in one persistent cooperative launch
+    // (grid barriers between the passes) instead of one launch per pass
+    int persistent = 0;
+    long long wait_limit = 0;   // polls of a grid-barrier wait before it gives up (persistent)
+    unsigned *status = nullptr; // device address of the context's status word (timeouts), or null
 };
 
 template <typename T>

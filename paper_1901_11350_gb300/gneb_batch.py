@@ -63,11 +63,14 @@ def prepare(n_chains=48, seed=4, precision="f32", relax_tol=1e-5, max_attempts=1
     return chains
 
 
-def run_batched(chains, dt=0.1, k_spring=1.0, tol=1e-5, chunk=200, max_iter=200000):
+def run_batched(chains, dt=0.1, k_spring=1.0, tol=1e-5, chunk=200, max_iter=200000, persistent=False):
     """Step all chains together until each max force < tol (chains leave the
-    batch as they converge).  Returns per-chain results and the summed
-    device time of the batched calls (CUDA events on the launching stream)."""
-    dtype = chains[0].ctx.dtype
+    batch as they converge).  persistent: each call's iterations run in one
+    persistent cooperative launch instead of one launch per pass.  Returns
+    per-chain results and the summed device time of the batched calls (CUDA
+    events on the launching stream)."""
+    for ch in chains:
+        ch.ctx.set_option("gneb_persistent", int(bool(persistent)))
     active = list(range(len(chains)))
     state = {}
     for k in active:

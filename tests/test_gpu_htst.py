@@ -86,16 +86,22 @@ def test_htst_single_spin_closed_form():
 
 
 def _converged_collapse_path():
-    # Neel skyrmion on a 9 x 8 periodic hexagonal lattice, relaxed; its
-    # collapse path to the ferromagnet by climbing-image GNEB in FP64
-    g = I.hexagonal(9, 8, periodic=(True, True), mu_s=2.0)
-    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.35], K=[0.08], Khat=[[0, 0, 1]], B=[0, 0, 1.2])
+    # the paper's HTST example in small: an isolated Neel skyrmion with J = 1,
+    # D = 0.6 J (interfacial), B = 4 T, on a 12 x 12 periodic hexagonal
+    # lattice, centred on a site and relaxed (metastable, 4.8 meV above the
+    # ferromagnet); its collapse path by climbing-image GNEB in FP64.  The
+    # minimum has two translational (near-)zero modes, the saddle one
+    # negative mode and no zero mode.
+    g = I.hexagonal(12, 12, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.6], K=[0.0], Khat=[[0, 0, 1]], B=[0, 0, 4.0])
     c = B.Context(g, h, "f64")
     r = I.site_positions(g)
-    sk = c.spins(I.neel_skyrmion(r, r.mean(axis=0), 3.5))
-    it, mt = c.minimise(sk, torch.zeros_like(sk), dt=0.1, tol=1e-10, max_iter=100000, check_every=500)
-    assert mt < 1e-10
-    chain0 = I.slerp_chain(_np(sk), I.ferromagnet(c.N), 9, r, r.mean(axis=0))
+    centre = r[6 * 12 + 6]
+    sk = c.spins(I.neel_skyrmion(r, centre, 2.5, I.SKYRMION_HELICITY))
+    it, mt = c.minimise(sk, torch.zeros_like(sk), dt=0.1, tol=1e-11, max_iter=100000, check_every=500)
+    assert mt < 1e-11
+    assert abs(c.topological_charge(sk).item() + 1) < 1e-6
+    chain0 = I.slerp_chain(_np(sk), I.ferromagnet(c.N), 9, r, centre)
     x = c.spins(chain0)
     v = torch.zeros_like(x)
     for _ in range(400):
@@ -110,13 +116,14 @@ def _converged_collapse_path():
 def test_htst_skyrmion_collapse_matches_oracle():
     g, h, c, nm, ns = _converged_collapse_path()
     o = oracle.System(g, h)
-    zt = 1e-6
+    zt = 1e-5
     r = c.htst(nm, ns, zero_tol=zt)
     ro = o.htst(_np(nm), _np(ns), zero_tol=zt)
-    print("HTST 9x8 skyrmion collapse: dE %.6g meV, Omega0 %.6g, v %.6g, prefactor %.6g, lowest eigenvalues "
+    print("HTST 12x12 skyrmion collapse: dE %.6g meV, Omega0 %.6g, v %.6g, prefactor %.6g, lowest eigenvalues "
           "min %s sad %s" % (r["dE"], r["omega0"], r["v"], r["prefactor"], ro["eig_min"][:3], ro["eig_sad"][:3]))
     assert r["n_neg_sad"] == ro["n_neg_sad"] == 1
     assert r["n_neg_min"] == ro["n_neg_min"] == 0
+    assert r["n_zero_min"] == 2 and r["n_zero_sad"] == 0
     assert (r["n_zero_min"], r["n_zero_sad"]) == (ro["n_zero_min"], ro["n_zero_sad"])
     for k in ("log_det_min", "log_det_sad"):
         assert abs(r[k] - ro[k]) <= 1e-9 * abs(ro[k]) + 1e-9

@@ -107,7 +107,10 @@ def test_vp_fp32_ten_iterations_and_convergence_against_oracle():
     it, mt = c.minimise(x, v, dt=0.1, tol=1e-6, max_iter=40000, check_every=50)
     no, _, ito, mto = o.minimise(n1, dt=0.1, tol=1e-8, max_iter=40000)
     assert mt < 1e-6 and mto < 1e-8
-    e32 = o.energy(_np(x))[0]
+    # the FP32 state as a point on the manifold: its records are unit vectors
+    # only to FP32 rounding, which alone moves the energy by ~1e-8
+    x32 = _np(x)
+    e32 = o.energy(x32 / np.linalg.norm(x32, axis=1, keepdims=True))[0]
     e64 = o.energy(no)[0]
     print("VP FP32 relaxed energy vs oracle: %.3g relative (FP32 %d iterations)" % (abs(e32 - e64) / abs(e64), it))
     assert abs(e32 - e64) <= 1e-8 * abs(e64)
@@ -123,13 +126,18 @@ GNEB_KINDS = {
 
 @pytest.mark.parametrize("kind", list(GNEB_KINDS))
 def test_gneb_fp32_per_iteration_against_oracle(kind):
+    # per iteration: the step (positions, velocities) against the oracle's
+    # step from the same state; the energies and max force the FP32 call
+    # reports against the oracle's on the FP32 call's own new state (the
+    # force at a position moved by dx differs by about |dB/dn| dx, so it is
+    # compared where both evaluate it)
     g, h, chain0 = _chain_case()
     kw = dict(k_spring=1.0, dt=0.1, **GNEB_KINDS[kind])
     o = oracle.System(g, h)
     c = B.Context(g, h, "f32")
     x = c.spins(chain0)
     v = torch.zeros_like(x)
-    worst = 0.0
+    worst = [0.0, 0.0, 0.0, 0.0]
     for k in range(10):
         xs, vs = _np(x), _np(v)
         E, F = c.gneb_step(x, v, n_iter=1, **kw)
@@ -137,10 +145,15 @@ def test_gneb_fp32_per_iteration_against_oracle(kind):
         dx = np.abs(_np(x) - xo).max()
         dv = np.abs(_np(v) - vo).max() / max(1.0, np.abs(vo).max())
         assert dx <= 1e-5 and dv <= 1e-5, (k, dx, dv)
-        assert abs(F.item() - mfo) <= 1e-5 * max(mfo, 1.0)
-        assert np.abs(E.cpu().numpy() - Eo).max() <= 1e-6 * np.abs(Eo).max()
-        worst = max(worst, dx)
-    print("GNEB FP32 (%s) per-iteration max |dn| = %.3g" % (kind, worst))
+        xn = _np(x)
+        Fo, En, _, _ = o.gneb_forces(xn, **kw)
+        mfn = np.linalg.norm(Fo[1:-1], axis=-1).max()
+        dF = abs(F.item() - mfn) / mfn
+        dE = np.abs(E.cpu().numpy() - En).max() / np.abs(En).max()
+        assert dF <= 1e-5 and dE <= 1e-8, (k, dF, dE)
+        worst = [max(a, b) for a, b in zip(worst, (dx, dv, dF, dE))]
+    print("GNEB FP32 (%s) per iteration: max |dn| %.3g, |dv| %.3g, max-force %.3g, energies %.3g relative"
+          % (kind, *worst))
 
 
 def test_gneb_fp32_image_energies_and_forces_on_one_state():
@@ -190,11 +203,19 @@ def test_gneb_fp32_full_size_chain_against_oracle():
 
 
 def test_gneb_fp32_converged_barrier_against_oracle():
-    # a small skyrmion-collapse chain converged by the FP32 path and by the
-    # oracle to 1e-5 meV/rad: the barriers (FP64 re-evaluation of the FP32
-    # chain's image energies) agree
-    g, h, chain0 = _chain_case()
+    # a small skyrmion-collapse chain (a metastable Neel skyrmion on a 12 x 12
+    # periodic hexagonal lattice, J = 1, D = 0.6, B = 4 T, relaxed by the
+    # oracle) converged by the FP32 path and by the oracle to 1e-5 meV/rad:
+    # the barriers (FP64 re-evaluation of the FP32 chain's image energies)
+    # agree
+    g = I.hexagonal(12, 12, periodic=(True, True), mu_s=2.0)
+    h = dict(J=[1.0], dmi_kind="interfacial", D=[0.6], K=[0.0], Khat=[[0, 0, 1]], B=[0, 0, 4.0])
     o = oracle.System(g, h)
+    r = I.site_positions(g)
+    centre = r[6 * 12 + 6]
+    sk, _, _, mt = o.minimise(I.neel_skyrmion(r, centre, 2.5, I.SKYRMION_HELICITY), dt=0.1, tol=1e-10,
+                              max_iter=100000)
+    chain0 = _f32(I.slerp_chain(sk, I.ferromagnet(o.N), 9, r, centre))
     c = B.Context(g, h, "f32")
     x = c.spins(chain0)
     v = torch.zeros_like(x)
