@@ -269,6 +269,23 @@ int sp_llg_step(sp_ctx *ctx, void *n_dev, const sp_llg_params *p, int n_steps, v
 int sp_llg_step_replicas(sp_ctx *ctx, void *spins_dev, int n_rep, const double *T, const sp_llg_params *p,
                          int n_steps, void *stream);
 
+/* n_steps LLG steps of n_sys systems of different lattices and Hamiltonians
+ * at once (the stochastic LLG of Eq. 3-4, Appendix B): system k, described
+ * by ctxs[k] (all of one precision, no dipole term), holds its N_k records at
+ * record offset offsets[k] of ONE device buffer spins_dev (systems must not
+ * overlap), sits at temperature T[k] (K, host array; p->T is ignored) and
+ * draws its thermal field from stream p->replica + k.  Every pass is one
+ * launch over all systems (a table of (system, block of 256 spins));
+ * each system's result is, bit for bit, the one sp_llg_step gives it alone
+ * with the neighbour-list kernels (SP_OPT_GENERIC_STENCIL = 1,
+ * SP_OPT_SMALL_PATH = 0) at T[k] and replica p->replica + k.  Solvers
+ * Depondt, Heun and SIB (RK4: SP_ERR_UNSUPPORTED).  Scratch (2 records per
+ * spin of the buffer) and tables belong to ctxs[0]; a call with a new batch
+ * layout uploads the tables and synchronises `stream`.  The spin state is
+ * checked for non-finite values afterwards (the status word of ctxs[0]). */
+int sp_llg_step_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, const long long *offsets, const double *T,
+                      const sp_llg_params *p, int n_steps, void *stream);
+
 /* ------------------------------------------------------------------------
  * Energy minimisation (Appendix D)
  * ------------------------------------------------------------------------ */

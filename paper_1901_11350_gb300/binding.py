@@ -104,6 +104,8 @@ SIGNATURES = {
     "sp_llg_step": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
     "sp_llg_step_replicas": (_i, [_vp, _vp, _i, C.POINTER(_d), C.POINTER(LLGParams), _i, _vp]),
     "sp_sample": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "sp_llg_step_batch": (_i, [C.POINTER(_vp), _i, _vp, C.POINTER(C.c_longlong), C.POINTER(_d), C.POINTER(LLGParams),
+                              _i, _vp]),
     "sp_minimise": (_i, [_vp, _vp, _vp, _d, _d, _d, _i, _i, C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_gneb_step": (_i, [_vp, _vp, _vp, _i, C.POINTER(GNEBParams), _i, _vp, _vp, _vp]),
     "sp_gneb_batch_step": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
@@ -463,6 +465,29 @@ def gneb_batch_step(ctxs, chains, vel, offsets, n_images, n_iter=1, k_spring=1.0
     if rc:
         raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
     return E, F
+
+
+def llg_step_batch(ctxs, spins, offsets, T, n_steps=1, solver="heun", dt=1e-3, alpha=0.1, seed=0, step0=0,
+                   replica=0):
+    """LLG steps of many systems of different lattices (one context each)
+    together; `spins` is one flat CUDA tensor of 4-wide records, system k
+    starting at record offsets[k], at temperature T[k] on the thermal stream
+    replica + k."""
+    L = lib()
+    n = len(ctxs)
+    dtype = ctxs[0].dtype
+    if not (spins.is_cuda and spins.dtype == dtype and spins.is_contiguous() and spins.shape[-1] == 4):
+        raise ValueError("spins must be a contiguous CUDA %s tensor of 4-wide records" % dtype)
+    if len(T) != n or len(offsets) != n:
+        raise ValueError("one offset and one temperature per system")
+    handles = (C.c_void_p * n)(*[c._h for c in ctxs])
+    offs = (C.c_longlong * n)(*[int(x) for x in offsets])
+    Th = (C.c_double * n)(*[float(t) for t in T])
+    p = LLGParams(SOLVER[solver], float(dt), float(alpha), 0.0, int(seed), int(step0), int(replica))
+    rc = L.sp_llg_step_batch(handles, n, _ptr(spins), offs, Th, C.byref(p), int(n_steps), _stream())
+    if rc:
+        raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
+    return spins
 
 
 def minimise_batch(ctxs, spins, vel, offsets, dt=0.1, mass=1.0, tol=1e-6, max_iter=10000, check_every=64):

@@ -561,6 +561,68 @@ int replicas_run(sp_ctx *c, void *n, const sp_llg_params *p, int n_steps, cudaSt
     return SP_OK;
 }
 
+// n_steps steps of n_sys systems of (possibly) different lattices, system k
+// (context ctxs[k]) at records spin0[k] at temperature temps[k] on the
+// thermal stream p->replica + k: one launch per pass for all of them.
+template <typename T>
+int llg_batch_run(sp_ctx *const *ctxs, int n_sys, void *spins, const long long *spin0, const double *temps,
+                  const sp_llg_params *p, int n_steps, cudaStream_t st)
+{
+    sp_ctx *c0 = ctxs[0];
+    std::vector<Stencil<T>> sten(n_sys);
+    std::vector<LlgSys<T>> sys(n_sys);
+    std::vector<int2> blk;
+    long long total = 0;
+    bool hot = false;
+    for (int k = 0; k < n_sys; ++k) {
+        sp_ctx *c = ctxs[k];
+        sten[k] = *(const Stencil<T> *)(c->prec == SP_F64 ? (const void *)&c->Sd : (const void *)&c->Sf);
+        LlgSys<T> s{};
+        s.spin0 = spin0[k];
+        s.N = c->N;
+        s.replica = p->replica + (uint32_t)k;
+        for (int b = 0; b < c->nb; ++b) {  // as llg_const does for one lattice
+            double mu = c->mu_s[b] * kMuB;
+            s.cA[b] = (T)(-kGamma / ((1.0 + p->alpha * p->alpha) * mu));
+            s.sig[b] = (T)std::sqrt(2.0 * p->alpha * kBoltzmann * temps[k] * mu / (kGamma * p->dt));
+        }
+        sys[k] = s;
+        for (int t = 0; t < blocks_for(c->N); ++t) blk.push_back(make_int2(k, t));
+        total = std::max(total, spin0[k] + (long long)c->N);
+        hot = hot || temps[k] > 0;
+    }
+    int rc = ensure(c0, c0->pred, 2 * sizeof(rec_t<T>) * (size_t)total);
+    if (rc) return rc;
+    size_t sb = sizeof(Stencil<T>) * n_sys, yb = sizeof(LlgSys<T>) * n_sys, bb = sizeof(int2) * blk.size();
+    size_t o1 = (sb + 255) / 256 * 256, o2 = o1 + (yb + 255) / 256 * 256;
+    std::vector<char> key(o2 + bb);
+    std::memcpy(key.data(), sten.data(), sb);
+    std::memcpy(key.data() + o1, sys.data(), yb);
+    std::memcpy(key.data() + o2, blk.data(), bb);
+    if (key != c0->lb_key) {
+        if ((rc = ensure(c0, c0->lb_tab, key.size()))) return rc;
+        cudaError_t e = cudaMemcpyAsync(c0->lb_tab.p, key.data(), key.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host copy is freed on return
+        if (e != cudaSuccess) return cuda_fail(c0, e, "batch tables");
+        c0->lb_key.swap(key);
+    }
+    const char *tab = (const char *)c0->lb_tab.p;
+    const Stencil<T> *Sv = (const Stencil<T> *)tab;
+    const LlgSys<T> *Y = (const LlgSys<T> *)(tab + o1);
+    const int2 *B = (const int2 *)(tab + o2);
+    rec_t<T> *nn = (rec_t<T> *)spins, *np = (rec_t<T> *)c0->pred.p, *q = np + total;
+    LlgConst<T> k = llg_const<T>(c0, p);  // dt, alpha, seed round keys; the rest per system
+    k.thermal = (hot && p->alpha > 0) ? 1 : 0;
+    const int nblk = (int)blk.size();
+    for (int s = 0; s < n_steps; ++s) {
+        k.step = p->step0 + (uint64_t)s;
+        cudaError_t e = launch_llg_batch<T>(0, p->solver, nblk, B, Sv, Y, nn, np, q, k, st);
+        if (e == cudaSuccess) e = launch_llg_batch<T>(1, p->solver, nblk, B, Sv, Y, nn, np, q, k, st);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "batched LLG launch");
+    }
+    return SP_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -726,6 +788,7 @@ int sp_destroy(sp_ctx *c)
     if (c->qbuf.p) cudaFree(c->qbuf.p);
     if (c->rsig.p) cudaFree(c->rsig.p);
     if (c->step_ctr.p) cudaFree(c->step_ctr.p);
+    if (c->lb_tab.p) cudaFree(c->lb_tab.p);
     if (c->status_h) cudaFreeHost(c->status_h);
     for (auto &g : c->lg_graphs) cudaGraphExecDestroy(g.exec);
     if (c->lg_stream) cudaStreamDestroy(c->lg_stream);
@@ -940,6 +1003,45 @@ int sp_llg_step_replicas(sp_ctx *c, void *spins_dev, int n_rep, const double *T,
                                : replicas_run<float>(c, spins_dev, p, n_steps, st, n_rep, T);
     }
     return rc ? rc : status_check_records(c, spins_dev, (long)n_rep * c->N, SITE_STATE, st);
+}
+
+int sp_llg_step_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, const long long *offsets, const double *T,
+                      const sp_llg_params *p, int n_steps, void *stream)
+{
+    if (!ctxs || n_sys < 1 || !ctxs[0]) return SP_ERR_ARG;
+    sp_ctx *c0 = ctxs[0];
+    int rc = status_enter(c0);
+    if (rc) return rc;
+    if (!offsets || !T || !p) return fail(c0, SP_ERR_ARG, "NULL batch argument");
+    if ((rc = check_spins(c0, spins_dev, "spins"))) return rc;
+    if (p->solver != SP_DEPONDT && p->solver != SP_HEUN && p->solver != SP_SIB)
+        return fail(c0, p->solver == SP_RK4 ? SP_ERR_UNSUPPORTED : SP_ERR_ARG,
+                    "batched LLG steps take the Depondt, Heun or SIB solver");
+    if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(c0, SP_ERR_ARG, "dt must be positive");
+    if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return fail(c0, SP_ERR_ARG, "alpha must be >= 0");
+    if (n_steps < 0) return fail(c0, SP_ERR_ARG, "n_steps must be >= 0");
+    if ((unsigned long long)p->replica + (unsigned long long)n_sys > (1ULL << 29))
+        return fail(c0, SP_ERR_ARG, "thermal streams replica .. replica + n_sys - 1 must stay below 2^29");
+    std::vector<std::pair<long long, long long>> spans;
+    for (int k = 0; k < n_sys; ++k) {
+        sp_ctx *c = ctxs[k];
+        if (!c) return fail(c0, SP_ERR_ARG, "NULL context for system %d", k);
+        if (!c->have_geom || !c->have_ham) return fail(c0, SP_ERR_STATE, "system %d: context not configured", k);
+        if (c->prec != c0->prec) return fail(c0, SP_ERR_ARG, "system %d: precision differs from system 0", k);
+        if (c->h.dipole != SP_DIPOLE_NONE) return fail(c0, SP_ERR_UNSUPPORTED, "system %d: dipole term", k);
+        if (!(T[k] >= 0) || !std::isfinite(T[k])) return fail(c0, SP_ERR_ARG, "system %d: T must be >= 0", k);
+        if (offsets[k] < 0 || offsets[k] + c->N >= (1LL << 31)) return fail(c0, SP_ERR_ARG, "system %d: bad offset", k);
+        spans.push_back({offsets[k], offsets[k] + c->N});
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t k = 1; k < spans.size(); ++k)
+        if (spans[k].first < spans[k - 1].second) return fail(c0, SP_ERR_ARG, "systems overlap in the batch buffer");
+    if (n_steps == 0) return SP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = c0->prec == SP_F64 ? llg_batch_run<double>(ctxs, n_sys, spins_dev, offsets, T, p, n_steps, st)
+                            : llg_batch_run<float>(ctxs, n_sys, spins_dev, offsets, T, p, n_steps, st);
+    if (rc) return rc;
+    return status_check_records(c0, spins_dev, (long)spans.back().second, SITE_STATE, st);
 }
 
 int sp_minimise(sp_ctx *c, void *n_dev, void *v_dev, double dt, double mass, double tol, int max_iter, int check_every,
@@ -1276,7 +1378,8 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         *value = c->wait_limit;
         return SP_OK;
     case SP_OPT_SCRATCH_KIB: {
-        size_t b = c->pred.bytes + c->partials.bytes + c->bdd.bytes + c->qbuf.bytes + c->rsig.bytes + c->step_ctr.bytes;
+        size_t b = c->pred.bytes + c->partials.bytes + c->bdd.bytes + c->qbuf.bytes + c->rsig.bytes + c->step_ctr.bytes +
+               c->lb_tab.bytes;
         *value = (int)std::min<size_t>((b + 1023) / 1024, 0x7fffffff);
         return SP_OK;
     }

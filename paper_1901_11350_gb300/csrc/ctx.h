@@ -133,6 +133,8 @@ struct sp_ctx {
     DevBuf rsig;      // noise amplitudes of the last batch of replicas
     std::vector<double> rsig_key;  // what they were computed from
     DevBuf step_ctr;               // Philox step base of replayed replica graphs
+    DevBuf lb_tab;                 // tables of the last batch of lattices (sp_llg_step_batch)
+    std::vector<char> lb_key;      // what they were built from
     std::vector<LlgGraph> lg_graphs;
     cudaStream_t lg_stream = nullptr;  // capture stream of those graphs
     // device status word (mapped pinned host memory, allocated on first use;

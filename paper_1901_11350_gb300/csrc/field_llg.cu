@@ -129,6 +129,82 @@ __global__ void __launch_bounds__(kBlock) k_llg_corr(const __grid_constant__ Ste
     corr_spin<T, SOLVER>(S, n + o, np + o, q + o, Bdd, c, i);
 }
 
+// A batch of different lattices: each block belongs to one system, whose
+// constants (prefactors, noise amplitudes, thermal stream) the block takes
+// into a shared-memory copy of the common constants; then the per-spin
+// bodies of the single-lattice kernels run unchanged, so every system gets
+// the result a call on it alone gives.
+template <typename T>
+__device__ __forceinline__ const LlgConst<T> &batch_const(const LlgConst<T> &c, const LlgSys<T> &s)
+{
+    __shared__ LlgConst<T> cs;
+    if (threadIdx.x == 0) {
+        cs = c;
+        for (int b = 0; b < SP_MAX_BASIS; ++b) {
+            cs.cA[b] = s.cA[b];
+            cs.sig[b] = s.sig[b];
+        }
+        cs.replica = s.replica;
+        cs.rsig = nullptr;
+        cs.n_rep = 0;
+    }
+    __syncthreads();
+    return cs;
+}
+
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_bpred(const int2 *__restrict__ blk, const Stencil<T> *__restrict__ Sv,
+                                                      const LlgSys<T> *__restrict__ sys, const rec_t<T> *__restrict__ n,
+                                                      rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
+                                                      const LlgConst<T> c)
+{
+    allow_dependents();
+    wait_prerequisite();  // n comes from the kernels before
+    const int2 bt = blk[blockIdx.x];
+    const LlgConst<T> &cs = batch_const(c, sys[bt.x]);
+    const Stencil<T> &S = Sv[bt.x];
+    int i = bt.y * kBlock + threadIdx.x;
+    if (i >= S.N) return;
+    size_t o = (size_t)sys[bt.x].spin0;
+    pred_spin<T, SOLVER>(S, n + o, (const rec_t<T> *)nullptr, np + o, q + o, cs, i, 0);
+}
+
+template <typename T, int SOLVER>
+__global__ void __launch_bounds__(kBlock) k_llg_bcorr(const int2 *__restrict__ blk, const Stencil<T> *__restrict__ Sv,
+                                                      const LlgSys<T> *__restrict__ sys, rec_t<T> *__restrict__ n,
+                                                      const rec_t<T> *__restrict__ np, const rec_t<T> *__restrict__ q,
+                                                      const LlgConst<T> c)
+{
+    allow_dependents();
+    wait_prerequisite();  // np, q come from the kernels before
+    const int2 bt = blk[blockIdx.x];
+    const LlgConst<T> &cs = batch_const(c, sys[bt.x]);
+    const Stencil<T> &S = Sv[bt.x];
+    int i = bt.y * kBlock + threadIdx.x;
+    if (i >= S.N) return;
+    size_t o = (size_t)sys[bt.x].spin0;
+    corr_spin<T, SOLVER>(S, n + o, np + o, q + o, (const rec_t<T> *)nullptr, cs, i);
+}
+
+template <typename T>
+cudaError_t launch_llg_batch(int pass, int solver, int n_blk, const int2 *blk, const Stencil<T> *Sv,
+                             const LlgSys<T> *sys, rec_t<T> *n, rec_t<T> *np, rec_t<T> *q, const LlgConst<T> &c,
+                             cudaStream_t st)
+{
+    if (n_blk <= 0) return cudaSuccess;
+    dim3 g(n_blk), b(kBlock);
+    if (pass == 0) {
+        if (solver == SP_HEUN) return launch_pdl(k_llg_bpred<T, SP_HEUN>, g, b, 0, st, blk, Sv, sys, (const rec_t<T> *)n, np, q, c);
+        if (solver == SP_SIB) return launch_pdl(k_llg_bpred<T, SP_SIB>, g, b, 0, st, blk, Sv, sys, (const rec_t<T> *)n, np, q, c);
+        return launch_pdl(k_llg_bpred<T, SP_DEPONDT>, g, b, 0, st, blk, Sv, sys, (const rec_t<T> *)n, np, q, c);
+    }
+    if (solver == SP_HEUN)
+        return launch_pdl(k_llg_bcorr<T, SP_HEUN>, g, b, 0, st, blk, Sv, sys, n, (const rec_t<T> *)np, (const rec_t<T> *)q, c);
+    if (solver == SP_SIB)
+        return launch_pdl(k_llg_bcorr<T, SP_SIB>, g, b, 0, st, blk, Sv, sys, n, (const rec_t<T> *)np, (const rec_t<T> *)q, c);
+    return launch_pdl(k_llg_bcorr<T, SP_DEPONDT>, g, b, 0, st, blk, Sv, sys, n, (const rec_t<T> *)np, (const rec_t<T> *)q, c);
+}
+
 // Small FP32 lattices (N <= kSmallMax): one CTA keeps n, np and q in shared
 // memory and runs every step in the kernel, a CTA barrier between the passes
 // -- the same per-spin arithmetic as the two grid kernels, without 2 launches
@@ -434,7 +510,9 @@ cudaError_t launch_check_doubles(const double *v, long n_val, unsigned *flag, un
                                              rec_t<T> *, const rec_t<T> *, const LlgConst<T> &, cudaStream_t);         \
     template cudaError_t launch_energy<T>(const Stencil<T> &, const rec_t<T> *, const rec_t<T> *, double *, double *,   \
                                           double *, cudaStream_t);                                            \
-    template cudaError_t launch_check_records<T>(const rec_t<T> *, long, unsigned *, unsigned, cudaStream_t);
+    template cudaError_t launch_check_records<T>(const rec_t<T> *, long, unsigned *, unsigned, cudaStream_t);      \
+    template cudaError_t launch_llg_batch<T>(int, int, int, const int2 *, const Stencil<T> *, const LlgSys<T> *,       \
+                                             rec_t<T> *, rec_t<T> *, rec_t<T> *, const LlgConst<T> &, cudaStream_t);
 SPGB_INST(float)
 SPGB_INST(double)
 

@@ -61,6 +61,17 @@ template <typename T> __device__ __forceinline__ uint4 thermal_bits(const LlgCon
     return thermal_bits_at(c, llg_step_of(c), i, r);
 }
 
+// One system of a batch of different lattices stepped together
+// (sp_llg_step_batch): its first record, size, thermal stream and per-basis
+// LLG prefactors and noise amplitudes (computed on the host in FP64, as for a
+// single call).
+template <typename T> struct LlgSys {
+    long long spin0;
+    int N;
+    uint32_t replica;
+    T cA[SP_MAX_BASIS], sig[SP_MAX_BASIS];
+};
+
 constexpr int kBlock = 256;
 // single-CTA LLG path for small FP32 lattices: threads of the CTA, largest
 // lattice (3 records of 16 B per spin in shared memory: 96 KB)
@@ -105,6 +116,15 @@ cudaError_t launch_energy(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T>
 // projected onto the tangent planes first).
 template <typename T>
 cudaError_t launch_hvp(const Stencil<T> &S, const rec_t<T> *n, const rec_t<T> *v, rec_t<T> *out, cudaStream_t st);
+
+// One pass (0 predictor, 1 corrector) of a batch of systems: blk[b] = (system,
+// block of kBlock spins in it), Sv[k] and sys[k] per system, the records of
+// system k at sys[k].spin0 in n, np and q; c holds what all share (dt,
+// alpha, seed, step, thermal flag).
+template <typename T>
+cudaError_t launch_llg_batch(int pass, int solver, int n_blk, const int2 *blk, const Stencil<T> *Sv,
+                             const LlgSys<T> *sys, rec_t<T> *n, rec_t<T> *np, rec_t<T> *q, const LlgConst<T> &c,
+                             cudaStream_t st);
 
 // Finiteness check of results (the device status word): records n[0..n_rec)
 // (x, y, z; the padding lane is not looked at) or plain doubles v[0..n_val);
