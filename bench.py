@@ -390,7 +390,24 @@ def gneb_result(args, compact=False):
     chains = G.prepare(n_chains=args.chains, seed=4, precision="f32")
     prep_s = time.perf_counter() - t0
     kw = dict(dt=0.2, k_spring=1.0, tol=1e-5, chunk=args.gneb_chunk)
-    pk = dict(persistent=bool(args.gneb_persistent))
+    tune = None
+    if args.gneb_persistent < 0:
+        # launch mode of the batched iterations chosen by the autotuner on
+        # the full batch (one launch per pass, or the persistent kernel)
+        from paper_1901_11350_gb300 import binding as Bd
+        offs, Ms, off = [], [], 0
+        for ch in chains:
+            offs.append(off)
+            Ms.append(ch.M)
+            off += ch.M * ch.N
+        x = torch.cat([ch.ctx.spins(ch.chain0).reshape(-1, 4) for ch in chains])
+        choice, t0_ms, t1_ms = Bd.gneb_batch_autotune([ch.ctx for ch in chains], x, torch.zeros_like(x), offs, Ms,
+                                                      n_trial=16, k_spring=kw["k_spring"], dt=kw["dt"])
+        tune = {"per_pass_ms": t0_ms, "persistent_ms": t1_ms, "trial_iterations": 16}
+        del x
+        pk = dict(persistent=bool(choice))
+    else:
+        pk = dict(persistent=bool(args.gneb_persistent))
     G.run_batched(chains[:2], **dict(kw, chunk=10, tol=0.0, max_iter=10), **pk)  # warm-up (graph, tables)
     state, batch_s = G.run_batched(chains, **kw, **pk)
     if args.gneb_no_reference:  # profiling aid: the batched run alone
@@ -415,6 +432,7 @@ def gneb_result(args, compact=False):
            "higher_is_better": False, "dtype": "f32 forces, f64 energies", "data": "synthetic",
            "config": {"workload": "gneb%d_skyrmion_collapse" % len(chains), "chains": len(chains),
                       "launch": "persistent" if pk["persistent"] else "per pass (CUDA graph)",
+                      "launch_autotune": tune,
                       "spins_all_images": spins, "images": [c.M for c in chains],
                       "sides": [c.draw["L"] for c in chains], "redraws": sum(c.draw["attempt"] for c in chains),
                       "dt": kw["dt"], "k_spring": kw["k_spring"], "check_every": kw["chunk"]},
@@ -1078,8 +1096,9 @@ def main():
     ap.add_argument("--chains", type=int, default=48)
     ap.add_argument("--gneb-chunk", type=int, default=50)
     ap.add_argument("--gneb-no-reference", action="store_true", help="gneb48: skip the FP64 per-chain loop (profiling aid)")
-    ap.add_argument("--gneb-persistent", type=int, default=0, choices=[0, 1],
-                    help="gneb48: 1 = one persistent cooperative launch per call instead of one launch per pass")
+    ap.add_argument("--gneb-persistent", type=int, default=-1, choices=[-1, 0, 1],
+                    help="gneb48: 1 = one persistent cooperative launch per call, 0 = one launch per pass, "
+                         "-1 (default) = chosen by the autotuner")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
     ap.add_argument("--no-relax", action="store_true",
                     help="sc128: skip the relaxation half of the metric (GNEB batch, warm start)")

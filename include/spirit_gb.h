@@ -650,6 +650,20 @@ int sp_set_option(sp_ctx *ctx, int option, int value);
 int sp_autotune(sp_ctx *ctx, const void *n_dev, int *chosen, void *stream);
 int sp_get_option(const sp_ctx *ctx, int option, int *value);
 
+/* Choose by measurement how sp_gneb_batch_step runs a batch: for the batch
+ * described as in sp_gneb_batch_step, runs a warm-up call and then n_trial
+ * (>= 1) iterations with one launch per pass and with the persistent kernel,
+ * each from device copies of chains_dev and vel_dev (the caller's buffers
+ * are not changed; the copies are allocated and freed by this call), timed
+ * with CUDA events on `stream`, and sets SP_OPT_GNEB_PERSISTENT of ctxs[0]
+ * to the faster.  *persistent (host, may be NULL) receives the choice, ms
+ * (host, may be NULL, 2 doubles) the two times in ms.  Synchronises `stream`;
+ * a trial that met a non-finite value or a timed-out wait returns that
+ * error. */
+int sp_gneb_batch_autotune(sp_ctx *const *ctxs, int n_chains, const void *chains_dev, const void *vel_dev,
+                           const long long *offsets, const int *n_images, const sp_gneb_params *p, int n_trial,
+                           int *persistent, double *ms, void *stream);
+
 /* ------------------------------------------------------------------------
  * Kernel timing (tracing aid, not part of the method)
  * ------------------------------------------------------------------------ */

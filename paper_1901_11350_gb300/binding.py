@@ -121,6 +121,8 @@ SIGNATURES = {
     "sp_minimise_batch": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), _d, _d, _d, _i, _i,
                               C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_llg_step_static": (_i, [_vp, _vp, C.POINTER(LLGParams), _i, _vp]),
+    "sp_gneb_batch_autotune": (_i, [C.POINTER(_vp), _i, _vp, _vp, C.POINTER(C.c_longlong), C.POINTER(_i),
+                                   C.POINTER(GNEBParams), _i, C.POINTER(_i), C.POINTER(_d), _vp]),
     "sp_set_option": (_i, [_vp, _i, _i]),
     "sp_get_option": (_i, [_vp, _i, C.POINTER(_i)]),
     "sp_autotune": (_i, [_vp, _vp, C.POINTER(_i), _vp]),
@@ -488,6 +490,26 @@ def llg_step_batch(ctxs, spins, offsets, T, n_steps=1, solver="heun", dt=1e-3, a
     if rc:
         raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
     return spins
+
+
+def gneb_batch_autotune(ctxs, chains, vel, offsets, n_images, n_trial=16, k_spring=1.0, climbing=True, dt=0.1,
+                        mass=1.0, image_types=None, energy_weight=0.0):
+    """Time the batch with one launch per pass and with the persistent kernel
+    (on copies; the tensors are not changed) and keep the faster on
+    ctxs[0].  Returns (persistent, ms_per_pass, ms_persistent)."""
+    L = lib()
+    n = len(ctxs)
+    handles = (C.c_void_p * n)(*[c._h for c in ctxs])
+    offs = (C.c_longlong * n)(*[int(x) for x in offsets])
+    ims = (C.c_int * n)(*[int(x) for x in n_images])
+    p, _keep = gneb_params(dt, mass, k_spring, climbing, image_types, energy_weight)
+    choice = C.c_int()
+    ms = (C.c_double * 2)()
+    rc = L.sp_gneb_batch_autotune(handles, n, _ptr(chains), _ptr(vel), offs, ims, C.byref(p), int(n_trial),
+                                  C.byref(choice), ms, _stream())
+    if rc:
+        raise SpinError(rc, L.sp_last_error(ctxs[0]._h).decode())
+    return choice.value, ms[0], ms[1]
 
 
 def minimise_batch(ctxs, spins, vel, offsets, dt=0.1, mass=1.0, tol=1e-6, max_iter=10000, check_every=64):

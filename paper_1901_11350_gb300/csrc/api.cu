@@ -1292,6 +1292,68 @@ int sp_sync_status(sp_ctx *c)
     return status_take(c);
 }
 
+int sp_gneb_batch_autotune(sp_ctx *const *ctxs, int n_chains, const void *chains_dev, const void *vel_dev,
+                           const long long *offsets, const int *n_images, const sp_gneb_params *p, int n_trial,
+                           int *persistent, double *ms, void *stream)
+{
+    if (!ctxs || n_chains < 1 || !ctxs[0]) return SP_ERR_ARG;
+    sp_ctx *c0 = ctxs[0];
+    if (!offsets || !n_images || !p || !chains_dev || !vel_dev) return fail(c0, SP_ERR_ARG, "NULL batch description");
+    if (n_trial < 1) return fail(c0, SP_ERR_ARG, "n_trial must be >= 1");
+    long long total = 0, n_img = 0;
+    for (int k = 0; k < n_chains; ++k) {
+        if (!ctxs[k] || !ctxs[k]->have_geom) return fail(c0, SP_ERR_STATE, "chain %d: context not configured", k);
+        total = std::max(total, offsets[k] + (long long)n_images[k] * ctxs[k]->N);
+        n_img += n_images[k];
+    }
+    const size_t bytes = rec_bytes(c0) * (size_t)std::max(total, 1LL);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *x = nullptr, *v = nullptr;
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int keep = c0->gneb_persistent, rc = SP_OK;
+    double t[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&x, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&v, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(double) * (size_t)(n_img + n_chains));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // each mode: a warm-up call, then n_trial iterations timed, both from
+    // copies of the caller's chains and velocities
+    for (int mode = 0; mode < 2 && e == cudaSuccess && rc == SP_OK; ++mode) {
+        c0->gneb_persistent = mode;
+        for (int pass = 0; pass < 2 && e == cudaSuccess && rc == SP_OK; ++pass) {
+            e = cudaMemcpyAsync(x, chains_dev, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(v, vel_dev, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) break;
+            rc = sp_gneb_batch_step(ctxs, n_chains, x, v, offsets, n_images, p, pass ? n_trial : 2, out, out + n_img,
+                                    stream);
+            if (rc == SP_OK) e = cudaEventRecord(e1, st);
+            if (rc == SP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float f = 0;
+            if (rc == SP_OK && e == cudaSuccess && pass) e = cudaEventElapsedTime(&f, e0, e1);
+            t[mode] = f;
+        }
+    }
+    c0->gneb_persistent = keep;
+    if (x) cudaFree(x);
+    if (v) cudaFree(v);
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(c0, e, "GNEB batch autotune");
+    if ((rc = status_enter(c0))) return rc;  // a trial that timed out or met a non-finite value
+    c0->gneb_persistent = t[1] < t[0] ? 1 : 0;
+    if (persistent) *persistent = c0->gneb_persistent;
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    return SP_OK;
+}
+
 int sp_set_option(sp_ctx *c, int option, int value)
 {
     if (!c) return SP_ERR_ARG;

@@ -120,3 +120,22 @@ def test_single_chain_call_takes_the_persistent_kernel_too():
         res.append((x, v, E, F))
     for a, b in zip(res[0], res[1]):
         assert torch.equal(a, b)
+
+
+def test_autotune_picks_a_launch_mode_and_leaves_the_chains_alone():
+    chains = _chains()
+    ctxs = [B.Context(g, h, "f32") for g, h, _ in chains]
+    offs, Ms, off = [], [], 0
+    for (_, _, ch0) in chains:
+        offs.append(off)
+        Ms.append(ch0.shape[0])
+        off += ch0.shape[0] * ch0.shape[1]
+    x = torch.cat([c.spins(ch0).reshape(-1, 4) for c, (_, _, ch0) in zip(ctxs, chains)])
+    v = torch.zeros_like(x)
+    x0, v0 = x.clone(), v.clone()
+    choice, t_pass, t_pers = B.gneb_batch_autotune(ctxs, x, v, offs, Ms, n_trial=20, k_spring=0.7, dt=0.1)
+    print("GNEB batch autotune: per pass %.3f ms, persistent %.3f ms -> %s" % (
+        t_pass, t_pers, "persistent" if choice else "per pass"))
+    assert torch.equal(x, x0) and torch.equal(v, v0)
+    assert choice == (1 if t_pers < t_pass else 0) == ctxs[0].get_option("gneb_persistent")
+    assert t_pass > 0 and t_pers > 0
