@@ -245,6 +245,11 @@ def run_gpu(args):
     ctx = Bd.Context(g, h, "f32")
     if args.generic:
         ctx.set_option("generic_stencil", 1)
+    if args.cubic_rows:
+        rw = [int(x) for x in args.cubic_rows.split(",")]
+        ctx.set_option("cubic_rows", rw[0])
+        if len(rw) > 1:
+            ctx.set_option("cubic_rows_corr", rw[1])
     if args.zc:
         zc = [int(x) for x in args.zc.split(",")]
         ctx.set_option("planes_per_cta", zc[0])
@@ -259,8 +264,8 @@ def run_gpu(args):
               T=r["T"] if args.temperature is None else args.temperature, seed=r["seed"], replica=rank)
     bps = SOLVER_BYTES[args.solver]
     bytes_per_step = bps["llg_predictor"] + CORRECTOR_LAUNCHES[args.solver] * bps["llg_corrector"]
-    if not args.zc and not args.generic:
-        ctx.autotune(n)  # planes per CTA, chosen by timing before the timed region
+    if not args.zc and not args.generic and not args.cubic_rows:
+        ctx.autotune(n)  # tile height and planes per CTA, chosen by timing before the timed region
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
     step = 0
@@ -354,6 +359,7 @@ def run_gpu(args):
                           "cubic27" if ctx.get_option("has_cubic_path") else "generic"),
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),
+                      "columns_per_thread": [ctx.get_option("cubic_rows"), ctx.get_option("cubic_rows_corr")],
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
@@ -1071,6 +1077,8 @@ def main():
     ap.add_argument("--zc", default="", help="units per CTA of the 27-point path, P or P,C for predictor and "
                     "corrector (profiling aid; default: chosen by sp_autotune)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
+    ap.add_argument("--cubic-rows", default="", help="columns per thread of the 27-point kernels, R or R,C for "
+                                                     "predictor and corrector (default: chosen by sp_autotune)")
     ap.add_argument("--solver", default="heun", choices=["heun", "depondt", "sib", "rk4"],
                     help="sc128: LLG solver (the workload is stochastic Heun; the others for comparison)")
     ap.add_argument("--workload", default="sc128", choices=["sc128", "gneb48", "hex512", "warmstart", "unet", "mc30", "hessian",

@@ -633,15 +633,25 @@ enum {
     SP_OPT_GNEB_PERSISTENT = 9,
     /* polls (about 0.1-0.5 us each) a grid-barrier wait of the persistent
      * GNEB kernel makes before it gives up (>= 1); 0: the default, 2^21 */
-    SP_OPT_WAIT_LIMIT = 10
+    SP_OPT_WAIT_LIMIT = 10,
+    /* columns per thread of the 27-point kernels, 1 (default) or 2: with 2 a
+     * thread owns two columns of a 32 x 16 tile (the same arithmetic per
+     * spin, bit-identical results) -- FP32 single lattices without the
+     * dipole term only, other calls take 1.  Sets both passes; units of
+     * SP_OPT_PLANES_PER_CTA are then (32 x 16 tile, plane).  sp_autotune
+     * chooses it per pass.  Reading returns the predictor's value in use */
+    SP_OPT_CUBIC_ROWS = 11,
+    /* the same for the corrector pass alone */
+    SP_OPT_CUBIC_ROWS_CORR = 12
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
-/* Choose the work per CTA of the 27-point path by measurement, for each pass
- * separately (the passes have different register budgets and occupancy):
- * times the LLG predictor and corrector passes (Heun with the thermal field
- * on; they read n_dev and write only context scratch, so the spins are
- * unchanged) with CUDA events on `stream` for the balanced split, finer
- * splits and a few fixed run lengths, and keeps the fastest of each.  Allocates
+/* Choose the tile height (SP_OPT_CUBIC_ROWS) and the work per CTA of the
+ * 27-point path by measurement, for each pass separately (the passes have
+ * different register budgets and occupancy): times the LLG predictor and
+ * corrector passes (Heun with the thermal field on; they read n_dev and
+ * write only context scratch, so the spins are unchanged) with CUDA events
+ * on `stream`, for each tile height the balanced split, finer splits and a
+ * few fixed run lengths, and keeps the fastest of each pass.  Allocates
  * the LLG scratch if needed and synchronises `stream`.  SP_OK without effect
  * when the 27-point path does not apply.  *chosen (host, may be NULL)
  * receives the predictor's value (SP_OPT_PLANES_PER_CTA reads it back,

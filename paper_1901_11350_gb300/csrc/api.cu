@@ -397,7 +397,8 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
             for (int stg = 0; stg < 4; ++stg) {
                 if ((rc = dipole(c, src[stg], &bd, st))) return rc;
                 int pr = c->prof.begin(stg == 0 ? SP_PROF_LLG_PREDICTOR : SP_PROF_LLG_CORRECTOR, st);
-                cudaError_t e = cub ? launch_cubic<T>(stg, SP_RK4, CP, src[stg], dst[stg], acc, nn, nullptr, k, per0, st)
+                cudaError_t e = cub ? launch_cubic<T>(stg, SP_RK4, CP, src[stg], dst[stg], acc, nn, nullptr, k, per0, st,
+                                                      cubic_rows(c, 0))
                                     : launch_rk4_stage<T>(stg, S, nn, src[stg], dst[stg], acc, (const rec_t<T> *)bd, k,
                                                           st);
                 c->prof.end(pr, st);
@@ -407,13 +408,15 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         }
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
-        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, per0, st)
+        cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, per0, st,
+                                              cubic_rows(c, 0))
                             : launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
-        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, per1, st)
+        e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, per1, st,
+                                  cubic_rows(c, 1))
                 : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
@@ -644,49 +647,62 @@ template <typename T> int autotune_run(sp_ctx *c, const void *n, int *chosen, cu
         cudaEventDestroy(e0);
         return fail(c, SP_ERR_CUDA, "cudaEventCreate");
     }
-    auto launch = [&](int pass, int per) {
-        return pass == 0 ? launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st)
-                         : launch_cubic<T>(1, SP_HEUN, CP, np, nullptr, q, out, nullptr, k, per, st);
+    auto launch = [&](int pass, int per, int rows) {
+        return pass == 0
+                   ? launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st, rows)
+                   : launch_cubic<T>(1, SP_HEUN, CP, np, nullptr, q, out, nullptr, k, per, st, rows);
     };
-    int user = c->zc, user_corr = c->zc_corr;
+    int user = c->zc, user_corr = c->zc_corr, user_rows[2] = {c->rows[0], c->rows[1]};
     c->zc = 0;
     c->zc_corr = 0;
-    int best_of[2] = {1, 1};
+    int best_of[2] = {1, 1}, best_rows[2] = {1, 1};
     cudaError_t e = cudaSuccess;
-    // each pass: the balanced single-wave split for its own occupancy and
-    // finer ones (more CTAs, shorter runs of planes), plus fixed run lengths
+    // each pass and tile height (one or two columns per thread; two in FP32
+    // only): the balanced single-wave split for its own occupancy and finer
+    // ones (more CTAs, shorter runs of planes), plus fixed run lengths
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-        int bal = cubic_per(c, pass);
-        std::vector<int> cands = {bal, (bal + 1) / 2, (bal + 2) / 3, (bal + 3) / 4, (bal + 5) / 6, 4, 8, 16, 32};
-        std::sort(cands.begin(), cands.end());
-        cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-        if (pass == 1) e = launch(0, bal);  // the corrector reads the predictor's output
         float best = 1e30f;
-        best_of[pass] = bal;
-        for (int per : cands) {
-            if (per < 1 || e != cudaSuccess) continue;
-            e = launch(pass, per);  // warm-up
-            float t = 0;
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch(pass, per);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                t += ms;
-            }
-            if (e == cudaSuccess && t < best) {
-                best = t;
-                best_of[pass] = per;
+        for (int rows = 1; rows <= 2 && e == cudaSuccess; ++rows) {
+            c->rows[pass] = rows;
+            if (cubic_rows(c, pass) != rows) continue;
+            (pass == 0 ? c->zc_auto : c->zc_auto_corr) = 0;
+            int bal = cubic_per(c, pass);
+            std::vector<int> cands = {bal, (bal + 1) / 2, (bal + 2) / 3, (bal + 3) / 4, (bal + 5) / 6, 4, 8, 16, 32};
+            std::sort(cands.begin(), cands.end());
+            cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+            if (pass == 1) e = launch(0, cubic_per(c, 0), cubic_rows(c, 0));  // the corrector reads its output
+            if (rows == 1) best_of[pass] = bal;
+            for (int per : cands) {
+                if (per < 1 || e != cudaSuccess) continue;
+                e = launch(pass, per, rows);  // warm-up
+                float t = 0;
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                    e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess) e = launch(pass, per, rows);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    t += ms;
+                }
+                if (e == cudaSuccess && t < best) {
+                    best = t;
+                    best_of[pass] = per;
+                    best_rows[pass] = rows;
+                }
             }
         }
+        c->rows[pass] = best_rows[pass];
+        (pass == 0 ? c->zc_auto : c->zc_auto_corr) = 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) {
         c->zc = user;
         c->zc_corr = user_corr;
+        c->rows[0] = user_rows[0];
+        c->rows[1] = user_rows[1];
+        c->zc_auto = c->zc_auto_corr = 0;
         return cuda_fail(c, e, "autotune");
     }
     c->zc = best_of[0];
@@ -1382,6 +1398,13 @@ int sp_set_option(sp_ctx *c, int option, int value)
         if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "mc_resident takes 0 or 1");
         c->use_mc_resident = value == 1;
         return SP_OK;
+    case SP_OPT_CUBIC_ROWS:
+    case SP_OPT_CUBIC_ROWS_CORR:
+        if (value != 1 && value != 2) return fail(c, SP_ERR_ARG, "columns per thread: 1 or 2");
+        if (option == SP_OPT_CUBIC_ROWS) c->rows[0] = value;
+        c->rows[1] = value;
+        c->zc_auto = c->zc_auto_corr = 0;
+        return SP_OK;
     case SP_OPT_GNEB_PERSISTENT:
         if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "gneb_persistent takes 0 or 1");
         c->gneb_persistent = value;
@@ -1435,6 +1458,12 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_GNEB_PERSISTENT:
         *value = c->gneb_persistent;
+        return SP_OK;
+    case SP_OPT_CUBIC_ROWS:
+        *value = cubic_rows(c, 0);
+        return SP_OK;
+    case SP_OPT_CUBIC_ROWS_CORR:
+        *value = cubic_rows(c, 1);
         return SP_OK;
     case SP_OPT_WAIT_LIMIT:
         *value = c->wait_limit;

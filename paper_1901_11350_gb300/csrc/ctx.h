@@ -123,6 +123,7 @@ struct sp_ctx {
     int zc_corr = 0;        // the corrector's, when the autotuner chose it separately
     int zc_auto = 0;        // balanced value, computed on first use
     int zc_auto_corr = 0;   // the same for the corrector pass (its own occupancy)
+    int rows[2] = {1, 1};   // columns per thread of the 27-point predictor and corrector (1 or 2)
     CubicParams<float> Cf = {};
     CubicParams<double> Cd = {};
     // device scratch (allocated on first use)
@@ -183,8 +184,15 @@ inline int cubic_per_batch(sp_ctx *c, int pass, int n_rep)
     return (int)std::max(1L, (units + slots - 1) / slots);
 }
 
+// Columns per thread the 27-point pass of a single lattice takes.
+inline int cubic_rows(const sp_ctx *c, int pass)
+{
+    return cubic_rows_taken(c->prec, c->rows[pass], false, c->h.dipole != SP_DIPOLE_NONE);
+}
+
 // Units per CTA of the 27-point path: the user's choice, or the units spread
-// evenly over one wave of resident CTAs on the current device.
+// evenly over one wave of resident CTAs on the current device (units of the
+// pass's tile height, see cubic_rows).
 inline int cubic_per(sp_ctx *c, int pass = 0)
 {
     if (pass == 1 && c->zc_corr > 0) return c->zc_corr;
@@ -194,8 +202,9 @@ inline int cubic_per(sp_ctx *c, int pass = 0)
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
-        long slots = (long)nsm * cubic_resident_ctas(c->prec, pass);
-        long units = cubic_units(c->nc[0], c->nc[1], c->nc[2]);
+        const int rows = cubic_rows(c, pass);
+        long slots = (long)nsm * cubic_resident_ctas(c->prec, pass, rows);
+        long units = cubic_units(c->nc[0], c->nc[1], c->nc[2], rows);
         a = (int)std::max(1L, (units + slots - 1) / slots);
     }
     return a;

@@ -18,6 +18,8 @@
 // and the face DMI field is sum_axes (n(+o) - n(-o)) x D_o.  Every spin is read
 // from global memory about (1 + 2/ZC)(1 + halo) times per pass (L2 serves the
 // re-reads), and from shared memory 8 times.
+#include <type_traits>
+
 #include "internal.h"
 #include "cubic.h"
 
@@ -33,6 +35,13 @@ namespace {
 // budget: it has no thermal field to generate)
 #ifndef SPGB_CUBIC_MINB_CORR
 #define SPGB_CUBIC_MINB_CORR 4
+#endif
+// the same with two columns per thread (more state per thread)
+#ifndef SPGB_CUBIC_MINB2
+#define SPGB_CUBIC_MINB2 2
+#endif
+#ifndef SPGB_CUBIC_MINB2_CORR
+#define SPGB_CUBIC_MINB2_CORR 2
 #endif
 // plane buffers in shared memory per pass (planes are fetched NB - 1 ahead)
 // and how many planes ahead the corrector loads its folded term q (two
@@ -58,8 +67,17 @@ namespace {
 #define SPGB_CUBIC_PDL 1
 #endif
 
+// A CTA's 256 threads form TX x TY columns; each thread owns ROWS columns of
+// the CTA's TX x (TY ROWS) tile, at rows ty, ty + TY, ..  (ROWS 1 or 2: the
+// second column shares the thread's plane staging and loop work and gives it
+// a second, independent stencil and thermal-field chain to interleave).
 constexpr int TX = 32, TY = 8;
-constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY;
+constexpr int HX = TX + 2;
+template <int ROWS> struct Tile {
+    static constexpr int TYE = TY * ROWS;                 // rows of the tile
+    static constexpr int HN = HX * (TYE + 2);             // halo tile records
+    static constexpr int NS = (HN + TX * TY - 1) / (TX * TY);  // halo records per thread
+};
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -136,11 +154,11 @@ struct HaloSlot {
     int off;  // gy * nx + gx, or -1 outside the lattice in-plane
 };
 
-template <typename T>
+template <typename T, int ROWS>
 __device__ __forceinline__ HaloSlot halo_slot(const CubicParams<T> &P, int x0, int y0, int e)
 {
     HaloSlot h{-1};
-    if (e >= HN) return h;
+    if (e >= Tile<ROWS>::HN) return h;
     int hx = e % HX, hy = e / HX;
     int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
     bool in = true;
@@ -167,9 +185,9 @@ __device__ __forceinline__ void copy_rec(rec_t<T> *dst, const rec_t<T> *src)
     if (sizeof(rec_t<T>) == 32) cp_async16(reinterpret_cast<char *>(dst) + 16, reinterpret_cast<const char *>(src) + 16);
 }
 
-template <typename T>
+template <typename T, int ROWS>
 __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<T> *__restrict__ src, rec_t<T> *tile,
-                                           const HaloSlot &h0, const HaloSlot &h1, int z)
+                                           const HaloSlot (&h)[Tile<ROWS>::NS], int z)
 {
     bool zin = true;
     if (P.per2) {
@@ -179,17 +197,16 @@ __device__ __forceinline__ void load_plane(const CubicParams<T> &P, const rec_t<
         zin = z >= 0 && z < P.nz;
     }
     const rec_t<T> *plane = src + z * (P.nx * P.ny);
-    int e0 = threadIdx.x, e1 = threadIdx.x + TX * TY;
     rec_t<T> zero{};
-    if (zin && h0.off >= 0)
-        copy_rec<T>(tile + e0, plane + h0.off);
-    else
-        tile[e0] = zero;
-    if (e1 < HN) {
-        if (zin && h1.off >= 0)
-            copy_rec<T>(tile + e1, plane + h1.off);
-        else
-            tile[e1] = zero;
+#pragma unroll
+    for (int k = 0; k < Tile<ROWS>::NS; ++k) {
+        int e = threadIdx.x + k * TX * TY;
+        if (k == 0 || e < Tile<ROWS>::HN) {
+            if (zin && h[k].off >= 0)
+                copy_rec<T>(tile + e, plane + h[k].off);
+            else
+                tile[e] = zero;
+        }
     }
 }
 
@@ -261,28 +278,36 @@ template <typename T> __device__ __forceinline__ v3<T> onsite(const CubicParams<
 // the newest NB - 2 groups means "the plane needed next has landed".
 // REPL: the records belong to replica r of a batch (its noise amplitude and
 // thermal stream); otherwise r is 0 and the amplitude is c.sig[0].
-template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB, bool REPL>
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, int NB, bool REPL, int ROWS>
 __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> *__restrict__ src,
                                         rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                         rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
-                                        const LlgConst<T> &c, rec_t<T> (*tiles)[HN], rec_t<T> (*qt)[TX * TY], int r,
-                                        int x0, int y0, int za, int zb)
+                                        const LlgConst<T> &c, rec_t<T> (*tiles)[Tile<ROWS>::HN],
+                                        rec_t<T> (*qt)[TX * TY * ROWS], int r, int x0, int y0, int za, int zb)
 {
     constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
     static_assert(NB >= 2 && NB <= 4, "2 to 4 plane buffers");
     constexpr int QA = PASS == 1 && SOLVER != SP_RK4 ? SPGB_CUBIC_QAHEAD : 1;
     static_assert(QA >= 1 && QA <= 2, "q is fetched 1 or 2 planes ahead");
+    constexpr int NS = Tile<ROWS>::NS;
     int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    int x = x0 + tx, y = y0 + ty;
-    bool own = x < P.nx && y < P.ny;
-    HaloSlot h0 = halo_slot(P, x0, y0, threadIdx.x), h1 = halo_slot(P, x0, y0, threadIdx.x + TX * TY);
+    int x = x0 + tx;
+    bool own[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) own[j] = x < P.nx && y0 + ty + j * TY < P.ny;
+    HaloSlot h[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) h[k] = halo_slot<T, ROWS>(P, x0, y0, threadIdx.x + k * TX * TY);
     const int plane_sz = P.nx * P.ny;  // N < 2^31
     // one cp.async group per ring slot: plane p of src (and, QS, q of plane
-    // p - 1 at this thread's column)
+    // p - 1 at this thread's columns)
     auto load = [&](int slot, int p) {
-        if (p <= zb) load_plane<T>(P, src, tiles[slot], h0, h1, p);
-        if (QS && own && p - 1 >= za && p - 1 < zb)
-            copy_rec<T>(&qt[slot][threadIdx.x], q + (size_t)(p - 1) * plane_sz + y * P.nx + x);
+        if (p <= zb) load_plane<T, ROWS>(P, src, tiles[slot], h, p);
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j)
+            if (QS && own[j] && p - 1 >= za && p - 1 < zb)
+                copy_rec<T>(&qt[slot][threadIdx.x + j * TX * TY],
+                            q + (size_t)(p - 1) * plane_sz + (y0 + ty + j * TY) * P.nx + x);
         cp_async_commit();
     };
     // planes za-1 .. za+NB-2 in flight
@@ -290,52 +315,73 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
     for (int k = 0; k < NB; ++k) load(k, za - 1 + k);
     cp_async_wait<NB - 1>();
     __syncthreads();
-    Plane<T> below = summarise<T, DM>(P, tiles[0], tx, ty);
+    Plane<T> below[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) below[j] = summarise<T, DM>(P, tiles[0], tx, ty + j * TY);
     __syncthreads();
     load(0, za + NB - 1);
     cp_async_wait<NB - 1>();
     __syncthreads();
-    Plane<T> cur = summarise<T, DM>(P, tiles[1], tx, ty);
-    v3<T> acc = cur.e + below.w - zdmi<T, DM>(P, below.c) + onsite(P, cur.c);
-    v3<T> wcur = cur.w, ccur = cur.c;
-    int i = za * plane_sz + y * P.nx + x;
+    v3<T> acc[ROWS], wcur[ROWS], ccur[ROWS];
+    int i[ROWS];
     // per-spin global inputs of the planes being finished, fetched QA planes
     // (Bdd: one plane) ahead so that their latency overlaps the stencils
-    v3<T> qa[QA], bn = mk(T(0), T(0), T(0));
+    v3<T> qa[ROWS][QA], bn[ROWS];
 #pragma unroll
-    for (int k = 0; k < QA; ++k) {
-        qa[k] = mk(T(0), T(0), T(0));
-        if (PASS == 1 && SOLVER != SP_RK4 && !QS && own && za + k < zb) qa[k] = ld(q, i + k * plane_sz);
+    for (int j = 0; j < ROWS; ++j) {
+        Plane<T> cur = summarise<T, DM>(P, tiles[1], tx, ty + j * TY);
+        acc[j] = cur.e + below[j].w - zdmi<T, DM>(P, below[j].c) + onsite(P, cur.c);
+        wcur[j] = cur.w;
+        ccur[j] = cur.c;
+        i[j] = za * plane_sz + (y0 + ty + j * TY) * P.nx + x;
+        bn[j] = mk(T(0), T(0), T(0));
+#pragma unroll
+        for (int k = 0; k < QA; ++k) {
+            qa[j][k] = mk(T(0), T(0), T(0));
+            if (PASS == 1 && SOLVER != SP_RK4 && !QS && own[j] && za + k < zb) qa[j][k] = ld(q, i[j] + k * plane_sz);
+        }
+        if (HAS_BDD && own[j]) bn[j] = ld(Bdd, i[j]);
     }
-    if (HAS_BDD && own) bn = ld(Bdd, i);
     int s_next = 2 % NB, s_free = 1;  // slots of planes z+1 and z
     const uint64_t step = REPL && (PASS == 0 || SOLVER == SP_RK4) ? llg_step_of(c) : c.step;  // Philox step
-    for (int z = za; z < zb; ++z, i += plane_sz) {
+    for (int z = za; z < zb; ++z) {
         const int sn = s_next, sf = s_free;  // plane z+1 (landed after the wait); plane z, summarised
         s_next = s_next + 1 == NB ? 0 : s_next + 1;
         s_free = s_free + 1 == NB ? 0 : s_free + 1;
-        v3<T> qi = qa[0], bi = bn;
+        v3<T> qi[ROWS], bi[ROWS];
 #pragma unroll
-        for (int k = 0; k + 1 < QA; ++k) qa[k] = qa[k + 1];
-        if (own && z + QA < zb && PASS == 1 && SOLVER != SP_RK4 && !QS) qa[QA - 1] = ld(q, i + QA * plane_sz);
-        if (HAS_BDD && own && z + 1 < zb) bn = ld(Bdd, i + plane_sz);
+        for (int j = 0; j < ROWS; ++j) {
+            qi[j] = qa[j][0];
+            bi[j] = bn[j];
+#pragma unroll
+            for (int k = 0; k + 1 < QA; ++k) qa[j][k] = qa[j][k + 1];
+            if (own[j] && z + QA < zb && PASS == 1 && SOLVER != SP_RK4 && !QS)
+                qa[j][QA - 1] = ld(q, i[j] + QA * plane_sz);
+            if (HAS_BDD && own[j] && z + 1 < zb) bn[j] = ld(Bdd, i[j] + plane_sz);
+        }
         cp_async_wait<NB - 2>();
         __syncthreads();
-        if (QS && own) qi = ldc(qt[sn], threadIdx.x);  // q of plane z, landed with plane z+1
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j)
+            if (QS && own[j]) qi[j] = ldc(qt[sn], threadIdx.x + j * TX * TY);  // q of plane z, landed with plane z+1
         load(sf, z + NB);
-        Plane<T> up = summarise<T, DM>(P, tiles[sn], tx, ty);
-        v3<T> B = acc + up.w + zdmi<T, DM>(P, up.c);
-        acc = up.e + wcur - zdmi<T, DM>(P, ccur) + onsite(P, up.c);
-        v3<T> ni = ccur;
-        wcur = up.w;
-        ccur = up.c;
-        if (own) {
-            if (HAS_BDD) B = B + bi;
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j) {
+            Plane<T> up = summarise<T, DM>(P, tiles[sn], tx, ty + j * TY);
+            v3<T> B = acc[j] + up.w + zdmi<T, DM>(P, up.c);
+            acc[j] = up.e + wcur[j] - zdmi<T, DM>(P, ccur[j]) + onsite(P, up.c);
+            v3<T> ni = ccur[j];
+            wcur[j] = up.w;
+            ccur[j] = up.c;
+            const int ii = i[j];
+            i[j] += plane_sz;
+            if (!own[j]) continue;
+            if (HAS_BDD) B = B + bi[j];
             v3<T> Bth = mk(T(0), T(0), T(0));
             if ((PASS == 0 || SOLVER == SP_RK4) && c.thermal)
                 Bth = (REPL ? c.rsig[r] : c.sig[0]) *
-                      thermal_eta(REPL ? thermal_bits_at(c, step, (uint32_t)i, (uint32_t)r)
-                                       : thermal_bits_at(c, c.step, (uint32_t)i, 0u),
+                      thermal_eta(REPL ? thermal_bits_at(c, step, (uint32_t)ii, (uint32_t)r)
+                                       : thermal_bits_at(c, c.step, (uint32_t)ii, 0u),
                                   T(0));
             if (SOLVER == SP_RK4) {
                 // stage PASS of the fourth-order Runge-Kutta step (the same
@@ -344,15 +390,15 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
                 // written by stage 3)
                 v3<T> k = cross(ni, llg_A(c.cA[0], c.alpha, ni, B + Bth));
                 if (PASS == 0) {
-                    st(q, i, k);
-                    st(np, i, axpy(T(0.5) * c.dt, k, ni));
+                    st(q, ii, k);
+                    st(np, ii, axpy(T(0.5) * c.dt, k, ni));
                 } else {
-                    v3<T> n0 = ldc(nout, i);
+                    v3<T> n0 = ldc(nout, ii);
                     if (PASS < 3) {
-                        st(q, i, axpy(T(2), k, ldc(q, i)));
-                        st(np, i, axpy((PASS == 1 ? T(0.5) : T(1)) * c.dt, k, n0));
+                        st(q, ii, axpy(T(2), k, ldc(q, ii)));
+                        st(np, ii, axpy((PASS == 1 ? T(0.5) : T(1)) * c.dt, k, n0));
                     } else {
-                        st(nout, i, normalised(axpy(c.dt / T(6), ldc(q, i) + k, n0)));
+                        st(nout, ii, normalised(axpy(c.dt / T(6), ldc(q, ii) + k, n0)));
                     }
                 }
             } else if (PASS == 0) {
@@ -361,26 +407,26 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
                     v3<T> f = cross(ni, A);
                     v3<T> p = normalised(axpy(c.dt, f, ni));
                     v3<T> g = cross(p, llg_A(c.cA[0], c.alpha, p, Bth));
-                    st(np, i, p);
-                    st(q, i, axpy(T(0.5) * c.dt, f + g, ni));
+                    st(np, ii, p);
+                    st(q, ii, axpy(T(0.5) * c.dt, f + g, ni));
                 } else if (SOLVER == SP_SIB) {
                     // np holds the midpoint (n + x_p)/2, q the thermal part of A there
                     v3<T> m = T(0.5) * (ni + sib_solve(ni, A, c.dt));
-                    st(np, i, m);
-                    st(q, i, llg_A(c.cA[0], c.alpha, m, Bth));
+                    st(np, ii, m);
+                    st(q, ii, llg_A(c.cA[0], c.alpha, m, Bth));
                 } else {
                     v3<T> p = rotate(ni, A, c.dt);
-                    st(np, i, p);
-                    st(q, i, T(0.5) * (A + llg_A(c.cA[0], c.alpha, p, Bth)));
+                    st(np, ii, p);
+                    st(q, ii, T(0.5) * (A + llg_A(c.cA[0], c.alpha, p, Bth)));
                 }
             } else {
                 v3<T> Ap = llg_A(c.cA[0], c.alpha, ni, B);
                 if (SOLVER == SP_HEUN) {
-                    st(nout, i, normalised(axpy(T(0.5) * c.dt, cross(ni, Ap), qi)));
+                    st(nout, ii, normalised(axpy(T(0.5) * c.dt, cross(ni, Ap), qi[j])));
                 } else if (SOLVER == SP_SIB) {
-                    st(nout, i, sib_solve(ldc(nout, i), Ap + qi, c.dt));
+                    st(nout, ii, sib_solve(ldc(nout, ii), Ap + qi[j], c.dt));
                 } else {
-                    st(nout, i, rotate(ldc(nout, i), axpy(T(0.5), Ap, qi), c.dt));
+                    st(nout, ii, rotate(ldc(nout, ii), axpy(T(0.5), Ap, qi[j]), c.dt));
                 }
             }
         }
@@ -394,19 +440,25 @@ __device__ __forceinline__ void segment(const CubicParams<T> &P, const rec_t<T> 
 // takes units [b*per, (b+1)*per): a few contiguous runs of planes, each
 // streamed as one segment.  With per = units / (SMs x resident CTAs) every SM
 // gets the same amount of work in a single wave.
-template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, bool REPL>
-__global__ void __launch_bounds__(TX *TY, PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
+// resident CTAs per SM a kernel's register allocation is held to
+template <int SOLVER, int PASS, int ROWS> struct MinBlocks {
+    static constexpr int value = ROWS == 1 ? (PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_MINB : SPGB_CUBIC_MINB_CORR)
+                                           : (PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_MINB2 : SPGB_CUBIC_MINB2_CORR);
+};
+
+template <typename T, int SOLVER, int PASS, int DM, bool HAS_BDD, bool REPL, int ROWS>
+__global__ void __launch_bounds__(TX *TY, (MinBlocks<SOLVER, PASS, ROWS>::value)) k_cubic(const __grid_constant__ CubicParams<T> P, const rec_t<T> *__restrict__ src,
                                                   rec_t<T> *__restrict__ np, rec_t<T> *__restrict__ q,
                                                   rec_t<T> *__restrict__ nout, const rec_t<T> *__restrict__ Bdd,
                                                   const LlgConst<T> c, int per)
 {
     constexpr int NB = PASS == 0 || SOLVER == SP_RK4 ? SPGB_CUBIC_NB_PRED : SPGB_CUBIC_NB_CORR;
     constexpr bool QS = PASS == 1 && SOLVER == SP_HEUN && SPGB_CUBIC_QSMEM;
-    __shared__ __align__(32) rec_t<T> tiles[NB][HN];
-    __shared__ __align__(32) rec_t<T> qtiles[QS ? NB : 1][QS ? TX * TY : 1];
+    __shared__ __align__(32) rec_t<T> tiles[NB][Tile<ROWS>::HN];
+    __shared__ __align__(32) rec_t<T> qtiles[QS ? NB : 1][QS ? TX * TY * ROWS : 1];
     allow_dependents();
     wait_prerequisite();  // the previous pass reads what this one overwrites
-    int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
+    int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + Tile<ROWS>::TYE - 1) / Tile<ROWS>::TYE;
     long ntile = (long)tiles_x * tiles_y;
     long total = ntile * P.nz * (REPL ? llg_reps(c) : 1);
     long u = (long)blockIdx.x * per, u1 = min(u + per, total);
@@ -417,9 +469,11 @@ __global__ void __launch_bounds__(TX *TY, PASS == 0 || SOLVER == SP_RK4 ? SPGB_C
         int r = REPL ? (int)(tg / ntile) : 0;
         int tile = (int)(tg - (long)r * ntile);
         size_t o = REPL ? (size_t)r * ((size_t)P.nx * P.ny * P.nz) : 0;
-        segment<T, SOLVER, PASS, DM, HAS_BDD, NB, REPL>(P, src + o, np ? np + o : np, q + o, nout ? nout + o : nout,
-                                                        Bdd, c, tiles, (rec_t<T>(*)[TX * TY])qtiles, r,
-                                                        (tile % tiles_x) * TX, (tile / tiles_x) * TY, za, zb);
+        segment<T, SOLVER, PASS, DM, HAS_BDD, NB, REPL, ROWS>(P, src + o, np ? np + o : np, q + o,
+                                                              nout ? nout + o : nout, Bdd, c, tiles,
+                                                              (rec_t<T>(*)[TX * TY * ROWS])qtiles, r,
+                                                              (tile % tiles_x) * TX, (tile / tiles_x) * Tile<ROWS>::TYE,
+                                                              za, zb);
         u += zb - za;
     }
 }
@@ -436,7 +490,7 @@ cudaError_t launch_one(K kern, int grid, const CubicParams<T> &P, const rec_t<T>
 #endif
 }
 
-template <typename T, int DM, bool HB, bool RP>
+template <typename T, int DM, bool HB, bool RP, int RW>
 cudaError_t launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
                        rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per,
                        cudaStream_t st)
@@ -446,72 +500,89 @@ cudaError_t launch_dmb(int pass, int solver, int grid, const CubicParams<T> &P, 
             return cudaErrorNotSupported;
         } else {
             switch (pass) {
-            case 0: return launch_one(k_cubic<T, SP_RK4, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
-            case 1: return launch_one(k_cubic<T, SP_RK4, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
-            case 2: return launch_one(k_cubic<T, SP_RK4, 2, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
-            default: return launch_one(k_cubic<T, SP_RK4, 3, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            case 0: return launch_one(k_cubic<T, SP_RK4, 0, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            case 1: return launch_one(k_cubic<T, SP_RK4, 1, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            case 2: return launch_one(k_cubic<T, SP_RK4, 2, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            default: return launch_one(k_cubic<T, SP_RK4, 3, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
             }
         }
     }
     if (pass == 0) {
         if (solver == SP_HEUN)
-            return launch_one(k_cubic<T, SP_HEUN, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            return launch_one(k_cubic<T, SP_HEUN, 0, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
         if (solver == SP_SIB)
-            return launch_one(k_cubic<T, SP_SIB, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
-        return launch_one(k_cubic<T, SP_DEPONDT, 0, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+            return launch_one(k_cubic<T, SP_SIB, 0, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_one(k_cubic<T, SP_DEPONDT, 0, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
     }
     if (solver == SP_HEUN)
-        return launch_one(k_cubic<T, SP_HEUN, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_one(k_cubic<T, SP_HEUN, 1, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
     if (solver == SP_SIB)
-        return launch_one(k_cubic<T, SP_SIB, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
-    return launch_one(k_cubic<T, SP_DEPONDT, 1, DM, HB, RP>, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_one(k_cubic<T, SP_SIB, 1, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
+    return launch_one(k_cubic<T, SP_DEPONDT, 1, DM, HB, RP, RW>, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 // (a batch of replicas never carries the dipole field)
+// (two columns per thread only for FP32 single lattices without the dipole
+// field; other calls take one)
 template <typename T, int DM>
 cudaError_t launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np,
-                      rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per,
+                      rec_t<T> *q, rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, int rows,
                       cudaStream_t st)
 {
     if (llg_reps(c) > 1)
-        return launch_dmb<T, DM, false, true>(pass, solver, grid, P, src, np, q, nout, nullptr, c, per, st);
-    if (Bdd) return launch_dmb<T, DM, true, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    return launch_dmb<T, DM, false, false>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+        return launch_dmb<T, DM, false, true, 1>(pass, solver, grid, P, src, np, q, nout, nullptr, c, per, st);
+    if (Bdd) return launch_dmb<T, DM, true, false, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    if constexpr (std::is_same<T, float>::value)
+        if (rows == 2) return launch_dmb<T, DM, false, false, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    return launch_dmb<T, DM, false, false, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st)
+                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st, int rows)
 {
-    long total = cubic_units(P.nx, P.ny, P.nz) * llg_reps(c);
+    rows = cubic_rows_taken(sizeof(T) == 8 ? SP_F64 : SP_F32, rows, llg_reps(c) > 1, Bdd != nullptr);
+    long total = cubic_units(P.nx, P.ny, P.nz, rows) * llg_reps(c);
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
     int grid = (int)((total + per - 1) / per);
-    if (P.dmi_mode == 0) return launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    if (P.dmi_mode == 1) return launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
-    return launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, st);
+    if (P.dmi_mode == 0) return launch_dm<T, 0>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, rows, st);
+    if (P.dmi_mode == 1) return launch_dm<T, 1>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, rows, st);
+    return launch_dm<T, 2>(pass, solver, grid, P, src, np, q, nout, Bdd, c, per, rows, st);
 }
 
-long cubic_units(int nx, int ny, int nz) { return (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz; }
+int cubic_rows_taken(int prec, int rows, bool replicas, bool dipole)
+{
+    return (rows == 2 && prec == SP_F32 && !replicas && !dipole) ? 2 : 1;
+}
 
-int cubic_resident_ctas(int prec, int pass)
+long cubic_units(int nx, int ny, int nz, int rows)
+{
+    const int tye = TY * (rows == 2 ? 2 : 1);
+    return (long)((nx + TX - 1) / TX) * ((ny + tye - 1) / tye) * nz;
+}
+
+int cubic_resident_ctas(int prec, int pass, int rows)
 {
     int n = 0;
     cudaError_t e;
-    if (pass == 0)
-        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false, false>, TX * TY, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false, false>, TX * TY, 0);
+    if (prec == SP_F32 && rows == 2)
+        e = pass == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false, false, 2>, TX * TY, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false, false, 2>, TX * TY, 0);
+    else if (pass == 0)
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 0, 1, false, false, 1>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 0, 1, false, false, 1>, TX * TY, 0);
     else
-        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 1, 1, false, false>, TX * TY, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false, false>, TX * TY, 0);
+        e = prec == SP_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<double, SP_HEUN, 1, 1, false, false, 1>, TX * TY, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cubic<float, SP_HEUN, 1, 1, false, false, 1>, TX * TY, 0);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 template cudaError_t launch_cubic<float>(int, int, const CubicParams<float> &, const float4 *, float4 *, float4 *,
-                                         float4 *, const float4 *, const LlgConst<float> &, int, cudaStream_t);
+                                         float4 *, const float4 *, const LlgConst<float> &, int, cudaStream_t, int);
 template cudaError_t launch_cubic<double>(int, int, const CubicParams<double> &, const dq4 *, dq4 *, dq4 *, dq4 *,
-                                          const dq4 *, const LlgConst<double> &, int, cudaStream_t);
+                                          const dq4 *, const LlgConst<double> &, int, cudaStream_t, int);
 
 }  // namespace spgb

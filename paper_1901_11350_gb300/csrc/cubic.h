@@ -14,17 +14,23 @@ template <typename T> struct CubicParams {
     int dmi_mode;          // 0 none, 1 bulk (D_o = D ohat, one D), 2 any face vectors
 };
 
-// Work units of the 27-point path: (32 x 8 column tile, plane) pairs.
-long cubic_units(int nx, int ny, int nz);
+// Columns per thread the 27-point kernels take for a request of `rows` (1 or
+// 2): two only in FP32, for a single lattice without the dipole field.
+int cubic_rows_taken(int prec, int rows, bool replicas, bool dipole);
+// Work units of the 27-point path: (32 x 8 rows column tile, plane) pairs.
+long cubic_units(int nx, int ny, int nz, int rows = 1);
 // Resident 256-thread CTAs per SM of the 27-point kernels (occupancy query).
-int cubic_resident_ctas(int prec, int pass);
+int cubic_resident_ctas(int prec, int pass, int rows = 1);
 
 // pass 0: predictor (stencil on src = n, writes np and q);
 // pass 1: corrector (stencil on src = np, reads q, writes nout = n).
 // CTA b streams the units [b*per, (b+1)*per), tile-major; with c.n_rep > 1
 // the units of all replicas (stored one after another), replica-major.
+// rows: columns per thread (1 or 2, see cubic_rows_taken); per counts units
+// of that tile height.
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st);
+                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st,
+                         int rows = 1);
 
 }  // namespace spgb

@@ -321,8 +321,8 @@ def test_gneb_stoner_wohlfarth_barrier_fp64():
     assert abs(E.max() - E[0] - K * (1 - hh) ** 2) < 1e-12
 
 
-@pytest.mark.parametrize("zc", [None, 3, 128])
-def test_sc128_heun_step_fp32_full_size(zc):
+@pytest.mark.parametrize("zc,rows", [(None, 1), (3, 1), (128, 1), (None, 2), (7, 2)])
+def test_sc128_heun_step_fp32_full_size(zc, rows):
     # the 128^3 stochastic Heun workload at full size, in the launch
     # configuration the benchmark uses (and two other plane chunkings),
     # every spin checked
@@ -331,6 +331,7 @@ def test_sc128_heun_step_fp32_full_size(zc):
     o = _oracle(g, h)
     c = B.Context(g, h, "f32")
     assert c.get_option("has_cubic_path") == 1
+    c.set_option("cubic_rows", rows)
     if zc is not None:
         c.set_option("planes_per_cta", zc)
     n0 = I.random_spins(o.N, cfg["spin_seed"]).astype(np.float32).astype(np.float64)
@@ -691,3 +692,47 @@ def test_small_lattice_path_equals_the_multi_launch_path(name, solver, prec):
         a.llg_step(x, 40, **kw)
         b.llg_step(y, 40, **kw)
         assert torch.equal(x, y), (name, solver, prec, T)
+
+
+@pytest.mark.parametrize("dims", [(13, 11, 9), (32, 16, 5), (40, 37, 6), (8, 8, 8)])
+@pytest.mark.parametrize("solver", ["heun", "depondt", "sib", "rk4"])
+def test_cubic_two_columns_per_thread_is_bit_identical(dims, solver):
+    # the 27-point kernels with two columns per thread (32 x 16 tiles) run the
+    # same per-spin arithmetic as with one (32 x 8): the same bits, on
+    # ragged tiles and with several work splits
+    c2 = I.cfg_sc_128(4)
+    g, h = dict(c2["geometry"], n_cells=list(dims)), dict(c2["hamiltonian"], B=[0.2, 0, 0.5])
+    n0 = I.random_spins(int(np.prod(dims)), 31)
+    kw = dict(solver=solver, dt=2e-3, alpha=0.2, T=8.0, seed=3, step0=11)
+    ref = None
+    for rows, per in ((1, 0), (2, 0), (2, 1), (2, 3)):
+        c = _ctx(g, h, "f32", "cubic")
+        c.set_option("cubic_rows", rows)
+        if per:
+            c.set_option("planes_per_cta", per)
+        assert c.get_option("cubic_rows") == rows
+        n = c.spins(n0)
+        c.llg_step(n, 5, **kw)
+        if ref is None:
+            ref = n
+        else:
+            assert torch.equal(n, ref), (rows, per)
+
+
+def test_autotune_chooses_a_tile_height_and_split():
+    cfg = I.cfg_sc_128(64)
+    c = B.Context(cfg["geometry"], cfg["hamiltonian"], "f32")
+    n = c.spins(I.random_spins(c.N, 1))
+    n0 = n.clone()
+    c.autotune(n)
+    assert torch.equal(n, n0)
+    assert c.get_option("cubic_rows") in (1, 2) and c.get_option("cubic_rows_corr") in (1, 2)
+    assert c.get_option("planes_per_cta") >= 1 and c.get_option("planes_per_cta_corr") >= 1
+    # whatever was chosen, the step gives the one-column result bit for bit
+    ref = B.Context(cfg["geometry"], cfg["hamiltonian"], "f32")
+    ref.set_option("small_path", 0)
+    m = ref.spins(I.random_spins(c.N, 1))
+    kw = dict(solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=1)
+    c.llg_step(n, 3, **kw)
+    ref.llg_step(m, 3, **kw)
+    assert torch.equal(n, m)
