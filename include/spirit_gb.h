@@ -281,7 +281,10 @@ int sp_llg_step_replicas(sp_ctx *ctx, void *spins_dev, int n_rep, const double *
  * SP_OPT_SMALL_PATH = 0) at T[k] and replica p->replica + k.  Solvers
  * Depondt, Heun and SIB (RK4: SP_ERR_UNSUPPORTED).  Scratch (2 records per
  * spin of the buffer) and tables belong to ctxs[0]; a call with a new batch
- * layout uploads the tables and synchronises `stream`.  The spin state is
+ * layout uploads the tables and synchronises `stream`.  Outside a stream
+ * capture, runs of up to 32 steps replay a CUDA graph captured for the
+ * layout (kernels read the Philox step from a device counter the call sets;
+ * graphs are kept as for sp_llg_step_replicas).  The spin state is
  * checked for non-finite values afterwards (the status word of ctxs[0]). */
 int sp_llg_step_batch(sp_ctx *const *ctxs, int n_sys, void *spins_dev, const long long *offsets, const double *T,
                       const sp_llg_params *p, int n_steps, void *stream);

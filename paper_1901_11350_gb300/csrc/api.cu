@@ -617,11 +617,50 @@ int llg_batch_run(sp_ctx *const *ctxs, int n_sys, void *spins, const long long *
     LlgConst<T> k = llg_const<T>(c0, p);  // dt, alpha, seed round keys; the rest per system
     k.thermal = (hot && p->alpha > 0) ? 1 : 0;
     const int nblk = (int)blk.size();
-    for (int s = 0; s < n_steps; ++s) {
+    auto one_step = [&](const LlgConst<T> &kk, cudaStream_t s) -> cudaError_t {
+        cudaError_t e = launch_llg_batch<T>(0, p->solver, nblk, B, Sv, Y, nn, np, q, kk, s);
+        return e == cudaSuccess ? launch_llg_batch<T>(1, p->solver, nblk, B, Sv, Y, nn, np, q, kk, s) : e;
+    };
+    // runs of kLlgGraphSteps steps replay a CUDA graph whose kernels read the
+    // Philox step from a device counter (as the replica batches do)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "stream query");
+    int s = 0;
+    if (n_steps >= 2 && cap == cudaStreamCaptureStatusNone) {
+        if ((rc = ensure(c0, c0->step_ctr, sizeof(unsigned long long)))) return rc;
+        int G = std::min(n_steps, kLlgGraphSteps);
+        unsigned long long *ctr = (unsigned long long *)c0->step_ctr.p;
+        LlgConst<T> kk;
+        std::memcpy(&kk, &k, sizeof kk);  // byte copy: the key compares padding too
+        kk.step = 0;
+        kk.step_base = ctr;
+        struct Key {
+            const void *n, *pred, *ctr, *tab;
+            int solver, G, nblk, tag;
+        } gkey;
+        std::memset(&gkey, 0, sizeof gkey);
+        gkey.n = nn;
+        gkey.pred = c0->pred.p;
+        gkey.ctr = ctr;
+        gkey.tab = tab;
+        gkey.solver = p->solver;
+        gkey.G = G;
+        gkey.nblk = nblk;
+        gkey.tag = 0x4c42;  // batches of lattices (the replica graphs carry other keys)
+        std::vector<char> kb(sizeof gkey + sizeof kk);
+        std::memcpy(kb.data(), &gkey, sizeof gkey);
+        std::memcpy(kb.data() + sizeof gkey, &kk, sizeof kk);
+        cudaGraphExec_t exec = nullptr;
+        if ((rc = replica_graph<T>(c0, kb, G, k, ctr, one_step, &exec))) return rc;
+        k_set_u64<<<1, 1, 0, st>>>(ctr, (unsigned long long)p->step0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c0, e, "step counter");
+        for (; s + G <= n_steps; s += G)
+            if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return cuda_fail(c0, e, "batch graph launch");
+    }
+    for (; s < n_steps; ++s) {
         k.step = p->step0 + (uint64_t)s;
-        cudaError_t e = launch_llg_batch<T>(0, p->solver, nblk, B, Sv, Y, nn, np, q, k, st);
-        if (e == cudaSuccess) e = launch_llg_batch<T>(1, p->solver, nblk, B, Sv, Y, nn, np, q, k, st);
-        if (e != cudaSuccess) return cuda_fail(c0, e, "batched LLG launch");
+        if ((e = one_step(k, st)) != cudaSuccess) return cuda_fail(c0, e, "batched LLG launch");
     }
     return SP_OK;
 }

@@ -203,6 +203,9 @@ def gneb_batch(n_chains=48, seed=4, sizes=(64, 96, 128), images=(12, 40)):
 
 # ---------------------------------------------------------------- warm start
 WARMSTART_SEEDS = dict(train=5, heldout=6)
+# the learned warm start of GNEB paths: gneb_draw chains of 128 x 128 lattices
+# with 16 images, training and held-out seeds
+GNEB_WARMSTART_SEEDS = dict(train=7, heldout=8)
 
 
 def warmstart_draw(seed, index, L=128):

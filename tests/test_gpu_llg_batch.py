@@ -59,6 +59,13 @@ def test_batch_of_lattices_matches_single_calls(prec, solver):
     B.llg_step_batch(ctxs, flat, offs, [T for _, _, T in sy], n_steps=7, replica=3, **kw)
     for c, o, n in zip(ctxs, offs, singles):
         assert torch.equal(flat[o:o + c.N], n)
+    # a longer run continues the step counter: graph replays of 32 steps and
+    # 8 single steps, against the single calls' per-step launches
+    kw2 = dict(kw, step0=kw["step0"] + 7)
+    B.llg_step_batch(ctxs, flat, offs, [T for _, _, T in sy], n_steps=72, replica=3, **kw2)
+    for k, (c, o, n) in enumerate(zip(ctxs, offs, singles)):
+        c.llg_step(n, 72, T=sy[k][2], replica=3 + k, **kw2)
+        assert torch.equal(flat[o:o + c.N], n)
     assert ctxs[0].sync_status()[0] == 0
 
 
