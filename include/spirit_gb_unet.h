@@ -128,12 +128,28 @@ int sp_conv3x3_get_kernel(void);
  * SP_OK.  Synchronises the device and clears the flag. */
 int sp_unet_device_error(void);
 
+/* How many clock cycles a pipeline wait of the tcgen05 convolution (kernel
+ * 1) and weight gradient (a stage waiting for the MMAs that read it) polls
+ * before the CTA gives
+ * up: it then stops loading and issuing, waits for the MMAs it issued (with
+ * the default limit), frees its tensor memory, writes no output and sets the
+ * flag sp_unet_device_error reports.  Default 2^32 (about two seconds); 0
+ * makes every such wait give up at once.  SP_ERR_ARG if cycles < 0.  Process
+ * wide and not thread-safe: set it before launching work.  The
+ * warp-specialised kernel (2) keeps the default limit. */
+int sp_conv3x3_set_wait_limit(long long cycles);
+
 /* Workspace bytes sp_conv3x3_wgrad needs for this shape. */
 long long sp_conv3x3_wgrad_workspace(int B, int H, int Wd, int Cin, int Cout);
 
 /* Weight gradient dW[co][t][ci] = sum_p dz[p][co] * in_t[p][ci] (FP32) and,
  * if db is not NULL, db[co] = sum_p dz[p][co], with the input read as in
- * sp_conv3x3_forward.  Deterministic (fixed summation order). */
+ * sp_conv3x3_forward.  Deterministic (fixed summation order).  With the
+ * convolution kernel set to 1 or 2 (sp_conv3x3_set_kernel) the products run
+ * on tcgen05 MMAs (M = 128 tap-channel rows, N = output channels, K = the
+ * pixels of one split, FP32 accumulators in tensor memory, splits added in a
+ * fixed order; its pipeline waits obey sp_conv3x3_set_wait_limit); with 0
+ * on mma.sync. */
 int sp_conv3x3_wgrad(const uint16_t *src0, int C0, int up0, const uint16_t *src1, int C1, const uint16_t *dz, int B,
                      int H, int Wd, int Cout, float *dW, float *db, void *workspace, long long workspace_bytes,
                      void *stream);

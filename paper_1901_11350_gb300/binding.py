@@ -145,6 +145,7 @@ SIGNATURES = {
     "sp_conv3x3_set_kernel": (_i, [_i]),
     "sp_conv3x3_get_kernel": (_i, []),
     "sp_unet_device_error": (_i, []),
+    "sp_conv3x3_set_wait_limit": (_i, [C.c_longlong]),
     "sp_conv3x3_wgrad": (_i, [_vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, C.c_longlong, _vp]),
 }
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}

@@ -12,6 +12,7 @@
 // accumulators.  Shared-memory rows are 64 bytes with the 16-byte chunks
 // XOR-swizzled so ldmatrix reads are free of bank conflicts.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -232,15 +233,24 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
-// Wait for completion of the phase with this parity, for at most ~2^32
-// cycles (about two seconds); false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+// Wait for completion of the phase with this parity, for at most `limit`
+// cycles (2^32 is about two seconds); false when the limit ran out.  A limit
+// of 0 gives up at once, without polling.
+constexpr long long kWaitCycles = 1LL << 32;
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit = kWaitCycles)
 {
+    if (limit <= 0) return false;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1LL << 32)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
+
+// Cycles k_conv_tc's pipeline waits (a stage's MMAs releasing its buffers)
+// poll before they give up; sp_conv3x3_set_wait_limit.  The final wait for
+// the accumulator always keeps kWaitCycles, so that every MMA a CTA issued
+// has finished before it frees its tensor memory.
+__device__ long long g_tc_wait_limit = kWaitCycles;
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -301,6 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int HW = H * W;
+    const long long wait_limit = g_tc_wait_limit;
     const int ar = tid >> 2, ac = tid & 3;
     int pb[2], py[2], px[2];
 #pragma unroll
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
         const int kn = k + kTcStages - 1;
         if (kn < nk) {
             const int sn = kn % kTcStages;  // the stage the MMAs of iteration k-1 read
-            if (k >= 1 && !mbar_wait(bar0 + 8 * sn, ((k - 1) / kTcStages) & 1)) failed = 1;
+            if (k >= 1 && !mbar_wait(bar0 + 8 * sn, ((k - 1) / kTcStages) & 1, wait_limit)) failed = 1;
             if (!failed) load(kn, sn);
         }
         cp_commit();
@@ -674,6 +685,174 @@ __global__ void __launch_bounds__(128) k_wgrad(ConvSrc S, const bf16 *__restrict
                     make_float2(acc[mi][ni][2 * h], acc[mi][ni][2 * h + 1]);
             }
         }
+}
+
+// ------------------------------------------------------------------ wgrad, tcgen05
+// The weight gradient on the 5th-generation tensor cores, one GEMM per
+// (row tile, output-channel tile, pixel split):
+//     D[r][co] = sum_p in[p + off(t)][ci] dz[p][co],   r = t Cin + ci,
+// M = 128 rows r (four runs of 32 channels of one tap each), N = BN output
+// channels, K = the split's pixels, 32 per pipeline stage (two 128 x BN x 16
+// MMAs).  Both operands are copied straight from their pixel-major tensors,
+// so they enter the MMA MN-major: 64-byte swizzle atoms of 32 consecutive
+// channels x 8 pixels, stored with the four pixel groups of a stage next to
+// each other (SBO = 512 B between pixel groups, LBO = 2048 B between channel
+// runs).  The FP32 accumulator (128 lanes x BN columns of tensor memory) is
+// this split's partial sum part[z][co][t][ci]; k_sum_parts adds the splits
+// in a fixed order.  Waits are bounded as in k_conv_tc.
+constexpr int kWgPix = 32;  // pixels per stage
+
+template <int BN>
+constexpr size_t wgrad_tc_smem()
+{
+    // + 2 KB: the descriptors of the last stage never reach past the end
+    return 1024 + (size_t)kTcStages * (4 * 4 * 512 + (BN / 32) * 4 * 512) + 8 * kTcStages + 16 + 2048;
+}
+
+// MN-major SWIZZLE_64B descriptor: start >> 4 | LBO >> 4 (between atoms
+// along M or N) | SBO >> 4 (between groups of 8 along K) | version 1 |
+// layout 4 = 64-byte swizzle
+__device__ __forceinline__ uint64_t desc_mn64(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_wgrad_tc(ConvSrc S, const bf16 *__restrict__ dz, int H, int W, int Cout,
+                                                       int P, int pix_per_split, float *__restrict__ part)
+{
+    constexpr int NA = BN / 32;                 // channel runs (atoms) of the B tile
+    constexpr int A_BYTES = 4 * 4 * 512;        // 4 runs x 4 pixel groups
+    constexpr int STAGE = A_BYTES + NA * 4 * 512;
+    constexpr int BG = BN / 8;                  // 16-byte chunks of dz per pixel
+    constexpr int BJ = (kWgPix * BG + kThreads - 1) / kThreads;  // B chunks per thread
+    constexpr unsigned TCOLS = BN;
+    constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                               ((unsigned)(BN >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = smem_u32(smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;
+    const unsigned bar0 = base + kTcStages * STAGE;
+    const unsigned slot = bar0 + 8 * kTcStages;
+    volatile unsigned *slot_ptr = reinterpret_cast<volatile unsigned *>(smem_raw + (slot - raw));
+
+    const int Cin = S.C0 + S.C1, R = 9 * Cin;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int p_begin = blockIdx.z * pix_per_split;
+    const int nk = (min(P, p_begin + pix_per_split) - p_begin) / kWgPix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HW = H * W;
+    const long long wait_limit = g_tc_wait_limit;
+    // A: this thread copies chunk ag of run ar at pixels apx and apx + 16
+    const int ar = (tid >> 2) & 3, ag = tid & 3, apx = tid >> 4;
+    const int r_run = m0 + 32 * ar;
+    const bool a_on = r_run < R;
+    const int a_t = a_on ? r_run / Cin : 0;
+    const int a_ci = (a_on ? r_run - a_t * Cin : 0) + 8 * ag;
+    const int a_dy = a_t / 3 - 1, a_dx = a_t % 3 - 1;
+    auto load = [&](int k, int stage) {
+        const int pk = p_begin + k * kWgPix;
+        const unsigned sa = base + stage * STAGE, sb = sa + A_BYTES;
+        if (a_on) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int px = apx + 16 * j, p = pk + px;
+                const int b = p / HW, q = p - b * HW, y = q / W, x = q - y * W;
+                cp16(sa + (ar * 4 + (px >> 3)) * 512 + swz64(px & 7, ag),
+                     src_at(S, b, wrap(y + a_dy, H), wrap(x + a_dx, W), H, W, a_ci));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BJ; ++j) {
+            const int idx = tid + kThreads * j;
+            if (idx < kWgPix * BG) {
+                const int px = idx / BG, c = idx % BG;
+                cp16(sb + ((c >> 2) * 4 + (px >> 3)) * 512 + swz64(px & 7, c & 3),
+                     dz + (size_t)(pk + px) * Cout + n0 + 8 * c);
+            }
+        }
+    };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // runs past the last row (9 Cin not a multiple of 128) stay zero
+    for (int s = 0; s < kTcStages; ++s)
+        for (int i = tid; i < 4 * 128; i += kThreads) {
+            const int run = i >> 7;
+            if (m0 + 32 * run >= R)
+                *reinterpret_cast<uint4 *>(smem_raw + (base - raw) + s * STAGE + run * 2048 + (i & 127) * 16) =
+                    make_uint4(0u, 0u, 0u, 0u);
+        }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot_ptr;
+
+#pragma unroll
+    for (int s = 0; s < kTcStages - 1; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    int failed = 0, issued = 0;
+    for (int k = 0; k < nk; ++k) {
+        const int s = k % kTcStages;
+        cp_wait<kTcStages - 2>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (__syncthreads_or(failed)) {
+            failed = 1;
+            break;
+        }
+        if (tid == 0) {
+            tc_fence_after();
+            const unsigned sa = base + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+                tc_mma(tmem, desc_mn64(sa + kk * 1024, 2048, 512), desc_mn64(sb + kk * 1024, 2048, 512), IDESC,
+                       (k > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(bar0 + 8 * s);
+        }
+        issued = k + 1;
+        const int kn = k + kTcStages - 1;
+        if (kn < nk) {
+            const int sn = kn % kTcStages;  // the stage the MMAs of iteration k-1 read
+            if (k >= 1 && !mbar_wait(bar0 + 8 * sn, ((k - 1) / kTcStages) & 1, wait_limit)) failed = 1;
+            if (!failed) load(kn, sn);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    if (issued > 0 && !mbar_wait(bar0 + 8 * ((issued - 1) % kTcStages), ((issued - 1) / kTcStages) & 1)) failed = 1;
+    failed = __syncthreads_or(failed) || issued < nk;
+    tc_fence_after();
+    const int q = warp & 3, half = warp >> 2;
+    const int r = m0 + q * 32 + lane;
+    const int t = r / Cin, ci = r - t * Cin;
+    float *pz = part + (size_t)blockIdx.z * Cout * R;
+#pragma unroll
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+        float v[16];
+        tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0, v);
+        if (failed || r >= R) continue;
+        if (nk == 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) pz[((size_t)(n0 + c0 + e) * 9 + t) * Cin + ci] = v[e];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+    if (failed && tid == 0) atomicExch(&g_tc_error, 1);
 }
 
 // out[i] = sum_{z < nz} part[z * n + i], in order of z.
@@ -1047,17 +1226,26 @@ cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int 
 
 struct WgradPlan {
     int bmc, splits, pix_per_split, bias_blocks, bias_pix;
+    int tc_bn;              // > 0: k_wgrad_tc with this many output channels per CTA
     long long part_floats;  // partial weight sums
     long long bias_floats;  // partial bias sums
 };
 
-WgradPlan wgrad_plan(long long P, int Cin, int Cout)
+int wgrad_tc_bn(int Cout) { return Cout % 256 == 0 ? 256 : (Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32)); }
+
+// Pixel splits: enough CTAs for a few per SM over the tiles; each split a
+// whole number of 32-pixel steps.
+WgradPlan wgrad_plan(long long P, int Cin, int Cout, bool tc)
 {
     WgradPlan w;
     w.bmc = Cout % 64 == 0 ? 64 : 32;
-    long long base = (long long)(Cout / w.bmc) * 9 * (Cin / kBK);
+    w.tc_bn = tc ? wgrad_tc_bn(Cout) : 0;
+    long long base = tc ? ((9LL * Cin + 127) / 128) * (Cout / w.tc_bn) : (long long)(Cout / w.bmc) * 9 * (Cin / kBK);
     long long chunks = P / 32;
-    long long s = (4LL * 152 + base - 1) / base;
+    // tcgen05: one wave of CTAs at the occupancy the stages' shared memory
+    // allows (fewer splits also mean fewer partial sums to add up)
+    const long long res = !tc ? 4 : (w.tc_bn == 256 ? 2 : (w.tc_bn == 128 ? 3 : (w.tc_bn == 64 ? 4 : 5)));
+    long long s = tc ? std::max(1LL, 152 * res / base) : (4LL * 152 + base - 1) / base;
     if (s > chunks) s = chunks;
     if (s < 1) s = 1;
     long long per = (chunks + s - 1) / s;
@@ -1070,10 +1258,31 @@ WgradPlan wgrad_plan(long long P, int Cin, int Cout)
     return w;
 }
 
+// workspace for either kernel, so that a workspace sized once stays valid
+// when the kernel choice changes
 long long wgrad_ws_bytes(long long P, int Cin, int Cout)
 {
-    WgradPlan w = wgrad_plan(P, Cin, Cout);
-    return (w.part_floats + w.bias_floats) * (long long)sizeof(float);
+    long long b = 0;
+    for (int tc = 0; tc < 2; ++tc) {
+        WgradPlan w = wgrad_plan(P, Cin, Cout, tc != 0);
+        b = std::max(b, (w.part_floats + w.bias_floats) * (long long)sizeof(float));
+    }
+    return b;
+}
+
+template <int BN>
+cudaError_t wgrad_tc_launch(dim3 grid, const ConvSrc &S, const bf16 *dz, int H, int Wd, int Cout, int P, int pps,
+                            float *part, cudaStream_t st)
+{
+    static bool attr = false;  // per process; the attribute is per function
+    constexpr size_t sm = wgrad_tc_smem<BN>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_wgrad_tc<BN><<<grid, kThreads, sm, st>>>(S, dz, H, Wd, Cout, P, pps, part);
+    return cudaGetLastError();
 }
 
 cudaError_t wgrad_launch(const ConvSrc &S, const bf16 *dz, int B, int H, int Wd, int Cout, float *dW, float *db,
@@ -1081,12 +1290,24 @@ cudaError_t wgrad_launch(const ConvSrc &S, const bf16 *dz, int B, int H, int Wd,
 {
     long long P = (long long)B * H * Wd;
     int Cin = S.C0 + S.C1;
-    WgradPlan w = wgrad_plan(P, Cin, Cout);
-    dim3 grid((unsigned)(Cout / w.bmc), (unsigned)(9 * (Cin / kBK)), (unsigned)w.splits);
-    if (w.bmc == 64)
-        k_wgrad<64><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
-    else
-        k_wgrad<32><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
+    WgradPlan w = wgrad_plan(P, Cin, Cout, g_use_tc != 0);
+    if (w.tc_bn) {
+        dim3 grid((unsigned)((9 * Cin + 127) / 128), (unsigned)(Cout / w.tc_bn), (unsigned)w.splits);
+        cudaError_t e;
+        switch (w.tc_bn) {
+        case 256: e = wgrad_tc_launch<256>(grid, S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws, st); break;
+        case 128: e = wgrad_tc_launch<128>(grid, S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws, st); break;
+        case 64: e = wgrad_tc_launch<64>(grid, S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws, st); break;
+        default: e = wgrad_tc_launch<32>(grid, S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws, st); break;
+        }
+        if (e != cudaSuccess) return e;
+    } else {
+        dim3 grid((unsigned)(Cout / w.bmc), (unsigned)(9 * (Cin / kBK)), (unsigned)w.splits);
+        if (w.bmc == 64)
+            k_wgrad<64><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
+        else
+            k_wgrad<32><<<grid, 128, 0, st>>>(S, dz, H, Wd, Cout, (int)P, w.pix_per_split, ws);
+    }
     long long n = (long long)Cout * 9 * Cin;
     k_sum_parts<<<grid_for(n), 256, 0, st>>>(ws, w.splits, n, dW);
     if (db) {
@@ -1474,6 +1695,13 @@ int sp_conv3x3_set_kernel(int tcgen05)
 }
 
 int sp_conv3x3_get_kernel(void) { return g_use_tc; }
+
+int sp_conv3x3_set_wait_limit(long long cycles)
+{
+    if (cycles < 0) return SP_ERR_ARG;
+    if (cudaMemcpyToSymbol(g_tc_wait_limit, &cycles, sizeof cycles) != cudaSuccess) return SP_ERR_CUDA;
+    return SP_OK;
+}
 
 int sp_unet_device_error(void)
 {

@@ -41,6 +41,14 @@ def check_device_error():
         raise SpinError(rc, "a tensor-core pipeline wait timed out (outputs not written)")
 
 
+def set_wait_limit(cycles=1 << 32):
+    """Cycles a pipeline wait of the tcgen05 convolution polls before its CTA
+    gives up (0: at once); the default is 2^32."""
+    rc = lib().sp_conv3x3_set_wait_limit(int(cycles))
+    if rc:
+        raise SpinError(rc, "bad wait limit")
+
+
 def n_params():
     return int(lib().sp_unet_n_params())
 

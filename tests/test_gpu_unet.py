@@ -116,7 +116,7 @@ def test_conv_data_gradient(case, kernel):
     (1, 16, 16, 128, 0, 0, 256),
     (16, 32, 32, 32, 0, 0, 64),
 ])
-def test_conv_weight_gradient(case):
+def test_conv_weight_gradient(case, kernel):
     B, H, W, C0, up0, C1, Cout = case
     rng = np.random.default_rng(7 + C0 + Cout + B)
     h0, w0 = (H // 2, W // 2) if up0 else (H, W)
@@ -232,3 +232,50 @@ def test_network_rejects_bad_batches():
     f = torch.zeros((16, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(Exception):
         net.predict(s, f)  # more than batch_max
+
+
+def test_conv_pipeline_wait_that_runs_out_reports_and_leaves_the_device_usable():
+    """With a wait limit of zero every CTA of the tcgen05 convolution gives up
+    its first pipeline wait: it drains the MMAs it issued, frees its tensor
+    memory and writes nothing, and the device flag reports SP_ERR_TIMEOUT.
+    With the default limit restored the same call is correct again."""
+    old = UN.conv_kernel()
+    UN.set_conv_kernel("tcgen05")
+    UN.check_device_error()
+    B, H, W, C0, Cout = 2, 16, 16, 64, 64  # 18 K steps: the pipeline wait is reached
+    rng = np.random.default_rng(11)
+    s0, x0 = rand_bf(rng, (B, H, W, C0))
+    Wt, Wn = rand_bf(rng, (Cout, 9, C0), 1.0 / np.sqrt(9 * C0))
+    lib = UN.lib
+    try:
+        UN.set_wait_limit(0)
+        out = torch.full((B, H, W, Cout), 7.0, dtype=torch.bfloat16, device="cuda")
+        rc = lib().sp_conv3x3_forward(s0.data_ptr(), C0, 0, None, 0, Wt.data_ptr(), None, 0, None, B, H, W, Cout,
+                                      out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert rc == 0
+        assert lib().sp_unet_device_error() == -5  # SP_ERR_TIMEOUT
+        assert bool(torch.all(out == 7.0)), "a CTA whose wait ran out wrote outputs"
+    finally:
+        UN.set_wait_limit()
+    out = UN.conv3x3_forward(s0, Wt)
+    assert lib().sp_unet_device_error() == 0
+    ref = U.conv3x3(x0, Wn, np.zeros(Cout))
+    S = U.conv3x3(np.abs(x0), np.abs(Wn), np.zeros(Cout))
+    tol = 2.0 ** -8 * np.abs(ref) + 2 * 9 * C0 * 2.0 ** -24 * S
+    assert np.all(np.abs(f64(out) - ref) <= tol)
+    # the weight gradient's pipeline: 16 x 32 x 32 pixels give every split
+    # more stages than the pipeline holds, so its wait is reached
+    s0, x0 = rand_bf(rng, (16, 32, 32, C0))
+    dzt, dz = rand_bf(rng, (16, 32, 32, Cout))
+    try:
+        UN.set_wait_limit(0)
+        UN.conv3x3_wgrad(s0, dzt)
+        assert lib().sp_unet_device_error() == -5
+    finally:
+        UN.set_wait_limit()
+    dW, _ = UN.conv3x3_wgrad(s0, dzt)
+    assert lib().sp_unet_device_error() == 0
+    _, rW, _ = U.conv3x3_backward(x0, np.zeros((Cout, 9, C0)), dz)
+    _, SW, _ = U.conv3x3_backward(np.abs(x0), np.zeros((Cout, 9, C0)), np.abs(dz))
+    assert np.all(np.abs(dW.cpu().numpy() - rW) <= 2 * (16 * 32 * 32 + 1024) * 2.0 ** -24 * SW)
+    UN.set_conv_kernel(old)
