@@ -46,8 +46,11 @@ constexpr int rev5(int i)
 }
 
 // In-register radix-2 DIT FFT of 32 points (natural order in and out);
-// INV: conjugate twiddles (unnormalised inverse).
-template <bool INV> __device__ __forceinline__ void fft32(float2 (&a)[32])
+// INV: conjugate twiddles (unnormalised inverse).  The twiddles W^0 = 1 and
+// W^8 = -i (+i inverse) are applied exactly, without multiplications.
+// ZIN: the upper half of the input (a[16..31]) is zero, so the first
+// stage's butterflies reduce to copies (a zero-padded transform).
+template <bool INV, bool ZIN = false> __device__ __forceinline__ void fft32(float2 (&a)[32])
 {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -64,13 +67,20 @@ template <bool INV> __device__ __forceinline__ void fft32(float2 (&a)[32])
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int j = k % half, i0 = (k / half) * span + j, i1 = i0 + half;
+            if (ZIN && s == 1) {  // a[i1] came from an input index >= 16
+                a[i1] = a[i0];
+                continue;
+            }
+            const int w = j * (32 / span);
             float2 t;
-            if (j == 0) {
+            if (w == 0) {
                 t = a[i1];
+            } else if (w == 8) {
+                t = INV ? make_float2(-a[i1].y, a[i1].x) : make_float2(a[i1].y, -a[i1].x);
             } else {
-                float2 w = c_w32[j * (32 / span)];
-                if (INV) w.y = -w.y;
-                t = cm(a[i1], w);
+                float2 tw = c_w32[w];
+                if (INV) tw.y = -tw.y;
+                t = cm(a[i1], tw);
             }
             a[i1] = cs(a[i0], t);
             a[i0] = ca(a[i0], t);
@@ -78,41 +88,21 @@ template <bool INV> __device__ __forceinline__ void fft32(float2 (&a)[32])
     }
 }
 
-// Per-lane twiddles W_1024^(l k2): the base W^l and anchors W^(8 l), W^(16 l),
-// W^(24 l); the other powers follow by at most 7 multiplications.
-struct Tw {
-    float2 base, a8, a16, a24;
-};
-
-__device__ __forceinline__ Tw twiddles(int lane, bool inv)
-{
-    Tw t;
-    float s, c;
-    float sg = inv ? 1.f : -1.f;
-    sincospif(sg * (float)lane / 512.f, &s, &c);
-    t.base = make_float2(c, s);
-    sincospif(sg * (float)(8 * lane) / 512.f, &s, &c);
-    t.a8 = make_float2(c, s);
-    sincospif(sg * (float)(16 * lane) / 512.f, &s, &c);
-    t.a16 = make_float2(c, s);
-    sincospif(sg * (float)(24 * lane) / 512.f, &s, &c);
-    t.a24 = make_float2(c, s);
-    return t;
-}
+// Twiddles of the four-step transform, W_1024^(l k2) = exp(-2 pi i l k2 /
+// 1024) for k2 = 0..31 (rows) and lane l (contiguous), rounded from FP64 on
+// the host; the inverse uses their conjugates.
+__device__ float2 g_tw1024[32 * 32];
 
 // Four-step 1024-point FFT by one warp: on entry a[n2] = x[32 n2 + lane], on
 // exit a[k1] = X[lane + 32 k1].  tr: this warp's 32 x 33 transpose tile.
-template <bool INV> __device__ __forceinline__ void fft1024(float2 (&a)[32], float2 *tr, int lane, const Tw &tw)
+// ZIN: x[512..1023] = 0 (a[16..31] are not read).
+template <bool INV, bool ZIN = false> __device__ __forceinline__ void fft1024(float2 (&a)[32], float2 *tr, int lane)
 {
-    fft32<INV>(a);
-    float2 w = make_float2(1.f, 0.f);
+    fft32<INV, ZIN>(a);
 #pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-        if (k2 == 8) w = tw.a8;
-        else if (k2 == 16) w = tw.a16;
-        else if (k2 == 24) w = tw.a24;
-        else if (k2 > 0) w = cm(w, tw.base);
-        if (k2 > 0) a[k2] = cm(a[k2], w);
+    for (int k2 = 1; k2 < 32; ++k2) {
+        const float2 w = __ldg(&g_tw1024[k2 * 32 + lane]);
+        a[k2] = cm(a[k2], INV ? cj(w) : w);
     }
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) tr[k2 * 33 + lane] = a[k2];
@@ -137,16 +127,16 @@ __global__ void __launch_bounds__(64 * kRows) k_rows(int n0, int n1, const float
     int y0 = blockIdx.x * kRows, y = y0 + w;
     bool row = y < n1;
     allow_dependents();
-    Tw tw = twiddles(lane, false);
     wait_prerequisite();  // the spins may come from the pass just before
     float2 a[32];
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) {
+    for (int n2 = 0; n2 < 16; ++n2) {  // x < 512: the upper half is padding
         int x = 32 * n2 + lane;
         float4 v = (row && x < n0) ? __ldg(&n[(long)y * n0 + x]) : make_float4(0.f, 0.f, 0.f, 0.f);
         a[n2] = part ? make_float2(v.x, v.y) : make_float2(v.z, 0.f);
+        a[n2 + 16] = make_float2(0.f, 0.f);
     }
-    fft1024<false>(a, tr, lane, tw);
+    fft1024<false, true>(a, tr, lane);
     if (part == 0) {
 #pragma unroll
         for (int k1 = 0; k1 <= 16; ++k1) {
@@ -187,6 +177,11 @@ __device__ __forceinline__ void cp16(void *smem, const void *gmem)
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
+__device__ __forceinline__ void cp8(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
 
 __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, const float *__restrict__ Kt)
 {
@@ -203,16 +198,16 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
     allow_dependents();
     for (int t = threadIdx.x; t < 6 * 1024 / 4; t += blockDim.x) cp16(ks + 4 * t, K + 4 * t);
     asm volatile("cp.async.commit_group;\n" ::);
-    Tw twf = twiddles(lane, false);
     wait_prerequisite();  // the row spectra
     float2 *col = ST + ((long)c * 513 + kx) * n1;
     float2 a[32];
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) {
+    for (int n2 = 0; n2 < 16; ++n2) {  // y < 512: the upper half is padding
         int y = 32 * n2 + lane;
         a[n2] = y < n1 ? col[y] : make_float2(0.f, 0.f);
+        a[n2 + 16] = make_float2(0.f, 0.f);
     }
-    fft1024<false>(a, tr, lane, twf);
+    fft1024<false, true>(a, tr, lane);
     __syncthreads();  // every warp is done with its transpose tile
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) spec[c * 1024 + lane + 32 * k1] = a[k1];
@@ -230,7 +225,7 @@ __global__ void __launch_bounds__(96) k_cols(int n1, float2 *__restrict__ ST, co
         a[n2] = make_float2(r0 * X.x + r1 * Y.x + r2 * Z.x, r0 * X.y + r1 * Y.y + r2 * Z.y);
     }
     __syncthreads();  // every warp has read the spectra before the tiles reuse them
-    fft1024<true>(a, tr, lane, twiddles(lane, true));
+    fft1024<true>(a, tr, lane);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) {
         int y = lane + 32 * k1;
@@ -251,12 +246,16 @@ __global__ void __launch_bounds__(64 * kRows) k_irows(int n0, int n1, const floa
     int w = wid >> 1, part = wid & 1;
     int y0 = blockIdx.x * kRows, y = y0 + w;
     allow_dependents();
-    Tw tw = twiddles(lane, true);
     wait_prerequisite();  // the column pass's spectra
     for (int t = threadIdx.x; t < 3 * 513 * kRows; t += blockDim.x) {
         int r = t % kRows, ck = t / kRows;
-        stage[t] = (y0 + r < n1) ? ST[(long)ck * n1 + y0 + r] : make_float2(0.f, 0.f);
+        if (y0 + r < n1)
+            cp8(stage + t, ST + (long)ck * n1 + y0 + r);
+        else
+            stage[t] = make_float2(0.f, 0.f);
     }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     float2 a[32];
 #pragma unroll
@@ -276,7 +275,7 @@ __global__ void __launch_bounds__(64 * kRows) k_irows(int n0, int n1, const floa
             a[n2] = make_float2(X.x - Y.y, X.y + Y.x);  // X + i Y
         }
     }
-    fft1024<true>(a, tr, lane, tw);
+    fft1024<true>(a, tr, lane);
     if (part == 0) {
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) zs[w * 512 + lane + 32 * k1] = a[k1].x;
@@ -299,6 +298,18 @@ static_assert(3 * kTr >= 3 * 1024, "the transpose tiles must cover the spectra t
 
 cudaError_t dipole_fast_setup()
 {
+    static bool table = false;  // per process
+    if (!table) {
+        float2 tw[32 * 32];
+        for (int k2 = 0; k2 < 32; ++k2)
+            for (int l = 0; l < 32; ++l) {
+                const double ph = -2.0 * M_PI * (double)(k2 * l) / 1024.0;
+                tw[k2 * 32 + l] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+            }
+        cudaError_t e = cudaMemcpyToSymbol(g_tw1024, tw, sizeof tw);
+        if (e != cudaSuccess) return e;
+        table = true;
+    }
     cudaError_t e = cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_irows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem);

@@ -284,10 +284,13 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16])
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// + the CTA's tap table: for each of the 9 taps and 128 pixels the source
+// pixel index in src0's grid and in the full-resolution grid (2 x 4.5 KB)
+constexpr int kTapTable = 2 * 9 * kBM * 4;
 template <int BN>
 constexpr size_t conv_tc_smem()
 {
-    return 1024 + (size_t)kTcStages * (kBM * 64 + BN * 64) + 8 * kTcStages + 16;
+    return 1024 + (size_t)kTcStages * (kBM * 64 + BN * 64) + 8 * kTcStages + 16 + 16 + kTapTable;
 }
 
 template <int BN>
@@ -306,6 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
     const unsigned bar0 = base + kTcStages * STAGE;
     const unsigned slot = bar0 + 8 * kTcStages;
     volatile unsigned *slot_ptr = reinterpret_cast<volatile unsigned *>(smem_raw + (slot - raw));
+    int *tq = reinterpret_cast<int *>(smem_raw + (slot + 16 - raw));  // [2][9][kBM]
 
     const int Cin = S.C0 + S.C1, nkc = Cin / kBK, nk = 9 * nkc;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
@@ -313,27 +317,45 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
     const int HW = H * W;
     const long long wait_limit = g_tc_wait_limit;
     const int ar = tid >> 2, ac = tid & 3;
-    int pb[2], py[2], px[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        int p = m0 + ar + 64 * j;
-        pb[j] = p / HW;
-        int q = p - pb[j] * HW;
-        py[j] = q / W;
-        px[j] = q - py[j] * W;
+    // the tap table, once per CTA: pixel indices of every (tap, pixel) with
+    // the periodic wrap applied, so that a stage's copies only add offsets
+    for (int e = tid; e < 9 * kBM; e += kThreads) {
+        const int t = e / kBM, p = m0 + (e - t * kBM);
+        const int b = p / HW, q = p - b * HW, y = q / W, x = q - y * W;
+        const int yy = wrap(y + t / 3 - 1, H), xx = wrap(x + t % 3 - 1, W);
+        const int full = (b * H + yy) * W + xx;
+        tq[e] = S.up0 ? (b * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1) : full;
+        tq[9 * kBM + e] = full;
     }
-    auto load = [&](int k, int stage) {
-        int t = k / nkc, cc = (k - t * nkc) * kBK;
-        int dy = t / 3 - 1, dx = t % 3 - 1;
-        unsigned sa = base + stage * STAGE;
+    // this thread's weight rows: chunk idx = tid + 256 i of the BN x 4 chunks
+    constexpr int BW = (BN * 4 + kThreads - 1) / kThreads;
+    const bf16 *wrow[BW];
+    unsigned woff[BW];
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
-            cp16(sa + swz64(ar + 64 * j, ac),
-                 src_at(S, pb[j], wrap(py[j] + dy, H), wrap(px[j] + dx, W), H, W, cc + ac * 8));
-        unsigned sb = sa + A_BYTES;
-        for (int idx = tid; idx < BN * 4; idx += kThreads) {
-            int r = idx >> 2, c = idx & 3;
-            cp16(sb + swz64(r, c), Wk + (size_t)(n0 + r) * 9 * Cin + t * Cin + cc + c * 8);
+    for (int i = 0; i < BW; ++i) {
+        const int idx = tid + kThreads * i, r = idx >> 2, c = idx & 3;
+        wrow[i] = Wk + (size_t)(n0 + (idx < BN * 4 ? r : 0)) * 9 * Cin + c * 8;
+        woff[i] = swz64(r, c);
+    }
+    const unsigned aoff0 = swz64(ar, ac), aoff1 = swz64(ar + 64, ac);
+    // the next stage to load: K step k_ld = tap t_ld, channels [cc_ld, cc_ld + 32)
+    int k_ld = 0, t_ld = 0, cc_ld = 0;
+    auto load = [&](int stage) {
+        const unsigned sa = base + stage * STAGE;
+        const int *q = tq + (cc_ld < S.C0 ? 0 : 9 * kBM) + t_ld * kBM + ar;
+        const bf16 *src = cc_ld < S.C0 ? S.s0 + cc_ld + ac * 8 : S.s1 + (cc_ld - S.C0) + ac * 8;
+        const int cs = cc_ld < S.C0 ? S.C0 : S.C1;
+        cp16(sa + aoff0, src + (size_t)q[0] * cs);
+        cp16(sa + aoff1, src + (size_t)q[64] * cs);
+        const unsigned sb = sa + A_BYTES;
+#pragma unroll
+        for (int i = 0; i < BW; ++i)
+            if (tid + kThreads * i < BN * 4) cp16(sb + woff[i], wrow[i] + k_ld * kBK);
+        ++k_ld;
+        cc_ld += kBK;
+        if (cc_ld == Cin) {
+            cc_ld = 0;
+            ++t_ld;
         }
     };
 
@@ -347,13 +369,13 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    __syncthreads();  // also publishes the tap table
     tc_fence_after();
     const unsigned tmem = *slot_ptr;
 
 #pragma unroll
     for (int s = 0; s < kTcStages - 1; ++s) {
-        if (s < nk) load(s, s);
+        if (s < nk) load(s);
         cp_commit();
     }
     int failed = 0, issued = 0;
@@ -378,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvSrc S, const bf16 *__r
         if (kn < nk) {
             const int sn = kn % kTcStages;  // the stage the MMAs of iteration k-1 read
             if (k >= 1 && !mbar_wait(bar0 + 8 * sn, ((k - 1) / kTcStages) & 1, wait_limit)) failed = 1;
-            if (!failed) load(kn, sn);
+            if (!failed) load(sn);
         }
         cp_commit();
     }
@@ -751,16 +773,34 @@ __global__ void __launch_bounds__(kThreads) k_wgrad_tc(ConvSrc S, const bf16 *__
     const int a_t = a_on ? r_run / Cin : 0;
     const int a_ci = (a_on ? r_run - a_t * Cin : 0) + 8 * ag;
     const int a_dy = a_t / 3 - 1, a_dx = a_t % 3 - 1;
+    // this thread's two pixels of the stage to load next, (b, y, x), advanced
+    // by kWgPix pixels per stage
+    int lb[2], ly[2], lx[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int p = p_begin + apx + 16 * j;
+        lb[j] = p / HW;
+        const int q = p - lb[j] * HW;
+        ly[j] = q / W;
+        lx[j] = q - ly[j] * W;
+    }
     auto load = [&](int k, int stage) {
         const int pk = p_begin + k * kWgPix;
         const unsigned sa = base + stage * STAGE, sb = sa + A_BYTES;
         if (a_on) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int px = apx + 16 * j, p = pk + px;
-                const int b = p / HW, q = p - b * HW, y = q / W, x = q - y * W;
+                const int px = apx + 16 * j;
                 cp16(sa + (ar * 4 + (px >> 3)) * 512 + swz64(px & 7, ag),
-                     src_at(S, b, wrap(y + a_dy, H), wrap(x + a_dx, W), H, W, a_ci));
+                     src_at(S, lb[j], wrap(ly[j] + a_dy, H), wrap(lx[j] + a_dx, W), H, W, a_ci));
+                lx[j] += kWgPix;
+                while (lx[j] >= W) {
+                    lx[j] -= W;
+                    if (++ly[j] == H) {
+                        ly[j] = 0;
+                        ++lb[j];
+                    }
+                }
             }
         }
 #pragma unroll
