@@ -46,6 +46,12 @@ __device__ __forceinline__ void cp16(unsigned dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
+// the same through L1 (the weight gradient's taps re-read shifted copies of
+// the same input rows; measured slower for the forward convolution)
+__device__ __forceinline__ void cp16_ca(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
@@ -454,11 +460,6 @@ constexpr int kWsStages = 6;
 constexpr int kWsLoaders = 224;  // warps 0-6
 constexpr int kWsRows = (kBM * 4 + kWsLoaders - 1) / kWsLoaders;  // A chunks per loader (3)
 
-__device__ __forceinline__ void cp16_ca(unsigned dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
-}
-
 __device__ __forceinline__ void cp_arrive_noinc(unsigned bar)
 {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
@@ -791,8 +792,8 @@ __global__ void __launch_bounds__(kThreads) k_wgrad_tc(ConvSrc S, const bf16 *__
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int px = apx + 16 * j;
-                cp16(sa + (ar * 4 + (px >> 3)) * 512 + swz64(px & 7, ag),
-                     src_at(S, lb[j], wrap(ly[j] + a_dy, H), wrap(lx[j] + a_dx, W), H, W, a_ci));
+                cp16_ca(sa + (ar * 4 + (px >> 3)) * 512 + swz64(px & 7, ag),
+                        src_at(S, lb[j], wrap(ly[j] + a_dy, H), wrap(lx[j] + a_dx, W), H, W, a_ci));
                 lx[j] += kWgPix;
                 while (lx[j] >= W) {
                     lx[j] -= W;
