@@ -929,6 +929,58 @@ def run_hessian(args):
     return 0
 
 
+# (lattice side, channels from the level below or the previous layer,
+# upsampled, skip channels, output channels): the distinct convolution shapes
+# of the network at 128 x 128
+UNET_SHAPES = [(128, 32, 0, 0, 32), (128, 64, 1, 32, 32), (64, 64, 0, 0, 64), (32, 128, 0, 0, 128),
+               (32, 256, 1, 128, 128), (16, 256, 0, 0, 256)]
+
+
+def unet_layer_times(batch, reps=20):
+    """Per-shape device times of the 3x3 convolution (forward) and its
+    weight gradient for each convolution kernel, batch `batch` (CUDA events
+    around `reps` launches after three warm-up launches)."""
+    import torch
+    from paper_1901_11350_gb300 import unet as UN
+
+    old = UN.conv_kernel()
+    g = torch.Generator(device="cuda").manual_seed(0)
+
+    def rnd(*shape):
+        return (torch.randn(*shape, device="cuda", generator=g) * 0.5).to(torch.bfloat16)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = []
+    for L, c0, up, c1, co in UNET_SHAPES:
+        h = L // 2 if up else L
+        s0, s1 = rnd(batch, h, h, c0), (rnd(batch, L, L, c1) if c1 else None)
+        dz, w = rnd(batch, L, L, co), rnd(co, 9, c0 + c1) * 0.05
+        flops = 2.0 * batch * L * L * co * 9 * (c0 + c1)
+        row = {"L": L, "cin": c0 + c1, "cout": co, "upsampled": bool(up)}
+        for k in ("mma", "tcgen05", "tcgen05_ws"):
+            UN.set_conv_kernel(k)
+            ms = timed(lambda: UN.conv3x3_forward(s0, w, None, src1=s1, up0=bool(up)))
+            row["forward_" + k] = {"ms": ms, "tflops": flops / ms / 1e9}
+            if k != "tcgen05_ws":  # kernel 2 shares the weight gradient of kernel 1
+                ms = timed(lambda: UN.conv3x3_wgrad(s0, dz, src1=s1, up0=bool(up)))
+                row["wgrad_" + k] = {"ms": ms, "tflops": flops / ms / 1e9}
+            UN.check_device_error()
+        out.append(row)
+    UN.set_conv_kernel(old)
+    return out
+
+
 def run_unet(args):
     """The warm-start network alone (BF16 U-Net, 128x128 inputs, batch 64):
     training samples/s of a full step (forward, backward, Adam) and
@@ -995,6 +1047,9 @@ def run_unet(args):
                         "note": "whole training step (all kernels) against the convolution FLOPs x 3"},
            "predict": {"ms": res["predict"][0], "tflops": res["predict"][1],
                        "frac": res["predict"][1] / peaks["bf16_tflops"], "samples_per_s": bm / (res["predict"][0] / 1e3)}}
+    if args.unet_layers:
+        del net
+        out["layers"] = unet_layer_times(bm)
     print(json.dumps(out))
     return 0
 
@@ -1107,6 +1162,8 @@ def main():
     ap.add_argument("--gneb-persistent", type=int, default=-1, choices=[-1, 0, 1],
                     help="gneb48: 1 = one persistent cooperative launch per call, 0 = one launch per pass, "
                          "-1 (default) = chosen by the autotuner")
+    ap.add_argument("--unet-layers", action="store_true",
+                    help="unet: add per-shape forward and weight-gradient times of every convolution kernel")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")
     ap.add_argument("--no-relax", action="store_true",
                     help="sc128: skip the relaxation half of the metric (GNEB batch, warm start)")
