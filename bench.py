@@ -56,6 +56,12 @@ METHOD_STEP_BYTES = {"heun": 80, "depondt": 80, "sib": 80}
 CORRECTOR_LAUNCHES = {"heun": 1, "depondt": 1, "sib": 1, "rk4": 3}
 KERNEL_SOURCES = ["paper_1901_11350_gb300/csrc/field_llg.cu", "paper_1901_11350_gb300/csrc/cubic.cu",
                   "paper_1901_11350_gb300/csrc/common.cuh"]
+# GNEB: bytes per spin and iteration of the method's three passes with FP32
+# records (read n, write g 32; read the three images and g 64; read n, g, v
+# and write n, v 80, plus the per-image reductions' re-reads, about 190) and
+# of this design's four passes (move 80, field 48, tangent 80, force 96)
+GNEB_METHOD_BYTES = 190
+GNEB_DESIGN_BYTES = 304
 
 
 def rank_info():
@@ -451,10 +457,10 @@ def gneb_result(args, compact=False):
            "barrier_rel_diff_f32_batch_vs_f64": {"max": float(np.max(np.abs(bar32 - bar64) / np.abs(bar64))),
                                                  "median": float(np.median(np.abs(bar32 - bar64) / np.abs(bar64)))},
            "setup_s": prep_s}
-    # per-iteration roofline over the full batch: algorithmic bytes per spin
-    # and iteration (FP32 records): move 80 (read F, v, x; write v, x), field
-    # 48 (x, next image; write Pg), tangent 80 (three images, Pg; write tau),
-    # force 96 (tau, Pg, F, v; write v, F)
+    # per-iteration roofline over the full batch (GNEB_METHOD_BYTES; the
+    # design's passes move GNEB_DESIGN_BYTES: move 80 (read F, v, x; write v,
+    # x), field 48 (x, next image; write Pg), tangent 80 (three images, Pg;
+    # write tau), force 96 (tau, Pg, F, v; write v, F))
     import torch
     offs, Ms, ctxs, off = [], [], [], 0
     for ch in chains:
@@ -474,10 +480,12 @@ def gneb_result(args, compact=False):
     torch.cuda.synchronize()
     it_s = e0.elapsed_time(e1) / 64 / 1e3
     peaks, pk = measured_peaks()
-    gbs = 304 * off / it_s / 1e9
+    gbs = GNEB_METHOD_BYTES * off / it_s / 1e9
     out["roofline"] = {"bound": "hbm", "kernel": "one GNEB iteration of all chains (move, field, tangent, force)",
                        "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                       "traffic": None, "peak_source": pk, "algorithmic_bytes_per_spin_iteration": 304,
+                       "traffic": None, "peak_source": pk, "algorithmic_bytes_per_spin_iteration": GNEB_METHOD_BYTES,
+                       "design_bytes_per_spin_iteration": GNEB_DESIGN_BYTES,
+                       "design_frac": GNEB_DESIGN_BYTES * off / it_s / 1e9 / peaks["hbm_gbs"],
                        "ms_per_iteration": it_s * 1e3}
     # the oracle on the largest chain, scaled to the spin-iterations this run needed
     import oracle
