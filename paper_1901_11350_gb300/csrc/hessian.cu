@@ -45,7 +45,8 @@ int grow_h(DevBuf &b, size_t bytes)
 // the field of the projected w without the Zeeman term.
 template <typename T>
 __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> S, const rec_t<T> *__restrict__ n,
-                                             const rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ out)
+                                             const rec_t<T> *__restrict__ v, rec_t<T> *__restrict__ out,
+                                             unsigned *status = nullptr)
 {
     allow_dependents();
     wait_prerequisite();  // n and v may come from the kernels before
@@ -72,6 +73,13 @@ __global__ void __launch_bounds__(kHB) k_hvp(const __grid_constant__ Stencil<T> 
     // P (Hbar w) with Hbar w = -Lw, plus the Weingarten term (n . B) w
     v3<T> r3 = (dot(Lw, ni) * ni - Lw) + dot(ni, Bn) * wi;
     st(out, i, r3);
+    // status != null: a non-finite product sets the Hessian bit of the
+    // context's status word (the check of the output, without a second pass)
+    if (status) {
+        const bool bad = !(isfinite(r3.x) && isfinite(r3.y) && isfinite(r3.z));
+        const unsigned act = __activemask();
+        if (__any_sync(act, bad) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr_system(status, (unsigned)SITE_HESSIAN);
+    }
 }
 
 // out = v projected per spin onto the tangent plane of n
@@ -483,12 +491,14 @@ int sp_hessian_apply(sp_ctx *c, const void *n_dev, const void *v_dev, void *out_
     if (!hrecords_aligned(c, {n_dev, v_dev, out_dev})) return hfail(c, SP_ERR_ARG, "misaligned record array");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned nb = hblocks(c->N);
+    unsigned *w = status_word(c);
+    if (!w) return hfail(c, SP_ERR_CUDA, "status word");
     cudaError_t e = c->prec == SP_F64 ? launch_pdl(k_hvp<double>, dim3(nb), dim3(kHB), 0, st, c->Sd, (const dq4 *)n_dev,
-                                                   (const dq4 *)v_dev, (dq4 *)out_dev)
+                                                   (const dq4 *)v_dev, (dq4 *)out_dev, w)
                                       : launch_pdl(k_hvp<float>, dim3(nb), dim3(kHB), 0, st, c->Sf,
-                                                   (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev);
+                                                   (const float4 *)n_dev, (const float4 *)v_dev, (float4 *)out_dev, w);
     if (e != cudaSuccess) return hfail(c, SP_ERR_CUDA, "Hessian launch failed");
-    return status_check_records(c, out_dev, c->N, SITE_HESSIAN, st);
+    return SP_OK;
 }
 
 int sp_lowest_mode(sp_ctx *c, const void *n_dev, void *mode_dev, int krylov, double *lambda, void *stream)

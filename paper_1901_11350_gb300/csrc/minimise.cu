@@ -432,12 +432,23 @@ __device__ __forceinline__ double slope_of(const double *scal, int g)
 // images' energies and slopes), by adaptive Simpson with Lyness' criterion
 // and Richardson correction to 1e-13 h, subdivision depth at most 40 (an
 // explicit stack of at most 41 intervals).
+// The per-image scalars below are computed both by one-thread-per-image
+// kernels and inside the persistent kernel; every product and sum is written
+// with the non-contracting intrinsics, so that the two give the same bits
+// whatever fused multiply-adds the compiler would otherwise form.
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
 __device__ double seg_integrand(double Ea, double Eb, double da, double db, double h, double w, double s)
 {
-    double t = s / h;
-    double dE = ((6 * t * t - 6 * t) * Ea + (-6 * t * t + 6 * t) * Eb) / h + (3 * t * t - 4 * t + 1) * da +
-                (3 * t * t - 2 * t) * db;
-    return sqrt((1 - w) * (1 - w) + w * w * dE * dE);
+    double t = s / h, t2 = dmul(t, t);
+    double c6 = dadd(dmul(6.0, t2), -dmul(6.0, t));  // 6 t^2 - 6 t
+    double ce = dadd(dmul(c6, Ea), dmul(-c6, Eb)) / h;
+    double ca = dadd(dadd(dmul(3.0, t2), -dmul(4.0, t)), 1.0);  // 3 t^2 - 4 t + 1
+    double cb = dadd(dmul(3.0, t2), -dmul(2.0, t));            // 3 t^2 - 2 t
+    double dE = dadd(dadd(ce, dmul(ca, da)), dmul(cb, db));
+    double u = 1.0 - w;
+    return sqrt(dadd(dmul(u, u), dmul(dmul(w, w), dmul(dE, dE))));
 }
 
 __device__ double seg_length(double Ea, double Eb, double da, double db, double h, double w)
@@ -451,16 +462,17 @@ __device__ double seg_length(double Ea, double Eb, double da, double db, double 
     int sp = 0;
     double fa = seg_integrand(Ea, Eb, da, db, h, w, 0.0), fm = seg_integrand(Ea, Eb, da, db, h, w, 0.5 * h),
            fb = seg_integrand(Ea, Eb, da, db, h, w, h);
-    stk[sp++] = Iv{0.0, h, fa, fm, fb, h / 6 * (fa + 4 * fm + fb), 1e-13 * h, 40};
+    stk[sp++] = Iv{0.0, h, fa, fm, fb, dmul(h / 6, dadd(dadd(fa, dmul(4.0, fm)), fb)), 1e-13 * h, 40};
     double total = 0.0;
     while (sp > 0) {
         Iv c = stk[--sp];
         double m = 0.5 * (c.a + c.b), lm = 0.5 * (c.a + m), rm = 0.5 * (m + c.b);
         double flm = seg_integrand(Ea, Eb, da, db, h, w, lm), frm = seg_integrand(Ea, Eb, da, db, h, w, rm);
-        double left = (m - c.a) / 6 * (c.fa + 4 * flm + c.fm), right = (c.b - m) / 6 * (c.fm + 4 * frm + c.fb);
-        double d = left + right - c.whole;
+        double left = dmul((m - c.a) / 6, dadd(dadd(c.fa, dmul(4.0, flm)), c.fm));
+        double right = dmul((c.b - m) / 6, dadd(dadd(c.fm, dmul(4.0, frm)), c.fb));
+        double d = dadd(dadd(left, right), -c.whole);
         if (c.depth <= 0 || fabs(d) <= 15 * c.eps) {
-            total += left + right + d / 15;
+            total = dadd(total, dadd(dadd(left, right), d / 15));
         } else {
             // right half below the left one: the left half is finished first
             stk[sp++] = Iv{m, c.b, c.fm, frm, c.fb, right, 0.5 * c.eps, c.depth - 1};
@@ -511,14 +523,14 @@ __device__ __forceinline__ double force_coef(const ImgInfo &im, int g, double ks
     }
     double tt = scal[kS * g + kTT];
     double inv = tt > 0 ? 1.0 / sqrt(tt) : 0.0;
-    double gt = scal[kS * g + kGT] * inv;
-    double fs = weighted ? kspring * (lw_g - lw_gm)
-                         : kspring * (sqrt(scal[kS * g + kL2]) - sqrt(scal[kS * (g - 1) + kL2]));
+    double gt = dmul(scal[kS * g + kGT], inv);
+    double fs = weighted ? dmul(kspring, lw_g - lw_gm)
+                         : dmul(kspring, sqrt(scal[kS * g + kL2]) - sqrt(scal[kS * (g - 1) + kL2]));
     int kind = im.kind >= 0 ? im.kind : (im.nu == ci ? SP_IMAGE_CLIMBING : SP_IMAGE_NORMAL);
     // climbing: tangential component inverted, no spring; falling: the full
     // projected gradient, no spring (descends to a minimum along the path)
-    double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : gt + fs);
-    return coef * inv;
+    double coef = kind == SP_IMAGE_CLIMBING ? 2.0 * gt : (kind == SP_IMAGE_FALLING ? 0.0 : dadd(gt, fs));
+    return dmul(coef, inv);
 }
 
 __global__ void k_g_coef(const ImgInfo *__restrict__ img, int n_img, double kspring, int climbing, int weighted,
