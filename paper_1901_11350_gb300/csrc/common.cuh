@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cstddef>
 #include <stdint.h>
 
 #include "spirit_gb.h"
@@ -201,7 +202,7 @@ __device__ __forceinline__ int fdiv(int n, const FastDiv &f)
 // Everything a kernel needs to evaluate the local part of Eq. 1 at a spin:
 // lattice extents, per-basis on-site terms and the neighbour stencil.  Passed
 // by value as a __grid_constant__ kernel parameter (about 3-5 KB).
-template <typename T> struct Stencil {
+template <typename T> struct alignas(16) Stencil {
     int nb, n0, n1, n2, per0, per1, per2, N;
     int r0, r1, r2;             // largest |d| of the entries along each direction
     FastDiv fnb, fn0, fn1;      // division by nb, n0, n1
@@ -212,6 +213,23 @@ template <typename T> struct Stencil {
     T Kh[SP_MAX_BASIS][3];      // anisotropy axis
     NbrEntry<T> e[SP_MAX_NBR];
 };
+
+static_assert(sizeof(Stencil<float>) % 16 == 0 && sizeof(Stencil<double>) % 16 == 0, "16-byte copies of a stencil");
+
+// Copy of the part of a stencil in global memory that is in use (header and
+// the entries of every basis atom) into shared memory, by the whole block;
+// the block's later per-neighbour reads then come from shared memory.
+template <typename T>
+__device__ __forceinline__ void stage_stencil(const Stencil<T> *__restrict__ g, Stencil<T> *s)
+{
+    const int ne = g->off[g->nb];
+    const size_t bytes = offsetof(Stencil<T>, e) + (size_t)ne * sizeof(NbrEntry<T>);
+    const int n16 = (int)((bytes + 15) / 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(g);
+    uint4 *dst = reinterpret_cast<uint4 *>(s);
+    for (int k = threadIdx.x; k < n16; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
 
 // Periodic wrap for |d| <= n (checked on the host); -1 across an open edge.
 __device__ __forceinline__ int wrap(int x, int n, int per)

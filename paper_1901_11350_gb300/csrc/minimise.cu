@@ -284,7 +284,10 @@ __device__ __forceinline__ void g_field_body(int vb, const BlkInfo *__restrict__
 {
     BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
-    const Stencil<T> &St = S[im.chain];
+    // the chain's stencil, staged in shared memory for the neighbour loop
+    __shared__ __align__(16) unsigned char st_raw[sizeof(Stencil<T>)];
+    Stencil<T> &St = *reinterpret_cast<Stencil<T> *>(st_raw);
+    stage_stencil(S + im.chain, &St);
     int i = bi.t * kBlock + threadIdx.x;
     const R *xb = x + im.spin0 + (long long)im.nu * im.N;
     // energy and squared angle sums: FP64, or float-float for FP32 (the
