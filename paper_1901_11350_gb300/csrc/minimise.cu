@@ -736,12 +736,15 @@ __global__ void __launch_bounds__(kBlock) k_g_persistent(const __grid_constant__
 __global__ void k_g_finish(const ImgInfo *__restrict__ img, int n_img, const double *scal, double *E, double *fmax_out,
                            int n_chains)
 {
-    for (int g = threadIdx.x; g < n_img; g += blockDim.x) E[g] = scal[kS * g + kE];
-    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+    // one thread per image; the thread of each chain's image 0 also takes the
+    // chain's max force over its interior images (in image order)
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_img; g += gridDim.x * blockDim.x) {
+        E[g] = scal[kS * g + kE];
+        const ImgInfo im = img[g];
+        if (im.nu != 0 || im.chain >= n_chains) continue;
         double m = 0;
-        for (int g = 0; g < n_img; ++g)
-            if (img[g].chain == c && img[g].nu > 0 && img[g].nu < img[g].M - 1) m = nan_max(m, scal[kS * g + kFMAX]);
-        fmax_out[c] = sqrt(m);  // the slot holds max |F|^2
+        for (int nu = 1; nu < im.M - 1; ++nu) m = nan_max(m, scal[kS * (im.g0 + nu) + kFMAX]);
+        fmax_out[im.chain] = sqrt(m);  // the slot holds max |F|^2
     }
 }
 
@@ -1108,7 +1111,7 @@ int gneb_batch_run(MinScratch **sp, const std::vector<Stencil<T>> &stencils, con
     }
     for (; remaining > 0; --remaining) iteration(st);
     if (a.n_iter > 0) k_g_move<T><<<n_blk, kBlock, 0, st>>>(B, I, x, v, F, a.dt, dt2_2m, 2, scal);
-    k_g_finish<<<1, 256, 0, st>>>(I, n_img, scal, E_dev, fmax_dev, C);
+    k_g_finish<<<(n_img + 255) / 256, 256, 0, st>>>(I, n_img, scal, E_dev, fmax_dev, C);
     return cudaGetLastError() == cudaSuccess ? 0 : SP_ERR_CUDA;
 }
 
