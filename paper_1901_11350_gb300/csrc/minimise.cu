@@ -367,9 +367,10 @@ __device__ __forceinline__ void g_tangent_body(int vb, const BlkInfo *__restrict
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     bool end = im.nu == 0 || im.nu == im.M - 1;
-    // weights of the forward and backward differences
-    __shared__ T s_wp, s_wm;
-    if (threadIdx.x == 0 && !end) {
+    // weights of the forward and backward differences, read (or computed
+    // from the three energies) by every thread: no block barrier
+    T s_wp = T(0), s_wm = T(0);
+    if (!end) {
         if (LOCALW) {
             double wp, wm;
             tangent_weights(scal, bi.g, &wp, &wm);
@@ -380,7 +381,6 @@ __device__ __forceinline__ void g_tangent_body(int vb, const BlkInfo *__restrict
             s_wm = (T)scal[kS * bi.g + kWM];
         }
     }
-    __syncthreads();
     using A = typename Acc<T>::type;
     A r[2] = {A{}, A{}};
     if (i < im.N && end) {
@@ -563,20 +563,24 @@ __device__ __forceinline__ void g_force_body(int vb, const BlkInfo *__restrict__
     if (im.nu == 0 || im.nu == im.M - 1) return;
     // the image's force is -G + a Tau (a from k_g_coef, or computed here from
     // the same slots by the same function)
-    __shared__ T s_a;
-    if (threadIdx.x == 0) {
-        if (LOCALC) {
+    // (k_g_coef's slot: every thread reads it, no block barrier; computed in
+    // place: thread 0 evaluates it once and the block waits)
+    __shared__ T sh_a;
+    T s_a;
+    if (LOCALC) {
+        if (threadIdx.x == 0) {
             double lw = 0, lwm = 0;
             if (ca.weighted) {
                 lw = segment_of(scal, bi.g, ca.w);
                 lwm = segment_of(scal, bi.g - 1, ca.w);
             }
-            s_a = (T)force_coef(im, bi.g, ca.kspring, ca.climbing, ca.weighted, scal, lw, lwm);
-        } else {
-            s_a = (T)scal[kS * bi.g + kA];
+            sh_a = (T)force_coef(im, bi.g, ca.kspring, ca.climbing, ca.weighted, scal, lw, lwm);
         }
+        __syncthreads();
+        s_a = sh_a;
+    } else {
+        s_a = (T)scal[kS * bi.g + kA];
     }
-    __syncthreads();
     int i = bi.t * kBlock + threadIdx.x;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     using A = typename Acc<T>::type;
@@ -612,15 +616,15 @@ __device__ __forceinline__ void g_move_body(int vb, const BlkInfo *__restrict__ 
     BlkInfo bi = blk[vb];
     ImgInfo im = img[bi.g];
     if (im.nu == 0 || im.nu == im.M - 1) return;
-    __shared__ T s_c;  // projection coefficient of the last force pass
-    if (threadIdx.x == 0 && mode >= 1) s_c = (T)scal[kS * bi.g + kC];
-    __syncthreads();
+    // projection coefficient of the last force pass: every thread reads the
+    // image's slot (one broadcast load, no block barrier)
+    const T c = mode >= 1 ? (T)scal[kS * bi.g + kC] : T(0);
     int i = bi.t * kBlock + threadIdx.x;
     if (i >= im.N) return;
     long long p = im.spin0 + (long long)im.nu * im.N + i;
     v3<T> vi;
     if (mode >= 1) {
-        vi = s_c * ldc(F, p);
+        vi = c * ldc(F, p);
         st(v, p, vi);
     } else {
         vi = ldc(v, p);
