@@ -251,6 +251,7 @@ def run_gpu(args):
     ctx = Bd.Context(g, h, "f32")
     if args.generic:
         ctx.set_option("generic_stencil", 1)
+    ctx.set_option("cubic_lean", args.cubic_lean)
     if args.cubic_rows:
         rw = [int(x) for x in args.cubic_rows.split(",")]
         ctx.set_option("cubic_rows", rw[0])
@@ -366,6 +367,7 @@ def run_gpu(args):
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),
                       "columns_per_thread": [ctx.get_option("cubic_rows"), ctx.get_option("cubic_rows_corr")],
+                      "lean_heun_passes": bool(ctx.get_option("cubic_lean")) and args.solver == "heun",
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
@@ -1140,6 +1142,8 @@ def main():
     ap.add_argument("--zc", default="", help="units per CTA of the 27-point path, P or P,C for predictor and "
                     "corrector (profiling aid; default: chosen by sp_autotune)")
     ap.add_argument("--generic", action="store_true", help="force the generic neighbour-list kernels")
+    ap.add_argument("--cubic-lean", type=int, default=1, choices=[0, 1],
+                    help="0: the general 27-point Heun passes even where the lean ones fit")
     ap.add_argument("--cubic-rows", default="", help="columns per thread of the 27-point kernels, R or R,C for "
                                                      "predictor and corrector (default: chosen by sp_autotune)")
     ap.add_argument("--solver", default="heun", choices=["heun", "depondt", "sib", "rk4"],

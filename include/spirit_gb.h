@@ -645,7 +645,15 @@ enum {
      * chooses it per pass.  Reading returns the predictor's value in use */
     SP_OPT_CUBIC_ROWS = 11,
     /* the same for the corrector pass alone */
-    SP_OPT_CUBIC_ROWS_CORR = 12
+    SP_OPT_CUBIC_ROWS_CORR = 12,
+    /* 1 (default): FP32 stochastic Heun on the 27-point path takes the lean
+     * passes where the lattice's xy plane is cut into whole 32 x 8 column
+     * tiles (nx a multiple of 32, ny of 8) and one column per thread is in
+     * use; the same method and stencil, fewer instructions per spin, results
+     * equal to the general passes within FP32 rounding (not bit for bit).
+     * 0: always the general passes.  Reading returns 1 when the lean passes
+     * would be taken for a Heun call of this context */
+    SP_OPT_CUBIC_LEAN = 13
 };
 int sp_set_option(sp_ctx *ctx, int option, int value);
 /* Choose the tile height (SP_OPT_CUBIC_ROWS) and the work per CTA of the

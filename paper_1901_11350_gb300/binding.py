@@ -151,7 +151,7 @@ SIGNATURES = {
 PROFILE_KINDS = {"llg_predictor": 0, "llg_corrector": 1, "dipole": 2}
 OPTIONS = {"generic_stencil": 1, "planes_per_cta": 2, "has_cubic_path": 3, "generic_fft": 4, "small_path": 5,
            "planes_per_cta_corr": 6, "mc_resident": 7, "scratch_kib": 8, "gneb_persistent": 9,
-           "wait_limit": 10, "cubic_rows": 11, "cubic_rows_corr": 12}
+           "wait_limit": 10, "cubic_rows": 11, "cubic_rows_corr": 12, "cubic_lean": 13}
 
 
 def library_path():

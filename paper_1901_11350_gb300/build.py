@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspirit_gb.so")
-SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "topo.cu", "static_step.cu", "dipole_fast.cu", "unet.cu", "mc.cu", "hessian.cu", "htst.cu"]
+SOURCES = ["api.cu", "field_llg.cu", "minimise.cu", "dipole.cu", "cubic.cu", "cubic_lean.cu", "topo.cu", "static_step.cu", "dipole_fast.cu", "unet.cu", "mc.cu", "hessian.cu", "htst.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

@@ -409,14 +409,14 @@ template <typename T> int llg_run(sp_ctx *c, void *n, const sp_llg_params *p, in
         if ((rc = dipole(c, nn, &bd, st))) return rc;
         int pr = c->prof.begin(SP_PROF_LLG_PREDICTOR, st);
         cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, (const rec_t<T> *)bd, k, per0, st,
-                                              cubic_rows(c, 0))
+                                              cubic_rows(c, 0), cubic_lean_taken(c, 0))
                             : launch_llg_pred<T>(p->solver, S, nn, (const rec_t<T> *)bd, np, q, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG predictor launch");
         if ((rc = dipole(c, np, &bd, st))) return rc;
         pr = c->prof.begin(SP_PROF_LLG_CORRECTOR, st);
         e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, (const rec_t<T> *)bd, k, per1, st,
-                                  cubic_rows(c, 1))
+                                  cubic_rows(c, 1), cubic_lean_taken(c, 1))
                 : launch_llg_corr<T>(p->solver, S, nn, np, q, (const rec_t<T> *)bd, k, st);
         c->prof.end(pr, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LLG corrector launch");
@@ -688,8 +688,10 @@ template <typename T> int autotune_run(sp_ctx *c, const void *n, int *chosen, cu
     }
     auto launch = [&](int pass, int per, int rows) {
         return pass == 0
-                   ? launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st, rows)
-                   : launch_cubic<T>(1, SP_HEUN, CP, np, nullptr, q, out, nullptr, k, per, st, rows);
+                   ? launch_cubic<T>(0, SP_HEUN, CP, (const rec_t<T> *)n, np, q, nullptr, nullptr, k, per, st, rows,
+                                     cubic_lean_taken(c, 0))
+                   : launch_cubic<T>(1, SP_HEUN, CP, np, nullptr, q, out, nullptr, k, per, st, rows,
+                                     cubic_lean_taken(c, 1));
     };
     int user = c->zc, user_corr = c->zc_corr, user_rows[2] = {c->rows[0], c->rows[1]};
     c->zc = 0;
@@ -1447,6 +1449,11 @@ int sp_set_option(sp_ctx *c, int option, int value)
         c->rows[1] = value;
         c->zc_auto = c->zc_auto_corr = 0;
         return SP_OK;
+    case SP_OPT_CUBIC_LEAN:
+        if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "cubic_lean takes 0 or 1");
+        c->lean = value;
+        c->zc_auto = c->zc_auto_corr = 0;
+        return SP_OK;
     case SP_OPT_GNEB_PERSISTENT:
         if (value != 0 && value != 1) return fail(c, SP_ERR_ARG, "gneb_persistent takes 0 or 1");
         c->gneb_persistent = value;
@@ -1506,6 +1513,9 @@ int sp_get_option(const sp_ctx *c, int option, int *value)
         return SP_OK;
     case SP_OPT_CUBIC_ROWS_CORR:
         *value = cubic_rows(c, 1);
+        return SP_OK;
+    case SP_OPT_CUBIC_LEAN:
+        *value = cubic_lean_taken(c, 0) ? 1 : 0;
         return SP_OK;
     case SP_OPT_WAIT_LIMIT:
         *value = c->wait_limit;

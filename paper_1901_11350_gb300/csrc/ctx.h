@@ -124,6 +124,7 @@ struct sp_ctx {
     int zc_auto = 0;        // balanced value, computed on first use
     int zc_auto_corr = 0;   // the same for the corrector pass (its own occupancy)
     int rows[2] = {1, 1};   // columns per thread of the 27-point predictor and corrector (1 or 2)
+    int lean = 1;           // the lean FP32 Heun passes where the lattice fits them (SP_OPT_CUBIC_LEAN)
     CubicParams<float> Cf = {};
     CubicParams<double> Cd = {};
     // device scratch (allocated on first use)
@@ -190,6 +191,15 @@ inline int cubic_rows(const sp_ctx *c, int pass)
     return cubic_rows_taken(c->prec, c->rows[pass], false, c->h.dipole != SP_DIPOLE_NONE);
 }
 
+// Whether a Heun pass of this context on the 27-point path takes the lean
+// FP32 kernels (cubic_lean.cu): option on, FP32, no dipole field, one column
+// per thread and a lattice cut into whole 32 x 8 column tiles.
+inline bool cubic_lean_taken(const sp_ctx *c, int pass)
+{
+    return c->lean && c->prec == SP_F32 && c->cubic && c->use_cubic && c->h.dipole == SP_DIPOLE_NONE &&
+           cubic_rows(c, pass) == 1 && cubic_lean_fits(c->nc[0], c->nc[1]);
+}
+
 // Units per CTA of the 27-point path: the user's choice, or the units spread
 // evenly over one wave of resident CTAs on the current device (units of the
 // pass's tile height, see cubic_rows).
@@ -203,7 +213,8 @@ inline int cubic_per(sp_ctx *c, int pass = 0)
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
         const int rows = cubic_rows(c, pass);
-        long slots = (long)nsm * cubic_resident_ctas(c->prec, pass, rows);
+        long slots = (long)nsm * (cubic_lean_taken(c, pass) ? cubic_lean_resident_ctas(pass)
+                                                             : cubic_resident_ctas(c->prec, pass, rows));
         long units = cubic_units(c->nc[0], c->nc[1], c->nc[2], rows);
         a = (int)std::max(1L, (units + slots - 1) / slots);
     }

@@ -541,9 +541,14 @@ cudaError_t launch_dm(int pass, int solver, int grid, const CubicParams<T> &P, c
 
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
-                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st, int rows)
+                         rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st, int rows,
+                         bool lean)
 {
     rows = cubic_rows_taken(sizeof(T) == 8 ? SP_F64 : SP_F32, rows, llg_reps(c) > 1, Bdd != nullptr);
+    if constexpr (std::is_same<T, float>::value)
+        if (lean && solver == SP_HEUN && pass <= 1 && rows == 1 && !Bdd && llg_reps(c) == 1 &&
+            cubic_lean_fits(P.nx, P.ny))
+            return launch_cubic_lean(pass, P, src, np, q, nout, c, per, st);
     long total = cubic_units(P.nx, P.ny, P.nz, rows) * llg_reps(c);
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
@@ -581,8 +586,9 @@ int cubic_resident_ctas(int prec, int pass, int rows)
 }
 
 template cudaError_t launch_cubic<float>(int, int, const CubicParams<float> &, const float4 *, float4 *, float4 *,
-                                         float4 *, const float4 *, const LlgConst<float> &, int, cudaStream_t, int);
+                                         float4 *, const float4 *, const LlgConst<float> &, int, cudaStream_t, int,
+                                         bool);
 template cudaError_t launch_cubic<double>(int, int, const CubicParams<double> &, const dq4 *, dq4 *, dq4 *, dq4 *,
-                                          const dq4 *, const LlgConst<double> &, int, cudaStream_t, int);
+                                          const dq4 *, const LlgConst<double> &, int, cudaStream_t, int, bool);
 
 }  // namespace spgb

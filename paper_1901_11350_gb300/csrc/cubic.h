@@ -27,10 +27,19 @@ int cubic_resident_ctas(int prec, int pass, int rows = 1);
 // CTA b streams the units [b*per, (b+1)*per), tile-major; with c.n_rep > 1
 // the units of all replicas (stored one after another), replica-major.
 // rows: columns per thread (1 or 2, see cubic_rows_taken); per counts units
-// of that tile height.
+// of that tile height.  lean: FP32 stochastic Heun passes of one lattice
+// without the dipole field take launch_cubic_lean where the lattice fits it.
 template <typename T>
 cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const rec_t<T> *src, rec_t<T> *np, rec_t<T> *q,
                          rec_t<T> *nout, const rec_t<T> *Bdd, const LlgConst<T> &c, int per, cudaStream_t st,
-                         int rows = 1);
+                         int rows = 1, bool lean = false);
+
+// The lean stochastic Heun passes (cubic_lean.cu): FP32, one lattice without
+// the dipole field, nx % 32 == 0 and ny % 8 == 0 (cubic_lean_fits); the same
+// (32 x 8 column tile, plane) units and `per` as launch_cubic with rows = 1.
+bool cubic_lean_fits(int nx, int ny);
+cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q,
+                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st);
+int cubic_lean_resident_ctas(int pass);
 
 }  // namespace spgb

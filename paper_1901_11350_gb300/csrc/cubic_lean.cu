@@ -1,0 +1,400 @@
+// cubic_lean.cu -- the stochastic Heun passes (App. B, Heun scheme with the
+// thermal field of the stochastic LLG equation) on the shell-symmetric
+// 27-point stencil, FP32, for one lattice without the dipole term whose xy
+// plane is cut into whole 32 x 8 column tiles (nx % 32 == 0, ny % 8 == 0).
+//
+// The plane streaming is that of cubic.cu: a CTA owns a 32 x 8 column tile
+// and a run of planes, planes pass through a ring of three shared-memory
+// tiles with a one-cell halo, and each thread carries one plane's summary
+// (centre spin c, the part w it gives the planes above and below, the open
+// field accumulator) in registers from plane to plane.  What differs is the
+// per-spin instruction budget of the loop, which bounds these passes:
+//   * every tile record is read as one 16-byte vector and summed as two
+//     f32x2 halves (x, y | z, pad), so no load is split and every vector sum
+//     is two packed instructions;
+//   * whole tiles only: no per-spin ownership tests;
+//   * the ring slot of every plane is a compile-time offset (the plane loop
+//     is unrolled by the ring size), staging addresses are fixed per segment
+//     and the halo slots that lie outside an open lattice are zeroed once
+//     per segment;
+//   * the thermal field is a template switch, and the multi-function-unit
+//     operations (log2, reciprocal square root, sine, cosine) are the
+//     flush-to-zero forms, which give the same values on the normal
+//     arguments they receive here.
+#include <type_traits>
+
+#include "internal.h"
+#include "cubic.h"
+
+namespace spgb {
+
+namespace {
+
+constexpr int LX = 32, LY = 8, LT = LX * LY;       // column tile = threads per CTA
+constexpr int LHX = LX + 2, LHN = LHX * (LY + 2);  // halo tile: 34 x 10 records
+constexpr int LNB = 3;                             // plane ring
+#ifndef SPGB_LEAN_MINB
+#define SPGB_LEAN_MINB 3
+#endif
+#ifndef SPGB_LEAN_MINB_CORR
+#define SPGB_LEAN_MINB_CORR 4
+#endif
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16(unsigned s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void wait_groups() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void st_zero(unsigned s)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(s), "f"(0.f) : "memory");
+}
+
+// multi-function-unit operations, flush-to-zero forms
+__device__ __forceinline__ float lg2f(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqf(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sinf_(float x)
+{
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float cosf_(float x)
+{
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// A record as two f32x2 halves: a = (x, y), b = (z, pad).  Tile records are
+// loaded and summed in this form (one 16-byte load each); the pad lane is
+// carried through those sums and never read back.
+struct p4 {
+    float2 a, b;
+};
+__device__ __forceinline__ p4 ld4(const float4 *t)
+{
+    float4 v = *t;
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ p4 operator+(p4 u, p4 v) { return {__fadd2_rn(u.a, v.a), __fadd2_rn(u.b, v.b)}; }
+// u - v (v times -1 is exact, so one rounding, as a subtraction)
+__device__ __forceinline__ p4 minus(p4 u, p4 v)
+{
+    const float2 m = make_float2(-1.f, -1.f);
+    return {__ffma2_rn(v.a, m, u.a), __ffma2_rn(v.b, m, u.b)};
+}
+
+// A 3-vector as (x, y) in one f32x2 register pair and z: the form of the
+// values carried from plane to plane (no pad lane to keep live).
+struct pv {
+    float2 a;
+    float z;
+};
+__device__ __forceinline__ pv pvof(p4 u) { return {u.a, u.b.x}; }
+__device__ __forceinline__ pv operator+(pv u, pv v) { return {__fadd2_rn(u.a, v.a), u.z + v.z}; }
+__device__ __forceinline__ pv pfma(float2 s, pv u, pv v) { return {__ffma2_rn(s, u.a, v.a), fmaf(s.x, u.z, v.z)}; }
+__device__ __forceinline__ pv pmul(float2 s, pv u) { return {__fmul2_rn(s, u.a), s.x * u.z}; }
+__device__ __forceinline__ v3<float> v3of(pv u) { return {u.a.x, u.a.y, u.z}; }
+
+__device__ __forceinline__ v3<float> unit(v3<float> a) { return rsqf(dot(a, a)) * a; }
+
+// Three standard normals from one Philox block by Box-Muller, scaled by the
+// noise amplitude s: (u0, u1) -> eta_x, eta_y and (u2, u3) -> eta_z with
+// u = (x + 1/2) 2^-32; sin and cos of 2 pi u are taken as -sin and -cos of
+// 2 pi (u - 1/2), whose argument lies in (-pi, pi).
+__device__ __forceinline__ v3<float> thermal(uint4 x, float s)
+{
+    const float k = 2.3283064365386963e-10f, h = 0.5f * 2.3283064365386963e-10f;
+    const float twopi = 6.283185307179586f, pi = 3.141592653589793f;
+    const float m2ln2 = -1.3862943611198906f;  // -2 ln 2 (x2 of the FP32 ln 2: exact)
+    float u0 = fmaf((float)x.x, k, h), u1 = fmaf((float)x.y, k, h);
+    float u2 = fmaf((float)x.z, k, h), u3 = fmaf((float)x.w, k, h);
+    float t0 = fmaxf(m2ln2 * lg2f(u0), 1e-30f), t1 = fmaxf(m2ln2 * lg2f(u2), 1e-30f);
+    float r0 = -s * (t0 * rsqf(t0)), r1 = -s * (t1 * rsqf(t1));
+    float a = fmaf(twopi, u1, -pi), b = fmaf(twopi, u3, -pi);
+    return {r0 * cosf_(a), r0 * sinf_(a), r1 * cosf_(b)};
+}
+
+// Summary of one plane at a thread's column (see cubic.cu): centre c, the
+// part w = J1 c + J2 f + J3 k it gives the planes above and below, and the
+// part e = J1 f + J2 k + in-plane face DMI it gives itself (f, k: sums of the
+// four in-plane face and corner neighbours).
+struct Sum {
+    pv c, w, e;
+};
+
+struct LeanConst {
+    float2 J1, J2, J3;
+};
+
+template <int DM>
+__device__ __forceinline__ Sum summarise(const CubicParams<float> &P, const LeanConst &L, const float4 *t)
+{
+    // t: the thread's centre record in the plane's tile
+    const p4 xp = ld4(t + 1), xm = ld4(t - 1), yp = ld4(t + LHX), ym = ld4(t - LHX);
+    const pv c = pvof(ld4(t));
+    const pv f = pvof((xp + xm) + (yp + ym));
+    const pv k = pvof((ld4(t + LHX + 1) + ld4(t - LHX - 1)) + (ld4(t - LHX + 1) + ld4(t + LHX - 1)));
+    Sum r;
+    r.c = c;
+    r.w = pfma(L.J1, c, pfma(L.J2, f, pmul(L.J3, k)));
+    pv e = pfma(L.J1, f, pmul(L.J2, k));
+    if (DM != 0) {
+        const pv dx = pvof(minus(xp, xm)), dy = pvof(minus(yp, ym));
+        if (DM == 1) {
+            // D [(n(+x) - n(-x)) x xhat + (n(+y) - n(-y)) x yhat]
+            const float D = P.Dx[0];
+            e.a.x = fmaf(-D, dy.z, e.a.x);
+            e.a.y = fmaf(D, dx.z, e.a.y);
+            e.z = fmaf(D, dy.a.x - dx.a.y, e.z);
+        } else {
+            v3<float> ee = v3of(e) + cross(v3of(dx), mk(P.Dx[0], P.Dx[1], P.Dx[2])) +
+                           cross(v3of(dy), mk(P.Dy[0], P.Dy[1], P.Dy[2]));
+            e = {make_float2(ee.x, ee.y), ee.z};
+        }
+    }
+    r.e = e;
+    return r;
+}
+
+// s * (c x D_{+z}) added to the (x, y, z) lanes of v
+template <int DM> __device__ __forceinline__ pv add_zdmi(const CubicParams<float> &P, pv v, pv c, float s)
+{
+    if (DM == 1) {
+        const float d = s * P.Dz[2];
+        v.a.x = fmaf(d, c.a.y, v.a.x);
+        v.a.y = fmaf(-d, c.a.x, v.a.y);
+    } else if (DM == 2) {
+        v3<float> z = cross(v3of(c), mk(P.Dz[0], P.Dz[1], P.Dz[2]));
+        v.a.x = fmaf(s, z.x, v.a.x);
+        v.a.y = fmaf(s, z.y, v.a.y);
+        v.z = fmaf(s, z.z, v.z);
+    }
+    return v;
+}
+
+// on-site field mu B + 2 K (Khat . c) Khat added to v
+__device__ __forceinline__ pv add_onsite(const CubicParams<float> &P, pv v, pv c)
+{
+    const float kn = 2.f * P.K * (P.Kh[0] * c.a.x + P.Kh[1] * c.a.y + P.Kh[2] * c.z);
+    v.a.x += fmaf(kn, P.Kh[0], P.Bz[0]);
+    v.a.y += fmaf(kn, P.Kh[1], P.Bz[1]);
+    v.z += fmaf(kn, P.Kh[2], P.Bz[2]);
+    return v;
+}
+
+template <int V> using I_ = std::integral_constant<int, V>;
+
+// One segment: planes [za, zb) of the column tile at (x0, y0).  PASS 0: the
+// predictor on src = n (writes np and the folded term q); PASS 1: the
+// corrector on src = np (q of each plane arrives with the ring, writes
+// nout = n).  Plane p lives in ring slot (p - za + 1) % 3; every fetch is one
+// cp.async group, so that waiting for all but the newest group means "the
+// next plane has landed".
+template <int PASS, int DM, bool TH>
+__device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const LeanConst &L, const LlgConst<float> &c,
+                                             const float4 *__restrict__ src, float4 *__restrict__ np,
+                                             float4 *__restrict__ q, float4 *__restrict__ nout, float4 (*tiles)[LHN],
+                                             float4 (*qt)[LT], int x0, int y0, int za, int zb)
+{
+    const int tid = threadIdx.x, tx = tid & (LX - 1), ty = tid / LX;
+    const int plane = P.nx * P.ny;  // N < 2^31
+    // this thread stages halo records tid and tid + 256 of every plane: their
+    // in-plane offsets (-1: outside an open lattice, -2: no such record)
+    int g[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int e = tid + s * LT;
+        if (e >= LHN) {
+            g[s] = -2;
+            continue;
+        }
+        int gx = x0 - 1 + e % LHX, gy = y0 - 1 + e / LHX;
+        bool in = true;
+        if (P.per0)
+            gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        else
+            in = gx >= 0 && gx < P.nx;
+        if (P.per1)
+            gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        else
+            in = in && gy >= 0 && gy < P.ny;
+        g[s] = in ? gy * P.nx + gx : -1;
+    }
+    const unsigned sd0 = smem_addr(&tiles[0][tid]), sd1 = sd0 + 16u * LT;
+    const unsigned qd = smem_addr(&qt[0][tid]);
+    constexpr unsigned kSlot = 16u * LHN, kQSlot = 16u * LT;
+#pragma unroll
+    for (int b = 0; b < LNB; ++b) {
+        if (g[0] == -1) st_zero(sd0 + b * kSlot);
+        if (g[1] == -1) st_zero(sd1 + b * kSlot);
+    }
+    const int col = (y0 + ty) * P.nx + x0 + tx;
+    auto load = [&](auto slot, int p) {
+        constexpr unsigned S = decltype(slot)::value;
+        if (p <= zb) {
+            int pz = p;
+            bool zin = true;
+            if (P.per2) {
+                pz += pz < 0 ? P.nz : 0;
+                pz -= pz >= P.nz ? P.nz : 0;
+            } else {
+                zin = pz >= 0 && pz < P.nz;
+            }
+            if (zin) {
+                const float4 *base = src + (size_t)pz * plane;
+                if (g[0] >= 0) cp16(sd0 + S * kSlot, base + g[0]);
+                if (g[1] >= 0) cp16(sd1 + S * kSlot, base + g[1]);
+            } else {
+                if (g[0] != -2) st_zero(sd0 + S * kSlot);
+                if (g[1] != -2) st_zero(sd1 + S * kSlot);
+            }
+            if (PASS == 1 && p - 1 >= za && p - 1 < zb) cp16(qd + S * kQSlot, q + (size_t)(p - 1) * plane + col);
+        }
+        commit();
+    };
+    // planes za-1, za, za+1 in flight
+    load(I_<0>{}, za - 1);
+    load(I_<1>{}, za);
+    load(I_<2>{}, za + 1);
+    wait_groups<2>();
+    __syncthreads();
+    const float4 *tc = &tiles[0][(ty + 1) * LHX + tx + 1];  // the thread's centre record in slot 0
+    const Sum below = summarise<DM>(P, L, tc);
+    __syncthreads();
+    load(I_<0>{}, za + 2);
+    wait_groups<2>();
+    __syncthreads();
+    const Sum cur = summarise<DM>(P, L, tc + LHN);
+    // the open accumulator of the plane being finished, its w and centre
+    pv acc = add_onsite(P, add_zdmi<DM>(P, cur.e + below.w, below.c, -1.f), cur.c);
+    pv wcur = cur.w, ccur = cur.c;
+    int i = za * plane + col;
+    const float cA = c.cA[0], al = c.alpha, dt = c.dt, hdt = 0.5f * c.dt;
+    // plane z: plane z+1 (slot SN) has landed; plane z's slot SF is refilled
+    // with plane z+3.  B(z) = acc + w(z+1) + c(z+1) x D_{+z}; then plane z+1
+    // opens A(z+1) = e(z+1) + w(z) - c(z) x D_{+z} + onsite(c(z+1)).
+    auto step = [&](auto sn, auto sf, int z) {
+        constexpr int SN = decltype(sn)::value;
+        wait_groups<1>();
+        __syncthreads();
+        p4 qi;
+        if (PASS == 1) qi = ld4(&qt[SN][tid]);
+        load(sf, z + 3);
+        const Sum up = summarise<DM>(P, L, tc + SN * LHN);
+        const pv Bp = add_zdmi<DM>(P, acc + up.w, up.c, 1.f);
+        acc = add_onsite(P, add_zdmi<DM>(P, up.e + wcur, ccur, -1.f), up.c);
+        const v3<float> n = v3of(ccur), B = v3of(Bp);
+        wcur = up.w;
+        ccur = up.c;
+        if (PASS == 0) {
+            v3<float> Bth = mk(0.f, 0.f, 0.f);
+            if (TH) Bth = thermal(thermal_bits_at(c, c.step, (uint32_t)i, 0u), c.sig[0]);
+            const v3<float> A = llg_A(cA, al, n, B + Bth);
+            const v3<float> f = cross(n, A);
+            const v3<float> p = unit(axpy(dt, f, n));
+            if (TH) {
+                const v3<float> gth = cross(p, llg_A(cA, al, p, Bth));
+                st(q, i, axpy(hdt, f + gth, n));
+            } else {
+                st(q, i, axpy(hdt, f, n));
+            }
+            st(np, i, p);
+        } else {
+            const v3<float> Ap = llg_A(cA, al, n, B);
+            st(nout, i, unit(axpy(hdt, cross(n, Ap), v3of(pvof(qi)))));
+        }
+        i += plane;
+    };
+    for (int z = za; z < zb; z += LNB) {
+        step(I_<2>{}, I_<1>{}, z);
+        if (z + 1 >= zb) break;
+        step(I_<0>{}, I_<2>{}, z + 1);
+        if (z + 2 >= zb) break;
+        step(I_<1>{}, I_<0>{}, z + 2);
+    }
+    wait_groups<0>();
+    __syncthreads();  // the next segment reuses the ring
+}
+
+// Work: the (32 x 8 column tile, plane) units in tile-major order, CTA b
+// takes units [b per, (b + 1) per) as runs of planes, one segment each.
+template <int PASS, int DM, bool TH>
+__global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MINB_CORR)
+    k_lean(const __grid_constant__ CubicParams<float> P, const float4 *__restrict__ src, float4 *__restrict__ np,
+           float4 *__restrict__ q, float4 *__restrict__ nout, const __grid_constant__ LlgConst<float> c, int per)
+{
+    __shared__ __align__(16) float4 tiles[LNB][LHN];
+    __shared__ __align__(16) float4 qt[PASS == 1 ? LNB : 1][LT];
+    allow_dependents();
+    wait_prerequisite();  // the previous pass wrote what this one reads
+    const LeanConst L{make_float2(P.J1, P.J1), make_float2(P.J2, P.J2), make_float2(P.J3, P.J3)};
+    const int tiles_x = P.nx / LX;
+    const long total = (long)tiles_x * (P.ny / LY) * P.nz;
+    long u = (long)blockIdx.x * per;
+    const long u1 = min(u + per, total);
+    while (u < u1) {
+        const int tile = (int)(u / P.nz), za = (int)(u % P.nz);
+        const int zb = (int)min((long)P.nz, za + (u1 - u));
+        lean_segment<PASS, DM, TH>(P, L, c, src, np, q, nout, tiles, qt, (tile % tiles_x) * LX,
+                                   (tile / tiles_x) * LY, za, zb);
+        u += zb - za;
+    }
+}
+
+template <int PASS, int DM>
+cudaError_t lean_launch(int grid, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q, float4 *nout,
+                        const LlgConst<float> &c, int per, cudaStream_t st)
+{
+    if constexpr (PASS == 0)
+        if (c.thermal)
+            return launch_pdl(k_lean<PASS, DM, true>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, per);
+    return launch_pdl(k_lean<PASS, DM, false>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, per);
+}
+
+template <int PASS>
+cudaError_t lean_dm(int grid, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q, float4 *nout,
+                    const LlgConst<float> &c, int per, cudaStream_t st)
+{
+    if (P.dmi_mode == 0) return lean_launch<PASS, 0>(grid, P, src, np, q, nout, c, per, st);
+    if (P.dmi_mode == 1) return lean_launch<PASS, 1>(grid, P, src, np, q, nout, c, per, st);
+    return lean_launch<PASS, 2>(grid, P, src, np, q, nout, c, per, st);
+}
+
+}  // namespace
+
+bool cubic_lean_fits(int nx, int ny) { return nx > 0 && ny > 0 && nx % LX == 0 && ny % LY == 0; }
+
+cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q,
+                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st)
+{
+    const long total = (long)(P.nx / LX) * (P.ny / LY) * P.nz;
+    if (total == 0) return cudaSuccess;
+    if (per < 1) per = 1;
+    const int grid = (int)((total + per - 1) / per);
+    return pass == 0 ? lean_dm<0>(grid, P, src, np, q, nout, c, per, st)
+                     : lean_dm<1>(grid, P, src, np, q, nout, c, per, st);
+}
+
+int cubic_lean_resident_ctas(int pass)
+{
+    int n = 0;
+    cudaError_t e = pass == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<0, 1, true>, LT, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<1, 1, false>, LT, 0);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+}  // namespace spgb

@@ -72,11 +72,11 @@ template <typename T> int run_static(sp_ctx *c, void *n, const sp_llg_params *p,
     for (int s = 0; s < n_steps; ++s) {
         k.step = p->step0 + (uint64_t)s;
         cudaError_t e = cub ? launch_cubic<T>(0, p->solver, CP, nn, np, q, nn, nullptr, k, cubic_per(c), st,
-                                              cubic_rows(c, 0))
+                                              cubic_rows(c, 0), cubic_lean_taken(c, 0))
                             : launch_llg_pred<T>(p->solver, S, nn, nullptr, np, q, k, st);
         if (e == cudaSuccess)
             e = cub ? launch_cubic<T>(1, p->solver, CP, np, nullptr, q, nn, nullptr, k, cubic_per(c, 1), st,
-                                      cubic_rows(c, 1))
+                                      cubic_rows(c, 1), cubic_lean_taken(c, 1))
                     : launch_llg_corr<T>(p->solver, S, nn, np, q, nullptr, k, st);
         if (e != cudaSuccess) {
             c->err = std::string("LLG launch: ") + cudaGetErrorString(e);
