@@ -34,8 +34,15 @@ constexpr int LX = 32, LY = 8, LT = LX * LY;       // column tile = threads per 
 constexpr int LHX = LX + 2, LHN = LHX * (LY + 2);  // halo tile: 34 x 10 records
 constexpr int LNB = 3;                             // plane ring
 #ifndef SPGB_LEAN_MINB
-#define SPGB_LEAN_MINB 3
+#define SPGB_LEAN_MINB 4
 #endif
+// 1: the folded term q travels as its x in the pad word of the predicted
+// record and (y, z) in an 8-byte record (the step moves the method's 80 B per
+// spin instead of 96); 0: q as a 16-byte record of its own
+#ifndef SPGB_LEAN_PACKQ
+#define SPGB_LEAN_PACKQ 1
+#endif
+constexpr unsigned kQRec = SPGB_LEAN_PACKQ ? 8u : 16u;  // bytes of a q record in its array and ring
 #ifndef SPGB_LEAN_MINB_CORR
 #define SPGB_LEAN_MINB_CORR 4
 #endif
@@ -44,6 +51,16 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)
 __device__ __forceinline__ void cp16(unsigned s, const void *g)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp8(unsigned s, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ float2 lds2(unsigned s)
+{
+    float2 r;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(s));
+    return r;
 }
 __device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void wait_groups() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -84,17 +101,19 @@ __device__ __forceinline__ float cosf_(float x)
 struct p4 {
     float2 a, b;
 };
-__device__ __forceinline__ p4 ld4(const float4 *t)
+// the record at shared-memory byte address s + OFF.  The compiler picks one
+// 16-byte or two 8-byte loads (forcing 16-byte loads by inline PTX was
+// measured slower: the quad-register destinations cost spills)
+template <int OFF> __device__ __forceinline__ p4 ld4(unsigned s)
 {
-    float4 v = *t;
+    const float4 v = *reinterpret_cast<const float4 *>(__cvta_shared_to_generic(s + OFF));
     return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
 __device__ __forceinline__ p4 operator+(p4 u, p4 v) { return {__fadd2_rn(u.a, v.a), __fadd2_rn(u.b, v.b)}; }
 // u - v (v times -1 is exact, so one rounding, as a subtraction)
-__device__ __forceinline__ p4 minus(p4 u, p4 v)
+__device__ __forceinline__ p4 minus(p4 u, p4 v, float2 m1)
 {
-    const float2 m = make_float2(-1.f, -1.f);
-    return {__ffma2_rn(v.a, m, u.a), __ffma2_rn(v.b, m, u.b)};
+    return {__ffma2_rn(v.a, m1, u.a), __ffma2_rn(v.b, m1, u.b)};
 }
 
 // A 3-vector as (x, y) in one f32x2 register pair and z: the form of the
@@ -110,6 +129,12 @@ __device__ __forceinline__ pv pmul(float2 s, pv u) { return {__fmul2_rn(s, u.a),
 __device__ __forceinline__ v3<float> v3of(pv u) { return {u.a.x, u.a.y, u.z}; }
 
 __device__ __forceinline__ v3<float> unit(v3<float> a) { return rsqf(dot(a, a)) * a; }
+
+// A(n, B) of Eq. 3 for a field already in units of c = -gamma/((1+alpha^2) mu):
+// B + alpha n x B (the kernels receive the stencil constants, the on-site
+// terms and the noise amplitude multiplied by c, so the field they form is
+// c B and no per-spin scaling is left)
+__device__ __forceinline__ v3<float> lA(float al, v3<float> n, v3<float> B) { return axpy(al, cross(n, B), B); }
 
 // Three standard normals from one Philox block by Box-Muller, scaled by the
 // noise amplitude s: (u0, u1) -> eta_x, eta_y and (u2, u3) -> eta_z with
@@ -134,26 +159,32 @@ __device__ __forceinline__ v3<float> thermal(uint4 x, float s)
 // four in-plane face and corner neighbours).
 struct Sum {
     pv c, w, e;
+    float cw;  // the centre record's pad word
 };
 
+// the exchange constants of the three shells as f32x2 pairs, and -1 for
+// the packed subtractions (a kernel parameter, read from the constant bank)
 struct LeanConst {
-    float2 J1, J2, J3;
+    float2 J1, J2, J3, m1;
 };
 
-template <int DM>
-__device__ __forceinline__ Sum summarise(const CubicParams<float> &P, const LeanConst &L, const float4 *t)
+template <int DM, int SLOT>
+__device__ __forceinline__ Sum summarise(const CubicParams<float> &P, const LeanConst &L, unsigned t)
 {
-    // t: the thread's centre record in the plane's tile
-    const p4 xp = ld4(t + 1), xm = ld4(t - 1), yp = ld4(t + LHX), ym = ld4(t - LHX);
-    const pv c = pvof(ld4(t));
+    // t: shared-memory address of the thread's centre record in ring slot 0
+    constexpr int B = SLOT * LHN * 16, X = 16, Y = 16 * LHX;
+    const p4 xp = ld4<B + X>(t), xm = ld4<B - X>(t), yp = ld4<B + Y>(t), ym = ld4<B - Y>(t);
+    const p4 c4 = ld4<B>(t);
+    const pv c = pvof(c4);
     const pv f = pvof((xp + xm) + (yp + ym));
-    const pv k = pvof((ld4(t + LHX + 1) + ld4(t - LHX - 1)) + (ld4(t - LHX + 1) + ld4(t + LHX - 1)));
+    const pv k = pvof((ld4<B + Y + X>(t) + ld4<B - Y - X>(t)) + (ld4<B - Y + X>(t) + ld4<B + Y - X>(t)));
     Sum r;
     r.c = c;
+    r.cw = c4.b.y;
     r.w = pfma(L.J1, c, pfma(L.J2, f, pmul(L.J3, k)));
     pv e = pfma(L.J1, f, pmul(L.J2, k));
     if (DM != 0) {
-        const pv dx = pvof(minus(xp, xm)), dy = pvof(minus(yp, ym));
+        const pv dx = pvof(minus(xp, xm, L.m1)), dy = pvof(minus(yp, ym, L.m1));
         if (DM == 1) {
             // D [(n(+x) - n(-x)) x xhat + (n(+y) - n(-y)) x yhat]
             const float D = P.Dx[0];
@@ -208,7 +239,7 @@ template <int PASS, int DM, bool TH>
 __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const LeanConst &L, const LlgConst<float> &c,
                                              const float4 *__restrict__ src, float4 *__restrict__ np,
                                              float4 *__restrict__ q, float4 *__restrict__ nout, float4 (*tiles)[LHN],
-                                             float4 (*qt)[LT], int x0, int y0, int za, int zb)
+                                             unsigned char *qt, int x0, int y0, int za, int zb)
 {
     const int tid = threadIdx.x, tx = tid & (LX - 1), ty = tid / LX;
     const int plane = P.nx * P.ny;  // N < 2^31
@@ -235,8 +266,9 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
         g[s] = in ? gy * P.nx + gx : -1;
     }
     const unsigned sd0 = smem_addr(&tiles[0][tid]), sd1 = sd0 + 16u * LT;
-    const unsigned qd = smem_addr(&qt[0][tid]);
-    constexpr unsigned kSlot = 16u * LHN, kQSlot = 16u * LT;
+    const unsigned qd = smem_addr(qt + kQRec * tid);
+    constexpr unsigned kSlot = 16u * LHN, kQSlot = kQRec * LT;
+    float2 *const q2 = reinterpret_cast<float2 *>(q);  // (y, z) of q, packed layout
 #pragma unroll
     for (int b = 0; b < LNB; ++b) {
         if (g[0] == -1) st_zero(sd0 + b * kSlot);
@@ -262,7 +294,12 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
                 if (g[0] != -2) st_zero(sd0 + S * kSlot);
                 if (g[1] != -2) st_zero(sd1 + S * kSlot);
             }
-            if (PASS == 1 && p - 1 >= za && p - 1 < zb) cp16(qd + S * kQSlot, q + (size_t)(p - 1) * plane + col);
+            if (PASS == 1 && p - 1 >= za && p - 1 < zb) {
+                if (SPGB_LEAN_PACKQ)
+                    cp8(qd + S * kQSlot, q2 + (size_t)(p - 1) * plane + col);
+                else
+                    cp16(qd + S * kQSlot, q + (size_t)(p - 1) * plane + col);
+            }
         }
         commit();
     };
@@ -272,18 +309,19 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     load(I_<2>{}, za + 1);
     wait_groups<2>();
     __syncthreads();
-    const float4 *tc = &tiles[0][(ty + 1) * LHX + tx + 1];  // the thread's centre record in slot 0
-    const Sum below = summarise<DM>(P, L, tc);
+    const unsigned tc = smem_addr(&tiles[0][(ty + 1) * LHX + tx + 1]);  // the thread's centre record in slot 0
+    const Sum below = summarise<DM, 0>(P, L, tc);
     __syncthreads();
     load(I_<0>{}, za + 2);
     wait_groups<2>();
     __syncthreads();
-    const Sum cur = summarise<DM>(P, L, tc + LHN);
+    const Sum cur = summarise<DM, 1>(P, L, tc);
     // the open accumulator of the plane being finished, its w and centre
     pv acc = add_onsite(P, add_zdmi<DM>(P, cur.e + below.w, below.c, -1.f), cur.c);
     pv wcur = cur.w, ccur = cur.c;
+    float qx = cur.cw;  // x of q of the plane being finished (packed layout, corrector)
     int i = za * plane + col;
-    const float cA = c.cA[0], al = c.alpha, dt = c.dt, hdt = 0.5f * c.dt;
+    const float al = c.alpha, dt = c.dt, hdt = 0.5f * c.dt;
     // plane z: plane z+1 (slot SN) has landed; plane z's slot SF is refilled
     // with plane z+3.  B(z) = acc + w(z+1) + c(z+1) x D_{+z}; then plane z+1
     // opens A(z+1) = e(z+1) + w(z) - c(z) x D_{+z} + onsite(c(z+1)).
@@ -291,31 +329,40 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
         constexpr int SN = decltype(sn)::value;
         wait_groups<1>();
         __syncthreads();
-        p4 qi;
-        if (PASS == 1) qi = ld4(&qt[SN][tid]);
+        v3<float> qi;
+        if (PASS == 1) {
+            if (SPGB_LEAN_PACKQ) {
+                const float2 yz = lds2(qd + SN * kQSlot);
+                qi = mk(qx, yz.x, yz.y);
+            } else {
+                qi = v3of(pvof(ld4<SN * int(kQSlot)>(qd)));
+            }
+        }
         load(sf, z + 3);
-        const Sum up = summarise<DM>(P, L, tc + SN * LHN);
+        const Sum up = summarise<DM, SN>(P, L, tc);
         const pv Bp = add_zdmi<DM>(P, acc + up.w, up.c, 1.f);
         acc = add_onsite(P, add_zdmi<DM>(P, up.e + wcur, ccur, -1.f), up.c);
         const v3<float> n = v3of(ccur), B = v3of(Bp);
         wcur = up.w;
         ccur = up.c;
+        qx = up.cw;
         if (PASS == 0) {
             v3<float> Bth = mk(0.f, 0.f, 0.f);
             if (TH) Bth = thermal(thermal_bits_at(c, c.step, (uint32_t)i, 0u), c.sig[0]);
-            const v3<float> A = llg_A(cA, al, n, B + Bth);
+            const v3<float> A = lA(al, n, B + Bth);
             const v3<float> f = cross(n, A);
             const v3<float> p = unit(axpy(dt, f, n));
-            if (TH) {
-                const v3<float> gth = cross(p, llg_A(cA, al, p, Bth));
-                st(q, i, axpy(hdt, f + gth, n));
+            const v3<float> qv = TH ? axpy(hdt, f + cross(p, lA(al, p, Bth)), n) : axpy(hdt, f, n);
+            if (SPGB_LEAN_PACKQ) {
+                np[i] = make_float4(p.x, p.y, p.z, qv.x);
+                q2[i] = make_float2(qv.y, qv.z);
             } else {
-                st(q, i, axpy(hdt, f, n));
+                st(q, i, qv);
+                st(np, i, p);
             }
-            st(np, i, p);
         } else {
-            const v3<float> Ap = llg_A(cA, al, n, B);
-            st(nout, i, unit(axpy(hdt, cross(n, Ap), v3of(pvof(qi)))));
+            const v3<float> Ap = lA(al, n, B);
+            st(nout, i, unit(axpy(hdt, cross(n, Ap), qi)));
         }
         i += plane;
     };
@@ -335,13 +382,13 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
 template <int PASS, int DM, bool TH>
 __global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MINB_CORR)
     k_lean(const __grid_constant__ CubicParams<float> P, const float4 *__restrict__ src, float4 *__restrict__ np,
-           float4 *__restrict__ q, float4 *__restrict__ nout, const __grid_constant__ LlgConst<float> c, int per)
+           float4 *__restrict__ q, float4 *__restrict__ nout, const __grid_constant__ LlgConst<float> c,
+           const __grid_constant__ LeanConst L, int per)
 {
     __shared__ __align__(16) float4 tiles[LNB][LHN];
-    __shared__ __align__(16) float4 qt[PASS == 1 ? LNB : 1][LT];
+    __shared__ __align__(16) unsigned char qt[PASS == 1 ? LNB * LT * kQRec : 16];
     allow_dependents();
     wait_prerequisite();  // the previous pass wrote what this one reads
-    const LeanConst L{make_float2(P.J1, P.J1), make_float2(P.J2, P.J2), make_float2(P.J3, P.J3)};
     const int tiles_x = P.nx / LX;
     const long total = (long)tiles_x * (P.ny / LY) * P.nz;
     long u = (long)blockIdx.x * per;
@@ -359,10 +406,12 @@ template <int PASS, int DM>
 cudaError_t lean_launch(int grid, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q, float4 *nout,
                         const LlgConst<float> &c, int per, cudaStream_t st)
 {
+    const LeanConst L{make_float2(P.J1, P.J1), make_float2(P.J2, P.J2), make_float2(P.J3, P.J3),
+                      make_float2(-1.f, -1.f)};
     if constexpr (PASS == 0)
         if (c.thermal)
-            return launch_pdl(k_lean<PASS, DM, true>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, per);
-    return launch_pdl(k_lean<PASS, DM, false>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, per);
+            return launch_pdl(k_lean<PASS, DM, true>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
+    return launch_pdl(k_lean<PASS, DM, false>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
 }
 
 template <int PASS>
@@ -385,8 +434,24 @@ cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
     const int grid = (int)((total + per - 1) / per);
-    return pass == 0 ? lean_dm<0>(grid, P, src, np, q, nout, c, per, st)
-                     : lean_dm<1>(grid, P, src, np, q, nout, c, per, st);
+    // every field term and the noise amplitude in units of c = cA[0] (one
+    // atom per cell): the kernels form c B directly
+    const float s = c.cA[0];
+    CubicParams<float> Ps = P;
+    Ps.J1 *= s;
+    Ps.J2 *= s;
+    Ps.J3 *= s;
+    for (int k = 0; k < 3; ++k) {
+        Ps.Dx[k] *= s;
+        Ps.Dy[k] *= s;
+        Ps.Dz[k] *= s;
+        Ps.Bz[k] *= s;
+    }
+    Ps.K *= s;
+    LlgConst<float> cs = c;
+    cs.sig[0] *= s;
+    return pass == 0 ? lean_dm<0>(grid, Ps, src, np, q, nout, cs, per, st)
+                     : lean_dm<1>(grid, Ps, src, np, q, nout, cs, per, st);
 }
 
 int cubic_lean_resident_ctas(int pass)
