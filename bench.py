@@ -53,8 +53,13 @@ SOLVER_BYTES = {"heun": {"llg_predictor": 48, "llg_corrector": 48},
 # place of recomputing the stencil on n and the noise.)  RK4 has no two-stage
 # figure and is charged with the design's bytes.
 METHOD_STEP_BYTES = {"heun": 80, "depondt": 80, "sib": 80}
+# the lean FP32 Heun passes (whole 32 x 8 tiles) pack q into the predicted
+# record's pad word plus 8 bytes: read n, write n^p|q_x and q_yz (40 B); read
+# those, write n (40 B)
+LEAN_HEUN_BYTES = {"llg_predictor": 40, "llg_corrector": 40}
 CORRECTOR_LAUNCHES = {"heun": 1, "depondt": 1, "sib": 1, "rk4": 3}
 KERNEL_SOURCES = ["paper_1901_11350_gb300/csrc/field_llg.cu", "paper_1901_11350_gb300/csrc/cubic.cu",
+                  "paper_1901_11350_gb300/csrc/cubic_lean.cu",
                   "paper_1901_11350_gb300/csrc/common.cuh"]
 # GNEB: bytes per spin and iteration of the method's three passes with FP32
 # records (read n, write g 32; read the three images and g 64; read n, g, v
@@ -269,7 +274,8 @@ def run_gpu(args):
     n = host0.to("cuda")
     kw = dict(solver=args.solver, dt=r["dt"], alpha=r["alpha"],
               T=r["T"] if args.temperature is None else args.temperature, seed=r["seed"], replica=rank)
-    bps = SOLVER_BYTES[args.solver]
+    lean = args.solver == "heun" and bool(ctx.get_option("cubic_lean"))
+    bps = LEAN_HEUN_BYTES if lean else SOLVER_BYTES[args.solver]
     bytes_per_step = bps["llg_predictor"] + CORRECTOR_LAUNCHES[args.solver] * bps["llg_corrector"]
     if not args.zc and not args.generic and not args.cubic_rows:
         ctx.autotune(n)  # tile height and planes per CTA, chosen by timing before the timed region
@@ -367,7 +373,7 @@ def run_gpu(args):
                       "planes_per_cta": ctx.get_option("planes_per_cta"),
                       "planes_per_cta_corr": ctx.get_option("planes_per_cta_corr"),
                       "columns_per_thread": [ctx.get_option("cubic_rows"), ctx.get_option("cubic_rows_corr")],
-                      "lean_heun_passes": bool(ctx.get_option("cubic_lean")) and args.solver == "heun",
+                      "lean_heun_passes": lean,
                       "T_K": r["T"], "thermal_rng": "philox4x32-10", "l2": "flushed (256 MB write) before each step",
                       "parallelism": "replicas" if world > 1 else "single"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},

@@ -44,7 +44,7 @@ constexpr int LNB = 3;                             // plane ring
 #endif
 constexpr unsigned kQRec = SPGB_LEAN_PACKQ ? 8u : 16u;  // bytes of a q record in its array and ring
 #ifndef SPGB_LEAN_MINB_CORR
-#define SPGB_LEAN_MINB_CORR 4
+#define SPGB_LEAN_MINB_CORR 3
 #endif
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -245,14 +245,8 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     const int plane = P.nx * P.ny;  // N < 2^31
     // this thread stages halo records tid and tid + 256 of every plane: their
     // in-plane offsets (-1: outside an open lattice, -2: no such record)
-    int g[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int e = tid + s * LT;
-        if (e >= LHN) {
-            g[s] = -2;
-            continue;
-        }
+    auto halo = [&](int e) {
+        if (e >= LHN) return -2;
         int gx = x0 - 1 + e % LHX, gy = y0 - 1 + e / LHX;
         bool in = true;
         if (P.per0)
@@ -263,16 +257,17 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
         else
             in = in && gy >= 0 && gy < P.ny;
-        g[s] = in ? gy * P.nx + gx : -1;
-    }
+        return in ? gy * P.nx + gx : -1;
+    };
+    const int g0 = halo(tid), g1 = halo(tid + LT);
     const unsigned sd0 = smem_addr(&tiles[0][tid]), sd1 = sd0 + 16u * LT;
     const unsigned qd = smem_addr(qt + kQRec * tid);
     constexpr unsigned kSlot = 16u * LHN, kQSlot = kQRec * LT;
     float2 *const q2 = reinterpret_cast<float2 *>(q);  // (y, z) of q, packed layout
 #pragma unroll
     for (int b = 0; b < LNB; ++b) {
-        if (g[0] == -1) st_zero(sd0 + b * kSlot);
-        if (g[1] == -1) st_zero(sd1 + b * kSlot);
+        if (g0 == -1) st_zero(sd0 + b * kSlot);
+        if (g1 == -1) st_zero(sd1 + b * kSlot);
     }
     const int col = (y0 + ty) * P.nx + x0 + tx;
     auto load = [&](auto slot, int p) {
@@ -288,11 +283,11 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             }
             if (zin) {
                 const float4 *base = src + (size_t)pz * plane;
-                if (g[0] >= 0) cp16(sd0 + S * kSlot, base + g[0]);
-                if (g[1] >= 0) cp16(sd1 + S * kSlot, base + g[1]);
+                if (g0 >= 0) cp16(sd0 + S * kSlot, base + g0);
+                if (g1 >= 0) cp16(sd1 + S * kSlot, base + g1);
             } else {
-                if (g[0] != -2) st_zero(sd0 + S * kSlot);
-                if (g[1] != -2) st_zero(sd1 + S * kSlot);
+                if (g0 != -2) st_zero(sd0 + S * kSlot);
+                if (g1 != -2) st_zero(sd1 + S * kSlot);
             }
             if (PASS == 1 && p - 1 >= za && p - 1 < zb) {
                 if (SPGB_LEAN_PACKQ)
@@ -366,6 +361,9 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
         }
         i += plane;
     };
+    // (a second copy of the loop for the segment's interior, without the
+    // range tests of `load`, was measured: it costs the predictor spills at 64
+    // registers and gains the corrector nothing at 80)
     for (int z = za; z < zb; z += LNB) {
         step(I_<2>{}, I_<1>{}, z);
         if (z + 1 >= zb) break;
