@@ -4,8 +4,9 @@
 // plane is cut into whole 32 x 8 column tiles (nx % 32 == 0, ny % 8 == 0).
 //
 // The plane streaming is that of cubic.cu: a CTA owns a 32 x 8 column tile
-// and a run of planes, planes pass through a ring of three shared-memory
-// tiles with a one-cell halo, and each thread carries one plane's summary
+// and a run of planes, planes pass through a ring of shared-memory tiles with
+// a one-cell halo (four, finished two planes per block barrier), and each
+// thread carries one plane's summary
 // (centre spin c, the part w it gives the planes above and below, the open
 // field accumulator) in registers from plane to plane.  What differs is the
 // per-spin instruction budget of the loop, which bounds these passes:
@@ -32,7 +33,13 @@ namespace {
 
 constexpr int LX = 32, LY = 8, LT = LX * LY;       // column tile = threads per CTA
 constexpr int LHX = LX + 2, LHN = LHX * (LY + 2);  // halo tile: 34 x 10 records
-constexpr int LNB = 3;                             // plane ring
+// 1: planes are finished in pairs between two block barriers (a ring of four
+// plane buffers, one cp.async group per pair); 0: one plane per barrier
+// (a ring of three)
+#ifndef SPGB_LEAN_PAIRS
+#define SPGB_LEAN_PAIRS 1
+#endif
+constexpr int LNB = SPGB_LEAN_PAIRS ? 4 : 3;  // plane ring
 #ifndef SPGB_LEAN_MINB
 #define SPGB_LEAN_MINB 4
 #endif
@@ -232,9 +239,10 @@ template <int V> using I_ = std::integral_constant<int, V>;
 // One segment: planes [za, zb) of the column tile at (x0, y0).  PASS 0: the
 // predictor on src = n (writes np and the folded term q); PASS 1: the
 // corrector on src = np (q of each plane arrives with the ring, writes
-// nout = n).  Plane p lives in ring slot (p - za + 1) % 3; every fetch is one
-// cp.async group, so that waiting for all but the newest group means "the
-// next plane has landed".
+// nout = n).  Plane p lives in ring slot (p - za + 1) % LNB.  With pairs,
+// the two planes a pair fetches form one cp.async group, waited for at the
+// start of the next pair; with one plane per barrier every fetch is a group
+// and waiting for all but the newest means "the next plane has landed".
 template <int PASS, int DM, bool TH>
 __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const LeanConst &L, const LlgConst<float> &c,
                                              const float4 *__restrict__ src, float4 *__restrict__ np,
@@ -270,7 +278,7 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
         if (g1 == -1) st_zero(sd1 + b * kSlot);
     }
     const int col = (y0 + ty) * P.nx + x0 + tx;
-    auto load = [&](auto slot, int p) {
+    auto issue = [&](auto slot, int p) {
         constexpr unsigned S = decltype(slot)::value;
         if (p <= zb) {
             int pz = p;
@@ -296,34 +304,49 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
                     cp16(qd + S * kQSlot, q + (size_t)(p - 1) * plane + col);
             }
         }
+    };
+    auto load = [&](auto slot, int p) {
+        issue(slot, p);
         commit();
     };
+    const unsigned tc = smem_addr(&tiles[0][(ty + 1) * LHX + tx + 1]);  // the thread's centre record in slot 0
+#if SPGB_LEAN_PAIRS
+    // planes za-1, za (slots 0, 1) and za+1, za+2 (slots 2, 3) in flight
+    issue(I_<0>{}, za - 1);
+    issue(I_<1>{}, za);
+    commit();
+    issue(I_<2>{}, za + 1);
+    issue(I_<3>{}, za + 2);
+    commit();
+    wait_groups<1>();
+    __syncthreads();
+    const Sum below = summarise<DM, 0>(P, L, tc);
+    const Sum cur = summarise<DM, 1>(P, L, tc);
+#else
     // planes za-1, za, za+1 in flight
     load(I_<0>{}, za - 1);
     load(I_<1>{}, za);
     load(I_<2>{}, za + 1);
     wait_groups<2>();
     __syncthreads();
-    const unsigned tc = smem_addr(&tiles[0][(ty + 1) * LHX + tx + 1]);  // the thread's centre record in slot 0
     const Sum below = summarise<DM, 0>(P, L, tc);
     __syncthreads();
     load(I_<0>{}, za + 2);
     wait_groups<2>();
     __syncthreads();
     const Sum cur = summarise<DM, 1>(P, L, tc);
+#endif
     // the open accumulator of the plane being finished, its w and centre
     pv acc = add_onsite(P, add_zdmi<DM>(P, cur.e + below.w, below.c, -1.f), cur.c);
     pv wcur = cur.w, ccur = cur.c;
     float qx = cur.cw;  // x of q of the plane being finished (packed layout, corrector)
     int i = za * plane + col;
     const float al = c.alpha, dt = c.dt, hdt = 0.5f * c.dt;
-    // plane z: plane z+1 (slot SN) has landed; plane z's slot SF is refilled
-    // with plane z+3.  B(z) = acc + w(z+1) + c(z+1) x D_{+z}; then plane z+1
-    // opens A(z+1) = e(z+1) + w(z) - c(z) x D_{+z} + onsite(c(z+1)).
-    auto step = [&](auto sn, auto sf, int z) {
+    // finish the next plane z, whose upper neighbour z+1 sits in ring slot
+    // SN: B(z) = acc + w(z+1) + c(z+1) x D_{+z}; then plane z+1 opens
+    // A(z+1) = e(z+1) + w(z) - c(z) x D_{+z} + onsite(c(z+1)).
+    auto finish = [&](auto sn) {
         constexpr int SN = decltype(sn)::value;
-        wait_groups<1>();
-        __syncthreads();
         v3<float> qi;
         if (PASS == 1) {
             if (SPGB_LEAN_PACKQ) {
@@ -333,7 +356,6 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
                 qi = v3of(pvof(ld4<SN * int(kQSlot)>(qd)));
             }
         }
-        load(sf, z + 3);
         const Sum up = summarise<DM, SN>(P, L, tc);
         const pv Bp = add_zdmi<DM>(P, acc + up.w, up.c, 1.f);
         acc = add_onsite(P, add_zdmi<DM>(P, up.e + wcur, ccur, -1.f), up.c);
@@ -364,6 +386,31 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     // (a second copy of the loop for the segment's interior, without the
     // range tests of `load`, was measured: it costs the predictor spills at 64
     // registers and gains the corrector nothing at 80)
+#if SPGB_LEAN_PAIRS
+    // planes z and z+1: planes z+1, z+2 have landed (slots S0, S1); the slots
+    // of planes z-1 and z (R0, R1), read before the barrier, take z+3, z+4
+    auto pair = [&](auto s0, auto s1, auto r0, auto r1, int z) {
+        wait_groups<0>();
+        __syncthreads();
+        issue(r0, z + 3);
+        issue(r1, z + 4);
+        commit();
+        finish(s0);
+        if (z + 1 < zb) finish(s1);
+    };
+    for (int z = za; z < zb; z += LNB) {
+        pair(I_<2>{}, I_<3>{}, I_<0>{}, I_<1>{}, z);
+        if (z + 2 >= zb) break;
+        pair(I_<0>{}, I_<1>{}, I_<2>{}, I_<3>{}, z + 2);
+    }
+#else
+    // plane z: plane z+1 (slot SN) has landed; plane z's slot SF takes z+3
+    auto step = [&](auto sn, auto sf, int z) {
+        wait_groups<1>();
+        __syncthreads();
+        load(sf, z + 3);
+        finish(sn);
+    };
     for (int z = za; z < zb; z += LNB) {
         step(I_<2>{}, I_<1>{}, z);
         if (z + 1 >= zb) break;
@@ -371,6 +418,7 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
         if (z + 2 >= zb) break;
         step(I_<1>{}, I_<0>{}, z + 2);
     }
+#endif
     wait_groups<0>();
     __syncthreads();  // the next segment reuses the ring
 }
@@ -387,16 +435,25 @@ __global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MIN
     __shared__ __align__(16) unsigned char qt[PASS == 1 ? LNB * LT * kQRec : 16];
     allow_dependents();
     wait_prerequisite();  // the previous pass wrote what this one reads
+    // units: (tile, plane) pairs, fewer than 2^31 (N < 2^31 spins, 256 per
+    // tile and plane); one division per CTA, then the runs advance tile by tile
     const int tiles_x = P.nx / LX;
-    const long total = (long)tiles_x * (P.ny / LY) * P.nz;
-    long u = (long)blockIdx.x * per;
-    const long u1 = min(u + per, total);
+    const int total = tiles_x * (P.ny / LY) * P.nz;
+    int u = blockIdx.x * per;
+    const int u1 = min(u + per, total);
+    if (u >= u1) return;
+    const int tile = u / P.nz;
+    int za = u - tile * P.nz;
+    int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     while (u < u1) {
-        const int tile = (int)(u / P.nz), za = (int)(u % P.nz);
-        const int zb = (int)min((long)P.nz, za + (u1 - u));
-        lean_segment<PASS, DM, TH>(P, L, c, src, np, q, nout, tiles, qt, (tile % tiles_x) * LX,
-                                   (tile / tiles_x) * LY, za, zb);
+        const int zb = min(P.nz, za + (u1 - u));
+        lean_segment<PASS, DM, TH>(P, L, c, src, np, q, nout, tiles, qt, tx * LX, ty * LY, za, zb);
         u += zb - za;
+        za = 0;
+        if (++tx == tiles_x) {
+            tx = 0;
+            ++ty;
+        }
     }
 }
 
