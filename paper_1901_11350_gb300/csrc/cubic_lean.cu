@@ -33,13 +33,17 @@ namespace {
 
 constexpr int LX = 32, LY = 8, LT = LX * LY;       // column tile = threads per CTA
 constexpr int LHX = LX + 2, LHN = LHX * (LY + 2);  // halo tile: 34 x 10 records
-// 1: planes are finished in pairs between two block barriers (a ring of four
-// plane buffers, one cp.async group per pair); 0: one plane per barrier
-// (a ring of three)
-#ifndef SPGB_LEAN_PAIRS
-#define SPGB_LEAN_PAIRS 1
+// planes finished between two block barriers (2, 3 or 4): a group of LK
+// planes is one cp.async group, fetched one group ahead into a ring of 2 LK
+// plane buffers (measured at 128^3: pairs 50.8 G spin-updates/s, three per
+// barrier 50.4, four 49.9 (spills), one plane per barrier with a ring of
+// three fetched two planes ahead 49.3)
+#ifndef SPGB_LEAN_LK
+#define SPGB_LEAN_LK 2
 #endif
-constexpr int LNB = SPGB_LEAN_PAIRS ? 4 : 3;  // plane ring
+constexpr int LK = SPGB_LEAN_LK;
+static_assert(LK >= 2 && LK <= 4, "2 to 4 planes per barrier");
+constexpr int LNB = 2 * LK;  // plane ring
 #ifndef SPGB_LEAN_MINB
 #define SPGB_LEAN_MINB 4
 #endif
@@ -235,6 +239,11 @@ __device__ __forceinline__ pv add_onsite(const CubicParams<float> &P, pv v, pv c
 }
 
 template <int V> using I_ = std::integral_constant<int, V>;
+// f(I_<0>), f(I_<1>), .. f(I_<K-1>) in order
+template <typename F, int... J> __device__ __forceinline__ void each(F &&f, std::integer_sequence<int, J...>)
+{
+    (f(I_<J>{}), ...);
+}
 
 // One segment: planes [za, zb) of the column tile at (x0, y0).  PASS 0: the
 // predictor on src = n (writes np and the folded term q); PASS 1: the
@@ -305,37 +314,18 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             }
         }
     };
-    auto load = [&](auto slot, int p) {
-        issue(slot, p);
-        commit();
-    };
     const unsigned tc = smem_addr(&tiles[0][(ty + 1) * LHX + tx + 1]);  // the thread's centre record in slot 0
-#if SPGB_LEAN_PAIRS
-    // planes za-1, za (slots 0, 1) and za+1, za+2 (slots 2, 3) in flight
+    // planes za-1, za (slots 0, 1), then za+1 .. za+LK (slots 2 .. LK+1) in flight
     issue(I_<0>{}, za - 1);
     issue(I_<1>{}, za);
     commit();
-    issue(I_<2>{}, za + 1);
-    issue(I_<3>{}, za + 2);
+    each([&](auto j) { issue(I_<2 + decltype(j)::value>{}, za + 1 + decltype(j)::value); },
+         std::make_integer_sequence<int, LK>{});
     commit();
     wait_groups<1>();
     __syncthreads();
     const Sum below = summarise<DM, 0>(P, L, tc);
     const Sum cur = summarise<DM, 1>(P, L, tc);
-#else
-    // planes za-1, za, za+1 in flight
-    load(I_<0>{}, za - 1);
-    load(I_<1>{}, za);
-    load(I_<2>{}, za + 1);
-    wait_groups<2>();
-    __syncthreads();
-    const Sum below = summarise<DM, 0>(P, L, tc);
-    __syncthreads();
-    load(I_<0>{}, za + 2);
-    wait_groups<2>();
-    __syncthreads();
-    const Sum cur = summarise<DM, 1>(P, L, tc);
-#endif
     // the open accumulator of the plane being finished, its w and centre
     pv acc = add_onsite(P, add_zdmi<DM>(P, cur.e + below.w, below.c, -1.f), cur.c);
     pv wcur = cur.w, ccur = cur.c;
@@ -386,39 +376,26 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     // (a second copy of the loop for the segment's interior, without the
     // range tests of `load`, was measured: it costs the predictor spills at 64
     // registers and gains the corrector nothing at 80)
-#if SPGB_LEAN_PAIRS
-    // planes z and z+1: planes z+1, z+2 have landed (slots S0, S1); the slots
-    // of planes z-1 and z (R0, R1), read before the barrier, take z+3, z+4
-    auto pair = [&](auto s0, auto s1, auto r0, auto r1, int z) {
+    // planes z .. z+LK-1: planes z+1 .. z+LK have landed in slots BASE ..
+    // BASE+LK-1 (mod 2 LK); the other half of the ring, read before the
+    // barrier, takes planes z+LK+1 .. z+2LK
+    auto group = [&](auto base, int z) {
+        constexpr int BASE = decltype(base)::value;
         wait_groups<0>();
         __syncthreads();
-        issue(r0, z + 3);
-        issue(r1, z + 4);
+        each([&](auto j) { issue(I_<(BASE + LK + decltype(j)::value) % LNB>{}, z + LK + 1 + decltype(j)::value); },
+             std::make_integer_sequence<int, LK>{});
         commit();
-        finish(s0);
-        if (z + 1 < zb) finish(s1);
+        each([&](auto j) {
+            constexpr int J = decltype(j)::value;
+            if (J == 0 || z + J < zb) finish(I_<(BASE + J) % LNB>{});
+        }, std::make_integer_sequence<int, LK>{});
     };
     for (int z = za; z < zb; z += LNB) {
-        pair(I_<2>{}, I_<3>{}, I_<0>{}, I_<1>{}, z);
-        if (z + 2 >= zb) break;
-        pair(I_<0>{}, I_<1>{}, I_<2>{}, I_<3>{}, z + 2);
+        group(I_<2>{}, z);
+        if (z + LK >= zb) break;
+        group(I_<2 + LK>{}, z + LK);
     }
-#else
-    // plane z: plane z+1 (slot SN) has landed; plane z's slot SF takes z+3
-    auto step = [&](auto sn, auto sf, int z) {
-        wait_groups<1>();
-        __syncthreads();
-        load(sf, z + 3);
-        finish(sn);
-    };
-    for (int z = za; z < zb; z += LNB) {
-        step(I_<2>{}, I_<1>{}, z);
-        if (z + 1 >= zb) break;
-        step(I_<0>{}, I_<2>{}, z + 1);
-        if (z + 2 >= zb) break;
-        step(I_<1>{}, I_<0>{}, z + 2);
-    }
-#endif
     wait_groups<0>();
     __syncthreads();  // the next segment reuses the ring
 }
