@@ -647,10 +647,11 @@ enum {
     /* the same for the corrector pass alone */
     SP_OPT_CUBIC_ROWS_CORR = 12,
     /* 1 (default): FP32 stochastic Heun on the 27-point path takes the lean
-     * passes where the lattice's xy plane is cut into whole 32 x 8 column
-     * tiles (nx a multiple of 32, ny of 8) and one column per thread is in
-     * use; the same method and stencil, fewer instructions per spin, results
-     * equal to the general passes within FP32 rounding (not bit for bit).
+     * passes where the lattice's xy plane is cut into whole column tiles of
+     * the tile height in use (nx a multiple of 32; ny of 8 with one column
+     * per thread, of 16 with two); the same method and stencil, fewer
+     * instructions per spin, results equal to the general passes within FP32
+     * rounding (not bit for bit; one and two columns give the same bits).
      * 0: always the general passes.  Reading returns 1 when the lean passes
      * would be taken for a Heun call of this context */
     SP_OPT_CUBIC_LEAN = 13

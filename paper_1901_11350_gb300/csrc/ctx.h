@@ -192,12 +192,12 @@ inline int cubic_rows(const sp_ctx *c, int pass)
 }
 
 // Whether a Heun pass of this context on the 27-point path takes the lean
-// FP32 kernels (cubic_lean.cu): option on, FP32, no dipole field, one column
-// per thread and a lattice cut into whole 32 x 8 column tiles.
+// FP32 kernels (cubic_lean.cu): option on, FP32, no dipole field and a
+// lattice cut into whole column tiles of the pass's height (32 x 8 rows).
 inline bool cubic_lean_taken(const sp_ctx *c, int pass)
 {
     return c->lean && c->prec == SP_F32 && c->cubic && c->use_cubic && c->h.dipole == SP_DIPOLE_NONE &&
-           cubic_rows(c, pass) == 1 && cubic_lean_fits(c->nc[0], c->nc[1]);
+           cubic_lean_fits(c->nc[0], c->nc[1], cubic_rows(c, pass));
 }
 
 // Units per CTA of the 27-point path: the user's choice, or the units spread
@@ -213,7 +213,7 @@ inline int cubic_per(sp_ctx *c, int pass = 0)
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
         const int rows = cubic_rows(c, pass);
-        long slots = (long)nsm * (cubic_lean_taken(c, pass) ? cubic_lean_resident_ctas(pass)
+        long slots = (long)nsm * (cubic_lean_taken(c, pass) ? cubic_lean_resident_ctas(pass, rows)
                                                              : cubic_resident_ctas(c->prec, pass, rows));
         long units = cubic_units(c->nc[0], c->nc[1], c->nc[2], rows);
         a = (int)std::max(1L, (units + slots - 1) / slots);

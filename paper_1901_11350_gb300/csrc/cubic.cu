@@ -546,9 +546,8 @@ cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const re
 {
     rows = cubic_rows_taken(sizeof(T) == 8 ? SP_F64 : SP_F32, rows, llg_reps(c) > 1, Bdd != nullptr);
     if constexpr (std::is_same<T, float>::value)
-        if (lean && solver == SP_HEUN && pass <= 1 && rows == 1 && !Bdd && llg_reps(c) == 1 &&
-            cubic_lean_fits(P.nx, P.ny))
-            return launch_cubic_lean(pass, P, src, np, q, nout, c, per, st);
+        if (lean && solver == SP_HEUN && pass <= 1 && !Bdd && llg_reps(c) == 1 && cubic_lean_fits(P.nx, P.ny, rows))
+            return launch_cubic_lean(pass, P, src, np, q, nout, c, per, st, rows);
     long total = cubic_units(P.nx, P.ny, P.nz, rows) * llg_reps(c);
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;

@@ -35,11 +35,12 @@ cudaError_t launch_cubic(int pass, int solver, const CubicParams<T> &P, const re
                          int rows = 1, bool lean = false);
 
 // The lean stochastic Heun passes (cubic_lean.cu): FP32, one lattice without
-// the dipole field, nx % 32 == 0 and ny % 8 == 0 (cubic_lean_fits); the same
-// (32 x 8 column tile, plane) units and `per` as launch_cubic with rows = 1.
-bool cubic_lean_fits(int nx, int ny);
+// the dipole field cut into whole 32 x 8 rows column tiles (nx % 32 == 0,
+// ny % (8 rows) == 0: cubic_lean_fits); the same (tile, plane) units and
+// `per` as launch_cubic with the same rows (1 or 2 columns per thread).
+bool cubic_lean_fits(int nx, int ny, int rows);
 cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q,
-                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st);
-int cubic_lean_resident_ctas(int pass);
+                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st, int rows);
+int cubic_lean_resident_ctas(int pass, int rows);
 
 }  // namespace spgb

@@ -57,6 +57,13 @@ constexpr unsigned kQRec = SPGB_LEAN_PACKQ ? 8u : 16u;  // bytes of a q record i
 #ifndef SPGB_LEAN_MINB_CORR
 #define SPGB_LEAN_MINB_CORR 3
 #endif
+// the same with two columns per thread
+#ifndef SPGB_LEAN_MINB2
+#define SPGB_LEAN_MINB2 2
+#endif
+#ifndef SPGB_LEAN_MINB2_CORR
+#define SPGB_LEAN_MINB2_CORR 2
+#endif
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp16(unsigned s, const void *g)
@@ -106,6 +113,13 @@ __device__ __forceinline__ float cosf_(float x)
     return r;
 }
 
+template <int V> using I_ = std::integral_constant<int, V>;
+// f(I_<0>), f(I_<1>), .. f(I_<K-1>) in order
+template <typename F, int... J> __device__ __forceinline__ void each(F &&f, std::integer_sequence<int, J...>)
+{
+    (f(I_<J>{}), ...);
+}
+
 // A record as two f32x2 halves: a = (x, y), b = (z, pad).  Tile records are
 // loaded and summed in this form (one 16-byte load each); the pad lane is
 // carried through those sums and never read back.
@@ -117,7 +131,7 @@ struct p4 {
 // measured slower: the quad-register destinations cost spills)
 template <int OFF> __device__ __forceinline__ p4 ld4(unsigned s)
 {
-    const float4 v = *reinterpret_cast<const float4 *>(__cvta_shared_to_generic(s + OFF));
+    const float4 v = *reinterpret_cast<const float4 *>(__cvta_shared_to_generic((unsigned)((int)s + OFF)));
     return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
 __device__ __forceinline__ p4 operator+(p4 u, p4 v) { return {__fadd2_rn(u.a, v.a), __fadd2_rn(u.b, v.b)}; }
@@ -179,23 +193,21 @@ struct LeanConst {
     float2 J1, J2, J3, m1;
 };
 
-template <int DM, int SLOT>
-__device__ __forceinline__ Sum summarise(const CubicParams<float> &P, const LeanConst &L, unsigned t)
+// The summary of one column from its centre record c, the sums f and k of
+// its in-plane face and corner neighbours and the face differences
+// dx = n(+x) - n(-x), dy = n(+y) - n(-y).
+template <int DM>
+__device__ __forceinline__ Sum summary(const CubicParams<float> &P, const LeanConst &L, p4 c4, p4 f4, p4 k4, p4 dx4,
+                                       p4 dy4)
 {
-    // t: shared-memory address of the thread's centre record in ring slot 0
-    constexpr int B = SLOT * LHN * 16, X = 16, Y = 16 * LHX;
-    const p4 xp = ld4<B + X>(t), xm = ld4<B - X>(t), yp = ld4<B + Y>(t), ym = ld4<B - Y>(t);
-    const p4 c4 = ld4<B>(t);
-    const pv c = pvof(c4);
-    const pv f = pvof((xp + xm) + (yp + ym));
-    const pv k = pvof((ld4<B + Y + X>(t) + ld4<B - Y - X>(t)) + (ld4<B - Y + X>(t) + ld4<B + Y - X>(t)));
+    const pv c = pvof(c4), f = pvof(f4), k = pvof(k4);
     Sum r;
     r.c = c;
     r.cw = c4.b.y;
     r.w = pfma(L.J1, c, pfma(L.J2, f, pmul(L.J3, k)));
     pv e = pfma(L.J1, f, pmul(L.J2, k));
     if (DM != 0) {
-        const pv dx = pvof(minus(xp, xm, L.m1)), dy = pvof(minus(yp, ym, L.m1));
+        const pv dx = pvof(dx4), dy = pvof(dy4);
         if (DM == 1) {
             // D [(n(+x) - n(-x)) x xhat + (n(+y) - n(-y)) x yhat]
             const float D = P.Dx[0];
@@ -210,6 +222,36 @@ __device__ __forceinline__ Sum summarise(const CubicParams<float> &P, const Lean
     }
     r.e = e;
     return r;
+}
+
+// Summaries of a thread's R columns (rows 0 .. R-1 of its strip, adjacent in
+// y) in the plane of ring slot SLOT.  t: shared-memory address of the row-0
+// centre record in slot 0; HN: records per ring slot.  Rows r-1, r, r+1 of
+// column r are read once for both columns, and the sums follow one
+// association for either R, so both give the same bits:
+//   f = (n(x-1) + n(x+1)) + (n(y+1) + n(y-1)),
+//   k = (n(x-1,y-1) + n(x+1,y-1)) + (n(x-1,y+1) + n(x+1,y+1)).
+template <int DM, int R, int SLOT, int HN>
+__device__ __forceinline__ void summarise(const CubicParams<float> &P, const LeanConst &L, unsigned t, Sum (&s)[R])
+{
+    constexpr int B = SLOT * HN * 16, X = 16, Y = 16 * LHX;
+    // row -1 (above row 0): its x-neighbour sum and centre
+    p4 up_m = ld4<B - Y - X>(t), up_p = ld4<B - Y + X>(t);
+    p4 up_s = up_m + up_p, up_c = ld4<B - Y>(t);
+    p4 rm = ld4<B - X>(t), rp = ld4<B + X>(t);
+    p4 r_s = rm + rp, r_c = ld4<B>(t), r_d = minus(rp, rm, L.m1);
+    each([&](auto jj) {
+        constexpr int J = decltype(jj)::value;
+        // row J + 1 (below row J)
+        const p4 dm = ld4<B + (J + 1) * Y - X>(t), dp = ld4<B + (J + 1) * Y + X>(t);
+        const p4 d_s = dm + dp, d_c = ld4<B + (J + 1) * Y>(t);
+        s[J] = summary<DM>(P, L, r_c, r_s + (d_c + up_c), up_s + d_s, r_d, minus(d_c, up_c, L.m1));
+        up_s = r_s;
+        up_c = r_c;
+        r_s = d_s;
+        r_c = d_c;
+        r_d = minus(dp, dm, L.m1);
+    }, std::make_integer_sequence<int, R>{});
 }
 
 // s * (c x D_{+z}) added to the (x, y, z) lanes of v
@@ -238,32 +280,34 @@ __device__ __forceinline__ pv add_onsite(const CubicParams<float> &P, pv v, pv c
     return v;
 }
 
-template <int V> using I_ = std::integral_constant<int, V>;
-// f(I_<0>), f(I_<1>), .. f(I_<K-1>) in order
-template <typename F, int... J> __device__ __forceinline__ void each(F &&f, std::integer_sequence<int, J...>)
-{
-    (f(I_<J>{}), ...);
-}
 
-// One segment: planes [za, zb) of the column tile at (x0, y0).  PASS 0: the
-// predictor on src = n (writes np and the folded term q); PASS 1: the
+// Halo tile of a 32 x 8R column tile: (32 + 2) x (8R + 2) records per ring
+// slot, staged by the CTA's 256 threads, NSL records each at most.
+template <int R> struct LTile {
+    static constexpr int HN = LHX * (LY * R + 2);
+    static constexpr int NSL = (HN + LT - 1) / LT;
+};
+
+// One segment: planes [za, zb) of the column tile at (x0, y0), each thread R
+// columns adjacent in y.  PASS 0: the predictor on src = n (writes the
+// predicted record with q's x in its pad word, and q's y, z); PASS 1: the
 // corrector on src = np (q of each plane arrives with the ring, writes
-// nout = n).  Plane p lives in ring slot (p - za + 1) % LNB.  With pairs,
-// the two planes a pair fetches form one cp.async group, waited for at the
-// start of the next pair; with one plane per barrier every fetch is a group
-// and waiting for all but the newest means "the next plane has landed".
-template <int PASS, int DM, bool TH>
+// nout = n).  Plane p lives in ring slot (p - za + 1) % LNB; the LK planes
+// a group fetches form one cp.async group, waited for at the start of the
+// next group.
+template <int PASS, int DM, bool TH, int R>
 __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const LeanConst &L, const LlgConst<float> &c,
                                              const float4 *__restrict__ src, float4 *__restrict__ np,
-                                             float4 *__restrict__ q, float4 *__restrict__ nout, float4 (*tiles)[LHN],
+                                             float4 *__restrict__ q, float4 *__restrict__ nout, float4 *tiles,
                                              unsigned char *qt, int x0, int y0, int za, int zb)
 {
+    constexpr int HN = LTile<R>::HN, NSL = LTile<R>::NSL;
     const int tid = threadIdx.x, tx = tid & (LX - 1), ty = tid / LX;
     const int plane = P.nx * P.ny;  // N < 2^31
-    // this thread stages halo records tid and tid + 256 of every plane: their
-    // in-plane offsets (-1: outside an open lattice, -2: no such record)
+    // this thread stages halo records tid, tid + 256, .. of every plane:
+    // their in-plane offsets (-1: outside an open lattice, -2: no such record)
     auto halo = [&](int e) {
-        if (e >= LHN) return -2;
+        if (e >= HN) return -2;
         int gx = x0 - 1 + e % LHX, gy = y0 - 1 + e / LHX;
         bool in = true;
         if (P.per0)
@@ -276,17 +320,19 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             in = in && gy >= 0 && gy < P.ny;
         return in ? gy * P.nx + gx : -1;
     };
-    const int g0 = halo(tid), g1 = halo(tid + LT);
-    const unsigned sd0 = smem_addr(&tiles[0][tid]), sd1 = sd0 + 16u * LT;
+    int g[NSL];
+#pragma unroll
+    for (int k = 0; k < NSL; ++k) g[k] = halo(tid + k * LT);
+    const unsigned sd = smem_addr(tiles + tid);
     const unsigned qd = smem_addr(qt + kQRec * tid);
-    constexpr unsigned kSlot = 16u * LHN, kQSlot = kQRec * LT;
+    constexpr unsigned kSlot = 16u * HN, kQSlot = kQRec * LT * R;
     float2 *const q2 = reinterpret_cast<float2 *>(q);  // (y, z) of q, packed layout
 #pragma unroll
-    for (int b = 0; b < LNB; ++b) {
-        if (g0 == -1) st_zero(sd0 + b * kSlot);
-        if (g1 == -1) st_zero(sd1 + b * kSlot);
-    }
-    const int col = (y0 + ty) * P.nx + x0 + tx;
+    for (int b = 0; b < LNB; ++b)
+#pragma unroll
+        for (int k = 0; k < NSL; ++k)
+            if (g[k] == -1) st_zero(sd + b * kSlot + k * 16u * LT);
+    const int col = (y0 + R * ty) * P.nx + x0 + tx;  // row 0 of the thread's strip
     auto issue = [&](auto slot, int p) {
         constexpr unsigned S = decltype(slot)::value;
         if (p <= zb) {
@@ -300,21 +346,29 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             }
             if (zin) {
                 const float4 *base = src + (size_t)pz * plane;
-                if (g0 >= 0) cp16(sd0 + S * kSlot, base + g0);
-                if (g1 >= 0) cp16(sd1 + S * kSlot, base + g1);
+#pragma unroll
+                for (int k = 0; k < NSL; ++k)
+                    if (g[k] >= 0) cp16(sd + S * kSlot + k * 16u * LT, base + g[k]);
             } else {
-                if (g0 != -2) st_zero(sd0 + S * kSlot);
-                if (g1 != -2) st_zero(sd1 + S * kSlot);
+#pragma unroll
+                for (int k = 0; k < NSL; ++k)
+                    if (g[k] != -2) st_zero(sd + S * kSlot + k * 16u * LT);
             }
             if (PASS == 1 && p - 1 >= za && p - 1 < zb) {
-                if (SPGB_LEAN_PACKQ)
-                    cp8(qd + S * kQSlot, q2 + (size_t)(p - 1) * plane + col);
-                else
-                    cp16(qd + S * kQSlot, q + (size_t)(p - 1) * plane + col);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const unsigned qs = qd + S * kQSlot + j * kQRec * LT;
+                    const size_t qi = (size_t)(p - 1) * plane + col + j * P.nx;
+                    if (SPGB_LEAN_PACKQ)
+                        cp8(qs, q2 + qi);
+                    else
+                        cp16(qs, q + qi);
+                }
             }
         }
     };
-    const unsigned tc = smem_addr(&tiles[0][(ty + 1) * LHX + tx + 1]);  // the thread's centre record in slot 0
+    // the thread's row-0 centre record in slot 0
+    const unsigned tc = smem_addr(tiles + (R * ty + 1) * LHX + tx + 1);
     // planes za-1, za (slots 0, 1), then za+1 .. za+LK (slots 2 .. LK+1) in flight
     issue(I_<0>{}, za - 1);
     issue(I_<1>{}, za);
@@ -324,12 +378,21 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     commit();
     wait_groups<1>();
     __syncthreads();
-    const Sum below = summarise<DM, 0>(P, L, tc);
-    const Sum cur = summarise<DM, 1>(P, L, tc);
-    // the open accumulator of the plane being finished, its w and centre
-    pv acc = add_onsite(P, add_zdmi<DM>(P, cur.e + below.w, below.c, -1.f), cur.c);
-    pv wcur = cur.w, ccur = cur.c;
-    float qx = cur.cw;  // x of q of the plane being finished (packed layout, corrector)
+    pv acc[R], wcur[R], ccur[R];
+    float qx[R];  // x of q of the plane being finished (packed layout, corrector)
+    {
+        Sum below[R], cur[R];
+        summarise<DM, R, 0, HN>(P, L, tc, below);
+        summarise<DM, R, 1, HN>(P, L, tc, cur);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            // the open accumulator of the plane being finished, its w and centre
+            acc[j] = add_onsite(P, add_zdmi<DM>(P, cur[j].e + below[j].w, below[j].c, -1.f), cur[j].c);
+            wcur[j] = cur[j].w;
+            ccur[j] = cur[j].c;
+            qx[j] = cur[j].cw;
+        }
+    }
     int i = za * plane + col;
     const float al = c.alpha, dt = c.dt, hdt = 0.5f * c.dt;
     // finish the next plane z, whose upper neighbour z+1 sits in ring slot
@@ -337,45 +400,50 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     // A(z+1) = e(z+1) + w(z) - c(z) x D_{+z} + onsite(c(z+1)).
     auto finish = [&](auto sn) {
         constexpr int SN = decltype(sn)::value;
-        v3<float> qi;
-        if (PASS == 1) {
-            if (SPGB_LEAN_PACKQ) {
-                const float2 yz = lds2(qd + SN * kQSlot);
-                qi = mk(qx, yz.x, yz.y);
-            } else {
-                qi = v3of(pvof(ld4<SN * int(kQSlot)>(qd)));
+        Sum up[R];
+        summarise<DM, R, SN, HN>(P, L, tc, up);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int ij = i + j * P.nx;
+            v3<float> qi;
+            if (PASS == 1) {
+                if (SPGB_LEAN_PACKQ) {
+                    const float2 yz = lds2(qd + SN * kQSlot + j * kQRec * LT);
+                    qi = mk(qx[j], yz.x, yz.y);
+                } else {
+                    qi = v3of(pvof(ld4<0>(qd + SN * kQSlot + j * kQRec * LT)));
+                }
             }
-        }
-        const Sum up = summarise<DM, SN>(P, L, tc);
-        const pv Bp = add_zdmi<DM>(P, acc + up.w, up.c, 1.f);
-        acc = add_onsite(P, add_zdmi<DM>(P, up.e + wcur, ccur, -1.f), up.c);
-        const v3<float> n = v3of(ccur), B = v3of(Bp);
-        wcur = up.w;
-        ccur = up.c;
-        qx = up.cw;
-        if (PASS == 0) {
-            v3<float> Bth = mk(0.f, 0.f, 0.f);
-            if (TH) Bth = thermal(thermal_bits_at(c, c.step, (uint32_t)i, 0u), c.sig[0]);
-            const v3<float> A = lA(al, n, B + Bth);
-            const v3<float> f = cross(n, A);
-            const v3<float> p = unit(axpy(dt, f, n));
-            const v3<float> qv = TH ? axpy(hdt, f + cross(p, lA(al, p, Bth)), n) : axpy(hdt, f, n);
-            if (SPGB_LEAN_PACKQ) {
-                np[i] = make_float4(p.x, p.y, p.z, qv.x);
-                q2[i] = make_float2(qv.y, qv.z);
+            const pv Bp = add_zdmi<DM>(P, acc[j] + up[j].w, up[j].c, 1.f);
+            acc[j] = add_onsite(P, add_zdmi<DM>(P, up[j].e + wcur[j], ccur[j], -1.f), up[j].c);
+            const v3<float> n = v3of(ccur[j]), B = v3of(Bp);
+            wcur[j] = up[j].w;
+            ccur[j] = up[j].c;
+            qx[j] = up[j].cw;
+            if (PASS == 0) {
+                v3<float> Bth = mk(0.f, 0.f, 0.f);
+                if (TH) Bth = thermal(thermal_bits_at(c, c.step, (uint32_t)ij, 0u), c.sig[0]);
+                const v3<float> A = lA(al, n, B + Bth);
+                const v3<float> f = cross(n, A);
+                const v3<float> p = unit(axpy(dt, f, n));
+                const v3<float> qv = TH ? axpy(hdt, f + cross(p, lA(al, p, Bth)), n) : axpy(hdt, f, n);
+                if (SPGB_LEAN_PACKQ) {
+                    np[ij] = make_float4(p.x, p.y, p.z, qv.x);
+                    q2[ij] = make_float2(qv.y, qv.z);
+                } else {
+                    st(q, ij, qv);
+                    st(np, ij, p);
+                }
             } else {
-                st(q, i, qv);
-                st(np, i, p);
+                const v3<float> Ap = lA(al, n, B);
+                st(nout, ij, unit(axpy(hdt, cross(n, Ap), qi)));
             }
-        } else {
-            const v3<float> Ap = lA(al, n, B);
-            st(nout, i, unit(axpy(hdt, cross(n, Ap), qi)));
         }
         i += plane;
     };
     // (a second copy of the loop for the segment's interior, without the
-    // range tests of `load`, was measured: it costs the predictor spills at 64
-    // registers and gains the corrector nothing at 80)
+    // range tests of `issue`, was measured: it costs the predictor spills at
+    // 64 registers and gains the corrector nothing at 80)
     // planes z .. z+LK-1: planes z+1 .. z+LK have landed in slots BASE ..
     // BASE+LK-1 (mod 2 LK); the other half of the ring, read before the
     // barrier, takes planes z+LK+1 .. z+2LK
@@ -400,22 +468,28 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
     __syncthreads();  // the next segment reuses the ring
 }
 
-// Work: the (32 x 8 column tile, plane) units in tile-major order, CTA b
+// resident CTAs per SM each pass and column count is compiled for
+template <int PASS, int R> struct LeanMinB {
+    static constexpr int value = R == 1 ? (PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MINB_CORR)
+                                        : (PASS == 0 ? SPGB_LEAN_MINB2 : SPGB_LEAN_MINB2_CORR);
+};
+
+// Work: the (32 x 8R column tile, plane) units in tile-major order, CTA b
 // takes units [b per, (b + 1) per) as runs of planes, one segment each.
-template <int PASS, int DM, bool TH>
-__global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MINB_CORR)
+template <int PASS, int DM, bool TH, int R>
+__global__ void __launch_bounds__(LT, (LeanMinB<PASS, R>::value))
     k_lean(const __grid_constant__ CubicParams<float> P, const float4 *__restrict__ src, float4 *__restrict__ np,
            float4 *__restrict__ q, float4 *__restrict__ nout, const __grid_constant__ LlgConst<float> c,
            const __grid_constant__ LeanConst L, int per)
 {
-    __shared__ __align__(16) float4 tiles[LNB][LHN];
-    __shared__ __align__(16) unsigned char qt[PASS == 1 ? LNB * LT * kQRec : 16];
+    __shared__ __align__(16) float4 tiles[LNB * LTile<R>::HN];
+    __shared__ __align__(16) unsigned char qt[PASS == 1 ? LNB * LT * R * kQRec : 16];
     allow_dependents();
     wait_prerequisite();  // the previous pass wrote what this one reads
-    // units: (tile, plane) pairs, fewer than 2^31 (N < 2^31 spins, 256 per
+    // units: (tile, plane) pairs, fewer than 2^31 (N < 2^31 spins, 256 R per
     // tile and plane); one division per CTA, then the runs advance tile by tile
     const int tiles_x = P.nx / LX;
-    const int total = tiles_x * (P.ny / LY) * P.nz;
+    const int total = tiles_x * (P.ny / (LY * R)) * P.nz;
     int u = blockIdx.x * per;
     const int u1 = min(u + per, total);
     if (u >= u1) return;
@@ -424,7 +498,7 @@ __global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MIN
     int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     while (u < u1) {
         const int zb = min(P.nz, za + (u1 - u));
-        lean_segment<PASS, DM, TH>(P, L, c, src, np, q, nout, tiles, qt, tx * LX, ty * LY, za, zb);
+        lean_segment<PASS, DM, TH, R>(P, L, c, src, np, q, nout, tiles, qt, tx * LX, ty * LY * R, za, zb);
         u += zb - za;
         za = 0;
         if (++tx == tiles_x) {
@@ -434,7 +508,7 @@ __global__ void __launch_bounds__(LT, PASS == 0 ? SPGB_LEAN_MINB : SPGB_LEAN_MIN
     }
 }
 
-template <int PASS, int DM>
+template <int PASS, int DM, int R>
 cudaError_t lean_launch(int grid, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q, float4 *nout,
                         const LlgConst<float> &c, int per, cudaStream_t st)
 {
@@ -442,27 +516,31 @@ cudaError_t lean_launch(int grid, const CubicParams<float> &P, const float4 *src
                       make_float2(-1.f, -1.f)};
     if constexpr (PASS == 0)
         if (c.thermal)
-            return launch_pdl(k_lean<PASS, DM, true>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
-    return launch_pdl(k_lean<PASS, DM, false>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
+            return launch_pdl(k_lean<PASS, DM, true, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
+    return launch_pdl(k_lean<PASS, DM, false, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
 }
 
-template <int PASS>
+template <int PASS, int R>
 cudaError_t lean_dm(int grid, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q, float4 *nout,
                     const LlgConst<float> &c, int per, cudaStream_t st)
 {
-    if (P.dmi_mode == 0) return lean_launch<PASS, 0>(grid, P, src, np, q, nout, c, per, st);
-    if (P.dmi_mode == 1) return lean_launch<PASS, 1>(grid, P, src, np, q, nout, c, per, st);
-    return lean_launch<PASS, 2>(grid, P, src, np, q, nout, c, per, st);
+    if (P.dmi_mode == 0) return lean_launch<PASS, 0, R>(grid, P, src, np, q, nout, c, per, st);
+    if (P.dmi_mode == 1) return lean_launch<PASS, 1, R>(grid, P, src, np, q, nout, c, per, st);
+    return lean_launch<PASS, 2, R>(grid, P, src, np, q, nout, c, per, st);
 }
 
 }  // namespace
 
-bool cubic_lean_fits(int nx, int ny) { return nx > 0 && ny > 0 && nx % LX == 0 && ny % LY == 0; }
+bool cubic_lean_fits(int nx, int ny, int rows)
+{
+    return nx > 0 && ny > 0 && nx % LX == 0 && ny % (LY * (rows == 2 ? 2 : 1)) == 0;
+}
 
 cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float4 *src, float4 *np, float4 *q,
-                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st)
+                              float4 *nout, const LlgConst<float> &c, int per, cudaStream_t st, int rows)
 {
-    const long total = (long)(P.nx / LX) * (P.ny / LY) * P.nz;
+    const int R = rows == 2 ? 2 : 1;
+    const long total = (long)(P.nx / LX) * (P.ny / (LY * R)) * P.nz;
     if (total == 0) return cudaSuccess;
     if (per < 1) per = 1;
     const int grid = (int)((total + per - 1) / per);
@@ -482,15 +560,23 @@ cudaError_t launch_cubic_lean(int pass, const CubicParams<float> &P, const float
     Ps.K *= s;
     LlgConst<float> cs = c;
     cs.sig[0] *= s;
-    return pass == 0 ? lean_dm<0>(grid, Ps, src, np, q, nout, cs, per, st)
-                     : lean_dm<1>(grid, Ps, src, np, q, nout, cs, per, st);
+    if (R == 2)
+        return pass == 0 ? lean_dm<0, 2>(grid, Ps, src, np, q, nout, cs, per, st)
+                         : lean_dm<1, 2>(grid, Ps, src, np, q, nout, cs, per, st);
+    return pass == 0 ? lean_dm<0, 1>(grid, Ps, src, np, q, nout, cs, per, st)
+                     : lean_dm<1, 1>(grid, Ps, src, np, q, nout, cs, per, st);
 }
 
-int cubic_lean_resident_ctas(int pass)
+int cubic_lean_resident_ctas(int pass, int rows)
 {
     int n = 0;
-    cudaError_t e = pass == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<0, 1, true>, LT, 0)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<1, 1, false>, LT, 0);
+    cudaError_t e;
+    if (rows == 2)
+        e = pass == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<0, 1, true, 2>, LT, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<1, 1, false, 2>, LT, 0);
+    else
+        e = pass == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<0, 1, true, 1>, LT, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lean<1, 1, false, 1>, LT, 0);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 

@@ -11,7 +11,8 @@ passes with a smaller instruction budget per spin, so the checks are:
   * five steps against the general passes of the same context type, to a
     bound of FP32 rounding differences (2e-6);
   * bit-identical results under every split of the (tile, plane) units
-    between CTAs (the per-spin arithmetic does not depend on it).
+    between CTAs, and with one or two columns per thread (32 x 8 or 32 x 16
+    tiles): the per-spin arithmetic depends on neither.
 """
 import numpy as np
 import pytest
@@ -72,9 +73,12 @@ def test_lean_option_reports_when_the_passes_are_taken():
     c = _ctx(I.simple_cubic(33, 16, 4), SC, 1)
     assert c.get_option("cubic_lean") == 0
     assert B.Context(I.simple_cubic(32, 16, 4), SC, "f64").get_option("cubic_lean") == 0
-    c = _ctx(I.simple_cubic(32, 16, 4), SC, 1)
+    c = _ctx(I.simple_cubic(32, 8, 4), SC, 1)  # 8 rows: no whole 32 x 16 tiles
     c.set_option("cubic_rows", 2)
     assert c.get_option("cubic_lean") == 0
+    c = _ctx(I.simple_cubic(32, 16, 4), SC, 1)
+    c.set_option("cubic_rows", 2)
+    assert c.get_option("cubic_lean") == 1
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -107,12 +111,35 @@ def test_lean_steps_match_the_general_passes(name):
     assert (out[0] - out[1]).abs().max().item() <= 2e-6
 
 
+@pytest.mark.parametrize("name", [k for k, (g, h) in CASES.items() if g["n_cells"][1] % 16 == 0])
+@pytest.mark.parametrize("T", [0.0, 10.0])
+def test_lean_two_columns_per_thread_give_the_same_bits(name, T):
+    # two adjacent columns per thread (32 x 16 tiles) share the rows they
+    # read; the per-spin arithmetic is that of one column per thread
+    g, h = CASES[name]
+    n0 = I.random_spins(int(np.prod(g["n_cells"])), 12)
+    kw = dict(solver="heun", dt=2e-3, alpha=0.2, T=T, seed=4, step0=7)
+    out = []
+    for rows in ((1, 1), (2, 2), (2, 1), (1, 2)):
+        c = _ctx(g, h, 1)
+        c.set_option("cubic_rows", rows[0])
+        c.set_option("cubic_rows_corr", rows[1])
+        assert c.get_option("cubic_lean") == 1
+        n = c.spins(n0)
+        c.llg_step(n, 4, **kw)
+        out.append(n)
+    for n in out[1:]:
+        assert torch.equal(n, out[0])
+
+
 @pytest.mark.parametrize("zc,zcc", [(1, 0), (2, 1), (5, 3), (7, 0), (40, 2), (1000, 11)])
-def test_lean_plane_chunking_is_exact(zc, zcc):
+@pytest.mark.parametrize("rows", [1, 2])
+def test_lean_plane_chunking_is_exact(zc, zcc, rows):
     g, h = I.simple_cubic(64, 16, 23), dict(SC, B=[0.2, 0, 0.5])
     n0 = I.random_spins(int(np.prod(g["n_cells"])), 2)
     kw = dict(solver="heun", dt=1e-3, alpha=0.1, T=10.0, seed=3)
     c = _ctx(g, h, 1)
+    c.set_option("cubic_rows", rows)
     a = c.spins(n0)
     c.llg_step(a, 3, **kw)
     c.set_option("planes_per_cta", zc)
