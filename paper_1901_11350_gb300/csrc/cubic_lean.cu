@@ -21,7 +21,10 @@
 //   * the thermal field is a template switch, and the multi-function-unit
 //     operations (log2, reciprocal square root, sine, cosine) are the
 //     flush-to-zero forms, which give the same values on the normal
-//     arguments they receive here.
+//     arguments they receive here;
+//   * the parts of Philox rounds 0 and 1 that do not depend on the site are
+//     computed once per launch on the host (the same bits: 18 of the 20
+//     32 x 32 -> 64 multiplications remain per site).
 #include <type_traits>
 
 #include "internal.h"
@@ -161,6 +164,47 @@ __device__ __forceinline__ v3<float> unit(v3<float> a) { return rsqf(dot(a, a)) 
 // c B and no per-spin scaling is left)
 __device__ __forceinline__ v3<float> lA(float al, v3<float> n, v3<float> B) { return axpy(al, cross(n, B), B); }
 
+// Philox4x32-10 of the counter (i, step, replica 8) for the sites of one
+// launch.  Only the site index i differs between threads: half of round 0
+// (the product of the counter's third word) and half of round 1 (the product
+// of round 0's first output word) are the same for every site and are
+// computed once on the host; the rest is the published round function.
+struct LeanRng {
+    uint32_t wk;      // replica 8 ^ k1                 (round 0, third output word)
+    uint32_t yk;      // lo(M1 step_hi) ^ k0'           (round 1, first output word)
+    uint32_t hk;      // hi(M0 x1) ^ k1'                (round 1, third output word)
+    uint32_t l1;      // lo(M0 x1)                      (round 1, fourth output word)
+    uint32_t rk[16];  // round keys of rounds 2 .. 9
+};
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+__device__ __forceinline__ uint4 lean_bits(const LeanRng &G, uint32_t i)
+{
+    const uint32_t z1 = __umulhi(kPhiloxM0, i) ^ G.wk, w1 = kPhiloxM0 * i;
+    uint4 c = make_uint4(__umulhi(kPhiloxM1, z1) ^ G.yk, kPhiloxM1 * z1, w1 ^ G.hk, G.l1);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ G.rk[2 * r], lo1, hi0 ^ c.w ^ G.rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+// the launch-uniform words of rounds 0 and 1 for the counter's step and
+// replica (x1 = round 0's first output word)
+LeanRng lean_rng(const LlgConst<float> &c)
+{
+    auto hi = [](uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); };
+    const uint32_t slo = (uint32_t)c.step, shi = (uint32_t)(c.step >> 32);
+    const uint32_t x1 = hi(kPhiloxM1, shi) ^ slo ^ c.rk[0], y1 = kPhiloxM1 * shi;
+    LeanRng G;
+    G.wk = (c.replica * 8u) ^ c.rk[1];
+    G.yk = y1 ^ c.rk[2];
+    G.hk = hi(kPhiloxM0, x1) ^ c.rk[3];
+    G.l1 = kPhiloxM0 * x1;
+    for (int k = 0; k < 16; ++k) G.rk[k] = c.rk[4 + k];
+    return G;
+}
+
 // Three standard normals from one Philox block by Box-Muller, scaled by the
 // noise amplitude s: (u0, u1) -> eta_x, eta_y and (u2, u3) -> eta_z with
 // u = (x + 1/2) 2^-32; sin and cos of 2 pi u are taken as -sin and -cos of
@@ -298,8 +342,8 @@ template <int R> struct LTile {
 template <int PASS, int DM, bool TH, int R>
 __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const LeanConst &L, const LlgConst<float> &c,
                                              const float4 *__restrict__ src, float4 *__restrict__ np,
-                                             float4 *__restrict__ q, float4 *__restrict__ nout, float4 *tiles,
-                                             unsigned char *qt, int x0, int y0, int za, int zb)
+                                             float4 *__restrict__ q, float4 *__restrict__ nout, const LeanRng &G,
+                                             float4 *tiles, unsigned char *qt, int x0, int y0, int za, int zb)
 {
     constexpr int HN = LTile<R>::HN, NSL = LTile<R>::NSL;
     const int tid = threadIdx.x, tx = tid & (LX - 1), ty = tid / LX;
@@ -422,7 +466,7 @@ __device__ __forceinline__ void lean_segment(const CubicParams<float> &P, const 
             qx[j] = up[j].cw;
             if (PASS == 0) {
                 v3<float> Bth = mk(0.f, 0.f, 0.f);
-                if (TH) Bth = thermal(thermal_bits_at(c, c.step, (uint32_t)ij, 0u), c.sig[0]);
+                if (TH) Bth = thermal(lean_bits(G, (uint32_t)ij), c.sig[0]);
                 const v3<float> A = lA(al, n, B + Bth);
                 const v3<float> f = cross(n, A);
                 const v3<float> p = unit(axpy(dt, f, n));
@@ -480,7 +524,7 @@ template <int PASS, int DM, bool TH, int R>
 __global__ void __launch_bounds__(LT, (LeanMinB<PASS, R>::value))
     k_lean(const __grid_constant__ CubicParams<float> P, const float4 *__restrict__ src, float4 *__restrict__ np,
            float4 *__restrict__ q, float4 *__restrict__ nout, const __grid_constant__ LlgConst<float> c,
-           const __grid_constant__ LeanConst L, int per)
+           const __grid_constant__ LeanConst L, const __grid_constant__ LeanRng G, int per)
 {
     __shared__ __align__(16) float4 tiles[LNB * LTile<R>::HN];
     __shared__ __align__(16) unsigned char qt[PASS == 1 ? LNB * LT * R * kQRec : 16];
@@ -498,7 +542,7 @@ __global__ void __launch_bounds__(LT, (LeanMinB<PASS, R>::value))
     int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     while (u < u1) {
         const int zb = min(P.nz, za + (u1 - u));
-        lean_segment<PASS, DM, TH, R>(P, L, c, src, np, q, nout, tiles, qt, tx * LX, ty * LY * R, za, zb);
+        lean_segment<PASS, DM, TH, R>(P, L, c, src, np, q, nout, G, tiles, qt, tx * LX, ty * LY * R, za, zb);
         u += zb - za;
         za = 0;
         if (++tx == tiles_x) {
@@ -514,10 +558,12 @@ cudaError_t lean_launch(int grid, const CubicParams<float> &P, const float4 *src
 {
     const LeanConst L{make_float2(P.J1, P.J1), make_float2(P.J2, P.J2), make_float2(P.J3, P.J3),
                       make_float2(-1.f, -1.f)};
+    const LeanRng G = lean_rng(c);
     if constexpr (PASS == 0)
         if (c.thermal)
-            return launch_pdl(k_lean<PASS, DM, true, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
-    return launch_pdl(k_lean<PASS, DM, false, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, per);
+            return launch_pdl(k_lean<PASS, DM, true, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, G,
+                              per);
+    return launch_pdl(k_lean<PASS, DM, false, R>, dim3(grid), dim3(LT), 0, st, P, src, np, q, nout, c, L, G, per);
 }
 
 template <int PASS, int R>
