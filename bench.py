@@ -984,11 +984,11 @@ def unet_layer_times(batch, reps=20):
         dz, w = rnd(batch, L, L, co), rnd(co, 9, c0 + c1) * 0.05
         flops = 2.0 * batch * L * L * co * 9 * (c0 + c1)
         row = {"L": L, "cin": c0 + c1, "cout": co, "upsampled": bool(up)}
-        for k in ("mma", "tcgen05", "tcgen05_ws"):
+        for k in ("mma", "tcgen05", "tcgen05_ws", "tcgen05_halo"):
             UN.set_conv_kernel(k)
             ms = timed(lambda: UN.conv3x3_forward(s0, w, None, src1=s1, up0=bool(up)))
             row["forward_" + k] = {"ms": ms, "tflops": flops / ms / 1e9}
-            if k != "tcgen05_ws":  # kernel 2 shares the weight gradient of kernel 1
+            if k in ("mma", "tcgen05"):  # kernels 2 and 3 share the weight gradient of kernel 1
                 ms = timed(lambda: UN.conv3x3_wgrad(s0, dz, src1=s1, up0=bool(up)))
                 row["wgrad_" + k] = {"ms": ms, "tflops": flops / ms / 1e9}
             UN.check_device_error()
@@ -1010,6 +1010,8 @@ def run_unet(args):
 
     torch.cuda.set_device(0)
     build.build()
+    if args.conv_kernel:
+        UN.set_conv_kernel(args.conv_kernel)
     L, bm = 128, 64
     net = UN.UNet(L, bm, I.unet_init(0))
     draws = [I.warmstart_draw(I.WARMSTART_SEEDS["heldout"], 100000 + i, L) for i in range(bm)]
@@ -1180,6 +1182,8 @@ def main():
     ap.add_argument("--gneb-persistent", type=int, default=-1, choices=[-1, 0, 1],
                     help="gneb48: 1 = one persistent cooperative launch per call, 0 = one launch per pass, "
                          "-1 (default) = chosen by the autotuner")
+    ap.add_argument("--conv-kernel", default="", choices=["", "mma", "tcgen05", "tcgen05_ws", "tcgen05_halo"],
+                    help="unet: convolution kernel of the timed steps (default: the library's)")
     ap.add_argument("--unet-layers", action="store_true",
                     help="unet: add per-shape forward and weight-gradient times of every convolution kernel")
     ap.add_argument("--side", type=int, default=128, help="lattice side (profiling aid; the workload is 128)")

@@ -116,10 +116,14 @@ int sp_conv3x3_forward(const uint16_t *src0, int C0, int up0, const uint16_t *sr
 int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, void *stream);
 
 /* Which kernel computes the 3x3 convolutions (forward and data gradient) of
- * this process: 1 (default) = tcgen05 MMAs with tensor-memory accumulators,
- * 2 = the same with warp-specialised loads and MMA issue (mbarrier
- * pipeline), 0 = the mma.sync kernel.  SP_ERR_ARG for other values.  Not
- * thread-safe: set it before launching work. */
+ * this process: 3 (default) = tcgen05 on halo tiles for image rows of at
+ * least 64 pixels (a CTA stages the input of a band of whole rows once per
+ * 32-channel chunk and takes the nine taps as offsets into it) and kernel 1
+ * for shorter rows or where the band does not fit; 1 = tcgen05 MMAs with
+ * tensor-memory accumulators on a four-stage pipeline of one tap x 32
+ * channels; 2 = the same with warp-specialised loads and MMA issue
+ * (mbarrier pipeline); 0 = the mma.sync kernel.  SP_ERR_ARG for other
+ * values.  Not thread-safe: set it before launching work. */
 int sp_conv3x3_set_kernel(int tcgen05);
 int sp_conv3x3_get_kernel(void);
 
@@ -145,7 +149,7 @@ long long sp_conv3x3_wgrad_workspace(int B, int H, int Wd, int Cin, int Cout);
 /* Weight gradient dW[co][t][ci] = sum_p dz[p][co] * in_t[p][ci] (FP32) and,
  * if db is not NULL, db[co] = sum_p dz[p][co], with the input read as in
  * sp_conv3x3_forward.  Deterministic (fixed summation order).  With the
- * convolution kernel set to 1 or 2 (sp_conv3x3_set_kernel) the products run
+ * convolution kernel set to 1, 2 or 3 (sp_conv3x3_set_kernel) the products run
  * on tcgen05 MMAs (M = 128 tap-channel rows, N = output channels, K = the
  * pixels of one split, FP32 accumulators in tensor memory, splits added in a
  * fixed order; its pipeline waits obey sp_conv3x3_set_wait_limit); with 0

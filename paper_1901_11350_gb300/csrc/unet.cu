@@ -613,6 +613,186 @@ __global__ void __launch_bounds__(kThreads) k_conv_ws(ConvSrc S, const bf16 *__r
     if (failed && tid == 0) atomicExch(&g_tc_error, 1);
 }
 
+// ------------------------------------------------------------------ conv, tcgen05, halo tiles
+// The same convolution with the input of a band of whole image rows loaded
+// once per chunk of 32 input channels.  A CTA computes R rows of one image
+// for BN output channels.  Per chunk it stages the band's halo tile -- R + 2
+// rows of W + 2 pixels, the periodic wrap, the upsampling and the channel
+// concatenation resolved through a per-CTA pixel table -- in the no-swizzle
+// K-major layout (four planes of 8 channels, 16 bytes per pixel, pixels
+// consecutive) and the chunk's weights of all nine taps.  Outputs are
+// numbered in "slots" with the tile's row pitch W + 2, so that a tap is a
+// fixed pixel offset: the MMA of tap (dy, dx) over slots [s, s + 128) reads
+// A from tile pixel s + (1 + dy)(W + 2) + 1 + dx -- a 16-byte aligned start
+// address -- and the nine taps re-read nothing from memory.  Slots in the two
+// halo columns, and past the band, compute values that are not stored.  The
+// accumulators of all slots (MT tiles of 128 slots x BN columns) stay in
+// tensor memory across the chunks.  One stage: the chunk's copies, a CTA
+// barrier, the MMAs (one thread issues and commits them), and the next
+// chunk's copies wait for that commit; two CTAs per SM overlap one's copies
+// with the other's MMAs.  Waits are bounded as in k_conv_tc.
+struct HaloGeom {
+    int R, Wp, npix, slots, MT, apix;
+    unsigned a_bytes, b_bytes, tbl_bytes, smem, tcols;
+};
+
+constexpr unsigned kHaloSmemMax = 113 * 1024;  // two CTAs per SM
+constexpr unsigned kHaloTmemMax = 256;         // tensor-memory columns per CTA (two per SM)
+
+__host__ __device__ inline HaloGeom halo_geom(int R, int W, int BN)
+{
+    HaloGeom g;
+    g.R = R;
+    g.Wp = W + 2;
+    g.npix = (R + 2) * g.Wp;
+    g.slots = R * g.Wp;
+    g.MT = (g.slots + kBM - 1) / kBM;
+    g.apix = g.MT * kBM + 2 * g.Wp + 2;  // the last tile's reads of tap (+1, +1) stay inside
+    g.a_bytes = 64u * g.apix;
+    g.b_bytes = 9u * 64u * BN;
+    g.tbl_bytes = 8u * g.npix;
+    g.smem = 128 + g.a_bytes + g.b_bytes + g.tbl_bytes + 16;
+    unsigned cols = 32;
+    while (cols < (unsigned)(g.MT * BN)) cols *= 2;
+    g.tcols = cols;
+    return g;
+}
+
+__device__ __forceinline__ uint64_t desc_ns(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    // start >> 4 | leading byte offset (between core matrices along K) |
+    // stride byte offset (between 8-row groups) | descriptor version 1 |
+    // no swizzle
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv_halo(ConvSrc S, const bf16 *__restrict__ Wk,
+                                                        const float *__restrict__ bias, int relu,
+                                                        const bf16 *__restrict__ mask, int H, int W, int Cout, int R,
+                                                        bf16 *__restrict__ out)
+{
+    constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
+                               ((unsigned)(kBM >> 4) << 24);
+    const HaloGeom G = halo_geom(R, W, BN);
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = smem_u32(smem_raw);
+    const unsigned base = (raw + 127u) & ~127u;
+    const unsigned sa = base, sb = base + G.a_bytes;
+    int *tbl = reinterpret_cast<int *>(smem_raw + (sb + G.b_bytes - raw));  // [2][npix]
+    const unsigned bar = sb + G.b_bytes + G.tbl_bytes, slot = bar + 8;
+    volatile unsigned *slot_ptr = reinterpret_cast<volatile unsigned *>(smem_raw + (slot - raw));
+
+    const int Cin = S.C0 + S.C1, nch = Cin / kBK;
+    const int bands = H / R, b = blockIdx.x / bands, y0 = (blockIdx.x - b * bands) * R;
+    const int n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long wait_limit = g_tc_wait_limit;
+    // pixel table: source pixel of every tile pixel in src0's grid and in the
+    // full-resolution grid
+    for (int hp = tid; hp < G.npix; hp += kThreads) {
+        const int hy = hp / G.Wp, hx = hp - hy * G.Wp;
+        const int y = wrap(y0 - 1 + hy, H), x = wrap(hx - 1, W);
+        const int full = (b * H + y) * W + x;
+        tbl[hp] = S.up0 ? (b * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1) : full;
+        tbl[G.npix + hp] = full;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(G.tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();  // also publishes the pixel table
+    tc_fence_after();
+    const unsigned tmem = *slot_ptr;
+    const unsigned lbo_a = 16u * G.apix, lbo_b = 16u * BN;
+
+    int failed = 0, issued = 0;
+    for (int c = 0; c < nch; ++c) {
+        // the MMAs of the previous chunk read the buffers this one refills
+        if (c > 0 && !mbar_wait(bar, (c - 1) & 1, wait_limit)) failed = 1;
+        if (__syncthreads_or(failed)) {
+            failed = 1;
+            break;
+        }
+        const int cc = c * kBK;
+        const bool first = cc < S.C0;
+        const bf16 *src = first ? S.s0 + cc : S.s1 + (cc - S.C0);
+        const int cs = first ? S.C0 : S.C1;
+        const int *tp = tbl + (first ? 0 : G.npix);
+        for (int e = tid; e < 4 * G.npix; e += kThreads) {
+            const int hp = e >> 2, g = e & 3;
+            cp16(sa + g * lbo_a + 16u * hp, src + (size_t)tp[hp] * cs + g * 8);
+        }
+        for (int e = tid; e < 36 * BN; e += kThreads) {
+            const int g = e & 3, nt = e >> 2, n = nt / 9, t = nt - n * 9;
+            cp16(sb + (unsigned)(t * 4 + g) * lbo_b + 16u * n, Wk + ((size_t)(n0 + n) * 9 + t) * Cin + cc + g * 8);
+        }
+        cp_commit();
+        cp_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int mt = 0; mt < G.MT; ++mt)
+                for (int t = 0; t < 9; ++t) {
+                    const unsigned a0 = sa + 16u * (unsigned)(mt * kBM + (t / 3) * G.Wp + t % 3);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        tc_mma(tmem + (unsigned)(mt * BN), desc_ns(a0 + kk * 2 * lbo_a, lbo_a, 128),
+                               desc_ns(sb + (unsigned)(t * 4 + kk * 2) * lbo_b, lbo_b, 128), IDESC,
+                               (c > 0 || t > 0 || kk > 0) ? 1u : 0u);
+                }
+            tc_commit(bar);
+        }
+        issued = c + 1;
+    }
+    // the last commit tracks every MMA issued before it
+    if (issued > 0 && !mbar_wait(bar, (issued - 1) & 1)) failed = 1;
+    failed = __syncthreads_or(failed) || issued < nch;
+    tc_fence_after();
+    const int q = warp & 3, half = warp >> 2;
+    for (int mt = 0; mt < G.MT; ++mt) {
+        const int s = mt * kBM + q * 32 + lane, y = s / G.Wp, x = s - y * G.Wp;
+        const bool valid = !failed && y < R && x < W;
+        const size_t pix = (size_t)(b * H + y0 + y) * W + x;
+#pragma unroll
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(mt * BN + c0), v);
+            if (!valid) continue;
+            const int co = n0 + c0;
+            const size_t o = pix * Cout + co;
+            __align__(16) bf16 mk[16];
+            if (mask) {
+                *reinterpret_cast<uint4 *>(mk) = *reinterpret_cast<const uint4 *>(mask + o);
+                *reinterpret_cast<uint4 *>(mk + 8) = *reinterpret_cast<const uint4 *>(mask + o + 8);
+            }
+            __align__(16) bf16 r[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                float xv = v[e] + (bias ? bias[co + e] : 0.f);
+                if (relu) xv = fmaxf(xv, 0.f);
+                if (mask && !(__bfloat162float(mk[e]) > 0.f)) xv = 0.f;
+                r[e] = __float2bfloat16(xv);
+            }
+            *reinterpret_cast<uint4 *>(out + o) = *reinterpret_cast<const uint4 *>(r);
+            *reinterpret_cast<uint4 *>(out + o + 8) = *reinterpret_cast<const uint4 *>(r + 8);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G.tcols) : "memory");
+    if (failed && tid == 0) atomicExch(&g_tc_error, 1);
+}
+
 // ------------------------------------------------------------------ wgrad
 // part[z][co][t][ci] = sum over pixels p of split z of dz[p][co] in[p+off(t)][ci].
 // Grid (Cout/BMC, 9 * Cin/32, splits), 128 threads as 2 x 2 warps of
@@ -1196,7 +1376,7 @@ bool conv_shape_ok(int C0, int C1, int up0, int B, int H, int W, int Cout)
     return P < (1LL << 31) - 256;
 }
 
-int g_use_tc = 1;  // 0: mma.sync, 1: tcgen05 (default), 2: tcgen05 warp-specialised
+int g_use_tc = 3;  // 0: mma.sync, 1: tcgen05, 2: tcgen05 warp-specialised, 3: tcgen05 halo tiles (default)
 
 template <int BN>
 cudaError_t conv_tc_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask,
@@ -1228,12 +1408,60 @@ cudaError_t conv_ws_launch(dim3 grid, const ConvSrc &S, const bf16 *W, const flo
     return cudaGetLastError();
 }
 
+// Kernel 3 takes the halo tiles for image rows of at least this many pixels
+// and kernel 1 below.  Measured at batch 64 (forward, ms, kernel 1 -> halo):
+// 128^2 32->32 0.109 -> 0.087, 96->32 0.245 -> 0.172, 64^2 64->64 0.065 ->
+// 0.059; 32^2 128->128 0.048 -> 0.077, 384->128 0.115 -> 0.182, 16^2
+// 256->256 0.046 -> 0.073: on short rows with many channel chunks the
+// halo kernel's single stage (copies, then MMAs) loses to kernel 1's
+// four-stage pipeline.
+constexpr int kHaloMinWidth = 64;
+
+// Rows per CTA of the halo-tile kernel: the most of 8, 4, 2, 1 that divide H
+// with the accumulators and the stage inside a two-per-SM share; 0 if none.
+int halo_rows(int H, int W, int BN)
+{
+    for (int R = 8; R >= 1; R /= 2) {
+        if (H % R) continue;
+        const HaloGeom g = halo_geom(R, W, BN);
+        if ((unsigned)(g.MT * BN) <= kHaloTmemMax && g.smem <= kHaloSmemMax) return R;
+    }
+    return 0;
+}
+
+template <int BN>
+cudaError_t conv_halo_launch(int R, const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask,
+                             int B, int H, int Wd, int Cout, bf16 *out, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv_halo<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHaloSmemMax);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const HaloGeom g = halo_geom(R, Wd, BN);
+    dim3 grid((unsigned)(B * (H / R)), (unsigned)(Cout / BN));
+    k_conv_halo<BN><<<grid, kThreads, g.smem, st>>>(S, W, bias, relu, mask, H, Wd, Cout, R, out);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int relu, const bf16 *mask, int B, int H,
                         int Wd, int Cout, bf16 *out, cudaStream_t st)
 {
     long long P = (long long)B * H * Wd;
     int bn = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
     dim3 grid((unsigned)(P / kBM), (unsigned)(Cout / bn));
+    if (g_use_tc == 3 && Wd >= kHaloMinWidth) {
+        const int R = halo_rows(H, Wd, bn);
+        if (R > 0) {
+            switch (bn) {
+            case 128: return conv_halo_launch<128>(R, S, W, bias, relu, mask, B, H, Wd, Cout, out, st);
+            case 64: return conv_halo_launch<64>(R, S, W, bias, relu, mask, B, H, Wd, Cout, out, st);
+            default: return conv_halo_launch<32>(R, S, W, bias, relu, mask, B, H, Wd, Cout, out, st);
+            }
+        }
+    }
     if (g_use_tc == 2) {
         switch (bn) {
         case 128: return conv_ws_launch<128>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
@@ -1241,7 +1469,7 @@ cudaError_t conv_launch(const ConvSrc &S, const bf16 *W, const float *bias, int 
         default: return conv_ws_launch<32>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
         }
     }
-    if (g_use_tc) {
+    if (g_use_tc) {  // 1, and 3 where the halo tiles do not fit
         switch (bn) {
         case 128: return conv_tc_launch<128>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
         case 64: return conv_tc_launch<64>(grid, S, W, bias, relu, mask, H, Wd, Cout, out, st);
@@ -1730,7 +1958,7 @@ int sp_conv3x3_transpose(const uint16_t *W, int Cout, int Cin, uint16_t *Wt, voi
 
 int sp_conv3x3_set_kernel(int tcgen05)
 {
-    if (tcgen05 < 0 || tcgen05 > 2) return SP_ERR_ARG;
+    if (tcgen05 < 0 || tcgen05 > 3) return SP_ERR_ARG;
     g_use_tc = tcgen05;
     return SP_OK;
 }

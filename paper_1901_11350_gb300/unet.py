@@ -23,15 +23,18 @@ def _check_cuda(t, dtype, name):
 
 
 def set_conv_kernel(name):
-    """'tcgen05' (tensor-memory accumulators), 'tcgen05_ws' (the same with
-    warp-specialised loads and MMA issue) or 'mma' (mma.sync)."""
-    rc = lib().sp_conv3x3_set_kernel({"mma": 0, "tcgen05": 1, "tcgen05_ws": 2}[name])
+    """'tcgen05_halo' (default: the input of a band of image rows staged once
+    per channel chunk, the nine taps as offsets into it, for rows of at least
+    64 pixels; 'tcgen05' below), 'tcgen05' (tensor-memory accumulators, a
+    four-stage pipeline of one tap x 32 channels), 'tcgen05_ws' (the same
+    with warp-specialised loads and MMA issue) or 'mma' (mma.sync)."""
+    rc = lib().sp_conv3x3_set_kernel({"mma": 0, "tcgen05": 1, "tcgen05_ws": 2, "tcgen05_halo": 3}[name])
     if rc:
         raise SpinError(rc, "bad kernel name")
 
 
 def conv_kernel():
-    return {0: "mma", 1: "tcgen05", 2: "tcgen05_ws"}[lib().sp_conv3x3_get_kernel()]
+    return {0: "mma", 1: "tcgen05", 2: "tcgen05_ws", 3: "tcgen05_halo"}[lib().sp_conv3x3_get_kernel()]
 
 
 def check_device_error():

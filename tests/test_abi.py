@@ -138,7 +138,7 @@ def test_unet_layout_and_host_side_rejections():
     assert L.sp_conv3x3_forward(None, 32, 0, None, 0, dummy, None, 1, None, 1, 16, 16, 32, dummy, None) == -1
     assert L.sp_conv3x3_wgrad(dummy, 32, 0, None, 0, dummy, 1, 16, 16, 32, dummy, None, dummy, 0, None) == -1
     assert L.sp_conv3x3_set_wait_limit(-1) == -1                  # a negative wait limit
-    assert L.sp_conv3x3_set_kernel(3) == -1 and L.sp_conv3x3_set_kernel(-1) == -1
+    assert L.sp_conv3x3_set_kernel(4) == -1 and L.sp_conv3x3_set_kernel(-1) == -1
 
 
 def test_option_round_trip_and_rejections():

@@ -40,7 +40,7 @@ def rand_bf(rng, shape, scale=1.0):
     return t, f64(t)
 
 
-@pytest.fixture(params=["mma", "tcgen05", "tcgen05_ws"])
+@pytest.fixture(params=["mma", "tcgen05", "tcgen05_ws", "tcgen05_halo"])
 def kernel(request):
     old = UN.conv_kernel()
     UN.set_conv_kernel(request.param)
@@ -62,6 +62,10 @@ CONV_CASES = [
     (8, 8, 8, 256, 1, 128, 128),
     (2, 16, 16, 32, 0, 0, 96),
     (2, 8, 24, 64, 0, 0, 192),
+    # rows of 64 and 128 pixels: the halo tiles of kernel 3
+    (1, 8, 64, 32, 0, 0, 32),
+    (1, 8, 64, 64, 1, 32, 64),
+    (1, 4, 128, 64, 1, 32, 32),
 ]
 
 
@@ -87,7 +91,7 @@ def test_conv_forward(case, relu, kernel):
     assert np.all(err <= tol), float(np.max(err - tol))
 
 
-@pytest.mark.parametrize("case", [(2, 16, 16, 96, 32), (2, 8, 8, 256, 256), (4, 16, 16, 32, 64)])
+@pytest.mark.parametrize("case", [(2, 16, 16, 96, 32), (2, 8, 8, 256, 256), (4, 16, 16, 32, 64), (1, 8, 64, 32, 64)])
 def test_conv_data_gradient(case, kernel):
     # the data gradient is the forward kernel with transposed weights and the
     # input's ReLU mask
@@ -279,3 +283,37 @@ def test_conv_pipeline_wait_that_runs_out_reports_and_leaves_the_device_usable()
     _, SW, _ = U.conv3x3_backward(np.abs(x0), np.zeros((Cout, 9, C0)), np.abs(dz))
     assert np.all(np.abs(dW.cpu().numpy() - rW) <= 2 * (16 * 32 * 32 + 1024) * 2.0 ** -24 * SW)
     UN.set_conv_kernel(old)
+
+
+
+def test_halo_conv_wait_that_runs_out_reports_and_leaves_the_device_usable():
+    """The halo-tile kernel waits for a chunk's MMAs before it refills the
+    chunk's buffers: with a wait limit of zero every CTA of a two-chunk
+    convolution gives up there, drains the MMAs it issued, frees its tensor
+    memory and writes nothing, and the device flag reports SP_ERR_TIMEOUT;
+    with the default limit restored the same call is correct."""
+    old = UN.conv_kernel()
+    UN.set_conv_kernel("tcgen05_halo")
+    UN.check_device_error()
+    B, H, W, C0, Cout = 2, 8, 64, 64, 64  # rows of 64 pixels, two chunks of 32 input channels
+    rng = np.random.default_rng(13)
+    s0, x0 = rand_bf(rng, (B, H, W, C0))
+    Wt, Wn = rand_bf(rng, (Cout, 9, C0), 1.0 / np.sqrt(9 * C0))
+    lib = UN.lib
+    try:
+        UN.set_wait_limit(0)
+        out = torch.full((B, H, W, Cout), 7.0, dtype=torch.bfloat16, device="cuda")
+        rc = lib().sp_conv3x3_forward(s0.data_ptr(), C0, 0, None, 0, Wt.data_ptr(), None, 0, None, B, H, W, Cout,
+                                      out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert rc == 0
+        assert lib().sp_unet_device_error() == -5  # SP_ERR_TIMEOUT
+        assert bool(torch.all(out == 7.0)), "a CTA whose wait ran out wrote outputs"
+    finally:
+        UN.set_wait_limit()
+    out = UN.conv3x3_forward(s0, Wt)
+    assert lib().sp_unet_device_error() == 0
+    UN.set_conv_kernel(old)
+    ref = U.conv3x3(x0, Wn, np.zeros(Cout))
+    S = U.conv3x3(np.abs(x0), np.abs(Wn), np.zeros(Cout))
+    tol = 2.0 ** -8 * np.abs(ref) + 2 * 9 * C0 * 2.0 ** -24 * S
+    assert np.all(np.abs(f64(out) - ref) <= tol)
