@@ -1079,29 +1079,71 @@ __global__ void __launch_bounds__(kThreads) k_wgrad_tc(ConvSrc S, const bf16 *__
 // out[i] = sum_{z < nz} part[z * n + i], in order of z.
 __global__ void k_sum_parts(const float *__restrict__ part, int nz, long long n, float *__restrict__ out)
 {
+    // four running sums over z = 4k + j (four loads in flight), added as
+    // (s0 + s1) + (s2 + s3): a fixed order
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < nz; ++z) s += part[(size_t)z * n + i];
-        out[i] = s;
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        int z = 0;
+        for (; z + 3 < nz; z += 4) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] += __ldg(part + (size_t)(z + j) * n + i);
+        }
+        for (int j = 0; z < nz; ++z, ++j) s[j] += __ldg(part + (size_t)z * n + i);
+        out[i] = (s[0] + s[1]) + (s[2] + s[3]);
     }
 }
 
-// part[blk][c] = sum over the block's pixels of dz[p][c]; C in {32,...,256}
-// dividing 256.
+// part[blk][c] = sum over the block's pixels of dz[p][c]; C a multiple of 32
+// (blockIdx.y takes channels in slices of 256).
 __global__ void __launch_bounds__(256) k_colsum(const bf16 *__restrict__ dz, int P, int C, int pix_per_blk,
                                                 float *__restrict__ part)
 {
-    __shared__ float sh[256];
-    int c = threadIdx.x % C, r = threadIdx.x / C, R = 256 / C;
-    int p0 = blockIdx.x * pix_per_blk, p1 = min(P, p0 + pix_per_blk);
-    float s = 0.f;
-    for (int p = p0 + r; p < p1; p += R) s += __bfloat162float(dz[(size_t)p * C + c]);
-    sh[threadIdx.x] = s;
+    // block (x, y): pixels [x pix_per_blk, (x + 1) pix_per_blk), channels
+    // [256 y, 256 y + Cs).  Each thread sums 8 channels (one 16-byte vector)
+    // of every G-th pixel of the run, four vectors in flight; the block's G
+    // partial sums of a channel are then added in a fixed order.
+    __shared__ float sh[256][8];
+    const int c0 = 256 * blockIdx.y, Cs = min(256, C - c0);
+    const int ng = Cs >> 3, G = 256 / ng;  // channel groups per pixel, pixels per pass
+    const int cg = threadIdx.x % ng, r = threadIdx.x / ng;
+    dz += c0;
+    const int p0 = blockIdx.x * pix_per_blk, p1 = min(P, p0 + pix_per_blk);
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool in = r < G;
+    int p = p0 + r;
+    for (; in && p + 3 * G < p1; p += 4 * G) {
+        uint4 u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[k] = __ldg(reinterpret_cast<const uint4 *>(dz + (size_t)(p + k * G) * C) + cg);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u[k]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h[e]);
+                a[2 * e] += f.x;
+                a[2 * e + 1] += f.y;
+            }
+        }
+    }
+    for (; in && p < p1; p += G) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(dz + (size_t)p * C) + cg);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(h[e]);
+            a[2 * e] += f.x;
+            a[2 * e + 1] += f.y;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sh[threadIdx.x][e] = a[e];
     __syncthreads();
-    if (threadIdx.x < C) {
-        float a = 0.f;
-        for (int k = 0; k < R; ++k) a += sh[k * C + threadIdx.x];
-        part[(size_t)blockIdx.x * C + threadIdx.x] = a;
+    if ((int)threadIdx.x < Cs) {
+        const int c = threadIdx.x;
+        float t = 0.f;
+        for (int k = 0; k < G; ++k) t += sh[k * ng + (c >> 3)][c & 7];
+        part[(size_t)blockIdx.x * C + c0 + c] = t;
     }
 }
 
@@ -1289,20 +1331,34 @@ __global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ a, const 
     for (int j = threadIdx.x; j < kHeadVals; j += blockDim.x) {
         float s = 0.f;
         for (int k = 0; k < 8; ++k) s += red[k][j];
-        part[(size_t)blockIdx.x * kHeadVals + j] = s;
+        part[(size_t)j * gridDim.x + blockIdx.x] = s;  // value-major: k_head_reduce reads a row
     }
 }
 
 // grad[0..98] = sum of the per-block head sums; *loss = their loss sum / P.
-__global__ void k_head_reduce(const float *__restrict__ part, int nblk, double inv_P, float *__restrict__ grad,
-                              double *__restrict__ loss)
+// Value j = blockIdx.x of the head's block partials (value-major rows of
+// nblk): each thread adds a strided subset in FP64, then a fixed-order tree
+// over the block.
+__global__ void __launch_bounds__(256) k_head_reduce(const float *__restrict__ part, int nblk, double inv_P,
+                                                     float *__restrict__ grad, double *__restrict__ loss)
 {
-    int j = threadIdx.x;
-    if (j >= kHeadVals) return;
+    __shared__ double sh[256];
+    const int j = blockIdx.x;
+    const float *row = part + (size_t)j * nblk;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * kHeadVals + j];
-    if (j < 99) grad[j] = (float)s;
-    else if (loss) *loss = s * inv_P;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += row[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (j < 99)
+            grad[j] = (float)sh[0];
+        else if (loss)
+            *loss = sh[0] * inv_P;
+    }
 }
 
 // ------------------------------------------------------------------ weights
@@ -1521,7 +1577,9 @@ WgradPlan wgrad_plan(long long P, int Cin, int Cout, bool tc)
     w.pix_per_split = (int)(per * 32);
     w.splits = (int)((chunks + per - 1) / per);
     w.part_floats = (long long)w.splits * Cout * 9 * Cin;
-    w.bias_pix = 2048;
+    // bias partial sums: one wave of two blocks per SM (at least 1024 pixels
+    // each)
+    w.bias_pix = (int)std::max(1024LL, ((P + 2 * 152 - 1) / (2 * 152) + 63) / 64 * 64);
     w.bias_blocks = (int)((P + w.bias_pix - 1) / w.bias_pix);
     w.bias_floats = (long long)w.bias_blocks * Cout;
     return w;
@@ -1581,7 +1639,7 @@ cudaError_t wgrad_launch(const ConvSrc &S, const bf16 *dz, int B, int H, int Wd,
     k_sum_parts<<<grid_for(n), 256, 0, st>>>(ws, w.splits, n, dW);
     if (db) {
         float *bp = ws + w.part_floats;
-        k_colsum<<<w.bias_blocks, 256, 0, st>>>(dz, (int)P, Cout, w.bias_pix, bp);
+        k_colsum<<<dim3(w.bias_blocks, (Cout + 255) / 256), 256, 0, st>>>(dz, (int)P, Cout, w.bias_pix, bp);
         k_sum_parts<<<grid_for(Cout), 256, 0, st>>>(bp, w.bias_blocks, Cout, db);
     }
     return cudaGetLastError();
@@ -1909,8 +1967,8 @@ int sp_unet_loss_grad(sp_unet *net, const float *spins_dev, const float *feature
     int nb = (int)((P + 255) / 256);
     k_head<true><<<nb, 256, 0, st>>>(net->act[SP_UNET_LAYERS - 1], net->params + net->off.w[SP_UNET_LAYERS], target_dev,
                                      P, (float)(1.0 / (double)P), nullptr, net->dz[SP_UNET_LAYERS - 1], net->head_part);
-    k_head_reduce<<<1, 128, 0, st>>>(net->head_part, nb, 1.0 / (double)P, net->grad + net->off.w[SP_UNET_LAYERS],
-                                     loss_dev);
+    k_head_reduce<<<kHeadVals, 256, 0, st>>>(net->head_part, nb, 1.0 / (double)P,
+                                             net->grad + net->off.w[SP_UNET_LAYERS], loss_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(net, e, "head");
     e = backward(net, batch, st);

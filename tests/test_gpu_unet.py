@@ -119,6 +119,7 @@ def test_conv_data_gradient(case, kernel):
     (8, 8, 8, 256, 1, 128, 128),
     (1, 16, 16, 128, 0, 0, 256),
     (16, 32, 32, 32, 0, 0, 64),
+    (1, 16, 16, 32, 0, 0, 288),  # the bias sum takes channels in slices of 256
 ])
 def test_conv_weight_gradient(case, kernel):
     B, H, W, C0, up0, C1, Cout = case
