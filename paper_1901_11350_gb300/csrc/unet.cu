@@ -1254,6 +1254,7 @@ __global__ void k_skip_grad(const bf16 *__restrict__ dcat, int C0, int C1, const
 
 // ------------------------------------------------------------------ head
 constexpr int kHeadVals = 3 * 32 + 3 + 1;  // dWh, dbh, loss
+constexpr int kHeadRow = 37;                 // floats per pixel row of k_head's block sums
 
 // Per pixel: y = Wh a + bh, m = y/|y|.  predict: out[p] = (m, 0).  train:
 // loss 1 - m.m_t, dy = -(m_t - (m.m_t) m) / (|y| P), dz[p][c] = (Wh^T dy)_c
@@ -1264,7 +1265,9 @@ __global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ a, const 
                                               float4 *__restrict__ out, bf16 *__restrict__ dz, float *__restrict__ part)
 {
     __shared__ float w[3 * 32 + 3];
-    __shared__ float red[8][kHeadVals];
+    // per-pixel values for the block sums (row of 36 floats, padded to 37
+    // against bank conflicts of the column reads)
+    __shared__ float hv[256 * kHeadRow];
     for (int k = threadIdx.x; k < 3 * 32 + 3; k += blockDim.x) w[k] = Wh[k];
     __syncthreads();
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1316,21 +1319,28 @@ __global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ a, const 
         for (int g = 0; g < 4; ++g)
             *reinterpret_cast<uint4 *>(dz + p * 32 + g * 8) = reinterpret_cast<const uint4 *>(d)[g];
     }
-    // block sums: value j of kHeadVals; warp shuffles, then 8 warps
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = 0; j < kHeadVals; ++j) {
-        float v;
-        if (j < 96) v = dy[j / 32] * av[j % 32];
-        else if (j < 99) v = dy[j - 96];
-        else v = loss;
+    // block sums of value j of kHeadVals (dWh[o][c] = sum dy[o] av[c], dbh[o]
+    // = sum dy[o], the loss): every thread leaves its pixel's 32 activations,
+    // 3 output gradients and loss in shared memory, then thread j adds value
+    // j over the block's pixels in pixel order
+    float *row = hv + threadIdx.x * kHeadRow;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][j] = v;
-    }
+    for (int c = 0; c < 32; ++c) row[c] = av[c];
+    row[32] = dy[0];
+    row[33] = dy[1];
+    row[34] = dy[2];
+    row[35] = loss;
     __syncthreads();
-    for (int j = threadIdx.x; j < kHeadVals; j += blockDim.x) {
+    const int j = threadIdx.x;
+    if (j < kHeadVals) {
         float s = 0.f;
-        for (int k = 0; k < 8; ++k) s += red[k][j];
+        if (j < 96) {
+            const int o = j >> 5, c = j & 31;
+            for (int k = 0; k < (int)blockDim.x; ++k) s = fmaf(hv[k * kHeadRow + 32 + o], hv[k * kHeadRow + c], s);
+        } else {
+            const int col = j < 99 ? 32 + (j - 96) : 35;
+            for (int k = 0; k < (int)blockDim.x; ++k) s += hv[k * kHeadRow + col];
+        }
         part[(size_t)j * gridDim.x + blockIdx.x] = s;  // value-major: k_head_reduce reads a row
     }
 }
